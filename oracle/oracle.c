@@ -1,0 +1,1194 @@
+/*
+ * CPU oracle: plain, sequential, FP64 statement of the fully implicit Newton
+ * step of the paper (TEST INFRASTRUCTURE ONLY -- see oracle.h).
+ *
+ * Everything here is written for a reader checking it against the paper by
+ * eye: one loop per mathematical step, no blocking, no fusion, no threads.
+ * Derivatives are carried by small forward-mode dual numbers, so the
+ * Jacobian is the exact derivative of the residual that the same code
+ * evaluates (and the tests pin it against central finite differences).
+ *
+ * Readings of points the paper leaves open (all shared with the GPU path by
+ * definition, not by code):
+ *  - z is depth, positive downwards.  The well rate Eq. (6) is used as
+ *    printed; the potential of Eq. (4) is taken as Phi = p - rho g z / 1e5
+ *    (bar), i.e. the printed "+" is read as the elevation convention, so that
+ *    a fluid column at rest has no flow.
+ *  - capillary pressure is zero (Sec. 4.1 neglects it).
+ *  - two-point flux with harmonic transmissibility, single-point upstream
+ *    weighting per phase (upstream = the cell of higher potential; a tie goes
+ *    to the lower-index cell), arithmetic mean phase density in the gravity
+ *    term.
+ *  - Peaceman well index for a vertical well in an anisotropic cell; water
+ *    injectors inject water at the cell's total mobility; backflow allowed.
+ *  - primary unknowns (p, Sw) for oil-water and (p, Sw, Sg | pb) for black
+ *    oil with per-cell variable switching (Sec. 2.4.1 lists the unknowns).
+ *  - equations ordered (water, oil, gas) per cell; unknowns (p, Sw, x3).
+ *  - CPR: quasi-IMPES weights w = (1, -d_ps D_ss^-1) from the diagonal block;
+ *    stage P = one aggregation-AMG V(1,1) cycle on the decoupled pressure
+ *    block; stage F = block ILU(0) in red-black order (or block-Jacobi) of
+ *    the decoupled matrix applied to the stage-P residual.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define GRAV 9.80665
+/* Darcy unit factor: q [m3/day] = C k[mD] A[m2] dp[bar] / (mu[cP] L[m]) */
+#define DARCY_C (86400.0 * 9.869233e-16 * 1e5 / 1e-3)
+
+/* ------------------------------------------------------------------------ */
+/* dual numbers: value + gradient with respect to the cell's own unknowns    */
+/* ------------------------------------------------------------------------ */
+typedef struct { double v, d[3]; } dual;
+
+static dual dc(double v) { dual r; r.v = v; r.d[0] = r.d[1] = r.d[2] = 0.0; return r; }
+static dual dv(double v, int k) { dual r = dc(v); r.d[k] = 1.0; return r; }
+static dual dadd(dual a, dual b) { dual r; r.v = a.v + b.v; for (int k = 0; k < 3; k++) r.d[k] = a.d[k] + b.d[k]; return r; }
+static dual dsub(dual a, dual b) { dual r; r.v = a.v - b.v; for (int k = 0; k < 3; k++) r.d[k] = a.d[k] - b.d[k]; return r; }
+static dual dmul(dual a, dual b) { dual r; r.v = a.v * b.v; for (int k = 0; k < 3; k++) r.d[k] = a.d[k] * b.v + a.v * b.d[k]; return r; }
+static dual ddiv(dual a, dual b) {
+    dual r; r.v = a.v / b.v;
+    for (int k = 0; k < 3; k++) r.d[k] = (a.d[k] * b.v - a.v * b.d[k]) / (b.v * b.v);
+    return r;
+}
+static dual dscale(dual a, double s) { dual r; r.v = a.v * s; for (int k = 0; k < 3; k++) r.d[k] = a.d[k] * s; return r; }
+static dual dshift(dual a, double s) { a.v += s; return a; }
+static dual dexp(dual a) { dual r; r.v = exp(a.v); for (int k = 0; k < 3; k++) r.d[k] = r.v * a.d[k]; return r; }
+
+/* normalised saturation clipped to [0, 1], raised to the Corey exponent */
+static dual corey(dual s, double n) {
+    if (s.v <= 0.0) return dc(0.0);
+    if (s.v >= 1.0) return dc(1.0);
+    dual r; r.v = pow(s.v, n);
+    double dr = n * pow(s.v, n - 1.0);
+    for (int k = 0; k < 3; k++) r.d[k] = dr * s.d[k];
+    return r;
+}
+
+/* piecewise-linear table, linear extrapolation beyond the end nodes */
+static dual table(const double *xp, const double *yp, int n, dual x) {
+    int k = 0;
+    while (k + 1 <= n - 2 && x.v >= xp[k + 1]) k++;
+    double slope = (yp[k + 1] - yp[k]) / (xp[k + 1] - xp[k]);
+    return dshift(dscale(dshift(x, -xp[k]), slope), yp[k]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* per-cell properties (Eq. 3-5 ingredients)                                 */
+/* ------------------------------------------------------------------------ */
+enum { PW = 0, PO = 1, PG = 2 };           /* phases */
+enum { CW = 0, CO = 1, CG = 2 };           /* components = equation rows */
+
+typedef struct {
+    dual acc[3];        /* component mass in the cell, kg */
+    dual rho[3];        /* phase mass density, kg/m3 */
+    dual mob[3][3];     /* mob[phase][component] = component density in phase * kr / mu */
+    dual lamt;          /* total mobility sum kr/mu, 1/cP */
+    dual rhow;          /* water mass per water volume */
+    dual kr[3];
+    dual bo, rs, muo;
+    double pv0;
+} cellprops;
+
+/* which components each phase carries */
+static int carries(int model, int a, int c) {
+    if (a == PW) return c == CW;
+    if (a == PO) return c == CO || (model == 3 && c == CG);
+    if (a == PG) return model == 3 && c == CG;
+    return 0;
+}
+
+static void eval_props(const ora_input *in, double poro, double vol, const double *x, int ph, cellprops *o) {
+    memset(o, 0, sizeof(*o));
+    dual P = dv(x[0], 0), SW = dv(x[1], 1);
+    dual phi = dscale(dshift(dscale(dshift(P, -in->p_ref), in->c_rock), 1.0), poro);
+    dual pv = dscale(phi, vol);
+    o->pv0 = poro * vol;
+    if (in->model == 2) {
+        dual rw = dscale(dexp(dscale(dshift(P, -in->p_ref), in->c_w)), in->rho_w_ref);
+        dual ro = dscale(dexp(dscale(dshift(P, -in->p_ref), in->c_o)), in->rho_o_ref);
+        dual se = dscale(dshift(SW, -in->swc), 1.0 / (1.0 - in->swc - in->sor));
+        dual krw = corey(se, in->nw);
+        dual kro = corey(dsub(dc(1.0), se), in->now);
+        dual so = dsub(dc(1.0), SW);
+        o->acc[CW] = dmul(pv, dmul(rw, SW));
+        o->acc[CO] = dmul(pv, dmul(ro, so));
+        o->rho[PW] = rw; o->rho[PO] = ro; o->rho[PG] = dc(0.0);
+        o->mob[PW][CW] = dscale(dmul(rw, krw), 1.0 / in->mu_w);
+        o->mob[PO][CO] = dscale(dmul(ro, kro), 1.0 / in->mu_o);
+        o->lamt = dadd(dscale(krw, 1.0 / in->mu_w), dscale(kro, 1.0 / in->mu_o));
+        o->rhow = rw;
+        o->kr[PW] = krw; o->kr[PO] = kro; o->kr[PG] = dc(0.0);
+        return;
+    }
+    /* black oil */
+    dual SG, BO, RS, MUO;
+    if (ph) {               /* saturated: x3 = Sg, oil at its bubble point */
+        SG = dv(x[2], 2);
+        BO = table(in->pvt_p, in->pvt_bo, in->npvt, P);
+        RS = table(in->pvt_p, in->pvt_rs, in->npvt, P);
+        MUO = table(in->pvt_p, in->pvt_muo, in->npvt, P);
+    } else {                /* undersaturated: x3 = pb, no free gas */
+        dual PB = dv(x[2], 2);
+        SG = dc(0.0);
+        dual dpu = dsub(P, PB);
+        BO = dmul(table(in->pvt_p, in->pvt_bo, in->npvt, PB), dsub(dc(1.0), dscale(dpu, in->bo_c_us)));
+        RS = table(in->pvt_p, in->pvt_rs, in->npvt, PB);
+        MUO = dmul(table(in->pvt_p, in->pvt_muo, in->npvt, PB), dadd(dc(1.0), dscale(dpu, in->muo_c_us)));
+    }
+    dual bwi = dshift(dscale(dshift(P, -in->bw_pref), in->bw_c), 1.0);          /* 1/Bw */
+    dual boi = ddiv(dc(1.0), BO);                                              /* 1/Bo */
+    dual bgi = ddiv(dc(1.0), table(in->pvt_p, in->pvt_bg, in->npvt, P));      /* 1/Bg */
+    dual MUG = table(in->pvt_p, in->pvt_mug, in->npvt, P);
+    dual SO = dsub(dsub(dc(1.0), SW), SG);
+
+    /* Corey two-phase curves and Stone II (normalised so that krow(Swc) = 1) */
+    dual krw = corey(dscale(dshift(SW, -in->swc), 1.0 / (1.0 - in->swc - in->sor)), in->nw);
+    dual krow = corey(dscale(dsub(dc(1.0 - in->sor), SW), 1.0 / (1.0 - in->swc - in->sor)), in->now);
+    dual krg = corey(dscale(dshift(SG, -in->sgc), 1.0 / (1.0 - in->swc - in->sorg - in->sgc)), in->ng);
+    dual krog = corey(dscale(dsub(dc(1.0 - in->swc - in->sorg), SG), 1.0 / (1.0 - in->swc - in->sorg)), in->nog);
+    dual kro = dsub(dmul(dadd(krow, krw), dadd(krog, krg)), dadd(krw, krg));
+    if (kro.v < 0.0) kro = dc(0.0);
+
+    o->acc[CW] = dmul(pv, dscale(dmul(bwi, SW), in->rho_ws));
+    o->acc[CO] = dmul(pv, dscale(dmul(boi, SO), in->rho_os));
+    o->acc[CG] = dmul(pv, dscale(dadd(dmul(RS, dmul(boi, SO)), dmul(bgi, SG)), in->rho_gs));
+    o->rho[PW] = dscale(bwi, in->rho_ws);
+    o->rho[PO] = dmul(dshift(dscale(RS, in->rho_gs), in->rho_os), boi);
+    o->rho[PG] = dscale(bgi, in->rho_gs);
+    dual lw = dscale(krw, 1.0 / in->mu_w);
+    dual lo = ddiv(kro, MUO);
+    dual lg = ddiv(krg, MUG);
+    o->mob[PW][CW] = dmul(o->rho[PW], lw);
+    o->mob[PO][CO] = dmul(dscale(boi, in->rho_os), lo);
+    o->mob[PO][CG] = dmul(dscale(dmul(RS, boi), in->rho_gs), lo);
+    o->mob[PG][CG] = dmul(o->rho[PG], lg);
+    o->lamt = dadd(dadd(lw, lo), lg);
+    o->rhow = o->rho[PW];
+    o->kr[PW] = krw; o->kr[PO] = kro; o->kr[PG] = krg;
+    o->bo = BO; o->rs = RS; o->muo = MUO;
+}
+
+/* ------------------------------------------------------------------------ */
+/* simulator state                                                           */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int n, nnz;
+    int32_t *rowptr, *col;
+    double *val, *dl1;
+    int32_t *agg;       /* fine -> next level (absent on the coarsest) */
+    int32_t *mem4;      /* next-level aggregate -> up to 4 members of this level */
+    double *lu;         /* coarsest: dense LU factors */
+    int32_t *piv;
+    double *t1, *t2, *t3;
+} level_t;
+
+struct ora_sim {
+    ora_input in;
+    double *kx, *ky, *kz, *poro, *pvt[6];
+    int32_t *wi_, *wj_, *wk0, *wk1, *wt;
+    double *wbhp, *wrw, *wskin;
+    int N, b;
+    double vol;
+    double *T[3];       /* transmissibility to the + neighbour in x, y, z */
+    double *depth;
+    int nperf;
+    int32_t *perf_cell, *perf_type;
+    double *perf_wi, *perf_zh, *perf_bhp;
+    double *x, *x_old; int8_t *ph, *ph_old;
+    double *mold;
+    double *R, *J;
+    double qtot[3], cum_well[3];
+    cellprops *props;
+    /* CPR */
+    double *qiw, *ahat, *dinv;
+    int nlev;
+    level_t lev[32];
+    int precond_ready;
+    /* Krylov workspace */
+    double *V, *Z, *w, *r, *tmp, *tmp2, *tmp3;
+    double *H, *g, *cs, *sn, *y;
+};
+
+static void *xmalloc(size_t n) { void *p = calloc(n ? n : 1, 1); if (!p) { fprintf(stderr, "oracle: out of memory\n"); abort(); } return p; }
+static double *dup_d(const double *a, int n) { double *r = xmalloc(sizeof(double) * n); memcpy(r, a, sizeof(double) * n); return r; }
+static int32_t *dup_i(const int32_t *a, int n) { int32_t *r = xmalloc(sizeof(int32_t) * (n ? n : 1)); if (n) memcpy(r, a, sizeof(int32_t) * n); return r; }
+
+static void cell_ijk(const ora_sim *s, int i, int *ix, int *iy, int *iz) {
+    *ix = i % s->in.nx; *iy = (i / s->in.nx) % s->in.ny; *iz = i / (s->in.nx * s->in.ny);
+}
+
+/* neighbour of cell i in direction d (1..6), or -1 outside the grid */
+static int nbr(const ora_sim *s, int i, int d) {
+    int ix, iy, iz; cell_ijk(s, i, &ix, &iy, &iz);
+    int nx = s->in.nx, ny = s->in.ny, nz = s->in.nz;
+    switch (d) {
+    case 0: return i;
+    case 1: return ix > 0 ? i - 1 : -1;
+    case 2: return ix < nx - 1 ? i + 1 : -1;
+    case 3: return iy > 0 ? i - nx : -1;
+    case 4: return iy < ny - 1 ? i + nx : -1;
+    case 5: return iz > 0 ? i - nx * ny : -1;
+    case 6: return iz < nz - 1 ? i + nx * ny : -1;
+    }
+    return -1;
+}
+static int opp(int d) { return d == 0 ? 0 : (d % 2 ? d + 1 : d - 1); }
+
+#define JB(s, i, d) (&(s)->J[(((size_t)(i) * 7 + (d)) * (s)->b) * (s)->b])
+#define AH(s, i, d) (&(s)->ahat[(((size_t)(i) * 7 + (d)) * (s)->b) * (s)->b])
+
+ora_sim *ora_create(const ora_input *in) {
+    ora_sim *s = xmalloc(sizeof(ora_sim));
+    s->in = *in;
+    int N = in->nx * in->ny * in->nz;
+    s->N = N; s->b = in->model == 3 ? 3 : 2;
+    s->kx = dup_d(in->kx, N); s->ky = dup_d(in->ky, N); s->kz = dup_d(in->kz, N); s->poro = dup_d(in->poro, N);
+    s->in.kx = s->kx; s->in.ky = s->ky; s->in.kz = s->kz; s->in.poro = s->poro;
+    if (in->model == 3) {
+        const double *src[6] = {in->pvt_p, in->pvt_bo, in->pvt_rs, in->pvt_muo, in->pvt_bg, in->pvt_mug};
+        for (int t = 0; t < 6; t++) s->pvt[t] = dup_d(src[t], in->npvt);
+        s->in.pvt_p = s->pvt[0]; s->in.pvt_bo = s->pvt[1]; s->in.pvt_rs = s->pvt[2];
+        s->in.pvt_muo = s->pvt[3]; s->in.pvt_bg = s->pvt[4]; s->in.pvt_mug = s->pvt[5];
+    }
+    int nw = in->nwells;
+    s->wi_ = dup_i(in->w_i, nw); s->wj_ = dup_i(in->w_j, nw); s->wk0 = dup_i(in->w_k0, nw);
+    s->wk1 = dup_i(in->w_k1, nw); s->wt = dup_i(in->w_type, nw);
+    s->wbhp = dup_d(in->w_bhp, nw ? nw : 1); s->wrw = dup_d(in->w_rw, nw ? nw : 1); s->wskin = dup_d(in->w_skin, nw ? nw : 1);
+    s->in.w_i = s->wi_; s->in.w_j = s->wj_; s->in.w_k0 = s->wk0; s->in.w_k1 = s->wk1; s->in.w_type = s->wt;
+    s->in.w_bhp = s->wbhp; s->in.w_rw = s->wrw; s->in.w_skin = s->wskin;
+
+    int nx = in->nx, ny = in->ny, nz = in->nz;
+    double dx = in->dx, dy = in->dy, dz = in->dz;
+    s->vol = dx * dy * dz;
+    /* Eq. (11): geometric part of the transmissibility, harmonic average of
+       the two half-cell conductances */
+    for (int a = 0; a < 3; a++) s->T[a] = xmalloc(sizeof(double) * N);
+    s->depth = xmalloc(sizeof(double) * N);
+    for (int i = 0; i < N; i++) {
+        int ix, iy, iz; cell_ijk(s, i, &ix, &iy, &iz);
+        s->depth[i] = in->top_depth + (iz + 0.5) * dz;
+        if (ix < nx - 1) s->T[0][i] = DARCY_C * 2.0 * dy * dz / (dx / s->kx[i] + dx / s->kx[i + 1]);
+        if (iy < ny - 1) s->T[1][i] = DARCY_C * 2.0 * dx * dz / (dy / s->ky[i] + dy / s->ky[i + nx]);
+        if (iz < nz - 1) s->T[2][i] = DARCY_C * 2.0 * dx * dy / (dz / s->kz[i] + dz / s->kz[i + nx * ny]);
+    }
+    /* perforations with the Peaceman well index (vertical well) */
+    int np = 0;
+    for (int w = 0; w < nw; w++) np += s->wk1[w] - s->wk0[w] + 1;
+    s->nperf = np;
+    s->perf_cell = xmalloc(sizeof(int32_t) * (np + 1)); s->perf_type = xmalloc(sizeof(int32_t) * (np + 1));
+    s->perf_wi = xmalloc(sizeof(double) * (np + 1)); s->perf_zh = xmalloc(sizeof(double) * (np + 1));
+    s->perf_bhp = xmalloc(sizeof(double) * (np + 1));
+    np = 0;
+    for (int w = 0; w < nw; w++) {
+        double zh = in->top_depth + (s->wk0[w] + 0.5) * dz;
+        for (int k = s->wk0[w]; k <= s->wk1[w]; k++) {
+            int c = s->wi_[w] + nx * (s->wj_[w] + ny * k);
+            double kxx = s->kx[c], kyy = s->ky[c];
+            double ro = 0.28 * sqrt(sqrt(kyy / kxx) * dx * dx + sqrt(kxx / kyy) * dy * dy)
+                        / (pow(kyy / kxx, 0.25) + pow(kxx / kyy, 0.25));
+            s->perf_cell[np] = c;
+            s->perf_type[np] = s->wt[w];
+            s->perf_wi[np] = 2.0 * M_PI * DARCY_C * sqrt(kxx * kyy) * dz / (log(ro / s->wrw[w]) + s->wskin[w]);
+            s->perf_zh[np] = zh;
+            s->perf_bhp[np] = s->wbhp[w];
+            np++;
+        }
+    }
+    int b = s->b;
+    s->x = xmalloc(sizeof(double) * N * b); s->x_old = xmalloc(sizeof(double) * N * b);
+    s->ph = xmalloc(N); s->ph_old = xmalloc(N);
+    s->mold = xmalloc(sizeof(double) * N * b);
+    s->R = xmalloc(sizeof(double) * N * b);
+    s->J = xmalloc(sizeof(double) * (size_t)N * 7 * b * b);
+    s->props = xmalloc(sizeof(cellprops) * N);
+    s->qiw = xmalloc(sizeof(double) * N * b);
+    s->ahat = xmalloc(sizeof(double) * (size_t)N * 7 * b * b);
+    s->dinv = xmalloc(sizeof(double) * (size_t)N * b * b);
+    int m = in->gmres_m, n = N * b;
+    s->V = xmalloc(sizeof(double) * (size_t)(m + 1) * n);
+    s->Z = xmalloc(sizeof(double) * (size_t)m * n);
+    s->w = xmalloc(sizeof(double) * n); s->r = xmalloc(sizeof(double) * n);
+    s->tmp = xmalloc(sizeof(double) * n); s->tmp2 = xmalloc(sizeof(double) * n); s->tmp3 = xmalloc(sizeof(double) * n);
+    s->H = xmalloc(sizeof(double) * (m + 1) * (m + 1));
+    s->g = xmalloc(sizeof(double) * (m + 1)); s->cs = xmalloc(sizeof(double) * (m + 1));
+    s->sn = xmalloc(sizeof(double) * (m + 1)); s->y = xmalloc(sizeof(double) * (m + 1));
+    return s;
+}
+
+static void free_levels(ora_sim *s) {
+    for (int l = 0; l < s->nlev; l++) {
+        level_t *L = &s->lev[l];
+        free(L->rowptr); free(L->col); free(L->val); free(L->dl1); free(L->agg); free(L->mem4);
+        free(L->lu); free(L->piv); free(L->t1); free(L->t2); free(L->t3);
+        memset(L, 0, sizeof(*L));
+    }
+    s->nlev = 0;
+}
+
+void ora_destroy(ora_sim *s) {
+    if (!s) return;
+    free_levels(s);
+    free(s->kx); free(s->ky); free(s->kz); free(s->poro);
+    for (int t = 0; t < 6; t++) free(s->pvt[t]);
+    free(s->wi_); free(s->wj_); free(s->wk0); free(s->wk1); free(s->wt); free(s->wbhp); free(s->wrw); free(s->wskin);
+    for (int a = 0; a < 3; a++) free(s->T[a]);
+    free(s->depth); free(s->perf_cell); free(s->perf_type); free(s->perf_wi); free(s->perf_zh); free(s->perf_bhp);
+    free(s->x); free(s->x_old); free(s->ph); free(s->ph_old); free(s->mold); free(s->R); free(s->J); free(s->props);
+    free(s->qiw); free(s->ahat); free(s->dinv);
+    free(s->V); free(s->Z); free(s->w); free(s->r); free(s->tmp); free(s->tmp2); free(s->tmp3);
+    free(s->H); free(s->g); free(s->cs); free(s->sn); free(s->y);
+    free(s);
+}
+
+int ora_block_size(const ora_sim *s) { return s->b; }
+
+/* accumulation of the last accepted state (the f^n of Eq. 10) */
+static void begin_step(ora_sim *s) {
+    int b = s->b;
+    memcpy(s->x_old, s->x, sizeof(double) * s->N * b);
+    memcpy(s->ph_old, s->ph, s->N);
+    for (int i = 0; i < s->N; i++) {
+        cellprops cp;
+        eval_props(&s->in, s->poro[i], s->vol, &s->x[i * b], s->ph[i], &cp);
+        for (int c = 0; c < b; c++) s->mold[i * b + c] = cp.acc[c].v;
+    }
+}
+
+void ora_set_state(ora_sim *s, const double *p, const double *sw, const double *x3, const int8_t *ph) {
+    int b = s->b;
+    for (int i = 0; i < s->N; i++) {
+        s->x[i * b] = p[i]; s->x[i * b + 1] = sw[i];
+        if (b == 3) s->x[i * b + 2] = x3[i];
+        s->ph[i] = b == 3 ? ph[i] : 1;
+    }
+    begin_step(s);
+    s->cum_well[0] = s->cum_well[1] = s->cum_well[2] = 0.0;
+}
+
+void ora_get_state(const ora_sim *s, double *p, double *sw, double *x3, int8_t *ph) {
+    int b = s->b;
+    for (int i = 0; i < s->N; i++) {
+        p[i] = s->x[i * b]; sw[i] = s->x[i * b + 1];
+        x3[i] = b == 3 ? s->x[i * b + 2] : 0.0;
+        ph[i] = s->ph[i];
+    }
+}
+
+void ora_set_iterate(ora_sim *s, const double *x, const int8_t *ph) {
+    memcpy(s->x, x, sizeof(double) * s->N * s->b);
+    memcpy(s->ph, ph, s->N);
+}
+void ora_get_iterate(const ora_sim *s, double *x, int8_t *ph) {
+    memcpy(x, s->x, sizeof(double) * s->N * s->b);
+    memcpy(ph, s->ph, s->N);
+}
+
+/* ------------------------------------------------------------------------ */
+/* residual and Jacobian (Eq. 3/5 discretised by Eq. 10-11, wells Eq. 6-7)   */
+/* ------------------------------------------------------------------------ */
+void ora_assemble(ora_sim *s, double dt) {
+    const ora_input *in = &s->in;
+    int N = s->N, b = s->b, np = in->model == 3 ? 3 : 2;
+    memset(s->R, 0, sizeof(double) * N * b);
+    memset(s->J, 0, sizeof(double) * (size_t)N * 7 * b * b);
+    for (int i = 0; i < N; i++) eval_props(in, s->poro[i], s->vol, &s->x[i * b], s->ph[i], &s->props[i]);
+
+    /* accumulation (f^{n+1} - f^n) / dt */
+    for (int i = 0; i < N; i++) {
+        double *D = JB(s, i, 0);
+        for (int c = 0; c < b; c++) {
+            s->R[i * b + c] += (s->props[i].acc[c].v - s->mold[i * b + c]) / dt;
+            for (int k = 0; k < b; k++) D[c * b + k] += s->props[i].acc[c].d[k] / dt;
+        }
+    }
+    /* inter-cell fluxes, each face once in the orientation (L, R = L + stride) */
+    int strides[3] = {1, in->nx, in->nx * in->ny};
+    for (int L = 0; L < N; L++) {
+        for (int a = 0; a < 3; a++) {
+            int Rr = nbr(s, L, 2 * a + 2);
+            if (Rr < 0) continue;
+            (void)strides;
+            double T = s->T[a][L];
+            const cellprops *PL = &s->props[L], *PR = &s->props[Rr];
+            double gdz = GRAV * (s->depth[Rr] - s->depth[L]) / 1e5;
+            for (int ph = 0; ph < np; ph++) {
+                double rbar = 0.5 * (PL->rho[ph].v + PR->rho[ph].v);
+                double dphi = (s->x[Rr * b] - s->x[L * b]) - rbar * gdz;
+                double dphiL[3], dphiR[3];
+                for (int k = 0; k < 3; k++) {
+                    dphiL[k] = -gdz * 0.5 * PL->rho[ph].d[k];
+                    dphiR[k] = -gdz * 0.5 * PR->rho[ph].d[k];
+                }
+                dphiL[0] -= 1.0; dphiR[0] += 1.0;
+                int upR = dphi > 0.0;
+                const cellprops *PU = upR ? PR : PL;
+                for (int c = 0; c < b; c++) {
+                    if (!carries(in->model, ph, c)) continue;
+                    const dual *m = &PU->mob[ph][c];
+                    double F = T * m->v * dphi;
+                    double dFL[3], dFR[3];
+                    for (int k = 0; k < b; k++) {
+                        dFL[k] = T * ((upR ? 0.0 : m->d[k] * dphi) + m->v * dphiL[k]);
+                        dFR[k] = T * ((upR ? m->d[k] * dphi : 0.0) + m->v * dphiR[k]);
+                    }
+                    /* F flows from R into L */
+                    s->R[L * b + c] -= F;
+                    s->R[Rr * b + c] += F;
+                    double *JLL = JB(s, L, 0), *JLR = JB(s, L, 2 * a + 2);
+                    double *JRR = JB(s, Rr, 0), *JRL = JB(s, Rr, 2 * a + 1);
+                    for (int k = 0; k < b; k++) {
+                        JLL[c * b + k] -= dFL[k];
+                        JLR[c * b + k] -= dFR[k];
+                        JRR[c * b + k] += dFR[k];
+                        JRL[c * b + k] += dFL[k];
+                    }
+                }
+            }
+        }
+    }
+    /* wells under bottom-hole-pressure control, Eq. (6)-(7) */
+    s->qtot[0] = s->qtot[1] = s->qtot[2] = 0.0;
+    for (int q = 0; q < s->nperf; q++) {
+        int i = s->perf_cell[q];
+        const cellprops *P = &s->props[i];
+        double WI = s->perf_wi[q];
+        double dh = GRAV * (s->perf_zh[q] - s->depth[i]) / 1e5;
+        double p = s->x[i * b];
+        double *D = JB(s, i, 0);
+        if (s->perf_type[q] == 1) {
+            /* water injector: water at the cell's total mobility */
+            double Dw = s->perf_bhp[q] - p - P->rho[PW].v * dh;
+            dual lam = dmul(P->rhow, P->lamt);
+            double qw = WI * lam.v * Dw;
+            s->R[i * b + CW] -= qw;
+            s->qtot[CW] += qw;
+            for (int k = 0; k < b; k++) {
+                double dD = (k == 0 ? -1.0 : 0.0) - P->rho[PW].d[k] * dh;
+                D[CW * b + k] -= WI * (lam.d[k] * Dw + lam.v * dD);
+            }
+        } else {
+            for (int ph = 0; ph < np; ph++) {
+                double Dp = s->perf_bhp[q] - p - P->rho[ph].v * dh;
+                for (int c = 0; c < b; c++) {
+                    if (!carries(in->model, ph, c)) continue;
+                    const dual *m = &P->mob[ph][c];
+                    double qc = WI * m->v * Dp;
+                    s->R[i * b + c] -= qc;
+                    s->qtot[c] += qc;
+                    for (int k = 0; k < b; k++) {
+                        double dD = (k == 0 ? -1.0 : 0.0) - P->rho[ph].d[k] * dh;
+                        D[c * b + k] -= WI * (m->d[k] * Dp + m->v * dD);
+                    }
+                }
+            }
+        }
+    }
+    s->precond_ready = 0;
+}
+
+void ora_get_residual(const ora_sim *s, double *R) { memcpy(R, s->R, sizeof(double) * s->N * s->b); }
+void ora_get_jacobian(const ora_sim *s, double *J) { memcpy(J, s->J, sizeof(double) * (size_t)s->N * 7 * s->b * s->b); }
+void ora_set_jacobian(ora_sim *s, const double *J) {
+    memcpy(s->J, J, sizeof(double) * (size_t)s->N * 7 * s->b * s->b);
+    s->precond_ready = 0;
+}
+
+/* CNV: largest component residual in pore-volume-saturation units */
+double ora_cnv(const ora_sim *s, double dt) {
+    double m = 0.0;
+    for (int i = 0; i < s->N; i++) {
+        double pv0 = s->poro[i] * s->vol;
+        for (int c = 0; c < s->b; c++) {
+            double v = fabs(s->R[i * s->b + c]) * dt / (pv0 * s->in.cnv_rho[c]);
+            if (!(v <= m)) m = v;       /* NaN propagates */
+        }
+    }
+    return m;
+}
+
+void ora_component_mass(const ora_sim *s, double *m) {
+    m[0] = m[1] = m[2] = 0.0;
+    for (int i = 0; i < s->N; i++) {
+        cellprops cp;
+        eval_props(&s->in, s->poro[i], s->vol, &s->x[i * s->b], s->ph[i], &cp);
+        for (int c = 0; c < s->b; c++) m[c] += cp.acc[c].v;
+    }
+}
+void ora_cumulative_well_mass(const ora_sim *s, double *m) { for (int c = 0; c < 3; c++) m[c] = s->cum_well[c]; }
+void ora_well_rates(const ora_sim *s, double *q) { for (int c = 0; c < 3; c++) q[c] = s->qtot[c]; }
+
+/* ------------------------------------------------------------------------ */
+/* small dense algebra                                                       */
+/* ------------------------------------------------------------------------ */
+static void inv_block(int b, const double *A, double *Ai) {
+    if (b == 2) {
+        double det = A[0] * A[3] - A[1] * A[2];
+        Ai[0] = A[3] / det; Ai[1] = -A[1] / det; Ai[2] = -A[2] / det; Ai[3] = A[0] / det;
+    } else {
+        double c00 = A[4] * A[8] - A[5] * A[7];
+        double c01 = A[5] * A[6] - A[3] * A[8];
+        double c02 = A[3] * A[7] - A[4] * A[6];
+        double det = A[0] * c00 + A[1] * c01 + A[2] * c02;
+        Ai[0] = c00 / det; Ai[1] = (A[2] * A[7] - A[1] * A[8]) / det; Ai[2] = (A[1] * A[5] - A[2] * A[4]) / det;
+        Ai[3] = c01 / det; Ai[4] = (A[0] * A[8] - A[2] * A[6]) / det; Ai[5] = (A[2] * A[3] - A[0] * A[5]) / det;
+        Ai[6] = c02 / det; Ai[7] = (A[1] * A[6] - A[0] * A[7]) / det; Ai[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+    }
+}
+static void matmul_block(int b, const double *A, const double *B, double *C) {
+    for (int r = 0; r < b; r++)
+        for (int c = 0; c < b; c++) {
+            double t = 0.0;
+            for (int k = 0; k < b; k++) t += A[r * b + k] * B[k * b + c];
+            C[r * b + c] = t;
+        }
+}
+static void matvec_block(int b, const double *A, const double *x, double *y) {
+    for (int r = 0; r < b; r++) { double t = 0.0; for (int k = 0; k < b; k++) t += A[r * b + k] * x[k]; y[r] = t; }
+}
+
+/* dense LU with partial pivoting, row-major, in place; returns 0 on success */
+static int lu_factor(int n, double *A, int32_t *piv) {
+    for (int k = 0; k < n; k++) {
+        int p = k; double best = fabs(A[(size_t)k * n + k]);
+        for (int i = k + 1; i < n; i++) if (fabs(A[(size_t)i * n + k]) > best) { best = fabs(A[(size_t)i * n + k]); p = i; }
+        piv[k] = p;
+        if (best == 0.0) return -1;
+        if (p != k) for (int j = 0; j < n; j++) { double t = A[(size_t)k * n + j]; A[(size_t)k * n + j] = A[(size_t)p * n + j]; A[(size_t)p * n + j] = t; }
+        for (int i = k + 1; i < n; i++) {
+            double l = A[(size_t)i * n + k] / A[(size_t)k * n + k];
+            A[(size_t)i * n + k] = l;
+            for (int j = k + 1; j < n; j++) A[(size_t)i * n + j] -= l * A[(size_t)k * n + j];
+        }
+    }
+    return 0;
+}
+static void lu_solve(int n, const double *LU, const int32_t *piv, double *x) {
+    for (int k = 0; k < n; k++) if (piv[k] != k) { double t = x[k]; x[k] = x[piv[k]]; x[piv[k]] = t; }
+    for (int i = 0; i < n; i++) { double t = x[i]; for (int j = 0; j < i; j++) t -= LU[(size_t)i * n + j] * x[j]; x[i] = t; }
+    for (int i = n - 1; i >= 0; i--) { double t = x[i]; for (int j = i + 1; j < n; j++) t -= LU[(size_t)i * n + j] * x[j]; x[i] = t / LU[(size_t)i * n + i]; }
+}
+int ora_dense_lu_solve(int n, double *A, double *b) {
+    int32_t *piv = xmalloc(sizeof(int32_t) * n);
+    int rc = lu_factor(n, A, piv);
+    if (rc == 0) lu_solve(n, A, piv, b);
+    free(piv);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* sparse matrix-vector product with the 7-point block Jacobian              */
+/* ------------------------------------------------------------------------ */
+static void block_spmv(const ora_sim *s, const double *A, const double *x, double *y) {
+    int b = s->b;
+    for (int i = 0; i < s->N; i++) {
+        double acc[3] = {0, 0, 0}, t[3];
+        for (int d = 0; d < 7; d++) {
+            int j = nbr(s, i, d);
+            if (j < 0) continue;
+            matvec_block(b, &A[(((size_t)i * 7 + d) * b) * b], &x[j * b], t);
+            for (int r = 0; r < b; r++) acc[r] += t[r];
+        }
+        for (int r = 0; r < b; r++) y[i * b + r] = acc[r];
+    }
+}
+void ora_spmv(const ora_sim *s, const double *x, double *y) { block_spmv(s, s->J, x, y); }
+
+/* ------------------------------------------------------------------------ */
+/* aggregation AMG on the pressure block                                     */
+/* ------------------------------------------------------------------------ */
+/* splitmix64 finaliser, used only to break exact ties between equal edge
+   strengths deterministically (a symmetric key of the unordered pair) */
+static uint64_t edge_hash(int a, int b) {
+    uint64_t lo = (uint64_t)(a < b ? a : b), hi = (uint64_t)(a < b ? b : a);
+    uint64_t z = ((hi << 32) | lo) + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* strength band of a positive coupling: its binary exponent (one band per
+   factor of two), read from the IEEE-754 bit pattern */
+static int strength_band(double a) {
+    uint64_t u; memcpy(&u, &a, sizeof(u));
+    return (int)((u >> 52) & 0x7FF);
+}
+
+/* one matching pass: rounds of handshakes among unmatched nodes.  In each
+   round every unmatched node picks, among its unmatched strong neighbours
+   (strong: -a_ij >= theta * max_k -a_ik), the one in the highest strength
+   band, ties broken by the larger pair hash, then by the smaller index;
+   mutual picks become pairs.  partner[i] = -1 for nodes left single. */
+int ora_match_pass(int n, const int32_t *rowptr, const int32_t *col, const double *val,
+                   double theta, int rounds, int32_t *partner) {
+    int32_t *pick = xmalloc(sizeof(int32_t) * (n ? n : 1));
+    for (int i = 0; i < n; i++) partner[i] = -1;
+    int done_rounds = 0;
+    for (int r = 0; r < rounds; r++) {
+        for (int i = 0; i < n; i++) {
+            pick[i] = -1;
+            if (partner[i] >= 0) continue;
+            double mx = 0.0;
+            for (int k = rowptr[i]; k < rowptr[i + 1]; k++)
+                if (col[k] != i && -val[k] > mx) mx = -val[k];
+            if (mx <= 0.0) continue;
+            int best = -1, bs = 0; uint64_t bh = 0;
+            for (int k = rowptr[i]; k < rowptr[i + 1]; k++) {
+                int j = col[k];
+                if (j == i || partner[j] >= 0) continue;
+                double a = -val[k];
+                if (!(a > 0.0) || a < theta * mx) continue;
+                int band = strength_band(a);
+                uint64_t h = edge_hash(i, j);
+                if (best < 0 || band > bs || (band == bs && (h > bh || (h == bh && j < best)))) { best = j; bs = band; bh = h; }
+            }
+            pick[i] = best;
+        }
+        int any = 0;
+        for (int i = 0; i < n; i++)
+            if (partner[i] < 0 && pick[i] >= 0 && pick[pick[i]] == i) { partner[i] = pick[i]; any = 1; }
+        done_rounds++;
+        if (!any) break;
+    }
+    free(pick);
+    return done_rounds;
+}
+
+/* number the pairs/singletons by their lowest member */
+static int number_aggregates(int n, const int32_t *partner, int32_t *agg, int32_t *mem2) {
+    int nc = 0;
+    for (int i = 0; i < n; i++) {
+        int p = partner[i];
+        if (p < 0 || i < p) { mem2[2 * nc] = i; mem2[2 * nc + 1] = p; agg[i] = nc; if (p >= 0) agg[p] = nc; nc++; }
+    }
+    return nc;
+}
+
+/* Galerkin product P^T A P for piecewise-constant P: coarse row I sums the
+   rows of its members (in member order, then column order) into columns
+   agg[j]; coarse columns sorted ascending */
+static void galerkin(int n, const int32_t *rowptr, const int32_t *col, const double *val,
+                     const int32_t *agg, const int32_t *mem, int memw, int nc,
+                     int32_t **rp_out, int32_t **col_out, double **val_out) {
+    int cap = 64;
+    int32_t *cols = xmalloc(sizeof(int32_t) * cap); double *vals = xmalloc(sizeof(double) * cap);
+    int32_t *rp = xmalloc(sizeof(int32_t) * (nc + 1));
+    size_t nnzcap = (size_t)rowptr[n] + 16, nnz = 0;
+    int32_t *oc = xmalloc(sizeof(int32_t) * nnzcap); double *ov = xmalloc(sizeof(double) * nnzcap);
+    (void)n;
+    for (int I = 0; I < nc; I++) {
+        int cnt = 0;
+        for (int s = 0; s < memw; s++) {
+            int m = mem[(size_t)I * memw + s];
+            if (m < 0) continue;
+            for (int k = rowptr[m]; k < rowptr[m + 1]; k++) {
+                int Jc = agg[col[k]], f = -1;
+                for (int t = 0; t < cnt; t++) if (cols[t] == Jc) { f = t; break; }
+                if (f < 0) {
+                    if (cnt == cap) { cap *= 2; cols = realloc(cols, sizeof(int32_t) * cap); vals = realloc(vals, sizeof(double) * cap); }
+                    cols[cnt] = Jc; vals[cnt] = 0.0; f = cnt++;
+                }
+                vals[f] += val[k];
+            }
+        }
+        /* insertion sort by column */
+        for (int a = 1; a < cnt; a++) {
+            int cj = cols[a]; double cv = vals[a]; int t = a - 1;
+            while (t >= 0 && cols[t] > cj) { cols[t + 1] = cols[t]; vals[t + 1] = vals[t]; t--; }
+            cols[t + 1] = cj; vals[t + 1] = cv;
+        }
+        rp[I] = (int32_t)nnz;
+        if (nnz + cnt > nnzcap) { nnzcap = 2 * (nnz + cnt); oc = realloc(oc, sizeof(int32_t) * nnzcap); ov = realloc(ov, sizeof(double) * nnzcap); }
+        for (int t = 0; t < cnt; t++) { oc[nnz] = cols[t]; ov[nnz] = vals[t]; nnz++; }
+    }
+    rp[nc] = (int32_t)nnz;
+    free(cols); free(vals);
+    *rp_out = rp; *col_out = oc; *val_out = ov;
+}
+
+static void level_finish(level_t *L) {
+    L->dl1 = xmalloc(sizeof(double) * L->n);
+    for (int i = 0; i < L->n; i++) {
+        double t = 0.0;
+        for (int k = L->rowptr[i]; k < L->rowptr[i + 1]; k++) t += fabs(L->val[k]);
+        L->dl1[i] = t;
+    }
+    L->nnz = L->rowptr[L->n];
+    L->t1 = xmalloc(sizeof(double) * L->n); L->t2 = xmalloc(sizeof(double) * L->n); L->t3 = xmalloc(sizeof(double) * L->n);
+}
+
+static void amg_setup(ora_sim *s, int32_t *rp0, int32_t *col0, double *val0, int n0) {
+    free_levels(s);
+    const ora_input *in = &s->in;
+    level_t *L = &s->lev[0];
+    L->n = n0; L->rowptr = rp0; L->col = col0; L->val = val0;
+    level_finish(L);
+    s->nlev = 1;
+    while (1) {
+        L = &s->lev[s->nlev - 1];
+        if (L->n <= in->amg_coarse_max || s->nlev >= in->amg_max_levels || s->nlev >= 32) break;
+        int n = L->n;
+        int32_t *p1 = xmalloc(sizeof(int32_t) * n), *agg1 = xmalloc(sizeof(int32_t) * n), *mem1 = xmalloc(sizeof(int32_t) * 2 * n);
+        ora_match_pass(n, L->rowptr, L->col, L->val, in->amg_theta, in->amg_rounds, p1);
+        int n1 = number_aggregates(n, p1, agg1, mem1);
+        int32_t *rp1, *c1; double *v1;
+        galerkin(n, L->rowptr, L->col, L->val, agg1, mem1, 2, n1, &rp1, &c1, &v1);
+        int32_t *p2 = xmalloc(sizeof(int32_t) * n1), *agg2 = xmalloc(sizeof(int32_t) * n1), *mem2 = xmalloc(sizeof(int32_t) * 2 * n1);
+        ora_match_pass(n1, rp1, c1, v1, in->amg_theta, in->amg_rounds, p2);
+        int n2 = number_aggregates(n1, p2, agg2, mem2);
+        if (4 * (long)n2 > 3 * (long)n) {  /* coarsening stalled (> 3/4 kept): this level is the coarsest */
+            free(p1); free(agg1); free(mem1); free(rp1); free(c1); free(v1); free(p2); free(agg2); free(mem2);
+            break;
+        }
+        level_t *C = &s->lev[s->nlev];
+        galerkin(n1, rp1, c1, v1, agg2, mem2, 2, n2, &C->rowptr, &C->col, &C->val);
+        C->n = n2;
+        L->agg = xmalloc(sizeof(int32_t) * n);
+        for (int i = 0; i < n; i++) L->agg[i] = agg2[agg1[i]];
+        L->mem4 = xmalloc(sizeof(int32_t) * 4 * n2);
+        for (int I = 0; I < n2; I++)
+            for (int a = 0; a < 2; a++) {
+                int m1 = mem2[2 * I + a];
+                for (int c = 0; c < 2; c++) L->mem4[4 * I + 2 * a + c] = m1 >= 0 ? mem1[2 * m1 + c] : -1;
+            }
+        level_finish(C);
+        s->nlev++;
+        free(p1); free(agg1); free(mem1); free(rp1); free(c1); free(v1); free(p2); free(agg2); free(mem2);
+    }
+    /* coarsest level: dense LU */
+    L = &s->lev[s->nlev - 1];
+    int n = L->n;
+    L->lu = xmalloc(sizeof(double) * (size_t)n * n);
+    L->piv = xmalloc(sizeof(int32_t) * n);
+    for (int i = 0; i < n; i++)
+        for (int k = L->rowptr[i]; k < L->rowptr[i + 1]; k++) L->lu[(size_t)i * n + L->col[k]] += L->val[k];
+    lu_factor(n, L->lu, L->piv);
+}
+
+static void csr_residual(const level_t *L, const double *f, const double *e, double *r) {
+    for (int i = 0; i < L->n; i++) {
+        double t = 0.0;
+        for (int k = L->rowptr[i]; k < L->rowptr[i + 1]; k++) t += L->val[k] * e[L->col[k]];
+        r[i] = f[i] - t;
+    }
+}
+
+/* V(1,1) cycle with l1-Jacobi smoothing, zero initial guess */
+static void vcycle(ora_sim *s, int l, const double *f, double *e) {
+    level_t *L = &s->lev[l];
+    int n = L->n;
+    if (l == s->nlev - 1) {
+        memcpy(e, f, sizeof(double) * n);
+        lu_solve(n, L->lu, L->piv, e);
+        return;
+    }
+    level_t *C = &s->lev[l + 1];
+    for (int i = 0; i < n; i++) e[i] = f[i] / L->dl1[i];
+    csr_residual(L, f, e, L->t1);
+    double *fc = C->t2, *ec = C->t3;
+    for (int I = 0; I < C->n; I++) {
+        double t = 0.0;
+        for (int a = 0; a < 4; a++) { int m = L->mem4[4 * I + a]; if (m >= 0) t += L->t1[m]; }
+        fc[I] = t;
+    }
+    vcycle(s, l + 1, fc, ec);
+    for (int i = 0; i < n; i++) e[i] += ec[L->agg[i]];
+    csr_residual(L, f, e, L->t1);
+    for (int i = 0; i < n; i++) e[i] += L->t1[i] / L->dl1[i];
+}
+
+/* ------------------------------------------------------------------------ */
+/* CPR preconditioner (Sec. 2.4.2)                                           */
+/* ------------------------------------------------------------------------ */
+void ora_precond_setup(ora_sim *s) {
+    int N = s->N, b = s->b;
+    const ora_input *in = &s->in;
+    if (in->precond == 1) {
+        for (int i = 0; i < N; i++) inv_block(b, JB(s, i, 0), &s->dinv[(size_t)i * b * b]);
+        s->precond_ready = 1;
+        return;
+    }
+    if (in->precond != 2) { s->precond_ready = 1; return; }
+    /* quasi-IMPES weights from the diagonal block D = J_ii */
+    for (int i = 0; i < N; i++) {
+        const double *D = JB(s, i, 0);
+        double *w = &s->qiw[i * b];
+        w[0] = 1.0;
+        if (b == 2) {
+            w[1] = -(D[1] / D[3]);
+        } else {
+            double det = D[4] * D[8] - D[5] * D[7];
+            w[1] = (D[2] * D[7] - D[1] * D[8]) / det;
+            w[2] = (D[1] * D[5] - D[2] * D[4]) / det;
+        }
+    }
+    /* decoupled matrix: pressure row replaced by the weighted row sum */
+    for (int i = 0; i < N; i++) {
+        const double *w = &s->qiw[i * b];
+        for (int d = 0; d < 7; d++) {
+            const double *A = JB(s, i, d);
+            double *Ah = AH(s, i, d);
+            memcpy(Ah, A, sizeof(double) * b * b);
+            for (int c = 0; c < b; c++) {
+                double t = A[c] + w[1] * A[b + c];
+                if (b == 3) t = t + w[2] * A[2 * b + c];
+                Ah[c] = t;
+            }
+        }
+    }
+    /* pressure block as CSR with ascending columns: -z, -y, -x, centre, +x, +y, +z */
+    static const int dorder[7] = {5, 3, 1, 0, 2, 4, 6};
+    int32_t *rp = xmalloc(sizeof(int32_t) * (N + 1));
+    int32_t *col = xmalloc(sizeof(int32_t) * (size_t)N * 7);
+    double *val = xmalloc(sizeof(double) * (size_t)N * 7);
+    int nnz = 0;
+    for (int i = 0; i < N; i++) {
+        rp[i] = nnz;
+        for (int t = 0; t < 7; t++) {
+            int d = dorder[t], j = nbr(s, i, d);
+            if (j < 0) continue;
+            col[nnz] = j; val[nnz] = AH(s, i, d)[0]; nnz++;
+        }
+    }
+    rp[N] = nnz;
+    amg_setup(s, rp, col, val, N);
+    /* second stage on the decoupled matrix */
+    for (int i = 0; i < N; i++) {
+        int ix, iy, iz; cell_ijk(s, i, &ix, &iy, &iz);
+        double *Di = &s->dinv[(size_t)i * b * b];
+        if (in->stage2 == 1 && ((ix + iy + iz) & 1)) continue;   /* black cells after all red ones */
+        inv_block(b, AH(s, i, 0), Di);
+    }
+    if (in->stage2 == 1) {
+        for (int i = 0; i < N; i++) {
+            int ix, iy, iz; cell_ijk(s, i, &ix, &iy, &iz);
+            if (!((ix + iy + iz) & 1)) continue;
+            double D[9], T1[9], T2[9];
+            memcpy(D, AH(s, i, 0), sizeof(double) * b * b);
+            for (int d = 1; d < 7; d++) {
+                int k = nbr(s, i, d);
+                if (k < 0) continue;
+                matmul_block(b, &s->dinv[(size_t)k * b * b], AH(s, k, opp(d)), T1);
+                matmul_block(b, AH(s, i, d), T1, T2);
+                for (int t = 0; t < b * b; t++) D[t] -= T2[t];
+            }
+            inv_block(b, D, &s->dinv[(size_t)i * b * b]);
+        }
+    }
+    s->precond_ready = 1;
+}
+
+void ora_precond_apply(ora_sim *s, const double *r, double *z) {
+    int N = s->N, b = s->b;
+    const ora_input *in = &s->in;
+    if (!s->precond_ready) ora_precond_setup(s);
+    if (in->precond == 0) { memcpy(z, r, sizeof(double) * N * b); return; }
+    if (in->precond == 1) {
+        for (int i = 0; i < N; i++) matvec_block(b, &s->dinv[(size_t)i * b * b], &r[i * b], &z[i * b]);
+        return;
+    }
+    double *rh = s->tmp, *ep = s->tmp2, *fp = s->tmp3;
+    /* decoupled residual, pressure part */
+    for (int i = 0; i < N; i++) {
+        const double *w = &s->qiw[i * b];
+        for (int c = 0; c < b; c++) rh[i * b + c] = r[i * b + c];
+        double t = r[i * b] + w[1] * r[i * b + 1];
+        if (b == 3) t = t + w[2] * r[i * b + 2];
+        rh[i * b] = t;
+        fp[i] = t;
+    }
+    /* stage P: one AMG V-cycle on the pressure block */
+    vcycle(s, 0, fp, ep);
+    /* residual of the decoupled system after stage P (pressure columns only) */
+    for (int i = 0; i < N; i++) {
+        for (int c = 0; c < b; c++) {
+            double t = rh[i * b + c];
+            for (int d = 0; d < 7; d++) {
+                int j = nbr(s, i, d);
+                if (j < 0) continue;
+                t -= AH(s, i, d)[c * b] * ep[j];
+            }
+            z[i * b + c] = t;      /* z holds r2 for now */
+        }
+    }
+    memcpy(rh, z, sizeof(double) * N * b);
+    /* stage F */
+    if (in->stage2 == 1) {
+        double t[3], u[3];
+        for (int i = 0; i < N; i++) {           /* forward, red */
+            int ix, iy, iz; cell_ijk(s, i, &ix, &iy, &iz);
+            if ((ix + iy + iz) & 1) continue;
+            matvec_block(b, &s->dinv[(size_t)i * b * b], &rh[i * b], &z[i * b]);
+        }
+        for (int i = 0; i < N; i++) {           /* forward, black */
+            int ix, iy, iz; cell_ijk(s, i, &ix, &iy, &iz);
+            if (!((ix + iy + iz) & 1)) continue;
+            for (int c = 0; c < b; c++) t[c] = rh[i * b + c];
+            for (int d = 1; d < 7; d++) {
+                int k = nbr(s, i, d);
+                if (k < 0) continue;
+                matvec_block(b, AH(s, i, d), &z[k * b], u);
+                for (int c = 0; c < b; c++) t[c] -= u[c];
+            }
+            matvec_block(b, &s->dinv[(size_t)i * b * b], t, &z[i * b]);
+        }
+        for (int i = 0; i < N; i++) {           /* backward, red (black unchanged) */
+            int ix, iy, iz; cell_ijk(s, i, &ix, &iy, &iz);
+            if ((ix + iy + iz) & 1) continue;
+            for (int c = 0; c < b; c++) t[c] = 0.0;
+            for (int d = 1; d < 7; d++) {
+                int k = nbr(s, i, d);
+                if (k < 0) continue;
+                matvec_block(b, AH(s, i, d), &z[k * b], u);
+                for (int c = 0; c < b; c++) t[c] += u[c];
+            }
+            matvec_block(b, &s->dinv[(size_t)i * b * b], t, u);
+            for (int c = 0; c < b; c++) z[i * b + c] -= u[c];
+        }
+    } else {
+        for (int i = 0; i < N; i++) matvec_block(b, &s->dinv[(size_t)i * b * b], &rh[i * b], &z[i * b]);
+    }
+    for (int i = 0; i < N; i++) z[i * b] += ep[i];
+}
+
+void ora_get_qi(const ora_sim *s, double *w, double *ap) {
+    memcpy(w, s->qiw, sizeof(double) * s->N * s->b);
+    for (int i = 0; i < s->N; i++)
+        for (int d = 0; d < 7; d++) ap[i * 7 + d] = s->ahat[(((size_t)i * 7 + d) * s->b) * s->b];
+}
+int ora_amg_levels(const ora_sim *s) { return s->nlev; }
+int ora_amg_level_n(const ora_sim *s, int l) { return s->lev[l].n; }
+int ora_amg_level_nnz(const ora_sim *s, int l) { return s->lev[l].nnz; }
+void ora_amg_level_csr(const ora_sim *s, int l, int32_t *rp, int32_t *col, double *val) {
+    const level_t *L = &s->lev[l];
+    memcpy(rp, L->rowptr, sizeof(int32_t) * (L->n + 1));
+    memcpy(col, L->col, sizeof(int32_t) * L->nnz);
+    memcpy(val, L->val, sizeof(double) * L->nnz);
+}
+void ora_amg_level_agg(const ora_sim *s, int l, int32_t *agg) {
+    const level_t *L = &s->lev[l];
+    if (L->agg) memcpy(agg, L->agg, sizeof(int32_t) * L->n);
+}
+void ora_ilu_dinv(const ora_sim *s, double *dinv) { memcpy(dinv, s->dinv, sizeof(double) * (size_t)s->N * s->b * s->b); }
+
+/* ------------------------------------------------------------------------ */
+/* right-preconditioned FGMRES(m) with classical Gram-Schmidt + one full     */
+/* reorthogonalisation, Givens rotations, zero initial guess (Alg. 1 step 4) */
+/* ------------------------------------------------------------------------ */
+static double dot(const double *a, const double *b, int n) { double t = 0.0; for (int i = 0; i < n; i++) t += a[i] * b[i]; return t; }
+
+int ora_linear_solve(ora_sim *s, const double *bvec, double *x, ora_lin_info *info) {
+    const ora_input *in = &s->in;
+    int n = s->N * s->b, m = in->gmres_m;
+    ora_lin_info li; memset(&li, 0, sizeof(li));
+    if (!s->precond_ready) ora_precond_setup(s);
+    double bn = sqrt(dot(bvec, bvec, n));
+    li.b_norm = bn;
+    for (int i = 0; i < n; i++) x[i] = 0.0;
+    if (bn == 0.0) { li.converged = 1; if (info) *info = li; return 0; }
+    double tol = in->lin_tol * bn;
+    memcpy(s->r, bvec, sizeof(double) * n);
+    double beta = bn;
+    double *H = s->H, *g = s->g, *cs = s->cs, *sn = s->sn, *y = s->y, *h2 = s->tmp3;
+    (void)h2;
+    double hcol[64], hre[64];
+    for (int cyc = 0; cyc <= in->gmres_max_restarts; cyc++) {
+        double *V0 = s->V;
+        for (int i = 0; i < n; i++) V0[i] = s->r[i] / beta;
+        for (int j = 0; j <= m; j++) g[j] = 0.0;
+        g[0] = beta;
+        int k = 0;
+        for (int j = 0; j < m; j++) {
+            double *vj = s->V + (size_t)j * n, *zj = s->Z + (size_t)j * n, *w = s->w;
+            ora_precond_apply(s, vj, zj);
+            block_spmv(s, s->J, zj, w);
+            /* CGS pass 1 */
+            for (int i = 0; i <= j; i++) hcol[i] = dot(s->V + (size_t)i * n, w, n);
+            for (int i = 0; i <= j; i++) { const double *vi = s->V + (size_t)i * n; for (int t = 0; t < n; t++) w[t] -= hcol[i] * vi[t]; }
+            /* CGS pass 2 */
+            for (int i = 0; i <= j; i++) hre[i] = dot(s->V + (size_t)i * n, w, n);
+            for (int i = 0; i <= j; i++) { const double *vi = s->V + (size_t)i * n; for (int t = 0; t < n; t++) w[t] -= hre[i] * vi[t]; }
+            for (int i = 0; i <= j; i++) hcol[i] += hre[i];
+            double hn = sqrt(dot(w, w, n));
+            double *vn = s->V + (size_t)(j + 1) * n;
+            if (hn > 0.0) for (int t = 0; t < n; t++) vn[t] = w[t] / hn;
+            else for (int t = 0; t < n; t++) vn[t] = 0.0;
+            /* previous rotations on column j */
+            for (int i = 0; i < j; i++) {
+                double a = hcol[i], c2 = hcol[i + 1];
+                hcol[i] = cs[i] * a + sn[i] * c2;
+                hcol[i + 1] = -sn[i] * a + cs[i] * c2;
+            }
+            double a = hcol[j], bb = hn;
+            double rr = sqrt(a * a + bb * bb);
+            if (rr == 0.0) { cs[j] = 1.0; sn[j] = 0.0; }
+            else { cs[j] = a / rr; sn[j] = bb / rr; }
+            hcol[j] = rr;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            for (int i = 0; i <= j; i++) H[i * (m + 1) + j] = hcol[i];
+            li.iterations++;
+            k = j + 1;
+            if (fabs(g[j + 1]) <= tol) break;
+        }
+        /* back substitution H y = g */
+        for (int i = k - 1; i >= 0; i--) {
+            double t = g[i];
+            for (int c = i + 1; c < k; c++) t -= H[i * (m + 1) + c] * y[c];
+            y[i] = t / H[i * (m + 1) + i];
+        }
+        for (int i = 0; i < k; i++) { const double *zi = s->Z + (size_t)i * n; for (int t = 0; t < n; t++) x[t] += y[i] * zi[t]; }
+        block_spmv(s, s->J, x, s->w);
+        for (int t = 0; t < n; t++) s->r[t] = bvec[t] - s->w[t];
+        beta = sqrt(dot(s->r, s->r, n));
+        li.r_norm = beta;
+        if (beta <= tol) { li.converged = 1; break; }
+        if (!(beta == beta)) break;
+        li.restarts++;
+    }
+    if (info) *info = li;
+    return li.converged ? 0 : 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* inexact Newton (Algorithm 1) and time stepping                            */
+/* ------------------------------------------------------------------------ */
+/* x += dx with the per-cell Appleyard chop, saturations clamped to their
+   physical range, then the black-oil variable switch: free gas vanishing
+   (Sg < 0) makes the cell undersaturated at pb = p; pb rising above p, or
+   the oil leaving the cell (no oil, no bubble point), makes it saturated at
+   Sg = 0 */
+static void newton_update(ora_sim *s, const double *dx) {
+    int b = s->b;
+    const ora_input *in = &s->in;
+    for (int i = 0; i < s->N; i++) {
+        double *xi = &s->x[i * b];
+        const double *d = &dx[i * b];
+        double ds = fabs(d[1]), dp = fabs(d[0]);
+        if (b == 3) { if (s->ph[i]) { if (fabs(d[2]) > ds) ds = fabs(d[2]); } else { if (fabs(d[2]) > dp) dp = fabs(d[2]); } }
+        double f = 1.0;
+        if (ds > in->chop_ds) f = in->chop_ds / ds;
+        if (dp > in->chop_dp && in->chop_dp / dp < f) f = in->chop_dp / dp;
+        for (int c = 0; c < b; c++) xi[c] += f * d[c];
+        /* saturations stay physical: 0 <= Sw <= 1, Sg <= 1 - Sw */
+        if (xi[1] < 0.0) xi[1] = 0.0;
+        if (xi[1] > 1.0) xi[1] = 1.0;
+        if (b == 3) {
+            if (s->ph[i] && xi[2] < 0.0) { s->ph[i] = 0; xi[2] = xi[0]; }
+            else if (!s->ph[i] && xi[2] > xi[0]) { s->ph[i] = 1; xi[2] = 0.0; }
+            if (!s->ph[i] && xi[1] > 1.0 - 1e-6) { s->ph[i] = 1; xi[2] = 0.0; }
+            if (s->ph[i] && xi[2] > 1.0 - xi[1]) xi[2] = 1.0 - xi[1];
+        }
+    }
+}
+
+static int finite_vec(const double *a, int n) { for (int i = 0; i < n; i++) if (!(a[i] - a[i] == 0.0)) return 0; return 1; }
+
+/* one Newton iteration: assemble, solve J dx = -R, update */
+int ora_newton_step(ora_sim *s, double dt, ora_newton_info *info) {
+    int n = s->N * s->b;
+    ora_assemble(s, dt);
+    double cnv = ora_cnv(s, dt);
+    ora_newton_info ni; memset(&ni, 0, sizeof(ni));
+    ni.cnv = cnv;
+    if (cnv <= s->in.newton_tol) { ni.converged = 1; if (info) *info = ni; return 0; }
+    double *rhs = xmalloc(sizeof(double) * n), *dx = xmalloc(sizeof(double) * n);
+    for (int t = 0; t < n; t++) rhs[t] = -s->R[t];
+    ora_lin_info li;
+    ora_linear_solve(s, rhs, dx, &li);
+    ni.newton_iterations = 1; ni.linear_iterations = li.iterations; ni.linear_failures = !li.converged;
+    int ok = finite_vec(dx, n);
+    if (ok) newton_update(s, dx);
+    free(rhs); free(dx);
+    if (info) *info = ni;
+    return ok ? 0 : 2;
+}
+
+/* Newton loop of Algorithm 1 until CNV <= tol; 0 = converged */
+int ora_newton_solve(ora_sim *s, double dt, ora_newton_info *info) {
+    int n = s->N * s->b;
+    ora_newton_info ni; memset(&ni, 0, sizeof(ni));
+    double *rhs = xmalloc(sizeof(double) * n), *dx = xmalloc(sizeof(double) * n);
+    int rc = 1;
+    for (int l = 0;; l++) {
+        ora_assemble(s, dt);
+        double cnv = ora_cnv(s, dt);
+        ni.cnv = cnv;
+        if (!(cnv == cnv)) { rc = 2; break; }
+        if (cnv <= s->in.newton_tol) { rc = 0; ni.converged = 1; break; }
+        if (l >= s->in.newton_max) { rc = 1; break; }
+        for (int t = 0; t < n; t++) rhs[t] = -s->R[t];
+        ora_lin_info li;
+        ora_linear_solve(s, rhs, dx, &li);
+        ni.newton_iterations++; ni.linear_iterations += li.iterations; ni.linear_failures += !li.converged;
+        if (!finite_vec(dx, n)) { rc = 2; break; }
+        newton_update(s, dx);
+    }
+    free(rhs); free(dx);
+    if (info) *info = ni;
+    return rc;
+}
+
+/* advance by dt; a failed Newton solve restores the last state and halves the step */
+int ora_step(ora_sim *s, double dt, ora_step_info *info) {
+    ora_step_info si; memset(&si, 0, sizeof(si));
+    double remaining = dt, h = dt;
+    int rc = 0;
+    while (remaining > 1e-12 * dt) {
+        if (h > remaining) h = remaining;
+        ora_newton_info ni;
+        int r = ora_newton_solve(s, h, &ni);
+        si.newton_iterations += ni.newton_iterations;
+        si.linear_iterations += ni.linear_iterations;
+        if (r == 0) {
+            for (int c = 0; c < 3; c++) s->cum_well[c] += h * s->qtot[c];
+            remaining -= h;
+            si.substeps++;
+            begin_step(s);
+        } else {
+            memcpy(s->x, s->x_old, sizeof(double) * s->N * s->b);
+            memcpy(s->ph, s->ph_old, s->N);
+            si.cuts++;
+            if (si.cuts > s->in.max_cuts) { rc = 1; break; }
+            h *= 0.5;
+        }
+    }
+    si.ok = rc == 0;
+    if (info) *info = si;
+    return rc;
+}
+
+/* property probe for the closed-form pins */
+double ora_props_probe(const ora_input *in, int what, double p, double sw, double x3, int ph, double *grad) {
+    cellprops cp;
+    double x[3] = {p, sw, x3};
+    eval_props(in, 1.0, 1.0, x, ph, &cp);
+    dual r;
+    switch (what) {
+    case 0: r = cp.kr[PW]; break;
+    case 1: r = cp.kr[PO]; break;
+    case 2: r = cp.kr[PG]; break;
+    case 3: r = cp.rho[PW]; break;
+    case 4: r = cp.rho[PO]; break;
+    case 5: r = cp.rho[PG]; break;
+    case 6: r = cp.mob[PW][CW]; break;
+    case 7: r = cp.mob[PO][CO]; break;
+    case 8: r = cp.mob[PO][CG]; break;
+    case 9: r = cp.mob[PG][CG]; break;
+    case 10: r = cp.bo; break;
+    case 11: r = cp.rs; break;
+    case 12: r = cp.muo; break;
+    case 13: r = cp.acc[CW]; break;
+    case 14: r = cp.acc[CO]; break;
+    case 15: r = cp.acc[CG]; break;
+    case 16: r = cp.lamt; break;
+    default: r = dc(NAN);
+    }
+    if (grad) for (int k = 0; k < 3; k++) grad[k] = r.d[k];
+    return r.v;
+}

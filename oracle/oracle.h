@@ -1,0 +1,116 @@
+/*
+ * CPU oracle for the fully implicit oil-water / black-oil Newton step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library is the plain, slow, FP64 statement
+ * of what the GPU path computes.  Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline leg load it.  It shares no code, header or table
+ * with the CUDA library; the two meet only through the seeded input arrays.
+ *
+ * Followed passages (paper sections / equations):
+ *   Eq. (1)-(3)  black-oil mass conservation with Darcy flux
+ *   Eq. (4)      closure relations (capillary pressure taken as zero, Sec. 4.1)
+ *   Eq. (5)      two-phase oil-water model
+ *   Eq. (6)      well rate per perforation, Peaceman well index (Sec. 2.3)
+ *   Eq. (7)      fixed bottom-hole pressure control
+ *   Eq. (10)     backward Euler in time
+ *   Eq. (11)     cell-centred transmissibility on a structured grid
+ *   Algorithm 1  inexact Newton with forcing term theta
+ *   Eq. (16)     pressure / saturation block ordering of the Jacobian
+ *   Sec. 2.4.2   CPR-type two-stage preconditioning with quasi-IMPES
+ *                decoupling and AMG on the pressure block
+ * Readings of passages the paper leaves open are stated where they are used.
+ *
+ * Layouts (oracle-private): vectors interleaved per cell, v[i*b + c];
+ * Jacobian blocks J[((i*7 + d)*b + r)*b + c], d = 0 centre, 1 -x, 2 +x,
+ * 3 -y, 4 +y, 5 -z, 6 +z.  Cell index i = ix + nx*(iy + ny*iz).
+ */
+#ifndef ORACLE_H
+#define ORACLE_H
+#include <stdint.h>
+
+typedef struct {
+    int32_t nx, ny, nz;
+    double dx, dy, dz, top_depth;
+    int32_t model;                 /* 2 oil-water, 3 black oil */
+    const double *kx, *ky, *kz, *poro;
+    double c_rock, p_ref;
+    /* oil-water fluid: rho = rho_ref * exp(c (p - p_ref)) */
+    double rho_w_ref, rho_o_ref, c_w, c_o, mu_w, mu_o;
+    /* black-oil fluid */
+    double rho_ws, rho_os, rho_gs, bw_c, bw_pref, bo_c_us, muo_c_us;
+    int32_t npvt;
+    const double *pvt_p, *pvt_bo, *pvt_rs, *pvt_muo, *pvt_bg, *pvt_mug;
+    /* relative permeability (Corey two-phase curves, Stone II for three phases) */
+    double swc, sor, sgc, sorg, nw, now, ng, nog;
+    /* wells: type 0 producer, 1 water injector; BHP control */
+    int32_t nwells;
+    const int32_t *w_i, *w_j, *w_k0, *w_k1, *w_type;
+    const double *w_bhp, *w_rw, *w_skin;
+    /* scaling densities of the CNV convergence test, per component */
+    double cnv_rho[3];
+    /* nonlinear / linear solver options */
+    double newton_tol; int32_t newton_max;
+    double lin_tol; int32_t gmres_m, gmres_max_restarts;
+    int32_t precond;               /* 0 none, 1 block-Jacobi, 2 CPR */
+    int32_t stage2;                /* CPR second stage: 0 block-Jacobi, 1 red-black block ILU(0) */
+    double amg_theta; int32_t amg_rounds, amg_coarse_max, amg_max_levels;
+    double chop_ds, chop_dp; int32_t max_cuts;
+} ora_input;
+
+typedef struct {
+    int32_t iterations;            /* FGMRES inner iterations */
+    int32_t restarts;
+    int32_t converged;
+    double b_norm, r_norm;         /* ||b||, true ||b - A x|| at exit */
+} ora_lin_info;
+
+typedef struct {
+    int32_t newton_iterations;     /* linear solves performed */
+    int32_t linear_iterations;
+    int32_t converged;
+    int32_t linear_failures;
+    double cnv;                    /* CNV at exit */
+} ora_newton_info;
+
+typedef struct {
+    int32_t cuts, newton_iterations, linear_iterations, substeps, ok;
+} ora_step_info;
+
+typedef struct ora_sim ora_sim;
+
+ora_sim *ora_create(const ora_input *in);
+void ora_destroy(ora_sim *s);
+int ora_block_size(const ora_sim *s);
+void ora_set_state(ora_sim *s, const double *p, const double *sw, const double *x3, const int8_t *ph);
+void ora_get_state(const ora_sim *s, double *p, double *sw, double *x3, int8_t *ph);
+void ora_set_iterate(ora_sim *s, const double *x, const int8_t *ph);
+void ora_get_iterate(const ora_sim *s, double *x, int8_t *ph);
+void ora_assemble(ora_sim *s, double dt);
+void ora_get_residual(const ora_sim *s, double *R);
+void ora_get_jacobian(const ora_sim *s, double *J);
+void ora_set_jacobian(ora_sim *s, const double *J);
+double ora_cnv(const ora_sim *s, double dt);
+void ora_spmv(const ora_sim *s, const double *x, double *y);
+void ora_precond_setup(ora_sim *s);
+void ora_precond_apply(ora_sim *s, const double *r, double *z);
+int ora_linear_solve(ora_sim *s, const double *b, double *x, ora_lin_info *info);
+int ora_newton_step(ora_sim *s, double dt, ora_newton_info *info);
+int ora_newton_solve(ora_sim *s, double dt, ora_newton_info *info);
+int ora_step(ora_sim *s, double dt, ora_step_info *info);
+void ora_component_mass(const ora_sim *s, double *m);
+void ora_cumulative_well_mass(const ora_sim *s, double *m);
+void ora_well_rates(const ora_sim *s, double *q);
+void ora_get_qi(const ora_sim *s, double *w, double *ap);
+int ora_amg_levels(const ora_sim *s);
+int ora_amg_level_n(const ora_sim *s, int level);
+int ora_amg_level_nnz(const ora_sim *s, int level);
+void ora_amg_level_csr(const ora_sim *s, int level, int32_t *rowptr, int32_t *col, double *val);
+void ora_amg_level_agg(const ora_sim *s, int level, int32_t *agg);
+void ora_ilu_dinv(const ora_sim *s, double *dinv);
+
+/* standalone pieces used by the pins */
+int ora_dense_lu_solve(int n, double *A, double *b);
+int ora_match_pass(int n, const int32_t *rowptr, const int32_t *col, const double *val,
+                   double theta, int rounds, int32_t *partner);
+double ora_props_probe(const ora_input *in, int what, double p, double sw, double x3, int ph, double *grad);
+#endif
