@@ -1,0 +1,327 @@
+"""Benchmark: Newton cell-iterations per second of the fully implicit black-oil
+step (CPR-FGMRES(30), tolerance 1e-8) on the 100x100x20 synthetic reservoir.
+
+A step is one 10-day time step: the Newton loop (assembly, CPR-FGMRES solve,
+update) until the CNV test passes.  value = cells x Newton iterations / s over
+the K timed steps, device time from CUDA events on the library's stream.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--precision fp64|mixed] [--workload bo100|bo200|bo400]
+
+Prints one JSON line.  Under torchrun every rank runs its own replica of the
+workload (the single-grid path does not shard), the time is the max over
+ranks and the value sums the ranks' work ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Newton cell-iters/s"
+UNIT = "cell-iters/s"
+
+
+def workload(name: str):
+    from paper_1606_00548_gb300 import synth
+    if name == "bo100":
+        return synth.black_oil_100x100x20(), "black-oil 100x100x20 (200k cells, 3x3 blocks), 10-day steps"
+    if name == "bo200":
+        return synth.black_oil_400cube(n=200), "black-oil 200^3 (8M cells), 10-day steps"
+    if name == "bo400":
+        return synth.black_oil_400cube(n=400), "black-oil 400^3 (64M cells), 10-day steps"
+    raise SystemExit(f"unknown workload {name}")
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": len(self.rows)}
+        if not self.rows:
+            return out
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for k, nm in enumerate(names):
+                if len(r) > 3 + k and r[3 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        out.update(sm_mhz=float(np.median(sm)) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                   reasons=sorted(reasons))
+        return out
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, v):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(ws, v):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def cpu_oracle_sample(case, newton_its=1):
+    """The oracle as it stands, one thread: a bounded number of Newton iterations
+    of the first time step of the workload.  Returns (cell-iters/s, seconds)."""
+    import oracle
+    o = oracle.Oracle(case)
+    dt = case["dt"][0]
+    N = case["nx"] * case["ny"] * case["nz"]
+    t0 = time.perf_counter()
+    its = 0
+    for _ in range(newton_its):
+        rc, info = o.newton_step(dt)
+        its += info.newton_iterations
+        if info.converged:
+            break
+    t = time.perf_counter() - t0
+    return N * max(its, 1) / t, t
+
+
+def run_reference(args):
+    ws, rank = dist_info()
+    if rank != 0:
+        return 0
+    case, desc = workload(args.workload)
+    N = case["nx"] * case["ny"] * case["nz"]
+    import oracle
+    oracle.build()
+    o = oracle.Oracle(case)
+    dt = case["dt"][0]
+    # warm-up and timed steps: one oracle Newton iteration each (a bounded sample)
+    for _ in range(args.warmup):
+        o.newton_step(dt)
+    t0 = time.perf_counter()
+    its = 0
+    for _ in range(args.steps):
+        rc, info = o.newton_step(dt)
+        its += max(1, info.newton_iterations)
+    t = time.perf_counter() - t0
+    value = N * its / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "sample": "one oracle Newton iteration per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} Newton iterations of the first time step, 1 thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    ws, rank = dist_info()
+    if ws > 1:
+        import torch.distributed as dist
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.cuda.current_device()
+    from paper_1606_00548_gb300 import build
+    build.build()
+    from paper_1606_00548_gb300.sim import Simulator
+
+    case, desc = workload(args.workload)
+    N = case["nx"] * case["ny"] * case["nz"]
+    prec = 1 if args.precision == "mixed" else 0
+    stream = torch.cuda.Stream()
+    sim = Simulator(case, precision=prec, stream=stream.cuda_stream)
+    dts = case["dt"]
+
+    def dt_of(k):
+        return dts[k % len(dts)]
+
+    k = 0
+    for _ in range(args.warmup):
+        sim.step(dt_of(k)); k += 1
+    torch.cuda.synchronize()
+    st0 = sim.stats()
+    sampler = ClockSampler(dev) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    newton = 0
+    lin = 0
+    cuts = 0
+    for _ in range(args.steps):
+        st, info = sim.step(dt_of(k)); k += 1
+        newton += info.newton_iterations
+        lin += info.linear_iterations
+        cuts += info.cuts
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = sampler.stop() if sampler else None
+    t_dev = e0.elapsed_time(e1) / 1e3
+    st1 = sim.stats()
+    t_max = max_over_ranks(ws, t_dev)
+    work = sum_over_ranks(ws, float(N * newton))
+    value = work / t_max
+
+    # end to end through the C ABI with host buffers: H2D state, step, D2H state
+    p, sw, x3, ph = sim.get_state()
+    p = np.ascontiguousarray(p); sw = np.ascontiguousarray(sw); x3 = np.ascontiguousarray(x3)
+    e2e_newton = 0
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sim.set_state(p, sw, x3, ph)
+        st, info = sim.step(dt_of(k)); k += 1
+        e2e_newton += info.newton_iterations
+        p, sw, x3, ph = sim.get_state()
+    torch.cuda.synchronize()
+    t_e2e = max_over_ranks(ws, time.perf_counter() - t0)
+    e2e_value = sum_over_ranks(ws, float(N * e2e_newton)) / t_e2e
+    state_bytes = N * (3 * 8 + 1)
+
+    # roofline of the block SpMV: y = J x, 7 b^2 + 2 b doubles per cell
+    b = sim.b
+    x = torch.randn(N * b, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            sim.spmv(x, y)
+        torch.cuda.synchronize()
+        s0 = torch.cuda.Event(enable_timing=True); s1 = torch.cuda.Event(enable_timing=True)
+        reps = 20
+        s0.record(stream)
+        for _ in range(reps):
+            sim.spmv(x, y)
+        s1.record(stream)
+    torch.cuda.synchronize()
+    t_spmv = s0.elapsed_time(s1) / 1e3 / reps
+    bytes_spmv = (7 * b * b + 2 * b) * 8 * N
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        peak = float(peaks["hbm_gbs"]); peak_src = "measured"
+    except Exception:
+        peak = 6800.0; peak_src = "fallback"
+    achieved = bytes_spmv / t_spmv / 1e9
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        v, t = cpu_oracle_sample(case, 1)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one Newton iteration of the first 10-day step ({t:.1f} s, 1 thread)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else "f64+f32",
+            "data": "synthetic",
+            "config": {"workload": desc, "precision": args.precision,
+                       "solver": "CPR(QI, aggregation AMG V(1,1), red-black block ILU0) FGMRES(30), theta 1e-8",
+                       "newton_iterations": newton, "linear_iterations": lin, "cuts": cuts,
+                       "l2": "working set (J 101 MB + Krylov basis 149 MB + ...) larger than L2"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+                    "d2h_bytes_per_step": state_bytes},
+            "gpu_launches": int(st1.kernel_launches - st0.kernel_launches),
+            "roofline": {"kernel": "block stencil SpMV y = J x", "bound": "hbm", "achieved": achieved,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "peak_source": peak_src, "bytes_per_cell": (7 * b * b + 2 * b) * 8,
+                         "launch_us": t_spmv * 1e6},
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--workload", default="bo100", choices=["bo100", "bo200", "bo400"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

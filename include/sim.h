@@ -1,0 +1,204 @@
+/*
+ * sim.h -- C ABI of the GB300 fully implicit reservoir Newton step.
+ *
+ * Method (arXiv:1606.00548): oil-water (Eq. 5) and three-component black-oil
+ * (Eq. 3-4) mass conservation with Darcy flux (Eq. 1-2), BHP-controlled
+ * Peaceman wells (Eq. 6-7), backward Euler (Eq. 10) and cell-centred
+ * two-point transmissibilities (Eq. 11) on a structured 7-point grid,
+ * solved by inexact Newton (Algorithm 1) whose linear systems (Eq. 16) are
+ * solved by CPR-preconditioned FGMRES (Sec. 2.4.2: quasi-IMPES decoupling,
+ * AMG on the pressure block, block ILU(0) / block-Jacobi second stage).
+ *
+ * Conventions
+ *   - cell index i = ix + nx*(iy + ny*iz), x fastest; N = nx*ny*nz.
+ *   - b = unknowns (= equations) per cell: 2 (oil-water) or 3 (black oil).
+ *     Unknown order (p, Sw, x3) with x3 = Sg (saturated cell) or pb
+ *     (undersaturated cell); equation order (water, oil, gas).
+ *   - vectors on the device are component-major: v[c*N + i] (FP64).
+ *   - Jacobian blocks: J[((d*b + r)*b + c)*N + i] = dR_r(i)/dx_c(nbr_d(i)),
+ *     d = 0 centre, 1 -x, 2 +x, 3 -y, 4 +y, 5 -z, 6 +z; blocks that point
+ *     outside the grid are zero.
+ *   - units: bar, m, day, mD, cP, kg/m3; residuals in kg/day.
+ *
+ * Ownership and errors
+ *   - the library owns every device buffer it allocates; callers own their
+ *     host arrays (copied on entry) and any device pointers they pass.
+ *   - every call returns sim_status; nothing aborts or throws across the ABI
+ *     and no kernel traps.  The first error is kept (sticky) together with a
+ *     message, readable with sim_last_error(), until sim_clear_error().
+ *   - all work is ordered on the CUDA stream given to sim_create (NULL: the
+ *     library creates its own).  Calls that return host data synchronise it.
+ */
+#ifndef GB300_SIM_H
+#define GB300_SIM_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SIM_OK = 0,
+    SIM_EINVAL = 1,            /* bad argument or inconsistent input */
+    SIM_ENOMEM = 2,            /* device allocation failed */
+    SIM_ECUDA = 3,             /* CUDA runtime error */
+    SIM_ENAN = 4,              /* non-finite residual or update */
+    SIM_ENOCONV_LINEAR = 5,    /* FGMRES hit its restart limit */
+    SIM_ENOCONV_NEWTON = 6,    /* Newton failed and the time-step cuts ran out */
+    SIM_ETIMEOUT = 7,          /* a bounded device wait gave up */
+    SIM_ELIMIT = 8             /* a size limit of the implementation was exceeded */
+} sim_status;
+
+typedef struct sim sim_t;
+
+/* structured grid (Sec. 2.4: structured grids, finite differences) */
+typedef struct {
+    int32_t nx, ny, nz;
+    double dx, dy, dz;          /* cell size, m */
+    double top_depth;           /* depth of the top face, m (depth positive down) */
+} sim_grid;
+
+/* rock: host arrays of N doubles, copied at sim_create */
+typedef struct {
+    const double *kx, *ky, *kz; /* absolute permeability, mD */
+    const double *poro;         /* porosity at p_ref */
+    double c_rock, p_ref;       /* phi = poro (1 + c_rock (p - p_ref)) */
+} sim_rock;
+
+/* fluid (Sec. 2.1-2.2).  model 2: rho = rho_ref exp(c (p - p_ref)), constant
+   viscosities.  model 3: tabulated Bo, Rs, mu_o, Bg, mu_g (piecewise linear,
+   linear extrapolation), undersaturated Bo = Bo(pb)(1 - bo_c_us (p - pb)),
+   mu_o = mu_o(pb)(1 + muo_c_us (p - pb)), 1/Bw = 1 + bw_c (p - bw_pref).
+   Relative permeability: Corey curves, Stone II for k_ro (model 3). */
+typedef struct {
+    int32_t model;
+    double rho_w_ref, rho_o_ref, c_w, c_o, mu_w, mu_o;
+    double rho_ws, rho_os, rho_gs, bw_c, bw_pref, bo_c_us, muo_c_us;
+    int32_t npvt;               /* table nodes (2..64) */
+    const double *pvt_p, *pvt_bo, *pvt_rs, *pvt_muo, *pvt_bg, *pvt_mug;
+    double swc, sor, sgc, sorg, nw, now, ng, nog;
+    double cnv_rho[3];          /* per-component density scale of the CNV test */
+} sim_fluid;
+
+#define SIM_WELL_PRODUCER 0
+#define SIM_WELL_WATER_INJECTOR 1
+/* vertical well perforated in layers k_top..k_bot, BHP control (Eq. 7) */
+typedef struct {
+    int32_t i, j, k_top, k_bot, type;
+    double bhp;                 /* bar, at the depth of the top perforation */
+    double r_w, skin;           /* Peaceman well radius (m) and skin */
+} sim_well;
+
+#define SIM_PRECOND_NONE 0
+#define SIM_PRECOND_BJACOBI 1
+#define SIM_PRECOND_CPR 2
+#define SIM_STAGE2_BJACOBI 0
+#define SIM_STAGE2_ILU0_RB 1
+#define SIM_PRECISION_FP64 0
+#define SIM_PRECISION_MIXED 1   /* FP32 preconditioner + FP32 Krylov directions Z */
+
+typedef struct {
+    double newton_tol;          /* CNV tolerance */
+    int32_t newton_max;         /* Newton iterations per time step */
+    double lin_tol;             /* forcing term theta: ||b - J dx|| <= theta ||b|| */
+    int32_t gmres_m, gmres_max_restarts;   /* 1 <= m <= 32 */
+    int32_t precond, stage2;
+    double amg_theta;           /* strength threshold */
+    int32_t amg_rounds;         /* handshake rounds per matching pass */
+    int32_t amg_coarse_max;     /* coarsest level size (<= 1024) */
+    int32_t amg_max_levels;
+    double chop_ds, chop_dp;    /* Appleyard chop limits */
+    int32_t max_cuts;           /* time-step halvings per sim_step */
+    int32_t precision;          /* SIM_PRECISION_* */
+} sim_options;
+
+typedef struct {
+    int32_t iterations, restarts, converged;
+    double b_norm, r_norm;      /* ||b||, true ||b - J x|| at exit */
+} sim_linear_info;
+
+typedef struct {
+    int32_t newton_iterations;  /* linear solves performed */
+    int32_t linear_iterations;
+    int32_t converged;
+    int32_t linear_failures;
+    double cnv;
+} sim_newton_info;
+
+typedef struct {
+    int32_t cuts, newton_iterations, linear_iterations, substeps, ok;
+} sim_step_info;
+
+typedef struct {
+    int64_t kernel_launches;    /* kernels launched by this handle so far */
+    int64_t newton_iterations, linear_iterations;
+    int64_t device_bytes;       /* device memory held by the handle */
+} sim_stats;
+
+/* Create a simulator (copies every host array).  Validates sizes, table
+   monotonicity, well positions (no two perforations in one cell).
+   cuda_stream: a cudaStream_t or NULL.  *out receives the handle; on error
+   *out is NULL and the message is printed by sim_last_error(NULL). */
+sim_status sim_create(const sim_grid *g, const sim_rock *r, const sim_fluid *f,
+                      const sim_well *w, int32_t nwells, const sim_options *o,
+                      void *cuda_stream, sim_t **out);
+void sim_destroy(sim_t *s);
+
+/* Accepted state (host arrays of N): pressure, Sw, x3 (Sg or pb), phase
+   (1 saturated, 0 undersaturated; ignored for oil-water).  set_state also
+   zeroes the cumulative well masses and starts a new time step from it. */
+sim_status sim_set_state(sim_t *s, const double *p, const double *sw, const double *x3, const int8_t *phase);
+sim_status sim_get_state(sim_t *s, double *p, double *sw, double *x3, int8_t *phase);
+
+/* Advance by dt days (Algorithm 1 per step; a failed Newton solve halves the
+   step, at most max_cuts times). */
+sim_status sim_step(sim_t *s, double dt, sim_step_info *info);
+/* Newton loop of Algorithm 1 for one step of dt from the accepted state
+   (no cuts; on failure the iterate is left where Newton stopped). */
+sim_status sim_newton_solve(sim_t *s, double dt, sim_newton_info *info);
+/* One Newton iteration at the current iterate: assemble, test CNV, solve
+   J dx = -R, update.  info->converged = 1 means CNV already met (no solve). */
+sim_status sim_newton_step(sim_t *s, double dt, sim_newton_info *info);
+/* Solve J x = b with the current Jacobian (FGMRES + the configured
+   preconditioner).  b_dev, x_dev: device pointers, N*b doubles each,
+   component-major; they may not alias.  Returns SIM_ENOCONV_LINEAR (not
+   sticky) when the restart limit is hit; x_dev then holds the last iterate. */
+sim_status sim_linear_solve(sim_t *s, const double *b_dev, double *x_dev, sim_linear_info *info);
+
+/* ---- inspection entry points (used by the parity tests) ---- */
+/* current Newton iterate, host arrays: x[b*N] component-major, phase[N] */
+sim_status sim_set_iterate(sim_t *s, const double *x, const int8_t *phase);
+sim_status sim_get_iterate(sim_t *s, double *x, int8_t *phase);
+/* residual and Jacobian at the current iterate for step length dt */
+sim_status sim_assemble(sim_t *s, double dt);
+sim_status sim_get_residual(sim_t *s, double *R);       /* host, b*N */
+sim_status sim_get_jacobian(sim_t *s, double *J);       /* host, 7*b*b*N */
+sim_status sim_set_jacobian(sim_t *s, const double *J); /* host, 7*b*b*N */
+sim_status sim_cnv(sim_t *s, double dt, double *cnv);
+/* y = J x, device pointers (component-major, FP64) */
+sim_status sim_spmv(sim_t *s, const double *x_dev, double *y_dev);
+sim_status sim_precond_setup(sim_t *s);
+sim_status sim_precond_apply(sim_t *s, const double *r_dev, double *z_dev);
+/* quasi-IMPES weights w[b*N] and pressure-block coefficients ap[7*N] */
+sim_status sim_get_qi(sim_t *s, double *w, double *ap);
+int32_t sim_amg_levels(sim_t *s);
+/* level size and ELL width (level 0 is the 7-point stencil: width 7) */
+sim_status sim_amg_level_info(sim_t *s, int32_t level, int32_t *n, int32_t *width);
+/* fine -> coarse aggregate map of a level (n ints; not for the coarsest) */
+sim_status sim_amg_level_agg(sim_t *s, int32_t level, int32_t *agg);
+/* ELL matrix of a level >= 1: col[width*n] (-1 padding), val[width*n],
+   entry k of row i at k*n + i, columns ascending */
+sim_status sim_amg_level_ell(sim_t *s, int32_t level, int32_t *col, double *val);
+sim_status sim_component_mass(sim_t *s, double *m3);
+sim_status sim_cumulative_well_mass(sim_t *s, double *m3);
+sim_status sim_well_rates(sim_t *s, double *q3);
+sim_status sim_get_stats(sim_t *s, sim_stats *st);
+int32_t sim_block_size(sim_t *s);
+
+const char *sim_last_error(sim_t *s);   /* s may be NULL: last create error */
+void sim_clear_error(sim_t *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

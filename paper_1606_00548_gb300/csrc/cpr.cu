@@ -1,0 +1,992 @@
+// CPR two-stage preconditioner on the device (paper Sec. 2.4.2).
+//
+//   setup (FP64):  quasi-IMPES weights w_i = (1, -d_ps D_ss^-1) from the
+//                  diagonal block; decoupled matrix Ahat (pressure row
+//                  replaced by w^T rows); pressure block A_p; aggregation AMG
+//                  hierarchy of A_p; red-black block ILU(0) (or block-Jacobi)
+//                  of Ahat.
+//   apply (T):     rp = w^T r; e_p = V(1,1)-cycle(A_p, rp);
+//                  r2 = rhat - Ahat[:, p] e_p;  z = ILU0(Ahat)^-1 r2 + e_p.
+// T = double for the plain form, float for the mixed form (FP32 hierarchy,
+// factors and smoothers; the FGMRES outer loop stays FP64).
+//
+// AMG: two pairwise matching passes per level (handshakes among unmatched
+// nodes; candidate = strongest unmatched strong neighbour compared by
+// strength band (binary exponent), then a symmetric splitmix64 pair hash,
+// then the smaller index); piecewise-constant prolongation; Galerkin coarse
+// operators summed in member order then column order; l1-Jacobi V(1,1);
+// dense inverse on the coarsest level.  The setup is deterministic and its
+// integer results do not depend on thread scheduling.
+//
+// Layouts: level 0 is the 7-point stencil A_p [7][N]; coarser levels are ELL,
+// entry k of row i at k*n + i, columns ascending, -1 padding.
+#include <algorithm>
+#include "sim_internal.cuh"
+
+namespace {
+
+constexpr int MAXE = SIM_MAX_ELL;
+
+__device__ __forceinline__ bool skip(const int *done) { return done != nullptr && *(volatile const int *)done; }
+
+// stencil neighbours in ascending column order: -z, -y, -x, centre, +x, +y, +z
+__device__ __constant__ int kAscend[7] = {5, 3, 1, 0, 2, 4, 6};
+
+__device__ __forceinline__ int nbr7(const GridDesc &g, int i, int d) {
+    const int ix = i % g.nx, t = i / g.nx, iy = t % g.ny, iz = t / g.ny;
+    switch (d) {
+    case 0: return i;
+    case 1: return ix > 0 ? i - 1 : -1;
+    case 2: return ix < g.nx - 1 ? i + 1 : -1;
+    case 3: return iy > 0 ? i - g.nx : -1;
+    case 4: return iy < g.ny - 1 ? i + g.nx : -1;
+    case 5: return iz > 0 ? i - g.nx * g.ny : -1;
+    default: return iz < g.nz - 1 ? i + g.nx * g.ny : -1;
+    }
+}
+__device__ __forceinline__ int opp(int d) { return d == 0 ? 0 : ((d & 1) ? d + 1 : d - 1); }
+__device__ __forceinline__ bool is_black(const GridDesc &g, int i) {
+    const int ix = i % g.nx, t = i / g.nx, iy = t % g.ny, iz = t / g.ny;
+    return ((ix + iy + iz) & 1) != 0;
+}
+
+// A row of a level matrix: structured (level 0) or ELL
+template <typename V>
+struct Mat {
+    bool st;
+    GridDesc g;      // structured
+    const V *val;    // structured: [7][n]; ELL: [width][n]
+    const int *col;  // ELL
+    int n, width;
+};
+
+// visit the entries of row i in ascending column order: f(col, val)
+template <typename V, typename F>
+__device__ __forceinline__ void for_row(const Mat<V> &A, int i, F f) {
+    if (A.st) {
+#pragma unroll
+        for (int t = 0; t < 7; t++) {
+            const int d = kAscend[t];
+            const int j = nbr7(A.g, i, d);
+            if (j >= 0) f(j, A.val[(long)d * A.n + i]);
+        }
+    } else {
+        for (int k = 0; k < A.width; k++) {
+            const int j = A.col[(long)k * A.n + i];
+            if (j < 0) break;
+            f(j, A.val[(long)k * A.n + i]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// quasi-IMPES decoupling (FP64, rounding-exact: no contraction)
+// ---------------------------------------------------------------------------
+template <int B>
+__device__ __forceinline__ void qi_weights(const double *__restrict__ J, int N, int i, double *w) {
+    const double D01 = J[(0 * B + 1) * (long)N + i], D11 = J[(1 * B + 1) * (long)N + i];
+    w[0] = 1.0;
+    if constexpr (B == 2) {
+        w[1] = -(D01 / D11);
+    } else {
+        const double D02 = J[(0 * B + 2) * (long)N + i];
+        const double D12 = J[(1 * B + 2) * (long)N + i], D21 = J[(2 * B + 1) * (long)N + i],
+                     D22 = J[(2 * B + 2) * (long)N + i];
+        const double det = __dsub_rn(__dmul_rn(D11, D22), __dmul_rn(D12, D21));
+        w[1] = __ddiv_rn(__dsub_rn(__dmul_rn(D02, D21), __dmul_rn(D01, D22)), det);
+        w[2] = __ddiv_rn(__dsub_rn(__dmul_rn(D01, D12), __dmul_rn(D02, D11)), det);
+    }
+}
+
+// decoupled block (row cell i, direction d) from J and the weights of i
+template <int B>
+__device__ __forceinline__ void ahat_block(const double *__restrict__ J, int N, int i, int d, const double *w, double *A) {
+#pragma unroll
+    for (int r = 0; r < B; r++)
+#pragma unroll
+        for (int c = 0; c < B; c++) A[r * B + c] = J[(long)((d * B + r) * B + c) * N + i];
+#pragma unroll
+    for (int c = 0; c < B; c++) {
+        double t = __dadd_rn(A[c], __dmul_rn(w[1], A[B + c]));
+        if (B == 3) t = __dadd_rn(t, __dmul_rn(w[2], A[2 * B + c]));
+        A[c] = t;
+    }
+}
+
+template <int B, typename T>
+__global__ void qi_kernel(GridDesc g, const double *__restrict__ J, double *__restrict__ qiw, T *__restrict__ qiwT,
+                          double *__restrict__ ap, T *__restrict__ apT, T *__restrict__ ahat) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int N = g.N;
+    if (i >= N) return;
+    double w[3] = {1.0, 0.0, 0.0};
+    qi_weights<B>(J, N, i, w);
+#pragma unroll
+    for (int c = 0; c < B; c++) { qiw[(long)c * N + i] = w[c]; qiwT[(long)c * N + i] = (T)w[c]; }
+    for (int d = 0; d < 7; d++) {
+        double A[B * B];
+        ahat_block<B>(J, N, i, d, w, A);
+        const bool has = nbr7(g, i, d) >= 0;
+        ap[(long)d * N + i] = has ? A[0] : 0.0;
+        apT[(long)d * N + i] = has ? (T)A[0] : (T)0;
+#pragma unroll
+        for (int t = 0; t < B * B; t++) ahat[(long)(d * B * B + t) * N + i] = (T)A[t];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// block inverses and red-black ILU(0) setup (FP64)
+// ---------------------------------------------------------------------------
+template <int B>
+__device__ __forceinline__ void inv_block(const double *A, double *Ai) {
+    if constexpr (B == 2) {
+        const double det = A[0] * A[3] - A[1] * A[2];
+        Ai[0] = A[3] / det; Ai[1] = -A[1] / det; Ai[2] = -A[2] / det; Ai[3] = A[0] / det;
+    } else {
+        const double c00 = A[4] * A[8] - A[5] * A[7];
+        const double c01 = A[5] * A[6] - A[3] * A[8];
+        const double c02 = A[3] * A[7] - A[4] * A[6];
+        const double det = A[0] * c00 + A[1] * c01 + A[2] * c02;
+        const double id = 1.0 / det;
+        Ai[0] = c00 * id; Ai[1] = (A[2] * A[7] - A[1] * A[8]) * id; Ai[2] = (A[1] * A[5] - A[2] * A[4]) * id;
+        Ai[3] = c01 * id; Ai[4] = (A[0] * A[8] - A[2] * A[6]) * id; Ai[5] = (A[2] * A[3] - A[0] * A[5]) * id;
+        Ai[6] = c02 * id; Ai[7] = (A[1] * A[6] - A[0] * A[7]) * id; Ai[8] = (A[0] * A[4] - A[1] * A[3]) * id;
+    }
+}
+
+// mode 0: inverse of Ahat_ii for every cell (block-Jacobi) or red cells only (mode 1);
+// mode 2: inverse of J_ii (plain block-Jacobi, no decoupling)
+template <int B>
+__global__ void diag_inv_kernel(GridDesc g, const double *__restrict__ J, const double *__restrict__ qiw, int mode,
+                                double *__restrict__ dinv) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int N = g.N;
+    if (i >= N) return;
+    if (mode == 1 && is_black(g, i)) return;
+    double w[3] = {1.0, 0.0, 0.0}, A[B * B], Ai[B * B];
+    if (mode == 2) {
+#pragma unroll
+        for (int t = 0; t < B * B; t++) A[t] = J[(long)t * N + i];
+    } else {
+#pragma unroll
+        for (int c = 0; c < B; c++) w[c] = qiw[(long)c * N + i];
+        ahat_block<B>(J, N, i, 0, w, A);
+    }
+    inv_block<B>(A, Ai);
+#pragma unroll
+    for (int t = 0; t < B * B; t++) dinv[(long)t * N + i] = Ai[t];
+}
+
+// black cells: D = Ahat_ii - sum_d Ahat_{i,d} Dinv_k Ahat_{k,opp(d)}
+template <int B>
+__global__ void ilu_black_kernel(GridDesc g, const double *__restrict__ J, const double *__restrict__ qiw,
+                                 double *__restrict__ dinv) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int N = g.N;
+    if (i >= N || !is_black(g, i)) return;
+    double wi[3] = {1.0, 0.0, 0.0};
+#pragma unroll
+    for (int c = 0; c < B; c++) wi[c] = qiw[(long)c * N + i];
+    double D[B * B];
+    ahat_block<B>(J, N, i, 0, wi, D);
+    for (int d = 1; d < 7; d++) {
+        const int k = nbr7(g, i, d);
+        if (k < 0) continue;
+        double wk[3] = {1.0, 0.0, 0.0}, Aik[B * B], Aki[B * B], Dk[B * B], T1[B * B];
+#pragma unroll
+        for (int c = 0; c < B; c++) wk[c] = qiw[(long)c * N + k];
+        ahat_block<B>(J, N, i, d, wi, Aik);
+        ahat_block<B>(J, N, k, opp(d), wk, Aki);
+#pragma unroll
+        for (int t = 0; t < B * B; t++) Dk[t] = dinv[(long)t * N + k];
+#pragma unroll
+        for (int r = 0; r < B; r++)
+#pragma unroll
+            for (int c = 0; c < B; c++) {
+                double s = 0.0;
+#pragma unroll
+                for (int q = 0; q < B; q++) s += Dk[r * B + q] * Aki[q * B + c];
+                T1[r * B + c] = s;
+            }
+#pragma unroll
+        for (int r = 0; r < B; r++)
+#pragma unroll
+            for (int c = 0; c < B; c++) {
+                double s = 0.0;
+#pragma unroll
+                for (int q = 0; q < B; q++) s += Aik[r * B + q] * T1[q * B + c];
+                D[r * B + c] -= s;
+            }
+    }
+    double Di[B * B];
+    inv_block<B>(D, Di);
+#pragma unroll
+    for (int t = 0; t < B * B; t++) dinv[(long)t * N + i] = Di[t];
+}
+
+template <typename T>
+__global__ void cast_kernel(const double *__restrict__ a, T *__restrict__ b, long n) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) b[i] = (T)a[i];
+}
+
+// ---------------------------------------------------------------------------
+// AMG setup kernels (FP64 values, integer results)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long edge_hash(int a, int b) {
+    const unsigned long long lo = (unsigned long long)(a < b ? a : b), hi = (unsigned long long)(a < b ? b : a);
+    unsigned long long z = ((hi << 32) | lo) + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ int strength_band(double a) {
+    return (int)((__double_as_longlong(a) >> 52) & 0x7FF);
+}
+
+__global__ void match_pick_kernel(Mat<double> A, const int *__restrict__ partner, int *__restrict__ pick, double theta) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.n) return;
+    pick[i] = -1;
+    if (partner[i] >= 0) return;
+    double mx = 0.0;
+    for_row(A, i, [&](int j, double a) { if (j != i && -a > mx) mx = -a; });
+    if (mx <= 0.0) return;
+    int best = -1, bs = 0;
+    unsigned long long bh = 0ULL;
+    const double lim = theta * mx;
+    for_row(A, i, [&](int j, double v) {
+        if (j == i || partner[j] >= 0) return;
+        const double a = -v;
+        if (!(a > 0.0) || a < lim) return;
+        const int band = strength_band(a);
+        const unsigned long long h = edge_hash(i, j);
+        if (best < 0 || band > bs || (band == bs && (h > bh || (h == bh && j < best)))) { best = j; bs = band; bh = h; }
+    });
+    pick[i] = best;
+}
+
+__global__ void match_confirm_kernel(int n, const int *__restrict__ pick, int *__restrict__ partner) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int p = pick[i];
+    if (partner[i] < 0 && p >= 0 && pick[p] == i) partner[i] = p;
+}
+
+// exclusive scan of leader flags in chunks of SCAN_CHUNK per block
+constexpr int SCAN_CHUNK = 4096;
+__device__ __forceinline__ int leader_flag(const int *partner, int i) { const int p = partner[i]; return (p < 0 || i < p) ? 1 : 0; }
+
+__global__ void scan_count_kernel(int n, const int *__restrict__ partner, int *__restrict__ bsum) {
+    __shared__ int sh[SIM_THREADS];
+    const int base = blockIdx.x * SCAN_CHUNK;
+    int c = 0;
+    for (int t = threadIdx.x; t < SCAN_CHUNK; t += blockDim.x) {
+        const int i = base + t;
+        if (i < n) c += leader_flag(partner, i);
+    }
+    sh[threadIdx.x] = c;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) bsum[blockIdx.x] = sh[0];
+}
+
+// single block: exclusive scan of nb block sums in place, total into *total
+__global__ void scan_blocks_kernel(int nb, int *__restrict__ bsum, int *__restrict__ total) {
+    __shared__ int carry;
+    __shared__ int sh[1024];
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nb; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const int v = i < nb ? bsum[i] : 0;
+        sh[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+            const int t = (int)threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+            __syncthreads();
+            sh[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (i < nb) bsum[i] = carry + sh[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry += sh[threadIdx.x];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+// ids of leaders; agg of every node; members (leader, partner) of each aggregate ([2][nc])
+__global__ void number_kernel(int n, const int *__restrict__ partner, const int *__restrict__ bsum, int *__restrict__ id,
+                              int nc_cap, int *__restrict__ mem) {
+    __shared__ int sh[SIM_THREADS];
+    const int base = blockIdx.x * SCAN_CHUNK;
+    constexpr int PER = SCAN_CHUNK / SIM_THREADS;
+    const int t0 = base + threadIdx.x * PER;
+    int local = 0;
+    for (int k = 0; k < PER; k++) { const int i = t0 + k; if (i < n) local += leader_flag(partner, i); }
+    sh[threadIdx.x] = local;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+        const int t = (int)threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+        __syncthreads();
+        sh[threadIdx.x] += t;
+        __syncthreads();
+    }
+    int run = bsum[blockIdx.x] + sh[threadIdx.x] - local;
+    for (int k = 0; k < PER; k++) {
+        const int i = t0 + k;
+        if (i >= n) break;
+        if (leader_flag(partner, i)) {
+            id[i] = run;
+            if (run < nc_cap) { mem[run] = i; mem[nc_cap + run] = partner[i]; }
+            run++;
+        }
+    }
+}
+
+__global__ void agg_kernel(int n, const int *__restrict__ partner, const int *__restrict__ id, int *__restrict__ agg) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int p = partner[i];
+    agg[i] = (p < 0 || i < p) ? id[i] : id[p];
+}
+
+// Galerkin row I of P^T A P: members mem[s*nc + I] (s < memw), entries summed
+// in member order then column order, columns sorted ascending.
+// mode 0: row length into len[I]; mode 1: write the ELL row of width W
+__global__ void galerkin_kernel(Mat<double> A, const int *__restrict__ agg, const int *__restrict__ mem, int memw,
+                                int mstride, int nc, int mode, int *__restrict__ len, int W, int *__restrict__ ccol,
+                                double *__restrict__ cval, int *err) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc) return;
+    int cols[MAXE];
+    double vals[MAXE];
+    int cnt = 0;
+    bool over = false;
+    for (int s = 0; s < memw; s++) {
+        const int m = mem[(long)s * mstride + I];
+        if (m < 0) continue;
+        for_row(A, m, [&](int j, double a) {
+            const int Jc = agg[j];
+            int f = -1;
+            for (int t = 0; t < cnt; t++) if (cols[t] == Jc) { f = t; break; }
+            if (f < 0) {
+                if (cnt == MAXE) { over = true; return; }
+                cols[cnt] = Jc; vals[cnt] = 0.0; f = cnt++;
+            }
+            vals[f] = __dadd_rn(vals[f], a);
+        });
+    }
+    if (over) { atomicExch(err, 1); return; }
+    for (int a = 1; a < cnt; a++) {
+        const int cj = cols[a];
+        const double cv = vals[a];
+        int t = a - 1;
+        while (t >= 0 && cols[t] > cj) { cols[t + 1] = cols[t]; vals[t + 1] = vals[t]; t--; }
+        cols[t + 1] = cj; vals[t + 1] = cv;
+    }
+    if (mode == 0) { len[I] = cnt; atomicMax(len + nc, cnt); return; }
+    for (int t = 0; t < W; t++) {
+        ccol[(long)t * nc + I] = t < cnt ? cols[t] : -1;
+        cval[(long)t * nc + I] = t < cnt ? vals[t] : 0.0;
+    }
+}
+
+__global__ void compose_kernel(int n, const int *__restrict__ aggA, const int *__restrict__ aggB, int *__restrict__ agg) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) agg[i] = aggB[aggA[i]];
+}
+// members of the composed aggregate I: pass-2 members (stride sB) expanded
+// into their pass-1 members (stride sA), slot order (a, c)
+__global__ void compose_mem_kernel(int n2, const int *__restrict__ memA, int sA, const int *__restrict__ memB, int sB,
+                                   int *__restrict__ mem4) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= n2) return;
+    for (int a = 0; a < 2; a++) {
+        const int m1 = memB[(long)a * sB + I];
+        for (int c = 0; c < 2; c++) mem4[(long)(2 * a + c) * n2 + I] = m1 >= 0 ? memA[(long)c * sA + m1] : -1;
+    }
+}
+
+template <typename T>
+__global__ void l1_kernel(Mat<double> A, T *__restrict__ dinv) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.n) return;
+    double s = 0.0;
+    for_row(A, i, [&](int, double a) { s += fabs(a); });
+    dinv[i] = (T)(1.0 / s);
+}
+
+__global__ void dense_kernel(Mat<double> A, double *__restrict__ D) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.n) return;
+    for_row(A, i, [&](int j, double a) { D[(long)i * A.n + j] += a; });
+}
+
+__global__ void identity_kernel(int n, double *__restrict__ I) {
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t < (long)n * n) I[t] = ((t / n) == (t % n)) ? 1.0 : 0.0;
+}
+
+// Gauss-Jordan step k with partial pivoting (one block): pick the pivot row,
+// swap, scale the pivot row, and keep the column multipliers in f
+__global__ void gj_pivot_kernel(int n, int k, double *__restrict__ A, double *__restrict__ Inv, double *__restrict__ f) {
+    __shared__ double bv[1024];
+    __shared__ int bi[1024];
+    __shared__ double piv;
+    double best = -1.0;
+    int arg = k;
+    for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+        const double v = fabs(A[(long)i * n + k]);
+        if (v > best) { best = v; arg = i; }
+    }
+    bv[threadIdx.x] = best; bi[threadIdx.x] = arg;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            const double o = bv[threadIdx.x + s];
+            const int oi = bi[threadIdx.x + s];
+            if (o > bv[threadIdx.x] || (o == bv[threadIdx.x] && oi < bi[threadIdx.x])) { bv[threadIdx.x] = o; bi[threadIdx.x] = oi; }
+        }
+        __syncthreads();
+    }
+    const int p = bi[0];
+    if (p != k)
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            double t = A[(long)k * n + j]; A[(long)k * n + j] = A[(long)p * n + j]; A[(long)p * n + j] = t;
+            t = Inv[(long)k * n + j]; Inv[(long)k * n + j] = Inv[(long)p * n + j]; Inv[(long)p * n + j] = t;
+        }
+    __syncthreads();
+    if (threadIdx.x == 0) piv = A[(long)k * n + k];
+    __syncthreads();
+    const double ip = 1.0 / piv;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) f[i] = A[(long)i * n + k];
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        A[(long)k * n + j] *= ip;
+        Inv[(long)k * n + j] *= ip;
+    }
+}
+
+__global__ void gj_elim_kernel(int n, int k, double *__restrict__ A, double *__restrict__ Inv, const double *__restrict__ f) {
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= (long)n * n) return;
+    const int i = (int)(t / n), j = (int)(t % n);
+    if (i == k) return;
+    const double fi = f[i];
+    if (j >= k) A[(long)i * n + j] -= fi * A[(long)k * n + j];
+    Inv[(long)i * n + j] -= fi * Inv[(long)k * n + j];
+}
+
+// ---------------------------------------------------------------------------
+// apply kernels (precision T)
+// ---------------------------------------------------------------------------
+template <int B, typename T>
+__global__ void restrict_p_kernel(int N, const double *__restrict__ r, const T *__restrict__ wT, const T *__restrict__ dinv0,
+                                  T *__restrict__ f0, T *__restrict__ e0, const int *done) {
+    if (skip(done)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    T t = (T)r[i] + wT[(long)N + i] * (T)r[(long)N + i];
+    if (B == 3) t += wT[2L * N + i] * (T)r[2L * N + i];
+    f0[i] = t;
+    e0[i] = t * dinv0[i];
+}
+
+// f_c = P^T (f - A e) ; e_c = f_c / l1 (pre-smoothing on the coarse level)
+template <typename T>
+__global__ void resid_restrict_kernel(Mat<T> A, const T *__restrict__ f, const T *__restrict__ e, const int *__restrict__ mem4,
+                                      int nc, T *__restrict__ fc, T *__restrict__ ec, const T *__restrict__ dinvc,
+                                      const int *done) {
+    if (skip(done)) return;
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc) return;
+    T s = (T)0;
+    for (int a = 0; a < 4; a++) {
+        const int m = mem4[(long)a * nc + I];
+        if (m < 0) continue;
+        T t = (T)0;
+        for_row(A, m, [&](int j, T v) { t += v * e[j]; });
+        s += f[m] - t;
+    }
+    fc[I] = s;
+    if (ec) ec[I] = s * dinvc[I];
+}
+
+// e2 = ep + (f - A ep) / l1 with ep = e + P e_c  (prolongation + post-smoothing)
+template <typename T>
+__global__ void prolong_smooth_kernel(Mat<T> A, const T *__restrict__ f, const T *__restrict__ e, const T *__restrict__ ec,
+                                      const int *__restrict__ agg, const T *__restrict__ dinv, T *__restrict__ e2,
+                                      const int *done) {
+    if (skip(done)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.n) return;
+    T t = (T)0;
+    for_row(A, i, [&](int j, T v) { t += v * (e[j] + ec[agg[j]]); });
+    const T ep = e[i] + ec[agg[i]];
+    e2[i] = ep + (f[i] - t) * dinv[i];
+}
+
+// e = Inv f on the coarsest level: one warp per row
+template <typename T>
+__global__ void coarse_solve_kernel(int n, const T *__restrict__ Inv, const T *__restrict__ f, T *__restrict__ e,
+                                    const int *done) {
+    if (skip(done)) return;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    T s = (T)0;
+    for (int j = lane; j < n; j += 32) s += Inv[(long)warp * n + j] * f[j];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) e[warp] = s;
+}
+
+// stage F, pass 1: r2 = rhat - Ahat[:,p] e_p; red cells z = Dinv r2, black keep r2
+template <int B, typename T>
+__global__ void stage2_a_kernel(GridDesc g, const double *__restrict__ r, const T *__restrict__ wT,
+                                const T *__restrict__ ahat, const T *__restrict__ dinv, const T *__restrict__ ep,
+                                T *__restrict__ r2, T *__restrict__ z, int rb, const int *done) {
+    if (skip(done)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int N = g.N;
+    if (i >= N) return;
+    T v[B];
+#pragma unroll
+    for (int c = 0; c < B; c++) v[c] = (T)r[(long)c * N + i];
+    T rp = v[0] + wT[(long)N + i] * v[1];
+    if (B == 3) rp += wT[2L * N + i] * v[2];
+    v[0] = rp;
+#pragma unroll
+    for (int d = 0; d < 7; d++) {
+        const int j = nbr7(g, i, d);
+        if (j < 0) continue;
+        const T e = ep[j];
+#pragma unroll
+        for (int c = 0; c < B; c++) v[c] -= ahat[(long)(d * B * B + c * B) * N + i] * e;
+    }
+    if (rb && is_black(g, i)) {
+#pragma unroll
+        for (int c = 0; c < B; c++) r2[(long)c * N + i] = v[c];
+        return;
+    }
+#pragma unroll
+    for (int c = 0; c < B; c++) {
+        T s = (T)0;
+#pragma unroll
+        for (int q = 0; q < B; q++) s += dinv[(long)(c * B + q) * N + i] * v[q];
+        z[(long)c * N + i] = s;
+    }
+}
+
+// stage F, pass 2 (black cells): z = Dinv (r2 - sum_d Ahat_{i,d} z_red(nbr)); out = z + e_p
+template <int B, typename T, typename TZ>
+__global__ void stage2_b_kernel(GridDesc g, const T *__restrict__ ahat, const T *__restrict__ dinv,
+                                const T *__restrict__ r2, T *__restrict__ z, const T *__restrict__ ep, TZ *__restrict__ out,
+                                const int *done) {
+    if (skip(done)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int N = g.N;
+    if (i >= N || !is_black(g, i)) return;
+    T t[B];
+#pragma unroll
+    for (int c = 0; c < B; c++) t[c] = r2[(long)c * N + i];
+#pragma unroll
+    for (int d = 1; d < 7; d++) {
+        const int k = nbr7(g, i, d);
+        if (k < 0) continue;
+        T zk[B];
+#pragma unroll
+        for (int c = 0; c < B; c++) zk[c] = z[(long)c * N + k];
+#pragma unroll
+        for (int r = 0; r < B; r++)
+#pragma unroll
+            for (int c = 0; c < B; c++) t[r] -= ahat[(long)(d * B * B + r * B + c) * N + i] * zk[c];
+    }
+#pragma unroll
+    for (int r = 0; r < B; r++) {
+        T s = (T)0;
+#pragma unroll
+        for (int q = 0; q < B; q++) s += dinv[(long)(r * B + q) * N + i] * t[q];
+        z[(long)r * N + i] = s;
+        out[(long)r * N + i] = (TZ)(r == 0 ? s + ep[i] : s);
+    }
+}
+
+// stage F, pass 3 (red cells): x = z - Dinv sum_d Ahat_{i,d} z_black(nbr); out = x + e_p
+// (rb = 0: block-Jacobi, out = z + e_p for every cell)
+template <int B, typename T, typename TZ>
+__global__ void stage2_c_kernel(GridDesc g, const T *__restrict__ ahat, const T *__restrict__ dinv, const T *__restrict__ z,
+                                const T *__restrict__ ep, TZ *__restrict__ out, int rb, const int *done) {
+    if (skip(done)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int N = g.N;
+    if (i >= N) return;
+    if (!rb) {
+#pragma unroll
+        for (int r = 0; r < B; r++) {
+            const T s = z[(long)r * N + i];
+            out[(long)r * N + i] = (TZ)(r == 0 ? s + ep[i] : s);
+        }
+        return;
+    }
+    if (is_black(g, i)) return;
+    T t[B];
+#pragma unroll
+    for (int c = 0; c < B; c++) t[c] = (T)0;
+#pragma unroll
+    for (int d = 1; d < 7; d++) {
+        const int k = nbr7(g, i, d);
+        if (k < 0) continue;
+        T zk[B];
+#pragma unroll
+        for (int c = 0; c < B; c++) zk[c] = z[(long)c * N + k];
+#pragma unroll
+        for (int r = 0; r < B; r++)
+#pragma unroll
+            for (int c = 0; c < B; c++) t[r] += ahat[(long)(d * B * B + r * B + c) * N + i] * zk[c];
+    }
+#pragma unroll
+    for (int r = 0; r < B; r++) {
+        T s = (T)0;
+#pragma unroll
+        for (int q = 0; q < B; q++) s += dinv[(long)(r * B + q) * N + i] * t[q];
+        const T x = z[(long)r * N + i] - s;
+        out[(long)r * N + i] = (TZ)(r == 0 ? x + ep[i] : x);
+    }
+}
+
+// no preconditioner / plain block-Jacobi on J (no decoupling)
+template <int B, typename TZ>
+__global__ void simple_prec_kernel(int N, const double *__restrict__ r, const double *__restrict__ dinv, TZ *__restrict__ z,
+                                   int use_dinv, const int *done) {
+    if (skip(done)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double v[B];
+#pragma unroll
+    for (int c = 0; c < B; c++) v[c] = r[(long)c * N + i];
+#pragma unroll
+    for (int rr = 0; rr < B; rr++) {
+        double s = v[rr];
+        if (use_dinv) {
+            s = 0.0;
+#pragma unroll
+            for (int q = 0; q < B; q++) s += dinv[(long)(rr * B + q) * N + i] * v[q];
+        }
+        z[(long)rr * N + i] = (TZ)s;
+    }
+}
+
+}  // namespace
+
+// ===========================================================================
+// host side
+// ===========================================================================
+bool sim_mixed(const sim_t *s) { return s->opt.precision == SIM_PRECISION_MIXED; }
+
+static void *dev_alloc_async(sim_t *s, size_t bytes) {
+    void *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(&p, bytes, s->stream);
+    if (e != cudaSuccess) { sim_cuda_ok(s, e, "cudaMallocAsync (AMG hierarchy)"); return nullptr; }
+    return p;
+}
+static void dev_free_async(sim_t *s, void *p) { if (p) cudaFreeAsync(p, s->stream); }
+
+static void free_level(sim_t *s, AmgLevel &L) {
+    // valT may alias the FP64 values or the level-0 stencil owned by the handle
+    if (L.valT != (void *)L.val && L.valT != s->apT) dev_free_async(s, L.valT);
+    dev_free_async(s, L.col); dev_free_async(s, L.val); dev_free_async(s, L.dinvT);
+    dev_free_async(s, L.agg); dev_free_async(s, L.mem4); dev_free_async(s, L.f); dev_free_async(s, L.e);
+    dev_free_async(s, L.e2); dev_free_async(s, L.coarse_inv);
+    L = AmgLevel();
+}
+
+void cpr_free(sim_t *s) {
+    for (auto &L : s->lev) free_level(s, L);
+    s->lev.clear();
+}
+
+static Mat<double> level_mat(sim_t *s, const AmgLevel &L, int l) {
+    Mat<double> A;
+    A.st = (l == 0); A.g = s->gd; A.n = L.n; A.width = L.width;
+    A.val = l == 0 ? s->ap : L.val;
+    A.col = L.col;
+    return A;
+}
+template <typename T>
+static Mat<T> level_matT(sim_t *s, const AmgLevel &L, int l) {
+    Mat<T> A;
+    A.st = (l == 0); A.g = s->gd; A.n = L.n; A.width = L.width;
+    A.val = (const T *)L.valT;
+    A.col = L.col;
+    return A;
+}
+
+// one pairwise pass on A (n rows): partner -> agg (n), mem [2][nc]; returns nc
+static int pair_pass(sim_t *s, const Mat<double> &A, int *agg, int *mem, int mem_cap) {
+    const int n = A.n;
+    if (!sim_cuda_ok(s, cudaMemsetAsync(s->partner, 0xff, sizeof(int) * n, s->stream), "memset")) return -1;
+    for (int r = 0; r < s->opt.amg_rounds; r++) {
+        match_pick_kernel<<<sim_blocks(n), SIM_THREADS, 0, s->stream>>>(A, s->partner, s->pick, s->opt.amg_theta);
+        s->launches++;
+        match_confirm_kernel<<<sim_blocks(n), SIM_THREADS, 0, s->stream>>>(n, s->pick, s->partner);
+        s->launches++;
+    }
+    const int nb = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
+    scan_count_kernel<<<nb, SIM_THREADS, 0, s->stream>>>(n, s->partner, s->scan);
+    scan_blocks_kernel<<<1, 1024, 0, s->stream>>>(nb, s->scan, s->iscal);
+    number_kernel<<<nb, SIM_THREADS, 0, s->stream>>>(n, s->partner, s->scan, s->pick, mem_cap, mem);
+    agg_kernel<<<sim_blocks(n), SIM_THREADS, 0, s->stream>>>(n, s->partner, s->pick, agg);
+    s->launches += 4;
+    if (!sim_cuda_ok(s, cudaGetLastError(), "AMG matching")) return -1;
+    int nc = 0;
+    if (!sim_cuda_ok(s, cudaMemcpyAsync(&s->h_pinned[0], s->iscal, sizeof(int), cudaMemcpyDeviceToHost, s->stream), "copy")) return -1;
+    if (!sim_cuda_ok(s, cudaStreamSynchronize(s->stream), "sync")) return -1;
+    memcpy(&nc, &s->h_pinned[0], sizeof(int));
+    return nc;
+}
+
+// Galerkin product into a freshly allocated ELL matrix; returns width or -1.
+// mem: members [2][mstride] of each coarse row
+static int galerkin(sim_t *s, const Mat<double> &A, const int *agg, const int *mem, int mstride, int nc, int **col,
+                    double **val) {
+    int *len = (int *)dev_alloc_async(s, sizeof(int) * (nc + 1));
+    if (!len) return -1;
+    if (!sim_cuda_ok(s, cudaMemsetAsync(len + nc, 0, sizeof(int), s->stream), "memset")) return -1;
+    if (!sim_cuda_ok(s, cudaMemsetAsync(s->iscal + 1, 0, sizeof(int), s->stream), "memset")) return -1;
+    galerkin_kernel<<<sim_blocks(nc), SIM_THREADS, 0, s->stream>>>(A, agg, mem, 2, mstride, nc, 0, len, 0, nullptr, nullptr,
+                                                                   s->iscal + 1);
+    s->launches++;
+    int hv[2];
+    if (!sim_cuda_ok(s, cudaMemcpyAsync(&s->h_pinned[0], len + nc, sizeof(int), cudaMemcpyDeviceToHost, s->stream), "copy") ||
+        !sim_cuda_ok(s, cudaMemcpyAsync((char *)&s->h_pinned[0] + 4, s->iscal + 1, sizeof(int), cudaMemcpyDeviceToHost, s->stream), "copy") ||
+        !sim_cuda_ok(s, cudaStreamSynchronize(s->stream), "sync"))
+        return -1;
+    memcpy(hv, &s->h_pinned[0], 8);
+    if (hv[1]) { sim_fail(s, SIM_ELIMIT, "AMG coarse row wider than the setup limit"); return -1; }
+    const int W = hv[0] < 1 ? 1 : hv[0];
+    *col = (int *)dev_alloc_async(s, sizeof(int) * (size_t)W * nc);
+    *val = (double *)dev_alloc_async(s, sizeof(double) * (size_t)W * nc);
+    if (!*col || !*val) return -1;
+    galerkin_kernel<<<sim_blocks(nc), SIM_THREADS, 0, s->stream>>>(A, agg, mem, 2, mstride, nc, 1, len, W, *col, *val,
+                                                                   s->iscal + 1);
+    s->launches++;
+    dev_free_async(s, len);
+    if (!sim_cuda_ok(s, cudaGetLastError(), "Galerkin")) return -1;
+    return W;
+}
+
+template <typename T>
+static sim_status finish_levels(sim_t *s) {
+    // l1 inverse diagonals, apply-precision values, work vectors; coarsest dense inverse
+    const int nl = (int)s->lev.size();
+    for (int l = 0; l < nl; l++) {
+        AmgLevel &L = s->lev[l];
+        Mat<double> A = level_mat(s, L, l);
+        L.dinvT = dev_alloc_async(s, sizeof(T) * L.n);
+        L.f = dev_alloc_async(s, sizeof(T) * L.n);
+        L.e = dev_alloc_async(s, sizeof(T) * L.n);
+        L.e2 = dev_alloc_async(s, sizeof(T) * L.n);
+        if (!L.dinvT || !L.f || !L.e || !L.e2) return s->err;
+        l1_kernel<T><<<sim_blocks(L.n), SIM_THREADS, 0, s->stream>>>(A, (T *)L.dinvT);
+        s->launches++;
+        if (l > 0) {
+            if (sizeof(T) == sizeof(double)) {
+                L.valT = L.val;              // FP64 apply reads the setup values
+            } else {
+                L.valT = dev_alloc_async(s, sizeof(T) * (size_t)L.width * L.n);
+                if (!L.valT) return s->err;
+                cast_kernel<T><<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(L.val, (T *)L.valT, (long)L.width * L.n);
+                s->launches++;
+            }
+        }
+    }
+    // coarsest: dense Gauss-Jordan inverse in FP64
+    AmgLevel &C = s->lev[nl - 1];
+    const int n = C.n;
+    double *D = (double *)dev_alloc_async(s, sizeof(double) * (size_t)n * n);
+    double *Inv = (double *)dev_alloc_async(s, sizeof(double) * (size_t)n * n);
+    double *f = (double *)dev_alloc_async(s, sizeof(double) * n);
+    if (!D || !Inv || !f) return s->err;
+    SIM_CK(s, cudaMemsetAsync(D, 0, sizeof(double) * (size_t)n * n, s->stream));
+    dense_kernel<<<sim_blocks(n), SIM_THREADS, 0, s->stream>>>(level_mat(s, C, nl - 1), D);
+    identity_kernel<<<sim_blocks((long)n * n), SIM_THREADS, 0, s->stream>>>(n, Inv);
+    s->launches += 2;
+    for (int k = 0; k < n; k++) {
+        gj_pivot_kernel<<<1, 1024, 0, s->stream>>>(n, k, D, Inv, f);
+        gj_elim_kernel<<<sim_blocks((long)n * n), SIM_THREADS, 0, s->stream>>>(n, k, D, Inv, f);
+        s->launches += 2;
+    }
+    C.coarse_inv = dev_alloc_async(s, sizeof(T) * (size_t)n * n);
+    if (!C.coarse_inv) return s->err;
+    cast_kernel<T><<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(Inv, (T *)C.coarse_inv, (long)n * n);
+    s->launches++;
+    dev_free_async(s, D); dev_free_async(s, Inv); dev_free_async(s, f);
+    SIM_CK(s, cudaGetLastError());
+    return SIM_OK;
+}
+
+static sim_status amg_setup(sim_t *s) {
+    cpr_free(s);
+    AmgLevel L0;
+    L0.n = s->N; L0.width = 7;
+    s->lev.push_back(L0);
+    const int cmax = s->opt.amg_coarse_max;
+    while (true) {
+        const int l = (int)s->lev.size() - 1;
+        AmgLevel &L = s->lev[l];
+        if (L.n <= cmax || (int)s->lev.size() >= s->opt.amg_max_levels) break;
+        const int n = L.n;
+        Mat<double> A = level_mat(s, L, l);
+        const int n1 = pair_pass(s, A, s->aggA, s->memA, n);
+        if (n1 < 0) return s->err;
+        int *c1 = nullptr; double *v1 = nullptr;
+        const int W1 = galerkin(s, A, s->aggA, s->memA, n, n1, &c1, &v1);
+        if (W1 < 0) return s->err;
+        Mat<double> A1; A1.st = false; A1.g = s->gd; A1.n = n1; A1.width = W1; A1.col = c1; A1.val = v1;
+        const int n2 = pair_pass(s, A1, s->aggB, s->memB, n1);
+        if (n2 < 0) return s->err;
+        if (4L * n2 > 3L * n) {   // coarsening stalled: this level is the coarsest
+            dev_free_async(s, c1); dev_free_async(s, v1);
+            break;
+        }
+        AmgLevel C;
+        C.n = n2;
+        const int W2 = galerkin(s, A1, s->aggB, s->memB, n1, n2, &C.col, &C.val);
+        if (W2 < 0) return s->err;
+        C.width = W2;
+        AmgLevel &Lr = s->lev[l];    // (reference still valid: no push yet)
+        Lr.agg = (int *)dev_alloc_async(s, sizeof(int) * n);
+        Lr.mem4 = (int *)dev_alloc_async(s, sizeof(int) * 4 * (size_t)n2);
+        if (!Lr.agg || !Lr.mem4) return s->err;
+        compose_kernel<<<sim_blocks(n), SIM_THREADS, 0, s->stream>>>(n, s->aggA, s->aggB, Lr.agg);
+        compose_mem_kernel<<<sim_blocks(n2), SIM_THREADS, 0, s->stream>>>(n2, s->memA, n, s->memB, n1, Lr.mem4);
+        s->launches += 2;
+        dev_free_async(s, c1); dev_free_async(s, v1);
+        s->lev.push_back(C);
+    }
+    if (s->lev.back().n > 1024) return sim_fail(s, SIM_ELIMIT, "AMG coarsest level larger than 1024 rows");
+    return sim_mixed(s) ? finish_levels<float>(s) : finish_levels<double>(s);
+}
+
+template <int B, typename T>
+static sim_status setup_bt(sim_t *s) {
+    const int N = s->N;
+    const int nb = sim_blocks(N);
+    if (s->opt.precond == SIM_PRECOND_BJACOBI) {
+        diag_inv_kernel<B><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, s->J, s->qiw, 2, s->dinv_d);
+        SIM_LAUNCHED(s);
+        return SIM_OK;
+    }
+    if (s->opt.precond != SIM_PRECOND_CPR) return SIM_OK;
+    qi_kernel<B, T><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, s->J, s->qiw, (T *)s->qiwT, s->ap, (T *)s->apT, (T *)s->ahat);
+    SIM_LAUNCHED(s);
+    if (amg_setup(s) != SIM_OK) return s->err;
+    s->lev[0].valT = s->apT;
+    const int rb = s->opt.stage2 == SIM_STAGE2_ILU0_RB;
+    diag_inv_kernel<B><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, s->J, s->qiw, rb ? 1 : 0, s->dinv_d);
+    SIM_LAUNCHED(s);
+    if (rb) {
+        ilu_black_kernel<B><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, s->J, s->qiw, s->dinv_d);
+        SIM_LAUNCHED(s);
+    }
+    if (sizeof(T) != sizeof(double)) {
+        cast_kernel<T><<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(s->dinv_d, (T *)s->dinv, (long)B * B * N);
+        SIM_LAUNCHED(s);
+    }
+    return SIM_OK;
+}
+
+sim_status cpr_setup(sim_t *s) {
+    sim_status st;
+    if (s->b == 2) st = sim_mixed(s) ? setup_bt<2, float>(s) : setup_bt<2, double>(s);
+    else st = sim_mixed(s) ? setup_bt<3, float>(s) : setup_bt<3, double>(s);
+    if (st != SIM_OK) return st;
+    s->precond_ready = true;
+    return SIM_OK;
+}
+
+template <typename T>
+static sim_status vcycle(sim_t *s, const int *done) {
+    const int nl = (int)s->lev.size();
+    // down: f_{l+1} = P^T (f_l - A_l e_l), e_{l+1} = f_{l+1} / l1 (not on the coarsest)
+    for (int l = 0; l + 1 < nl; l++) {
+        AmgLevel &L = s->lev[l], &C = s->lev[l + 1];
+        const bool coarsest = (l + 1 == nl - 1);
+        resid_restrict_kernel<T><<<sim_blocks(C.n), SIM_THREADS, 0, s->stream>>>(
+            level_matT<T>(s, L, l), (const T *)L.f, (const T *)L.e, L.mem4, C.n, (T *)C.f,
+            coarsest ? nullptr : (T *)C.e, (const T *)C.dinvT, done);
+        SIM_LAUNCHED(s);
+    }
+    AmgLevel &Cn = s->lev[nl - 1];
+    coarse_solve_kernel<T><<<sim_blocks((long)Cn.n * 32), SIM_THREADS, 0, s->stream>>>(Cn.n, (const T *)Cn.coarse_inv,
+                                                                                    (const T *)Cn.f, (T *)Cn.e, done);
+    SIM_LAUNCHED(s);
+    // up: e_l <- smooth(e_l + P e_{l+1})
+    for (int l = nl - 2; l >= 0; l--) {
+        AmgLevel &L = s->lev[l], &C = s->lev[l + 1];
+        const T *ec = (l + 1 == nl - 1) ? (const T *)C.e : (const T *)C.e2;
+        prolong_smooth_kernel<T><<<sim_blocks(L.n), SIM_THREADS, 0, s->stream>>>(
+            level_matT<T>(s, L, l), (const T *)L.f, (const T *)L.e, ec, L.agg, (const T *)L.dinvT, (T *)L.e2, done);
+        SIM_LAUNCHED(s);
+    }
+    return SIM_OK;
+}
+
+template <int B, typename T, typename TZ>
+static sim_status apply_btz(sim_t *s, const double *r, TZ *z, const int *done) {
+    const int N = s->N;
+    const int nb = sim_blocks(N);
+    if (s->opt.precond != SIM_PRECOND_CPR) {
+        simple_prec_kernel<B, TZ><<<nb, SIM_THREADS, 0, s->stream>>>(N, r, s->dinv_d, z,
+                                                                   s->opt.precond == SIM_PRECOND_BJACOBI, done);
+        SIM_LAUNCHED(s);
+        return SIM_OK;
+    }
+    AmgLevel &L0 = s->lev[0];
+    restrict_p_kernel<B, T><<<nb, SIM_THREADS, 0, s->stream>>>(N, r, (const T *)s->qiwT, (const T *)L0.dinvT, (T *)L0.f,
+                                                              (T *)L0.e, done);
+    SIM_LAUNCHED(s);
+    const T *ep;
+    if (s->lev.size() == 1) {
+        coarse_solve_kernel<T><<<sim_blocks((long)L0.n * 32), SIM_THREADS, 0, s->stream>>>(L0.n, (const T *)L0.coarse_inv,
+                                                                                        (const T *)L0.f, (T *)L0.e2, done);
+        SIM_LAUNCHED(s);
+    } else if (vcycle<T>(s, done) != SIM_OK) {
+        return s->err;
+    }
+    ep = (const T *)L0.e2;
+    const int rb = s->opt.stage2 == SIM_STAGE2_ILU0_RB;
+    const T *dinv = sizeof(T) == sizeof(double) ? (const T *)s->dinv_d : (const T *)s->dinv;
+    stage2_a_kernel<B, T><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, r, (const T *)s->qiwT, (const T *)s->ahat, dinv, ep,
+                                                            (T *)s->r2, (T *)s->zr, rb, done);
+    SIM_LAUNCHED(s);
+    if (rb) {
+        stage2_b_kernel<B, T, TZ><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, (const T *)s->ahat, dinv, (const T *)s->r2,
+                                                                    (T *)s->zr, ep, z, done);
+        SIM_LAUNCHED(s);
+    }
+    stage2_c_kernel<B, T, TZ><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, (const T *)s->ahat, dinv, (const T *)s->zr, ep, z,
+                                                                rb, done);
+    SIM_LAUNCHED(s);
+    return SIM_OK;
+}
+
+sim_status cpr_apply(sim_t *s, const double *r, void *z, const int *done) {
+    if (!s->precond_ready) { if (cpr_setup(s) != SIM_OK) return s->err; }
+    if (s->b == 2)
+        return sim_mixed(s) ? apply_btz<2, float, float>(s, r, (float *)z, done) : apply_btz<2, double, double>(s, r, (double *)z, done);
+    return sim_mixed(s) ? apply_btz<3, float, float>(s, r, (float *)z, done) : apply_btz<3, double, double>(s, r, (double *)z, done);
+}
+
+sim_status cpr_copy_level_ell(sim_t *s, int level, int *col, double *val) {
+    if (level < 1 || level >= (int)s->lev.size()) return sim_fail(s, SIM_EINVAL, "level out of range");
+    const AmgLevel &L = s->lev[level];
+    SIM_CK(s, cudaMemcpyAsync(col, L.col, sizeof(int) * (size_t)L.width * L.n, cudaMemcpyDeviceToHost, s->stream));
+    SIM_CK(s, cudaMemcpyAsync(val, L.val, sizeof(double) * (size_t)L.width * L.n, cudaMemcpyDeviceToHost, s->stream));
+    SIM_CK(s, cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}

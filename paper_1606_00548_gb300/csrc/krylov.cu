@@ -1,0 +1,373 @@
+// Block-stencil SpMV and right-preconditioned FGMRES(m) (FP64 outer loop).
+//
+// FGMRES with classical Gram-Schmidt plus one full re-orthogonalisation
+// (CGS2), Givens rotations and restarts; it solves the Newton correction of
+// Algorithm 1 to ||b - J dx|| <= theta ||b||.  One inner iteration is a fixed
+// sequence of kernels with no host synchronisation: every kernel first reads
+// the device flag ctl->done and returns at once when the Arnoldi residual
+// estimate has already met the tolerance, so a whole restart cycle is
+// enqueued up front and the host reads the control block once per cycle.
+//
+// Reductions are deterministic: a fixed grid, per-block partials reduced in
+// block order by the last block to finish (ticket counter).
+#include "sim_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ bool skip(const int *done) { return done != nullptr && *(volatile const int *)done; }
+
+template <typename X> __device__ __forceinline__ double ld(const X *p, long i) { return (double)p[i]; }
+
+// y = J x on the 7-point block stencil; blocks of absent neighbours are skipped
+template <int B, typename X>
+__global__ void __launch_bounds__(SIM_THREADS) spmv_kernel(GridDesc g, const double *__restrict__ J,
+                                                           const X *__restrict__ x, double *__restrict__ y,
+                                                           const int *done) {
+    if (skip(done)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int N = g.N;
+    if (i >= N) return;
+    const int ix = i % g.nx, t = i / g.nx, iy = t % g.ny, iz = t / g.ny;
+    const int nxy = g.nx * g.ny;
+    double acc[B];
+#pragma unroll
+    for (int r = 0; r < B; r++) acc[r] = 0.0;
+#pragma unroll
+    for (int d = 0; d < 7; d++) {
+        int j;
+        if (d == 0) j = i;
+        else if (d == 1) j = ix > 0 ? i - 1 : -1;
+        else if (d == 2) j = ix < g.nx - 1 ? i + 1 : -1;
+        else if (d == 3) j = iy > 0 ? i - g.nx : -1;
+        else if (d == 4) j = iy < g.ny - 1 ? i + g.nx : -1;
+        else if (d == 5) j = iz > 0 ? i - nxy : -1;
+        else j = iz < g.nz - 1 ? i + nxy : -1;
+        if (j < 0) continue;
+        double xv[B];
+#pragma unroll
+        for (int c = 0; c < B; c++) xv[c] = ld(x, (long)c * N + j);
+#pragma unroll
+        for (int r = 0; r < B; r++) {
+            double s = 0.0;
+#pragma unroll
+            for (int c = 0; c < B; c++) s += J[(long)((d * B + r) * B + c) * N + i] * xv[c];
+            acc[r] += s;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < B; r++) y[(long)r * N + i] = acc[r];
+}
+
+// ---- block reduction of nv partial sums into partials[k][gridDim] ----------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int NV>
+__device__ void block_partials(const double (&acc)[NV], int nv, double *partials) {
+    __shared__ double sh[SIM_THREADS / 32][NV];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        if (k < nv) {
+            double v = warp_sum(acc[k]);
+            if (lane == 0) sh[wid][k] = v;
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += sh[w][k];
+        partials[k * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+// returns true in the last block to arrive (all partials visible)
+__device__ bool last_block(unsigned int *ticket) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int t = atomicAdd(ticket, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+__device__ void fold(const double *partials, int nv, double *out) {
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < (int)gridDim.x; b++) s += ((volatile const double *)partials)[k * gridDim.x + b];
+        out[k] = s;
+    }
+}
+
+constexpr int NVMAX = SIM_MAX_M + 1;
+
+// h[k] = V_k . w, k < nv
+__global__ void __launch_bounds__(SIM_THREADS) dots_kernel(const double *__restrict__ V, const double *__restrict__ w,
+                                                           long n, int nv, double *partials, unsigned int *ticket,
+                                                           double *out, const int *done) {
+    if (skip(done)) return;
+    double acc[NVMAX];
+#pragma unroll
+    for (int k = 0; k < NVMAX; k++) acc[k] = 0.0;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const double wi = w[i];
+#pragma unroll
+        for (int k = 0; k < NVMAX; k++)
+            if (k < nv) acc[k] += V[k * n + i] * wi;
+    }
+    block_partials<NVMAX>(acc, nv, partials);
+    if (last_block(ticket)) {
+        fold(partials, nv, out);
+        if (threadIdx.x == 0) *ticket = 0u;
+    }
+}
+
+// w -= sum_k h[k] V_k ; out[k] = V_k . w (second Gram-Schmidt pass)
+__global__ void __launch_bounds__(SIM_THREADS) orth_dots_kernel(const double *__restrict__ V, double *__restrict__ w,
+                                                                long n, int nv, const double *h, double *partials,
+                                                                unsigned int *ticket, double *out, const int *done) {
+    if (skip(done)) return;
+    __shared__ double hs[NVMAX];
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) hs[k] = h[k];
+    __syncthreads();
+    double acc[NVMAX];
+#pragma unroll
+    for (int k = 0; k < NVMAX; k++) acc[k] = 0.0;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        double wi = w[i];
+        for (int k = 0; k < nv; k++) wi -= hs[k] * V[k * n + i];
+        w[i] = wi;
+#pragma unroll
+        for (int k = 0; k < NVMAX; k++)
+            if (k < nv) acc[k] += V[k * n + i] * wi;
+    }
+    block_partials<NVMAX>(acc, nv, partials);
+    if (last_block(ticket)) {
+        fold(partials, nv, out);
+        if (threadIdx.x == 0) *ticket = 0u;
+    }
+}
+
+// w -= sum_k h2[k] V_k ; ||w||; last block: Hessenberg column j, Givens, test
+__global__ void __launch_bounds__(SIM_THREADS) orth_norm_kernel(const double *__restrict__ V, double *__restrict__ w,
+                                                                long n, int j, int m, double *partials,
+                                                                unsigned int *ticket, KrylovCtl *ctl) {
+    if (ctl->done) return;
+    const int nv = j + 1;
+    __shared__ double hs[NVMAX];
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) hs[k] = ctl->h2[k];
+    __syncthreads();
+    double acc[1] = {0.0};
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        double wi = w[i];
+        for (int k = 0; k < nv; k++) wi -= hs[k] * V[k * n + i];
+        w[i] = wi;
+        acc[0] += wi * wi;
+    }
+    block_partials<1>(acc, 1, partials);
+    if (last_block(ticket)) {
+        __shared__ double nrm;
+        fold(partials, 1, &nrm);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            *ticket = 0u;
+            const double hn = sqrt(nrm);
+            double col[NVMAX + 1];
+            for (int k = 0; k <= j; k++) col[k] = ctl->h[k] + ctl->h2[k];
+            for (int k = 0; k < j; k++) {
+                const double a = col[k], c2 = col[k + 1];
+                col[k] = ctl->cs[k] * a + ctl->sn[k] * c2;
+                col[k + 1] = -ctl->sn[k] * a + ctl->cs[k] * c2;
+            }
+            const double a = col[j], bb = hn;
+            const double rr = sqrt(a * a + bb * bb);
+            double c, s;
+            if (rr == 0.0) { c = 1.0; s = 0.0; }
+            else { c = a / rr; s = bb / rr; }
+            ctl->cs[j] = c; ctl->sn[j] = s;
+            col[j] = rr;
+            ctl->g[j + 1] = -s * ctl->g[j];
+            ctl->g[j] = c * ctl->g[j];
+            for (int k = 0; k <= j; k++) ctl->H[k * (SIM_MAX_M + 1) + j] = col[k];
+            ctl->rnorm2 = hn;             // normaliser of v_{j+1}
+            ctl->k = j + 1;
+            if (fabs(ctl->g[j + 1]) <= ctl->tol || j + 1 >= m) ctl->done = 1;
+        }
+    }
+}
+
+// v = w / scale (scale = ctl->rnorm2 inside a cycle, ctl->beta at a restart)
+__global__ void scale_kernel(const double *__restrict__ w, double *__restrict__ v, long n, const KrylovCtl *ctl,
+                             int use_beta) {
+    if (!use_beta && ctl->done) return;
+    const double sc = use_beta ? ctl->beta : ctl->rnorm2;
+    const double inv = sc > 0.0 ? 1.0 / sc : 0.0;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        v[i] = sc > 0.0 ? w[i] * inv : 0.0;
+}
+
+// y = H^{-1} g (k x k upper triangular), single thread
+__global__ void backsolve_kernel(KrylovCtl *ctl) {
+    if (threadIdx.x != 0) return;
+    const int k = ctl->k;
+    for (int i = k - 1; i >= 0; i--) {
+        double t = ctl->g[i];
+        for (int c = i + 1; c < k; c++) t -= ctl->H[i * (SIM_MAX_M + 1) + c] * ctl->y[c];
+        ctl->y[i] = t / ctl->H[i * (SIM_MAX_M + 1) + i];
+    }
+}
+
+// x += sum_k y_k Z_k
+template <typename Z>
+__global__ void xupdate_kernel(double *__restrict__ x, const Z *__restrict__ Zb, long n, const KrylovCtl *ctl) {
+    __shared__ double ys[NVMAX];
+    const int k = ctl->k;
+    for (int t = threadIdx.x; t < k; t += blockDim.x) ys[t] = ctl->y[t];
+    __syncthreads();
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        double s = x[i];
+        for (int t = 0; t < k; t++) s += ys[t] * (double)Zb[t * n + i];
+        x[i] = s;
+    }
+}
+
+// r = b - y ; beta = ||r|| into ctl->beta
+__global__ void __launch_bounds__(SIM_THREADS) resid_kernel(const double *__restrict__ b, const double *__restrict__ y,
+                                                            double *__restrict__ r, long n, double *partials,
+                                                            unsigned int *ticket, KrylovCtl *ctl) {
+    double acc[1] = {0.0};
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const double v = b[i] - y[i];
+        r[i] = v;
+        acc[0] += v * v;
+    }
+    block_partials<1>(acc, 1, partials);
+    if (last_block(ticket)) {
+        __shared__ double nrm;
+        fold(partials, 1, &nrm);
+        __syncthreads();
+        if (threadIdx.x == 0) { *ticket = 0u; ctl->beta = sqrt(nrm); }
+    }
+}
+
+__global__ void norm_kernel(const double *__restrict__ v, long n, double *partials, unsigned int *ticket, double *out) {
+    double acc[1] = {0.0};
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) acc[0] += v[i] * v[i];
+    block_partials<1>(acc, 1, partials);
+    if (last_block(ticket)) {
+        __shared__ double nrm;
+        fold(partials, 1, &nrm);
+        __syncthreads();
+        if (threadIdx.x == 0) { *ticket = 0u; out[0] = sqrt(nrm); }
+    }
+}
+
+// start of a restart cycle: clear flags and the Givens state, g = beta e1
+__global__ void cycle_init_kernel(KrylovCtl *ctl, double tol) {
+    const int t = threadIdx.x;
+    if (t == 0) { ctl->done = 0; ctl->k = 0; ctl->tol = tol; ctl->g[0] = ctl->beta; }
+    for (int k = t + 1; k <= SIM_MAX_M; k += blockDim.x) ctl->g[k] = 0.0;
+}
+
+}  // namespace
+
+// ===========================================================================
+sim_status k_spmv(sim_t *s, const double *x, double *y) {
+    if (s->b == 2) spmv_kernel<2, double><<<sim_blocks(s->N), SIM_THREADS, 0, s->stream>>>(s->gd, s->J, x, y, nullptr);
+    else spmv_kernel<3, double><<<sim_blocks(s->N), SIM_THREADS, 0, s->stream>>>(s->gd, s->J, x, y, nullptr);
+    SIM_LAUNCHED(s);
+    return SIM_OK;
+}
+
+static sim_status spmv_done(sim_t *s, const void *x, bool xf, double *y, const int *done) {
+    const int nb = sim_blocks(s->N);
+    if (s->b == 2) {
+        if (xf) spmv_kernel<2, float><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, s->J, (const float *)x, y, done);
+        else spmv_kernel<2, double><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, s->J, (const double *)x, y, done);
+    } else {
+        if (xf) spmv_kernel<3, float><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, s->J, (const float *)x, y, done);
+        else spmv_kernel<3, double><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, s->J, (const double *)x, y, done);
+    }
+    SIM_LAUNCHED(s);
+    return SIM_OK;
+}
+
+sim_status k_spmv_f(sim_t *s, const float *x, double *y) { return spmv_done(s, x, true, y, nullptr); }
+
+sim_status k_norm2(sim_t *s, const double *v, long n, double *out) {
+    norm_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(v, n, s->red, s->ticket, s->scal);
+    SIM_LAUNCHED(s);
+    SIM_CK(s, cudaMemcpyAsync(s->h_pinned, s->scal, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    SIM_CK(s, cudaStreamSynchronize(s->stream));
+    *out = s->h_pinned[0];
+    return SIM_OK;
+}
+
+sim_status k_fgmres(sim_t *s, const double *b, double *x, sim_linear_info *info) {
+    const long n = (long)s->N * s->b;
+    const int m = s->m;
+    const bool zf = sim_mixed(s);
+    const size_t zes = zf ? sizeof(float) : sizeof(double);
+    sim_linear_info li = {0, 0, 0, 0.0, 0.0};
+    if (!s->precond_ready) { if (cpr_setup(s) != SIM_OK) return s->err; }
+    double bn;
+    if (k_norm2(s, b, n, &bn) != SIM_OK) return s->err;
+    li.b_norm = bn;
+    SIM_CK(s, cudaMemsetAsync(x, 0, sizeof(double) * n, s->stream));
+    if (bn == 0.0) { li.converged = 1; if (info) *info = li; return SIM_OK; }
+    if (!(bn == bn)) { if (info) *info = li; return sim_fail(s, SIM_ENAN, "non-finite right-hand side"); }
+    const double tol = s->opt.lin_tol * bn;
+    KrylovCtl *ctl = s->ctl;
+    const int *done = &ctl->done;
+    SIM_CK(s, cudaMemcpyAsync(s->r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->stream));
+    SIM_CK(s, cudaMemcpyAsync(&ctl->beta, &bn, sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    for (int cyc = 0; cyc <= s->opt.gmres_max_restarts; cyc++) {
+        cycle_init_kernel<<<1, 64, 0, s->stream>>>(ctl, tol);
+        SIM_LAUNCHED(s);
+        scale_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(s->r, s->V, n, ctl, 1);
+        SIM_LAUNCHED(s);
+        for (int j = 0; j < m; j++) {
+            double *vj = s->V + (size_t)j * n;
+            void *zj = (char *)s->Z + (size_t)j * n * zes;
+            if (cpr_apply(s, vj, zj, done) != SIM_OK) return s->err;
+            if (spmv_done(s, zj, zf, s->w, done) != SIM_OK) return s->err;
+            dots_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(s->V, s->w, n, j + 1, s->red, s->ticket, ctl->h, done);
+            SIM_LAUNCHED(s);
+            orth_dots_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(s->V, s->w, n, j + 1, ctl->h, s->red, s->ticket,
+                                                                            ctl->h2, done);
+            SIM_LAUNCHED(s);
+            orth_norm_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(s->V, s->w, n, j, m, s->red, s->ticket, ctl);
+            SIM_LAUNCHED(s);
+            scale_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(s->w, s->V + (size_t)(j + 1) * n, n, ctl, 0);
+            SIM_LAUNCHED(s);
+        }
+        backsolve_kernel<<<1, 32, 0, s->stream>>>(ctl);
+        SIM_LAUNCHED(s);
+        if (zf) xupdate_kernel<float><<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(x, (const float *)s->Z, n, ctl);
+        else xupdate_kernel<double><<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(x, (const double *)s->Z, n, ctl);
+        SIM_LAUNCHED(s);
+        if (k_spmv(s, x, s->w) != SIM_OK) return s->err;
+        resid_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(b, s->w, s->r, n, s->red, s->ticket, ctl);
+        SIM_LAUNCHED(s);
+        SIM_CK(s, cudaMemcpyAsync(s->ctl_host, ctl, offsetof(KrylovCtl, h), cudaMemcpyDeviceToHost, s->stream));
+        SIM_CK(s, cudaStreamSynchronize(s->stream));
+        const int k = s->ctl_host->k;
+        const double beta = s->ctl_host->beta;
+        li.iterations += k;
+        li.r_norm = beta;
+        if (beta <= tol) { li.converged = 1; break; }
+        if (!(beta == beta)) break;
+        if (cyc < s->opt.gmres_max_restarts) li.restarts++;
+    }
+    s->linear_total += li.iterations;
+    if (info) *info = li;
+    if (!(li.r_norm == li.r_norm)) return sim_fail(s, SIM_ENAN, "non-finite linear residual");
+    return SIM_OK;
+}

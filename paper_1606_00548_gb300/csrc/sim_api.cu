@@ -1,0 +1,519 @@
+// C ABI of the GB300 reservoir Newton step (declarations and contracts in
+// include/sim.h).  Host orchestration only: every arithmetic step of the
+// method runs in the kernels of assemble.cu, krylov.cu and cpr.cu.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <set>
+
+#include "sim_internal.cuh"
+
+static thread_local std::string g_create_error;
+
+sim_status sim_fail(sim_t *s, sim_status st, const std::string &m) {
+    if (!s) { g_create_error = m; return st; }
+    if (s->err == SIM_OK) { s->err = st; s->msg = m; }
+    return s->err;
+}
+
+bool sim_cuda_ok(sim_t *s, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return true;
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    sim_fail(s, e == cudaErrorMemoryAllocation ? SIM_ENOMEM : SIM_ECUDA, m);
+    return false;
+}
+
+void *sim_alloc(sim_t *s, size_t bytes) {
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        sim_fail(s, SIM_ENOMEM, std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
+        return nullptr;
+    }
+    s->allocs.push_back(p);
+    s->bytes += bytes;
+    return p;
+}
+
+void sim_free(sim_t *s, void *p) {
+    for (size_t k = 0; k < s->allocs.size(); k++)
+        if (s->allocs[k] == p) { s->allocs.erase(s->allocs.begin() + k); break; }
+    cudaFree(p);
+}
+
+namespace {
+__global__ void widen_kernel(const float *__restrict__ a, double *__restrict__ b, long n) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) b[i] = (double)a[i];
+}
+__global__ void negate_kernel(const double *__restrict__ a, double *__restrict__ b, long n) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) b[i] = -a[i];
+}
+}  // namespace
+
+#define CHECK_HANDLE(s) do { if (!(s)) return SIM_EINVAL; if ((s)->err != SIM_OK) return (s)->err; } while (0)
+
+extern "C" {
+
+const char *sim_last_error(sim_t *s) { return s ? s->msg.c_str() : g_create_error.c_str(); }
+void sim_clear_error(sim_t *s) { if (s) { s->err = SIM_OK; s->msg.clear(); } }
+int32_t sim_block_size(sim_t *s) { return s ? s->b : 0; }
+
+void sim_destroy(sim_t *s) {
+    if (!s) return;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    cpr_free(s);
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    for (void *p : s->allocs) cudaFree(p);
+    if (s->h_pinned) cudaFreeHost(s->h_pinned);
+    if (s->ctl_host) cudaFreeHost(s->ctl_host);
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+sim_status sim_create(const sim_grid *g, const sim_rock *r, const sim_fluid *f, const sim_well *w, int32_t nwells,
+                      const sim_options *o, void *cuda_stream, sim_t **out) {
+    if (!out) return sim_fail(nullptr, SIM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!g || !r || !f || !o || (nwells > 0 && !w)) return sim_fail(nullptr, SIM_EINVAL, "NULL argument");
+    if (g->nx < 1 || g->ny < 1 || g->nz < 1 || (long)g->nx * g->ny * g->nz > 0x7fffffffL / 8)
+        return sim_fail(nullptr, SIM_EINVAL, "grid dimensions out of range");
+    if (!(g->dx > 0 && g->dy > 0 && g->dz > 0)) return sim_fail(nullptr, SIM_EINVAL, "cell sizes must be positive");
+    if (f->model != 2 && f->model != 3) return sim_fail(nullptr, SIM_EINVAL, "fluid model must be 2 or 3");
+    if (!r->kx || !r->ky || !r->kz || !r->poro) return sim_fail(nullptr, SIM_EINVAL, "rock arrays missing");
+    if (o->gmres_m < 1 || o->gmres_m > SIM_MAX_M) return sim_fail(nullptr, SIM_EINVAL, "gmres_m must be in 1..32");
+    if (o->precond < 0 || o->precond > 2 || o->stage2 < 0 || o->stage2 > 1 || o->precision < 0 || o->precision > 1)
+        return sim_fail(nullptr, SIM_EINVAL, "bad preconditioner options");
+    if (o->amg_coarse_max < 1 || o->amg_coarse_max > 1024 || o->amg_rounds < 1 || o->amg_max_levels < 1)
+        return sim_fail(nullptr, SIM_EINVAL, "bad AMG options");
+    if (f->model == 3) {
+        if (f->npvt < 2 || f->npvt > SIM_MAX_PVT) return sim_fail(nullptr, SIM_EINVAL, "npvt must be in 2..64");
+        if (!f->pvt_p || !f->pvt_bo || !f->pvt_rs || !f->pvt_muo || !f->pvt_bg || !f->pvt_mug)
+            return sim_fail(nullptr, SIM_EINVAL, "PVT table missing");
+        for (int k = 0; k + 1 < f->npvt; k++)
+            if (!(f->pvt_p[k + 1] > f->pvt_p[k])) return sim_fail(nullptr, SIM_EINVAL, "PVT pressures must increase");
+    }
+    const long N = (long)g->nx * g->ny * g->nz;
+    for (long i = 0; i < N; i++)
+        if (!(r->kx[i] > 0 && r->ky[i] > 0 && r->kz[i] > 0 && r->poro[i] > 0 && std::isfinite(r->kx[i]) &&
+              std::isfinite(r->poro[i])))
+            return sim_fail(nullptr, SIM_EINVAL, "permeability and porosity must be positive and finite");
+    // perforations: distinct cells
+    std::vector<int> pc, pt;
+    std::vector<double> pb, pz, prw, pskin;
+    std::set<int> seen;
+    for (int k = 0; k < nwells; k++) {
+        const sim_well &W = w[k];
+        if (W.i < 0 || W.i >= g->nx || W.j < 0 || W.j >= g->ny || W.k_top < 0 || W.k_bot >= g->nz || W.k_top > W.k_bot)
+            return sim_fail(nullptr, SIM_EINVAL, "well " + std::to_string(k) + " outside the grid");
+        if (W.type != SIM_WELL_PRODUCER && W.type != SIM_WELL_WATER_INJECTOR)
+            return sim_fail(nullptr, SIM_EINVAL, "unknown well type");
+        if (!(W.r_w > 0)) return sim_fail(nullptr, SIM_EINVAL, "well radius must be positive");
+        const double zh = g->top_depth + (W.k_top + 0.5) * g->dz;
+        for (int kk = W.k_top; kk <= W.k_bot; kk++) {
+            const int c = W.i + g->nx * (W.j + g->ny * kk);
+            if (!seen.insert(c).second) return sim_fail(nullptr, SIM_EINVAL, "two perforations share a cell");
+            pc.push_back(c); pt.push_back(W.type); pb.push_back(W.bhp); pz.push_back(zh);
+            prw.push_back(W.r_w); pskin.push_back(W.skin);
+        }
+    }
+
+    sim_t *s = new sim_t();
+    s->opt = *o;
+    s->N = (int)N;
+    s->b = f->model == 3 ? 3 : 2;
+    s->m = o->gmres_m;
+    s->gd.nx = g->nx; s->gd.ny = g->ny; s->gd.nz = g->nz; s->gd.N = (int)N;
+    s->gd.dx = g->dx; s->gd.dy = g->dy; s->gd.dz = g->dz; s->gd.top = g->top_depth;
+    FluidConst &c = s->fc;
+    memset(&c, 0, sizeof(c));
+    c.model = f->model; c.b = s->b; c.npvt = f->model == 3 ? f->npvt : 0;
+    c.rho_w_ref = f->rho_w_ref; c.rho_o_ref = f->rho_o_ref; c.c_w = f->c_w; c.c_o = f->c_o; c.mu_w = f->mu_w; c.mu_o = f->mu_o;
+    c.rho_ws = f->rho_ws; c.rho_os = f->rho_os; c.rho_gs = f->rho_gs; c.bw_c = f->bw_c; c.bw_pref = f->bw_pref;
+    c.bo_c_us = f->bo_c_us; c.muo_c_us = f->muo_c_us;
+    c.swc = f->swc; c.sor = f->sor; c.sgc = f->sgc; c.sorg = f->sorg; c.nw = f->nw; c.now = f->now; c.ng = f->ng; c.nog = f->nog;
+    c.c_rock = r->c_rock; c.p_ref = r->p_ref;
+    for (int k = 0; k < c.npvt; k++) {
+        c.pvt_p[k] = f->pvt_p[k]; c.pvt_bo[k] = f->pvt_bo[k]; c.pvt_rs[k] = f->pvt_rs[k];
+        c.pvt_muo[k] = f->pvt_muo[k]; c.pvt_bg[k] = f->pvt_bg[k]; c.pvt_mug[k] = f->pvt_mug[k];
+    }
+    for (int k = 0; k < 3; k++) c.cnv_rho[k] = f->cnv_rho[k] > 0 ? f->cnv_rho[k] : 1.0;
+
+    if (cuda_stream) s->stream = (cudaStream_t)cuda_stream;
+    else {
+        if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete s;
+            return sim_fail(nullptr, SIM_ECUDA, "cannot create a CUDA stream (no GPU?)");
+        }
+        s->own_stream = true;
+    }
+    const int b = s->b;
+    const long n = N * b;
+    const bool mixed = o->precision == SIM_PRECISION_MIXED;
+    const size_t tsz = mixed ? sizeof(float) : sizeof(double);
+    const int nq = b == 2 ? 4 : 7;
+    bool ok = true;
+    auto A = [&](size_t bytes) -> void * { void *p = ok ? sim_alloc(s, bytes) : nullptr; if (!p) ok = false; return p; };
+    s->T = (double *)A(sizeof(double) * 3 * N);
+    s->poro = (double *)A(sizeof(double) * N);
+    s->nperf = (int)pc.size();
+    s->perf_cell = (int *)A(sizeof(int) * (pc.size() + 1));
+    s->perf_type = (int *)A(sizeof(int) * (pc.size() + 1));
+    s->perf_wi = (double *)A(sizeof(double) * (pc.size() + 1));
+    s->perf_zh = (double *)A(sizeof(double) * (pc.size() + 1));
+    s->perf_bhp = (double *)A(sizeof(double) * (pc.size() + 1));
+    s->x = (double *)A(sizeof(double) * n);
+    s->x_old = (double *)A(sizeof(double) * n);
+    s->ph = (int8_t *)A(N);
+    s->ph_old = (int8_t *)A(N);
+    s->mold = (double *)A(sizeof(double) * n);
+    s->R = (double *)A(sizeof(double) * n);
+    s->J = (double *)A(sizeof(double) * 7 * b * b * N);
+    s->props = (double *)A(sizeof(double) * nq * (b + 1) * N);
+    s->qtot = (double *)A(sizeof(double) * 4);
+    s->red = (double *)A(sizeof(double) * (SIM_MAX_M + 2) * SIM_RED_BLOCKS);
+    s->scal = (double *)A(sizeof(double) * 64);
+    s->ticket = (unsigned int *)A(sizeof(unsigned int) * 4);
+    s->V = (double *)A(sizeof(double) * (s->m + 1) * n);
+    s->Z = A(tsz * s->m * n);
+    s->w = (double *)A(sizeof(double) * n);
+    s->r = (double *)A(sizeof(double) * n);
+    s->xl = (double *)A(sizeof(double) * n);
+    s->bl = (double *)A(sizeof(double) * n);
+    s->dx = (double *)A(sizeof(double) * n);
+    s->ctl = (KrylovCtl *)A(sizeof(KrylovCtl));
+    s->qiw = (double *)A(sizeof(double) * n);
+    s->ap = (double *)A(sizeof(double) * 7 * N);
+    s->qiwT = mixed ? A(sizeof(float) * n) : (void *)s->qiw;
+    s->apT = mixed ? A(sizeof(float) * 7 * N) : (void *)s->ap;
+    s->ahat = A(tsz * 7 * b * b * N);
+    s->dinv_d = (double *)A(sizeof(double) * b * b * N);
+    s->dinv = mixed ? A(sizeof(float) * b * b * N) : (void *)s->dinv_d;
+    s->r2 = A(tsz * n);
+    s->zr = A(tsz * n);
+    s->partner = (int *)A(sizeof(int) * N);
+    s->pick = (int *)A(sizeof(int) * N);
+    s->aggA = (int *)A(sizeof(int) * N);
+    s->aggB = (int *)A(sizeof(int) * N);
+    s->memA = (int *)A(sizeof(int) * 2 * N);
+    s->memB = (int *)A(sizeof(int) * 2 * N);
+    s->scan = (int *)A(sizeof(int) * (N / 4096 + 2));
+    s->iscal = (int *)A(sizeof(int) * 8);
+    if (!ok) {
+        std::string m = s->msg;
+        sim_destroy(s);
+        return sim_fail(nullptr, SIM_ENOMEM, m);
+    }
+    if (cudaMallocHost(&s->h_pinned, sizeof(double) * 64) != cudaSuccess ||
+        cudaMallocHost(&s->ctl_host, sizeof(KrylovCtl)) != cudaSuccess) {
+        sim_destroy(s);
+        return sim_fail(nullptr, SIM_ENOMEM, "pinned host allocation failed");
+    }
+    // a stream-ordered memory pool that keeps freed AMG buffers for reuse
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = ~0ULL;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaMemsetAsync(s->ticket, 0, sizeof(unsigned int) * 4, s->stream);
+    cudaMemsetAsync(s->x, 0, sizeof(double) * n, s->stream);
+    cudaMemsetAsync(s->ph, 1, N, s->stream);
+    if (k_geometry(s, r->kx, r->ky, r->kz, r->poro, pc.data(), pt.data(), pb.data(), pz.data(), prw.data(),
+                   pskin.data()) != SIM_OK) {
+        std::string m = s->msg;
+        sim_status st = s->err;
+        sim_destroy(s);
+        return sim_fail(nullptr, st, m);
+    }
+    *out = s;
+    return SIM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// state
+// ---------------------------------------------------------------------------
+static sim_status begin_step(sim_t *s) {
+    const long n = (long)s->N * s->b;
+    SIM_CK(s, cudaMemcpyAsync(s->x_old, s->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->stream));
+    SIM_CK(s, cudaMemcpyAsync(s->ph_old, s->ph, s->N, cudaMemcpyDeviceToDevice, s->stream));
+    return k_accumulation(s, s->x, s->ph, s->mold);
+}
+
+sim_status sim_set_state(sim_t *s, const double *p, const double *sw, const double *x3, const int8_t *phase) {
+    CHECK_HANDLE(s);
+    if (!p || !sw || (s->b == 3 && (!x3 || !phase))) return sim_fail(s, SIM_EINVAL, "NULL state array");
+    const int N = s->N;
+    SIM_CK(s, cudaMemcpyAsync(s->x, p, sizeof(double) * N, cudaMemcpyHostToDevice, s->stream));
+    SIM_CK(s, cudaMemcpyAsync(s->x + N, sw, sizeof(double) * N, cudaMemcpyHostToDevice, s->stream));
+    if (s->b == 3) {
+        SIM_CK(s, cudaMemcpyAsync(s->x + 2L * N, x3, sizeof(double) * N, cudaMemcpyHostToDevice, s->stream));
+        SIM_CK(s, cudaMemcpyAsync(s->ph, phase, N, cudaMemcpyHostToDevice, s->stream));
+    } else {
+        SIM_CK(s, cudaMemsetAsync(s->ph, 1, N, s->stream));
+    }
+    s->cum_well[0] = s->cum_well[1] = s->cum_well[2] = 0.0;
+    if (begin_step(s) != SIM_OK) return s->err;
+    SIM_CK(s, cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}
+
+sim_status sim_get_state(sim_t *s, double *p, double *sw, double *x3, int8_t *phase) {
+    CHECK_HANDLE(s);
+    const int N = s->N;
+    if (p) SIM_CK(s, cudaMemcpyAsync(p, s->x, sizeof(double) * N, cudaMemcpyDeviceToHost, s->stream));
+    if (sw) SIM_CK(s, cudaMemcpyAsync(sw, s->x + N, sizeof(double) * N, cudaMemcpyDeviceToHost, s->stream));
+    if (x3) {
+        if (s->b == 3) SIM_CK(s, cudaMemcpyAsync(x3, s->x + 2L * N, sizeof(double) * N, cudaMemcpyDeviceToHost, s->stream));
+        else memset(x3, 0, sizeof(double) * N);
+    }
+    if (phase) SIM_CK(s, cudaMemcpyAsync(phase, s->ph, N, cudaMemcpyDeviceToHost, s->stream));
+    SIM_CK(s, cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}
+
+sim_status sim_set_iterate(sim_t *s, const double *x, const int8_t *phase) {
+    CHECK_HANDLE(s);
+    if (!x || !phase) return sim_fail(s, SIM_EINVAL, "NULL iterate");
+    SIM_CK(s, cudaMemcpyAsync(s->x, x, sizeof(double) * s->N * s->b, cudaMemcpyHostToDevice, s->stream));
+    SIM_CK(s, cudaMemcpyAsync(s->ph, phase, s->N, cudaMemcpyHostToDevice, s->stream));
+    SIM_CK(s, cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}
+
+sim_status sim_get_iterate(sim_t *s, double *x, int8_t *phase) {
+    CHECK_HANDLE(s);
+    if (x) SIM_CK(s, cudaMemcpyAsync(x, s->x, sizeof(double) * s->N * s->b, cudaMemcpyDeviceToHost, s->stream));
+    if (phase) SIM_CK(s, cudaMemcpyAsync(phase, s->ph, s->N, cudaMemcpyDeviceToHost, s->stream));
+    SIM_CK(s, cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Newton (Algorithm 1) and time stepping
+// ---------------------------------------------------------------------------
+sim_status sim_assemble(sim_t *s, double dt) {
+    CHECK_HANDLE(s);
+    if (!(dt > 0)) return sim_fail(s, SIM_EINVAL, "dt must be positive");
+    if (k_assemble(s, dt) != SIM_OK) return s->err;
+    SIM_CK(s, cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}
+
+sim_status sim_cnv(sim_t *s, double dt, double *cnv) {
+    CHECK_HANDLE(s);
+    return k_cnv(s, dt, cnv);
+}
+
+// solve J dx = -R and update; *lin receives the linear info
+static sim_status solve_and_update(sim_t *s, sim_linear_info *lin, bool *finite_ok) {
+    const long n = (long)s->N * s->b;
+    negate_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(s->R, s->bl, n);
+    SIM_LAUNCHED(s);
+    if (k_fgmres(s, s->bl, s->dx, lin) != SIM_OK) {
+        if (s->err == SIM_ENAN) { sim_clear_error(s); *finite_ok = false; return SIM_OK; }
+        return s->err;
+    }
+    int ok = 1;
+    if (k_finite(s, s->dx, n, &ok) != SIM_OK) return s->err;
+    *finite_ok = ok != 0;
+    if (!ok) return SIM_OK;
+    if (k_newton_update(s, s->dx) != SIM_OK) return s->err;
+    s->newton_total++;
+    return SIM_OK;
+}
+
+sim_status sim_newton_step(sim_t *s, double dt, sim_newton_info *info) {
+    CHECK_HANDLE(s);
+    if (!(dt > 0)) return sim_fail(s, SIM_EINVAL, "dt must be positive");
+    sim_newton_info ni;
+    memset(&ni, 0, sizeof(ni));
+    if (k_assemble(s, dt) != SIM_OK) return s->err;
+    double cnv;
+    if (k_cnv(s, dt, &cnv) != SIM_OK) return s->err;
+    ni.cnv = cnv;
+    if (cnv <= s->opt.newton_tol) { ni.converged = 1; if (info) *info = ni; return SIM_OK; }
+    sim_linear_info li;
+    bool fin = true;
+    if (solve_and_update(s, &li, &fin) != SIM_OK) return s->err;
+    ni.newton_iterations = 1;
+    ni.linear_iterations = li.iterations;
+    ni.linear_failures = !li.converged;
+    if (info) *info = ni;
+    return fin ? SIM_OK : SIM_ENAN;
+}
+
+// Newton loop; returns 0 converged, 1 not converged, 2 non-finite
+static int newton_solve(sim_t *s, double dt, sim_newton_info *ni) {
+    memset(ni, 0, sizeof(*ni));
+    for (int l = 0;; l++) {
+        if (k_assemble(s, dt) != SIM_OK) return -1;
+        double cnv;
+        if (k_cnv(s, dt, &cnv) != SIM_OK) return -1;
+        ni->cnv = cnv;
+        if (!(cnv == cnv)) return 2;
+        if (cnv <= s->opt.newton_tol) { ni->converged = 1; return 0; }
+        if (l >= s->opt.newton_max) return 1;
+        sim_linear_info li;
+        bool fin = true;
+        if (solve_and_update(s, &li, &fin) != SIM_OK) return -1;
+        ni->newton_iterations++;
+        ni->linear_iterations += li.iterations;
+        ni->linear_failures += !li.converged;
+        if (!fin) return 2;
+    }
+}
+
+sim_status sim_newton_solve(sim_t *s, double dt, sim_newton_info *info) {
+    CHECK_HANDLE(s);
+    if (!(dt > 0)) return sim_fail(s, SIM_EINVAL, "dt must be positive");
+    sim_newton_info ni;
+    const int rc = newton_solve(s, dt, &ni);
+    if (info) *info = ni;
+    if (rc < 0) return s->err;
+    return rc == 0 ? SIM_OK : (rc == 2 ? SIM_ENAN : SIM_ENOCONV_NEWTON);
+}
+
+sim_status sim_step(sim_t *s, double dt, sim_step_info *info) {
+    CHECK_HANDLE(s);
+    if (!(dt > 0)) return sim_fail(s, SIM_EINVAL, "dt must be positive");
+    sim_step_info si;
+    memset(&si, 0, sizeof(si));
+    double remaining = dt, h = dt;
+    sim_status st = SIM_OK;
+    while (remaining > 1e-12 * dt) {
+        if (h > remaining) h = remaining;
+        sim_newton_info ni;
+        const int rc = newton_solve(s, h, &ni);
+        if (rc < 0) return s->err;
+        si.newton_iterations += ni.newton_iterations;
+        si.linear_iterations += ni.linear_iterations;
+        if (rc == 0) {
+            SIM_CK(s, cudaMemcpyAsync(s->h_pinned, s->qtot, sizeof(double) * 3, cudaMemcpyDeviceToHost, s->stream));
+            SIM_CK(s, cudaStreamSynchronize(s->stream));
+            for (int c = 0; c < 3; c++) s->cum_well[c] += h * s->h_pinned[c];
+            remaining -= h;
+            si.substeps++;
+            if (begin_step(s) != SIM_OK) return s->err;
+        } else {
+            SIM_CK(s, cudaMemcpyAsync(s->x, s->x_old, sizeof(double) * s->N * s->b, cudaMemcpyDeviceToDevice, s->stream));
+            SIM_CK(s, cudaMemcpyAsync(s->ph, s->ph_old, s->N, cudaMemcpyDeviceToDevice, s->stream));
+            si.cuts++;
+            if (si.cuts > s->opt.max_cuts) { st = SIM_ENOCONV_NEWTON; break; }
+            h *= 0.5;
+        }
+    }
+    SIM_CK(s, cudaStreamSynchronize(s->stream));
+    si.ok = st == SIM_OK;
+    if (info) *info = si;
+    return st;
+}
+
+sim_status sim_linear_solve(sim_t *s, const double *b_dev, double *x_dev, sim_linear_info *info) {
+    CHECK_HANDLE(s);
+    if (!b_dev || !x_dev || b_dev == x_dev) return sim_fail(s, SIM_EINVAL, "bad vector pointers");
+    sim_linear_info li;
+    if (k_fgmres(s, b_dev, x_dev, &li) != SIM_OK) return s->err;
+    if (info) *info = li;
+    return li.converged ? SIM_OK : SIM_ENOCONV_LINEAR;
+}
+
+// ---------------------------------------------------------------------------
+// inspection
+// ---------------------------------------------------------------------------
+sim_status sim_get_residual(sim_t *s, double *R) {
+    CHECK_HANDLE(s);
+    SIM_CK(s, cudaMemcpyAsync(R, s->R, sizeof(double) * s->N * s->b, cudaMemcpyDeviceToHost, s->stream));
+    SIM_CK(s, cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}
+sim_status sim_get_jacobian(sim_t *s, double *J) {
+    CHECK_HANDLE(s);
+    SIM_CK(s, cudaMemcpyAsync(J, s->J, sizeof(double) * 7 * s->b * s->b * (size_t)s->N, cudaMemcpyDeviceToHost, s->stream));
+    SIM_CK(s, cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}
+sim_status sim_set_jacobian(sim_t *s, const double *J) {
+    CHECK_HANDLE(s);
+    SIM_CK(s, cudaMemcpyAsync(s->J, J, sizeof(double) * 7 * s->b * s->b * (size_t)s->N, cudaMemcpyHostToDevice, s->stream));
+    SIM_CK(s, cudaStreamSynchronize(s->stream));
+    s->precond_ready = false;
+    return SIM_OK;
+}
+sim_status sim_spmv(sim_t *s, const double *x_dev, double *y_dev) {
+    CHECK_HANDLE(s);
+    if (k_spmv(s, x_dev, y_dev) != SIM_OK) return s->err;
+    SIM_CK(s, cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}
+sim_status sim_precond_setup(sim_t *s) {
+    CHECK_HANDLE(s);
+    if (cpr_setup(s) != SIM_OK) return s->err;
+    SIM_CK(s, cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}
+sim_status sim_precond_apply(sim_t *s, const double *r_dev, double *z_dev) {
+    CHECK_HANDLE(s);
+    const long n = (long)s->N * s->b;
+    void *z = sim_mixed(s) ? s->Z : (void *)z_dev;
+    if (cpr_apply(s, r_dev, z, nullptr) != SIM_OK) return s->err;
+    if (sim_mixed(s)) {   // widen the FP32 result into the caller's FP64 buffer
+        widen_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>((const float *)s->Z, z_dev, n);
+        SIM_LAUNCHED(s);
+    }
+    SIM_CK(s, cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}
+sim_status sim_get_qi(sim_t *s, double *w, double *ap) {
+    CHECK_HANDLE(s);
+    if (!s->precond_ready) return sim_fail(s, SIM_EINVAL, "preconditioner not set up");
+    if (w) SIM_CK(s, cudaMemcpyAsync(w, s->qiw, sizeof(double) * s->N * s->b, cudaMemcpyDeviceToHost, s->stream));
+    if (ap) SIM_CK(s, cudaMemcpyAsync(ap, s->ap, sizeof(double) * 7 * (size_t)s->N, cudaMemcpyDeviceToHost, s->stream));
+    SIM_CK(s, cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}
+int32_t sim_amg_levels(sim_t *s) { return s ? (int32_t)s->lev.size() : 0; }
+sim_status sim_amg_level_info(sim_t *s, int32_t level, int32_t *n, int32_t *width) {
+    CHECK_HANDLE(s);
+    if (level < 0 || level >= (int)s->lev.size()) return sim_fail(s, SIM_EINVAL, "level out of range");
+    if (n) *n = s->lev[level].n;
+    if (width) *width = s->lev[level].width;
+    return SIM_OK;
+}
+sim_status sim_amg_level_agg(sim_t *s, int32_t level, int32_t *agg) {
+    CHECK_HANDLE(s);
+    if (level < 0 || level + 1 >= (int)s->lev.size()) return sim_fail(s, SIM_EINVAL, "level has no aggregates");
+    SIM_CK(s, cudaMemcpyAsync(agg, s->lev[level].agg, sizeof(int) * s->lev[level].n, cudaMemcpyDeviceToHost, s->stream));
+    SIM_CK(s, cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}
+sim_status sim_amg_level_ell(sim_t *s, int32_t level, int32_t *col, double *val) {
+    CHECK_HANDLE(s);
+    return cpr_copy_level_ell(s, level, col, val);
+}
+sim_status sim_component_mass(sim_t *s, double *m3) {
+    CHECK_HANDLE(s);
+    return k_component_mass(s, m3);
+}
+sim_status sim_cumulative_well_mass(sim_t *s, double *m3) {
+    CHECK_HANDLE(s);
+    for (int c = 0; c < 3; c++) m3[c] = s->cum_well[c];
+    return SIM_OK;
+}
+sim_status sim_well_rates(sim_t *s, double *q3) {
+    CHECK_HANDLE(s);
+    SIM_CK(s, cudaMemcpyAsync(s->h_pinned, s->qtot, sizeof(double) * 3, cudaMemcpyDeviceToHost, s->stream));
+    SIM_CK(s, cudaStreamSynchronize(s->stream));
+    for (int c = 0; c < 3; c++) q3[c] = s->h_pinned[c];
+    return SIM_OK;
+}
+sim_status sim_get_stats(sim_t *s, sim_stats *st) {
+    if (!s || !st) return SIM_EINVAL;
+    st->kernel_launches = s->launches;
+    st->newton_iterations = s->newton_total;
+    st->linear_iterations = s->linear_total;
+    st->device_bytes = (int64_t)s->bytes;
+    return SIM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,155 @@
+// Internal declarations of the GB300 reservoir library (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/sim.h"
+
+#define SIM_GRAV 9.80665
+#define SIM_DARCY (86400.0 * 9.869233e-16 * 1e5 / 1e-3)
+#define SIM_MAX_PVT 64
+#define SIM_MAX_M 32
+#define SIM_MAX_ELL 128      // widest coarse AMG row the setup kernels accept
+#define SIM_RED_BLOCKS 304   // 2 x 152 SMs: grid of the reduction kernels
+#define SIM_THREADS 256
+
+// fluid and rock constants, passed by value as a kernel parameter (about
+// 3.3 KB, under the 4 KB parameter limit), so handles never share state
+struct FluidConst {
+    int model, b, npvt;
+    double rho_w_ref, rho_o_ref, c_w, c_o, mu_w, mu_o;
+    double rho_ws, rho_os, rho_gs, bw_c, bw_pref, bo_c_us, muo_c_us;
+    double swc, sor, sgc, sorg, nw, now, ng, nog;
+    double c_rock, p_ref;
+    double pvt_p[SIM_MAX_PVT], pvt_bo[SIM_MAX_PVT], pvt_rs[SIM_MAX_PVT], pvt_muo[SIM_MAX_PVT],
+        pvt_bg[SIM_MAX_PVT], pvt_mug[SIM_MAX_PVT];
+    double cnv_rho[3];
+};
+
+struct GridDesc {
+    int nx, ny, nz, N;
+    double dx, dy, dz, top;
+};
+
+// device control block of one FGMRES solve (Givens, Hessenberg, flags)
+struct KrylovCtl {
+    int done;           // 1 once the Arnoldi residual estimate met the tolerance
+    int k;              // inner iterations completed in the current cycle
+    int breakdown;
+    int pad;
+    double tol, beta, rnorm2;
+    double h[SIM_MAX_M + 1], h2[SIM_MAX_M + 1];
+    double g[SIM_MAX_M + 1], cs[SIM_MAX_M + 1], sn[SIM_MAX_M + 1], y[SIM_MAX_M + 1];
+    double H[(SIM_MAX_M + 1) * (SIM_MAX_M + 1)];
+    unsigned int counter;   // last-block reduction ticket
+    unsigned int pad2;
+};
+
+struct AmgLevel {
+    int n = 0, width = 0;        // level 0: width 7, structured
+    int *col = nullptr;          // ELL columns [width][n] (levels >= 1)
+    double *val = nullptr;       // ELL values, FP64 (setup precision)
+    void *valT = nullptr;        // ELL values in apply precision (float copy for mixed)
+    void *dinvT = nullptr;       // 1 / l1 row sums, apply precision
+    int *agg = nullptr;          // fine -> next level
+    int *mem4 = nullptr;         // next-level aggregate -> 4 members [4][n_next]
+    void *f = nullptr, *e = nullptr, *e2 = nullptr;   // V-cycle vectors (apply precision)
+    void *coarse_inv = nullptr;  // coarsest: dense inverse, row-major n*n (apply precision)
+};
+
+struct sim {
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    sim_status err = SIM_OK;
+    std::string msg;
+    FluidConst fc;
+    GridDesc gd;
+    sim_options opt;
+    int N = 0, b = 0;
+    int64_t launches = 0, newton_total = 0, linear_total = 0;
+    size_t bytes = 0;
+    std::vector<void *> allocs;
+
+    // geometry
+    double *T = nullptr;         // [3][N] transmissibility to the + neighbour
+    double *poro = nullptr;      // [N] porosity at p_ref
+    int nperf = 0;
+    int *perf_cell = nullptr, *perf_type = nullptr;
+    double *perf_wi = nullptr, *perf_zh = nullptr, *perf_bhp = nullptr;
+
+    // state
+    double *x = nullptr, *x_old = nullptr;   // [b][N]
+    int8_t *ph = nullptr, *ph_old = nullptr;
+    double *mold = nullptr;                  // [b][N]
+    double *R = nullptr, *J = nullptr;       // [b][N], [7][b][b][N]
+    double *props = nullptr;                 // [nq*4][N]
+    double *qtot = nullptr;                  // [3] well rates of the last assembly
+    double cum_well[3] = {0, 0, 0};
+
+    // reductions
+    double *red = nullptr;       // partial sums [SIM_MAX_M+2][SIM_RED_BLOCKS]
+    double *scal = nullptr;      // small device scalars
+    unsigned int *ticket = nullptr;
+    double *h_pinned = nullptr;  // pinned host mirror for small reads
+
+    // Krylov
+    int m = 0;
+    double *V = nullptr;         // [(m+1)][n]
+    void *Z = nullptr;           // [m][n], FP64 or FP32
+    double *w = nullptr, *r = nullptr, *xl = nullptr, *bl = nullptr, *dx = nullptr;
+    KrylovCtl *ctl = nullptr;
+    KrylovCtl *ctl_host = nullptr;
+
+    // CPR
+    bool precond_ready = false;
+    double *qiw = nullptr;       // [b][N]
+    void *qiwT = nullptr;        // [b][N] apply precision (aliases qiw in FP64 mode)
+    double *ap = nullptr;        // [7][N] pressure block, FP64
+    void *apT = nullptr;         // [7][N] apply precision (aliases ap in FP64 mode)
+    void *ahat = nullptr;        // [7][b][b][N] decoupled matrix, apply precision
+    void *dinv = nullptr;        // [b][b][N] ILU / block-Jacobi inverse diagonal blocks
+    double *dinv_d = nullptr;    // FP64 scratch of the same
+    void *r2 = nullptr;          // [b][N] stage-2 work vector (apply precision)
+    void *zr = nullptr;          // [b][N]
+    std::vector<AmgLevel> lev;
+    // AMG setup scratch
+    int *partner = nullptr, *pick = nullptr, *aggA = nullptr, *memA = nullptr, *aggB = nullptr, *memB = nullptr;
+    int *scan = nullptr, *iscal = nullptr;
+    int *tcol = nullptr; double *tval = nullptr;   // intermediate (pass-1) matrix
+    int tcap = 0;
+};
+
+// ---- error helpers --------------------------------------------------------
+sim_status sim_fail(sim_t *s, sim_status st, const std::string &m);
+bool sim_cuda_ok(sim_t *s, cudaError_t e, const char *what);
+#define SIM_CK(s, call) do { if (!sim_cuda_ok((s), (call), #call)) return (s)->err; } while (0)
+#define SIM_LAUNCHED(s) do { (s)->launches++; if (!sim_cuda_ok((s), cudaGetLastError(), "kernel launch")) return (s)->err; } while (0)
+void *sim_alloc(sim_t *s, size_t bytes);
+void sim_free(sim_t *s, void *p);
+inline int sim_blocks(long n, int t = SIM_THREADS) { long b = (n + t - 1) / t; return (int)(b < 1 ? 1 : b); }
+bool sim_mixed(const sim_t *s);
+
+// ---- assemble.cu ----------------------------------------------------------
+sim_status k_geometry(sim_t *s, const double *kx, const double *ky, const double *kz, const double *poro,
+                      const int *wcell_host, const int *wtype_host, const double *wbhp_host,
+                      const double *wzh_host, const double *wrw_host, const double *wskin_host);
+sim_status k_accumulation(sim_t *s, const double *x, const int8_t *ph, double *acc);   // acc [b][N]
+sim_status k_assemble(sim_t *s, double dt);
+sim_status k_cnv(sim_t *s, double dt, double *cnv_host);
+sim_status k_component_mass(sim_t *s, double *m3_host);
+sim_status k_newton_update(sim_t *s, const double *dx);
+sim_status k_finite(sim_t *s, const double *v, long n, int *ok_host);
+
+// ---- krylov.cu ------------------------------------------------------------
+sim_status k_spmv(sim_t *s, const double *x, double *y);                 // y = J x
+sim_status k_spmv_f(sim_t *s, const float *x, double *y);
+sim_status k_fgmres(sim_t *s, const double *b, double *x, sim_linear_info *info);
+sim_status k_norm2(sim_t *s, const double *v, long n, double *out_host);
+
+// ---- cpr.cu ---------------------------------------------------------------
+sim_status cpr_setup(sim_t *s);
+sim_status cpr_apply(sim_t *s, const double *r, void *z, const int *done);   // z FP64 or FP32 (Z type)
+void cpr_free(sim_t *s);
+sim_status cpr_copy_level_ell(sim_t *s, int level, int *col, double *val);

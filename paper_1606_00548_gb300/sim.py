@@ -1,0 +1,353 @@
+"""ctypes binding of libsim.so (include/sim.h): argument marshalling only.
+
+Every step of the method runs in the CUDA library; this module only converts
+Python / numpy / torch arguments into the C structs and pointers of the ABI.
+There is no fallback: if the library or a GPU is missing, calls raise.
+
+Functions keep the ABI's names (sim_create, sim_step, sim_newton_step,
+sim_linear_solve, ...).  `Simulator` wraps one handle for a synthetic case
+from `synth` and exposes the same operations with numpy / torch arguments.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsim.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "sim.h")
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+_i8p = C.POINTER(C.c_int8)
+_vp = C.c_void_p
+
+SIM_OK, SIM_EINVAL, SIM_ENOMEM, SIM_ECUDA, SIM_ENAN, SIM_ENOCONV_LINEAR, SIM_ENOCONV_NEWTON, SIM_ETIMEOUT, SIM_ELIMIT = range(9)
+STATUS_NAMES = ["SIM_OK", "SIM_EINVAL", "SIM_ENOMEM", "SIM_ECUDA", "SIM_ENAN", "SIM_ENOCONV_LINEAR",
+                "SIM_ENOCONV_NEWTON", "SIM_ETIMEOUT", "SIM_ELIMIT"]
+
+
+class SimError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+class sim_grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double), ("top_depth", C.c_double)]
+
+
+class sim_rock(C.Structure):
+    _fields_ = [("kx", _dp), ("ky", _dp), ("kz", _dp), ("poro", _dp), ("c_rock", C.c_double), ("p_ref", C.c_double)]
+
+
+class sim_fluid(C.Structure):
+    _fields_ = [("model", C.c_int32),
+                ("rho_w_ref", C.c_double), ("rho_o_ref", C.c_double), ("c_w", C.c_double), ("c_o", C.c_double),
+                ("mu_w", C.c_double), ("mu_o", C.c_double),
+                ("rho_ws", C.c_double), ("rho_os", C.c_double), ("rho_gs", C.c_double), ("bw_c", C.c_double),
+                ("bw_pref", C.c_double), ("bo_c_us", C.c_double), ("muo_c_us", C.c_double),
+                ("npvt", C.c_int32),
+                ("pvt_p", _dp), ("pvt_bo", _dp), ("pvt_rs", _dp), ("pvt_muo", _dp), ("pvt_bg", _dp), ("pvt_mug", _dp),
+                ("swc", C.c_double), ("sor", C.c_double), ("sgc", C.c_double), ("sorg", C.c_double),
+                ("nw", C.c_double), ("now", C.c_double), ("ng", C.c_double), ("nog", C.c_double),
+                ("cnv_rho", C.c_double * 3)]
+
+
+class sim_well(C.Structure):
+    _fields_ = [("i", C.c_int32), ("j", C.c_int32), ("k_top", C.c_int32), ("k_bot", C.c_int32), ("type", C.c_int32),
+                ("bhp", C.c_double), ("r_w", C.c_double), ("skin", C.c_double)]
+
+
+class sim_options(C.Structure):
+    _fields_ = [("newton_tol", C.c_double), ("newton_max", C.c_int32), ("lin_tol", C.c_double),
+                ("gmres_m", C.c_int32), ("gmres_max_restarts", C.c_int32), ("precond", C.c_int32),
+                ("stage2", C.c_int32), ("amg_theta", C.c_double), ("amg_rounds", C.c_int32),
+                ("amg_coarse_max", C.c_int32), ("amg_max_levels", C.c_int32), ("chop_ds", C.c_double),
+                ("chop_dp", C.c_double), ("max_cuts", C.c_int32), ("precision", C.c_int32)]
+
+
+class sim_linear_info(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("restarts", C.c_int32), ("converged", C.c_int32),
+                ("b_norm", C.c_double), ("r_norm", C.c_double)]
+
+
+class sim_newton_info(C.Structure):
+    _fields_ = [("newton_iterations", C.c_int32), ("linear_iterations", C.c_int32), ("converged", C.c_int32),
+                ("linear_failures", C.c_int32), ("cnv", C.c_double)]
+
+
+class sim_step_info(C.Structure):
+    _fields_ = [("cuts", C.c_int32), ("newton_iterations", C.c_int32), ("linear_iterations", C.c_int32),
+                ("substeps", C.c_int32), ("ok", C.c_int32)]
+
+
+class sim_stats(C.Structure):
+    _fields_ = [("kernel_launches", C.c_int64), ("newton_iterations", C.c_int64),
+                ("linear_iterations", C.c_int64), ("device_bytes", C.c_int64)]
+
+
+_SIGS = {
+    "sim_create": ([C.POINTER(sim_grid), C.POINTER(sim_rock), C.POINTER(sim_fluid), C.POINTER(sim_well), C.c_int32,
+                    C.POINTER(sim_options), _vp, C.POINTER(_vp)], C.c_int),
+    "sim_destroy": ([_vp], None),
+    "sim_set_state": ([_vp, _dp, _dp, _dp, _i8p], C.c_int),
+    "sim_get_state": ([_vp, _dp, _dp, _dp, _i8p], C.c_int),
+    "sim_step": ([_vp, C.c_double, C.POINTER(sim_step_info)], C.c_int),
+    "sim_newton_solve": ([_vp, C.c_double, C.POINTER(sim_newton_info)], C.c_int),
+    "sim_newton_step": ([_vp, C.c_double, C.POINTER(sim_newton_info)], C.c_int),
+    "sim_linear_solve": ([_vp, _vp, _vp, C.POINTER(sim_linear_info)], C.c_int),
+    "sim_set_iterate": ([_vp, _dp, _i8p], C.c_int),
+    "sim_get_iterate": ([_vp, _dp, _i8p], C.c_int),
+    "sim_assemble": ([_vp, C.c_double], C.c_int),
+    "sim_get_residual": ([_vp, _dp], C.c_int),
+    "sim_get_jacobian": ([_vp, _dp], C.c_int),
+    "sim_set_jacobian": ([_vp, _dp], C.c_int),
+    "sim_cnv": ([_vp, C.c_double, _dp], C.c_int),
+    "sim_spmv": ([_vp, _vp, _vp], C.c_int),
+    "sim_precond_setup": ([_vp], C.c_int),
+    "sim_precond_apply": ([_vp, _vp, _vp], C.c_int),
+    "sim_get_qi": ([_vp, _dp, _dp], C.c_int),
+    "sim_amg_levels": ([_vp], C.c_int32),
+    "sim_amg_level_info": ([_vp, C.c_int32, _ip, _ip], C.c_int),
+    "sim_amg_level_agg": ([_vp, C.c_int32, _ip], C.c_int),
+    "sim_amg_level_ell": ([_vp, C.c_int32, _ip, _dp], C.c_int),
+    "sim_component_mass": ([_vp, _dp], C.c_int),
+    "sim_cumulative_well_mass": ([_vp, _dp], C.c_int),
+    "sim_well_rates": ([_vp, _dp], C.c_int),
+    "sim_get_stats": ([_vp, C.POINTER(sim_stats)], C.c_int),
+    "sim_block_size": ([_vp], C.c_int32),
+    "sim_last_error": ([_vp], C.c_char_p),
+    "sim_clear_error": ([_vp], None),
+}
+
+_lib = None
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/sim.h."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(sim_[a-z0-9_]+)\s*\(", txt)))
+
+
+def load(path: str = LIB_PATH):
+    """Load libsim.so (built by build.build()); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run paper_1606_00548_gb300.build.build())")
+    L = C.CDLL(path)
+    for name, (args, res) in _SIGS.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _check(handle, st):
+    if st != SIM_OK:
+        msg = load().sim_last_error(handle)
+        raise SimError(st, msg.decode() if msg else "")
+
+
+def _d(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_dp)
+
+
+def _ptr(t):
+    """Device pointer of a CUDA torch tensor (contiguous float64)."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return _vp(t.data_ptr())
+
+
+def options_from(solver: dict, precision: int = 0) -> sim_options:
+    o = sim_options()
+    for name in ("newton_tol", "lin_tol", "amg_theta", "chop_ds", "chop_dp"):
+        setattr(o, name, float(solver[name]))
+    for name in ("newton_max", "gmres_m", "gmres_max_restarts", "precond", "stage2", "amg_rounds",
+                 "amg_coarse_max", "amg_max_levels", "max_cuts"):
+        setattr(o, name, int(solver[name]))
+    o.precision = int(precision)
+    return o
+
+
+class Simulator:
+    """One simulator handle for a synth case (inputs copied into the library)."""
+
+    def __init__(self, case: dict, precision: int = 0, stream=None, **solver_overrides):
+        L = load()
+        self.L = L
+        self.case = case
+        keep = []
+        g = sim_grid(case["nx"], case["ny"], case["nz"], case["dx"], case["dy"], case["dz"], case["top_depth"])
+        r = sim_rock()
+        for name in ("kx", "ky", "kz", "poro"):
+            a, p = _d(case[name]); keep.append(a); setattr(r, name, p)
+        r.c_rock, r.p_ref = case["c_rock"], case["p_ref"]
+        fl = case["fluid"]
+        f = sim_fluid()
+        f.model = case["model"]
+        for name, _ in sim_fluid._fields_:
+            if name in fl and name not in ("pvt_p", "pvt_bo", "pvt_rs", "pvt_muo", "pvt_bg", "pvt_mug"):
+                setattr(f, name, float(fl[name]))
+        if case["model"] == 3:
+            f.npvt = len(fl["pvt_p"])
+            for name in ("pvt_p", "pvt_bo", "pvt_rs", "pvt_muo", "pvt_bg", "pvt_mug"):
+                a, p = _d(fl[name]); keep.append(a); setattr(f, name, p)
+        for c in range(3):
+            f.cnv_rho[c] = case["cnv_rho"][c]
+        ws = case["wells"]
+        W = (sim_well * max(1, len(ws)))()
+        for k, w in enumerate(ws):
+            W[k] = sim_well(w["i"], w["j"], w["k0"], w["k1"], w["type"], w["bhp"], w["rw"], w["skin"])
+        sv = dict(case["solver"]); sv.update(solver_overrides)
+        self.opts = options_from(sv, precision)
+        h = _vp()
+        st = L.sim_create(C.byref(g), C.byref(r), C.byref(f), W, len(ws), C.byref(self.opts),
+                          _vp(stream) if stream else None, C.byref(h))
+        if st != SIM_OK:
+            raise SimError(st, (L.sim_last_error(None) or b"").decode())
+        self.h = h
+        self.N = case["nx"] * case["ny"] * case["nz"]
+        self.b = L.sim_block_size(h)
+        ini = case["init"]
+        self.set_state(ini["p"], ini["sw"], ini["x3"], ini["phase"])
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.sim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # state --------------------------------------------------------------------
+    def set_state(self, p, sw, x3, phase):
+        p, pp = _d(p); sw, sp = _d(sw); x3, xp = _d(x3)
+        ph = np.ascontiguousarray(phase, dtype=np.int8)
+        _check(self.h, self.L.sim_set_state(self.h, pp, sp, xp, ph.ctypes.data_as(_i8p)))
+
+    def get_state(self):
+        N = self.N
+        p = np.zeros(N); sw = np.zeros(N); x3 = np.zeros(N); ph = np.zeros(N, np.int8)
+        _check(self.h, self.L.sim_get_state(self.h, p.ctypes.data_as(_dp), sw.ctypes.data_as(_dp),
+                                            x3.ctypes.data_as(_dp), ph.ctypes.data_as(_i8p)))
+        return p, sw, x3, ph
+
+    def set_iterate(self, x, phase):
+        x, xp = _d(x)
+        ph = np.ascontiguousarray(phase, dtype=np.int8)
+        _check(self.h, self.L.sim_set_iterate(self.h, xp, ph.ctypes.data_as(_i8p)))
+
+    def get_iterate(self):
+        x = np.zeros(self.N * self.b); ph = np.zeros(self.N, np.int8)
+        _check(self.h, self.L.sim_get_iterate(self.h, x.ctypes.data_as(_dp), ph.ctypes.data_as(_i8p)))
+        return x, ph
+
+    # nonlinear ----------------------------------------------------------------
+    def step(self, dt):
+        info = sim_step_info()
+        st = self.L.sim_step(self.h, float(dt), C.byref(info))
+        if st not in (SIM_OK, SIM_ENOCONV_NEWTON):
+            _check(self.h, st)
+        return st, info
+
+    def newton_solve(self, dt):
+        info = sim_newton_info()
+        st = self.L.sim_newton_solve(self.h, float(dt), C.byref(info))
+        if st not in (SIM_OK, SIM_ENOCONV_NEWTON, SIM_ENAN):
+            _check(self.h, st)
+        return st, info
+
+    def newton_step(self, dt):
+        info = sim_newton_info()
+        st = self.L.sim_newton_step(self.h, float(dt), C.byref(info))
+        if st not in (SIM_OK, SIM_ENAN):
+            _check(self.h, st)
+        return st, info
+
+    # assembly / linear algebra -------------------------------------------------
+    def assemble(self, dt):
+        _check(self.h, self.L.sim_assemble(self.h, float(dt)))
+
+    def residual(self):
+        R = np.zeros(self.N * self.b)
+        _check(self.h, self.L.sim_get_residual(self.h, R.ctypes.data_as(_dp)))
+        return R
+
+    def jacobian(self):
+        J = np.zeros(7 * self.b * self.b * self.N)
+        _check(self.h, self.L.sim_get_jacobian(self.h, J.ctypes.data_as(_dp)))
+        return J
+
+    def set_jacobian(self, J):
+        J, jp = _d(J)
+        _check(self.h, self.L.sim_set_jacobian(self.h, jp))
+
+    def cnv(self, dt):
+        v = C.c_double()
+        _check(self.h, self.L.sim_cnv(self.h, float(dt), C.byref(v)))
+        return v.value
+
+    def spmv(self, x_dev, y_dev):
+        _check(self.h, self.L.sim_spmv(self.h, _ptr(x_dev), _ptr(y_dev)))
+
+    def precond_setup(self):
+        _check(self.h, self.L.sim_precond_setup(self.h))
+
+    def precond_apply(self, r_dev, z_dev):
+        _check(self.h, self.L.sim_precond_apply(self.h, _ptr(r_dev), _ptr(z_dev)))
+
+    def linear_solve(self, b_dev, x_dev):
+        info = sim_linear_info()
+        st = self.L.sim_linear_solve(self.h, _ptr(b_dev), _ptr(x_dev), C.byref(info))
+        if st not in (SIM_OK, SIM_ENOCONV_LINEAR):
+            _check(self.h, st)
+        return st, info
+
+    def qi(self):
+        w = np.zeros(self.b * self.N); ap = np.zeros(7 * self.N)
+        _check(self.h, self.L.sim_get_qi(self.h, w.ctypes.data_as(_dp), ap.ctypes.data_as(_dp)))
+        return w, ap
+
+    def amg_levels(self):
+        out = []
+        for l in range(self.L.sim_amg_levels(self.h)):
+            n = C.c_int32(); w = C.c_int32()
+            _check(self.h, self.L.sim_amg_level_info(self.h, l, C.byref(n), C.byref(w)))
+            d = dict(n=n.value, width=w.value)
+            if l + 1 < self.L.sim_amg_levels(self.h):
+                agg = np.zeros(n.value, np.int32)
+                _check(self.h, self.L.sim_amg_level_agg(self.h, l, agg.ctypes.data_as(_ip)))
+                d["agg"] = agg
+            if l >= 1:
+                col = np.zeros(w.value * n.value, np.int32); val = np.zeros(w.value * n.value)
+                _check(self.h, self.L.sim_amg_level_ell(self.h, l, col.ctypes.data_as(_ip), val.ctypes.data_as(_dp)))
+                d["col"] = col.reshape(w.value, n.value); d["val"] = val.reshape(w.value, n.value)
+            out.append(d)
+        return out
+
+    def component_mass(self):
+        m = np.zeros(3); _check(self.h, self.L.sim_component_mass(self.h, m.ctypes.data_as(_dp))); return m
+
+    def cumulative_well_mass(self):
+        m = np.zeros(3); _check(self.h, self.L.sim_cumulative_well_mass(self.h, m.ctypes.data_as(_dp))); return m
+
+    def well_rates(self):
+        q = np.zeros(3); _check(self.h, self.L.sim_well_rates(self.h, q.ctypes.data_as(_dp))); return q
+
+    def stats(self):
+        s = sim_stats(); _check(self.h, self.L.sim_get_stats(self.h, C.byref(s))); return s
