@@ -182,7 +182,7 @@ typedef struct {
     int32_t *rowptr, *col;
     double *val, *dl1;
     int32_t *agg;       /* fine -> next level (absent on the coarsest) */
-    int32_t *mem4;      /* next-level aggregate -> up to 4 members of this level */
+    int32_t *moff, *mem;/* members of each next-level aggregate, ascending (CSR) */
     double *lu;         /* coarsest: dense LU factors */
     int32_t *piv;
     double *t1, *t2, *t3;
@@ -324,7 +324,7 @@ ora_sim *ora_create(const ora_input *in) {
 static void free_levels(ora_sim *s) {
     for (int l = 0; l < s->nlev; l++) {
         level_t *L = &s->lev[l];
-        free(L->rowptr); free(L->col); free(L->val); free(L->dl1); free(L->agg); free(L->mem4);
+        free(L->rowptr); free(L->col); free(L->val); free(L->dl1); free(L->agg); free(L->moff); free(L->mem);
         free(L->lu); free(L->piv); free(L->t1); free(L->t2); free(L->t3);
         memset(L, 0, sizeof(*L));
     }
@@ -659,36 +659,83 @@ int ora_match_pass(int n, const int32_t *rowptr, const int32_t *col, const doubl
     return done_rounds;
 }
 
-/* number the pairs/singletons by their lowest member */
-static int number_aggregates(int n, const int32_t *partner, int32_t *agg, int32_t *mem2) {
+/* aggregates of one pass: matched pairs, plus every single node that has a
+   strong matched neighbour joining the aggregate of the strongest such
+   neighbour (same key as the matching); other single nodes stay alone.
+   Aggregates are numbered in the order of their lowest-index founder
+   (pair leader or lone node).  Returns the number of aggregates. */
+static int form_aggregates(int n, const int32_t *rowptr, const int32_t *col, const double *val, double theta,
+                           const int32_t *partner, int32_t *agg) {
+    int32_t *host = xmalloc(sizeof(int32_t) * (n ? n : 1));
+    for (int i = 0; i < n; i++) {
+        host[i] = -1;
+        if (partner[i] >= 0) continue;
+        double mx = 0.0;
+        for (int k = rowptr[i]; k < rowptr[i + 1]; k++)
+            if (col[k] != i && -val[k] > mx) mx = -val[k];
+        if (mx <= 0.0) continue;
+        int best = -1, bs = 0; uint64_t bh = 0;
+        for (int k = rowptr[i]; k < rowptr[i + 1]; k++) {
+            int j = col[k];
+            if (j == i || partner[j] < 0) continue;
+            double a = -val[k];
+            if (!(a > 0.0) || a < theta * mx) continue;
+            int band = strength_band(a);
+            uint64_t h = edge_hash(i, j);
+            if (best < 0 || band > bs || (band == bs && (h > bh || (h == bh && j < best)))) { best = j; bs = band; bh = h; }
+        }
+        host[i] = best;
+    }
     int nc = 0;
     for (int i = 0; i < n; i++) {
         int p = partner[i];
-        if (p < 0 || i < p) { mem2[2 * nc] = i; mem2[2 * nc + 1] = p; agg[i] = nc; if (p >= 0) agg[p] = nc; nc++; }
+        if ((p >= 0 && i < p) || (p < 0 && host[i] < 0)) agg[i] = nc++;
+        else agg[i] = -1;
     }
+    for (int i = 0; i < n; i++) {
+        int p = partner[i];
+        if (p >= 0 && i > p) agg[i] = agg[p];
+    }
+    for (int i = 0; i < n; i++) {
+        if (partner[i] < 0 && host[i] >= 0) {
+            int h = host[i], hp = partner[h];
+            agg[i] = agg[h < hp ? h : hp];
+        }
+    }
+    free(host);
     return nc;
 }
 
+/* members of each aggregate in ascending order (CSR) */
+static void members_of(int n, const int32_t *agg, int nc, int32_t **moff_out, int32_t **mem_out) {
+    int32_t *moff = xmalloc(sizeof(int32_t) * (nc + 1)), *mem = xmalloc(sizeof(int32_t) * (n ? n : 1));
+    int32_t *pos = xmalloc(sizeof(int32_t) * (nc + 1));
+    for (int i = 0; i < n; i++) moff[agg[i] + 1]++;
+    for (int I = 0; I < nc; I++) moff[I + 1] += moff[I];
+    for (int I = 0; I < nc; I++) pos[I] = moff[I];
+    for (int i = 0; i < n; i++) mem[pos[agg[i]]++] = i;
+    free(pos);
+    *moff_out = moff; *mem_out = mem;
+}
+
 /* Galerkin product P^T A P for piecewise-constant P: coarse row I sums the
-   rows of its members (in member order, then column order) into columns
-   agg[j]; coarse columns sorted ascending */
+   rows of its members (ascending member order, then column order) into
+   columns agg[j]; coarse columns sorted ascending */
 static void galerkin(int n, const int32_t *rowptr, const int32_t *col, const double *val,
-                     const int32_t *agg, const int32_t *mem, int memw, int nc,
+                     const int32_t *agg, const int32_t *moff, const int32_t *mem, int nc,
                      int32_t **rp_out, int32_t **col_out, double **val_out) {
     int cap = 64;
     int32_t *cols = xmalloc(sizeof(int32_t) * cap); double *vals = xmalloc(sizeof(double) * cap);
     int32_t *rp = xmalloc(sizeof(int32_t) * (nc + 1));
     size_t nnzcap = (size_t)rowptr[n] + 16, nnz = 0;
     int32_t *oc = xmalloc(sizeof(int32_t) * nnzcap); double *ov = xmalloc(sizeof(double) * nnzcap);
-    (void)n;
     for (int I = 0; I < nc; I++) {
         int cnt = 0;
-        for (int s = 0; s < memw; s++) {
-            int m = mem[(size_t)I * memw + s];
-            if (m < 0) continue;
+        for (int t = moff[I]; t < moff[I + 1]; t++) {
+            int m = mem[t];
             for (int k = rowptr[m]; k < rowptr[m + 1]; k++) {
                 int Jc = agg[col[k]], f = -1;
-                for (int t = 0; t < cnt; t++) if (cols[t] == Jc) { f = t; break; }
+                for (int q = 0; q < cnt; q++) if (cols[q] == Jc) { f = q; break; }
                 if (f < 0) {
                     if (cnt == cap) { cap *= 2; cols = realloc(cols, sizeof(int32_t) * cap); vals = realloc(vals, sizeof(double) * cap); }
                     cols[cnt] = Jc; vals[cnt] = 0.0; f = cnt++;
@@ -698,13 +745,13 @@ static void galerkin(int n, const int32_t *rowptr, const int32_t *col, const dou
         }
         /* insertion sort by column */
         for (int a = 1; a < cnt; a++) {
-            int cj = cols[a]; double cv = vals[a]; int t = a - 1;
-            while (t >= 0 && cols[t] > cj) { cols[t + 1] = cols[t]; vals[t + 1] = vals[t]; t--; }
-            cols[t + 1] = cj; vals[t + 1] = cv;
+            int cj = cols[a]; double cv = vals[a]; int q = a - 1;
+            while (q >= 0 && cols[q] > cj) { cols[q + 1] = cols[q]; vals[q + 1] = vals[q]; q--; }
+            cols[q + 1] = cj; vals[q + 1] = cv;
         }
         rp[I] = (int32_t)nnz;
         if (nnz + cnt > nnzcap) { nnzcap = 2 * (nnz + cnt); oc = realloc(oc, sizeof(int32_t) * nnzcap); ov = realloc(ov, sizeof(double) * nnzcap); }
-        for (int t = 0; t < cnt; t++) { oc[nnz] = cols[t]; ov[nnz] = vals[t]; nnz++; }
+        for (int q = 0; q < cnt; q++) { oc[nnz] = cols[q]; ov[nnz] = vals[q]; nnz++; }
     }
     rp[nc] = (int32_t)nnz;
     free(cols); free(vals);
@@ -733,32 +780,32 @@ static void amg_setup(ora_sim *s, int32_t *rp0, int32_t *col0, double *val0, int
         L = &s->lev[s->nlev - 1];
         if (L->n <= in->amg_coarse_max || s->nlev >= in->amg_max_levels || s->nlev >= 32) break;
         int n = L->n;
-        int32_t *p1 = xmalloc(sizeof(int32_t) * n), *agg1 = xmalloc(sizeof(int32_t) * n), *mem1 = xmalloc(sizeof(int32_t) * 2 * n);
+        int32_t *p1 = xmalloc(sizeof(int32_t) * n), *agg1 = xmalloc(sizeof(int32_t) * n);
         ora_match_pass(n, L->rowptr, L->col, L->val, in->amg_theta, in->amg_rounds, p1);
-        int n1 = number_aggregates(n, p1, agg1, mem1);
+        int n1 = form_aggregates(n, L->rowptr, L->col, L->val, in->amg_theta, p1, agg1);
+        int32_t *o1, *m1;
+        members_of(n, agg1, n1, &o1, &m1);
         int32_t *rp1, *c1; double *v1;
-        galerkin(n, L->rowptr, L->col, L->val, agg1, mem1, 2, n1, &rp1, &c1, &v1);
-        int32_t *p2 = xmalloc(sizeof(int32_t) * n1), *agg2 = xmalloc(sizeof(int32_t) * n1), *mem2 = xmalloc(sizeof(int32_t) * 2 * n1);
+        galerkin(n, L->rowptr, L->col, L->val, agg1, o1, m1, n1, &rp1, &c1, &v1);
+        int32_t *p2 = xmalloc(sizeof(int32_t) * n1), *agg2 = xmalloc(sizeof(int32_t) * n1);
         ora_match_pass(n1, rp1, c1, v1, in->amg_theta, in->amg_rounds, p2);
-        int n2 = number_aggregates(n1, p2, agg2, mem2);
-        if (4 * (long)n2 > 3 * (long)n) {  /* coarsening stalled (> 3/4 kept): this level is the coarsest */
-            free(p1); free(agg1); free(mem1); free(rp1); free(c1); free(v1); free(p2); free(agg2); free(mem2);
-            break;
+        int n2 = form_aggregates(n1, rp1, c1, v1, in->amg_theta, p2, agg2);
+        int32_t *o2, *m2;
+        members_of(n1, agg2, n2, &o2, &m2);
+        int stalled = 4 * (long)n2 > 3 * (long)n;   /* coarsening stalled (> 3/4 kept) */
+        if (!stalled) {
+            level_t *C = &s->lev[s->nlev];
+            galerkin(n1, rp1, c1, v1, agg2, o2, m2, n2, &C->rowptr, &C->col, &C->val);
+            C->n = n2;
+            L->agg = xmalloc(sizeof(int32_t) * n);
+            for (int i = 0; i < n; i++) L->agg[i] = agg2[agg1[i]];
+            members_of(n, L->agg, n2, &L->moff, &L->mem);
+            level_finish(C);
+            s->nlev++;
         }
-        level_t *C = &s->lev[s->nlev];
-        galerkin(n1, rp1, c1, v1, agg2, mem2, 2, n2, &C->rowptr, &C->col, &C->val);
-        C->n = n2;
-        L->agg = xmalloc(sizeof(int32_t) * n);
-        for (int i = 0; i < n; i++) L->agg[i] = agg2[agg1[i]];
-        L->mem4 = xmalloc(sizeof(int32_t) * 4 * n2);
-        for (int I = 0; I < n2; I++)
-            for (int a = 0; a < 2; a++) {
-                int m1 = mem2[2 * I + a];
-                for (int c = 0; c < 2; c++) L->mem4[4 * I + 2 * a + c] = m1 >= 0 ? mem1[2 * m1 + c] : -1;
-            }
-        level_finish(C);
-        s->nlev++;
-        free(p1); free(agg1); free(mem1); free(rp1); free(c1); free(v1); free(p2); free(agg2); free(mem2);
+        free(p1); free(agg1); free(o1); free(m1); free(rp1); free(c1); free(v1);
+        free(p2); free(agg2); free(o2); free(m2);
+        if (stalled) break;
     }
     /* coarsest level: dense LU */
     L = &s->lev[s->nlev - 1];
@@ -793,7 +840,7 @@ static void vcycle(ora_sim *s, int l, const double *f, double *e) {
     double *fc = C->t2, *ec = C->t3;
     for (int I = 0; I < C->n; I++) {
         double t = 0.0;
-        for (int a = 0; a < 4; a++) { int m = L->mem4[4 * I + a]; if (m >= 0) t += L->t1[m]; }
+        for (int q = L->moff[I]; q < L->moff[I + 1]; q++) t += L->t1[L->mem[q]];
         fc[I] = t;
     }
     vcycle(s, l + 1, fc, ec);

@@ -476,13 +476,19 @@ __device__ void finish_grid(double *partials, int nv, unsigned int *ticket, doub
     __syncthreads();
     if (!last) return;
     __threadfence();
-    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    // one warp per value, lanes stride over the partials, fixed shuffle tree
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int v = wid; v < nv; v += nw) {
         double acc = 0.0;
-        for (int k = 0; k < (int)gridDim.x; k++) {
-            double p = ((volatile double *)partials)[v * gridDim.x + k];
+        for (int k = lane; k < (int)gridDim.x; k += 32) {
+            const double p = __ldcg(partials + (long)v * gridDim.x + k);
             acc = OP == 0 ? acc + p : nanmax(acc, p);
         }
-        out[v] = acc;
+        for (int o = 16; o > 0; o >>= 1) {
+            const double t = __shfl_down_sync(0xffffffffu, acc, o);
+            acc = OP == 0 ? acc + t : nanmax(acc, t);
+        }
+        if (lane == 0) out[v] = acc;
     }
     if (threadIdx.x == 0) *ticket = 0u;
 }

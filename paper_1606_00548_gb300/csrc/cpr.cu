@@ -272,17 +272,47 @@ __global__ void match_confirm_kernel(int n, const int *__restrict__ pick, int *_
     if (partner[i] < 0 && p >= 0 && pick[p] == i) partner[i] = p;
 }
 
-// exclusive scan of leader flags in chunks of SCAN_CHUNK per block
-constexpr int SCAN_CHUNK = 4096;
-__device__ __forceinline__ int leader_flag(const int *partner, int i) { const int p = partner[i]; return (p < 0 || i < p) ? 1 : 0; }
+// single nodes join the aggregate of their strongest strong matched
+// neighbour (same key as the matching): host[i], or -1
+__global__ void host_kernel(Mat<double> A, const int *__restrict__ partner, int *__restrict__ host, double theta) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.n) return;
+    host[i] = -1;
+    if (partner[i] >= 0) return;
+    double mx = 0.0;
+    for_row(A, i, [&](int j, double a) { if (j != i && -a > mx) mx = -a; });
+    if (mx <= 0.0) return;
+    int best = -1, bs = 0;
+    unsigned long long bh = 0ULL;
+    const double lim = theta * mx;
+    for_row(A, i, [&](int j, double v) {
+        if (j == i || partner[j] < 0) return;
+        const double a = -v;
+        if (!(a > 0.0) || a < lim) return;
+        const int band = strength_band(a);
+        const unsigned long long h = edge_hash(i, j);
+        if (best < 0 || band > bs || (band == bs && (h > bh || (h == bh && j < best)))) { best = j; bs = band; bh = h; }
+    });
+    host[i] = best;
+}
 
-__global__ void scan_count_kernel(int n, const int *__restrict__ partner, int *__restrict__ bsum) {
+// founders: pair leaders (lower index of a pair) and lone nodes without a host
+__global__ void founder_kernel(int n, const int *__restrict__ partner, const int *__restrict__ host, int *__restrict__ flag) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int p = partner[i];
+    flag[i] = ((p >= 0 && i < p) || (p < 0 && host[i] < 0)) ? 1 : 0;
+}
+
+// generic exclusive scan of n ints in chunks of SCAN_CHUNK per block
+constexpr int SCAN_CHUNK = 4096;
+__global__ void scan_sum_kernel(int n, const int *__restrict__ in, int *__restrict__ bsum) {
     __shared__ int sh[SIM_THREADS];
     const int base = blockIdx.x * SCAN_CHUNK;
     int c = 0;
     for (int t = threadIdx.x; t < SCAN_CHUNK; t += blockDim.x) {
         const int i = base + t;
-        if (i < n) c += leader_flag(partner, i);
+        if (i < n) c += in[i];
     }
     sh[threadIdx.x] = c;
     __syncthreads();
@@ -318,15 +348,15 @@ __global__ void scan_blocks_kernel(int nb, int *__restrict__ bsum, int *__restri
     if (threadIdx.x == 0) *total = carry;
 }
 
-// ids of leaders; agg of every node; members (leader, partner) of each aggregate ([2][nc])
-__global__ void number_kernel(int n, const int *__restrict__ partner, const int *__restrict__ bsum, int *__restrict__ id,
-                              int nc_cap, int *__restrict__ mem) {
+// out[i] = sum_{k<i} in[k]; out[n] = total
+__global__ void scan_write_kernel(int n, const int *__restrict__ in, const int *__restrict__ bsum, const int *__restrict__ total,
+                                  int *__restrict__ out) {
     __shared__ int sh[SIM_THREADS];
     const int base = blockIdx.x * SCAN_CHUNK;
     constexpr int PER = SCAN_CHUNK / SIM_THREADS;
     const int t0 = base + threadIdx.x * PER;
     int local = 0;
-    for (int k = 0; k < PER; k++) { const int i = t0 + k; if (i < n) local += leader_flag(partner, i); }
+    for (int k = 0; k < PER; k++) { const int i = t0 + k; if (i < n) local += in[i]; }
     sh[threadIdx.x] = local;
     __syncthreads();
     for (int o = 1; o < (int)blockDim.x; o <<= 1) {
@@ -339,36 +369,64 @@ __global__ void number_kernel(int n, const int *__restrict__ partner, const int 
     for (int k = 0; k < PER; k++) {
         const int i = t0 + k;
         if (i >= n) break;
-        if (leader_flag(partner, i)) {
-            id[i] = run;
-            if (run < nc_cap) { mem[run] = i; mem[nc_cap + run] = partner[i]; }
-            run++;
-        }
+        out[i] = run;
+        run += in[i];
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = *total;
 }
 
-__global__ void agg_kernel(int n, const int *__restrict__ partner, const int *__restrict__ id, int *__restrict__ agg) {
+// aggregate of every node: founders own ids; pair followers take the
+// leader's; absorbed nodes take their host pair's
+__global__ void agg_kernel(int n, const int *__restrict__ partner, const int *__restrict__ host, const int *__restrict__ id,
+                           int *__restrict__ agg) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int p = partner[i];
-    agg[i] = (p < 0 || i < p) ? id[i] : id[p];
+    int a;
+    if (p >= 0) a = id[i < p ? i : p];
+    else if (host[i] < 0) a = id[i];
+    else { const int h = host[i], hp = partner[h]; a = id[h < hp ? h : hp]; }
+    agg[i] = a;
 }
 
-// Galerkin row I of P^T A P: members mem[s*nc + I] (s < memw), entries summed
+__global__ void count_kernel(int n, const int *__restrict__ agg, int *__restrict__ cnt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicAdd(&cnt[agg[i]], 1);
+}
+__global__ void fill_kernel(int n, const int *__restrict__ agg, const int *__restrict__ moff, int *__restrict__ pos,
+                            int *__restrict__ mem) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int a = agg[i];
+    mem[moff[a] + atomicAdd(&pos[a], 1)] = i;
+}
+// members of each aggregate in ascending order (the fill order is arbitrary)
+__global__ void sort_members_kernel(int nc, const int *__restrict__ moff, int *__restrict__ mem) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc) return;
+    const int a0 = moff[I], a1 = moff[I + 1];
+    for (int a = a0 + 1; a < a1; a++) {
+        const int v = mem[a];
+        int t = a - 1;
+        while (t >= a0 && mem[t] > v) { mem[t + 1] = mem[t]; t--; }
+        mem[t + 1] = v;
+    }
+}
+
+// Galerkin row I of P^T A P: members moff/mem (ascending), entries summed
 // in member order then column order, columns sorted ascending.
 // mode 0: row length into len[I]; mode 1: write the ELL row of width W
-__global__ void galerkin_kernel(Mat<double> A, const int *__restrict__ agg, const int *__restrict__ mem, int memw,
-                                int mstride, int nc, int mode, int *__restrict__ len, int W, int *__restrict__ ccol,
-                                double *__restrict__ cval, int *err) {
+__global__ void galerkin_kernel(Mat<double> A, const int *__restrict__ agg, const int *__restrict__ moff,
+                                const int *__restrict__ mem, int nc, int mode, int *__restrict__ len, int W,
+                                int *__restrict__ ccol, double *__restrict__ cval, int *err) {
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nc) return;
     int cols[MAXE];
     double vals[MAXE];
     int cnt = 0;
     bool over = false;
-    for (int s = 0; s < memw; s++) {
-        const int m = mem[(long)s * mstride + I];
-        if (m < 0) continue;
+    for (int q = moff[I]; q < moff[I + 1]; q++) {
+        const int m = mem[q];
         for_row(A, m, [&](int j, double a) {
             const int Jc = agg[j];
             int f = -1;
@@ -399,18 +457,6 @@ __global__ void compose_kernel(int n, const int *__restrict__ aggA, const int *_
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) agg[i] = aggB[aggA[i]];
 }
-// members of the composed aggregate I: pass-2 members (stride sB) expanded
-// into their pass-1 members (stride sA), slot order (a, c)
-__global__ void compose_mem_kernel(int n2, const int *__restrict__ memA, int sA, const int *__restrict__ memB, int sB,
-                                   int *__restrict__ mem4) {
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
-    if (I >= n2) return;
-    for (int a = 0; a < 2; a++) {
-        const int m1 = memB[(long)a * sB + I];
-        for (int c = 0; c < 2; c++) mem4[(long)(2 * a + c) * n2 + I] = m1 >= 0 ? memA[(long)c * sA + m1] : -1;
-    }
-}
-
 template <typename T>
 __global__ void l1_kernel(Mat<double> A, T *__restrict__ dinv) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -498,16 +544,15 @@ __global__ void restrict_p_kernel(int N, const double *__restrict__ r, const T *
 
 // f_c = P^T (f - A e) ; e_c = f_c / l1 (pre-smoothing on the coarse level)
 template <typename T>
-__global__ void resid_restrict_kernel(Mat<T> A, const T *__restrict__ f, const T *__restrict__ e, const int *__restrict__ mem4,
-                                      int nc, T *__restrict__ fc, T *__restrict__ ec, const T *__restrict__ dinvc,
-                                      const int *done) {
+__global__ void resid_restrict_kernel(Mat<T> A, const T *__restrict__ f, const T *__restrict__ e, const int *__restrict__ moff,
+                                      const int *__restrict__ mem, int nc, T *__restrict__ fc, T *__restrict__ ec,
+                                      const T *__restrict__ dinvc, const int *done) {
     if (skip(done)) return;
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nc) return;
     T s = (T)0;
-    for (int a = 0; a < 4; a++) {
-        const int m = mem4[(long)a * nc + I];
-        if (m < 0) continue;
+    for (int q = moff[I]; q < moff[I + 1]; q++) {
+        const int m = mem[q];
         T t = (T)0;
         for_row(A, m, [&](int j, T v) { t += v * e[j]; });
         s += f[m] - t;
@@ -699,7 +744,7 @@ static void free_level(sim_t *s, AmgLevel &L) {
     // valT may alias the FP64 values or the level-0 stencil owned by the handle
     if (L.valT != (void *)L.val && L.valT != s->apT) dev_free_async(s, L.valT);
     dev_free_async(s, L.col); dev_free_async(s, L.val); dev_free_async(s, L.dinvT);
-    dev_free_async(s, L.agg); dev_free_async(s, L.mem4); dev_free_async(s, L.f); dev_free_async(s, L.e);
+    dev_free_async(s, L.agg); dev_free_async(s, L.moff); dev_free_async(s, L.mem); dev_free_async(s, L.f); dev_free_async(s, L.e);
     dev_free_async(s, L.e2); dev_free_async(s, L.coarse_inv);
     L = AmgLevel();
 }
@@ -725,39 +770,63 @@ static Mat<T> level_matT(sim_t *s, const AmgLevel &L, int l) {
     return A;
 }
 
-// one pairwise pass on A (n rows): partner -> agg (n), mem [2][nc]; returns nc
-static int pair_pass(sim_t *s, const Mat<double> &A, int *agg, int *mem, int mem_cap) {
+// exclusive scan of n ints: out[0..n] (out[n] = total); returns total or -1
+static int scan_ints(sim_t *s, const int *in, int n, int *out) {
+    const int nb = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
+    scan_sum_kernel<<<nb, SIM_THREADS, 0, s->stream>>>(n, in, s->scan);
+    scan_blocks_kernel<<<1, 1024, 0, s->stream>>>(nb, s->scan, s->iscal);
+    scan_write_kernel<<<nb, SIM_THREADS, 0, s->stream>>>(n, in, s->scan, s->iscal, out);
+    s->launches += 3;
+    if (!sim_cuda_ok(s, cudaGetLastError(), "scan")) return -1;
+    if (!sim_cuda_ok(s, cudaMemcpyAsync(&s->h_pinned[0], s->iscal, sizeof(int), cudaMemcpyDeviceToHost, s->stream), "copy")) return -1;
+    if (!sim_cuda_ok(s, cudaStreamSynchronize(s->stream), "sync")) return -1;
+    int total = 0;
+    memcpy(&total, &s->h_pinned[0], sizeof(int));
+    return total;
+}
+
+// members of each of nc aggregates in ascending order: moff[nc+1], mem[n]
+static bool build_members(sim_t *s, const int *agg, int n, int nc, int *moff, int *mem) {
+    if (!sim_cuda_ok(s, cudaMemsetAsync(s->cnt, 0, sizeof(int) * (nc + 1), s->stream), "memset")) return false;
+    count_kernel<<<sim_blocks(n), SIM_THREADS, 0, s->stream>>>(n, agg, s->cnt);
+    s->launches++;
+    if (scan_ints(s, s->cnt, nc, moff) < 0) return false;
+    if (!sim_cuda_ok(s, cudaMemsetAsync(s->cnt, 0, sizeof(int) * (nc + 1), s->stream), "memset")) return false;
+    fill_kernel<<<sim_blocks(n), SIM_THREADS, 0, s->stream>>>(n, agg, moff, s->cnt, mem);
+    sort_members_kernel<<<sim_blocks(nc), SIM_THREADS, 0, s->stream>>>(nc, moff, mem);
+    s->launches += 2;
+    return sim_cuda_ok(s, cudaGetLastError(), "members");
+}
+
+// one aggregation pass on A (n rows): matching rounds, absorption of single
+// nodes, numbering by founders; agg[n], members moff/mem; returns nc or -1
+static int aggregate_pass(sim_t *s, const Mat<double> &A, int *agg, int *moff, int *mem) {
     const int n = A.n;
     if (!sim_cuda_ok(s, cudaMemsetAsync(s->partner, 0xff, sizeof(int) * n, s->stream), "memset")) return -1;
     for (int r = 0; r < s->opt.amg_rounds; r++) {
         match_pick_kernel<<<sim_blocks(n), SIM_THREADS, 0, s->stream>>>(A, s->partner, s->pick, s->opt.amg_theta);
-        s->launches++;
         match_confirm_kernel<<<sim_blocks(n), SIM_THREADS, 0, s->stream>>>(n, s->pick, s->partner);
-        s->launches++;
+        s->launches += 2;
     }
-    const int nb = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
-    scan_count_kernel<<<nb, SIM_THREADS, 0, s->stream>>>(n, s->partner, s->scan);
-    scan_blocks_kernel<<<1, 1024, 0, s->stream>>>(nb, s->scan, s->iscal);
-    number_kernel<<<nb, SIM_THREADS, 0, s->stream>>>(n, s->partner, s->scan, s->pick, mem_cap, mem);
-    agg_kernel<<<sim_blocks(n), SIM_THREADS, 0, s->stream>>>(n, s->partner, s->pick, agg);
-    s->launches += 4;
-    if (!sim_cuda_ok(s, cudaGetLastError(), "AMG matching")) return -1;
-    int nc = 0;
-    if (!sim_cuda_ok(s, cudaMemcpyAsync(&s->h_pinned[0], s->iscal, sizeof(int), cudaMemcpyDeviceToHost, s->stream), "copy")) return -1;
-    if (!sim_cuda_ok(s, cudaStreamSynchronize(s->stream), "sync")) return -1;
-    memcpy(&nc, &s->h_pinned[0], sizeof(int));
+    host_kernel<<<sim_blocks(n), SIM_THREADS, 0, s->stream>>>(A, s->partner, s->host, s->opt.amg_theta);
+    founder_kernel<<<sim_blocks(n), SIM_THREADS, 0, s->stream>>>(n, s->partner, s->host, s->flag);
+    s->launches += 2;
+    const int nc = scan_ints(s, s->flag, n, s->pick);   // pick reused as founder ids
+    if (nc < 0) return -1;
+    agg_kernel<<<sim_blocks(n), SIM_THREADS, 0, s->stream>>>(n, s->partner, s->host, s->pick, agg);
+    s->launches++;
+    if (!build_members(s, agg, n, nc, moff, mem)) return -1;
     return nc;
 }
 
 // Galerkin product into a freshly allocated ELL matrix; returns width or -1.
-// mem: members [2][mstride] of each coarse row
-static int galerkin(sim_t *s, const Mat<double> &A, const int *agg, const int *mem, int mstride, int nc, int **col,
+static int galerkin(sim_t *s, const Mat<double> &A, const int *agg, const int *moff, const int *mem, int nc, int **col,
                     double **val) {
     int *len = (int *)dev_alloc_async(s, sizeof(int) * (nc + 1));
     if (!len) return -1;
     if (!sim_cuda_ok(s, cudaMemsetAsync(len + nc, 0, sizeof(int), s->stream), "memset")) return -1;
     if (!sim_cuda_ok(s, cudaMemsetAsync(s->iscal + 1, 0, sizeof(int), s->stream), "memset")) return -1;
-    galerkin_kernel<<<sim_blocks(nc), SIM_THREADS, 0, s->stream>>>(A, agg, mem, 2, mstride, nc, 0, len, 0, nullptr, nullptr,
+    galerkin_kernel<<<sim_blocks(nc), SIM_THREADS, 0, s->stream>>>(A, agg, moff, mem, nc, 0, len, 0, nullptr, nullptr,
                                                                    s->iscal + 1);
     s->launches++;
     int hv[2];
@@ -771,7 +840,7 @@ static int galerkin(sim_t *s, const Mat<double> &A, const int *agg, const int *m
     *col = (int *)dev_alloc_async(s, sizeof(int) * (size_t)W * nc);
     *val = (double *)dev_alloc_async(s, sizeof(double) * (size_t)W * nc);
     if (!*col || !*val) return -1;
-    galerkin_kernel<<<sim_blocks(nc), SIM_THREADS, 0, s->stream>>>(A, agg, mem, 2, mstride, nc, 1, len, W, *col, *val,
+    galerkin_kernel<<<sim_blocks(nc), SIM_THREADS, 0, s->stream>>>(A, agg, moff, mem, nc, 1, len, W, *col, *val,
                                                                    s->iscal + 1);
     s->launches++;
     dev_free_async(s, len);
@@ -841,13 +910,13 @@ static sim_status amg_setup(sim_t *s) {
         if (L.n <= cmax || (int)s->lev.size() >= s->opt.amg_max_levels) break;
         const int n = L.n;
         Mat<double> A = level_mat(s, L, l);
-        const int n1 = pair_pass(s, A, s->aggA, s->memA, n);
+        const int n1 = aggregate_pass(s, A, s->aggA, s->moffA, s->memA);
         if (n1 < 0) return s->err;
         int *c1 = nullptr; double *v1 = nullptr;
-        const int W1 = galerkin(s, A, s->aggA, s->memA, n, n1, &c1, &v1);
+        const int W1 = galerkin(s, A, s->aggA, s->moffA, s->memA, n1, &c1, &v1);
         if (W1 < 0) return s->err;
         Mat<double> A1; A1.st = false; A1.g = s->gd; A1.n = n1; A1.width = W1; A1.col = c1; A1.val = v1;
-        const int n2 = pair_pass(s, A1, s->aggB, s->memB, n1);
+        const int n2 = aggregate_pass(s, A1, s->aggB, s->moffB, s->memB);
         if (n2 < 0) return s->err;
         if (4L * n2 > 3L * n) {   // coarsening stalled: this level is the coarsest
             dev_free_async(s, c1); dev_free_async(s, v1);
@@ -855,16 +924,17 @@ static sim_status amg_setup(sim_t *s) {
         }
         AmgLevel C;
         C.n = n2;
-        const int W2 = galerkin(s, A1, s->aggB, s->memB, n1, n2, &C.col, &C.val);
+        const int W2 = galerkin(s, A1, s->aggB, s->moffB, s->memB, n2, &C.col, &C.val);
         if (W2 < 0) return s->err;
         C.width = W2;
         AmgLevel &Lr = s->lev[l];    // (reference still valid: no push yet)
         Lr.agg = (int *)dev_alloc_async(s, sizeof(int) * n);
-        Lr.mem4 = (int *)dev_alloc_async(s, sizeof(int) * 4 * (size_t)n2);
-        if (!Lr.agg || !Lr.mem4) return s->err;
+        Lr.moff = (int *)dev_alloc_async(s, sizeof(int) * (size_t)(n2 + 1));
+        Lr.mem = (int *)dev_alloc_async(s, sizeof(int) * (size_t)n);
+        if (!Lr.agg || !Lr.moff || !Lr.mem) return s->err;
         compose_kernel<<<sim_blocks(n), SIM_THREADS, 0, s->stream>>>(n, s->aggA, s->aggB, Lr.agg);
-        compose_mem_kernel<<<sim_blocks(n2), SIM_THREADS, 0, s->stream>>>(n2, s->memA, n, s->memB, n1, Lr.mem4);
-        s->launches += 2;
+        s->launches++;
+        if (!build_members(s, Lr.agg, n, n2, Lr.moff, Lr.mem)) return s->err;
         dev_free_async(s, c1); dev_free_async(s, v1);
         s->lev.push_back(C);
     }
@@ -917,7 +987,7 @@ static sim_status vcycle(sim_t *s, const int *done) {
         AmgLevel &L = s->lev[l], &C = s->lev[l + 1];
         const bool coarsest = (l + 1 == nl - 1);
         resid_restrict_kernel<T><<<sim_blocks(C.n), SIM_THREADS, 0, s->stream>>>(
-            level_matT<T>(s, L, l), (const T *)L.f, (const T *)L.e, L.mem4, C.n, (T *)C.f,
+            level_matT<T>(s, L, l), (const T *)L.f, (const T *)L.e, L.moff, L.mem, C.n, (T *)C.f,
             coarsest ? nullptr : (T *)C.e, (const T *)C.dinvT, done);
         SIM_LAUNCHED(s);
     }

@@ -98,11 +98,15 @@ __device__ bool last_block(unsigned int *ticket) {
     return last;
 }
 
+// one warp per value: lanes stride over the block partials, then a fixed
+// shuffle tree (the summation order does not depend on timing)
 __device__ void fold(const double *partials, int nv, double *out) {
-    for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = wid; k < nv; k += nw) {
         double s = 0.0;
-        for (int b = 0; b < (int)gridDim.x; b++) s += ((volatile const double *)partials)[k * gridDim.x + b];
-        out[k] = s;
+        for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(partials + (long)k * gridDim.x + b);
+        s = warp_sum(s);
+        if (lane == 0) out[k] = s;
     }
 }
 

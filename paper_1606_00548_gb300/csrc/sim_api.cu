@@ -191,11 +191,16 @@ sim_status sim_create(const sim_grid *g, const sim_rock *r, const sim_fluid *f, 
     s->r2 = A(tsz * n);
     s->zr = A(tsz * n);
     s->partner = (int *)A(sizeof(int) * N);
-    s->pick = (int *)A(sizeof(int) * N);
+    s->pick = (int *)A(sizeof(int) * (N + 1));   // also holds founder ids + total
     s->aggA = (int *)A(sizeof(int) * N);
     s->aggB = (int *)A(sizeof(int) * N);
-    s->memA = (int *)A(sizeof(int) * 2 * N);
-    s->memB = (int *)A(sizeof(int) * 2 * N);
+    s->host = (int *)A(sizeof(int) * N);
+    s->flag = (int *)A(sizeof(int) * N);
+    s->cnt = (int *)A(sizeof(int) * (N + 1));
+    s->moffA = (int *)A(sizeof(int) * (N + 1));
+    s->memA = (int *)A(sizeof(int) * N);
+    s->moffB = (int *)A(sizeof(int) * (N + 1));
+    s->memB = (int *)A(sizeof(int) * N);
     s->scan = (int *)A(sizeof(int) * (N / 4096 + 2));
     s->iscal = (int *)A(sizeof(int) * 8);
     if (!ok) {

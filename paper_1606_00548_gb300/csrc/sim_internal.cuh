@@ -54,7 +54,7 @@ struct AmgLevel {
     void *valT = nullptr;        // ELL values in apply precision (float copy for mixed)
     void *dinvT = nullptr;       // 1 / l1 row sums, apply precision
     int *agg = nullptr;          // fine -> next level
-    int *mem4 = nullptr;         // next-level aggregate -> 4 members [4][n_next]
+    int *moff = nullptr, *mem = nullptr;   // members of each next-level aggregate, ascending (CSR)
     void *f = nullptr, *e = nullptr, *e2 = nullptr;   // V-cycle vectors (apply precision)
     void *coarse_inv = nullptr;  // coarsest: dense inverse, row-major n*n (apply precision)
 };
@@ -115,7 +115,8 @@ struct sim {
     void *zr = nullptr;          // [b][N]
     std::vector<AmgLevel> lev;
     // AMG setup scratch
-    int *partner = nullptr, *pick = nullptr, *aggA = nullptr, *memA = nullptr, *aggB = nullptr, *memB = nullptr;
+    int *partner = nullptr, *pick = nullptr, *host = nullptr, *flag = nullptr, *cnt = nullptr;
+    int *aggA = nullptr, *moffA = nullptr, *memA = nullptr, *aggB = nullptr, *moffB = nullptr, *memB = nullptr;
     int *scan = nullptr, *iscal = nullptr;
     int *tcol = nullptr; double *tval = nullptr;   // intermediate (pass-1) matrix
     int tcap = 0;

@@ -7,7 +7,8 @@
 * the pairwise matching equals the sequential greedy matching on the same
   total order of edges (the handshake fixed point), brute force on small
   graphs;
-* each coarse AMG operator is the Galerkin product P^T A P;
+* each coarse AMG operator is the Galerkin product P^T A P, and every
+  member of an aggregate is coupled to another member;
 * quasi-IMPES decoupling removes the saturation columns of the pressure
   row of every diagonal block;
 * red-black block ILU(0): (D + L) D^-1 (D + U) reproduces the decoupled
@@ -163,7 +164,13 @@ def test_amg_galerkin_and_qi(oracle_lib, name, case, dt):
         Cm = sp.csr_matrix((Cl["val"], Cl["col"], Cl["rowptr"]), shape=(Cl["n"], Cl["n"])).toarray()
         assert np.abs(Ac - Cm).max() <= 1e-12 * np.abs(Ac).max()
         sizes = np.bincount(L["agg"], minlength=Cl["n"])
-        assert sizes.min() >= 1 and sizes.max() <= 4
+        assert sizes.min() >= 1
+        # every member of a multi-node aggregate couples (negatively) to another member
+        Ad = A.toarray()
+        for I in np.nonzero(sizes > 1)[0]:
+            mem = np.nonzero(L["agg"] == I)[0]
+            sub = Ad[np.ix_(mem, mem)] - np.diag(np.diag(Ad[np.ix_(mem, mem)]))
+            assert ((sub < 0).any(axis=1)).all()
     # quasi-IMPES: pressure row of each decoupled diagonal block has no saturation columns
     J = o.jacobian()
     w, ap = o.qi()
