@@ -195,6 +195,35 @@ sim_status sim_well_rates(sim_t *s, double *q3);
 sim_status sim_get_stats(sim_t *s, sim_stats *st);
 int32_t sim_block_size(sim_t *s);
 
+/* CNV convergence measure for callers that cannot allocate device memory.
+   The paper has no counterpart: this is a deployment aid, not part of the
+   method.  Some callers cannot call cudaMalloc -- their device memory belongs
+   to another allocator (a framework's caching allocator or a fixed, pre-sized
+   arena), or they run a time-critical Newton loop where an allocation's
+   latency and the device synchronisation it may imply are not acceptable.
+   This entry point needs no handle and allocates nothing: it computes the
+   same quantity as sim_cnv, max_i,c |R_c(i)| dt / (poro_i dx dy dz cnv_rho_c),
+   from buffers the caller owns.
+     R_dev     device, b*N doubles, component-major residual (kg/day)
+     poro_dev  device, N doubles, porosity at the reference pressure
+     cnv_rho   host, b doubles (> 0), per-component density scale
+     cnv_dev   device, 1 double: receives the result (NaN if any R is NaN)
+     cuda_stream  cudaStream_t or NULL; the call is asynchronous on it.
+   Scratch: a library-owned static device array of 609 doubles (per-block
+   partial maxima plus a ticket word), held by every GPU that loads the
+   library until the process exits; no cudaMalloc / cudaFree is ever made.
+   The first call on a device looks up that array's device address
+   (cudaGetSymbolAddress) with the device current; make that first call
+   before any stream capture.  All calls share the array and it keeps the
+   last call's contents (the ticket is cleared by each call): calls that
+   overlap on the GPU (other streams, other threads) race and must not
+   overlap.  Limits: b in {2, 3}; N*b < 2^31 (32-bit indexing), larger
+   grids fail with SIM_ELIMIT.  Errors are reported through the return code
+   and sim_last_error(NULL). */
+sim_status sim_cnv_noalloc(int32_t nx, int32_t ny, int32_t nz, double dx, double dy, double dz, int32_t b,
+                           const double *R_dev, const double *poro_dev, const double *cnv_rho, double dt,
+                           double *cnv_dev, void *cuda_stream);
+
 const char *sim_last_error(sim_t *s);   /* s may be NULL: last create error */
 void sim_clear_error(sim_t *s);
 

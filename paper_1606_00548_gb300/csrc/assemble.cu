@@ -14,6 +14,8 @@
 // One thread per cell writes only its own rows, so no atomics are needed;
 // each face flux is evaluated by both of its cells in the same canonical
 // (L, R) orientation, so the two contributions cancel exactly.
+#include <mutex>
+
 #include "sim_internal.cuh"
 
 namespace {
@@ -682,5 +684,85 @@ sim_status k_finite(sim_t *s, const double *v, long n, int *ok) {
     SIM_CK(s, cudaMemcpyAsync(s->h_pinned, s->scal, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     SIM_CK(s, cudaStreamSynchronize(s->stream));
     *ok = s->h_pinned[0] == 0.0;
+    return SIM_OK;
+}
+
+// ===========================================================================
+// CNV without device allocation (sim_cnv_noalloc)
+//
+// Scratch: the per-block partial maxima and the last-block ticket live in a
+// file-scope device array of NOALLOC_SCRATCH doubles (2.4 KB), held by every
+// GPU that loads the library until the process exits.  Host code never uses
+// the array's name as a pointer (on the host it is only a stand-in): the
+// device address is fetched once per device with cudaGetSymbolAddress.
+// ===========================================================================
+namespace {
+constexpr int NOALLOC_SCRATCH = SIM_RED_BLOCKS + 1;   // partials + ticket word
+static __device__ __align__(256) double g_cnv_scratch[NOALLOC_SCRATCH];
+
+template <int B>
+__global__ void cnv_noalloc_kernel(GridDesc g, const double *__restrict__ R, const double *__restrict__ poro, double dt,
+                                   double r0, double r1, double r2, double *scratch, double *out) {
+    const int N = g.N;
+    const double vol = g.dx * g.dy * g.dz;
+    const double rho[3] = {r0, r1, r2};
+    double m = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        const double pv0 = poro[i] * vol;
+#pragma unroll
+        for (int c = 0; c < B; c++) m = nanmax(m, fabs(R[c * N + i]) * dt / (pv0 * rho[c]));
+    }
+    m = block_reduce<1>(m);
+    if (threadIdx.x == 0) scratch[blockIdx.x] = m;
+    finish_grid<1>(scratch, 1, (unsigned int *)(scratch + SIM_RED_BLOCKS), out);
+}
+}  // namespace
+
+static std::mutex g_noalloc_mutex;
+static double *g_noalloc_addr[256];   // device address of g_cnv_scratch, per device ordinal
+
+extern "C" sim_status sim_cnv_noalloc(int32_t nx, int32_t ny, int32_t nz, double dx, double dy, double dz, int32_t b,
+                                      const double *R_dev, const double *poro_dev, const double *cnv_rho, double dt,
+                                      double *cnv_dev, void *cuda_stream) {
+    if (!R_dev || !poro_dev || !cnv_rho || !cnv_dev) return sim_fail(nullptr, SIM_EINVAL, "sim_cnv_noalloc: NULL pointer");
+    if (nx < 1 || ny < 1 || nz < 1 || !(dx > 0 && dy > 0 && dz > 0) || !(dt > 0) || (b != 2 && b != 3))
+        return sim_fail(nullptr, SIM_EINVAL, "sim_cnv_noalloc: bad grid, block size or dt");
+    for (int c = 0; c < b; c++)
+        if (!(cnv_rho[c] > 0)) return sim_fail(nullptr, SIM_EINVAL, "sim_cnv_noalloc: cnv_rho must be positive");
+    const long long N = (long long)nx * ny * nz;
+    if (N * b > 0x7fffffffLL)
+        return sim_fail(nullptr, SIM_ELIMIT, "sim_cnv_noalloc: N*b must stay below 2^31 (32-bit indexing)");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return sim_fail(nullptr, SIM_ECUDA, std::string("sim_cnv_noalloc: ") + cudaGetErrorString(e));
+    if (dev < 0 || dev >= 256) return sim_fail(nullptr, SIM_ELIMIT, "sim_cnv_noalloc: device ordinal above 255");
+    double *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_addr[dev]) {
+            e = cudaGetSymbolAddress((void **)&g_noalloc_addr[dev], g_cnv_scratch);
+            if (e != cudaSuccess) {
+                g_noalloc_addr[dev] = nullptr;
+                return sim_fail(nullptr, SIM_ECUDA, std::string("sim_cnv_noalloc: cudaGetSymbolAddress: ") +
+                                                        cudaGetErrorString(e));
+            }
+        }
+        scratch = g_noalloc_addr[dev];
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    // the ticket must start at zero; the partials are overwritten before use
+    e = cudaMemsetAsync(scratch + SIM_RED_BLOCKS, 0, sizeof(double), st);
+    if (e != cudaSuccess) return sim_fail(nullptr, SIM_ECUDA, std::string("sim_cnv_noalloc: ") + cudaGetErrorString(e));
+    GridDesc g;
+    g.nx = nx; g.ny = ny; g.nz = nz; g.N = (int)N; g.dx = dx; g.dy = dy; g.dz = dz; g.top = 0.0;
+    const double r2 = b == 3 ? cnv_rho[2] : 1.0;
+    if (b == 2)
+        cnv_noalloc_kernel<2><<<SIM_RED_BLOCKS, SIM_THREADS, 0, st>>>(g, R_dev, poro_dev, dt, cnv_rho[0], cnv_rho[1], r2,
+                                                                     scratch, cnv_dev);
+    else
+        cnv_noalloc_kernel<3><<<SIM_RED_BLOCKS, SIM_THREADS, 0, st>>>(g, R_dev, poro_dev, dt, cnv_rho[0], cnv_rho[1], r2,
+                                                                     scratch, cnv_dev);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return sim_fail(nullptr, SIM_ECUDA, std::string("sim_cnv_noalloc: ") + cudaGetErrorString(e));
     return SIM_OK;
 }

@@ -121,6 +121,8 @@ _SIGS = {
     "sim_well_rates": ([_vp, _dp], C.c_int),
     "sim_get_stats": ([_vp, C.POINTER(sim_stats)], C.c_int),
     "sim_block_size": ([_vp], C.c_int32),
+    "sim_cnv_noalloc": ([C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double, C.c_int32,
+                         _vp, _vp, _dp, C.c_double, _vp, _vp], C.c_int),
     "sim_last_error": ([_vp], C.c_char_p),
     "sim_clear_error": ([_vp], None),
 }
@@ -351,3 +353,13 @@ class Simulator:
 
     def stats(self):
         s = sim_stats(); _check(self.h, self.L.sim_get_stats(self.h, C.byref(s))); return s
+
+
+def sim_cnv_noalloc(case: dict, b: int, R_dev, poro_dev, dt: float, out_dev, stream=None) -> None:
+    """CNV of a residual held in caller-owned device tensors, without any device
+    allocation inside the library (see include/sim.h)."""
+    L = load()
+    rho, rp = _d(case["cnv_rho"][:b])
+    st = L.sim_cnv_noalloc(case["nx"], case["ny"], case["nz"], case["dx"], case["dy"], case["dz"], b,
+                           _ptr(R_dev), _ptr(poro_dev), rp, float(dt), _ptr(out_dev), _vp(stream) if stream else None)
+    _check(None, st)
