@@ -542,37 +542,51 @@ __global__ void restrict_p_kernel(int N, const double *__restrict__ r, const T *
     e0[i] = t * dinv0[i];
 }
 
-// f_c = P^T (f - A e) ; e_c = f_c / l1 (pre-smoothing on the coarse level)
+// r = f - A e (one thread per fine row: coalesced stencil / ELL reads)
 template <typename T>
-__global__ void resid_restrict_kernel(Mat<T> A, const T *__restrict__ f, const T *__restrict__ e, const int *__restrict__ moff,
-                                      const int *__restrict__ mem, int nc, T *__restrict__ fc, T *__restrict__ ec,
-                                      const T *__restrict__ dinvc, const int *done) {
-    if (skip(done)) return;
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
-    if (I >= nc) return;
-    T s = (T)0;
-    for (int q = moff[I]; q < moff[I + 1]; q++) {
-        const int m = mem[q];
-        T t = (T)0;
-        for_row(A, m, [&](int j, T v) { t += v * e[j]; });
-        s += f[m] - t;
-    }
-    fc[I] = s;
-    if (ec) ec[I] = s * dinvc[I];
-}
-
-// e2 = ep + (f - A ep) / l1 with ep = e + P e_c  (prolongation + post-smoothing)
-template <typename T>
-__global__ void prolong_smooth_kernel(Mat<T> A, const T *__restrict__ f, const T *__restrict__ e, const T *__restrict__ ec,
-                                      const int *__restrict__ agg, const T *__restrict__ dinv, T *__restrict__ e2,
-                                      const int *done) {
+__global__ void amg_resid_kernel(Mat<T> A, const T *__restrict__ f, const T *__restrict__ e, T *__restrict__ r,
+                                 const int *done) {
     if (skip(done)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= A.n) return;
     T t = (T)0;
-    for_row(A, i, [&](int j, T v) { t += v * (e[j] + ec[agg[j]]); });
-    const T ep = e[i] + ec[agg[i]];
-    e2[i] = ep + (f[i] - t) * dinv[i];
+    for_row(A, i, [&](int j, T v) { t += v * e[j]; });
+    r[i] = f[i] - t;
+}
+
+// f_c = P^T r (members in ascending order); e_c = f_c / l1 (coarse pre-smoothing)
+template <typename T>
+__global__ void amg_restrict_kernel(const T *__restrict__ r, const int *__restrict__ moff, const int *__restrict__ mem,
+                                    int nc, T *__restrict__ fc, T *__restrict__ ec, const T *__restrict__ dinvc,
+                                    const int *done) {
+    if (skip(done)) return;
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc) return;
+    T s = (T)0;
+    for (int q = moff[I]; q < moff[I + 1]; q++) s += r[mem[q]];
+    fc[I] = s;
+    if (ec) ec[I] = s * dinvc[I];
+}
+
+// e += P e_c
+template <typename T>
+__global__ void amg_prolong_kernel(int n, const int *__restrict__ agg, const T *__restrict__ ec, T *__restrict__ e,
+                                   const int *done) {
+    if (skip(done)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) e[i] += ec[agg[i]];
+}
+
+// e2 = e + (f - A e) / l1 (post-smoothing)
+template <typename T>
+__global__ void amg_smooth_kernel(Mat<T> A, const T *__restrict__ f, const T *__restrict__ e, const T *__restrict__ dinv,
+                                  T *__restrict__ e2, const int *done) {
+    if (skip(done)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.n) return;
+    T t = (T)0;
+    for_row(A, i, [&](int j, T v) { t += v * e[j]; });
+    e2[i] = e[i] + (f[i] - t) * dinv[i];
 }
 
 // e = Inv f on the coarsest level: one warp per row
@@ -982,25 +996,31 @@ sim_status cpr_setup(sim_t *s) {
 template <typename T>
 static sim_status vcycle(sim_t *s, const int *done) {
     const int nl = (int)s->lev.size();
-    // down: f_{l+1} = P^T (f_l - A_l e_l), e_{l+1} = f_{l+1} / l1 (not on the coarsest)
+    // down: r = f - A e; f_{l+1} = P^T r; e_{l+1} = f_{l+1} / l1 (not on the coarsest)
     for (int l = 0; l + 1 < nl; l++) {
         AmgLevel &L = s->lev[l], &C = s->lev[l + 1];
         const bool coarsest = (l + 1 == nl - 1);
-        resid_restrict_kernel<T><<<sim_blocks(C.n), SIM_THREADS, 0, s->stream>>>(
-            level_matT<T>(s, L, l), (const T *)L.f, (const T *)L.e, L.moff, L.mem, C.n, (T *)C.f,
-            coarsest ? nullptr : (T *)C.e, (const T *)C.dinvT, done);
+        amg_resid_kernel<T><<<sim_blocks(L.n, 128), 128, 0, s->stream>>>(level_matT<T>(s, L, l), (const T *)L.f,
+                                                                        (const T *)L.e, (T *)L.e2, done);
+        SIM_LAUNCHED(s);
+        amg_restrict_kernel<T><<<sim_blocks(C.n, 128), 128, 0, s->stream>>>((const T *)L.e2, L.moff, L.mem, C.n, (T *)C.f,
+                                                                           coarsest ? nullptr : (T *)C.e,
+                                                                           (const T *)C.dinvT, done);
         SIM_LAUNCHED(s);
     }
     AmgLevel &Cn = s->lev[nl - 1];
     coarse_solve_kernel<T><<<sim_blocks((long)Cn.n * 32), SIM_THREADS, 0, s->stream>>>(Cn.n, (const T *)Cn.coarse_inv,
                                                                                     (const T *)Cn.f, (T *)Cn.e, done);
     SIM_LAUNCHED(s);
-    // up: e_l <- smooth(e_l + P e_{l+1})
+    // up: e_l += P e_{l+1}; e2_l = smooth(e_l); the corrected vector of level l is e2_l
     for (int l = nl - 2; l >= 0; l--) {
         AmgLevel &L = s->lev[l], &C = s->lev[l + 1];
         const T *ec = (l + 1 == nl - 1) ? (const T *)C.e : (const T *)C.e2;
-        prolong_smooth_kernel<T><<<sim_blocks(L.n), SIM_THREADS, 0, s->stream>>>(
-            level_matT<T>(s, L, l), (const T *)L.f, (const T *)L.e, ec, L.agg, (const T *)L.dinvT, (T *)L.e2, done);
+        amg_prolong_kernel<T><<<sim_blocks(L.n, 128), 128, 0, s->stream>>>(L.n, L.agg, ec, (T *)L.e, done);
+        SIM_LAUNCHED(s);
+        amg_smooth_kernel<T><<<sim_blocks(L.n, 128), 128, 0, s->stream>>>(level_matT<T>(s, L, l), (const T *)L.f,
+                                                                         (const T *)L.e, (const T *)L.dinvT, (T *)L.e2,
+                                                                         done);
         SIM_LAUNCHED(s);
     }
     return SIM_OK;

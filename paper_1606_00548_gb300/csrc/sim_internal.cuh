@@ -12,7 +12,7 @@
 #define SIM_MAX_PVT 64
 #define SIM_MAX_M 32
 #define SIM_MAX_ELL 128      // widest coarse AMG row the setup kernels accept
-#define SIM_RED_BLOCKS 304   // 2 x 152 SMs: grid of the reduction kernels
+#define SIM_RED_BLOCKS 608   // 4 x 152 SMs: grid of the reduction kernels
 #define SIM_THREADS 256
 
 // fluid and rock constants, passed by value as a kernel parameter (about
