@@ -31,15 +31,19 @@ METRIC = "Newton cell-iters/s"
 UNIT = "cell-iters/s"
 
 
-def workload(name: str):
+def workload(name: str, **solver):
     from paper_1606_00548_gb300 import synth
     if name == "bo100":
-        return synth.black_oil_100x100x20(), "black-oil 100x100x20 (200k cells, 3x3 blocks), 10-day steps"
+        return synth.black_oil_100x100x20(**solver), "black-oil 100x100x20 (200k cells, 3x3 blocks), 10-day steps"
     if name == "bo200":
-        return synth.black_oil_400cube(n=200), "black-oil 200^3 (8M cells), 10-day steps"
+        return synth.black_oil_400cube(n=200, **solver), "black-oil 200^3 (8M cells), 10-day steps"
     if name == "bo400":
-        return synth.black_oil_400cube(n=400), "black-oil 400^3 (64M cells), 10-day steps"
+        return synth.black_oil_400cube(n=400, **solver), "black-oil 400^3 (64M cells), 10-day steps"
     raise SystemExit(f"unknown workload {name}")
+
+
+def solver_overrides(args):
+    return {} if args.amg_cycles is None else {"amg_cycles": args.amg_cycles}
 
 
 class ClockSampler:
@@ -146,7 +150,7 @@ def run_reference(args):
     ws, rank = dist_info()
     if rank != 0:
         return 0
-    case, desc = workload(args.workload)
+    case, desc = workload(args.workload, **solver_overrides(args))
     N = case["nx"] * case["ny"] * case["nz"]
     import oracle
     oracle.build()
@@ -188,7 +192,7 @@ def run_ours(args):
     build.build()
     from paper_1606_00548_gb300.sim import Simulator
 
-    case, desc = workload(args.workload)
+    case, desc = workload(args.workload, **solver_overrides(args))
     N = case["nx"] * case["ny"] * case["nz"]
     prec = 1 if args.precision == "mixed" else 0
     stream = torch.cuda.Stream()
@@ -262,6 +266,30 @@ def run_ours(args):
         s1.record(stream)
     torch.cuda.synchronize()
     t_spmv = s0.elapsed_time(s1) / 1e3 / reps
+    # breakdown at the current Newton system: preconditioner apply and one full solve
+    sim.assemble(dt_of(k))
+    sim.precond_setup()
+    z = torch.empty_like(x)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            sim.precond_apply(x, z)
+        torch.cuda.synchronize()
+        s0.record(stream)
+        for _ in range(reps):
+            sim.precond_apply(x, z)
+        s1.record(stream)
+    torch.cuda.synchronize()
+    t_prec = s0.elapsed_time(s1) / 1e3 / reps
+    rhs = torch.randn(N * b, dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(stream):
+        s0.record(stream)
+        _, li = sim.linear_solve(rhs, z)
+        s1.record(stream)
+    torch.cuda.synchronize()
+    t_solve = s0.elapsed_time(s1) / 1e3
+    breakdown = {"spmv_us": t_spmv * 1e6, "precond_apply_us": t_prec * 1e6,
+                 "solve_ms": t_solve * 1e3, "solve_iterations": li.iterations,
+                 "us_per_iteration": t_solve * 1e6 / max(1, li.iterations)}
     bytes_spmv = (7 * b * b + 2 * b) * 8 * N
     peaks = {}
     try:
@@ -286,7 +314,8 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else "f64+f32",
             "data": "synthetic",
             "config": {"workload": desc, "precision": args.precision,
-                       "solver": "CPR(QI, aggregation AMG V(1,1), red-black block ILU0) FGMRES(30), theta 1e-8",
+                       "solver": f"CPR(QI, aggregation AMG {case['solver']['amg_cycles']}x V(1,1), "
+                                 "red-black block ILU0) FGMRES(30), theta 1e-8",
                        "newton_iterations": newton, "linear_iterations": lin, "cuts": cuts,
                        "l2": "working set (J 101 MB + Krylov basis 149 MB + ...) larger than L2"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
@@ -297,6 +326,7 @@ def run_ours(args):
                          "peak_source": peak_src, "bytes_per_cell": (7 * b * b + 2 * b) * 8,
                          "launch_us": t_spmv * 1e6},
             "clocks": clocks,
+            "breakdown": breakdown,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -314,6 +344,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--workload", default="bo100", choices=["bo100", "bo200", "bo400"])
+    ap.add_argument("--amg-cycles", type=int, default=None, help="V-cycles per CPR pressure stage")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -110,6 +110,8 @@ typedef struct {
     double chop_ds, chop_dp;    /* Appleyard chop limits */
     int32_t max_cuts;           /* time-step halvings per sim_step */
     int32_t precision;          /* SIM_PRECISION_* */
+    int32_t amg_cycles;         /* V-cycles per stage-P application (>= 1) */
+    int32_t graphs;             /* 1: replay each FGMRES restart cycle as a CUDA graph */
 } sim_options;
 
 typedef struct {

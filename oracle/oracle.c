@@ -949,8 +949,15 @@ void ora_precond_apply(ora_sim *s, const double *r, double *z) {
         rh[i * b] = t;
         fp[i] = t;
     }
-    /* stage P: one AMG V-cycle on the pressure block */
+    /* stage P: AMG V-cycles on the pressure block, each on the residual left by the previous ones */
     vcycle(s, 0, fp, ep);
+    for (int c = 1; c < in->amg_cycles; c++) {
+        level_t *L0 = &s->lev[0];
+        double *rp = L0->t2, *dp = L0->t3;
+        csr_residual(L0, fp, ep, rp);
+        vcycle(s, 0, rp, dp);
+        for (int i = 0; i < N; i++) ep[i] += dp[i];
+    }
     /* residual of the decoupled system after stage P (pressure columns only) */
     for (int i = 0; i < N; i++) {
         for (int c = 0; c < b; c++) {

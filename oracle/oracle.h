@@ -55,6 +55,7 @@ typedef struct {
     int32_t stage2;                /* CPR second stage: 0 block-Jacobi, 1 red-black block ILU(0) */
     double amg_theta; int32_t amg_rounds, amg_coarse_max, amg_max_levels;
     double chop_ds, chop_dp; int32_t max_cuts;
+    int32_t amg_cycles;            /* V-cycles per stage-P application (>= 1) */
 } ora_input;
 
 typedef struct {

@@ -29,9 +29,21 @@ constexpr int MAXE = SIM_MAX_ELL;
 
 __device__ __forceinline__ bool skip(const int *done) { return done != nullptr && *(volatile const int *)done; }
 
-// stencil neighbours in ascending column order: -z, -y, -x, centre, +x, +y, +z
-__device__ __constant__ int kAscend[7] = {5, 3, 1, 0, 2, 4, 6};
-
+struct Cell { int i, ix, iy, iz; };
+__device__ __forceinline__ Cell cell_of(const GridDesc &g, int i) {
+    Cell c; c.i = i; c.ix = i % g.nx; const int t = i / g.nx; c.iy = t % g.ny; c.iz = t / g.ny; return c;
+}
+__device__ __forceinline__ int nbrc(const GridDesc &g, const Cell &c, int d) {
+    switch (d) {
+    case 0: return c.i;
+    case 1: return c.ix > 0 ? c.i - 1 : -1;
+    case 2: return c.ix < g.nx - 1 ? c.i + 1 : -1;
+    case 3: return c.iy > 0 ? c.i - g.nx : -1;
+    case 4: return c.iy < g.ny - 1 ? c.i + g.nx : -1;
+    case 5: return c.iz > 0 ? c.i - g.nx * g.ny : -1;
+    default: return c.iz < g.nz - 1 ? c.i + g.nx * g.ny : -1;
+    }
+}
 __device__ __forceinline__ int nbr7(const GridDesc &g, int i, int d) {
     const int ix = i % g.nx, t = i / g.nx, iy = t % g.ny, iz = t / g.ny;
     switch (d) {
@@ -54,6 +66,7 @@ __device__ __forceinline__ bool is_black(const GridDesc &g, int i) {
 template <typename V>
 struct Mat {
     bool st;
+    bool selfpad;    // ELL padded with (self column, 0) instead of -1: no early exit
     GridDesc g;      // structured
     const V *val;    // structured: [7][n]; ELL: [width][n]
     const int *col;  // ELL
@@ -61,15 +74,23 @@ struct Mat {
 };
 
 // visit the entries of row i in ascending column order: f(col, val)
+// (self-padded ELL rows end with zero entries on the diagonal column)
 template <typename V, typename F>
 __device__ __forceinline__ void for_row(const Mat<V> &A, int i, F f) {
     if (A.st) {
-#pragma unroll
-        for (int t = 0; t < 7; t++) {
-            const int d = kAscend[t];
-            const int j = nbr7(A.g, i, d);
-            if (j >= 0) f(j, A.val[(long)d * A.n + i]);
-        }
+        const int nx = A.g.nx, ny = A.g.ny, nxy = nx * ny;
+        const int ix = i % nx, t = i / nx, iy = t % ny, iz = t / ny;
+        const long n = A.n;
+        if (iz > 0) f(i - nxy, A.val[5 * n + i]);
+        if (iy > 0) f(i - nx, A.val[3 * n + i]);
+        if (ix > 0) f(i - 1, A.val[1 * n + i]);
+        f(i, A.val[i]);
+        if (ix < nx - 1) f(i + 1, A.val[2 * n + i]);
+        if (iy < ny - 1) f(i + nx, A.val[4 * n + i]);
+        if (iz < A.g.nz - 1) f(i + nxy, A.val[6 * n + i]);
+    } else if (A.selfpad) {
+#pragma unroll 4
+        for (int k = 0; k < A.width; k++) f(A.col[(long)k * A.n + i], A.val[(long)k * A.n + i]);
     } else {
         for (int k = 0; k < A.width; k++) {
             const int j = A.col[(long)k * A.n + i];
@@ -77,6 +98,14 @@ __device__ __forceinline__ void for_row(const Mat<V> &A, int i, F f) {
             f(j, A.val[(long)k * A.n + i]);
         }
     }
+}
+
+__global__ void selfpad_kernel(int n, int W, const int *__restrict__ col, int *__restrict__ colA) {
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= (long)n * W) return;
+    const int i = (int)(t % n);
+    const int c = col[t];
+    colA[t] = c < 0 ? i : c;
 }
 
 // ---------------------------------------------------------------------------
@@ -466,65 +495,33 @@ __global__ void l1_kernel(Mat<double> A, T *__restrict__ dinv) {
     dinv[i] = (T)(1.0 / s);
 }
 
-__global__ void dense_kernel(Mat<double> A, double *__restrict__ D) {
+// Gauss-Jordan step k without pivoting on the augmented [A | Inv] (n x 2n),
+// read from src and written to dst: the coarse pressure block is
+// diagonally dominant with a positive diagonal, so the pivots stay positive.
+__global__ void gj_step_kernel(int n, int k, const double *__restrict__ src, double *__restrict__ dst) {
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    const long w = 2L * n;
+    if (t >= (long)n * w) return;
+    const int i = (int)(t / w), j = (int)(t % w);
+    const double piv = src[(long)k * w + k];
+    const double pk = src[(long)k * w + j] / piv;
+    dst[t] = (i == k) ? pk : src[t] - src[(long)i * w + k] * pk;
+}
+
+__global__ void gj_init_kernel(Mat<double> A, double *__restrict__ aug) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= A.n) return;
-    for_row(A, i, [&](int j, double a) { D[(long)i * A.n + j] += a; });
+    const long w = 2L * A.n;
+    for (int j = 0; j < 2 * A.n; j++) aug[i * w + j] = (j - A.n == i) ? 1.0 : 0.0;
+    for_row(A, i, [&](int j, double a) { aug[i * w + j] += a; });
 }
 
-__global__ void identity_kernel(int n, double *__restrict__ I) {
-    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (t < (long)n * n) I[t] = ((t / n) == (t % n)) ? 1.0 : 0.0;
-}
-
-// Gauss-Jordan step k with partial pivoting (one block): pick the pivot row,
-// swap, scale the pivot row, and keep the column multipliers in f
-__global__ void gj_pivot_kernel(int n, int k, double *__restrict__ A, double *__restrict__ Inv, double *__restrict__ f) {
-    __shared__ double bv[1024];
-    __shared__ int bi[1024];
-    __shared__ double piv;
-    double best = -1.0;
-    int arg = k;
-    for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
-        const double v = fabs(A[(long)i * n + k]);
-        if (v > best) { best = v; arg = i; }
-    }
-    bv[threadIdx.x] = best; bi[threadIdx.x] = arg;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) {
-            const double o = bv[threadIdx.x + s];
-            const int oi = bi[threadIdx.x + s];
-            if (o > bv[threadIdx.x] || (o == bv[threadIdx.x] && oi < bi[threadIdx.x])) { bv[threadIdx.x] = o; bi[threadIdx.x] = oi; }
-        }
-        __syncthreads();
-    }
-    const int p = bi[0];
-    if (p != k)
-        for (int j = threadIdx.x; j < n; j += blockDim.x) {
-            double t = A[(long)k * n + j]; A[(long)k * n + j] = A[(long)p * n + j]; A[(long)p * n + j] = t;
-            t = Inv[(long)k * n + j]; Inv[(long)k * n + j] = Inv[(long)p * n + j]; Inv[(long)p * n + j] = t;
-        }
-    __syncthreads();
-    if (threadIdx.x == 0) piv = A[(long)k * n + k];
-    __syncthreads();
-    const double ip = 1.0 / piv;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) f[i] = A[(long)i * n + k];
-    __syncthreads();
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        A[(long)k * n + j] *= ip;
-        Inv[(long)k * n + j] *= ip;
-    }
-}
-
-__global__ void gj_elim_kernel(int n, int k, double *__restrict__ A, double *__restrict__ Inv, const double *__restrict__ f) {
+template <typename T>
+__global__ void gj_extract_kernel(int n, const double *__restrict__ aug, T *__restrict__ inv) {
     const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (t >= (long)n * n) return;
     const int i = (int)(t / n), j = (int)(t % n);
-    if (i == k) return;
-    const double fi = f[i];
-    if (j >= k) A[(long)i * n + j] -= fi * A[(long)k * n + j];
-    Inv[(long)i * n + j] -= fi * Inv[(long)k * n + j];
+    inv[t] = (T)aug[(long)i * 2 * n + n + j];
 }
 
 // ---------------------------------------------------------------------------
@@ -589,6 +586,28 @@ __global__ void amg_smooth_kernel(Mat<T> A, const T *__restrict__ f, const T *__
     e2[i] = e[i] + (f[i] - t) * dinv[i];
 }
 
+// next stage-P cycle: f0 = rp - A_p ep; e0 = f0 / l1
+template <typename T>
+__global__ void cycle_next_kernel(Mat<T> A, const T *__restrict__ rp, const T *__restrict__ ep, const T *__restrict__ dinv,
+                                  T *__restrict__ f0, T *__restrict__ e0, const int *done) {
+    if (skip(done)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.n) return;
+    T t = (T)0;
+    for_row(A, i, [&](int j, T v) { t += v * ep[j]; });
+    const T f = rp[i] - t;
+    f0[i] = f;
+    e0[i] = f * dinv[i];
+}
+
+// y = x (mode 0) or y += x (mode 1)
+template <typename T>
+__global__ void copy_add_kernel(int n, const T *__restrict__ x, T *__restrict__ y, int mode, const int *done) {
+    if (skip(done)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = mode ? y[i] + x[i] : x[i];
+}
+
 // e = Inv f on the coarsest level: one warp per row
 template <typename T>
 __global__ void coarse_solve_kernel(int n, const T *__restrict__ Inv, const T *__restrict__ f, T *__restrict__ e,
@@ -617,9 +636,10 @@ __global__ void stage2_a_kernel(GridDesc g, const double *__restrict__ r, const 
     T rp = v[0] + wT[(long)N + i] * v[1];
     if (B == 3) rp += wT[2L * N + i] * v[2];
     v[0] = rp;
+    const Cell cc = cell_of(g, i);
 #pragma unroll
     for (int d = 0; d < 7; d++) {
-        const int j = nbr7(g, i, d);
+        const int j = nbrc(g, cc, d);
         if (j < 0) continue;
         const T e = ep[j];
 #pragma unroll
@@ -647,13 +667,15 @@ __global__ void stage2_b_kernel(GridDesc g, const T *__restrict__ ahat, const T 
     if (skip(done)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int N = g.N;
-    if (i >= N || !is_black(g, i)) return;
+    if (i >= N) return;
+    const Cell cc = cell_of(g, i);
+    if (((cc.ix + cc.iy + cc.iz) & 1) == 0) return;
     T t[B];
 #pragma unroll
     for (int c = 0; c < B; c++) t[c] = r2[(long)c * N + i];
 #pragma unroll
     for (int d = 1; d < 7; d++) {
-        const int k = nbr7(g, i, d);
+        const int k = nbrc(g, cc, d);
         if (k < 0) continue;
         T zk[B];
 #pragma unroll
@@ -690,13 +712,14 @@ __global__ void stage2_c_kernel(GridDesc g, const T *__restrict__ ahat, const T 
         }
         return;
     }
-    if (is_black(g, i)) return;
+    const Cell cc = cell_of(g, i);
+    if ((cc.ix + cc.iy + cc.iz) & 1) return;
     T t[B];
 #pragma unroll
     for (int c = 0; c < B; c++) t[c] = (T)0;
 #pragma unroll
     for (int d = 1; d < 7; d++) {
-        const int k = nbr7(g, i, d);
+        const int k = nbrc(g, cc, d);
         if (k < 0) continue;
         T zk[B];
 #pragma unroll
@@ -757,7 +780,7 @@ static void dev_free_async(sim_t *s, void *p) { if (p) cudaFreeAsync(p, s->strea
 static void free_level(sim_t *s, AmgLevel &L) {
     // valT may alias the FP64 values or the level-0 stencil owned by the handle
     if (L.valT != (void *)L.val && L.valT != s->apT) dev_free_async(s, L.valT);
-    dev_free_async(s, L.col); dev_free_async(s, L.val); dev_free_async(s, L.dinvT);
+    dev_free_async(s, L.col); dev_free_async(s, L.colA); dev_free_async(s, L.val); dev_free_async(s, L.dinvT);
     dev_free_async(s, L.agg); dev_free_async(s, L.moff); dev_free_async(s, L.mem); dev_free_async(s, L.f); dev_free_async(s, L.e);
     dev_free_async(s, L.e2); dev_free_async(s, L.coarse_inv);
     L = AmgLevel();
@@ -770,7 +793,7 @@ void cpr_free(sim_t *s) {
 
 static Mat<double> level_mat(sim_t *s, const AmgLevel &L, int l) {
     Mat<double> A;
-    A.st = (l == 0); A.g = s->gd; A.n = L.n; A.width = L.width;
+    A.st = (l == 0); A.selfpad = false; A.g = s->gd; A.n = L.n; A.width = L.width;
     A.val = l == 0 ? s->ap : L.val;
     A.col = L.col;
     return A;
@@ -778,9 +801,9 @@ static Mat<double> level_mat(sim_t *s, const AmgLevel &L, int l) {
 template <typename T>
 static Mat<T> level_matT(sim_t *s, const AmgLevel &L, int l) {
     Mat<T> A;
-    A.st = (l == 0); A.g = s->gd; A.n = L.n; A.width = L.width;
+    A.st = (l == 0); A.selfpad = true; A.g = s->gd; A.n = L.n; A.width = L.width;
     A.val = (const T *)L.valT;
-    A.col = L.col;
+    A.col = L.colA;
     return A;
 }
 
@@ -877,6 +900,10 @@ static sim_status finish_levels(sim_t *s) {
         l1_kernel<T><<<sim_blocks(L.n), SIM_THREADS, 0, s->stream>>>(A, (T *)L.dinvT);
         s->launches++;
         if (l > 0) {
+            L.colA = (int *)dev_alloc_async(s, sizeof(int) * (size_t)L.width * L.n);
+            if (!L.colA) return s->err;
+            selfpad_kernel<<<sim_blocks((long)L.width * L.n), SIM_THREADS, 0, s->stream>>>(L.n, L.width, L.col, L.colA);
+            s->launches++;
             if (sizeof(T) == sizeof(double)) {
                 L.valT = L.val;              // FP64 apply reads the setup values
             } else {
@@ -890,24 +917,21 @@ static sim_status finish_levels(sim_t *s) {
     // coarsest: dense Gauss-Jordan inverse in FP64
     AmgLevel &C = s->lev[nl - 1];
     const int n = C.n;
-    double *D = (double *)dev_alloc_async(s, sizeof(double) * (size_t)n * n);
-    double *Inv = (double *)dev_alloc_async(s, sizeof(double) * (size_t)n * n);
-    double *f = (double *)dev_alloc_async(s, sizeof(double) * n);
-    if (!D || !Inv || !f) return s->err;
-    SIM_CK(s, cudaMemsetAsync(D, 0, sizeof(double) * (size_t)n * n, s->stream));
-    dense_kernel<<<sim_blocks(n), SIM_THREADS, 0, s->stream>>>(level_mat(s, C, nl - 1), D);
-    identity_kernel<<<sim_blocks((long)n * n), SIM_THREADS, 0, s->stream>>>(n, Inv);
-    s->launches += 2;
+    const size_t aug = (size_t)n * 2 * n;
+    double *A0 = (double *)dev_alloc_async(s, sizeof(double) * aug);
+    double *A1 = (double *)dev_alloc_async(s, sizeof(double) * aug);
+    if (!A0 || !A1) return s->err;
+    gj_init_kernel<<<sim_blocks(n), SIM_THREADS, 0, s->stream>>>(level_mat(s, C, nl - 1), A0);
+    s->launches++;
     for (int k = 0; k < n; k++) {
-        gj_pivot_kernel<<<1, 1024, 0, s->stream>>>(n, k, D, Inv, f);
-        gj_elim_kernel<<<sim_blocks((long)n * n), SIM_THREADS, 0, s->stream>>>(n, k, D, Inv, f);
-        s->launches += 2;
+        gj_step_kernel<<<sim_blocks((long)aug), SIM_THREADS, 0, s->stream>>>(n, k, (k & 1) ? A1 : A0, (k & 1) ? A0 : A1);
+        s->launches++;
     }
     C.coarse_inv = dev_alloc_async(s, sizeof(T) * (size_t)n * n);
     if (!C.coarse_inv) return s->err;
-    cast_kernel<T><<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(Inv, (T *)C.coarse_inv, (long)n * n);
+    gj_extract_kernel<T><<<sim_blocks((long)n * n), SIM_THREADS, 0, s->stream>>>(n, (n & 1) ? A1 : A0, (T *)C.coarse_inv);
     s->launches++;
-    dev_free_async(s, D); dev_free_async(s, Inv); dev_free_async(s, f);
+    dev_free_async(s, A0); dev_free_async(s, A1);
     SIM_CK(s, cudaGetLastError());
     return SIM_OK;
 }
@@ -929,7 +953,7 @@ static sim_status amg_setup(sim_t *s) {
         int *c1 = nullptr; double *v1 = nullptr;
         const int W1 = galerkin(s, A, s->aggA, s->moffA, s->memA, n1, &c1, &v1);
         if (W1 < 0) return s->err;
-        Mat<double> A1; A1.st = false; A1.g = s->gd; A1.n = n1; A1.width = W1; A1.col = c1; A1.val = v1;
+        Mat<double> A1; A1.st = false; A1.selfpad = false; A1.g = s->gd; A1.n = n1; A1.width = W1; A1.col = c1; A1.val = v1;
         const int n2 = aggregate_pass(s, A1, s->aggB, s->moffB, s->memB);
         if (n2 < 0) return s->err;
         if (4L * n2 > 3L * n) {   // coarsening stalled: this level is the coarsest
@@ -990,6 +1014,7 @@ sim_status cpr_setup(sim_t *s) {
     else st = sim_mixed(s) ? setup_bt<3, float>(s) : setup_bt<3, double>(s);
     if (st != SIM_OK) return st;
     s->precond_ready = true;
+    s->setup_gen++;
     return SIM_OK;
 }
 
@@ -1049,6 +1074,22 @@ static sim_status apply_btz(sim_t *s, const double *r, TZ *z, const int *done) {
         return s->err;
     }
     ep = (const T *)L0.e2;
+    if (s->opt.amg_cycles > 1 && s->lev.size() > 1) {
+        // further cycles on the pressure residual left by the previous ones
+        copy_add_kernel<T><<<sim_blocks(N), SIM_THREADS, 0, s->stream>>>(N, (const T *)L0.f, (T *)s->rpT, 0, done);
+        copy_add_kernel<T><<<sim_blocks(N), SIM_THREADS, 0, s->stream>>>(N, (const T *)L0.e2, (T *)s->epacc, 0, done);
+        SIM_LAUNCHED(s);
+        for (int c = 1; c < s->opt.amg_cycles; c++) {
+            cycle_next_kernel<T><<<sim_blocks(N, 128), 128, 0, s->stream>>>(level_matT<T>(s, L0, 0), (const T *)s->rpT,
+                                                                           (const T *)s->epacc, (const T *)L0.dinvT,
+                                                                           (T *)L0.f, (T *)L0.e, done);
+            SIM_LAUNCHED(s);
+            if (vcycle<T>(s, done) != SIM_OK) return s->err;
+            copy_add_kernel<T><<<sim_blocks(N), SIM_THREADS, 0, s->stream>>>(N, (const T *)L0.e2, (T *)s->epacc, 1, done);
+            SIM_LAUNCHED(s);
+        }
+        ep = (const T *)s->epacc;
+    }
     const int rb = s->opt.stage2 == SIM_STAGE2_ILU0_RB;
     const T *dinv = sizeof(T) == sizeof(double) ? (const T *)s->dinv_d : (const T *)s->dinv;
     stage2_a_kernel<B, T><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, r, (const T *)s->qiwT, (const T *)s->ahat, dinv, ep,

@@ -112,52 +112,76 @@ __device__ void fold(const double *partials, int nv, double *out) {
 
 constexpr int NVMAX = SIM_MAX_M + 1;
 
-// h[k] = V_k . w, k < nv
+// h[k] = V_k . w, k < NV (NV exact: no predicated work for absent vectors)
+template <int NV>
 __global__ void __launch_bounds__(SIM_THREADS) dots_kernel(const double *__restrict__ V, const double *__restrict__ w,
-                                                           long n, int nv, double *partials, unsigned int *ticket,
+                                                           long n, double *partials, unsigned int *ticket,
                                                            double *out, const int *done) {
     if (skip(done)) return;
-    double acc[NVMAX];
+    double acc[NV];
 #pragma unroll
-    for (int k = 0; k < NVMAX; k++) acc[k] = 0.0;
+    for (int k = 0; k < NV; k++) acc[k] = 0.0;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
         const double wi = w[i];
 #pragma unroll
-        for (int k = 0; k < NVMAX; k++)
-            if (k < nv) acc[k] += V[k * n + i] * wi;
+        for (int k = 0; k < NV; k++) acc[k] += V[k * n + i] * wi;
     }
-    block_partials<NVMAX>(acc, nv, partials);
+    block_partials<NV>(acc, NV, partials);
     if (last_block(ticket)) {
-        fold(partials, nv, out);
+        fold(partials, NV, out);
         if (threadIdx.x == 0) *ticket = 0u;
     }
 }
 
 // w -= sum_k h[k] V_k ; out[k] = V_k . w (second Gram-Schmidt pass)
+template <int NV>
 __global__ void __launch_bounds__(SIM_THREADS) orth_dots_kernel(const double *__restrict__ V, double *__restrict__ w,
-                                                                long n, int nv, const double *h, double *partials,
+                                                                long n, const double *h, double *partials,
                                                                 unsigned int *ticket, double *out, const int *done) {
     if (skip(done)) return;
-    __shared__ double hs[NVMAX];
-    for (int k = threadIdx.x; k < nv; k += blockDim.x) hs[k] = h[k];
-    __syncthreads();
-    double acc[NVMAX];
+    double hs[NV];
 #pragma unroll
-    for (int k = 0; k < NVMAX; k++) acc[k] = 0.0;
+    for (int k = 0; k < NV; k++) hs[k] = h[k];
+    double acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; k++) acc[k] = 0.0;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        double v[NV];
         double wi = w[i];
-        for (int k = 0; k < nv; k++) wi -= hs[k] * V[k * n + i];
+#pragma unroll
+        for (int k = 0; k < NV; k++) { v[k] = V[k * n + i]; wi -= hs[k] * v[k]; }
         w[i] = wi;
 #pragma unroll
-        for (int k = 0; k < NVMAX; k++)
-            if (k < nv) acc[k] += V[k * n + i] * wi;
+        for (int k = 0; k < NV; k++) acc[k] += v[k] * wi;
     }
-    block_partials<NVMAX>(acc, nv, partials);
+    block_partials<NV>(acc, NV, partials);
     if (last_block(ticket)) {
-        fold(partials, nv, out);
+        fold(partials, NV, out);
         if (threadIdx.x == 0) *ticket = 0u;
     }
 }
+
+// launch the NV-specialised kernels for a runtime vector count nv <= SIM_MAX_M
+template <int NV>
+struct OrthDispatch {
+    static void dots(int nv, cudaStream_t st, const double *V, const double *w, long n, double *part, unsigned int *tk,
+                     double *out, const int *done) {
+        if (nv == NV) dots_kernel<NV><<<SIM_RED_BLOCKS, SIM_THREADS, 0, st>>>(V, w, n, part, tk, out, done);
+        else OrthDispatch<NV - 1>::dots(nv, st, V, w, n, part, tk, out, done);
+    }
+    static void orth(int nv, cudaStream_t st, const double *V, double *w, long n, const double *h, double *part,
+                     unsigned int *tk, double *out, const int *done) {
+        if (nv == NV) orth_dots_kernel<NV><<<SIM_RED_BLOCKS, SIM_THREADS, 0, st>>>(V, w, n, h, part, tk, out, done);
+        else OrthDispatch<NV - 1>::orth(nv, st, V, w, n, h, part, tk, out, done);
+    }
+};
+template <>
+struct OrthDispatch<0> {
+    static void dots(int, cudaStream_t, const double *, const double *, long, double *, unsigned int *, double *,
+                     const int *) {}
+    static void orth(int, cudaStream_t, const double *, double *, long, const double *, double *, unsigned int *,
+                     double *, const int *) {}
+};
 
 // w -= sum_k h2[k] V_k ; ||w||; last block: Hessenberg column j, Givens, test
 __global__ void __launch_bounds__(SIM_THREADS) orth_norm_kernel(const double *__restrict__ V, double *__restrict__ w,
@@ -274,9 +298,10 @@ __global__ void norm_kernel(const double *__restrict__ v, long n, double *partia
 }
 
 // start of a restart cycle: clear flags and the Givens state, g = beta e1
-__global__ void cycle_init_kernel(KrylovCtl *ctl, double tol) {
+// (ctl->tol is set once per solve)
+__global__ void cycle_init_kernel(KrylovCtl *ctl) {
     const int t = threadIdx.x;
-    if (t == 0) { ctl->done = 0; ctl->k = 0; ctl->tol = tol; ctl->g[0] = ctl->beta; }
+    if (t == 0) { ctl->done = 0; ctl->k = 0; ctl->g[0] = ctl->beta; }
     for (int k = t + 1; k <= SIM_MAX_M; k += blockDim.x) ctl->g[k] = 0.0;
 }
 
@@ -314,11 +339,39 @@ sim_status k_norm2(sim_t *s, const double *v, long n, double *out) {
     return SIM_OK;
 }
 
-sim_status k_fgmres(sim_t *s, const double *b, double *x, sim_linear_info *info) {
+// one restart cycle of FGMRES from v0 = r / beta: m Arnoldi steps, each kernel
+// skipping its work once ctl->done is set (no host synchronisation inside)
+static sim_status enqueue_cycle(sim_t *s) {
     const long n = (long)s->N * s->b;
     const int m = s->m;
     const bool zf = sim_mixed(s);
     const size_t zes = zf ? sizeof(float) : sizeof(double);
+    KrylovCtl *ctl = s->ctl;
+    const int *done = &ctl->done;
+    cycle_init_kernel<<<1, 64, 0, s->stream>>>(ctl);
+    SIM_LAUNCHED(s);
+    scale_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(s->r, s->V, n, ctl, 1);
+    SIM_LAUNCHED(s);
+    for (int j = 0; j < m; j++) {
+        double *vj = s->V + (size_t)j * n;
+        void *zj = (char *)s->Z + (size_t)j * n * zes;
+        if (cpr_apply(s, vj, zj, done) != SIM_OK) return s->err;
+        if (spmv_done(s, zj, zf, s->w, done) != SIM_OK) return s->err;
+        OrthDispatch<SIM_MAX_M>::dots(j + 1, s->stream, s->V, s->w, n, s->red, s->ticket, ctl->h, done);
+        SIM_LAUNCHED(s);
+        OrthDispatch<SIM_MAX_M>::orth(j + 1, s->stream, s->V, s->w, n, ctl->h, s->red, s->ticket, ctl->h2, done);
+        SIM_LAUNCHED(s);
+        orth_norm_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(s->V, s->w, n, j, m, s->red, s->ticket, ctl);
+        SIM_LAUNCHED(s);
+        scale_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(s->w, s->V + (size_t)(j + 1) * n, n, ctl, 0);
+        SIM_LAUNCHED(s);
+    }
+    return SIM_OK;
+}
+
+sim_status k_fgmres(sim_t *s, const double *b, double *x, sim_linear_info *info) {
+    const long n = (long)s->N * s->b;
+    const bool zf = sim_mixed(s);
     sim_linear_info li = {0, 0, 0, 0.0, 0.0};
     if (!s->precond_ready) { if (cpr_setup(s) != SIM_OK) return s->err; }
     double bn;
@@ -329,28 +382,41 @@ sim_status k_fgmres(sim_t *s, const double *b, double *x, sim_linear_info *info)
     if (!(bn == bn)) { if (info) *info = li; return sim_fail(s, SIM_ENAN, "non-finite right-hand side"); }
     const double tol = s->opt.lin_tol * bn;
     KrylovCtl *ctl = s->ctl;
-    const int *done = &ctl->done;
     SIM_CK(s, cudaMemcpyAsync(s->r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->stream));
     SIM_CK(s, cudaMemcpyAsync(&ctl->beta, &bn, sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    SIM_CK(s, cudaMemcpyAsync(&ctl->tol, &tol, sizeof(double), cudaMemcpyHostToDevice, s->stream));
     for (int cyc = 0; cyc <= s->opt.gmres_max_restarts; cyc++) {
-        cycle_init_kernel<<<1, 64, 0, s->stream>>>(ctl, tol);
-        SIM_LAUNCHED(s);
-        scale_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(s->r, s->V, n, ctl, 1);
-        SIM_LAUNCHED(s);
-        for (int j = 0; j < m; j++) {
-            double *vj = s->V + (size_t)j * n;
-            void *zj = (char *)s->Z + (size_t)j * n * zes;
-            if (cpr_apply(s, vj, zj, done) != SIM_OK) return s->err;
-            if (spmv_done(s, zj, zf, s->w, done) != SIM_OK) return s->err;
-            dots_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(s->V, s->w, n, j + 1, s->red, s->ticket, ctl->h, done);
-            SIM_LAUNCHED(s);
-            orth_dots_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(s->V, s->w, n, j + 1, ctl->h, s->red, s->ticket,
-                                                                            ctl->h2, done);
-            SIM_LAUNCHED(s);
-            orth_norm_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(s->V, s->w, n, j, m, s->red, s->ticket, ctl);
-            SIM_LAUNCHED(s);
-            scale_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(s->w, s->V + (size_t)(j + 1) * n, n, ctl, 0);
-            SIM_LAUNCHED(s);
+        if (s->opt.graphs) {
+            // the restart cycle as one CUDA graph, captured once per preconditioner setup
+            if (!s->cycle_exec || s->cycle_gen != s->setup_gen) {
+                cudaGraph_t g = nullptr;
+                SIM_CK(s, cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+                const int64_t l0 = s->launches;
+                const sim_status st = enqueue_cycle(s);
+                const cudaError_t ec = cudaStreamEndCapture(s->stream, &g);
+                if (st != SIM_OK) { if (g) cudaGraphDestroy(g); return s->err; }
+                if (!sim_cuda_ok(s, ec, "cudaStreamEndCapture")) return s->err;
+                s->graph_nodes = s->launches - l0;
+                if (s->cycle_exec) {
+                    cudaGraphExecUpdateResultInfo ri;
+                    if (cudaGraphExecUpdate(s->cycle_exec, g, &ri) != cudaSuccess) {
+                        cudaGetLastError();
+                        cudaGraphExecDestroy(s->cycle_exec);
+                        s->cycle_exec = nullptr;
+                    }
+                }
+                if (!s->cycle_exec) {
+                    const cudaError_t ei = cudaGraphInstantiate(&s->cycle_exec, g, 0);
+                    if (ei != cudaSuccess) { cudaGraphDestroy(g); s->cycle_exec = nullptr; sim_cuda_ok(s, ei, "cudaGraphInstantiate"); return s->err; }
+                }
+                cudaGraphDestroy(g);
+                s->cycle_gen = s->setup_gen;
+            } else {
+                s->launches += s->graph_nodes;
+            }
+            SIM_CK(s, cudaGraphLaunch(s->cycle_exec, s->stream));
+        } else if (enqueue_cycle(s) != SIM_OK) {
+            return s->err;
         }
         backsolve_kernel<<<1, 32, 0, s->stream>>>(ctl);
         SIM_LAUNCHED(s);

@@ -63,6 +63,7 @@ void sim_destroy(sim_t *s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
     cpr_free(s);
     if (s->stream) cudaStreamSynchronize(s->stream);
+    if (s->cycle_exec) cudaGraphExecDestroy(s->cycle_exec);
     for (void *p : s->allocs) cudaFree(p);
     if (s->h_pinned) cudaFreeHost(s->h_pinned);
     if (s->ctl_host) cudaFreeHost(s->ctl_host);
@@ -83,7 +84,8 @@ sim_status sim_create(const sim_grid *g, const sim_rock *r, const sim_fluid *f, 
     if (o->gmres_m < 1 || o->gmres_m > SIM_MAX_M) return sim_fail(nullptr, SIM_EINVAL, "gmres_m must be in 1..32");
     if (o->precond < 0 || o->precond > 2 || o->stage2 < 0 || o->stage2 > 1 || o->precision < 0 || o->precision > 1)
         return sim_fail(nullptr, SIM_EINVAL, "bad preconditioner options");
-    if (o->amg_coarse_max < 1 || o->amg_coarse_max > 1024 || o->amg_rounds < 1 || o->amg_max_levels < 1)
+    if (o->amg_coarse_max < 1 || o->amg_coarse_max > 1024 || o->amg_rounds < 1 || o->amg_max_levels < 1 ||
+        o->amg_cycles < 1 || o->amg_cycles > 16)
         return sim_fail(nullptr, SIM_EINVAL, "bad AMG options");
     if (f->model == 3) {
         if (f->npvt < 2 || f->npvt > SIM_MAX_PVT) return sim_fail(nullptr, SIM_EINVAL, "npvt must be in 2..64");
@@ -189,6 +191,8 @@ sim_status sim_create(const sim_grid *g, const sim_rock *r, const sim_fluid *f, 
     s->dinv_d = (double *)A(sizeof(double) * b * b * N);
     s->dinv = mixed ? A(sizeof(float) * b * b * N) : (void *)s->dinv_d;
     s->r2 = A(tsz * n);
+    s->rpT = A(tsz * N);
+    s->epacc = A(tsz * N);
     s->zr = A(tsz * n);
     s->partner = (int *)A(sizeof(int) * N);
     s->pick = (int *)A(sizeof(int) * (N + 1));   // also holds founder ids + total

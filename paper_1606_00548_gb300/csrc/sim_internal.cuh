@@ -49,7 +49,8 @@ struct KrylovCtl {
 
 struct AmgLevel {
     int n = 0, width = 0;        // level 0: width 7, structured
-    int *col = nullptr;          // ELL columns [width][n] (levels >= 1)
+    int *col = nullptr;          // ELL columns [width][n] (levels >= 1), -1 padding
+    int *colA = nullptr;         // the same with padding on the row's own column (apply)
     double *val = nullptr;       // ELL values, FP64 (setup precision)
     void *valT = nullptr;        // ELL values in apply precision (float copy for mixed)
     void *dinvT = nullptr;       // 1 / l1 row sums, apply precision
@@ -101,6 +102,8 @@ struct sim {
     double *w = nullptr, *r = nullptr, *xl = nullptr, *bl = nullptr, *dx = nullptr;
     KrylovCtl *ctl = nullptr;
     KrylovCtl *ctl_host = nullptr;
+    cudaGraphExec_t cycle_exec = nullptr;   // captured restart cycle
+    int64_t setup_gen = 0, cycle_gen = -1, graph_nodes = 0;
 
     // CPR
     bool precond_ready = false;
@@ -112,6 +115,7 @@ struct sim {
     void *dinv = nullptr;        // [b][b][N] ILU / block-Jacobi inverse diagonal blocks
     double *dinv_d = nullptr;    // FP64 scratch of the same
     void *r2 = nullptr;          // [b][N] stage-2 work vector (apply precision)
+    void *rpT = nullptr, *epacc = nullptr;   // [N] stage-P residual and accumulated correction
     void *zr = nullptr;          // [b][N]
     std::vector<AmgLevel> lev;
     // AMG setup scratch

@@ -68,7 +68,8 @@ class sim_options(C.Structure):
                 ("gmres_m", C.c_int32), ("gmres_max_restarts", C.c_int32), ("precond", C.c_int32),
                 ("stage2", C.c_int32), ("amg_theta", C.c_double), ("amg_rounds", C.c_int32),
                 ("amg_coarse_max", C.c_int32), ("amg_max_levels", C.c_int32), ("chop_ds", C.c_double),
-                ("chop_dp", C.c_double), ("max_cuts", C.c_int32), ("precision", C.c_int32)]
+                ("chop_dp", C.c_double), ("max_cuts", C.c_int32), ("precision", C.c_int32),
+                ("amg_cycles", C.c_int32), ("graphs", C.c_int32)]
 
 
 class sim_linear_info(C.Structure):
@@ -177,9 +178,10 @@ def options_from(solver: dict, precision: int = 0) -> sim_options:
     for name in ("newton_tol", "lin_tol", "amg_theta", "chop_ds", "chop_dp"):
         setattr(o, name, float(solver[name]))
     for name in ("newton_max", "gmres_m", "gmres_max_restarts", "precond", "stage2", "amg_rounds",
-                 "amg_coarse_max", "amg_max_levels", "max_cuts"):
+                 "amg_coarse_max", "amg_max_levels", "max_cuts", "amg_cycles"):
         setattr(o, name, int(solver[name]))
     o.precision = int(precision)
+    o.graphs = int(solver.get("graphs", 1))
     return o
 
 

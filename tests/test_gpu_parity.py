@@ -129,12 +129,12 @@ def test_qi_and_amg_hierarchy_bitexact(torch_cuda, name):
 
 
 @pytest.mark.parametrize("name", ["ow_ragged", "bo_ragged"])
-@pytest.mark.parametrize("stage2", [0, 1])
-def test_cpr_apply_matches_oracle(torch_cuda, name, stage2):
+@pytest.mark.parametrize("stage2,cycles", [(0, 1), (1, 1), (1, 3)])
+def test_cpr_apply_matches_oracle(torch_cuda, name, stage2, cycles):
     torch = torch_cuda
     case = CASES[name]()
     dt = 10.0 if case["model"] == 3 else 1.0
-    g, o = _loaded_pair(case, dt, 6, stage2=stage2)
+    g, o = _loaded_pair(case, dt, 6, stage2=stage2, amg_cycles=cycles)
     N, b = g.N, g.b
     r = np.random.default_rng(2).standard_normal(N * b)
     zo = o.precond_apply(r)
@@ -144,12 +144,13 @@ def test_cpr_apply_matches_oracle(torch_cuda, name, stage2):
     assert rel_err(to_il(zd.cpu().numpy(), N, b), zo) <= 1e-9
 
 
-@pytest.mark.parametrize("name", ["ow_ragged", "bo_ragged", "ow_1d", "bo_column"])
-def test_linear_solve_matches_oracle(torch_cuda, name):
+@pytest.mark.parametrize("name,cycles", [("ow_ragged", 1), ("bo_ragged", 1), ("ow_1d", 1), ("bo_column", 1),
+                                         ("bo_ragged", 2)])
+def test_linear_solve_matches_oracle(torch_cuda, name, cycles):
     torch = torch_cuda
     case = CASES[name]()
     dt = 10.0 if case["model"] == 3 else 1.0
-    g, o = _loaded_pair(case, dt, None)
+    g, o = _loaded_pair(case, dt, None, amg_cycles=cycles)
     N, b = g.N, g.b
     rhs = np.random.default_rng(3).standard_normal(N * b)
     xo, io = o.linear_solve(rhs)
@@ -241,3 +242,19 @@ def test_full_size_black_oil_100x100x20(torch_cuda):
     assert (phg != pho).sum() <= 0
     assert rel_err(xg[:N], xo[:N]) <= 1e-6
     assert abs(ig.linear_iterations - io.linear_iterations) <= 2
+
+
+def test_graph_replay_matches_direct_launches(torch_cuda):
+    """The restart cycle replayed as a CUDA graph gives the same iterates as
+    launching its kernels one by one (identical arithmetic, same order)."""
+    case = synth.black_oil_case(nx=24, ny=24, nz=6, nsteps=2, dt=10.0, seed=48)
+    from paper_1606_00548_gb300.sim import Simulator
+    a = Simulator(case, graphs=1)
+    b = Simulator(case, graphs=0)
+    for dt in case["dt"]:
+        sa, ia = a.step(dt)
+        sb, ib = b.step(dt)
+        assert ia.newton_iterations == ib.newton_iterations and ia.linear_iterations == ib.linear_iterations
+    pa = a.get_state(); pb = b.get_state()
+    for u, v in zip(pa, pb):
+        assert np.array_equal(u, v)
