@@ -226,6 +226,12 @@ sim_status sim_cnv_noalloc(int32_t nx, int32_t ny, int32_t nz, double dx, double
                            const double *R_dev, const double *poro_dev, const double *cnv_rho, double dt,
                            double *cnv_dev, void *cuda_stream);
 
+/* Diagnostics (no paper counterpart): FP64 and FP32 fused-multiply-add rates
+   of the current device, measured with independent FMA chains and CUDA
+   events; the roofline of the FP64-bound kernels is taken against the FP64
+   rate.  Allocates a small scratch buffer; synchronises the device. */
+sim_status sim_probe_fma_rates(double *fp64_fma_per_s, double *fp32_fma_per_s);
+
 const char *sim_last_error(sim_t *s);   /* s may be NULL: last create error */
 void sim_clear_error(sim_t *s);
 

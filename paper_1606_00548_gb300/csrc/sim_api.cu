@@ -42,6 +42,18 @@ void sim_free(sim_t *s, void *p) {
 }
 
 namespace {
+// independent FMA chains, no memory traffic except one store per thread
+template <typename T>
+__global__ void fma_probe_kernel(T *out, int iters) {
+    T a0 = threadIdx.x * (T)1e-3, a1 = a0 + (T)1, a2 = a0 + (T)2, a3 = a0 + (T)3;
+    T a4 = a0 + (T)4, a5 = a0 + (T)5, a6 = a0 + (T)6, a7 = a0 + (T)7;
+    const T m = (T)0.9999999, c = (T)1e-7;
+    for (int i = 0; i < iters; i++) {
+        a0 = fma(a0, m, c); a1 = fma(a1, m, c); a2 = fma(a2, m, c); a3 = fma(a3, m, c);
+        a4 = fma(a4, m, c); a5 = fma(a5, m, c); a6 = fma(a6, m, c); a7 = fma(a7, m, c);
+    }
+    out[blockIdx.x * blockDim.x + threadIdx.x] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+}
 __global__ void widen_kernel(const float *__restrict__ a, double *__restrict__ b, long n) {
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) b[i] = (double)a[i];
 }
@@ -516,6 +528,39 @@ sim_status sim_well_rates(sim_t *s, double *q3) {
     for (int c = 0; c < 3; c++) q3[c] = s->h_pinned[c];
     return SIM_OK;
 }
+sim_status sim_probe_fma_rates(double *fp64_fma_per_s, double *fp32_fma_per_s) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return sim_fail(nullptr, SIM_ECUDA, "sim_probe_fma_rates: no CUDA device");
+    const int blocks = sms * 8, threads = 256;
+    void *buf = nullptr;
+    if (cudaMalloc(&buf, sizeof(double) * blocks * threads) != cudaSuccess)
+        return sim_fail(nullptr, SIM_ENOMEM, "sim_probe_fma_rates: allocation failed");
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0); cudaEventCreate(&e1);
+    float ms = 0.f;
+    const int it64 = 4096, it32 = 16384;
+    fma_probe_kernel<double><<<blocks, threads>>>((double *)buf, 16);
+    cudaEventRecord(e0);
+    fma_probe_kernel<double><<<blocks, threads>>>((double *)buf, it64);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (fp64_fma_per_s) *fp64_fma_per_s = (double)blocks * threads * it64 * 8 / (ms * 1e-3);
+    fma_probe_kernel<float><<<blocks, threads>>>((float *)buf, 16);
+    cudaEventRecord(e0);
+    fma_probe_kernel<float><<<blocks, threads>>>((float *)buf, it32);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (fp32_fma_per_s) *fp32_fma_per_s = (double)blocks * threads * it32 * 8 / (ms * 1e-3);
+    cudaEventDestroy(e0); cudaEventDestroy(e1);
+    cudaFree(buf);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return sim_fail(nullptr, SIM_ECUDA, std::string("sim_probe_fma_rates: ") + cudaGetErrorString(e));
+    return SIM_OK;
+}
+
 sim_status sim_get_stats(sim_t *s, sim_stats *st) {
     if (!s || !st) return SIM_EINVAL;
     st->kernel_launches = s->launches;

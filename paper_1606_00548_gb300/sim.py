@@ -124,6 +124,7 @@ _SIGS = {
     "sim_block_size": ([_vp], C.c_int32),
     "sim_cnv_noalloc": ([C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double, C.c_int32,
                          _vp, _vp, _dp, C.c_double, _vp, _vp], C.c_int),
+    "sim_probe_fma_rates": ([_dp, _dp], C.c_int),
     "sim_last_error": ([_vp], C.c_char_p),
     "sim_clear_error": ([_vp], None),
 }
@@ -365,3 +366,11 @@ def sim_cnv_noalloc(case: dict, b: int, R_dev, poro_dev, dt: float, out_dev, str
     st = L.sim_cnv_noalloc(case["nx"], case["ny"], case["nz"], case["dx"], case["dy"], case["dz"], b,
                            _ptr(R_dev), _ptr(poro_dev), rp, float(dt), _ptr(out_dev), _vp(stream) if stream else None)
     _check(None, st)
+
+
+def sim_probe_fma_rates():
+    """(FP64, FP32) fused-multiply-add rates of the current device, per second."""
+    L = load()
+    a = C.c_double(); b = C.c_double()
+    _check(None, L.sim_probe_fma_rates(C.byref(a), C.byref(b)))
+    return a.value, b.value
