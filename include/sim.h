@@ -226,6 +226,43 @@ sim_status sim_cnv_noalloc(int32_t nx, int32_t ny, int32_t nz, double dx, double
                            const double *R_dev, const double *poro_dev, const double *cnv_rho, double dt,
                            double *cnv_dev, void *cuda_stream);
 
+/* ---- learned pressure stage (no paper counterpart) ----
+   A 3-D convolutional network: 4 layers of 3x3x3 kernels (zero padding),
+   channels 4 -> 16 -> 16 -> 16 -> 1, ReLU between layers; BF16 weights and
+   activations, FP32 accumulation on the tensor cores (mma.sync), FP32 master
+   weights updated by Adam on the device.  Inputs per cell (x [N][4] FP32,
+   cell-major): the normalised pressure residual and three standardised log
+   face-transmissibility sums; output y [N] FP32: a normalised pressure
+   correction.  Parameters as one flat FP32 array: for each layer, W[27][cin][cout]
+   (tap t = (dz+1)*9 + (dy+1)*3 + (dx+1)) then b[cout]. */
+typedef struct sim_net sim_net_t;
+sim_status sim_net_create(int32_t nx, int32_t ny, int32_t nz, uint64_t seed, void *cuda_stream, sim_net_t **out);
+void sim_net_destroy(sim_net_t *n);
+int64_t sim_net_param_count(sim_net_t *n);
+sim_status sim_net_set_params(sim_net_t *n, const float *params);   /* host array */
+sim_status sim_net_get_params(sim_net_t *n, float *params);         /* host array */
+/* y = net(x); device pointers, asynchronous on the net's stream */
+sim_status sim_net_forward(sim_net_t *n, const float *x_dev, float *y_dev);
+/* mean-squared-error loss against target [N] and its gradient (host, flat like the parameters; may be NULL) */
+sim_status sim_net_loss_grad(sim_net_t *n, const float *x_dev, const float *target_dev, double *loss, float *grads);
+/* one Adam step (beta 0.9 / 0.999) on the loss; loss may be NULL (then no synchronisation) */
+sim_status sim_net_train_step(sim_net_t *n, const float *x_dev, const float *target_dev, float lr, double *loss);
+const char *sim_net_last_error(sim_net_t *n);
+/* Use net (same grid; not owned, must outlive its use) as an extra CPR stage
+   after the AMG V-cycles: the pressure residual left by stage P is normalised,
+   the network's correction is added to the pressure update.  enable = 0
+   turns it off.  A solve whose first restart cycle reduces the residual by
+   less than 10x (or turns non-finite) is redone with plain CPR. */
+sim_status sim_set_learned_stage(sim_t *s, sim_net_t *net, int32_t enable);
+/* Training pairs from the last linear solve: for the first k Krylov vectors
+   v_j of its last restart cycle (k <= its iterations + 1), x_j = features of
+   the decoupled pressure residual w^T v_j (normalised by its RMS) and
+   y_j = one AMG V-cycle applied to it (same scaling).  x_dev [k][N][4],
+   y_dev [k][N] (device, FP32). */
+sim_status sim_learned_pairs(sim_t *s, int32_t k, float *x_dev, float *y_dev);
+/* number of solves that fell back to plain CPR */
+int64_t sim_learned_fallbacks(sim_t *s);
+
 /* Diagnostics (no paper counterpart): FP64 and FP32 fused-multiply-add rates
    of the current device, measured with independent FMA chains and CUDA
    events; the roofline of the FP64-bound kernels is taken against the FP64

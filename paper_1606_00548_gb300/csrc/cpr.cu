@@ -21,6 +21,9 @@
 // Layouts: level 0 is the 7-point stencil A_p [7][N]; coarser levels are ELL,
 // entry k of row i at k*n + i, columns ascending, -1 padding.
 #include <algorithm>
+#include <cmath>
+#include <vector>
+
 #include "sim_internal.cuh"
 
 namespace {
@@ -761,6 +764,97 @@ __global__ void simple_prec_kernel(int N, const double *__restrict__ r, const do
     }
 }
 
+// ---- learned stage helpers ------------------------------------------------
+// RMS of a vector into *out (per-block partials folded in block order by the last block)
+template <typename T>
+__global__ void rms_kernel(int n, const T *__restrict__ v, double *partials, unsigned int *ticket, double *out,
+                           const int *done) {
+    if (skip(done)) return;
+    __shared__ double sh[SIM_THREADS];
+    __shared__ bool last;
+    double s = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) s += (double)v[i] * (double)v[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int b = 0; b < (int)gridDim.x; b++) t += __ldcg(partials + b);
+        *out = sqrt(t / n);
+        *ticket = 0u;
+    }
+}
+
+// network input: [r / rms, three standardised log-transmissibility features]
+template <typename T>
+__global__ void learned_in_kernel(int n, const T *__restrict__ r, const double *__restrict__ rms,
+                                  const float *__restrict__ feat, float *__restrict__ x, const int *done) {
+    if (skip(done)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double sc = *rms > 0.0 ? 1.0 / *rms : 0.0;
+    x[(long)i * 4] = (float)((double)r[i] * sc);
+    x[(long)i * 4 + 1] = feat[(long)i * 3];
+    x[(long)i * 4 + 2] = feat[(long)i * 3 + 1];
+    x[(long)i * 4 + 3] = feat[(long)i * 3 + 2];
+}
+
+// ep_out = ep + y * rms
+template <typename T>
+__global__ void learned_out_kernel(int n, const T *__restrict__ ep, const float *__restrict__ y,
+                                   const double *__restrict__ rms, T *__restrict__ out, const int *done) {
+    if (skip(done)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = ep[i] + (T)((double)y[i] * *rms);
+}
+
+// training pair j: x_j = [f / rms, features], y_j = e / rms
+template <typename T>
+__global__ void pair_kernel(int n, const T *__restrict__ f, const T *__restrict__ e, const double *__restrict__ rms,
+                            const float *__restrict__ feat, float *__restrict__ x, float *__restrict__ y) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double sc = *rms > 0.0 ? 1.0 / *rms : 0.0;
+    x[(long)i * 4] = (float)((double)f[i] * sc);
+    x[(long)i * 4 + 1] = feat[(long)i * 3];
+    x[(long)i * 4 + 2] = feat[(long)i * 3 + 1];
+    x[(long)i * 4 + 3] = feat[(long)i * 3 + 2];
+    y[i] = (float)((double)e[i] * sc);
+}
+
+// log of the summed face transmissibilities per direction
+__global__ void logt_kernel(GridDesc g, const double *__restrict__ T, float *__restrict__ feat) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.N) return;
+    const Cell c = cell_of(g, i);
+    const int N = g.N;
+    const double sx = T[i] + (c.ix > 0 ? T[i - 1] : 0.0);
+    const double sy = T[N + i] + (c.iy > 0 ? T[N + i - g.nx] : 0.0);
+    const double sz = T[2L * N + i] + (c.iz > 0 ? T[2L * N + i - g.nx * g.ny] : 0.0);
+    feat[(long)i * 3] = (float)log(sx + 1e-30);
+    feat[(long)i * 3 + 1] = (float)log(sy + 1e-30);
+    feat[(long)i * 3 + 2] = (float)log(sz + 1e-30);
+}
+
+__global__ void standardize_kernel(int n, float *__restrict__ feat, float m0, float m1, float m2, float s0, float s1,
+                                   float s2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    feat[(long)i * 3] = s0 > 0.f ? (feat[(long)i * 3] - m0) / s0 : 0.f;
+    feat[(long)i * 3 + 1] = s1 > 0.f ? (feat[(long)i * 3 + 1] - m1) / s1 : 0.f;
+    feat[(long)i * 3 + 2] = s2 > 0.f ? (feat[(long)i * 3 + 2] - m2) / s2 : 0.f;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -1090,6 +1184,22 @@ static sim_status apply_btz(sim_t *s, const double *r, TZ *z, const int *done) {
         }
         ep = (const T *)s->epacc;
     }
+    if (s->learned_active && s->net) {
+        // extra stage: the network's correction of the pressure residual left by stage P
+        const T *rp = (s->opt.amg_cycles > 1 && s->lev.size() > 1) ? (const T *)s->rpT : (const T *)L0.f;
+        amg_resid_kernel<T><<<sim_blocks(N, 128), 128, 0, s->stream>>>(level_matT<T>(s, L0, 0), rp, ep, (T *)s->lres, done);
+        SIM_LAUNCHED(s);
+        rms_kernel<T><<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(N, (const T *)s->lres, s->red, s->ticket, s->lrms, done);
+        SIM_LAUNCHED(s);
+        learned_in_kernel<T><<<sim_blocks(N), SIM_THREADS, 0, s->stream>>>(N, (const T *)s->lres, s->lrms, s->lfeat, s->lx, done);
+        SIM_LAUNCHED(s);
+        const int64_t l0 = net_launches(s->net);
+        if (net_infer(s->net, s->lx, s->ly, s->stream, done) != SIM_OK) return sim_fail(s, SIM_ECUDA, "learned stage inference");
+        s->launches += net_launches(s->net) - l0;
+        learned_out_kernel<T><<<sim_blocks(N), SIM_THREADS, 0, s->stream>>>(N, ep, s->ly, s->lrms, (T *)s->lep, done);
+        SIM_LAUNCHED(s);
+        ep = (const T *)s->lep;
+    }
     const int rb = s->opt.stage2 == SIM_STAGE2_ILU0_RB;
     const T *dinv = sizeof(T) == sizeof(double) ? (const T *)s->dinv_d : (const T *)s->dinv;
     stage2_a_kernel<B, T><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, r, (const T *)s->qiwT, (const T *)s->ahat, dinv, ep,
@@ -1119,5 +1229,55 @@ sim_status cpr_copy_level_ell(sim_t *s, int level, int *col, double *val) {
     SIM_CK(s, cudaMemcpyAsync(col, L.col, sizeof(int) * (size_t)L.width * L.n, cudaMemcpyDeviceToHost, s->stream));
     SIM_CK(s, cudaMemcpyAsync(val, L.val, sizeof(double) * (size_t)L.width * L.n, cudaMemcpyDeviceToHost, s->stream));
     SIM_CK(s, cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}
+
+template <typename T>
+static sim_status learned_pairs_t(sim_t *s, int k, float *x, float *y) {
+    const int N = s->N;
+    AmgLevel &L0 = s->lev[0];
+    for (int j = 0; j < k; j++) {
+        const double *v = s->V + (size_t)j * N * s->b;
+        if (s->b == 2) restrict_p_kernel<2, T><<<sim_blocks(N), SIM_THREADS, 0, s->stream>>>(N, v, (const T *)s->qiwT, (const T *)L0.dinvT, (T *)L0.f, (T *)L0.e, nullptr);
+        else restrict_p_kernel<3, T><<<sim_blocks(N), SIM_THREADS, 0, s->stream>>>(N, v, (const T *)s->qiwT, (const T *)L0.dinvT, (T *)L0.f, (T *)L0.e, nullptr);
+        SIM_LAUNCHED(s);
+        if (s->lev.size() == 1) {
+            coarse_solve_kernel<T><<<sim_blocks((long)L0.n * 32), SIM_THREADS, 0, s->stream>>>(L0.n, (const T *)L0.coarse_inv, (const T *)L0.f, (T *)L0.e2, nullptr);
+            SIM_LAUNCHED(s);
+        } else if (vcycle<T>(s, nullptr) != SIM_OK) {
+            return s->err;
+        }
+        rms_kernel<T><<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(N, (const T *)L0.f, s->red, s->ticket, s->lrms, nullptr);
+        SIM_LAUNCHED(s);
+        pair_kernel<T><<<sim_blocks(N), SIM_THREADS, 0, s->stream>>>(N, (const T *)L0.f, (const T *)L0.e2, s->lrms, s->lfeat,
+                                                                    x + (size_t)j * N * 4, y + (size_t)j * N);
+        SIM_LAUNCHED(s);
+    }
+    return SIM_OK;
+}
+
+sim_status cpr_learned_pairs(sim_t *s, int k, float *x, float *y) {
+    if (s->opt.precond != SIM_PRECOND_CPR || !s->precond_ready || s->lev.empty())
+        return sim_fail(s, SIM_EINVAL, "training pairs need a CPR preconditioner set up by a solve");
+    return sim_mixed(s) ? learned_pairs_t<float>(s, k, x, y) : learned_pairs_t<double>(s, k, x, y);
+}
+
+sim_status cpr_learned_features(sim_t *s) {
+    const int N = s->N;
+    logt_kernel<<<sim_blocks(N), SIM_THREADS, 0, s->stream>>>(s->gd, s->T, s->lfeat);
+    SIM_LAUNCHED(s);
+    std::vector<float> h((size_t)N * 3);
+    SIM_CK(s, cudaMemcpyAsync(h.data(), s->lfeat, sizeof(float) * 3 * (size_t)N, cudaMemcpyDeviceToHost, s->stream));
+    SIM_CK(s, cudaStreamSynchronize(s->stream));
+    double m[3] = {0, 0, 0}, q[3] = {0, 0, 0};
+    for (int i = 0; i < N; i++)
+        for (int c = 0; c < 3; c++) { const double v = h[(size_t)i * 3 + c]; m[c] += v; q[c] += v * v; }
+    float mf[3], sf[3];
+    for (int c = 0; c < 3; c++) {
+        const double mu = m[c] / N, var = q[c] / N - mu * mu;
+        mf[c] = (float)mu; sf[c] = (float)(var > 1e-12 ? std::sqrt(var) : 0.0);
+    }
+    standardize_kernel<<<sim_blocks(N), SIM_THREADS, 0, s->stream>>>(N, s->lfeat, mf[0], mf[1], mf[2], sf[0], sf[1], sf[2]);
+    SIM_LAUNCHED(s);
     return SIM_OK;
 }

@@ -385,10 +385,11 @@ sim_status k_fgmres(sim_t *s, const double *b, double *x, sim_linear_info *info)
     SIM_CK(s, cudaMemcpyAsync(s->r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->stream));
     SIM_CK(s, cudaMemcpyAsync(&ctl->beta, &bn, sizeof(double), cudaMemcpyHostToDevice, s->stream));
     SIM_CK(s, cudaMemcpyAsync(&ctl->tol, &tol, sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    s->learned_active = (s->learned_on && s->net && s->opt.precond == SIM_PRECOND_CPR) ? 1 : 0;
     for (int cyc = 0; cyc <= s->opt.gmres_max_restarts; cyc++) {
         if (s->opt.graphs) {
             // the restart cycle as one CUDA graph, captured once per preconditioner setup
-            if (!s->cycle_exec || s->cycle_gen != s->setup_gen) {
+            if (!s->cycle_exec || s->cycle_gen != s->setup_gen || s->cycle_learned != s->learned_active) {
                 cudaGraph_t g = nullptr;
                 SIM_CK(s, cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
                 const int64_t l0 = s->launches;
@@ -411,6 +412,7 @@ sim_status k_fgmres(sim_t *s, const double *b, double *x, sim_linear_info *info)
                 }
                 cudaGraphDestroy(g);
                 s->cycle_gen = s->setup_gen;
+                s->cycle_learned = s->learned_active;
             } else {
                 s->launches += s->graph_nodes;
             }
@@ -432,7 +434,18 @@ sim_status k_fgmres(sim_t *s, const double *b, double *x, sim_linear_info *info)
         const double beta = s->ctl_host->beta;
         li.iterations += k;
         li.r_norm = beta;
+        s->last_cycle_k = k;
         if (beta <= tol) { li.converged = 1; break; }
+        if (s->learned_active && cyc == 0 && !(beta <= 0.1 * bn)) {
+            // the learned stage did not pay off: redo the solve with plain CPR
+            s->learned_active = 0;
+            s->learned_fallbacks++;
+            SIM_CK(s, cudaMemsetAsync(x, 0, sizeof(double) * n, s->stream));
+            SIM_CK(s, cudaMemcpyAsync(s->r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->stream));
+            SIM_CK(s, cudaMemcpyAsync(&ctl->beta, &bn, sizeof(double), cudaMemcpyHostToDevice, s->stream));
+            li.restarts++;
+            continue;
+        }
         if (!(beta == beta)) break;
         if (cyc < s->opt.gmres_max_restarts) li.restarts++;
     }

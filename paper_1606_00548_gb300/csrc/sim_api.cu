@@ -528,6 +528,44 @@ sim_status sim_well_rates(sim_t *s, double *q3) {
     for (int c = 0; c < 3; c++) q3[c] = s->h_pinned[c];
     return SIM_OK;
 }
+sim_status sim_set_learned_stage(sim_t *s, sim_net_t *net, int32_t enable) {
+    CHECK_HANDLE(s);
+    if (enable && !net) return sim_fail(s, SIM_EINVAL, "learned stage enabled without a network");
+    if (net && net_cells(net) != s->N) return sim_fail(s, SIM_EINVAL, "network grid differs from the simulator grid");
+    if (enable && !s->lfeat) {
+        const size_t tsz = sim_mixed(s) ? sizeof(float) : sizeof(double);
+        s->lfeat = (float *)sim_alloc(s, sizeof(float) * 3 * (size_t)s->N);
+        s->lx = (float *)sim_alloc(s, sizeof(float) * 4 * (size_t)s->N);
+        s->ly = (float *)sim_alloc(s, sizeof(float) * (size_t)s->N);
+        s->lres = sim_alloc(s, tsz * s->N);
+        s->lep = sim_alloc(s, tsz * s->N);
+        s->lrms = (double *)sim_alloc(s, sizeof(double) * 2);
+        if (!s->lfeat || !s->lx || !s->ly || !s->lres || !s->lep || !s->lrms) return s->err;
+    }
+    if (s->lfeat && cpr_learned_features(s) != SIM_OK) return s->err;
+    s->net = net;
+    s->learned_on = enable ? 1 : 0;
+    SIM_CK(s, cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}
+
+sim_status sim_learned_pairs(sim_t *s, int32_t k, float *x_dev, float *y_dev) {
+    CHECK_HANDLE(s);
+    if (!x_dev || !y_dev || k < 1 || k > s->last_cycle_k + 1 || k > s->m + 1)
+        return sim_fail(s, SIM_EINVAL, "sim_learned_pairs: k must be in 1..(iterations of the last cycle + 1)");
+    if (!s->lfeat) {
+        s->lfeat = (float *)sim_alloc(s, sizeof(float) * 3 * (size_t)s->N);
+        s->lrms = (double *)sim_alloc(s, sizeof(double) * 2);
+        if (!s->lfeat || !s->lrms) return s->err;
+        if (cpr_learned_features(s) != SIM_OK) return s->err;
+    }
+    if (cpr_learned_pairs(s, k, x_dev, y_dev) != SIM_OK) return s->err;
+    SIM_CK(s, cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}
+
+int64_t sim_learned_fallbacks(sim_t *s) { return s ? s->learned_fallbacks : 0; }
+
 sim_status sim_probe_fma_rates(double *fp64_fma_per_s, double *fp32_fma_per_s) {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)

@@ -104,6 +104,8 @@ struct sim {
     KrylovCtl *ctl_host = nullptr;
     cudaGraphExec_t cycle_exec = nullptr;   // captured restart cycle
     int64_t setup_gen = 0, cycle_gen = -1, graph_nodes = 0;
+    int cycle_learned = -1;                  // learned-stage state the graph was captured with
+    int last_cycle_k = 0;                    // inner iterations of the last restart cycle
 
     // CPR
     bool precond_ready = false;
@@ -116,6 +118,16 @@ struct sim {
     double *dinv_d = nullptr;    // FP64 scratch of the same
     void *r2 = nullptr;          // [b][N] stage-2 work vector (apply precision)
     void *rpT = nullptr, *epacc = nullptr;   // [N] stage-P residual and accumulated correction
+    // learned pressure stage (extra CPR stage after the V-cycles)
+    sim_net_t *net = nullptr;
+    int learned_on = 0;          // requested
+    int learned_active = 0;      // used by the current solve (falls back to 0)
+    int64_t learned_fallbacks = 0;
+    float *lfeat = nullptr;      // [N][3] standardised log transmissibility features
+    float *lx = nullptr, *ly = nullptr;   // [N][4] network input, [N] output
+    void *lres = nullptr;        // [N] pressure residual after stage P (apply precision)
+    void *lep = nullptr;         // [N] pressure correction after the learned stage
+    double *lrms = nullptr;      // device scalar
     void *zr = nullptr;          // [b][N]
     std::vector<AmgLevel> lev;
     // AMG setup scratch
@@ -158,3 +170,10 @@ sim_status cpr_setup(sim_t *s);
 sim_status cpr_apply(sim_t *s, const double *r, void *z, const int *done);   // z FP64 or FP32 (Z type)
 void cpr_free(sim_t *s);
 sim_status cpr_copy_level_ell(sim_t *s, int level, int *col, double *val);
+sim_status cpr_learned_pairs(sim_t *s, int k, float *x_dev, float *y_dev);
+sim_status cpr_learned_features(sim_t *s);
+
+// ---- learned.cu -----------------------------------------------------------
+sim_status net_infer(sim_net_t *n, const float *x_dev, float *y_dev, cudaStream_t st, const int *done);
+int64_t net_launches(sim_net_t *n);
+int net_cells(sim_net_t *n);

@@ -125,6 +125,18 @@ _SIGS = {
     "sim_cnv_noalloc": ([C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double, C.c_int32,
                          _vp, _vp, _dp, C.c_double, _vp, _vp], C.c_int),
     "sim_probe_fma_rates": ([_dp, _dp], C.c_int),
+    "sim_net_create": ([C.c_int32, C.c_int32, C.c_int32, C.c_uint64, _vp, C.POINTER(_vp)], C.c_int),
+    "sim_net_destroy": ([_vp], None),
+    "sim_net_param_count": ([_vp], C.c_int64),
+    "sim_net_set_params": ([_vp, C.POINTER(C.c_float)], C.c_int),
+    "sim_net_get_params": ([_vp, C.POINTER(C.c_float)], C.c_int),
+    "sim_net_forward": ([_vp, _vp, _vp], C.c_int),
+    "sim_net_loss_grad": ([_vp, _vp, _vp, _dp, C.POINTER(C.c_float)], C.c_int),
+    "sim_net_train_step": ([_vp, _vp, _vp, C.c_float, _dp], C.c_int),
+    "sim_net_last_error": ([_vp], C.c_char_p),
+    "sim_set_learned_stage": ([_vp, _vp, C.c_int32], C.c_int),
+    "sim_learned_pairs": ([_vp, C.c_int32, _vp, _vp], C.c_int),
+    "sim_learned_fallbacks": ([_vp], C.c_int64),
     "sim_last_error": ([_vp], C.c_char_p),
     "sim_clear_error": ([_vp], None),
 }
@@ -172,6 +184,69 @@ def _ptr(t):
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
         raise TypeError("expected a contiguous float64 CUDA tensor")
     return _vp(t.data_ptr())
+
+
+def _ptrf(t):
+    """Device pointer of a CUDA torch tensor (contiguous float32)."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float32 CUDA tensor")
+    return _vp(t.data_ptr())
+
+
+class Net:
+    """The learned pressure stage's network (include/sim.h, sim_net_*)."""
+
+    def __init__(self, nx, ny, nz, seed=0, stream=None):
+        self.L = load()
+        h = _vp()
+        st = self.L.sim_net_create(nx, ny, nz, seed, _vp(stream) if stream else None, C.byref(h))
+        if st != SIM_OK:
+            raise SimError(st, (self.L.sim_last_error(None) or b"").decode())
+        self.h = h
+        self.N = nx * ny * nz
+        self.nparam = self.L.sim_net_param_count(h)
+
+    def _check(self, st):
+        if st != SIM_OK:
+            raise SimError(st, (self.L.sim_net_last_error(self.h) or b"").decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.sim_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.nparam
+        self._check(self.L.sim_net_set_params(self.h, p.ctypes.data_as(C.POINTER(C.c_float))))
+
+    def get_params(self):
+        p = np.zeros(self.nparam, np.float32)
+        self._check(self.L.sim_net_get_params(self.h, p.ctypes.data_as(C.POINTER(C.c_float))))
+        return p
+
+    def forward(self, x_dev, y_dev):
+        self._check(self.L.sim_net_forward(self.h, _ptrf(x_dev), _ptrf(y_dev)))
+
+    def loss_grad(self, x_dev, t_dev):
+        loss = C.c_double()
+        g = np.zeros(self.nparam, np.float32)
+        self._check(self.L.sim_net_loss_grad(self.h, _ptrf(x_dev), _ptrf(t_dev), C.byref(loss),
+                                             g.ctypes.data_as(C.POINTER(C.c_float))))
+        return loss.value, g
+
+    def train_step(self, x_dev, t_dev, lr, want_loss=True):
+        loss = C.c_double()
+        self._check(self.L.sim_net_train_step(self.h, _ptrf(x_dev), _ptrf(t_dev), float(lr),
+                                              C.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
 
 
 def options_from(solver: dict, precision: int = 0) -> sim_options:
@@ -353,6 +428,15 @@ class Simulator:
 
     def well_rates(self):
         q = np.zeros(3); _check(self.h, self.L.sim_well_rates(self.h, q.ctypes.data_as(_dp))); return q
+
+    def set_learned_stage(self, net, enable=True):
+        _check(self.h, self.L.sim_set_learned_stage(self.h, net.h if net is not None else None, 1 if enable else 0))
+
+    def learned_pairs(self, k, x_dev, y_dev):
+        _check(self.h, self.L.sim_learned_pairs(self.h, int(k), _ptrf(x_dev), _ptrf(y_dev)))
+
+    def learned_fallbacks(self):
+        return self.L.sim_learned_fallbacks(self.h)
 
     def stats(self):
         s = sim_stats(); _check(self.h, self.L.sim_get_stats(self.h, C.byref(s))); return s

@@ -1,0 +1,145 @@
+"""Learned pressure stage on the GPU: BF16 tensor-core convolution kernels
+against the FP64 reference network of the oracle.
+
+The reference applies the same roundings the device applies (weights,
+inputs, hidden activations and back-propagated gradients to BF16), so the
+remaining difference is FP32-versus-FP64 accumulation and the rare BF16
+rounding flip of an intermediate value.  The grid is ragged with respect to
+the 16-cell MMA tiles and 64-cell blocks.
+"""
+import numpy as np
+import pytest
+
+from paper_1606_00548_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+CIN = [4, 16, 16, 16]
+COUT = [16, 16, 16, 1]
+
+
+def bf16(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def unflatten(p):
+    out, off = [], 0
+    for l in range(4):
+        nw = 27 * CIN[l] * COUT[l]
+        W = p[off:off + nw].reshape(27, CIN[l], COUT[l]).astype(np.float64); off += nw
+        b = p[off:off + COUT[l]].astype(np.float64); off += COUT[l]
+        out.append((W, b))
+    return out
+
+
+def reference(x, target, params):
+    """loss and gradients with the device's BF16 roundings, FP64 arithmetic"""
+    from oracle import conv3d
+    acts = [bf16(x)]
+    for l in range(3):
+        z = conv3d.conv_fwd(acts[-1], bf16(params[l][0]), params[l][1])
+        acts.append(bf16(np.maximum(z, 0.0)))
+    y = conv3d.conv_fwd(acts[-1], bf16(params[3][0]), params[3][1])
+    n = y.size
+    loss = float(np.mean((y - target) ** 2))
+    g = bf16(2.0 * (y - target) / n)
+    grads = [None] * 4
+    for l in range(3, -1, -1):
+        dW, db = conv3d.conv_wgrad(acts[l], g)
+        grads[l] = (dW, db)
+        if l > 0:
+            gi = conv3d.conv_dgrad(g, bf16(params[l][0]))
+            g = bf16(gi * (acts[l] > 0))
+    return y, loss, grads
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1606_00548_gb300 import build
+    build.build()
+    return torch
+
+
+def test_forward_and_gradients_match_reference(torch_cuda):
+    torch = torch_cuda
+    from paper_1606_00548_gb300.sim import Net
+    nx, ny, nz = 13, 11, 5
+    net = Net(nx, ny, nz, seed=3)
+    rng = np.random.default_rng(4)
+    p = net.get_params()
+    p[:] = 0.5 * p + 0.05 * rng.standard_normal(p.size).astype(np.float32)   # non-zero biases too
+    net.set_params(p)
+    x = rng.standard_normal((nz, ny, nx, 4)).astype(np.float32)
+    t = rng.standard_normal((nz, ny, nx, 1)).astype(np.float32)
+    xd = torch.tensor(x.reshape(-1, 4), device="cuda").contiguous()
+    td = torch.tensor(t.reshape(-1), device="cuda").contiguous()
+    yd = torch.empty(nx * ny * nz, dtype=torch.float32, device="cuda")
+    net.forward(xd, yd)
+    loss_g, grads_g = net.loss_grad(xd, td)
+    params = unflatten(net.get_params())
+    y_ref, loss_ref, grads_ref = reference(x.astype(np.float64), t.astype(np.float64), params)
+    y_g = yd.cpu().numpy().reshape(nz, ny, nx, 1)
+    assert np.abs(y_g - y_ref).max() <= 1e-2 * np.abs(y_ref).max()
+    assert loss_g == pytest.approx(loss_ref, rel=2e-3)
+    g = unflatten(grads_g)
+    for l in range(4):
+        for a, b in zip(g[l], grads_ref[l]):
+            err = np.abs(a - b)
+            assert err.max() <= 2e-2 * np.abs(b).max(), (l, err.max(), np.abs(b).max())
+            assert np.median(err) <= 2e-3 * np.abs(b).max()
+
+
+def test_adam_training_reduces_the_loss(torch_cuda):
+    torch = torch_cuda
+    from paper_1606_00548_gb300.sim import Net
+    nx, ny, nz = 20, 16, 6
+    net = Net(nx, ny, nz, seed=5)
+    rng = np.random.default_rng(6)
+    x = rng.standard_normal((nx * ny * nz, 4)).astype(np.float32)
+    t = (0.5 * x[:, 0] - 0.2 * x[:, 1]).astype(np.float32)        # a learnable local map
+    xd = torch.tensor(x, device="cuda"); td = torch.tensor(t, device="cuda")
+    l0, _ = net.loss_grad(xd, td)
+    for _ in range(60):
+        net.train_step(xd, td, 3e-3, want_loss=False)
+    l1, _ = net.loss_grad(xd, td)
+    assert l1 < 0.3 * l0, (l0, l1)
+
+
+def test_learned_stage_inside_fgmres(torch_cuda):
+    """Pairs come from the simulator's own solve; with the trained network as an
+    extra CPR stage the Newton update still matches the oracle."""
+    torch = torch_cuda
+    import oracle
+    from paper_1606_00548_gb300.sim import Net, Simulator
+    from gpu_util import to_cm, rel_err
+    case = synth.black_oil_case(nx=24, ny=20, nz=6, seed=49)
+    g = Simulator(case, precision=1)
+    N = g.N
+    dt = 10.0
+    st, _ = g.newton_step(dt)                 # a solve fills the Krylov basis
+    k = 8
+    x = torch.empty((k, N, 4), dtype=torch.float32, device="cuda")
+    y = torch.empty((k, N), dtype=torch.float32, device="cuda")
+    g.learned_pairs(k, x, y)
+    assert torch.isfinite(x).all() and torch.isfinite(y).all()
+    net = Net(case["nx"], case["ny"], case["nz"], seed=7)
+    for it in range(40):
+        net.train_step(x[it % k].contiguous(), y[it % k].contiguous(), 2e-3, want_loss=False)
+    # fresh simulator with the learned stage: one Newton step vs the oracle
+    h = Simulator(case, precision=1)
+    h.set_learned_stage(net, True)
+    o = oracle.Oracle(case)
+    sh, ih = h.newton_step(dt)
+    so, io = o.newton_step(dt)
+    xh, phh = h.get_iterate()
+    xo, pho = o.get_iterate()
+    xo = to_cm(xo, N, 3)
+    assert np.array_equal(phh, pho)
+    assert rel_err(xh[:N], xo[:N]) <= 1e-6
+    assert h.learned_fallbacks() >= 0
