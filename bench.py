@@ -351,6 +351,30 @@ def run_ours(args):
     return 0
 
 
+def run_learned(args):
+    """Second metric: CPR-FGMRES time to 1e-8 relative residual on the 256x256x64
+    black-oil system (sigma 2), FP64 CPR vs FP32 CPR vs FP32 CPR + learned stage
+    (network trained on the device on 128x128x32 systems)."""
+    import torch
+    from paper_1606_00548_gb300 import build, learned
+    build.build()
+    ev = learned.evaluate(train_steps=args.train_steps)
+    r = ev["results"]
+    best = min(r, key=lambda k: r[k]["seconds"])
+    line = {
+        "metric": "CPR-FGMRES time to 1e-8 rel. residual", "value": r["mixed_cpr_learned"]["seconds"], "unit": "s",
+        "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64+f32+bf16", "data": "synthetic",
+        "config": {"workload": "black-oil 256x256x64 (4.2M cells), sigma 2, first Newton system; "
+                               "network trained on 128x128x32 (sigma 1) pairs",
+                   "train_seconds": ev["train_seconds"], "pairs_seconds": ev["pairs_seconds"],
+                   "train_loss": ev["train_loss"][-3:]},
+        "results": r, "fastest": best,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -358,7 +382,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--workload", default="bo100", choices=["bo100", "bo200", "bo400"])
+    ap.add_argument("--workload", default="bo100", choices=["bo100", "bo200", "bo400", "learned"])
+    ap.add_argument("--train-steps", type=int, default=300)
     ap.add_argument("--amg-cycles", type=int, default=None, help="V-cycles per CPR pressure stage")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -366,6 +391,8 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "learned":
+        return run_learned(args)
     return run_ours(args)
 
 

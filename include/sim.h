@@ -250,16 +250,21 @@ sim_status sim_net_train_step(sim_net_t *n, const float *x_dev, const float *tar
 const char *sim_net_last_error(sim_net_t *n);
 /* Use net (same grid; not owned, must outlive its use) as an extra CPR stage
    after the AMG V-cycles: the pressure residual left by stage P is normalised,
-   the network's correction is added to the pressure update.  enable = 0
+   the network's correction c, scaled by the minimal-residual step
+   alpha = (A_p c . r') / (A_p c . A_p c) so that it never increases the 2-norm
+   of that residual, is added to the pressure update.  enable = 0
    turns it off.  A solve whose first restart cycle reduces the residual by
    less than 10x (or turns non-finite) is redone with plain CPR. */
 sim_status sim_set_learned_stage(sim_t *s, sim_net_t *net, int32_t enable);
 /* Training pairs from the last linear solve: for the first k Krylov vectors
    v_j of its last restart cycle (k <= its iterations + 1), x_j = features of
    the decoupled pressure residual w^T v_j (normalised by its RMS) and
-   y_j = one AMG V-cycle applied to it (same scaling).  x_dev [k][N][4],
-   y_dev [k][N] (device, FP32). */
+   y_j = one AMG V-cycle applied to it (normalised by its own RMS).  x_dev [k][N][4],
+   y_dev [k][N] (device, FP32).  k outside 1..sim_learned_available(s)
+   returns SIM_EINVAL without making the handle's error sticky. */
 sim_status sim_learned_pairs(sim_t *s, int32_t k, float *x_dev, float *y_dev);
+/* Krylov vectors available to sim_learned_pairs after the last solve */
+int32_t sim_learned_available(sim_t *s);
 /* number of solves that fell back to plain CPR */
 int64_t sim_learned_fallbacks(sim_t *s);
 

@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(SIM_THREADS) props_kernel(FluidConst f, GridDe
                                                             double *__restrict__ J) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.N) return;
-    const int N = g.N;
+    const long N = g.N;
     Props<B> P;
     cell_props<B>(f, poro[i], g.dx * g.dy * g.dz, x[i], x[N + i], B == 3 ? x[2 * N + i] : 0.0, B == 3 ? ph[i] : 1, P);
     constexpr int W = B + 1;
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(SIM_THREADS) flux_kernel(GridDesc g, const dou
                                                            double *__restrict__ J) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.N) return;
-    const int N = g.N;
+    const long N = g.N;
     constexpr int W = B + 1;
     constexpr int NQ = Layout<B>::NQ;
     int ix, iy, iz;
@@ -387,7 +387,7 @@ __global__ void well_kernel(FluidConst f, GridDesc g, const double *__restrict__
                             const double *__restrict__ bhp, double *__restrict__ R, double *__restrict__ J,
                             double *__restrict__ qtot) {
     __shared__ double part[SIM_THREADS][3];
-    const int N = g.N;
+    const long N = g.N;
     double qs[3] = {0.0, 0.0, 0.0};
     for (int q = threadIdx.x; q < nperf; q += blockDim.x) {
         const int i = cell[q];
@@ -498,7 +498,7 @@ __device__ void finish_grid(double *partials, int nv, unsigned int *ticket, doub
 template <int B>
 __global__ void cnv_kernel(GridDesc g, const double *__restrict__ R, const double *__restrict__ poro, double dt,
                            FluidConst f, double *partials, unsigned int *ticket, double *out) {
-    const int N = g.N;
+    const long N = g.N;
     const double vol = g.dx * g.dy * g.dz;
     double m = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
@@ -514,7 +514,7 @@ __global__ void cnv_kernel(GridDesc g, const double *__restrict__ R, const doubl
 template <int B>
 __global__ void mass_kernel(FluidConst f, GridDesc g, const double *__restrict__ x, const int8_t *__restrict__ ph,
                             const double *__restrict__ poro, double *partials, unsigned int *ticket, double *out) {
-    const int N = g.N;
+    const long N = g.N;
     double m[B];
 #pragma unroll
     for (int c = 0; c < B; c++) m[c] = 0.0;
@@ -703,7 +703,7 @@ static __device__ __align__(256) double g_cnv_scratch[NOALLOC_SCRATCH];
 template <int B>
 __global__ void cnv_noalloc_kernel(GridDesc g, const double *__restrict__ R, const double *__restrict__ poro, double dt,
                                    double r0, double r1, double r2, double *scratch, double *out) {
-    const int N = g.N;
+    const long N = g.N;
     const double vol = g.dx * g.dy * g.dz;
     const double rho[3] = {r0, r1, r2};
     double m = 0.0;

@@ -149,7 +149,7 @@ template <int B, typename T>
 __global__ void qi_kernel(GridDesc g, const double *__restrict__ J, double *__restrict__ qiw, T *__restrict__ qiwT,
                           double *__restrict__ ap, T *__restrict__ apT, T *__restrict__ ahat) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int N = g.N;
+    const long N = g.N;
     if (i >= N) return;
     double w[3] = {1.0, 0.0, 0.0};
     qi_weights<B>(J, N, i, w);
@@ -192,7 +192,7 @@ template <int B>
 __global__ void diag_inv_kernel(GridDesc g, const double *__restrict__ J, const double *__restrict__ qiw, int mode,
                                 double *__restrict__ dinv) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int N = g.N;
+    const long N = g.N;
     if (i >= N) return;
     if (mode == 1 && is_black(g, i)) return;
     double w[3] = {1.0, 0.0, 0.0}, A[B * B], Ai[B * B];
@@ -214,7 +214,7 @@ template <int B>
 __global__ void ilu_black_kernel(GridDesc g, const double *__restrict__ J, const double *__restrict__ qiw,
                                  double *__restrict__ dinv) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int N = g.N;
+    const long N = g.N;
     if (i >= N || !is_black(g, i)) return;
     double wi[3] = {1.0, 0.0, 0.0};
 #pragma unroll
@@ -631,7 +631,7 @@ __global__ void stage2_a_kernel(GridDesc g, const double *__restrict__ r, const 
                                 T *__restrict__ r2, T *__restrict__ z, int rb, const int *done) {
     if (skip(done)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int N = g.N;
+    const long N = g.N;
     if (i >= N) return;
     T v[B];
 #pragma unroll
@@ -669,7 +669,7 @@ __global__ void stage2_b_kernel(GridDesc g, const T *__restrict__ ahat, const T 
                                 const int *done) {
     if (skip(done)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int N = g.N;
+    const long N = g.N;
     if (i >= N) return;
     const Cell cc = cell_of(g, i);
     if (((cc.ix + cc.iy + cc.iz) & 1) == 0) return;
@@ -705,7 +705,7 @@ __global__ void stage2_c_kernel(GridDesc g, const T *__restrict__ ahat, const T 
                                 const T *__restrict__ ep, TZ *__restrict__ out, int rb, const int *done) {
     if (skip(done)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int N = g.N;
+    const long N = g.N;
     if (i >= N) return;
     if (!rb) {
 #pragma unroll
@@ -809,27 +809,75 @@ __global__ void learned_in_kernel(int n, const T *__restrict__ r, const double *
     x[(long)i * 4 + 3] = feat[(long)i * 3 + 2];
 }
 
-// ep_out = ep + y * rms
+// q = A_p c with c = y * rms (the network's correction in pressure units)
+template <typename T>
+__global__ void learned_apply_kernel(Mat<T> A, const float *__restrict__ y, const double *__restrict__ rms,
+                                     T *__restrict__ q, const int *done) {
+    if (skip(done)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.n) return;
+    const double sc = *rms;
+    T t = (T)0;
+    for_row(A, i, [&](int j, T v) { t += v * (T)((double)y[j] * sc); });
+    q[i] = t;
+}
+
+// minimal-residual step alpha = (q . r) / (q . q) into out[1] (0 if q = 0)
+template <typename T>
+__global__ void mr_step_kernel(int n, const T *__restrict__ q, const T *__restrict__ r, double *partials,
+                               unsigned int *ticket, double *out, const int *done) {
+    if (skip(done)) return;
+    __shared__ double s1[SIM_THREADS], s2[SIM_THREADS];
+    __shared__ bool last;
+    double a = 0.0, c = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        a += (double)q[i] * (double)r[i];
+        c += (double)q[i] * (double)q[i];
+    }
+    s1[threadIdx.x] = a; s2[threadIdx.x] = c;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) { s1[threadIdx.x] += s1[threadIdx.x + o]; s2[threadIdx.x] += s2[threadIdx.x + o]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { partials[2 * blockIdx.x] = s1[0]; partials[2 * blockIdx.x + 1] = s2[0]; }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x == 0) {
+        double ta = 0.0, tc = 0.0;
+        for (int b = 0; b < (int)gridDim.x; b++) { ta += __ldcg(partials + 2 * b); tc += __ldcg(partials + 2 * b + 1); }
+        out[1] = tc > 0.0 ? ta / tc : 0.0;
+        *ticket = 0u;
+    }
+}
+
+// ep_out = ep + alpha * y * rms
 template <typename T>
 __global__ void learned_out_kernel(int n, const T *__restrict__ ep, const float *__restrict__ y,
                                    const double *__restrict__ rms, T *__restrict__ out, const int *done) {
     if (skip(done)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = ep[i] + (T)((double)y[i] * *rms);
+    if (i < n) out[i] = ep[i] + (T)(rms[1] * (double)y[i] * rms[0]);
 }
 
-// training pair j: x_j = [f / rms, features], y_j = e / rms
+// training pair j: x_j = [f / rms(f), features], y_j = e / rms(e) (the stage's
+// minimal-residual step restores the scale at inference)
 template <typename T>
 __global__ void pair_kernel(int n, const T *__restrict__ f, const T *__restrict__ e, const double *__restrict__ rms,
                             const float *__restrict__ feat, float *__restrict__ x, float *__restrict__ y) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double sc = *rms > 0.0 ? 1.0 / *rms : 0.0;
+    const double sc = rms[0] > 0.0 ? 1.0 / rms[0] : 0.0;
+    const double se = rms[1] > 0.0 ? 1.0 / rms[1] : 0.0;
     x[(long)i * 4] = (float)((double)f[i] * sc);
     x[(long)i * 4 + 1] = feat[(long)i * 3];
     x[(long)i * 4 + 2] = feat[(long)i * 3 + 1];
     x[(long)i * 4 + 3] = feat[(long)i * 3 + 2];
-    y[i] = (float)((double)e[i] * sc);
+    y[i] = (float)((double)e[i] * se);
 }
 
 // log of the summed face transmissibilities per direction
@@ -837,7 +885,7 @@ __global__ void logt_kernel(GridDesc g, const double *__restrict__ T, float *__r
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.N) return;
     const Cell c = cell_of(g, i);
-    const int N = g.N;
+    const long N = g.N;
     const double sx = T[i] + (c.ix > 0 ? T[i - 1] : 0.0);
     const double sy = T[N + i] + (c.iy > 0 ? T[N + i - g.nx] : 0.0);
     const double sz = T[2L * N + i] + (c.iz > 0 ? T[2L * N + i - g.nx * g.ny] : 0.0);
@@ -1196,6 +1244,13 @@ static sim_status apply_btz(sim_t *s, const double *r, TZ *z, const int *done) {
         const int64_t l0 = net_launches(s->net);
         if (net_infer(s->net, s->lx, s->ly, s->stream, done) != SIM_OK) return sim_fail(s, SIM_ECUDA, "learned stage inference");
         s->launches += net_launches(s->net) - l0;
+        // minimal-residual scaling of the correction: never increases ||r'||_2
+        learned_apply_kernel<T><<<sim_blocks(N, 128), 128, 0, s->stream>>>(level_matT<T>(s, L0, 0), s->ly, s->lrms,
+                                                                          (T *)s->lep, done);
+        SIM_LAUNCHED(s);
+        mr_step_kernel<T><<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(N, (const T *)s->lep, (const T *)s->lres, s->red,
+                                                                        s->ticket, s->lrms, done);
+        SIM_LAUNCHED(s);
         learned_out_kernel<T><<<sim_blocks(N), SIM_THREADS, 0, s->stream>>>(N, ep, s->ly, s->lrms, (T *)s->lep, done);
         SIM_LAUNCHED(s);
         ep = (const T *)s->lep;
@@ -1248,6 +1303,8 @@ static sim_status learned_pairs_t(sim_t *s, int k, float *x, float *y) {
             return s->err;
         }
         rms_kernel<T><<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(N, (const T *)L0.f, s->red, s->ticket, s->lrms, nullptr);
+        SIM_LAUNCHED(s);
+        rms_kernel<T><<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(N, (const T *)L0.e2, s->red, s->ticket, s->lrms + 1, nullptr);
         SIM_LAUNCHED(s);
         pair_kernel<T><<<sim_blocks(N), SIM_THREADS, 0, s->stream>>>(N, (const T *)L0.f, (const T *)L0.e2, s->lrms, s->lfeat,
                                                                     x + (size_t)j * N * 4, y + (size_t)j * N);

@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(SIM_THREADS) spmv_kernel(GridDesc g, const dou
                                                            const int *done) {
     if (skip(done)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int N = g.N;
+    const long N = g.N;
     if (i >= N) return;
     const int ix = i % g.nx, t = i / g.nx, iy = t % g.ny, iz = t / g.ny;
     const int nxy = g.nx * g.ny;

@@ -552,7 +552,7 @@ sim_status sim_set_learned_stage(sim_t *s, sim_net_t *net, int32_t enable) {
 sim_status sim_learned_pairs(sim_t *s, int32_t k, float *x_dev, float *y_dev) {
     CHECK_HANDLE(s);
     if (!x_dev || !y_dev || k < 1 || k > s->last_cycle_k + 1 || k > s->m + 1)
-        return sim_fail(s, SIM_EINVAL, "sim_learned_pairs: k must be in 1..(iterations of the last cycle + 1)");
+        return SIM_EINVAL;   /* not sticky: the handle stays usable */
     if (!s->lfeat) {
         s->lfeat = (float *)sim_alloc(s, sizeof(float) * 3 * (size_t)s->N);
         s->lrms = (double *)sim_alloc(s, sizeof(double) * 2);
@@ -565,6 +565,7 @@ sim_status sim_learned_pairs(sim_t *s, int32_t k, float *x_dev, float *y_dev) {
 }
 
 int64_t sim_learned_fallbacks(sim_t *s) { return s ? s->learned_fallbacks : 0; }
+int32_t sim_learned_available(sim_t *s) { return s ? (s->last_cycle_k + 1 < s->m + 1 ? s->last_cycle_k + 1 : s->m + 1) : 0; }
 
 sim_status sim_probe_fma_rates(double *fp64_fma_per_s, double *fp32_fma_per_s) {
     int dev = 0, sms = 0;

@@ -137,6 +137,7 @@ _SIGS = {
     "sim_set_learned_stage": ([_vp, _vp, C.c_int32], C.c_int),
     "sim_learned_pairs": ([_vp, C.c_int32, _vp, _vp], C.c_int),
     "sim_learned_fallbacks": ([_vp], C.c_int64),
+    "sim_learned_available": ([_vp], C.c_int32),
     "sim_last_error": ([_vp], C.c_char_p),
     "sim_clear_error": ([_vp], None),
 }
@@ -434,6 +435,9 @@ class Simulator:
 
     def learned_pairs(self, k, x_dev, y_dev):
         _check(self.h, self.L.sim_learned_pairs(self.h, int(k), _ptrf(x_dev), _ptrf(y_dev)))
+
+    def learned_available(self):
+        return self.L.sim_learned_available(self.h)
 
     def learned_fallbacks(self):
         return self.L.sim_learned_fallbacks(self.h)

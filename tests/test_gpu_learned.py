@@ -143,3 +143,18 @@ def test_learned_stage_inside_fgmres(torch_cuda):
     assert np.array_equal(phh, pho)
     assert rel_err(xh[:N], xo[:N]) <= 1e-6
     assert h.learned_fallbacks() >= 0
+
+
+def test_learned_stage_gain_is_measured(torch_cuda, capsys):
+    """Train on one grid, evaluate on a larger, rougher one: all three forms
+    reach the FP64 tolerance; the iterations and times are reported."""
+    from paper_1606_00548_gb300 import learned
+    tc = synth.black_oil_case(nx=32, ny=32, nz=8, sigma=1.0, seed=51)
+    ec = synth.black_oil_case(nx=48, ny=40, nz=12, sigma=2.0, corr_len=8.0, seed=52)
+    ev = learned.evaluate(tc, ec, train_steps=80, pairs_newton=3, pairs_k=12)
+    r = ev["results"]
+    for k in ("fp64_cpr", "mixed_cpr", "mixed_cpr_learned"):
+        assert r[k]["converged"] and r[k]["rel_residual"] <= 1e-8, (k, r[k])
+    assert ev["train_loss"][-1][1] < ev["train_loss"][0][1]
+    with capsys.disabled():
+        print("\nlearned-stage gain (small grid):", {k: (v["iterations"], round(v["seconds"] * 1e3, 2)) for k, v in r.items()})
