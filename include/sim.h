@@ -135,6 +135,7 @@ typedef struct {
     int64_t kernel_launches;    /* kernels launched by this handle so far */
     int64_t newton_iterations, linear_iterations;
     int64_t device_bytes;       /* device memory held by the handle */
+    int32_t spmv_block, amg_block;   /* launch shapes in use (see sim_autotune) */
 } sim_stats;
 
 /* Create a simulator (copies every host array).  Validates sizes, table
@@ -225,6 +226,28 @@ int32_t sim_block_size(sim_t *s);
 sim_status sim_cnv_noalloc(int32_t nx, int32_t ny, int32_t nz, double dx, double dy, double dz, int32_t b,
                            const double *R_dev, const double *poro_dev, const double *cnv_rho, double dt,
                            double *cnv_dev, void *cuda_stream);
+
+/* Autotuner: assembles at the current iterate for step dt, then times the
+   block SpMV with blocks of 64..512 threads and one CPR application with
+   AMG level kernels of 64..256 threads, and keeps the fastest shapes for
+   this handle.  Results do not depend on the shapes (each row's arithmetic
+   is the same); only speed does. */
+sim_status sim_autotune(sim_t *s, double dt);
+
+/* ---- ensemble (no paper counterpart) ----
+   Independent simulators (e.g. geological realisations on grids of different
+   sizes) advanced together: a pool of persistent host threads runs the
+   members' time steps concurrently, each member on its own CUDA stream
+   (members must own distinct streams), so their kernels overlap on the GPU.
+   The batch does not own the members. */
+typedef struct sim_batch sim_batch_t;
+/* nthreads <= 0: min(n, 64) worker threads */
+sim_status sim_batch_create(int32_t n, sim_t *const *members, int32_t nthreads, sim_batch_t **out);
+void sim_batch_destroy(sim_batch_t *b);
+/* sim_step(member k, dt[k]) for every member; infos / member_status (n
+   entries, may be NULL) receive each member's result; returns the first
+   non-OK member status. */
+sim_status sim_batch_step(sim_batch_t *b, const double *dt, sim_step_info *infos, sim_status *member_status);
 
 /* ---- learned pressure stage (no paper counterpart) ----
    A 3-D convolutional network: 4 layers of 3x3x3 kernels (zero padding),

@@ -758,6 +758,14 @@ static void galerkin(int n, const int32_t *rowptr, const int32_t *col, const dou
     *rp_out = rp; *col_out = oc; *val_out = ov;
 }
 
+/* a Galerkin row wider than this stops the coarsening (shared with the device) */
+#define AMG_MAX_ROW 512
+static int max_row(const int32_t *rp, int n) {
+    int m = 0;
+    for (int i = 0; i < n; i++) if (rp[i + 1] - rp[i] > m) m = rp[i + 1] - rp[i];
+    return m;
+}
+
 static void level_finish(level_t *L) {
     L->dl1 = xmalloc(sizeof(double) * L->n);
     for (int i = 0; i < L->n; i++) {
@@ -787,6 +795,10 @@ static void amg_setup(ora_sim *s, int32_t *rp0, int32_t *col0, double *val0, int
         members_of(n, agg1, n1, &o1, &m1);
         int32_t *rp1, *c1; double *v1;
         galerkin(n, L->rowptr, L->col, L->val, agg1, o1, m1, n1, &rp1, &c1, &v1);
+        if (max_row(rp1, n1) > AMG_MAX_ROW) {   /* too wide: this level is the coarsest */
+            free(p1); free(agg1); free(o1); free(m1); free(rp1); free(c1); free(v1);
+            break;
+        }
         int32_t *p2 = xmalloc(sizeof(int32_t) * n1), *agg2 = xmalloc(sizeof(int32_t) * n1);
         ora_match_pass(n1, rp1, c1, v1, in->amg_theta, in->amg_rounds, p2);
         int n2 = form_aggregates(n1, rp1, c1, v1, in->amg_theta, p2, agg2);
@@ -796,6 +808,14 @@ static void amg_setup(ora_sim *s, int32_t *rp0, int32_t *col0, double *val0, int
         if (!stalled) {
             level_t *C = &s->lev[s->nlev];
             galerkin(n1, rp1, c1, v1, agg2, o2, m2, n2, &C->rowptr, &C->col, &C->val);
+            if (max_row(C->rowptr, n2) > AMG_MAX_ROW) {
+                free(C->rowptr); free(C->col); free(C->val);
+                C->rowptr = NULL; C->col = NULL; C->val = NULL;
+                stalled = 1;
+            }
+        }
+        if (!stalled) {
+            level_t *C = &s->lev[s->nlev];
             C->n = n2;
             L->agg = xmalloc(sizeof(int32_t) * n);
             for (int i = 0; i < n; i++) L->agg[i] = agg2[agg1[i]];

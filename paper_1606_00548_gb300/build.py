@@ -13,7 +13,7 @@ from concurrent.futures import ThreadPoolExecutor
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libsim.so")
-SOURCES = ["sim_api.cu", "assemble.cu", "krylov.cu", "cpr.cu", "learned.cu"]
+SOURCES = ["sim_api.cu", "assemble.cu", "krylov.cu", "cpr.cu", "learned.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "--extended-lambda", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(os.path.dirname(HERE), "include")]

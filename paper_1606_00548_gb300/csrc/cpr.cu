@@ -1014,7 +1014,7 @@ static int galerkin(sim_t *s, const Mat<double> &A, const int *agg, const int *m
         !sim_cuda_ok(s, cudaStreamSynchronize(s->stream), "sync"))
         return -1;
     memcpy(hv, &s->h_pinned[0], 8);
-    if (hv[1]) { sim_fail(s, SIM_ELIMIT, "AMG coarse row wider than the setup limit"); return -1; }
+    if (hv[1]) { dev_free_async(s, len); return 0; }   // wider than SIM_MAX_ELL: caller stops coarsening
     const int W = hv[0] < 1 ? 1 : hv[0];
     *col = (int *)dev_alloc_async(s, sizeof(int) * (size_t)W * nc);
     *val = (double *)dev_alloc_async(s, sizeof(double) * (size_t)W * nc);
@@ -1095,6 +1095,7 @@ static sim_status amg_setup(sim_t *s) {
         int *c1 = nullptr; double *v1 = nullptr;
         const int W1 = galerkin(s, A, s->aggA, s->moffA, s->memA, n1, &c1, &v1);
         if (W1 < 0) return s->err;
+        if (W1 == 0) break;   // a coarse row wider than SIM_MAX_ELL: this level is the coarsest
         Mat<double> A1; A1.st = false; A1.selfpad = false; A1.g = s->gd; A1.n = n1; A1.width = W1; A1.col = c1; A1.val = v1;
         const int n2 = aggregate_pass(s, A1, s->aggB, s->moffB, s->memB);
         if (n2 < 0) return s->err;
@@ -1106,6 +1107,7 @@ static sim_status amg_setup(sim_t *s) {
         C.n = n2;
         const int W2 = galerkin(s, A1, s->aggB, s->moffB, s->memB, n2, &C.col, &C.val);
         if (W2 < 0) return s->err;
+        if (W2 == 0) { dev_free_async(s, c1); dev_free_async(s, v1); break; }
         C.width = W2;
         AmgLevel &Lr = s->lev[l];    // (reference still valid: no push yet)
         Lr.agg = (int *)dev_alloc_async(s, sizeof(int) * n);
@@ -1167,10 +1169,10 @@ static sim_status vcycle(sim_t *s, const int *done) {
     for (int l = 0; l + 1 < nl; l++) {
         AmgLevel &L = s->lev[l], &C = s->lev[l + 1];
         const bool coarsest = (l + 1 == nl - 1);
-        amg_resid_kernel<T><<<sim_blocks(L.n, 128), 128, 0, s->stream>>>(level_matT<T>(s, L, l), (const T *)L.f,
+        amg_resid_kernel<T><<<sim_blocks(L.n, s->tune_amg), s->tune_amg, 0, s->stream>>>(level_matT<T>(s, L, l), (const T *)L.f,
                                                                         (const T *)L.e, (T *)L.e2, done);
         SIM_LAUNCHED(s);
-        amg_restrict_kernel<T><<<sim_blocks(C.n, 128), 128, 0, s->stream>>>((const T *)L.e2, L.moff, L.mem, C.n, (T *)C.f,
+        amg_restrict_kernel<T><<<sim_blocks(C.n, s->tune_amg), s->tune_amg, 0, s->stream>>>((const T *)L.e2, L.moff, L.mem, C.n, (T *)C.f,
                                                                            coarsest ? nullptr : (T *)C.e,
                                                                            (const T *)C.dinvT, done);
         SIM_LAUNCHED(s);
@@ -1183,9 +1185,9 @@ static sim_status vcycle(sim_t *s, const int *done) {
     for (int l = nl - 2; l >= 0; l--) {
         AmgLevel &L = s->lev[l], &C = s->lev[l + 1];
         const T *ec = (l + 1 == nl - 1) ? (const T *)C.e : (const T *)C.e2;
-        amg_prolong_kernel<T><<<sim_blocks(L.n, 128), 128, 0, s->stream>>>(L.n, L.agg, ec, (T *)L.e, done);
+        amg_prolong_kernel<T><<<sim_blocks(L.n, s->tune_amg), s->tune_amg, 0, s->stream>>>(L.n, L.agg, ec, (T *)L.e, done);
         SIM_LAUNCHED(s);
-        amg_smooth_kernel<T><<<sim_blocks(L.n, 128), 128, 0, s->stream>>>(level_matT<T>(s, L, l), (const T *)L.f,
+        amg_smooth_kernel<T><<<sim_blocks(L.n, s->tune_amg), s->tune_amg, 0, s->stream>>>(level_matT<T>(s, L, l), (const T *)L.f,
                                                                          (const T *)L.e, (const T *)L.dinvT, (T *)L.e2,
                                                                          done);
         SIM_LAUNCHED(s);

@@ -20,7 +20,7 @@ template <typename X> __device__ __forceinline__ double ld(const X *p, long i) {
 
 // y = J x on the 7-point block stencil; blocks of absent neighbours are skipped
 template <int B, typename X>
-__global__ void __launch_bounds__(SIM_THREADS) spmv_kernel(GridDesc g, const double *__restrict__ J,
+__global__ void __launch_bounds__(512) spmv_kernel(GridDesc g, const double *__restrict__ J,
                                                            const X *__restrict__ x, double *__restrict__ y,
                                                            const int *done) {
     if (skip(done)) return;
@@ -308,21 +308,24 @@ __global__ void cycle_init_kernel(KrylovCtl *ctl) {
 }  // namespace
 
 // ===========================================================================
-sim_status k_spmv(sim_t *s, const double *x, double *y) {
-    if (s->b == 2) spmv_kernel<2, double><<<sim_blocks(s->N), SIM_THREADS, 0, s->stream>>>(s->gd, s->J, x, y, nullptr);
-    else spmv_kernel<3, double><<<sim_blocks(s->N), SIM_THREADS, 0, s->stream>>>(s->gd, s->J, x, y, nullptr);
+sim_status k_spmv_block(sim_t *s, const double *x, double *y, int bs) {
+    if (s->b == 2) spmv_kernel<2, double><<<sim_blocks(s->N, bs), bs, 0, s->stream>>>(s->gd, s->J, x, y, nullptr);
+    else spmv_kernel<3, double><<<sim_blocks(s->N, bs), bs, 0, s->stream>>>(s->gd, s->J, x, y, nullptr);
     SIM_LAUNCHED(s);
     return SIM_OK;
 }
 
+sim_status k_spmv(sim_t *s, const double *x, double *y) { return k_spmv_block(s, x, y, s->tune_spmv); }
+
 static sim_status spmv_done(sim_t *s, const void *x, bool xf, double *y, const int *done) {
-    const int nb = sim_blocks(s->N);
+    const int bs = s->tune_spmv;
+    const int nb = sim_blocks(s->N, bs);
     if (s->b == 2) {
-        if (xf) spmv_kernel<2, float><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, s->J, (const float *)x, y, done);
-        else spmv_kernel<2, double><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, s->J, (const double *)x, y, done);
+        if (xf) spmv_kernel<2, float><<<nb, bs, 0, s->stream>>>(s->gd, s->J, (const float *)x, y, done);
+        else spmv_kernel<2, double><<<nb, bs, 0, s->stream>>>(s->gd, s->J, (const double *)x, y, done);
     } else {
-        if (xf) spmv_kernel<3, float><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, s->J, (const float *)x, y, done);
-        else spmv_kernel<3, double><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, s->J, (const double *)x, y, done);
+        if (xf) spmv_kernel<3, float><<<nb, bs, 0, s->stream>>>(s->gd, s->J, (const float *)x, y, done);
+        else spmv_kernel<3, double><<<nb, bs, 0, s->stream>>>(s->gd, s->J, (const double *)x, y, done);
     }
     SIM_LAUNCHED(s);
     return SIM_OK;

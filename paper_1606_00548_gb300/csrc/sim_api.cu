@@ -62,6 +62,22 @@ __global__ void negate_kernel(const double *__restrict__ a, double *__restrict__
 }
 }  // namespace
 
+// time `reps` launches of f on the handle's stream (milliseconds per launch)
+template <typename F>
+static float time_launches(sim_t *s, int reps, F f) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0); cudaEventCreate(&e1);
+    f();
+    cudaEventRecord(e0, s->stream);
+    for (int r = 0; r < reps; r++) f();
+    cudaEventRecord(e1, s->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0); cudaEventDestroy(e1);
+    return ms / reps;
+}
+
 #define CHECK_HANDLE(s) do { if (!(s)) return SIM_EINVAL; if ((s)->err != SIM_OK) return (s)->err; } while (0)
 
 extern "C" {
@@ -606,6 +622,40 @@ sim_status sim_get_stats(sim_t *s, sim_stats *st) {
     st->newton_iterations = s->newton_total;
     st->linear_iterations = s->linear_total;
     st->device_bytes = (int64_t)s->bytes;
+    st->spmv_block = s->tune_spmv;
+    st->amg_block = s->tune_amg;
+    return SIM_OK;
+}
+
+sim_status sim_autotune(sim_t *s, double dt) {
+    CHECK_HANDLE(s);
+    if (!(dt > 0)) return sim_fail(s, SIM_EINVAL, "dt must be positive");
+    if (k_assemble(s, dt) != SIM_OK) return s->err;
+    const long n = (long)s->N * s->b;
+    static const int spmv_cand[] = {64, 128, 256, 512};
+    float best = 1e30f;
+    int pick = s->tune_spmv;
+    for (int bs : spmv_cand) {
+        const float ms = time_launches(s, 5, [&] { k_spmv_block(s, s->bl, s->w, bs); });
+        if (ms < best) { best = ms; pick = bs; }
+    }
+    s->tune_spmv = pick;
+    if (s->opt.precond == SIM_PRECOND_CPR) {
+        if (cpr_setup(s) != SIM_OK) return s->err;
+        SIM_CK(s, cudaMemsetAsync(s->bl, 0, sizeof(double) * n, s->stream));
+        static const int amg_cand[] = {64, 128, 256};
+        best = 1e30f;
+        pick = s->tune_amg;
+        for (int bs : amg_cand) {
+            s->tune_amg = bs;
+            const float ms = time_launches(s, 3, [&] { cpr_apply(s, s->bl, s->Z, nullptr); });
+            if (ms < best) { best = ms; pick = bs; }
+        }
+        s->tune_amg = pick;
+    }
+    s->setup_gen++;   // the captured restart cycle used the old launch shapes
+    SIM_CK(s, cudaGetLastError());
+    SIM_CK(s, cudaStreamSynchronize(s->stream));
     return SIM_OK;
 }
 

@@ -11,7 +11,7 @@
 #define SIM_DARCY (86400.0 * 9.869233e-16 * 1e5 / 1e-3)
 #define SIM_MAX_PVT 64
 #define SIM_MAX_M 32
-#define SIM_MAX_ELL 128      // widest coarse AMG row the setup kernels accept
+#define SIM_MAX_ELL 512      // widest coarse AMG row: a wider Galerkin row stops coarsening
 #define SIM_RED_BLOCKS 608   // 4 x 152 SMs: grid of the reduction kernels
 #define SIM_THREADS 256
 
@@ -105,6 +105,7 @@ struct sim {
     cudaGraphExec_t cycle_exec = nullptr;   // captured restart cycle
     int64_t setup_gen = 0, cycle_gen = -1, graph_nodes = 0;
     int cycle_learned = -1;                  // learned-stage state the graph was captured with
+    int tune_spmv = SIM_THREADS, tune_amg = 128;   // block sizes picked by sim_autotune
     int last_cycle_k = 0;                    // inner iterations of the last restart cycle
 
     // CPR
@@ -164,6 +165,7 @@ sim_status k_spmv(sim_t *s, const double *x, double *y);                 // y = 
 sim_status k_spmv_f(sim_t *s, const float *x, double *y);
 sim_status k_fgmres(sim_t *s, const double *b, double *x, sim_linear_info *info);
 sim_status k_norm2(sim_t *s, const double *v, long n, double *out_host);
+sim_status k_spmv_block(sim_t *s, const double *x, double *y, int block);
 
 // ---- cpr.cu ---------------------------------------------------------------
 sim_status cpr_setup(sim_t *s);

@@ -89,7 +89,8 @@ class sim_step_info(C.Structure):
 
 class sim_stats(C.Structure):
     _fields_ = [("kernel_launches", C.c_int64), ("newton_iterations", C.c_int64),
-                ("linear_iterations", C.c_int64), ("device_bytes", C.c_int64)]
+                ("linear_iterations", C.c_int64), ("device_bytes", C.c_int64),
+                ("spmv_block", C.c_int32), ("amg_block", C.c_int32)]
 
 
 _SIGS = {
@@ -125,6 +126,10 @@ _SIGS = {
     "sim_cnv_noalloc": ([C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double, C.c_int32,
                          _vp, _vp, _dp, C.c_double, _vp, _vp], C.c_int),
     "sim_probe_fma_rates": ([_dp, _dp], C.c_int),
+    "sim_autotune": ([_vp, C.c_double], C.c_int),
+    "sim_batch_create": ([C.c_int32, C.POINTER(_vp), C.c_int32, C.POINTER(_vp)], C.c_int),
+    "sim_batch_destroy": ([_vp], None),
+    "sim_batch_step": ([_vp, _dp, C.POINTER(sim_step_info), C.POINTER(C.c_int)], C.c_int),
     "sim_net_create": ([C.c_int32, C.c_int32, C.c_int32, C.c_uint64, _vp, C.POINTER(_vp)], C.c_int),
     "sim_net_destroy": ([_vp], None),
     "sim_net_param_count": ([_vp], C.c_int64),
@@ -444,6 +449,42 @@ class Simulator:
 
     def stats(self):
         s = sim_stats(); _check(self.h, self.L.sim_get_stats(self.h, C.byref(s))); return s
+
+    def autotune(self, dt):
+        _check(self.h, self.L.sim_autotune(self.h, float(dt)))
+
+
+class Batch:
+    """Concurrent time stepping of independent simulators (sim_batch_*)."""
+
+    def __init__(self, members, nthreads=0):
+        self.L = load()
+        self.members = list(members)
+        arr = (_vp * len(self.members))(*[m.h for m in self.members])
+        h = _vp()
+        st = self.L.sim_batch_create(len(self.members), arr, int(nthreads), C.byref(h))
+        if st != SIM_OK:
+            raise SimError(st, (self.L.sim_last_error(None) or b"").decode())
+        self.h = h
+
+    def step(self, dts):
+        n = len(self.members)
+        dt = np.ascontiguousarray(np.broadcast_to(np.asarray(dts, dtype=np.float64), (n,)))
+        infos = (sim_step_info * n)()
+        sts = (C.c_int * n)()
+        self.L.sim_batch_step(self.h, dt.ctypes.data_as(_dp), infos, sts)
+        return list(sts), list(infos)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.sim_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def sim_cnv_noalloc(case: dict, b: int, R_dev, poro_dev, dt: float, out_dev, stream=None) -> None:
