@@ -58,7 +58,7 @@ class OraInput(C.Structure):
         ("amg_theta", C.c_double), ("amg_rounds", C.c_int32), ("amg_coarse_max", C.c_int32),
         ("amg_max_levels", C.c_int32),
         ("chop_ds", C.c_double), ("chop_dp", C.c_double), ("max_cuts", C.c_int32),
-        ("amg_cycles", C.c_int32),
+        ("amg_cycles", C.c_int32), ("decouple", C.c_int32), ("cpr_stages", C.c_int32),
     ]
 
 
@@ -167,7 +167,7 @@ def make_input(case: dict, keep: list, **solver_overrides) -> OraInput:
     for name in ("newton_tol", "lin_tol", "amg_theta", "chop_ds", "chop_dp"):
         setattr(inp, name, float(sv[name]))
     for name in ("newton_max", "gmres_m", "gmres_max_restarts", "precond", "stage2", "amg_rounds",
-                 "amg_coarse_max", "amg_max_levels", "max_cuts", "amg_cycles"):
+                 "amg_coarse_max", "amg_max_levels", "max_cuts", "amg_cycles", "decouple", "cpr_stages"):
         setattr(inp, name, int(sv[name]))
     return inp
 

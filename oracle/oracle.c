@@ -206,7 +206,7 @@ struct ora_sim {
     double qtot[3], cum_well[3];
     cellprops *props;
     /* CPR */
-    double *qiw, *ahat, *dinv;
+    double *qiw, *lsc, *ahat, *dinv;   /* qiw: first row of the per-cell left scaling lsc */
     int nlev;
     level_t lev[32];
     int precond_ready;
@@ -308,6 +308,7 @@ ora_sim *ora_create(const ora_input *in) {
     s->J = xmalloc(sizeof(double) * (size_t)N * 7 * b * b);
     s->props = xmalloc(sizeof(cellprops) * N);
     s->qiw = xmalloc(sizeof(double) * N * b);
+    s->lsc = xmalloc(sizeof(double) * (size_t)N * b * b);
     s->ahat = xmalloc(sizeof(double) * (size_t)N * 7 * b * b);
     s->dinv = xmalloc(sizeof(double) * (size_t)N * b * b);
     int m = in->gmres_m, n = N * b;
@@ -340,7 +341,7 @@ void ora_destroy(ora_sim *s) {
     for (int a = 0; a < 3; a++) free(s->T[a]);
     free(s->depth); free(s->perf_cell); free(s->perf_type); free(s->perf_wi); free(s->perf_zh); free(s->perf_bhp);
     free(s->x); free(s->x_old); free(s->ph); free(s->ph_old); free(s->mold); free(s->R); free(s->J); free(s->props);
-    free(s->qiw); free(s->ahat); free(s->dinv);
+    free(s->qiw); free(s->lsc); free(s->ahat); free(s->dinv);
     free(s->V); free(s->Z); free(s->w); free(s->r); free(s->tmp); free(s->tmp2); free(s->tmp3);
     free(s->H); free(s->g); free(s->cs); free(s->sn); free(s->y);
     free(s);
@@ -881,31 +882,43 @@ void ora_precond_setup(ora_sim *s) {
         return;
     }
     if (in->precond != 2) { s->precond_ready = 1; return; }
-    /* quasi-IMPES weights from the diagonal block D = J_ii */
+    /* decoupling: a per-cell left scaling L_i of the cell's equations.
+       quasi-IMPES: the pressure (first) row becomes w^T times the rows with
+       w = (1, -d_ps D_ss^-1) from the diagonal block D = J_ii, the other rows
+       stay; ABF: L_i = D^-1 (alternate block factorisation). */
     for (int i = 0; i < N; i++) {
         const double *D = JB(s, i, 0);
-        double *w = &s->qiw[i * b];
-        w[0] = 1.0;
-        if (b == 2) {
-            w[1] = -(D[1] / D[3]);
+        double *L = &s->lsc[(size_t)i * b * b];
+        if (in->decouple == 1) {
+            inv_block(b, D, L);
         } else {
-            double det = D[4] * D[8] - D[5] * D[7];
-            w[1] = (D[2] * D[7] - D[1] * D[8]) / det;
-            w[2] = (D[1] * D[5] - D[2] * D[4]) / det;
+            double w1, w2 = 0.0;
+            if (b == 2) {
+                w1 = -(D[1] / D[3]);
+            } else {
+                double det = D[4] * D[8] - D[5] * D[7];
+                w1 = (D[2] * D[7] - D[1] * D[8]) / det;
+                w2 = (D[1] * D[5] - D[2] * D[4]) / det;
+            }
+            for (int t = 0; t < b * b; t++) L[t] = (t / b == t % b) ? 1.0 : 0.0;
+            L[1] = w1;
+            if (b == 3) L[2] = w2;
         }
+        for (int c = 0; c < b; c++) s->qiw[i * b + c] = L[c];
     }
-    /* decoupled matrix: pressure row replaced by the weighted row sum */
+    /* decoupled matrix Ahat_ij = L_i J_ij (products summed in row order) */
     for (int i = 0; i < N; i++) {
-        const double *w = &s->qiw[i * b];
+        const double *L = &s->lsc[(size_t)i * b * b];
         for (int d = 0; d < 7; d++) {
             const double *A = JB(s, i, d);
             double *Ah = AH(s, i, d);
-            memcpy(Ah, A, sizeof(double) * b * b);
-            for (int c = 0; c < b; c++) {
-                double t = A[c] + w[1] * A[b + c];
-                if (b == 3) t = t + w[2] * A[2 * b + c];
-                Ah[c] = t;
-            }
+            for (int r = 0; r < b; r++)
+                for (int c = 0; c < b; c++) {
+                    double t = L[r * b] * A[c];
+                    t = t + L[r * b + 1] * A[b + c];
+                    if (b == 3) t = t + L[r * b + 2] * A[2 * b + c];
+                    Ah[r * b + c] = t;
+                }
         }
     }
     /* pressure block as CSR with ascending columns: -z, -y, -x, centre, +x, +y, +z */
@@ -950,6 +963,59 @@ void ora_precond_setup(ora_sim *s) {
     s->precond_ready = 1;
 }
 
+/* stage F: one application of red-black block ILU(0) (or block-Jacobi) of
+   the decoupled matrix: out = M_F^-1 rhs */
+static void stage_f(ora_sim *s, const double *rhs, double *out) {
+    int N = s->N, b = s->b;
+    double t[3], u[3];
+    if (s->in.stage2 != 1) {
+        for (int i = 0; i < N; i++) matvec_block(b, &s->dinv[(size_t)i * b * b], &rhs[i * b], &out[i * b]);
+        return;
+    }
+    for (int i = 0; i < N; i++) {           /* forward, red */
+        int ix, iy, iz; cell_ijk(s, i, &ix, &iy, &iz);
+        if ((ix + iy + iz) & 1) continue;
+        matvec_block(b, &s->dinv[(size_t)i * b * b], &rhs[i * b], &out[i * b]);
+    }
+    for (int i = 0; i < N; i++) {           /* forward, black */
+        int ix, iy, iz; cell_ijk(s, i, &ix, &iy, &iz);
+        if (!((ix + iy + iz) & 1)) continue;
+        for (int c = 0; c < b; c++) t[c] = rhs[i * b + c];
+        for (int d = 1; d < 7; d++) {
+            int k = nbr(s, i, d);
+            if (k < 0) continue;
+            matvec_block(b, AH(s, i, d), &out[k * b], u);
+            for (int c = 0; c < b; c++) t[c] -= u[c];
+        }
+        matvec_block(b, &s->dinv[(size_t)i * b * b], t, &out[i * b]);
+    }
+    for (int i = 0; i < N; i++) {           /* backward, red (black unchanged) */
+        int ix, iy, iz; cell_ijk(s, i, &ix, &iy, &iz);
+        if ((ix + iy + iz) & 1) continue;
+        for (int c = 0; c < b; c++) t[c] = 0.0;
+        for (int d = 1; d < 7; d++) {
+            int k = nbr(s, i, d);
+            if (k < 0) continue;
+            matvec_block(b, AH(s, i, d), &out[k * b], u);
+            for (int c = 0; c < b; c++) t[c] += u[c];
+        }
+        matvec_block(b, &s->dinv[(size_t)i * b * b], t, u);
+        for (int c = 0; c < b; c++) out[i * b + c] -= u[c];
+    }
+}
+
+/* stage P: AMG V-cycles on fp, each on the residual left by the previous ones */
+static void stage_p(ora_sim *s, const double *fp, double *ep) {
+    vcycle(s, 0, fp, ep);
+    for (int c = 1; c < s->in.amg_cycles; c++) {
+        level_t *L0 = &s->lev[0];
+        double *rp = L0->t2, *dp = L0->t3;
+        csr_residual(L0, fp, ep, rp);
+        vcycle(s, 0, rp, dp);
+        for (int i = 0; i < s->N; i++) ep[i] += dp[i];
+    }
+}
+
 void ora_precond_apply(ora_sim *s, const double *r, double *z) {
     int N = s->N, b = s->b;
     const ora_input *in = &s->in;
@@ -960,24 +1026,26 @@ void ora_precond_apply(ora_sim *s, const double *r, double *z) {
         return;
     }
     double *rh = s->tmp, *ep = s->tmp2, *fp = s->tmp3;
-    /* decoupled residual, pressure part */
+    /* decoupled residual rh = L r */
     for (int i = 0; i < N; i++) {
-        const double *w = &s->qiw[i * b];
-        for (int c = 0; c < b; c++) rh[i * b + c] = r[i * b + c];
-        double t = r[i * b] + w[1] * r[i * b + 1];
-        if (b == 3) t = t + w[2] * r[i * b + 2];
-        rh[i * b] = t;
-        fp[i] = t;
+        const double *L = &s->lsc[(size_t)i * b * b];
+        for (int rr = 0; rr < b; rr++) {
+            double t = L[rr * b] * r[i * b];
+            t = t + L[rr * b + 1] * r[i * b + 1];
+            if (b == 3) t = t + L[rr * b + 2] * r[i * b + 2];
+            rh[i * b + rr] = t;
+        }
     }
-    /* stage P: AMG V-cycles on the pressure block, each on the residual left by the previous ones */
-    vcycle(s, 0, fp, ep);
-    for (int c = 1; c < in->amg_cycles; c++) {
-        level_t *L0 = &s->lev[0];
-        double *rp = L0->t2, *dp = L0->t3;
-        csr_residual(L0, fp, ep, rp);
-        vcycle(s, 0, rp, dp);
-        for (int i = 0; i < N; i++) ep[i] += dp[i];
+    double *x0 = NULL;
+    if (in->cpr_stages == 3) {
+        /* CPR-FPF: a stage F first; stage P then works on what it leaves */
+        x0 = xmalloc(sizeof(double) * N * b);
+        stage_f(s, rh, x0);
+        block_spmv(s, s->ahat, x0, z);                       /* z = Ahat x0 */
+        for (int t = 0; t < N * b; t++) rh[t] -= z[t];        /* rh = residual after the first F */
     }
+    for (int i = 0; i < N; i++) fp[i] = rh[i * b];
+    stage_p(s, fp, ep);
     /* residual of the decoupled system after stage P (pressure columns only) */
     for (int i = 0; i < N; i++) {
         for (int c = 0; c < b; c++) {
@@ -991,43 +1059,12 @@ void ora_precond_apply(ora_sim *s, const double *r, double *z) {
         }
     }
     memcpy(rh, z, sizeof(double) * N * b);
-    /* stage F */
-    if (in->stage2 == 1) {
-        double t[3], u[3];
-        for (int i = 0; i < N; i++) {           /* forward, red */
-            int ix, iy, iz; cell_ijk(s, i, &ix, &iy, &iz);
-            if ((ix + iy + iz) & 1) continue;
-            matvec_block(b, &s->dinv[(size_t)i * b * b], &rh[i * b], &z[i * b]);
-        }
-        for (int i = 0; i < N; i++) {           /* forward, black */
-            int ix, iy, iz; cell_ijk(s, i, &ix, &iy, &iz);
-            if (!((ix + iy + iz) & 1)) continue;
-            for (int c = 0; c < b; c++) t[c] = rh[i * b + c];
-            for (int d = 1; d < 7; d++) {
-                int k = nbr(s, i, d);
-                if (k < 0) continue;
-                matvec_block(b, AH(s, i, d), &z[k * b], u);
-                for (int c = 0; c < b; c++) t[c] -= u[c];
-            }
-            matvec_block(b, &s->dinv[(size_t)i * b * b], t, &z[i * b]);
-        }
-        for (int i = 0; i < N; i++) {           /* backward, red (black unchanged) */
-            int ix, iy, iz; cell_ijk(s, i, &ix, &iy, &iz);
-            if ((ix + iy + iz) & 1) continue;
-            for (int c = 0; c < b; c++) t[c] = 0.0;
-            for (int d = 1; d < 7; d++) {
-                int k = nbr(s, i, d);
-                if (k < 0) continue;
-                matvec_block(b, AH(s, i, d), &z[k * b], u);
-                for (int c = 0; c < b; c++) t[c] += u[c];
-            }
-            matvec_block(b, &s->dinv[(size_t)i * b * b], t, u);
-            for (int c = 0; c < b; c++) z[i * b + c] -= u[c];
-        }
-    } else {
-        for (int i = 0; i < N; i++) matvec_block(b, &s->dinv[(size_t)i * b * b], &rh[i * b], &z[i * b]);
-    }
+    stage_f(s, rh, z);
     for (int i = 0; i < N; i++) z[i * b] += ep[i];
+    if (x0) {
+        for (int t = 0; t < N * b; t++) z[t] += x0[t];
+        free(x0);
+    }
 }
 
 void ora_get_qi(const ora_sim *s, double *w, double *ap) {

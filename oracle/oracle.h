@@ -56,6 +56,8 @@ typedef struct {
     double amg_theta; int32_t amg_rounds, amg_coarse_max, amg_max_levels;
     double chop_ds, chop_dp; int32_t max_cuts;
     int32_t amg_cycles;            /* V-cycles per stage-P application (>= 1) */
+    int32_t decouple;              /* 0 quasi-IMPES, 1 ABF (alternate block factorisation) */
+    int32_t cpr_stages;            /* 2: P then F; 3: F, P, F (CPR-FPF) */
 } ora_input;
 
 typedef struct {

@@ -128,6 +128,7 @@ def default_solver(**kw):
         newton_tol=1e-10, newton_max=20, lin_tol=1e-8, gmres_m=30, gmres_max_restarts=20,
         precond=2, stage2=1, amg_theta=0.25, amg_rounds=4, amg_coarse_max=256,
         amg_max_levels=16, chop_ds=0.2, chop_dp=50.0, max_cuts=8, amg_cycles=1,
+        decouple=0, cpr_stages=2,
     )
     s.update(kw)
     return s

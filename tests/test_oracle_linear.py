@@ -12,7 +12,12 @@
 * quasi-IMPES decoupling removes the saturation columns of the pressure
   row of every diagonal block;
 * red-black block ILU(0): (D + L) D^-1 (D + U) reproduces the decoupled
-  matrix on its 7-point block pattern (the defining property of ILU(0)).
+  matrix on its 7-point block pattern (the defining property of ILU(0));
+* ABF decoupling (Sec. 3.2): the scaled diagonal block D_ii^-1 J_ii is the
+  identity, so the pressure row of every decoupled diagonal block is e_0;
+* CPR-FPF: the three-stage operator is the composition
+  z = x0 + M_2 (r - J x0), x0 = stage F of L r, where M_2 is the two-stage
+  operator on the same hierarchy (every stage is linear in its input).
 """
 import numpy as np
 import pytest
@@ -52,9 +57,11 @@ def test_fgmres_cpr_matches_dense_solve(oracle_lib, name, case, dt):
     ("bo", synth.black_oil_case(nx=3, ny=3, nz=2, seed=24), 10.0)])
 def test_preconditioners_give_same_solution(oracle_lib, name, case, dt):
     sols, its = [], []
-    for pc, st in [(0, 0), (1, 0), (2, 0), (2, 1)]:
+    for pc, st, dec, stg in [(0, 0, 0, 2), (1, 0, 0, 2), (2, 0, 0, 2), (2, 1, 0, 2), (2, 1, 1, 2), (2, 1, 0, 3),
+                             (2, 0, 1, 3)]:
         # m >= n: unrestarted, so even the unpreconditioned solve terminates
-        o = assembled(case, dt, lin_tol=1e-11, precond=pc, stage2=st, gmres_m=60, gmres_max_restarts=3)
+        o = assembled(case, dt, lin_tol=1e-11, precond=pc, stage2=st, decouple=dec, cpr_stages=stg, gmres_m=60,
+                      gmres_max_restarts=3)
         x, info = o.linear_solve(-o.residual())
         assert info.converged
         sols.append(x); its.append(info.iterations)
@@ -214,3 +221,37 @@ def test_red_black_ilu0_reproduces_pattern(oracle_lib, name, case, dt):
     Ad = dense_from_blocks(Ah, nx, ny, nz)
     mask = np.kron(pattern, np.ones((b, b), bool))
     assert np.abs((M - Ad)[mask]).max() <= 1e-10 * np.abs(Ad).max()
+
+
+@pytest.mark.parametrize("name,case,dt", tiny_cases())
+def test_abf_scaled_diagonal_is_identity(oracle_lib, name, case, dt):
+    o = assembled(case, dt, decouple=1)
+    o.precond_setup()
+    J = o.jacobian()
+    w, ap = o.qi()
+    w = w.reshape(o.N, o.b)
+    # first row of D_ii^-1 times D_ii is e_0 (the inverse computed by cofactors)
+    row = np.einsum("ir,irc->ic", w, J[:, 0])
+    e0 = np.zeros(o.b); e0[0] = 1.0
+    assert np.abs(row - e0).max() <= 1e-12
+    assert np.abs(ap[:, 0] - 1.0).max() <= 1e-12
+    # and the row is the first row of the true inverse
+    assert np.allclose(w, np.linalg.inv(J[:, 0])[:, 0, :], rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("name,case,dt", tiny_cases())
+@pytest.mark.parametrize("decouple", [0, 1])
+def test_fpf_is_the_composition_of_its_stages(oracle_lib, name, case, dt, decouple):
+    """Block-Jacobi stage F: x0 = (L J_ii)^-1 L r = J_ii^-1 r, for either L."""
+    o2 = assembled(case, dt, decouple=decouple, cpr_stages=2, stage2=0)
+    o3 = assembled(case, dt, decouple=decouple, cpr_stages=3, stage2=0)
+    N, b = o2.N, o2.b
+    J = o2.jacobian()
+    A = dense_from_blocks(J, case["nx"], case["ny"], case["nz"])
+    r = np.random.default_rng(7).standard_normal(N * b)
+    x0 = np.linalg.solve(J[:, 0], r.reshape(N, b)[:, :, None])[:, :, 0].reshape(-1)
+    z3 = o3.precond_apply(r)
+    zc = x0 + o2.precond_apply(r - A @ x0)
+    assert np.abs(z3 - zc).max() <= 1e-10 * np.abs(zc).max()
+    # and it differs from the two-stage operator (the first stage does something)
+    assert np.abs(z3 - o2.precond_apply(r)).max() > 1e-6 * np.abs(zc).max()
