@@ -59,6 +59,8 @@ class OraInput(C.Structure):
         ("amg_max_levels", C.c_int32),
         ("chop_ds", C.c_double), ("chop_dp", C.c_double), ("max_cuts", C.c_int32),
         ("amg_cycles", C.c_int32), ("decouple", C.c_int32), ("cpr_stages", C.c_int32),
+        ("krylov", C.c_int32), ("lin_max_iter", C.c_int32), ("forcing", C.c_int32),
+        ("ew_gamma", C.c_double), ("ew_beta", C.c_double), ("theta_max", C.c_double),
     ]
 
 
@@ -108,6 +110,7 @@ def lib():
         L.ora_newton_step.argtypes = [vp, C.c_double, C.POINTER(NewtonInfo)]
         L.ora_newton_solve.argtypes = [vp, C.c_double, C.POINTER(NewtonInfo)]
         L.ora_step.argtypes = [vp, C.c_double, C.POINTER(StepInfo)]
+        L.ora_forcing_history.argtypes = [vp, _dp, _dp, _dp, C.c_int]
         L.ora_component_mass.argtypes = [vp, _dp]
         L.ora_cumulative_well_mass.argtypes = [vp, _dp]
         L.ora_well_rates.argtypes = [vp, _dp]
@@ -164,10 +167,11 @@ def make_input(case: dict, keep: list, **solver_overrides) -> OraInput:
     for c in range(3):
         inp.cnv_rho[c] = case["cnv_rho"][c]
     sv = dict(case["solver"]); sv.update(solver_overrides)
-    for name in ("newton_tol", "lin_tol", "amg_theta", "chop_ds", "chop_dp"):
+    for name in ("newton_tol", "lin_tol", "amg_theta", "chop_ds", "chop_dp", "ew_gamma", "ew_beta", "theta_max"):
         setattr(inp, name, float(sv[name]))
     for name in ("newton_max", "gmres_m", "gmres_max_restarts", "precond", "stage2", "amg_rounds",
-                 "amg_coarse_max", "amg_max_levels", "max_cuts", "amg_cycles", "decouple", "cpr_stages"):
+                 "amg_coarse_max", "amg_max_levels", "max_cuts", "amg_cycles", "decouple", "cpr_stages",
+                 "krylov", "lin_max_iter", "forcing"):
         setattr(inp, name, int(sv[name]))
     return inp
 
@@ -288,6 +292,12 @@ class Oracle:
         info = NewtonInfo()
         rc = self.L.ora_newton_solve(self.h, float(dt), C.byref(info))
         return rc, info
+
+    def forcing_history(self):
+        th, bn, rn = np.zeros(64), np.zeros(64), np.zeros(64)
+        k = self.L.ora_forcing_history(self.h, th.ctypes.data_as(_dp), bn.ctypes.data_as(_dp),
+                                       rn.ctypes.data_as(_dp), 64)
+        return th[:k], bn[:k], rn[:k]
 
     def step(self, dt):
         info = StepInfo()

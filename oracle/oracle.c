@@ -213,6 +213,10 @@ struct ora_sim {
     /* Krylov workspace */
     double *V, *Z, *w, *r, *tmp, *tmp2, *tmp3;
     double *H, *g, *cs, *sn, *y;
+    double theta;                  /* forcing term of the next linear solve */
+    int nhist;                     /* forcing history of the last Newton solve */
+    double hist_theta[64], hist_b[64], hist_r[64];
+    double *rlin;                  /* linear residual b - A dx left by the last Newton solve */
 };
 
 static void *xmalloc(size_t n) { void *p = calloc(n ? n : 1, 1); if (!p) { fprintf(stderr, "oracle: out of memory\n"); abort(); } return p; }
@@ -312,9 +316,11 @@ ora_sim *ora_create(const ora_input *in) {
     s->ahat = xmalloc(sizeof(double) * (size_t)N * 7 * b * b);
     s->dinv = xmalloc(sizeof(double) * (size_t)N * b * b);
     int m = in->gmres_m, n = N * b;
-    s->V = xmalloc(sizeof(double) * (size_t)(m + 1) * n);
-    s->Z = xmalloc(sizeof(double) * (size_t)m * n);
+    s->V = xmalloc(sizeof(double) * (size_t)(m + 1 > 5 ? m + 1 : 5) * n);    /* BiCGSTAB uses 5 */
+    s->Z = xmalloc(sizeof(double) * (size_t)(m > 2 ? m : 2) * n);
     s->w = xmalloc(sizeof(double) * n); s->r = xmalloc(sizeof(double) * n);
+    s->rlin = xmalloc(sizeof(double) * n);
+    s->theta = in->lin_tol;
     s->tmp = xmalloc(sizeof(double) * n); s->tmp2 = xmalloc(sizeof(double) * n); s->tmp3 = xmalloc(sizeof(double) * n);
     s->H = xmalloc(sizeof(double) * (m + 1) * (m + 1));
     s->g = xmalloc(sizeof(double) * (m + 1)); s->cs = xmalloc(sizeof(double) * (m + 1));
@@ -342,7 +348,7 @@ void ora_destroy(ora_sim *s) {
     free(s->depth); free(s->perf_cell); free(s->perf_type); free(s->perf_wi); free(s->perf_zh); free(s->perf_bhp);
     free(s->x); free(s->x_old); free(s->ph); free(s->ph_old); free(s->mold); free(s->R); free(s->J); free(s->props);
     free(s->qiw); free(s->lsc); free(s->ahat); free(s->dinv);
-    free(s->V); free(s->Z); free(s->w); free(s->r); free(s->tmp); free(s->tmp2); free(s->tmp3);
+    free(s->V); free(s->Z); free(s->w); free(s->r); free(s->rlin); free(s->tmp); free(s->tmp2); free(s->tmp3);
     free(s->H); free(s->g); free(s->cs); free(s->sn); free(s->y);
     free(s);
 }
@@ -1093,16 +1099,19 @@ void ora_ilu_dinv(const ora_sim *s, double *dinv) { memcpy(dinv, s->dinv, sizeof
 /* ------------------------------------------------------------------------ */
 static double dot(const double *a, const double *b, int n) { double t = 0.0; for (int i = 0; i < n; i++) t += a[i] * b[i]; return t; }
 
+static int bicgstab(ora_sim *s, const double *bvec, double *x, ora_lin_info *info);
+
 int ora_linear_solve(ora_sim *s, const double *bvec, double *x, ora_lin_info *info) {
     const ora_input *in = &s->in;
+    if (in->krylov == 1) return bicgstab(s, bvec, x, info);
     int n = s->N * s->b, m = in->gmres_m;
     ora_lin_info li; memset(&li, 0, sizeof(li));
     if (!s->precond_ready) ora_precond_setup(s);
     double bn = sqrt(dot(bvec, bvec, n));
     li.b_norm = bn;
     for (int i = 0; i < n; i++) x[i] = 0.0;
-    if (bn == 0.0) { li.converged = 1; if (info) *info = li; return 0; }
-    double tol = in->lin_tol * bn;
+    if (bn == 0.0) { li.converged = 1; memcpy(s->r, bvec, sizeof(double) * n); if (info) *info = li; return 0; }
+    double tol = s->theta * bn;
     memcpy(s->r, bvec, sizeof(double) * n);
     double beta = bn;
     double *H = s->H, *g = s->g, *cs = s->cs, *sn = s->sn, *y = s->y, *h2 = s->tmp3;
@@ -1166,6 +1175,83 @@ int ora_linear_solve(ora_sim *s, const double *bvec, double *x, ora_lin_info *in
     return li.converged ? 0 : 1;
 }
 
+/* right-preconditioned BiCGSTAB (van der Vorst), the Krylov solver of the
+   paper's experiments (Sec. 4), zero initial guess.  When the recursive
+   residual meets the tolerance, the true residual b - A x decides; if it does
+   not, or on a breakdown (rho, (rhat, v) or omega zero), the method restarts
+   from the current x with rhat = r.  One iteration = two preconditioner
+   applications and two products with A (half an iteration counts as one). */
+static int bicgstab(ora_sim *s, const double *bvec, double *x, ora_lin_info *info) {
+    const ora_input *in = &s->in;
+    const int n = s->N * s->b;
+    ora_lin_info li; memset(&li, 0, sizeof(li));
+    if (!s->precond_ready) ora_precond_setup(s);
+    const double bn = sqrt(dot(bvec, bvec, n));
+    li.b_norm = bn;
+    for (int i = 0; i < n; i++) x[i] = 0.0;
+    double *r = s->r;
+    memcpy(r, bvec, sizeof(double) * n);
+    if (bn == 0.0) { li.converged = 1; if (info) *info = li; return 0; }
+    const double tol = s->theta * bn;
+    double *rh = s->V, *p = s->V + n, *v = s->V + 2 * (size_t)n, *sv = s->V + 3 * (size_t)n,
+           *t = s->V + 4 * (size_t)n, *ph = s->Z, *sh = s->Z + n;
+    memcpy(rh, r, sizeof(double) * n);
+    double rho_old = 1.0, alpha = 1.0, omega = 1.0;
+    int fresh = 1;                       /* first iteration of a (re)start */
+    li.r_norm = bn;
+    while (li.iterations < in->lin_max_iter) {
+        const double rho = dot(rh, r, n);
+        if (rho == 0.0 || !(rho == rho)) break;
+        if (fresh) memcpy(p, r, sizeof(double) * n);
+        else {
+            const double beta = (rho / rho_old) * (alpha / omega);
+            for (int i = 0; i < n; i++) p[i] = r[i] + beta * (p[i] - omega * v[i]);
+        }
+        ora_precond_apply(s, p, ph);
+        block_spmv(s, s->J, ph, v);
+        const double rv = dot(rh, v, n);
+        li.iterations++;
+        int check = 0, breakdown = 0;
+        if (rv == 0.0 || !(rv == rv)) breakdown = 1;
+        else {
+            alpha = rho / rv;
+            for (int i = 0; i < n; i++) sv[i] = r[i] - alpha * v[i];
+            if (sqrt(dot(sv, sv, n)) <= tol) {
+                for (int i = 0; i < n; i++) x[i] += alpha * ph[i];
+                check = 1;
+            } else {
+                ora_precond_apply(s, sv, sh);
+                block_spmv(s, s->J, sh, t);
+                const double tt = dot(t, t, n);
+                omega = tt > 0.0 ? dot(t, sv, n) / tt : 0.0;
+                for (int i = 0; i < n; i++) x[i] += alpha * ph[i] + omega * sh[i];
+                for (int i = 0; i < n; i++) r[i] = sv[i] - omega * t[i];
+                if (sqrt(dot(r, r, n)) <= tol) check = 1;
+                else if (omega == 0.0 || !(omega == omega)) breakdown = 1;
+            }
+        }
+        rho_old = rho;
+        fresh = 0;
+        if (check || breakdown) {
+            block_spmv(s, s->J, x, s->w);
+            for (int i = 0; i < n; i++) r[i] = bvec[i] - s->w[i];
+            li.r_norm = sqrt(dot(r, r, n));
+            if (li.r_norm <= tol) { li.converged = 1; break; }
+            if (!(li.r_norm == li.r_norm)) break;
+            memcpy(rh, r, sizeof(double) * n);
+            fresh = 1;
+            li.restarts++;
+        }
+    }
+    if (!li.converged) {
+        block_spmv(s, s->J, x, s->w);
+        for (int i = 0; i < n; i++) r[i] = bvec[i] - s->w[i];
+        li.r_norm = sqrt(dot(r, r, n));
+    }
+    if (info) *info = li;
+    return li.converged ? 0 : 1;
+}
+
 /* ------------------------------------------------------------------------ */
 /* inexact Newton (Algorithm 1) and time stepping                            */
 /* ------------------------------------------------------------------------ */
@@ -1220,12 +1306,46 @@ int ora_newton_step(ora_sim *s, double dt, ora_newton_info *info) {
     return ok ? 0 : 2;
 }
 
+/* forcing term theta_l of Algorithm 1 (Eq. 14).  Reading: norms are 2-norms of
+   the raw residual; r^{l-1} is the linear residual b^{l-1} - A dx left by the
+   previous solve; choice 2 takes the absolute value of its numerator; choice 3
+   uses gamma, beta as given.  The first iteration of a Newton solve uses
+   theta_max.  Safeguards of Eisenstat and Walker (1996): theta does not fall
+   below theta_{l-1}^((1+sqrt 5)/2) (choices 1, 2) or gamma theta_{l-1}^beta
+   (choice 3) while that bound exceeds 0.1; then lin_tol <= theta <= theta_max. */
+static double forcing_term(const ora_sim *s, int l, const double *bl, double bnorm, double bprev, double rprev,
+                           double theta_prev) {
+    const ora_input *in = &s->in;
+    if (in->forcing == 0) return in->lin_tol;
+    if (l == 0) return in->theta_max;
+    const int n = s->N * s->b;
+    double th, guard;
+    if (in->forcing == 1) {
+        double t2 = 0.0;
+        for (int i = 0; i < n; i++) { const double d = bl[i] - s->rlin[i]; t2 += d * d; }
+        th = sqrt(t2) / bprev;
+        guard = pow(theta_prev, 0.5 * (1.0 + sqrt(5.0)));
+    } else if (in->forcing == 2) {
+        th = fabs(bnorm - rprev) / bprev;
+        guard = pow(theta_prev, 0.5 * (1.0 + sqrt(5.0)));
+    } else {
+        th = in->ew_gamma * pow(bnorm / bprev, in->ew_beta);
+        guard = in->ew_gamma * pow(theta_prev, in->ew_beta);
+    }
+    if (guard > 0.1 && guard > th) th = guard;
+    if (th > in->theta_max) th = in->theta_max;
+    if (th < in->lin_tol) th = in->lin_tol;
+    return th;
+}
+
 /* Newton loop of Algorithm 1 until CNV <= tol; 0 = converged */
 int ora_newton_solve(ora_sim *s, double dt, ora_newton_info *info) {
     int n = s->N * s->b;
     ora_newton_info ni; memset(&ni, 0, sizeof(ni));
     double *rhs = xmalloc(sizeof(double) * n), *dx = xmalloc(sizeof(double) * n);
     int rc = 1;
+    double bprev = 0.0, rprev = 0.0, theta = s->in.lin_tol;
+    s->nhist = 0;
     for (int l = 0;; l++) {
         ora_assemble(s, dt);
         double cnv = ora_cnv(s, dt);
@@ -1234,8 +1354,18 @@ int ora_newton_solve(ora_sim *s, double dt, ora_newton_info *info) {
         if (cnv <= s->in.newton_tol) { rc = 0; ni.converged = 1; break; }
         if (l >= s->in.newton_max) { rc = 1; break; }
         for (int t = 0; t < n; t++) rhs[t] = -s->R[t];
+        const double bnorm = sqrt(dot(rhs, rhs, n));
+        theta = forcing_term(s, l, rhs, bnorm, bprev, rprev, theta);
+        s->theta = theta;
         ora_lin_info li;
         ora_linear_solve(s, rhs, dx, &li);
+        s->theta = s->in.lin_tol;
+        bprev = bnorm; rprev = li.r_norm;
+        memcpy(s->rlin, s->r, sizeof(double) * n);
+        if (s->nhist < 64) {
+            s->hist_theta[s->nhist] = theta; s->hist_b[s->nhist] = bnorm; s->hist_r[s->nhist] = li.r_norm;
+            s->nhist++;
+        }
         ni.newton_iterations++; ni.linear_iterations += li.iterations; ni.linear_failures += !li.converged;
         if (!finite_vec(dx, n)) { rc = 2; break; }
         newton_update(s, dx);
@@ -1243,6 +1373,12 @@ int ora_newton_solve(ora_sim *s, double dt, ora_newton_info *info) {
     free(rhs); free(dx);
     if (info) *info = ni;
     return rc;
+}
+
+int ora_forcing_history(const ora_sim *s, double *theta, double *b_norm, double *r_norm, int max) {
+    int k = s->nhist < max ? s->nhist : max;
+    for (int i = 0; i < k; i++) { theta[i] = s->hist_theta[i]; b_norm[i] = s->hist_b[i]; r_norm[i] = s->hist_r[i]; }
+    return k;
 }
 
 /* advance by dt; a failed Newton solve restores the last state and halves the step */

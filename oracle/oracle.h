@@ -58,10 +58,15 @@ typedef struct {
     int32_t amg_cycles;            /* V-cycles per stage-P application (>= 1) */
     int32_t decouple;              /* 0 quasi-IMPES, 1 ABF (alternate block factorisation) */
     int32_t cpr_stages;            /* 2: P then F; 3: F, P, F (CPR-FPF) */
+    int32_t krylov;                /* 0 FGMRES(m), 1 BiCGSTAB (the paper's solver, Sec. 4) */
+    int32_t lin_max_iter;          /* BiCGSTAB iteration limit per solve */
+    int32_t forcing;               /* 0: theta = lin_tol; 1, 2, 3: the choices of Eq. (14) */
+    double ew_gamma, ew_beta;      /* constants of choice 3 */
+    double theta_max;              /* theta of the first Newton iteration and upper safeguard */
 } ora_input;
 
 typedef struct {
-    int32_t iterations;            /* FGMRES inner iterations */
+    int32_t iterations;            /* FGMRES inner iterations or BiCGSTAB iterations */
     int32_t restarts;
     int32_t converged;
     double b_norm, r_norm;         /* ||b||, true ||b - A x|| at exit */
@@ -100,6 +105,9 @@ int ora_linear_solve(ora_sim *s, const double *b, double *x, ora_lin_info *info)
 int ora_newton_step(ora_sim *s, double dt, ora_newton_info *info);
 int ora_newton_solve(ora_sim *s, double dt, ora_newton_info *info);
 int ora_step(ora_sim *s, double dt, ora_step_info *info);
+/* forcing terms of the last ora_newton_solve: per linear solve theta_l, ||b^l||
+   and the true ||b^l - A dx|| at its exit; returns the number of solves (<= max) */
+int ora_forcing_history(const ora_sim *s, double *theta, double *b_norm, double *r_norm, int max);
 void ora_component_mass(const ora_sim *s, double *m);
 void ora_cumulative_well_mass(const ora_sim *s, double *m);
 void ora_well_rates(const ora_sim *s, double *q);

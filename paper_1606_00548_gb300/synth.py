@@ -128,8 +128,18 @@ def default_solver(**kw):
         newton_tol=1e-10, newton_max=20, lin_tol=1e-8, gmres_m=30, gmres_max_restarts=20,
         precond=2, stage2=1, amg_theta=0.25, amg_rounds=4, amg_coarse_max=256,
         amg_max_levels=16, chop_ds=0.2, chop_dp=50.0, max_cuts=8, amg_cycles=1,
-        decouple=0, cpr_stages=2,
+        decouple=0, cpr_stages=2, krylov=0, lin_max_iter=100, forcing=0, ew_gamma=0.9, ew_beta=2.0,
+        theta_max=0.5,
     )
+    s.update(kw)
+    return s
+
+
+def paper_solver(**kw):
+    """The settings of the paper's experiments (Sec. 4): BiCGSTAB with at most
+    100 iterations, inexact Newton with an adaptive forcing term (Eq. 14,
+    choice 2), CNV tolerance 1e-3, at most 20 Newton iterations."""
+    s = default_solver(krylov=1, lin_max_iter=100, forcing=2, newton_tol=1e-3)
     s.update(kw)
     return s
 
