@@ -61,6 +61,7 @@ class OraInput(C.Structure):
         ("amg_cycles", C.c_int32), ("decouple", C.c_int32), ("cpr_stages", C.c_int32),
         ("krylov", C.c_int32), ("lin_max_iter", C.c_int32), ("forcing", C.c_int32),
         ("ew_gamma", C.c_double), ("ew_beta", C.c_double), ("theta_max", C.c_double),
+        ("w_ctrl", C.POINTER(C.c_int32)), ("w_rate", C.POINTER(C.c_double)),
     ]
 
 
@@ -111,6 +112,11 @@ def lib():
         L.ora_newton_solve.argtypes = [vp, C.c_double, C.POINTER(NewtonInfo)]
         L.ora_step.argtypes = [vp, C.c_double, C.POINTER(StepInfo)]
         L.ora_forcing_history.argtypes = [vp, _dp, _dp, _dp, C.c_int]
+        L.ora_get_well_bhp.argtypes = [vp, _dp]
+        L.ora_set_well_bhp.argtypes = [vp, _dp]
+        L.ora_perforations.argtypes = [vp]
+        L.ora_get_well_system.argtypes = [vp, _dp, _dp, _dp, _dp]
+        L.ora_well_component_rates.argtypes = [vp, _dp]
         L.ora_component_mass.argtypes = [vp, _dp]
         L.ora_cumulative_well_mass.argtypes = [vp, _dp]
         L.ora_well_rates.argtypes = [vp, _dp]
@@ -164,6 +170,8 @@ def make_input(case: dict, keep: list, **solver_overrides) -> OraInput:
         a, p = _i([w[key] for w in ws] or [0]); keep.append(a); setattr(inp, name, p)
     for name, key in (("w_bhp", "bhp"), ("w_rw", "rw"), ("w_skin", "skin")):
         a, p = _d([w[key] for w in ws] or [0.0]); keep.append(a); setattr(inp, name, p)
+    a, p = _i([w.get("ctrl", 0) for w in ws] or [0]); keep.append(a); inp.w_ctrl = p
+    a, p = _d([w.get("rate", 0.0) for w in ws] or [0.0]); keep.append(a); inp.w_rate = p
     for c in range(3):
         inp.cnv_rho[c] = case["cnv_rho"][c]
     sv = dict(case["solver"]); sv.update(solver_overrides)
@@ -185,7 +193,10 @@ class Oracle:
         self.inp = make_input(case, self._keep, **solver_overrides)
         self.L = lib()
         self.h = self.L.ora_create(C.byref(self.inp))
+        if not self.h:
+            raise ValueError("oracle: invalid input (see stderr)")
         self.N = case["nx"] * case["ny"] * case["nz"]
+        self.nwells = len(case["wells"])
         self.b = self.L.ora_block_size(self.h)
         ini = case["init"]
         self.set_state(ini["p"], ini["sw"], ini["x3"], ini["phase"])
@@ -292,6 +303,31 @@ class Oracle:
         info = NewtonInfo()
         rc = self.L.ora_newton_solve(self.h, float(dt), C.byref(info))
         return rc, info
+
+    def well_bhp(self):
+        p = np.zeros(max(self.nwells, 1))
+        self.L.ora_get_well_bhp(self.h, p.ctypes.data_as(_dp))
+        return p[:self.nwells]
+
+    def set_well_bhp(self, bhp):
+        a, p = _d(np.asarray(bhp, dtype=np.float64).reshape(-1) if self.nwells else [0.0])
+        self.L.ora_set_well_bhp(self.h, p)
+
+    def well_component_rates(self):
+        q = np.zeros(3 * max(self.nwells, 1))
+        self.L.ora_well_component_rates(self.h, q.ctypes.data_as(_dp))
+        return q[:3 * self.nwells].reshape(self.nwells, 3)
+
+    def well_system(self):
+        """R_w, A_pw [nperf, b], A_wp [nperf, b], A_ww of the last assembly."""
+        nw, npf = max(self.nwells, 1), max(self.L.ora_perforations(self.h), 1)
+        Rw, Aww = np.zeros(nw), np.zeros(nw)
+        Apw, Awp = np.zeros(npf * self.b), np.zeros(npf * self.b)
+        self.L.ora_get_well_system(self.h, Rw.ctypes.data_as(_dp), Apw.ctypes.data_as(_dp),
+                                   Awp.ctypes.data_as(_dp), Aww.ctypes.data_as(_dp))
+        npf = self.L.ora_perforations(self.h)
+        return (Rw[:self.nwells], Apw[:npf * self.b].reshape(npf, self.b), Awp[:npf * self.b].reshape(npf, self.b),
+                Aww[:self.nwells])
 
     def forcing_history(self):
         th, bn, rn = np.zeros(64), np.zeros(64), np.zeros(64)

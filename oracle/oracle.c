@@ -199,7 +199,16 @@ struct ora_sim {
     double *depth;
     int nperf;
     int32_t *perf_cell, *perf_type;
-    double *perf_wi, *perf_zh, *perf_bhp;
+    double *perf_wi, *perf_zh;
+    int32_t *perf_well;                /* perforation -> well */
+    int32_t *cell_perf;                /* cell -> perforation of a rate-controlled well, or -1 */
+    int32_t *wctrl; double *wrate;     /* per well control and target */
+    double *wp, *wp_old;               /* per well bottom-hole pressure (an unknown under rate control) */
+    double *apw, *awp;                 /* [nperf][b]: dR_cell/dp_h and dR_w/dx_cell */
+    double *aww, *rw;                  /* [nw]: dR_w/dp_h and the well equation's residual */
+    double *qwell;                     /* [nw][3] component rates per well */
+    double *Jp;                        /* preconditioner matrix: J plus the wells' Schur complement on the stencil */
+    int nrate;                         /* rate-controlled wells */
     double *x, *x_old; int8_t *ph, *ph_old;
     double *mold;
     double *R, *J;
@@ -245,6 +254,7 @@ static int nbr(const ora_sim *s, int i, int d) {
 static int opp(int d) { return d == 0 ? 0 : (d % 2 ? d + 1 : d - 1); }
 
 #define JB(s, i, d) (&(s)->J[(((size_t)(i) * 7 + (d)) * (s)->b) * (s)->b])
+#define JP(s, i, d) (&(s)->Jp[(((size_t)(i) * 7 + (d)) * (s)->b) * (s)->b])
 #define AH(s, i, d) (&(s)->ahat[(((size_t)(i) * 7 + (d)) * (s)->b) * (s)->b])
 
 ora_sim *ora_create(const ora_input *in) {
@@ -287,7 +297,22 @@ ora_sim *ora_create(const ora_input *in) {
     s->nperf = np;
     s->perf_cell = xmalloc(sizeof(int32_t) * (np + 1)); s->perf_type = xmalloc(sizeof(int32_t) * (np + 1));
     s->perf_wi = xmalloc(sizeof(double) * (np + 1)); s->perf_zh = xmalloc(sizeof(double) * (np + 1));
-    s->perf_bhp = xmalloc(sizeof(double) * (np + 1));
+    s->perf_well = xmalloc(sizeof(int32_t) * (np + 1));
+    s->wctrl = xmalloc(sizeof(int32_t) * (nw + 1)); s->wrate = xmalloc(sizeof(double) * (nw + 1));
+    s->wp = xmalloc(sizeof(double) * (nw + 1)); s->wp_old = xmalloc(sizeof(double) * (nw + 1));
+    s->aww = xmalloc(sizeof(double) * (nw + 1)); s->rw = xmalloc(sizeof(double) * (nw + 1));
+    s->qwell = xmalloc(sizeof(double) * 3 * (nw + 1));
+    s->apw = xmalloc(sizeof(double) * (np + 1) * 3); s->awp = xmalloc(sizeof(double) * (np + 1) * 3);
+    s->cell_perf = xmalloc(sizeof(int32_t) * N);
+    for (int i = 0; i < N; i++) s->cell_perf[i] = -1;
+    s->nrate = 0;
+    for (int w = 0; w < nw; w++) {
+        s->wctrl[w] = in->w_ctrl ? in->w_ctrl[w] : 0;
+        s->wrate[w] = in->w_rate ? in->w_rate[w] : 0.0;
+        s->wp[w] = s->wbhp[w];
+        if (s->wctrl[w]) s->nrate++;
+    }
+    s->in.w_ctrl = s->wctrl; s->in.w_rate = s->wrate;
     np = 0;
     for (int w = 0; w < nw; w++) {
         double zh = in->top_depth + (s->wk0[w] + 0.5) * dz;
@@ -300,7 +325,14 @@ ora_sim *ora_create(const ora_input *in) {
             s->perf_type[np] = s->wt[w];
             s->perf_wi[np] = 2.0 * M_PI * DARCY_C * sqrt(kxx * kyy) * dz / (log(ro / s->wrw[w]) + s->wskin[w]);
             s->perf_zh[np] = zh;
-            s->perf_bhp[np] = s->wbhp[w];
+            s->perf_well[np] = w;
+            if (s->wctrl[w]) {
+                if (s->cell_perf[c] >= 0) {
+                    fprintf(stderr, "oracle: two rate-controlled perforations in cell %d\n", c);
+                    return NULL;     /* the caller treats NULL as an input error */
+                }
+                s->cell_perf[c] = np;
+            }
             np++;
         }
     }
@@ -310,6 +342,7 @@ ora_sim *ora_create(const ora_input *in) {
     s->mold = xmalloc(sizeof(double) * N * b);
     s->R = xmalloc(sizeof(double) * N * b);
     s->J = xmalloc(sizeof(double) * (size_t)N * 7 * b * b);
+    s->Jp = xmalloc(sizeof(double) * (size_t)N * 7 * b * b);
     s->props = xmalloc(sizeof(cellprops) * N);
     s->qiw = xmalloc(sizeof(double) * N * b);
     s->lsc = xmalloc(sizeof(double) * (size_t)N * b * b);
@@ -345,7 +378,9 @@ void ora_destroy(ora_sim *s) {
     for (int t = 0; t < 6; t++) free(s->pvt[t]);
     free(s->wi_); free(s->wj_); free(s->wk0); free(s->wk1); free(s->wt); free(s->wbhp); free(s->wrw); free(s->wskin);
     for (int a = 0; a < 3; a++) free(s->T[a]);
-    free(s->depth); free(s->perf_cell); free(s->perf_type); free(s->perf_wi); free(s->perf_zh); free(s->perf_bhp);
+    free(s->depth); free(s->perf_cell); free(s->perf_type); free(s->perf_wi); free(s->perf_zh); free(s->perf_well);
+    free(s->cell_perf); free(s->wctrl); free(s->wrate); free(s->wp); free(s->wp_old); free(s->aww); free(s->rw); free(s->qwell);
+    free(s->apw); free(s->awp); free(s->Jp);
     free(s->x); free(s->x_old); free(s->ph); free(s->ph_old); free(s->mold); free(s->R); free(s->J); free(s->props);
     free(s->qiw); free(s->lsc); free(s->ahat); free(s->dinv);
     free(s->V); free(s->Z); free(s->w); free(s->r); free(s->rlin); free(s->tmp); free(s->tmp2); free(s->tmp3);
@@ -360,6 +395,7 @@ static void begin_step(ora_sim *s) {
     int b = s->b;
     memcpy(s->x_old, s->x, sizeof(double) * s->N * b);
     memcpy(s->ph_old, s->ph, s->N);
+    memcpy(s->wp_old, s->wp, sizeof(double) * s->in.nwells);
     for (int i = 0; i < s->N; i++) {
         cellprops cp;
         eval_props(&s->in, s->poro[i], s->vol, &s->x[i * b], s->ph[i], &cp);
@@ -459,44 +495,91 @@ void ora_assemble(ora_sim *s, double dt) {
             }
         }
     }
-    /* wells under bottom-hole-pressure control, Eq. (6)-(7) */
+    /* wells, Eq. (6); each well's bottom-hole pressure p_h is the current
+       value of its unknown (fixed under BHP control).  The border blocks of
+       Eq. (16): A_pw = dR_cell/dp_h per perforation; the well equation is
+       p_h - c = 0 (BHP control, Eq. 7) or the perforations' summed rate of
+       the controlled component minus its target (Eq. 8-9) */
     s->qtot[0] = s->qtot[1] = s->qtot[2] = 0.0;
+    for (int w = 0; w < in->nwells; w++) {
+        s->qwell[w * 3] = s->qwell[w * 3 + 1] = s->qwell[w * 3 + 2] = 0.0;
+        if (s->wctrl[w]) { s->rw[w] = -s->wrate[w]; s->aww[w] = 0.0; }
+        else { s->rw[w] = s->wp[w] - s->wbhp[w]; s->aww[w] = 1.0; }
+    }
     for (int q = 0; q < s->nperf; q++) {
-        int i = s->perf_cell[q];
+        int i = s->perf_cell[q], w = s->perf_well[q];
         const cellprops *P = &s->props[i];
         double WI = s->perf_wi[q];
         double dh = GRAV * (s->perf_zh[q] - s->depth[i]) / 1e5;
         double p = s->x[i * b];
         double *D = JB(s, i, 0);
+        double *apw = &s->apw[q * 3], *awp = &s->awp[q * 3];
+        for (int k = 0; k < 3; k++) { apw[k] = 0.0; awp[k] = 0.0; }
+        const int cc = s->wctrl[w] == 1 ? CW : (s->wctrl[w] == 2 ? CO : -1);   /* controlled component */
         if (s->perf_type[q] == 1) {
             /* water injector: water at the cell's total mobility */
-            double Dw = s->perf_bhp[q] - p - P->rho[PW].v * dh;
+            double Dw = s->wp[w] - p - P->rho[PW].v * dh;
             dual lam = dmul(P->rhow, P->lamt);
             double qw = WI * lam.v * Dw;
             s->R[i * b + CW] -= qw;
             s->qtot[CW] += qw;
+            s->qwell[w * 3 + CW] += qw;
+            apw[CW] -= WI * lam.v;
             for (int k = 0; k < b; k++) {
                 double dD = (k == 0 ? -1.0 : 0.0) - P->rho[PW].d[k] * dh;
-                D[CW * b + k] -= WI * (lam.d[k] * Dw + lam.v * dD);
+                double dq = WI * (lam.d[k] * Dw + lam.v * dD);
+                D[CW * b + k] -= dq;
+                if (cc == CW) awp[k] += dq;
             }
+            if (cc == CW) { s->rw[w] += qw; s->aww[w] += WI * lam.v; }
         } else {
             for (int ph = 0; ph < np; ph++) {
-                double Dp = s->perf_bhp[q] - p - P->rho[ph].v * dh;
+                double Dp = s->wp[w] - p - P->rho[ph].v * dh;
                 for (int c = 0; c < b; c++) {
                     if (!carries(in->model, ph, c)) continue;
                     const dual *m = &P->mob[ph][c];
                     double qc = WI * m->v * Dp;
                     s->R[i * b + c] -= qc;
                     s->qtot[c] += qc;
+                    s->qwell[w * 3 + c] += qc;
+                    apw[c] -= WI * m->v;
                     for (int k = 0; k < b; k++) {
                         double dD = (k == 0 ? -1.0 : 0.0) - P->rho[ph].d[k] * dh;
-                        D[c * b + k] -= WI * (m->d[k] * Dp + m->v * dD);
+                        double dq = WI * (m->d[k] * Dp + m->v * dD);
+                        D[c * b + k] -= dq;
+                        if (c == cc) awp[k] += dq;
                     }
+                    if (c == cc) { s->rw[w] += qc; s->aww[w] += WI * m->v; }
                 }
             }
         }
     }
     s->precond_ready = 0;
+}
+
+/* well measure of the Newton test: largest |R_w| / max(|target|, 1 kg/day)
+   over the rate-controlled wells (BHP wells meet p_h = c exactly) */
+static double well_cnv(const ora_sim *s) {
+    double m = 0.0;
+    for (int w = 0; w < s->in.nwells; w++) {
+        if (!s->wctrl[w]) continue;
+        double sc = fabs(s->wrate[w]) > 1.0 ? fabs(s->wrate[w]) : 1.0;
+        double v = fabs(s->rw[w]) / sc;
+        if (!(v <= m)) m = v;
+    }
+    return m;
+}
+
+void ora_get_well_bhp(const ora_sim *s, double *bhp) { memcpy(bhp, s->wp, sizeof(double) * s->in.nwells); }
+void ora_set_well_bhp(ora_sim *s, const double *bhp) { memcpy(s->wp, bhp, sizeof(double) * s->in.nwells); }
+int ora_perforations(const ora_sim *s) { return s->nperf; }
+void ora_well_component_rates(const ora_sim *s, double *q) { memcpy(q, s->qwell, sizeof(double) * 3 * s->in.nwells); }
+void ora_get_well_system(const ora_sim *s, double *Rw, double *Apw, double *Awp, double *Aww) {
+    int b = s->b;
+    memcpy(Rw, s->rw, sizeof(double) * s->in.nwells);
+    memcpy(Aww, s->aww, sizeof(double) * s->in.nwells);
+    for (int q = 0; q < s->nperf; q++)
+        for (int c = 0; c < b; c++) { Apw[q * b + c] = s->apw[q * 3 + c]; Awp[q * b + c] = s->awp[q * 3 + c]; }
 }
 
 void ora_get_residual(const ora_sim *s, double *R) { memcpy(R, s->R, sizeof(double) * s->N * s->b); }
@@ -604,7 +687,27 @@ static void block_spmv(const ora_sim *s, const double *A, const double *x, doubl
         for (int r = 0; r < b; r++) y[i * b + r] = acc[r];
     }
 }
-void ora_spmv(const ora_sim *s, const double *x, double *y) { block_spmv(s, s->J, x, y); }
+/* y = S x, S = A - A_pw A_ww^-1 A_wp (the wells' unknowns eliminated): the
+   stencil product, then per well u = (A_wp x) / A_ww subtracted through A_pw */
+static void op_apply(const ora_sim *s, const double *x, double *y) {
+    int b = s->b;
+    block_spmv(s, s->J, x, y);
+    if (!s->nrate) return;
+    for (int w = 0; w < s->in.nwells; w++) {
+        if (!s->wctrl[w]) continue;
+        double u = 0.0;
+        for (int q = 0; q < s->nperf; q++) {
+            if (s->perf_well[q] != w) continue;
+            for (int k = 0; k < b; k++) u += s->awp[q * 3 + k] * x[s->perf_cell[q] * b + k];
+        }
+        u /= s->aww[w];
+        for (int q = 0; q < s->nperf; q++) {
+            if (s->perf_well[q] != w) continue;
+            for (int c = 0; c < b; c++) y[s->perf_cell[q] * b + c] -= s->apw[q * 3 + c] * u;
+        }
+    }
+}
+void ora_spmv(const ora_sim *s, const double *x, double *y) { op_apply(s, x, y); }
 
 /* ------------------------------------------------------------------------ */
 /* aggregation AMG on the pressure block                                     */
@@ -882,8 +985,27 @@ static void vcycle(ora_sim *s, int l, const double *f, double *e) {
 void ora_precond_setup(ora_sim *s) {
     int N = s->N, b = s->b;
     const ora_input *in = &s->in;
+    /* the preconditioner is built from Jp: the Schur complement S of the well
+       unknowns restricted to the 7-point block pattern, i.e. J minus
+       A_pw[q] A_ww^-1 A_wp[q'] for perforations q, q' of one rate-controlled
+       well whose cells coincide or are stencil neighbours */
+    memcpy(s->Jp, s->J, sizeof(double) * (size_t)N * 7 * b * b);
+    for (int q = 0; q < s->nperf; q++) {
+        int w = s->perf_well[q];
+        if (!s->wctrl[w]) continue;
+        int i = s->perf_cell[q];
+        for (int q2 = 0; q2 < s->nperf; q2++) {
+            if (s->perf_well[q2] != w) continue;
+            for (int d = 0; d < 7; d++) {
+                if (nbr(s, i, d) != s->perf_cell[q2]) continue;
+                double *B = JP(s, i, d);
+                for (int r = 0; r < b; r++)
+                    for (int c = 0; c < b; c++) B[r * b + c] -= s->apw[q * 3 + r] * s->awp[q2 * 3 + c] / s->aww[w];
+            }
+        }
+    }
     if (in->precond == 1) {
-        for (int i = 0; i < N; i++) inv_block(b, JB(s, i, 0), &s->dinv[(size_t)i * b * b]);
+        for (int i = 0; i < N; i++) inv_block(b, JP(s, i, 0), &s->dinv[(size_t)i * b * b]);
         s->precond_ready = 1;
         return;
     }
@@ -893,7 +1015,7 @@ void ora_precond_setup(ora_sim *s) {
        w = (1, -d_ps D_ss^-1) from the diagonal block D = J_ii, the other rows
        stay; ABF: L_i = D^-1 (alternate block factorisation). */
     for (int i = 0; i < N; i++) {
-        const double *D = JB(s, i, 0);
+        const double *D = JP(s, i, 0);
         double *L = &s->lsc[(size_t)i * b * b];
         if (in->decouple == 1) {
             inv_block(b, D, L);
@@ -916,7 +1038,7 @@ void ora_precond_setup(ora_sim *s) {
     for (int i = 0; i < N; i++) {
         const double *L = &s->lsc[(size_t)i * b * b];
         for (int d = 0; d < 7; d++) {
-            const double *A = JB(s, i, d);
+            const double *A = JP(s, i, d);
             double *Ah = AH(s, i, d);
             for (int r = 0; r < b; r++)
                 for (int c = 0; c < b; c++) {
@@ -1126,7 +1248,7 @@ int ora_linear_solve(ora_sim *s, const double *bvec, double *x, ora_lin_info *in
         for (int j = 0; j < m; j++) {
             double *vj = s->V + (size_t)j * n, *zj = s->Z + (size_t)j * n, *w = s->w;
             ora_precond_apply(s, vj, zj);
-            block_spmv(s, s->J, zj, w);
+            op_apply(s, zj, w);
             /* CGS pass 1 */
             for (int i = 0; i <= j; i++) hcol[i] = dot(s->V + (size_t)i * n, w, n);
             for (int i = 0; i <= j; i++) { const double *vi = s->V + (size_t)i * n; for (int t = 0; t < n; t++) w[t] -= hcol[i] * vi[t]; }
@@ -1163,7 +1285,7 @@ int ora_linear_solve(ora_sim *s, const double *bvec, double *x, ora_lin_info *in
             y[i] = t / H[i * (m + 1) + i];
         }
         for (int i = 0; i < k; i++) { const double *zi = s->Z + (size_t)i * n; for (int t = 0; t < n; t++) x[t] += y[i] * zi[t]; }
-        block_spmv(s, s->J, x, s->w);
+        op_apply(s, x, s->w);
         for (int t = 0; t < n; t++) s->r[t] = bvec[t] - s->w[t];
         beta = sqrt(dot(s->r, s->r, n));
         li.r_norm = beta;
@@ -1201,50 +1323,52 @@ static int bicgstab(ora_sim *s, const double *bvec, double *x, ora_lin_info *inf
     li.r_norm = bn;
     while (li.iterations < in->lin_max_iter) {
         const double rho = dot(rh, r, n);
-        if (rho == 0.0 || !(rho == rho)) break;
-        if (fresh) memcpy(p, r, sizeof(double) * n);
-        else {
-            const double beta = (rho / rho_old) * (alpha / omega);
-            for (int i = 0; i < n; i++) p[i] = r[i] + beta * (p[i] - omega * v[i]);
-        }
-        ora_precond_apply(s, p, ph);
-        block_spmv(s, s->J, ph, v);
-        const double rv = dot(rh, v, n);
-        li.iterations++;
         int check = 0, breakdown = 0;
-        if (rv == 0.0 || !(rv == rv)) breakdown = 1;
+        if (rho == 0.0 || !(rho == rho)) breakdown = 1;     /* r orthogonal to rh (r = 0 after a restart) */
         else {
-            alpha = rho / rv;
-            for (int i = 0; i < n; i++) sv[i] = r[i] - alpha * v[i];
-            if (sqrt(dot(sv, sv, n)) <= tol) {
-                for (int i = 0; i < n; i++) x[i] += alpha * ph[i];
-                check = 1;
-            } else {
-                ora_precond_apply(s, sv, sh);
-                block_spmv(s, s->J, sh, t);
-                const double tt = dot(t, t, n);
-                omega = tt > 0.0 ? dot(t, sv, n) / tt : 0.0;
-                for (int i = 0; i < n; i++) x[i] += alpha * ph[i] + omega * sh[i];
-                for (int i = 0; i < n; i++) r[i] = sv[i] - omega * t[i];
-                if (sqrt(dot(r, r, n)) <= tol) check = 1;
-                else if (omega == 0.0 || !(omega == omega)) breakdown = 1;
+            if (fresh) memcpy(p, r, sizeof(double) * n);
+            else {
+                const double beta = (rho / rho_old) * (alpha / omega);
+                for (int i = 0; i < n; i++) p[i] = r[i] + beta * (p[i] - omega * v[i]);
+            }
+            ora_precond_apply(s, p, ph);
+            op_apply(s, ph, v);
+            const double rv = dot(rh, v, n);
+            li.iterations++;
+            if (rv == 0.0 || !(rv == rv)) breakdown = 1;
+            else {
+                alpha = rho / rv;
+                for (int i = 0; i < n; i++) sv[i] = r[i] - alpha * v[i];
+                if (sqrt(dot(sv, sv, n)) <= tol) {
+                    for (int i = 0; i < n; i++) x[i] += alpha * ph[i];
+                    check = 1;
+                } else {
+                    ora_precond_apply(s, sv, sh);
+                    op_apply(s, sh, t);
+                    const double tt = dot(t, t, n);
+                    omega = tt > 0.0 ? dot(t, sv, n) / tt : 0.0;
+                    for (int i = 0; i < n; i++) x[i] += alpha * ph[i] + omega * sh[i];
+                    for (int i = 0; i < n; i++) r[i] = sv[i] - omega * t[i];
+                    if (sqrt(dot(r, r, n)) <= tol) check = 1;
+                    else if (omega == 0.0 || !(omega == omega)) breakdown = 1;
+                }
             }
         }
         rho_old = rho;
         fresh = 0;
         if (check || breakdown) {
-            block_spmv(s, s->J, x, s->w);
+            op_apply(s, x, s->w);
             for (int i = 0; i < n; i++) r[i] = bvec[i] - s->w[i];
             li.r_norm = sqrt(dot(r, r, n));
             if (li.r_norm <= tol) { li.converged = 1; break; }
-            if (!(li.r_norm == li.r_norm)) break;
+            if (!(li.r_norm == li.r_norm) || li.iterations >= in->lin_max_iter) break;
             memcpy(rh, r, sizeof(double) * n);
             fresh = 1;
             li.restarts++;
         }
     }
     if (!li.converged) {
-        block_spmv(s, s->J, x, s->w);
+        op_apply(s, x, s->w);
         for (int i = 0; i < n; i++) r[i] = bvec[i] - s->w[i];
         li.r_norm = sqrt(dot(r, r, n));
     }
@@ -1286,6 +1410,38 @@ static void newton_update(ora_sim *s, const double *dx) {
 
 static int finite_vec(const double *a, int n) { for (int i = 0; i < n; i++) if (!(a[i] - a[i] == 0.0)) return 0; return 1; }
 
+/* right-hand side of the reduced system: -R + A_pw A_ww^-1 R_w */
+static void reduced_rhs(const ora_sim *s, double *rhs) {
+    int b = s->b, n = s->N * b;
+    for (int t = 0; t < n; t++) rhs[t] = -s->R[t];
+    if (!s->nrate) return;
+    for (int q = 0; q < s->nperf; q++) {
+        int w = s->perf_well[q];
+        if (!s->wctrl[w]) continue;
+        double u = s->rw[w] / s->aww[w];
+        for (int c = 0; c < b; c++) rhs[s->perf_cell[q] * b + c] += s->apw[q * 3 + c] * u;
+    }
+}
+
+/* well update from the cell update: dp_h = (-R_w - A_wp dx) / A_ww, limited
+   to chop_dp like a cell pressure (zero for BHP-controlled wells) */
+static int well_update(ora_sim *s, const double *dx) {
+    int b = s->b;
+    for (int w = 0; w < s->in.nwells; w++) {
+        if (!s->wctrl[w]) continue;
+        double t = -s->rw[w];
+        for (int q = 0; q < s->nperf; q++) {
+            if (s->perf_well[q] != w) continue;
+            for (int k = 0; k < b; k++) t -= s->awp[q * 3 + k] * dx[s->perf_cell[q] * b + k];
+        }
+        double d = t / s->aww[w];
+        if (!(d - d == 0.0)) return 0;
+        if (fabs(d) > s->in.chop_dp) d = d > 0 ? s->in.chop_dp : -s->in.chop_dp;
+        s->wp[w] += d;
+    }
+    return 1;
+}
+
 /* one Newton iteration: assemble, solve J dx = -R, update */
 int ora_newton_step(ora_sim *s, double dt, ora_newton_info *info) {
     int n = s->N * s->b;
@@ -1293,13 +1449,14 @@ int ora_newton_step(ora_sim *s, double dt, ora_newton_info *info) {
     double cnv = ora_cnv(s, dt);
     ora_newton_info ni; memset(&ni, 0, sizeof(ni));
     ni.cnv = cnv;
-    if (cnv <= s->in.newton_tol) { ni.converged = 1; if (info) *info = ni; return 0; }
+    if (cnv <= s->in.newton_tol && well_cnv(s) <= s->in.newton_tol) { ni.converged = 1; if (info) *info = ni; return 0; }
     double *rhs = xmalloc(sizeof(double) * n), *dx = xmalloc(sizeof(double) * n);
-    for (int t = 0; t < n; t++) rhs[t] = -s->R[t];
+    reduced_rhs(s, rhs);
     ora_lin_info li;
     ora_linear_solve(s, rhs, dx, &li);
     ni.newton_iterations = 1; ni.linear_iterations = li.iterations; ni.linear_failures = !li.converged;
     int ok = finite_vec(dx, n);
+    if (ok) ok = well_update(s, dx);
     if (ok) newton_update(s, dx);
     free(rhs); free(dx);
     if (info) *info = ni;
@@ -1351,9 +1508,9 @@ int ora_newton_solve(ora_sim *s, double dt, ora_newton_info *info) {
         double cnv = ora_cnv(s, dt);
         ni.cnv = cnv;
         if (!(cnv == cnv)) { rc = 2; break; }
-        if (cnv <= s->in.newton_tol) { rc = 0; ni.converged = 1; break; }
+        if (cnv <= s->in.newton_tol && well_cnv(s) <= s->in.newton_tol) { rc = 0; ni.converged = 1; break; }
         if (l >= s->in.newton_max) { rc = 1; break; }
-        for (int t = 0; t < n; t++) rhs[t] = -s->R[t];
+        reduced_rhs(s, rhs);
         const double bnorm = sqrt(dot(rhs, rhs, n));
         theta = forcing_term(s, l, rhs, bnorm, bprev, rprev, theta);
         s->theta = theta;
@@ -1367,7 +1524,7 @@ int ora_newton_solve(ora_sim *s, double dt, ora_newton_info *info) {
             s->nhist++;
         }
         ni.newton_iterations++; ni.linear_iterations += li.iterations; ni.linear_failures += !li.converged;
-        if (!finite_vec(dx, n)) { rc = 2; break; }
+        if (!finite_vec(dx, n) || !well_update(s, dx)) { rc = 2; break; }
         newton_update(s, dx);
     }
     free(rhs); free(dx);
@@ -1399,6 +1556,7 @@ int ora_step(ora_sim *s, double dt, ora_step_info *info) {
             begin_step(s);
         } else {
             memcpy(s->x, s->x_old, sizeof(double) * s->N * s->b);
+            memcpy(s->wp, s->wp_old, sizeof(double) * s->in.nwells);
             memcpy(s->ph, s->ph_old, s->N);
             si.cuts++;
             if (si.cuts > s->in.max_cuts) { rc = 1; break; }

@@ -63,6 +63,13 @@ typedef struct {
     int32_t forcing;               /* 0: theta = lin_tol; 1, 2, 3: the choices of Eq. (14) */
     double ew_gamma, ew_beta;      /* constants of choice 3 */
     double theta_max;              /* theta of the first Newton iteration and upper safeguard */
+    /* well controls (NULL: every well under BHP control).  Control 0: fixed
+       BHP (Eq. 7); 1: fixed water rate, 2: fixed oil rate (Eq. 8-9), the
+       target being the component's mass rate summed over the perforations,
+       kg/day, positive into the reservoir; the BHP is then an unknown whose
+       initial guess is w_bhp.  Injectors take water-rate control only. */
+    const int32_t *w_ctrl;
+    const double *w_rate;
 } ora_input;
 
 typedef struct {
@@ -105,6 +112,22 @@ int ora_linear_solve(ora_sim *s, const double *b, double *x, ora_lin_info *info)
 int ora_newton_step(ora_sim *s, double dt, ora_newton_info *info);
 int ora_newton_solve(ora_sim *s, double dt, ora_newton_info *info);
 int ora_step(ora_sim *s, double dt, ora_step_info *info);
+/* Well unknowns (Eq. 16): every well has a bottom-hole pressure p_h; a
+   BHP-controlled well has the equation p_h - c = 0, a rate-controlled one
+   sum_m q_{c,m} - target = 0.  The Newton system
+       [A    A_pw] [dx ]     [R  ]
+       [A_wp A_ww] [dph] = - [R_w]
+   is solved through the Schur complement S = A - A_pw A_ww^-1 A_wp (A_ww is
+   diagonal, one entry per well): ora_spmv and ora_linear_solve act with S.
+   Layouts: bhp, R_w, A_ww [nwells]; A_pw, A_wp [nperf][b] in the order of the
+   wells' perforations (top to bottom, wells in input order). */
+void ora_get_well_bhp(const ora_sim *s, double *bhp);
+void ora_set_well_bhp(ora_sim *s, const double *bhp);
+int ora_perforations(const ora_sim *s);
+void ora_get_well_system(const ora_sim *s, double *Rw, double *Apw, double *Awp, double *Aww);
+/* component mass rates of each well at the last assembly, [nwells][3] (kg/day, + into the reservoir) */
+void ora_well_component_rates(const ora_sim *s, double *q);
+
 /* forcing terms of the last ora_newton_solve: per linear solve theta_l, ||b^l||
    and the true ||b^l - A dx|| at its exit; returns the number of solves (<= max) */
 int ora_forcing_history(const ora_sim *s, double *theta, double *b_norm, double *r_norm, int max);

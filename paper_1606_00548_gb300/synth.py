@@ -144,9 +144,12 @@ def paper_solver(**kw):
     return s
 
 
-def well(i, j, k0, k1, wtype, bhp, rw=0.1, skin=0.0):
+def well(i, j, k0, k1, wtype, bhp, rw=0.1, skin=0.0, ctrl=0, rate=0.0):
+    """A vertical well perforated in layers k0..k1.  ctrl 0: fixed BHP `bhp`;
+    ctrl 1 / 2: fixed water / oil component mass rate `rate` (kg/day, positive
+    into the reservoir), `bhp` then being the initial guess of its BHP."""
     return dict(i=int(i), j=int(j), k0=int(k0), k1=int(k1), type=int(wtype),
-                bhp=float(bhp), rw=float(rw), skin=float(skin))
+                bhp=float(bhp), rw=float(rw), skin=float(skin), ctrl=int(ctrl), rate=float(rate))
 
 
 def _hydrostatic(nx, ny, nz, dz, top_depth, p_top, rho):
