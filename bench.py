@@ -35,6 +35,8 @@ def workload(name: str, **solver):
     from paper_1606_00548_gb300 import synth
     if name == "bo100":
         return synth.black_oil_100x100x20(**solver), "black-oil 100x100x20 (200k cells, 3x3 blocks), 10-day steps"
+    if name == "bo100c":
+        return synth.black_oil_400cube(n=100, **solver), "black-oil 100^3 (1M cells), 10-day steps"
     if name == "bo200":
         return synth.black_oil_400cube(n=200, **solver), "black-oil 200^3 (8M cells), 10-day steps"
     if name == "bo400":
@@ -43,7 +45,39 @@ def workload(name: str, **solver):
 
 
 def solver_overrides(args):
-    return {} if args.amg_cycles is None else {"amg_cycles": args.amg_cycles}
+    """Solver options on top of the workload's defaults (FGMRES, theta 1e-8)."""
+    o = {}
+    if getattr(args, "solver", "default") == "paper":
+        # the paper's experiments (Sec. 4): BiCGSTAB (at most 100 iterations),
+        # adaptive forcing term (Eq. 14, choice 2), CNV tolerance 1e-3
+        o.update(krylov=1, lin_max_iter=100, forcing=2, newton_tol=1e-3)
+    if args.amg_cycles is not None:
+        o["amg_cycles"] = args.amg_cycles
+    if getattr(args, "decouple", "qi") == "abf":
+        o["decouple"] = 1
+    if getattr(args, "cpr_stages", 2) == 3:
+        o["cpr_stages"] = 3
+    return o
+
+
+def solver_desc(sv: dict) -> str:
+    dec = "ABF" if sv.get("decouple", 0) == 1 else "QI"
+    stages = "FPF" if sv.get("cpr_stages", 2) == 3 else "two-stage"
+    kry = "BiCGSTAB" if sv.get("krylov", 0) == 1 else f"FGMRES({sv.get('gmres_m', 30)})"
+    forcing = "theta 1e-8" if sv.get("forcing", 0) == 0 else f"forcing choice {sv['forcing']} of Eq. 14"
+    return (f"CPR {stages} ({dec}, aggregation AMG {sv.get('amg_cycles', 1)}x V(1,1), red-black block ILU0) "
+            f"{kry}, {forcing}, CNV {sv.get('newton_tol', 1e-10):g}")
+
+
+def kernel_sha1(name: str) -> str:
+    """SHA-1 of a kernel's source text in csrc/krylov.cu (template line to the
+    closing brace), so recorded ncu counters are dropped once the kernel changes."""
+    import hashlib
+    src = open(os.path.join(ROOT, "paper_1606_00548_gb300", "csrc", "krylov.cu")).read()
+    i = src.index(f" {name}(")
+    i = src.rindex("template", 0, i)
+    j = src.index("\n}\n", i)
+    return hashlib.sha1(src[i:j].encode()).hexdigest()
 
 
 class ClockSampler:
@@ -304,7 +338,8 @@ def run_ours(args):
     traffic = None
     try:
         ctr = json.load(open(os.path.join(ROOT, "profiles", "roofline_counters.json")))[f"spmv_kernel<{b}, double>"]
-        if ctr["workload_cells"] == N:
+        # counters count only for the kernel source they were taken on
+        if ctr["workload_cells"] == N and ctr.get("kernel_sha1") == kernel_sha1("spmv_kernel"):
             traffic = ctr["dram_bytes_per_launch"]
     except Exception:
         traffic = None
@@ -324,8 +359,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else "f64+f32",
             "data": "synthetic",
             "config": {"workload": desc, "precision": args.precision,
-                       "solver": f"CPR(QI, aggregation AMG {case['solver']['amg_cycles']}x V(1,1), "
-                                 "red-black block ILU0) FGMRES(30), theta 1e-8",
+                       "solver": solver_desc(case["solver"]),
                        "newton_iterations": newton, "linear_iterations": lin, "cuts": cuts,
                        "l2": "working set (J 101 MB + Krylov basis 149 MB + ...) larger than L2"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
@@ -446,9 +480,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--workload", default="bo100", choices=["bo100", "bo200", "bo400", "learned", "ensemble"])
+    ap.add_argument("--workload", default="bo100", choices=["bo100", "bo100c", "bo200", "bo400", "learned", "ensemble"])
     ap.add_argument("--train-steps", type=int, default=300)
     ap.add_argument("--amg-cycles", type=int, default=None, help="V-cycles per CPR pressure stage")
+    ap.add_argument("--solver", default="default", choices=["default", "paper"],
+                    help="paper: BiCGSTAB, adaptive forcing (Eq. 14 choice 2), CNV 1e-3")
+    ap.add_argument("--decouple", default="qi", choices=["qi", "abf"])
+    ap.add_argument("--cpr-stages", type=int, default=2, choices=[2, 3])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -82,11 +82,20 @@ typedef struct {
 
 #define SIM_WELL_PRODUCER 0
 #define SIM_WELL_WATER_INJECTOR 1
-/* vertical well perforated in layers k_top..k_bot, BHP control (Eq. 7) */
+#define SIM_WELL_BHP 0          /* fixed bottom-hole pressure (Eq. 7) */
+#define SIM_WELL_WATER_RATE 1   /* fixed water rate (Eq. 8); producers and injectors */
+#define SIM_WELL_OIL_RATE 2     /* fixed oil rate (Eq. 9); producers only */
+/* vertical well perforated in layers k_top..k_bot (Sec. 2.3).  Under a rate
+   control the well's bottom-hole pressure is an unknown of the Newton system
+   (Eq. 16) and bhp is its initial guess.  No two perforations (of any wells)
+   may share a cell. */
 typedef struct {
     int32_t i, j, k_top, k_bot, type;
     double bhp;                 /* bar, at the depth of the top perforation */
     double r_w, skin;           /* Peaceman well radius (m) and skin */
+    int32_t control;            /* SIM_WELL_BHP, SIM_WELL_WATER_RATE or SIM_WELL_OIL_RATE */
+    double rate;                /* target component mass rate summed over the perforations,
+                                   kg/day, positive into the reservoir (rate controls) */
 } sim_well;
 
 #define SIM_PRECOND_NONE 0
@@ -96,6 +105,14 @@ typedef struct {
 #define SIM_STAGE2_ILU0_RB 1
 #define SIM_PRECISION_FP64 0
 #define SIM_PRECISION_MIXED 1   /* FP32 preconditioner + FP32 Krylov directions Z */
+#define SIM_DECOUPLE_QI 0       /* quasi-IMPES: pressure row J_0 - d_ps D_ss^-1 J_s (Sec. 3.2) */
+#define SIM_DECOUPLE_ABF 1      /* alternate block factorisation: D_ii^-1 J (Sec. 3.2) */
+#define SIM_KRYLOV_FGMRES 0     /* right-preconditioned FGMRES(gmres_m), restarts */
+#define SIM_KRYLOV_BICGSTAB 1   /* right-preconditioned BiCGSTAB (the paper's solver, Sec. 4) */
+#define SIM_FORCING_FIXED 0     /* theta = lin_tol on every Newton iteration */
+#define SIM_FORCING_EW1 1       /* Eq. (14) choice 1: ||b^l - r^{l-1}|| / ||b^{l-1}|| */
+#define SIM_FORCING_EW2 2       /* Eq. (14) choice 2: | ||b^l|| - ||r^{l-1}|| | / ||b^{l-1}|| */
+#define SIM_FORCING_EW3 3       /* Eq. (14) choice 3: gamma (||b^l|| / ||b^{l-1}||)^beta */
 
 typedef struct {
     double newton_tol;          /* CNV tolerance */
@@ -112,6 +129,14 @@ typedef struct {
     int32_t precision;          /* SIM_PRECISION_* */
     int32_t amg_cycles;         /* V-cycles per stage-P application (>= 1) */
     int32_t graphs;             /* 1: replay each FGMRES restart cycle as a CUDA graph */
+    int32_t decouple;           /* SIM_DECOUPLE_*: left scaling applied before the CPR stages */
+    int32_t cpr_stages;         /* 2: stage P then stage F; 3: F, P, F (CPR-FPF) */
+    int32_t krylov;             /* SIM_KRYLOV_*: outer Krylov method of every linear solve */
+    int32_t lin_max_iter;       /* BiCGSTAB iteration limit per solve (>= 1) */
+    int32_t forcing;            /* SIM_FORCING_*: forcing term theta_l of the Newton loop */
+    double ew_gamma, ew_beta;   /* constants of forcing choice 3 (gamma in (0, 1], beta > 0) */
+    double theta_max;           /* theta of a Newton solve's first iteration and upper bound (lin_tol..1) */
+    int32_t fused_coarse;       /* 1: the coarse AMG levels of a V-cycle run in one cluster launch */
 } sim_options;
 
 typedef struct {
@@ -162,10 +187,13 @@ sim_status sim_newton_solve(sim_t *s, double dt, sim_newton_info *info);
 /* One Newton iteration at the current iterate: assemble, test CNV, solve
    J dx = -R, update.  info->converged = 1 means CNV already met (no solve). */
 sim_status sim_newton_step(sim_t *s, double dt, sim_newton_info *info);
-/* Solve J x = b with the current Jacobian (FGMRES + the configured
+/* Solve J x = b with the current Jacobian to ||b - J x|| <= lin_tol ||b||
+   (FGMRES or BiCGSTAB per options.krylov, with the configured
    preconditioner).  b_dev, x_dev: device pointers, N*b doubles each,
    component-major; they may not alias.  Returns SIM_ENOCONV_LINEAR (not
-   sticky) when the restart limit is hit; x_dev then holds the last iterate. */
+   sticky) when the restart / iteration limit is hit; x_dev then holds the
+   last iterate.  In the Newton loop (sim_step, sim_newton_solve) the
+   tolerance is the forcing term of options.forcing instead. */
 sim_status sim_linear_solve(sim_t *s, const double *b_dev, double *x_dev, sim_linear_info *info);
 
 /* ---- inspection entry points (used by the parity tests) ---- */
@@ -195,6 +223,24 @@ sim_status sim_amg_level_ell(sim_t *s, int32_t level, int32_t *col, double *val)
 sim_status sim_component_mass(sim_t *s, double *m3);
 sim_status sim_cumulative_well_mass(sim_t *s, double *m3);
 sim_status sim_well_rates(sim_t *s, double *q3);
+/* Well unknowns (Eq. 16).  Every well has a bottom-hole pressure p_h; under
+   BHP control its equation is p_h - c = 0, under a rate control the summed
+   component rate minus the target.  The Newton system
+       [A    A_pw] [dx ]     [R  ]
+       [A_wp A_ww] [dph] = - [R_w]
+   is solved through S = A - A_pw A_ww^-1 A_wp (A_ww diagonal): sim_spmv and
+   sim_linear_solve act with S, and the CPR preconditioner is built from S
+   restricted to the 7-point block pattern.  Host arrays: bhp, Rw, Aww
+   [nwells]; Apw, Awp [nperf][b] (perforations top to bottom, wells in input
+   order); q [nwells][3] component rates at the last assembly (kg/day). */
+int32_t sim_perforations(sim_t *s);
+sim_status sim_get_well_bhp(sim_t *s, double *bhp);
+sim_status sim_set_well_bhp(sim_t *s, const double *bhp);
+sim_status sim_well_component_rates(sim_t *s, double *q);
+sim_status sim_get_well_system(sim_t *s, double *Rw, double *Apw, double *Awp, double *Aww);
+/* replaces the border blocks of the last assembly (tests feed identical
+   systems to two implementations, as with sim_set_jacobian) */
+sim_status sim_set_well_system(sim_t *s, const double *Rw, const double *Apw, const double *Awp, const double *Aww);
 sim_status sim_get_stats(sim_t *s, sim_stats *st);
 int32_t sim_block_size(sim_t *s);
 
@@ -280,9 +326,11 @@ const char *sim_net_last_error(sim_net_t *n);
    less than 10x (or turns non-finite) is redone with plain CPR. */
 sim_status sim_set_learned_stage(sim_t *s, sim_net_t *net, int32_t enable);
 /* Training pairs from the last linear solve: for the first k Krylov vectors
-   v_j of its last restart cycle (k <= its iterations + 1), x_j = features of
-   the decoupled pressure residual w^T v_j (normalised by its RMS) and
-   y_j = one AMG V-cycle applied to it (normalised by its own RMS).  x_dev [k][N][4],
+   v_j of its last restart cycle (k <= its iterations + 1), with f = the
+   decoupled pressure residual (L v_j)_p and e_p one stage-P V-cycle on it,
+   x_j = features of r' = f - A_p e_p (the residual the learned stage sees,
+   normalised by its RMS) and y_j = A_p^-1 r' approximated by eight V-cycles
+   of iterative refinement (normalised by its own RMS).  x_dev [k][N][4],
    y_dev [k][N] (device, FP32).  k outside 1..sim_learned_available(s)
    returns SIM_EINVAL without making the handle's error sticky. */
 sim_status sim_learned_pairs(sim_t *s, int32_t k, float *x_dev, float *y_dev);

@@ -380,38 +380,57 @@ __global__ void __launch_bounds__(SIM_THREADS) flux_kernel(GridDesc g, const dou
 // assembly pass 3: well terms (Eq. 6) at the perforated cells; one block.
 // Perforations occupy distinct cells (checked at creation).
 // ---------------------------------------------------------------------------
+// Border blocks of Eq. (16) per perforation q: apw[c][q] = dR_c/dp_h and,
+// for the well's controlled component cc, awp[k][q] = dq_cc/dx_k; the
+// controlled rate of the perforation goes to qcc[q].  One block; afterwards
+// one thread per well sums its perforations in order: R_w, A_ww, the rates.
 template <int B>
 __global__ void well_kernel(FluidConst f, GridDesc g, const double *__restrict__ x, const int8_t *__restrict__ ph,
                             const double *__restrict__ poro, int nperf, const int *__restrict__ cell,
                             const int *__restrict__ type, const double *__restrict__ wi, const double *__restrict__ zh,
-                            const double *__restrict__ bhp, double *__restrict__ R, double *__restrict__ J,
-                            double *__restrict__ qtot) {
+                            const int *__restrict__ pwell, const int *__restrict__ woff, int nwells,
+                            const int *__restrict__ wctrl, const double *__restrict__ wrate,
+                            const double *__restrict__ wbhp_c, const double *__restrict__ wp, double *__restrict__ R,
+                            double *__restrict__ J, double *__restrict__ apw, double *__restrict__ awp,
+                            double *__restrict__ qperf, double *__restrict__ rw, double *__restrict__ aww,
+                            double *__restrict__ qwell, double *__restrict__ wcnv, double *__restrict__ qtot) {
     __shared__ double part[SIM_THREADS][3];
+    __shared__ double wmax[SIM_THREADS];
     const long N = g.N;
     double qs[3] = {0.0, 0.0, 0.0};
     for (int q = threadIdx.x; q < nperf; q += blockDim.x) {
         const int i = cell[q];
         const int iz = i / (g.nx * g.ny);
+        const int w = pwell[q];
+        const int ctrl = wctrl[w];
+        const int cc = ctrl == 1 ? 0 : (ctrl == 2 ? 1 : -1);    // controlled component (water 0, oil 1)
         Props<B> P;
         const double p = x[i];
         cell_props<B>(f, poro[i], g.dx * g.dy * g.dz, p, x[N + i], B == 3 ? x[2 * N + i] : 0.0, B == 3 ? ph[i] : 1, P);
         const double dh = SIM_GRAV * (zh[q] - (g.top + (iz + 0.5) * g.dz)) / 1e5;
         const double W = wi[q];
+        const double bhp = wp[w];
+        double a_pw[3] = {0.0, 0.0, 0.0}, a_wp[3] = {0.0, 0.0, 0.0}, qc4[4] = {0.0, 0.0, 0.0, 0.0};
         if (type[q] == SIM_WELL_WATER_INJECTOR) {
-            const double Dw = bhp[q] - p - P.rho[0].v * dh;
+            const double Dw = bhp - p - P.rho[0].v * dh;
             const Dl<B> lam = P.rho[0] * P.lamt;
             const double qw = W * lam.v * Dw;
             R[i] -= qw;
             qs[0] += qw;
+            qc4[0] = qw;
+            a_pw[0] -= W * lam.v;
 #pragma unroll
             for (int k = 0; k < B; k++) {
                 const double dD = (k == 0 ? -1.0 : 0.0) - P.rho[0].d[k] * dh;
-                J[k * N + i] -= W * (lam.d[k] * Dw + lam.v * dD);
+                const double dq = W * (lam.d[k] * Dw + lam.v * dD);
+                J[k * N + i] -= dq;
+                if (cc == 0) a_wp[k] += dq;
             }
+            if (cc == 0) { qc4[3] = qw; }
         } else {
 #pragma unroll
             for (int a = 0; a < B; a++) {
-                const double Dp = bhp[q] - p - P.rho[a].v * dh;
+                const double Dp = bhp - p - P.rho[a].v * dh;
 #pragma unroll
                 for (int pq = 0; pq < Layout<B>::NPAIR; pq++) {
                     if (Layout<B>::pair_phase(pq) != a) continue;
@@ -420,22 +439,119 @@ __global__ void well_kernel(FluidConst f, GridDesc g, const double *__restrict__
                     const double qc = W * m.v * Dp;
                     R[c * N + i] -= qc;
                     qs[c] += qc;
+                    qc4[c] += qc;
+                    a_pw[c] -= W * m.v;
 #pragma unroll
                     for (int k = 0; k < B; k++) {
                         const double dD = (k == 0 ? -1.0 : 0.0) - P.rho[a].d[k] * dh;
-                        J[(c * B + k) * N + i] -= W * (m.d[k] * Dp + m.v * dD);
+                        const double dq = W * (m.d[k] * Dp + m.v * dD);
+                        J[(c * B + k) * N + i] -= dq;
+                        if (c == cc) a_wp[k] += dq;
                     }
+                    if (c == cc) qc4[3] = qc;
                 }
             }
         }
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            apw[(long)c * nperf + q] = a_pw[c];
+            awp[(long)c * nperf + q] = a_wp[c];
+        }
+#pragma unroll
+        for (int c = 0; c < 4; c++) qperf[(long)c * nperf + q] = qc4[c];
     }
     for (int c = 0; c < 3; c++) part[threadIdx.x][c] = qs[c];
+    __syncthreads();    // qperf and apw of every perforation are visible to the block
+    double mx = 0.0;
+    for (int w = threadIdx.x; w < nwells; w += blockDim.x) {
+        const int ctrl = wctrl[w];
+        double r = ctrl ? -wrate[w] : wp[w] - wbhp_c[w], a = ctrl ? 0.0 : 1.0;
+        double qw[3] = {0.0, 0.0, 0.0};
+        const int cc = ctrl == 1 ? 0 : 1;
+        for (int q = woff[w]; q < woff[w + 1]; q++) {
+            for (int c = 0; c < 3; c++) qw[c] += qperf[(long)c * nperf + q];
+            if (ctrl) {
+                r += qperf[3L * nperf + q];
+                a -= apw[(long)cc * nperf + q];
+            }
+        }
+        rw[w] = r;
+        aww[w] = a;
+        for (int c = 0; c < 3; c++) qwell[(long)c * nwells + w] = qw[c];
+        if (ctrl) {
+            const double sc = fabs(wrate[w]) > 1.0 ? fabs(wrate[w]) : 1.0;
+            const double v = fabs(r) / sc;
+            if (!(v <= mx)) mx = v;        // NaN propagates
+        }
+    }
+    wmax[threadIdx.x] = mx;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t[3] = {0.0, 0.0, 0.0};
-        for (int k = 0; k < (int)blockDim.x; k++)
+        double t[3] = {0.0, 0.0, 0.0}, m = 0.0;
+        for (int k = 0; k < (int)blockDim.x; k++) {
             for (int c = 0; c < 3; c++) t[c] += part[k][c];
+            if (!(wmax[k] <= m)) m = wmax[k];
+        }
         for (int c = 0; c < 3; c++) qtot[c] = t[c];
+        *wcnv = m;
+    }
+}
+
+// b += A_pw A_ww^-1 R_w at the perforations of rate-controlled wells
+// (the right-hand side of the system with the well unknowns eliminated)
+__global__ void well_rhs_kernel(long N, int b, int nperf, const int *__restrict__ cell, const int *__restrict__ pwell,
+                                const int *__restrict__ wctrl, const double *__restrict__ apw,
+                                const double *__restrict__ rw, const double *__restrict__ aww, double *__restrict__ rhs) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nperf) return;
+    const int w = pwell[q];
+    if (!wctrl[w]) return;
+    const double u = rw[w] / aww[w];
+    const int i = cell[q];
+    for (int c = 0; c < b; c++) rhs[c * N + i] += apw[(long)c * nperf + q] * u;
+}
+
+// dp_h = (-R_w - A_wp dx) / A_ww, limited to chop_dp; one warp per well
+__global__ void well_update_kernel(long N, int b, int nperf, int nwells, const int *__restrict__ cell,
+                                   const int *__restrict__ woff, const int *__restrict__ wctrl,
+                                   const double *__restrict__ awp, const double *__restrict__ rw,
+                                   const double *__restrict__ aww, const double *__restrict__ dx, double chop_dp,
+                                   double *__restrict__ wp) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (w >= nwells || !wctrl[w]) return;
+    double t = 0.0;
+    for (int q = woff[w] + lane; q < woff[w + 1]; q += 32) {
+        const int i = cell[q];
+        for (int k = 0; k < b; k++) t += awp[(long)k * nperf + q] * dx[k * N + i];
+    }
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) {
+        double d = (-rw[w] - t) / aww[w];
+        if (fabs(d) > chop_dp) d = d > 0 ? chop_dp : -chop_dp;
+        wp[w] += d;
+    }
+}
+
+// y -= A_pw A_ww^-1 A_wp x at the rate-controlled wells' perforations; one warp per well
+template <typename X>
+__global__ void well_op_kernel(long N, int b, int nperf, int nwells, const int *__restrict__ cell,
+                               const int *__restrict__ woff, const int *__restrict__ wctrl,
+                               const double *__restrict__ apw, const double *__restrict__ awp,
+                               const double *__restrict__ aww, const X *__restrict__ x, double *__restrict__ y,
+                               const int *done) {
+    if (done && *(volatile const int *)done) return;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (w >= nwells || !wctrl[w]) return;
+    double t = 0.0;
+    for (int q = woff[w] + lane; q < woff[w + 1]; q += 32) {
+        const int i = cell[q];
+        for (int k = 0; k < b; k++) t += awp[(long)k * nperf + q] * (double)x[k * N + i];
+    }
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    const double u = __shfl_sync(0xffffffffu, t, 0) / aww[w];
+    for (int q = woff[w] + lane; q < woff[w + 1]; q += 32) {
+        const int i = cell[q];
+        for (int c = 0; c < b; c++) y[c * N + i] -= apw[(long)c * nperf + q] * u;
     }
 }
 
@@ -584,7 +700,7 @@ __global__ void update_kernel(int N, double chop_ds, double chop_dp, const doubl
 static double *poro_of(sim_t *s) { return s->poro; }
 
 sim_status k_geometry(sim_t *s, const double *kx, const double *ky, const double *kz, const double *poro,
-                      const int *wcell, const int *wtype, const double *wbhp, const double *wzh, const double *wrw,
+                      const int *wcell, const int *wtype, const int *pwell, const double *wzh, const double *wrw,
                       const double *wskin) {
     const int N = s->N;
     double *dk = (double *)sim_alloc(s, sizeof(double) * 3 * (size_t)N);
@@ -601,7 +717,7 @@ sim_status k_geometry(sim_t *s, const double *kx, const double *ky, const double
         if (!tmp) return s->err;
         SIM_CK(s, cudaMemcpyAsync(s->perf_cell, wcell, sizeof(int) * np, cudaMemcpyHostToDevice, s->stream));
         SIM_CK(s, cudaMemcpyAsync(s->perf_type, wtype, sizeof(int) * np, cudaMemcpyHostToDevice, s->stream));
-        SIM_CK(s, cudaMemcpyAsync(s->perf_bhp, wbhp, sizeof(double) * np, cudaMemcpyHostToDevice, s->stream));
+        SIM_CK(s, cudaMemcpyAsync(s->perf_well, pwell, sizeof(int) * np, cudaMemcpyHostToDevice, s->stream));
         SIM_CK(s, cudaMemcpyAsync(s->perf_zh, wzh, sizeof(double) * np, cudaMemcpyHostToDevice, s->stream));
         SIM_CK(s, cudaMemcpyAsync(tmp, wrw, sizeof(double) * np, cudaMemcpyHostToDevice, s->stream));
         SIM_CK(s, cudaMemcpyAsync(tmp + np, wskin, sizeof(double) * np, cudaMemcpyHostToDevice, s->stream));
@@ -633,10 +749,17 @@ static sim_status assemble_b(sim_t *s, double dt) {
     SIM_LAUNCHED(s);
     flux_kernel<B><<<sim_blocks(N), SIM_THREADS, 0, s->stream>>>(s->gd, s->x, s->props, s->T, s->R, s->J);
     SIM_LAUNCHED(s);
-    well_kernel<B><<<1, SIM_THREADS, 0, s->stream>>>(s->fc, s->gd, s->x, s->ph, poro_of(s), s->nperf, s->perf_cell,
-                                                     s->perf_type, s->perf_wi, s->perf_zh, s->perf_bhp, s->R, s->J,
-                                                     s->qtot);
-    SIM_LAUNCHED(s);
+    if (s->nwells > 0) {
+        well_kernel<B><<<1, SIM_THREADS, 0, s->stream>>>(s->fc, s->gd, s->x, s->ph, poro_of(s), s->nperf, s->perf_cell,
+                                                         s->perf_type, s->perf_wi, s->perf_zh, s->perf_well, s->woff,
+                                                         s->nwells, s->wctrl, s->wrate, s->wbhp_c, s->wp, s->R, s->J,
+                                                         s->apw, s->awp, s->qperf, s->rw, s->aww, s->qwell, s->wcnv,
+                                                         s->qtot);
+        SIM_LAUNCHED(s);
+    } else {
+        SIM_CK(s, cudaMemsetAsync(s->qtot, 0, sizeof(double) * 3, s->stream));
+        SIM_CK(s, cudaMemsetAsync(s->wcnv, 0, sizeof(double), s->stream));
+    }
     return SIM_OK;
 }
 
@@ -645,15 +768,44 @@ sim_status k_assemble(sim_t *s, double dt) {
     return s->b == 2 ? assemble_b<2>(s, dt) : assemble_b<3>(s, dt);
 }
 
-sim_status k_cnv(sim_t *s, double dt, double *cnv_host) {
+sim_status k_well_rhs(sim_t *s, double *rhs) {
+    if (s->nrate == 0) return SIM_OK;
+    well_rhs_kernel<<<sim_blocks(s->nperf), SIM_THREADS, 0, s->stream>>>(s->N, s->b, s->nperf, s->perf_cell, s->perf_well,
+                                                                         s->wctrl, s->apw, s->rw, s->aww, rhs);
+    SIM_LAUNCHED(s);
+    return SIM_OK;
+}
+
+sim_status k_well_update(sim_t *s, const double *dx) {
+    if (s->nrate == 0) return SIM_OK;
+    well_update_kernel<<<sim_blocks((long)s->nwells * 32), SIM_THREADS, 0, s->stream>>>(
+        s->N, s->b, s->nperf, s->nwells, s->perf_cell, s->woff, s->wctrl, s->awp, s->rw, s->aww, dx, s->opt.chop_dp, s->wp);
+    SIM_LAUNCHED(s);
+    return SIM_OK;
+}
+
+template <typename X>
+sim_status k_well_op(sim_t *s, const X *x, double *y, const int *done) {
+    if (s->nrate == 0) return SIM_OK;
+    well_op_kernel<X><<<sim_blocks((long)s->nwells * 32), SIM_THREADS, 0, s->stream>>>(
+        s->N, s->b, s->nperf, s->nwells, s->perf_cell, s->woff, s->wctrl, s->apw, s->awp, s->aww, x, y, done);
+    SIM_LAUNCHED(s);
+    return SIM_OK;
+}
+template sim_status k_well_op<double>(sim_t *, const double *, double *, const int *);
+template sim_status k_well_op<float>(sim_t *, const float *, double *, const int *);
+
+sim_status k_cnv(sim_t *s, double dt, double *cnv_host, double *well_cnv_host) {
     if (s->b == 2)
         cnv_kernel<2><<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(s->gd, s->R, poro_of(s), dt, s->fc, s->red, s->ticket, s->scal);
     else
         cnv_kernel<3><<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(s->gd, s->R, poro_of(s), dt, s->fc, s->red, s->ticket, s->scal);
     SIM_LAUNCHED(s);
     SIM_CK(s, cudaMemcpyAsync(s->h_pinned, s->scal, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    if (well_cnv_host) SIM_CK(s, cudaMemcpyAsync(s->h_pinned + 1, s->wcnv, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     SIM_CK(s, cudaStreamSynchronize(s->stream));
     *cnv_host = s->h_pinned[0];
+    if (well_cnv_host) *well_cnv_host = s->h_pinned[1];
     return SIM_OK;
 }
 

@@ -24,7 +24,11 @@
 #include <cmath>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "sim_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -114,51 +118,135 @@ __global__ void selfpad_kernel(int n, int W, const int *__restrict__ col, int *_
 // ---------------------------------------------------------------------------
 // quasi-IMPES decoupling (FP64, rounding-exact: no contraction)
 // ---------------------------------------------------------------------------
+// rate-controlled wells' Schur term in the preconditioner matrix: block (i, d)
+// of J loses A_pw[q] A_ww^-1 A_wp[q'] when cell i holds perforation q and its
+// neighbour j holds perforation q' of the same rate-controlled well
+struct WellCorr {
+    const int *cell_perf = nullptr;   // null: no rate-controlled wells
+    const int *pwell = nullptr;
+    const double *apw = nullptr, *awp = nullptr, *aww = nullptr;   // [3][nperf], [nwells]
+    int nperf = 0;
+};
+
+// block (row cell i, direction d, neighbour j) of the preconditioner matrix,
+// the correction rounded as written (the AMG hierarchy is built bit-exactly)
 template <int B>
-__device__ __forceinline__ void qi_weights(const double *__restrict__ J, int N, int i, double *w) {
-    const double D01 = J[(0 * B + 1) * (long)N + i], D11 = J[(1 * B + 1) * (long)N + i];
+__device__ __forceinline__ void load_jblock(const double *__restrict__ J, long N, int i, int d, int j, const WellCorr &wc,
+                                            double *Jb) {
+#pragma unroll
+    for (int t = 0; t < B * B; t++) Jb[t] = J[(long)(d * B * B + t) * N + i];
+    if (!wc.cell_perf || j < 0) return;
+    const int q = wc.cell_perf[i];
+    if (q < 0) return;
+    const int q2 = wc.cell_perf[j];
+    if (q2 < 0 || wc.pwell[q2] != wc.pwell[q]) return;
+    const double a = wc.aww[wc.pwell[q]];
+#pragma unroll
+    for (int r = 0; r < B; r++)
+#pragma unroll
+        for (int c = 0; c < B; c++)
+            Jb[r * B + c] = __dsub_rn(Jb[r * B + c],
+                                      __ddiv_rn(__dmul_rn(wc.apw[(long)r * wc.nperf + q], wc.awp[(long)c * wc.nperf + q2]), a));
+}
+
+template <int B>
+__device__ __forceinline__ void qi_weights(const double *D, double *w) {
+    const double D01 = D[0 * B + 1], D11 = D[1 * B + 1];
     w[0] = 1.0;
     if constexpr (B == 2) {
         w[1] = -(D01 / D11);
     } else {
-        const double D02 = J[(0 * B + 2) * (long)N + i];
-        const double D12 = J[(1 * B + 2) * (long)N + i], D21 = J[(2 * B + 1) * (long)N + i],
-                     D22 = J[(2 * B + 2) * (long)N + i];
+        const double D02 = D[0 * B + 2];
+        const double D12 = D[1 * B + 2], D21 = D[2 * B + 1], D22 = D[2 * B + 2];
         const double det = __dsub_rn(__dmul_rn(D11, D22), __dmul_rn(D12, D21));
         w[1] = __ddiv_rn(__dsub_rn(__dmul_rn(D02, D21), __dmul_rn(D01, D22)), det);
         w[2] = __ddiv_rn(__dsub_rn(__dmul_rn(D01, D12), __dmul_rn(D02, D11)), det);
     }
 }
 
-// decoupled block (row cell i, direction d) from J and the weights of i
+// decoupled block (row cell i, direction d): Ahat = L_i J_id, products summed in
+// row order without contraction (quasi-IMPES: L = [w^T; 0 I], so the pressure
+// row is J_0c + w1 J_1c + w2 J_2c exactly as the oracle forms it)
 template <int B>
-__device__ __forceinline__ void ahat_block(const double *__restrict__ J, int N, int i, int d, const double *w, double *A) {
+__device__ __forceinline__ void ahat_block(const double *__restrict__ J, long N, int i, int d, int j, const WellCorr &wc,
+                                           const double *L, double *A) {
+    double Jb[B * B];
+    load_jblock<B>(J, N, i, d, j, wc, Jb);
 #pragma unroll
     for (int r = 0; r < B; r++)
 #pragma unroll
-        for (int c = 0; c < B; c++) A[r * B + c] = J[(long)((d * B + r) * B + c) * N + i];
-#pragma unroll
-    for (int c = 0; c < B; c++) {
-        double t = __dadd_rn(A[c], __dmul_rn(w[1], A[B + c]));
-        if (B == 3) t = __dadd_rn(t, __dmul_rn(w[2], A[2 * B + c]));
-        A[c] = t;
-    }
+        for (int c = 0; c < B; c++) {
+            double t = __dmul_rn(L[r * B], Jb[c]);
+            t = __dadd_rn(t, __dmul_rn(L[r * B + 1], Jb[B + c]));
+            if (B == 3) t = __dadd_rn(t, __dmul_rn(L[r * B + 2], Jb[2 * B + c]));
+            A[r * B + c] = t;
+        }
 }
 
+template <int B>
+__device__ __forceinline__ void load_lsc(const double *__restrict__ lsc, long N, int i, double *L) {
+#pragma unroll
+    for (int t = 0; t < B * B; t++) L[t] = lsc[(long)t * N + i];
+}
+
+// inverse of a diagonal block by cofactors, every operation rounded as written
+// (the ABF scaling feeds the AMG hierarchy, which is built bit-exactly)
+template <int B>
+__device__ __forceinline__ void inv_block_rn(const double *A, double *Ai) {
+#define M_(a, b) __dmul_rn(A[a], A[b])
+    if constexpr (B == 2) {
+        const double det = __dsub_rn(M_(0, 3), M_(1, 2));
+        Ai[0] = __ddiv_rn(A[3], det); Ai[1] = __ddiv_rn(-A[1], det);
+        Ai[2] = __ddiv_rn(-A[2], det); Ai[3] = __ddiv_rn(A[0], det);
+    } else {
+        const double c00 = __dsub_rn(M_(4, 8), M_(5, 7));
+        const double c01 = __dsub_rn(M_(5, 6), M_(3, 8));
+        const double c02 = __dsub_rn(M_(3, 7), M_(4, 6));
+        const double det = __dadd_rn(__dadd_rn(__dmul_rn(A[0], c00), __dmul_rn(A[1], c01)), __dmul_rn(A[2], c02));
+        Ai[0] = __ddiv_rn(c00, det);
+        Ai[1] = __ddiv_rn(__dsub_rn(M_(2, 7), M_(1, 8)), det);
+        Ai[2] = __ddiv_rn(__dsub_rn(M_(1, 5), M_(2, 4)), det);
+        Ai[3] = __ddiv_rn(c01, det);
+        Ai[4] = __ddiv_rn(__dsub_rn(M_(0, 8), M_(2, 6)), det);
+        Ai[5] = __ddiv_rn(__dsub_rn(M_(2, 3), M_(0, 5)), det);
+        Ai[6] = __ddiv_rn(c02, det);
+        Ai[7] = __ddiv_rn(__dsub_rn(M_(1, 6), M_(0, 7)), det);
+        Ai[8] = __ddiv_rn(__dsub_rn(M_(0, 4), M_(1, 3)), det);
+    }
+#undef M_
+}
+
+// left scaling per cell (quasi-IMPES or ABF), its first row, the pressure
+// block A_p and the decoupled matrix in the apply precision
 template <int B, typename T>
-__global__ void qi_kernel(GridDesc g, const double *__restrict__ J, double *__restrict__ qiw, T *__restrict__ qiwT,
-                          double *__restrict__ ap, T *__restrict__ apT, T *__restrict__ ahat) {
+__global__ void qi_kernel(GridDesc g, const double *__restrict__ J, WellCorr wc, int abf, double *__restrict__ lsc,
+                          T *__restrict__ lscT, double *__restrict__ qiw, T *__restrict__ qiwT, double *__restrict__ ap,
+                          T *__restrict__ apT, T *__restrict__ ahat) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const long N = g.N;
     if (i >= N) return;
-    double w[3] = {1.0, 0.0, 0.0};
-    qi_weights<B>(J, N, i, w);
+    double L[B * B], D[B * B];
+    load_jblock<B>(J, N, i, 0, i, wc, D);
+    if (abf) {
+        inv_block_rn<B>(D, L);
+    } else {
+        double w[3] = {1.0, 0.0, 0.0};
+        qi_weights<B>(D, w);
 #pragma unroll
-    for (int c = 0; c < B; c++) { qiw[(long)c * N + i] = w[c]; qiwT[(long)c * N + i] = (T)w[c]; }
+        for (int t = 0; t < B * B; t++) L[t] = (t / B == t % B) ? 1.0 : 0.0;
+        L[1] = w[1];
+        if (B == 3) L[2] = w[2];
+    }
+#pragma unroll
+    for (int t = 0; t < B * B; t++) { lsc[(long)t * N + i] = L[t]; lscT[(long)t * N + i] = (T)L[t]; }
+#pragma unroll
+    for (int c = 0; c < B; c++) { qiw[(long)c * N + i] = L[c]; qiwT[(long)c * N + i] = (T)L[c]; }
+    const Cell cc = cell_of(g, i);
     for (int d = 0; d < 7; d++) {
         double A[B * B];
-        ahat_block<B>(J, N, i, d, w, A);
-        const bool has = nbr7(g, i, d) >= 0;
+        const int j = nbrc(g, cc, d);
+        ahat_block<B>(J, N, i, d, j, wc, L, A);
+        const bool has = j >= 0;
         ap[(long)d * N + i] = has ? A[0] : 0.0;
         apT[(long)d * N + i] = has ? (T)A[0] : (T)0;
 #pragma unroll
@@ -189,20 +277,18 @@ __device__ __forceinline__ void inv_block(const double *A, double *Ai) {
 // mode 0: inverse of Ahat_ii for every cell (block-Jacobi) or red cells only (mode 1);
 // mode 2: inverse of J_ii (plain block-Jacobi, no decoupling)
 template <int B>
-__global__ void diag_inv_kernel(GridDesc g, const double *__restrict__ J, const double *__restrict__ qiw, int mode,
-                                double *__restrict__ dinv) {
+__global__ void diag_inv_kernel(GridDesc g, const double *__restrict__ J, WellCorr wc, const double *__restrict__ lsc,
+                                int mode, double *__restrict__ dinv) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const long N = g.N;
     if (i >= N) return;
     if (mode == 1 && is_black(g, i)) return;
-    double w[3] = {1.0, 0.0, 0.0}, A[B * B], Ai[B * B];
+    double L[B * B], A[B * B], Ai[B * B];
     if (mode == 2) {
-#pragma unroll
-        for (int t = 0; t < B * B; t++) A[t] = J[(long)t * N + i];
+        load_jblock<B>(J, N, i, 0, i, wc, A);
     } else {
-#pragma unroll
-        for (int c = 0; c < B; c++) w[c] = qiw[(long)c * N + i];
-        ahat_block<B>(J, N, i, 0, w, A);
+        load_lsc<B>(lsc, N, i, L);
+        ahat_block<B>(J, N, i, 0, i, wc, L, A);
     }
     inv_block<B>(A, Ai);
 #pragma unroll
@@ -211,24 +297,22 @@ __global__ void diag_inv_kernel(GridDesc g, const double *__restrict__ J, const 
 
 // black cells: D = Ahat_ii - sum_d Ahat_{i,d} Dinv_k Ahat_{k,opp(d)}
 template <int B>
-__global__ void ilu_black_kernel(GridDesc g, const double *__restrict__ J, const double *__restrict__ qiw,
+__global__ void ilu_black_kernel(GridDesc g, const double *__restrict__ J, WellCorr wc, const double *__restrict__ lsc,
                                  double *__restrict__ dinv) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const long N = g.N;
     if (i >= N || !is_black(g, i)) return;
-    double wi[3] = {1.0, 0.0, 0.0};
-#pragma unroll
-    for (int c = 0; c < B; c++) wi[c] = qiw[(long)c * N + i];
+    double Li[B * B];
+    load_lsc<B>(lsc, N, i, Li);
     double D[B * B];
-    ahat_block<B>(J, N, i, 0, wi, D);
+    ahat_block<B>(J, N, i, 0, i, wc, Li, D);
     for (int d = 1; d < 7; d++) {
         const int k = nbr7(g, i, d);
         if (k < 0) continue;
-        double wk[3] = {1.0, 0.0, 0.0}, Aik[B * B], Aki[B * B], Dk[B * B], T1[B * B];
-#pragma unroll
-        for (int c = 0; c < B; c++) wk[c] = qiw[(long)c * N + k];
-        ahat_block<B>(J, N, i, d, wi, Aik);
-        ahat_block<B>(J, N, k, opp(d), wk, Aki);
+        double Lk[B * B], Aik[B * B], Aki[B * B], Dk[B * B], T1[B * B];
+        load_lsc<B>(lsc, N, k, Lk);
+        ahat_block<B>(J, N, i, d, k, wc, Li, Aik);
+        ahat_block<B>(J, N, k, opp(d), i, wc, Lk, Aki);
 #pragma unroll
         for (int t = 0; t < B * B; t++) Dk[t] = dinv[(long)t * N + k];
 #pragma unroll
@@ -530,13 +614,15 @@ __global__ void gj_extract_kernel(int n, const double *__restrict__ aug, T *__re
 // ---------------------------------------------------------------------------
 // apply kernels (precision T)
 // ---------------------------------------------------------------------------
+// f0 = first row of L times r (quasi-IMPES: L_00 = 1); e0 = f0 / l1
 template <int B, typename T>
-__global__ void restrict_p_kernel(int N, const double *__restrict__ r, const T *__restrict__ wT, const T *__restrict__ dinv0,
-                                  T *__restrict__ f0, T *__restrict__ e0, const int *done) {
+__global__ void restrict_p_kernel(int N, const double *__restrict__ r, const T *__restrict__ wT, int full,
+                                  const T *__restrict__ dinv0, T *__restrict__ f0, T *__restrict__ e0, const int *done) {
     if (skip(done)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    T t = (T)r[i] + wT[(long)N + i] * (T)r[(long)N + i];
+    const T r0 = full ? wT[i] * (T)r[i] : (T)r[i];
+    T t = r0 + wT[(long)N + i] * (T)r[(long)N + i];
     if (B == 3) t += wT[2L * N + i] * (T)r[2L * N + i];
     f0[i] = t;
     e0[i] = t * dinv0[i];
@@ -611,42 +697,140 @@ __global__ void copy_add_kernel(int n, const T *__restrict__ x, T *__restrict__ 
     if (i < n) y[i] = mode ? y[i] + x[i] : x[i];
 }
 
-// e = Inv f on the coarsest level: one warp per row
+// e = Inv f on the coarsest level (FP64 inverse and sum): one warp per row
 template <typename T>
-__global__ void coarse_solve_kernel(int n, const T *__restrict__ Inv, const T *__restrict__ f, T *__restrict__ e,
+__global__ void coarse_solve_kernel(int n, const double *__restrict__ Inv, const T *__restrict__ f, T *__restrict__ e,
                                     const int *done) {
     if (skip(done)) return;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= n) return;
-    T s = (T)0;
-    for (int j = lane; j < n; j += 32) s += Inv[(long)warp * n + j] * f[j];
+    double s = 0.0;
+    for (int j = lane; j < n; j += 32) s += Inv[(long)warp * n + j] * (double)f[j];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) e[warp] = s;
+    if (lane == 0) e[warp] = (T)s;
 }
 
-// stage F, pass 1: r2 = rhat - Ahat[:,p] e_p; red cells z = Dinv r2, black keep r2
+// ---- the coarse end of the V-cycle in one launch --------------------------
+// Levels l0..nl-1 (each at most kCoarseRows rows) run inside one thread-block
+// cluster: the same row operations as the per-level kernels, with a cluster
+// barrier between dependent sweeps instead of a kernel boundary.  On entry
+// level l0 holds f and its pre-smoothed e; on exit its corrected vector is e2.
+constexpr int kCoarseCtas = 8, kCoarseThreads = 1024, kCoarseRows = 2 * kCoarseCtas * kCoarseThreads;
+constexpr int kCoarseMaxLevels = 24;
+
+template <typename T>
+struct CoarseLevel {
+    int n, width;
+    const int *colA;     // self-padded ELL columns [width][n]
+    const T *val;        // [width][n]
+    const T *dinv;       // 1 / l1 row sums
+    const int *agg;      // row -> next-level aggregate
+    const int *moff, *mem;
+    T *f, *e, *e2;
+};
+
+template <typename T>
+struct CoarseCycle {
+    int nlev;                          // levels in lv (the last one is the coarsest)
+    const double *inv;                 // coarsest: dense inverse, row-major (FP64)
+    CoarseLevel<T> lv[kCoarseMaxLevels];
+};
+
+template <typename T>
+__device__ __forceinline__ T ell_dot(const CoarseLevel<T> &L, int i, const T *__restrict__ e) {
+    T t = (T)0;
+#pragma unroll 4
+    for (int k = 0; k < L.width; k++) t += L.val[(long)k * L.n + i] * e[L.colA[(long)k * L.n + i]];
+    return t;
+}
+
+__device__ __forceinline__ void cluster_barrier() {
+    __threadfence();                   // global writes of this thread before the barrier
+    cg::this_cluster().sync();
+}
+
+template <typename T>
+__global__ void __cluster_dims__(kCoarseCtas, 1, 1) __launch_bounds__(kCoarseThreads, 1)
+coarse_cycle_kernel(const CoarseCycle<T> cc, const int *done) {
+    if (skip(done)) return;            // uniform over the cluster: no thread reaches a barrier alone
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    const int last = cc.nlev - 1;
+    for (int l = 0; l < last; l++) {
+        const CoarseLevel<T> &L = cc.lv[l], &C = cc.lv[l + 1];
+        for (int i = tid; i < L.n; i += nt) L.e2[i] = L.f[i] - ell_dot(L, i, L.e);
+        cluster_barrier();
+        for (int I = tid; I < C.n; I += nt) {
+            T s = (T)0;
+            for (int q = L.moff[I]; q < L.moff[I + 1]; q++) s += L.e2[L.mem[q]];
+            C.f[I] = s;
+            if (l + 1 < last) C.e[I] = s * C.dinv[I];
+        }
+        cluster_barrier();
+    }
+    {
+        const CoarseLevel<T> &C = cc.lv[last];
+        const int warp = tid >> 5, lane = threadIdx.x & 31, nw = nt >> 5;
+        for (int r = warp; r < C.n; r += nw) {
+            double s = 0.0;
+            for (int j = lane; j < C.n; j += 32) s += cc.inv[(long)r * C.n + j] * (double)C.f[j];
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+            if (lane == 0) C.e[r] = (T)s;
+        }
+    }
+    cluster_barrier();
+    for (int l = last - 1; l >= 0; l--) {
+        const CoarseLevel<T> &L = cc.lv[l], &C = cc.lv[l + 1];
+        const T *ec = (l + 1 == last) ? C.e : C.e2;
+        for (int i = tid; i < L.n; i += nt) L.e[i] += ec[L.agg[i]];
+        cluster_barrier();
+        for (int i = tid; i < L.n; i += nt) L.e2[i] = L.e[i] + (L.f[i] - ell_dot(L, i, L.e)) * L.dinv[i];
+        if (l > 0) cluster_barrier();
+    }
+}
+
+// stage F, pass 1: r2 = rhat - Ahat[:,p] e_p; red cells z = Dinv r2, black keep r2.
+// rhat = L r from the FP64 residual (lscT = null: quasi-IMPES, only the first row
+// differs from the identity) or, when r is null, the given vector rh; ep may be null.
 template <int B, typename T>
 __global__ void stage2_a_kernel(GridDesc g, const double *__restrict__ r, const T *__restrict__ wT,
-                                const T *__restrict__ ahat, const T *__restrict__ dinv, const T *__restrict__ ep,
-                                T *__restrict__ r2, T *__restrict__ z, int rb, const int *done) {
+                                const T *__restrict__ lscT, const T *__restrict__ rh, const T *__restrict__ ahat,
+                                const T *__restrict__ dinv, const T *__restrict__ ep, T *__restrict__ r2,
+                                T *__restrict__ z, int rb, const int *done) {
     if (skip(done)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const long N = g.N;
     if (i >= N) return;
     T v[B];
+    if (!r) {
 #pragma unroll
-    for (int c = 0; c < B; c++) v[c] = (T)r[(long)c * N + i];
-    T rp = v[0] + wT[(long)N + i] * v[1];
-    if (B == 3) rp += wT[2L * N + i] * v[2];
-    v[0] = rp;
+        for (int c = 0; c < B; c++) v[c] = rh[(long)c * N + i];
+    } else if (lscT) {
+        T u[B];
+#pragma unroll
+        for (int c = 0; c < B; c++) u[c] = (T)r[(long)c * N + i];
+#pragma unroll
+        for (int rr = 0; rr < B; rr++) {
+            T t = lscT[(long)(rr * B) * N + i] * u[0] + lscT[(long)(rr * B + 1) * N + i] * u[1];
+            if (B == 3) t += lscT[(long)(rr * B + 2) * N + i] * u[2];
+            v[rr] = t;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < B; c++) v[c] = (T)r[(long)c * N + i];
+        T rp = v[0] + wT[(long)N + i] * v[1];
+        if (B == 3) rp += wT[2L * N + i] * v[2];
+        v[0] = rp;
+    }
     const Cell cc = cell_of(g, i);
+    if (ep) {
 #pragma unroll
-    for (int d = 0; d < 7; d++) {
-        const int j = nbrc(g, cc, d);
-        if (j < 0) continue;
-        const T e = ep[j];
+        for (int d = 0; d < 7; d++) {
+            const int j = nbrc(g, cc, d);
+            if (j < 0) continue;
+            const T e = ep[j];
 #pragma unroll
-        for (int c = 0; c < B; c++) v[c] -= ahat[(long)(d * B * B + c * B) * N + i] * e;
+            for (int c = 0; c < B; c++) v[c] -= ahat[(long)(d * B * B + c * B) * N + i] * e;
+        }
     }
     if (rb && is_black(g, i)) {
 #pragma unroll
@@ -662,11 +846,67 @@ __global__ void stage2_a_kernel(GridDesc g, const double *__restrict__ r, const 
     }
 }
 
+// CPR-FPF, after the first stage F (x0): rh = L r - Ahat x0 over the full 7-point
+// block stencil; f0 = rh_p, e0 = f0 / l1 start stage P
+template <int B, typename T>
+__global__ void fpf_resid_kernel(GridDesc g, const double *__restrict__ r, const T *__restrict__ wT,
+                                 const T *__restrict__ lscT, const T *__restrict__ ahat, const T *__restrict__ x0,
+                                 const T *__restrict__ dinv0, T *__restrict__ rh, T *__restrict__ f0, T *__restrict__ e0,
+                                 const int *done) {
+    if (skip(done)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const long N = g.N;
+    if (i >= N) return;
+    T v[B], u[B];
+#pragma unroll
+    for (int c = 0; c < B; c++) u[c] = (T)r[(long)c * N + i];
+    if (lscT) {
+#pragma unroll
+        for (int rr = 0; rr < B; rr++) {
+            T t = lscT[(long)(rr * B) * N + i] * u[0] + lscT[(long)(rr * B + 1) * N + i] * u[1];
+            if (B == 3) t += lscT[(long)(rr * B + 2) * N + i] * u[2];
+            v[rr] = t;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < B; c++) v[c] = u[c];
+        T rp = v[0] + wT[(long)N + i] * v[1];
+        if (B == 3) rp += wT[2L * N + i] * v[2];
+        v[0] = rp;
+    }
+    const Cell cc = cell_of(g, i);
+#pragma unroll
+    for (int d = 0; d < 7; d++) {
+        const int j = nbrc(g, cc, d);
+        if (j < 0) continue;
+        T xj[B];
+#pragma unroll
+        for (int c = 0; c < B; c++) xj[c] = x0[(long)c * N + j];
+#pragma unroll
+        for (int rr = 0; rr < B; rr++)
+#pragma unroll
+            for (int c = 0; c < B; c++) v[rr] -= ahat[(long)(d * B * B + rr * B + c) * N + i] * xj[c];
+    }
+#pragma unroll
+    for (int c = 0; c < B; c++) rh[(long)c * N + i] = v[c];
+    f0[i] = v[0];
+    e0[i] = v[0] * dinv0[i];
+}
+
+// stage-F output of component r: x (+ e_p on the pressure row) (+ addv, the first
+// stage F of CPR-FPF), added in the order the stages ran
+template <typename T>
+__device__ __forceinline__ T fin(T x, int r, int i, long N, const T *__restrict__ ep, const T *__restrict__ addv) {
+    if (r == 0 && ep) x += ep[i];
+    if (addv) x += addv[(long)r * N + i];
+    return x;
+}
+
 // stage F, pass 2 (black cells): z = Dinv (r2 - sum_d Ahat_{i,d} z_red(nbr)); out = z + e_p
 template <int B, typename T, typename TZ>
 __global__ void stage2_b_kernel(GridDesc g, const T *__restrict__ ahat, const T *__restrict__ dinv,
-                                const T *__restrict__ r2, T *__restrict__ z, const T *__restrict__ ep, TZ *__restrict__ out,
-                                const int *done) {
+                                const T *__restrict__ r2, T *__restrict__ z, const T *__restrict__ ep,
+                                const T *__restrict__ addv, TZ *__restrict__ out, const int *done) {
     if (skip(done)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const long N = g.N;
@@ -694,7 +934,7 @@ __global__ void stage2_b_kernel(GridDesc g, const T *__restrict__ ahat, const T 
 #pragma unroll
         for (int q = 0; q < B; q++) s += dinv[(long)(r * B + q) * N + i] * t[q];
         z[(long)r * N + i] = s;
-        out[(long)r * N + i] = (TZ)(r == 0 ? s + ep[i] : s);
+        out[(long)r * N + i] = (TZ)fin<T>(s, r, i, N, ep, addv);
     }
 }
 
@@ -702,7 +942,8 @@ __global__ void stage2_b_kernel(GridDesc g, const T *__restrict__ ahat, const T 
 // (rb = 0: block-Jacobi, out = z + e_p for every cell)
 template <int B, typename T, typename TZ>
 __global__ void stage2_c_kernel(GridDesc g, const T *__restrict__ ahat, const T *__restrict__ dinv, const T *__restrict__ z,
-                                const T *__restrict__ ep, TZ *__restrict__ out, int rb, const int *done) {
+                                const T *__restrict__ ep, const T *__restrict__ addv, TZ *__restrict__ out, int rb,
+                                const int *done) {
     if (skip(done)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const long N = g.N;
@@ -710,8 +951,7 @@ __global__ void stage2_c_kernel(GridDesc g, const T *__restrict__ ahat, const T 
     if (!rb) {
 #pragma unroll
         for (int r = 0; r < B; r++) {
-            const T s = z[(long)r * N + i];
-            out[(long)r * N + i] = (TZ)(r == 0 ? s + ep[i] : s);
+            out[(long)r * N + i] = (TZ)fin<T>(z[(long)r * N + i], r, i, N, ep, addv);
         }
         return;
     }
@@ -737,8 +977,7 @@ __global__ void stage2_c_kernel(GridDesc g, const T *__restrict__ ahat, const T 
         T s = (T)0;
 #pragma unroll
         for (int q = 0; q < B; q++) s += dinv[(long)(r * B + q) * N + i] * t[q];
-        const T x = z[(long)r * N + i] - s;
-        out[(long)r * N + i] = (TZ)(r == 0 ? x + ep[i] : x);
+        out[(long)r * N + i] = (TZ)fin<T>(z[(long)r * N + i] - s, r, i, N, ep, addv);
     }
 }
 
@@ -1069,9 +1308,12 @@ static sim_status finish_levels(sim_t *s) {
         gj_step_kernel<<<sim_blocks((long)aug), SIM_THREADS, 0, s->stream>>>(n, k, (k & 1) ? A1 : A0, (k & 1) ? A0 : A1);
         s->launches++;
     }
-    C.coarse_inv = dev_alloc_async(s, sizeof(T) * (size_t)n * n);
+    // the coarsest inverse stays FP64 in both forms: the coarse matrices of
+    // strongly heterogeneous fields are ill-conditioned, and the product is tiny
+    C.coarse_inv = dev_alloc_async(s, sizeof(double) * (size_t)n * n);
     if (!C.coarse_inv) return s->err;
-    gj_extract_kernel<T><<<sim_blocks((long)n * n), SIM_THREADS, 0, s->stream>>>(n, (n & 1) ? A1 : A0, (T *)C.coarse_inv);
+    gj_extract_kernel<double><<<sim_blocks((long)n * n), SIM_THREADS, 0, s->stream>>>(n, (n & 1) ? A1 : A0,
+                                                                                    (double *)C.coarse_inv);
     s->launches++;
     dev_free_async(s, A0); dev_free_async(s, A1);
     SIM_CK(s, cudaGetLastError());
@@ -1128,21 +1370,28 @@ template <int B, typename T>
 static sim_status setup_bt(sim_t *s) {
     const int N = s->N;
     const int nb = sim_blocks(N);
+    WellCorr wc;
+    if (s->nrate > 0) {
+        wc.cell_perf = s->cell_perf; wc.pwell = s->perf_well;
+        wc.apw = s->apw; wc.awp = s->awp; wc.aww = s->aww; wc.nperf = s->nperf;
+    }
     if (s->opt.precond == SIM_PRECOND_BJACOBI) {
-        diag_inv_kernel<B><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, s->J, s->qiw, 2, s->dinv_d);
+        diag_inv_kernel<B><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, s->J, wc, s->lsc, 2, s->dinv_d);
         SIM_LAUNCHED(s);
         return SIM_OK;
     }
     if (s->opt.precond != SIM_PRECOND_CPR) return SIM_OK;
-    qi_kernel<B, T><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, s->J, s->qiw, (T *)s->qiwT, s->ap, (T *)s->apT, (T *)s->ahat);
+    qi_kernel<B, T><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, s->J, wc, s->opt.decouple == SIM_DECOUPLE_ABF, s->lsc,
+                                                       (T *)s->lscT, s->qiw, (T *)s->qiwT, s->ap, (T *)s->apT,
+                                                       (T *)s->ahat);
     SIM_LAUNCHED(s);
     if (amg_setup(s) != SIM_OK) return s->err;
     s->lev[0].valT = s->apT;
     const int rb = s->opt.stage2 == SIM_STAGE2_ILU0_RB;
-    diag_inv_kernel<B><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, s->J, s->qiw, rb ? 1 : 0, s->dinv_d);
+    diag_inv_kernel<B><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, s->J, wc, s->lsc, rb ? 1 : 0, s->dinv_d);
     SIM_LAUNCHED(s);
     if (rb) {
-        ilu_black_kernel<B><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, s->J, s->qiw, s->dinv_d);
+        ilu_black_kernel<B><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, s->J, wc, s->lsc, s->dinv_d);
         SIM_LAUNCHED(s);
     }
     if (sizeof(T) != sizeof(double)) {
@@ -1162,11 +1411,39 @@ sim_status cpr_setup(sim_t *s) {
     return SIM_OK;
 }
 
+// first level handled by the one-launch coarse cycle (nl: no fusion)
+static int coarse_start(const sim_t *s) {
+    const int nl = (int)s->lev.size();
+    if (nl < 3) return nl;
+    int l0 = nl - 1;
+    while (l0 - 1 >= 1 && s->lev[l0 - 1].n <= kCoarseRows && nl - (l0 - 1) <= kCoarseMaxLevels) l0--;
+    return (nl - l0 >= 3) ? l0 : nl;   // worth a launch only when it replaces several
+}
+
+template <typename T>
+static sim_status coarse_cycle(sim_t *s, int l0, const int *done) {
+    const int nl = (int)s->lev.size();
+    CoarseCycle<T> cc;
+    cc.nlev = nl - l0;
+    cc.inv = (const double *)s->lev[nl - 1].coarse_inv;
+    for (int l = l0; l < nl; l++) {
+        const AmgLevel &L = s->lev[l];
+        CoarseLevel<T> &d = cc.lv[l - l0];
+        d.n = L.n; d.width = L.width; d.colA = L.colA; d.val = (const T *)L.valT; d.dinv = (const T *)L.dinvT;
+        d.agg = L.agg; d.moff = L.moff; d.mem = L.mem;
+        d.f = (T *)L.f; d.e = (T *)L.e; d.e2 = (T *)L.e2;
+    }
+    coarse_cycle_kernel<T><<<kCoarseCtas, kCoarseThreads, 0, s->stream>>>(cc, done);
+    SIM_LAUNCHED(s);
+    return SIM_OK;
+}
+
 template <typename T>
 static sim_status vcycle(sim_t *s, const int *done) {
     const int nl = (int)s->lev.size();
+    const int lf = s->opt.fused_coarse ? coarse_start(s) : nl;
     // down: r = f - A e; f_{l+1} = P^T r; e_{l+1} = f_{l+1} / l1 (not on the coarsest)
-    for (int l = 0; l + 1 < nl; l++) {
+    for (int l = 0; l + 1 < nl && l < lf; l++) {
         AmgLevel &L = s->lev[l], &C = s->lev[l + 1];
         const bool coarsest = (l + 1 == nl - 1);
         amg_resid_kernel<T><<<sim_blocks(L.n, s->tune_amg), s->tune_amg, 0, s->stream>>>(level_matT<T>(s, L, l), (const T *)L.f,
@@ -1177,12 +1454,16 @@ static sim_status vcycle(sim_t *s, const int *done) {
                                                                            (const T *)C.dinvT, done);
         SIM_LAUNCHED(s);
     }
-    AmgLevel &Cn = s->lev[nl - 1];
-    coarse_solve_kernel<T><<<sim_blocks((long)Cn.n * 32), SIM_THREADS, 0, s->stream>>>(Cn.n, (const T *)Cn.coarse_inv,
-                                                                                    (const T *)Cn.f, (T *)Cn.e, done);
-    SIM_LAUNCHED(s);
+    if (lf < nl) {
+        if (coarse_cycle<T>(s, lf, done) != SIM_OK) return s->err;
+    } else {
+        AmgLevel &Cn = s->lev[nl - 1];
+        coarse_solve_kernel<T><<<sim_blocks((long)Cn.n * 32), SIM_THREADS, 0, s->stream>>>(Cn.n, (const double *)Cn.coarse_inv,
+                                                                                        (const T *)Cn.f, (T *)Cn.e, done);
+        SIM_LAUNCHED(s);
+    }
     // up: e_l += P e_{l+1}; e2_l = smooth(e_l); the corrected vector of level l is e2_l
-    for (int l = nl - 2; l >= 0; l--) {
+    for (int l = (lf < nl ? lf : nl - 1) - 1; l >= 0; l--) {
         AmgLevel &L = s->lev[l], &C = s->lev[l + 1];
         const T *ec = (l + 1 == nl - 1) ? (const T *)C.e : (const T *)C.e2;
         amg_prolong_kernel<T><<<sim_blocks(L.n, s->tune_amg), s->tune_amg, 0, s->stream>>>(L.n, L.agg, ec, (T *)L.e, done);
@@ -1206,12 +1487,37 @@ static sim_status apply_btz(sim_t *s, const double *r, TZ *z, const int *done) {
         return SIM_OK;
     }
     AmgLevel &L0 = s->lev[0];
-    restrict_p_kernel<B, T><<<nb, SIM_THREADS, 0, s->stream>>>(N, r, (const T *)s->qiwT, (const T *)L0.dinvT, (T *)L0.f,
-                                                              (T *)L0.e, done);
-    SIM_LAUNCHED(s);
+    const int rb = s->opt.stage2 == SIM_STAGE2_ILU0_RB;
+    const T *dinv = sizeof(T) == sizeof(double) ? (const T *)s->dinv_d : (const T *)s->dinv;
+    const int full = s->opt.decouple == SIM_DECOUPLE_ABF;
+    const T *lscT = full ? (const T *)s->lscT : nullptr;
+    const bool fpf = s->opt.cpr_stages == 3;
+    if (fpf) {
+        // CPR-FPF: stage F on L r first (x0), then stage P on the residual it leaves
+        stage2_a_kernel<B, T><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, r, (const T *)s->qiwT, lscT, nullptr,
+                                                                (const T *)s->ahat, dinv, nullptr, (T *)s->r2,
+                                                                (T *)s->zr, rb, done);
+        SIM_LAUNCHED(s);
+        if (rb) {
+            stage2_b_kernel<B, T, T><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, (const T *)s->ahat, dinv, (const T *)s->r2,
+                                                                       (T *)s->zr, nullptr, nullptr, (T *)s->x0, done);
+            SIM_LAUNCHED(s);
+        }
+        stage2_c_kernel<B, T, T><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, (const T *)s->ahat, dinv, (const T *)s->zr,
+                                                                   nullptr, nullptr, (T *)s->x0, rb, done);
+        SIM_LAUNCHED(s);
+        fpf_resid_kernel<B, T><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, r, (const T *)s->qiwT, lscT, (const T *)s->ahat,
+                                                                 (const T *)s->x0, (const T *)L0.dinvT, (T *)s->rhT,
+                                                                 (T *)L0.f, (T *)L0.e, done);
+        SIM_LAUNCHED(s);
+    } else {
+        restrict_p_kernel<B, T><<<nb, SIM_THREADS, 0, s->stream>>>(N, r, (const T *)s->qiwT, full, (const T *)L0.dinvT,
+                                                                  (T *)L0.f, (T *)L0.e, done);
+        SIM_LAUNCHED(s);
+    }
     const T *ep;
     if (s->lev.size() == 1) {
-        coarse_solve_kernel<T><<<sim_blocks((long)L0.n * 32), SIM_THREADS, 0, s->stream>>>(L0.n, (const T *)L0.coarse_inv,
+        coarse_solve_kernel<T><<<sim_blocks((long)L0.n * 32), SIM_THREADS, 0, s->stream>>>(L0.n, (const double *)L0.coarse_inv,
                                                                                         (const T *)L0.f, (T *)L0.e2, done);
         SIM_LAUNCHED(s);
     } else if (vcycle<T>(s, done) != SIM_OK) {
@@ -1257,18 +1563,18 @@ static sim_status apply_btz(sim_t *s, const double *r, TZ *z, const int *done) {
         SIM_LAUNCHED(s);
         ep = (const T *)s->lep;
     }
-    const int rb = s->opt.stage2 == SIM_STAGE2_ILU0_RB;
-    const T *dinv = sizeof(T) == sizeof(double) ? (const T *)s->dinv_d : (const T *)s->dinv;
-    stage2_a_kernel<B, T><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, r, (const T *)s->qiwT, (const T *)s->ahat, dinv, ep,
-                                                            (T *)s->r2, (T *)s->zr, rb, done);
+    const T *addv = fpf ? (const T *)s->x0 : nullptr;
+    stage2_a_kernel<B, T><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, fpf ? nullptr : r, (const T *)s->qiwT, lscT,
+                                                            (const T *)s->rhT, (const T *)s->ahat, dinv, ep, (T *)s->r2,
+                                                            (T *)s->zr, rb, done);
     SIM_LAUNCHED(s);
     if (rb) {
         stage2_b_kernel<B, T, TZ><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, (const T *)s->ahat, dinv, (const T *)s->r2,
-                                                                    (T *)s->zr, ep, z, done);
+                                                                    (T *)s->zr, ep, addv, z, done);
         SIM_LAUNCHED(s);
     }
-    stage2_c_kernel<B, T, TZ><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, (const T *)s->ahat, dinv, (const T *)s->zr, ep, z,
-                                                                rb, done);
+    stage2_c_kernel<B, T, TZ><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, (const T *)s->ahat, dinv, (const T *)s->zr, ep, addv,
+                                                                z, rb, done);
     SIM_LAUNCHED(s);
     return SIM_OK;
 }
@@ -1289,27 +1595,57 @@ sim_status cpr_copy_level_ell(sim_t *s, int level, int *col, double *val) {
     return SIM_OK;
 }
 
+// Training pairs for the learned stage.  For Krylov vector v_j: f = (L v_j)_p,
+// one stage-P V-cycle e_p, the residual it leaves r' = f - A_p e_p (the input
+// of the learned stage in apply_btz), and as target the error that residual
+// corresponds to, A_p^-1 r', approximated by kRefine V-cycles of iterative
+// refinement.  Input r' / rms(r') with the log-transmissibility features;
+// target normalised by its own RMS (the stage is scaled by minimal residual).
+constexpr int kRefine = 8;
+
 template <typename T>
 static sim_status learned_pairs_t(sim_t *s, int k, float *x, float *y) {
     const int N = s->N;
     AmgLevel &L0 = s->lev[0];
+    const int full = s->opt.decouple == SIM_DECOUPLE_ABF;
+    const Mat<T> A0 = level_matT<T>(s, L0, 0);
+    auto cycle = [&](void) -> sim_status {
+        if (s->lev.size() == 1) {
+            coarse_solve_kernel<T><<<sim_blocks((long)L0.n * 32), SIM_THREADS, 0, s->stream>>>(
+                L0.n, (const double *)L0.coarse_inv, (const T *)L0.f, (T *)L0.e2, nullptr);
+            SIM_LAUNCHED(s);
+            return SIM_OK;
+        }
+        return vcycle<T>(s, nullptr);
+    };
     for (int j = 0; j < k; j++) {
         const double *v = s->V + (size_t)j * N * s->b;
-        if (s->b == 2) restrict_p_kernel<2, T><<<sim_blocks(N), SIM_THREADS, 0, s->stream>>>(N, v, (const T *)s->qiwT, (const T *)L0.dinvT, (T *)L0.f, (T *)L0.e, nullptr);
-        else restrict_p_kernel<3, T><<<sim_blocks(N), SIM_THREADS, 0, s->stream>>>(N, v, (const T *)s->qiwT, (const T *)L0.dinvT, (T *)L0.f, (T *)L0.e, nullptr);
+        if (s->b == 2) restrict_p_kernel<2, T><<<sim_blocks(N), SIM_THREADS, 0, s->stream>>>(N, v, (const T *)s->qiwT, full, (const T *)L0.dinvT, (T *)L0.f, (T *)L0.e, nullptr);
+        else restrict_p_kernel<3, T><<<sim_blocks(N), SIM_THREADS, 0, s->stream>>>(N, v, (const T *)s->qiwT, full, (const T *)L0.dinvT, (T *)L0.f, (T *)L0.e, nullptr);
         SIM_LAUNCHED(s);
-        if (s->lev.size() == 1) {
-            coarse_solve_kernel<T><<<sim_blocks((long)L0.n * 32), SIM_THREADS, 0, s->stream>>>(L0.n, (const T *)L0.coarse_inv, (const T *)L0.f, (T *)L0.e2, nullptr);
+        if (cycle() != SIM_OK) return s->err;
+        // r' = f - A_p e_p into rpT; the first refinement cycle starts from it
+        amg_resid_kernel<T><<<sim_blocks(N, 128), 128, 0, s->stream>>>(A0, (const T *)L0.f, (const T *)L0.e2, (T *)s->rpT,
+                                                                     nullptr);
+        SIM_LAUNCHED(s);
+        copy_add_kernel<T><<<sim_blocks(N), SIM_THREADS, 0, s->stream>>>(N, (const T *)s->rpT, (T *)s->lres, 0, nullptr);
+        SIM_LAUNCHED(s);
+        SIM_CK(s, cudaMemsetAsync(s->epacc, 0, sizeof(T) * (size_t)N, s->stream));
+        for (int c = 0; c < kRefine; c++) {
+            cycle_next_kernel<T><<<sim_blocks(N, 128), 128, 0, s->stream>>>(A0, (const T *)s->rpT, (const T *)s->epacc,
+                                                                           (const T *)L0.dinvT, (T *)L0.f, (T *)L0.e, nullptr);
             SIM_LAUNCHED(s);
-        } else if (vcycle<T>(s, nullptr) != SIM_OK) {
-            return s->err;
+            if (cycle() != SIM_OK) return s->err;
+            copy_add_kernel<T><<<sim_blocks(N), SIM_THREADS, 0, s->stream>>>(N, (const T *)L0.e2, (T *)s->epacc, 1, nullptr);
+            SIM_LAUNCHED(s);
         }
-        rms_kernel<T><<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(N, (const T *)L0.f, s->red, s->ticket, s->lrms, nullptr);
+        rms_kernel<T><<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(N, (const T *)s->lres, s->red, s->ticket, s->lrms, nullptr);
         SIM_LAUNCHED(s);
-        rms_kernel<T><<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(N, (const T *)L0.e2, s->red, s->ticket, s->lrms + 1, nullptr);
+        rms_kernel<T><<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(N, (const T *)s->epacc, s->red, s->ticket, s->lrms + 1,
+                                                                    nullptr);
         SIM_LAUNCHED(s);
-        pair_kernel<T><<<sim_blocks(N), SIM_THREADS, 0, s->stream>>>(N, (const T *)L0.f, (const T *)L0.e2, s->lrms, s->lfeat,
-                                                                    x + (size_t)j * N * 4, y + (size_t)j * N);
+        pair_kernel<T><<<sim_blocks(N), SIM_THREADS, 0, s->stream>>>(N, (const T *)s->lres, (const T *)s->epacc, s->lrms,
+                                                                    s->lfeat, x + (size_t)j * N * 4, y + (size_t)j * N);
         SIM_LAUNCHED(s);
     }
     return SIM_OK;

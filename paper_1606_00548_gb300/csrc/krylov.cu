@@ -46,13 +46,12 @@ __global__ void __launch_bounds__(512) spmv_kernel(GridDesc g, const double *__r
         double xv[B];
 #pragma unroll
         for (int c = 0; c < B; c++) xv[c] = ld(x, (long)c * N + j);
+        // accumulate straight into acc: b^2 FMAs per block and no separate adds
+        // (the SpMV is bound by the FP64 pipe, not by HBM, on this part)
 #pragma unroll
-        for (int r = 0; r < B; r++) {
-            double s = 0.0;
+        for (int r = 0; r < B; r++)
 #pragma unroll
-            for (int c = 0; c < B; c++) s += J[(long)((d * B + r) * B + c) * N + i] * xv[c];
-            acc[r] += s;
-        }
+            for (int c = 0; c < B; c++) acc[r] = fma(J[(long)((d * B + r) * B + c) * N + i], xv[c], acc[r]);
     }
 #pragma unroll
     for (int r = 0; r < B; r++) y[(long)r * N + i] = acc[r];
@@ -266,10 +265,10 @@ __global__ void xupdate_kernel(double *__restrict__ x, const Z *__restrict__ Zb,
     }
 }
 
-// r = b - y ; beta = ||r|| into ctl->beta
+// r = b - y ; ||r|| into *out
 __global__ void __launch_bounds__(SIM_THREADS) resid_kernel(const double *__restrict__ b, const double *__restrict__ y,
                                                             double *__restrict__ r, long n, double *partials,
-                                                            unsigned int *ticket, KrylovCtl *ctl) {
+                                                            unsigned int *ticket, double *out) {
     double acc[1] = {0.0};
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
         const double v = b[i] - y[i];
@@ -281,7 +280,7 @@ __global__ void __launch_bounds__(SIM_THREADS) resid_kernel(const double *__rest
         __shared__ double nrm;
         fold(partials, 1, &nrm);
         __syncthreads();
-        if (threadIdx.x == 0) { *ticket = 0u; ctl->beta = sqrt(nrm); }
+        if (threadIdx.x == 0) { *ticket = 0u; *out = sqrt(nrm); }
     }
 }
 
@@ -305,14 +304,198 @@ __global__ void cycle_init_kernel(KrylovCtl *ctl) {
     for (int k = t + 1; k <= SIM_MAX_M; k += blockDim.x) ctl->g[k] = 0.0;
 }
 
+// ---- BiCGSTAB (right-preconditioned, van der Vorst) ---------------------
+// One iteration is a fixed kernel sequence reading its scalars from the
+// device control block; the last block of each reduction updates them, so a
+// chunk of iterations is enqueued (or replayed as a graph) with no host
+// synchronisation.  Once ctl->done is set every later kernel returns at once.
+__device__ __forceinline__ bool bdone(const BicgCtl *c) { return *(volatile const int *)&c->done; }
+
+// start or restart from the current residual: rh = r, rho = (r, r)
+__global__ void __launch_bounds__(SIM_THREADS) bicg_restart_kernel(const double *__restrict__ r, double *__restrict__ rh,
+                                                                   long n, double *partials, unsigned int *ticket,
+                                                                   BicgCtl *ctl) {
+    double acc[1] = {0.0};
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const double v = r[i];
+        rh[i] = v;
+        acc[0] += v * v;
+    }
+    block_partials<1>(acc, 1, partials);
+    if (last_block(ticket)) {
+        __shared__ double d;
+        fold(partials, 1, &d);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            *ticket = 0u;
+            ctl->rho = d;
+            ctl->fresh = 1;
+            ctl->flag = 0;
+            ctl->half_j = -1;
+            ctl->done = (d == 0.0 || !(d == d)) ? 1 : 0;
+            if (ctl->done) ctl->flag = 2;
+        }
+    }
+}
+
+__global__ void bicg_init_kernel(BicgCtl *ctl, double tol, int max_it) {
+    ctl->tol = tol; ctl->max_it = max_it; ctl->it = 0;
+    ctl->rho_old = 1.0; ctl->alpha = 1.0; ctl->omega = 1.0;
+}
+
+__global__ void bicg_chunk_init_kernel(BicgCtl *ctl) { ctl->half_j = -1; }
+
+// p = r (first iteration of a start) or r + beta (p - omega v)
+__global__ void bicg_p_kernel(const double *__restrict__ r, const double *__restrict__ v, double *__restrict__ p, long n,
+                              const BicgCtl *ctl) {
+    if (bdone(ctl)) return;
+    const bool fresh = ctl->fresh;
+    const double om = ctl->omega;
+    const double beta = (ctl->rho / ctl->rho_old) * (ctl->alpha / om);
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        p[i] = fresh ? r[i] : r[i] + beta * (p[i] - om * v[i]);
+}
+
+// alpha = rho / (rh, v); one iteration counted
+__global__ void __launch_bounds__(SIM_THREADS) bicg_alpha_kernel(const double *__restrict__ rh, const double *__restrict__ v,
+                                                                 long n, double *partials, unsigned int *ticket,
+                                                                 BicgCtl *ctl) {
+    if (bdone(ctl)) return;
+    double acc[1] = {0.0};
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) acc[0] += rh[i] * v[i];
+    block_partials<1>(acc, 1, partials);
+    if (last_block(ticket)) {
+        __shared__ double d;
+        fold(partials, 1, &d);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            *ticket = 0u;
+            ctl->it++;
+            if (d == 0.0 || !(d == d)) { ctl->flag = 2; ctl->done = 1; }
+            else ctl->alpha = ctl->rho / d;
+        }
+    }
+}
+
+// s = r - alpha v; ||s|| <= tol ends the iteration at its half step (iteration j of the chunk)
+__global__ void __launch_bounds__(SIM_THREADS) bicg_s_kernel(const double *__restrict__ r, const double *__restrict__ v,
+                                                             double *__restrict__ sv, long n, double *partials,
+                                                             unsigned int *ticket, BicgCtl *ctl, int j) {
+    if (bdone(ctl)) return;
+    const double al = ctl->alpha;
+    double acc[1] = {0.0};
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const double t = r[i] - al * v[i];
+        sv[i] = t;
+        acc[0] += t * t;
+    }
+    block_partials<1>(acc, 1, partials);
+    if (last_block(ticket)) {
+        __shared__ double d;
+        fold(partials, 1, &d);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            *ticket = 0u;
+            if (sqrt(d) <= ctl->tol) { ctl->half_j = j; ctl->flag = 1; ctl->done = 1; }
+        }
+    }
+}
+
+// x += alpha p^ when iteration j stopped at its half step (runs after done is set)
+template <typename Z>
+__global__ void bicg_xhalf_kernel(double *__restrict__ x, const Z *__restrict__ ph, long n, const BicgCtl *ctl, int j) {
+    if (ctl->half_j != j) return;
+    const double al = ctl->alpha;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        x[i] += al * (double)ph[i];
+}
+
+// omega = (t, s) / (t, t)
+__global__ void __launch_bounds__(SIM_THREADS) bicg_omega_kernel(const double *__restrict__ t, const double *__restrict__ sv,
+                                                                 long n, double *partials, unsigned int *ticket,
+                                                                 BicgCtl *ctl) {
+    if (bdone(ctl)) return;
+    double acc[2] = {0.0, 0.0};
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const double ti = t[i];
+        acc[0] += ti * ti;
+        acc[1] += ti * sv[i];
+    }
+    block_partials<2>(acc, 2, partials);
+    if (last_block(ticket)) {
+        __shared__ double d[2];
+        fold(partials, 2, d);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            *ticket = 0u;
+            ctl->omega = d[0] > 0.0 ? d[1] / d[0] : 0.0;
+        }
+    }
+}
+
+// x += alpha p^ + omega s^; r = s - omega t; rho for the next iteration; tests
+template <typename Z>
+__global__ void __launch_bounds__(SIM_THREADS) bicg_xr_kernel(double *__restrict__ x, const Z *__restrict__ ph,
+                                                              const Z *__restrict__ sh, const double *__restrict__ sv,
+                                                              const double *__restrict__ t, double *__restrict__ r,
+                                                              const double *__restrict__ rh, long n, double *partials,
+                                                              unsigned int *ticket, BicgCtl *ctl) {
+    if (bdone(ctl)) return;
+    const double al = ctl->alpha, om = ctl->omega;
+    double acc[2] = {0.0, 0.0};
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        x[i] += al * (double)ph[i] + om * (double)sh[i];
+        const double ri = sv[i] - om * t[i];
+        r[i] = ri;
+        acc[0] += rh[i] * ri;
+        acc[1] += ri * ri;
+    }
+    block_partials<2>(acc, 2, partials);
+    if (last_block(ticket)) {
+        __shared__ double d[2];
+        fold(partials, 2, d);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            *ticket = 0u;
+            ctl->rho_old = ctl->rho;
+            ctl->rho = d[0];
+            ctl->rnorm = sqrt(d[1]);
+            ctl->fresh = 0;
+            if (ctl->rnorm <= ctl->tol) { ctl->flag = 1; ctl->done = 1; }
+            else if (om == 0.0 || !(om == om)) { ctl->flag = 2; ctl->done = 1; }
+            else if (d[0] == 0.0 || !(d[0] == d[0])) { ctl->flag = 2; ctl->done = 1; }
+            else if (ctl->it >= ctl->max_it) { ctl->flag = 3; ctl->done = 1; }
+        }
+    }
+}
+
+// ||a - b||
+__global__ void diff_norm_kernel(const double *__restrict__ a, const double *__restrict__ b, long n, double *partials,
+                                 unsigned int *ticket, double *out) {
+    double acc[1] = {0.0};
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const double d = a[i] - b[i];
+        acc[0] += d * d;
+    }
+    block_partials<1>(acc, 1, partials);
+    if (last_block(ticket)) {
+        __shared__ double nrm;
+        fold(partials, 1, &nrm);
+        __syncthreads();
+        if (threadIdx.x == 0) { *ticket = 0u; out[0] = sqrt(nrm); }
+    }
+}
+
 }  // namespace
 
 // ===========================================================================
+// y = S x: the block-stencil product, then the rate-controlled wells' Schur
+// term -A_pw A_ww^-1 A_wp x (Eq. 16 with the well unknowns eliminated)
 sim_status k_spmv_block(sim_t *s, const double *x, double *y, int bs) {
     if (s->b == 2) spmv_kernel<2, double><<<sim_blocks(s->N, bs), bs, 0, s->stream>>>(s->gd, s->J, x, y, nullptr);
     else spmv_kernel<3, double><<<sim_blocks(s->N, bs), bs, 0, s->stream>>>(s->gd, s->J, x, y, nullptr);
     SIM_LAUNCHED(s);
-    return SIM_OK;
+    return k_well_op<double>(s, x, y, nullptr);
 }
 
 sim_status k_spmv(sim_t *s, const double *x, double *y) { return k_spmv_block(s, x, y, s->tune_spmv); }
@@ -328,7 +511,7 @@ static sim_status spmv_done(sim_t *s, const void *x, bool xf, double *y, const i
         else spmv_kernel<3, double><<<nb, bs, 0, s->stream>>>(s->gd, s->J, (const double *)x, y, done);
     }
     SIM_LAUNCHED(s);
-    return SIM_OK;
+    return xf ? k_well_op<float>(s, (const float *)x, y, done) : k_well_op<double>(s, (const double *)x, y, done);
 }
 
 sim_status k_spmv_f(sim_t *s, const float *x, double *y) { return spmv_done(s, x, true, y, nullptr); }
@@ -381,9 +564,14 @@ sim_status k_fgmres(sim_t *s, const double *b, double *x, sim_linear_info *info)
     if (k_norm2(s, b, n, &bn) != SIM_OK) return s->err;
     li.b_norm = bn;
     SIM_CK(s, cudaMemsetAsync(x, 0, sizeof(double) * n, s->stream));
-    if (bn == 0.0) { li.converged = 1; if (info) *info = li; return SIM_OK; }
+    if (bn == 0.0) {
+        SIM_CK(s, cudaMemcpyAsync(s->r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->stream));
+        li.converged = 1;
+        if (info) *info = li;
+        return SIM_OK;
+    }
     if (!(bn == bn)) { if (info) *info = li; return sim_fail(s, SIM_ENAN, "non-finite right-hand side"); }
-    const double tol = s->opt.lin_tol * bn;
+    const double tol = s->theta * bn;
     KrylovCtl *ctl = s->ctl;
     SIM_CK(s, cudaMemcpyAsync(s->r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->stream));
     SIM_CK(s, cudaMemcpyAsync(&ctl->beta, &bn, sizeof(double), cudaMemcpyHostToDevice, s->stream));
@@ -429,7 +617,7 @@ sim_status k_fgmres(sim_t *s, const double *b, double *x, sim_linear_info *info)
         else xupdate_kernel<double><<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(x, (const double *)s->Z, n, ctl);
         SIM_LAUNCHED(s);
         if (k_spmv(s, x, s->w) != SIM_OK) return s->err;
-        resid_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(b, s->w, s->r, n, s->red, s->ticket, ctl);
+        resid_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(b, s->w, s->r, n, s->red, s->ticket, &ctl->beta);
         SIM_LAUNCHED(s);
         SIM_CK(s, cudaMemcpyAsync(s->ctl_host, ctl, offsetof(KrylovCtl, h), cudaMemcpyDeviceToHost, s->stream));
         SIM_CK(s, cudaStreamSynchronize(s->stream));
@@ -455,5 +643,150 @@ sim_status k_fgmres(sim_t *s, const double *b, double *x, sim_linear_info *info)
     s->linear_total += li.iterations;
     if (info) *info = li;
     if (!(li.r_norm == li.r_norm)) return sim_fail(s, SIM_ENAN, "non-finite linear residual");
+    return SIM_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// BiCGSTAB host driver
+// ---------------------------------------------------------------------------
+static constexpr int kBicgChunk = 4;   // iterations enqueued between host checks
+
+// vectors: rh, p, v, s, t in V; p^, s^ in Z (apply precision)
+static sim_status enqueue_bicg_chunk(sim_t *s, double *x) {
+    const long n = (long)s->N * s->b;
+    const bool zf = sim_mixed(s);
+    const size_t zes = zf ? sizeof(float) : sizeof(double);
+    BicgCtl *ctl = s->bctl;
+    const int *done = &ctl->done;
+    double *rh = s->V, *p = s->V + n, *v = s->V + 2 * n, *sv = s->V + 3 * n, *t = s->V + 4 * n;
+    void *ph = s->Z, *sh = (char *)s->Z + (size_t)n * zes;
+    bicg_chunk_init_kernel<<<1, 1, 0, s->stream>>>(ctl);
+    SIM_LAUNCHED(s);
+    for (int j = 0; j < kBicgChunk; j++) {
+        bicg_p_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(s->r, v, p, n, ctl);
+        SIM_LAUNCHED(s);
+        if (cpr_apply(s, p, ph, done) != SIM_OK) return s->err;
+        if (spmv_done(s, ph, zf, v, done) != SIM_OK) return s->err;
+        bicg_alpha_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(rh, v, n, s->red, s->ticket, ctl);
+        SIM_LAUNCHED(s);
+        bicg_s_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(s->r, v, sv, n, s->red, s->ticket, ctl, j);
+        SIM_LAUNCHED(s);
+        if (zf) bicg_xhalf_kernel<float><<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(x, (const float *)ph, n, ctl, j);
+        else bicg_xhalf_kernel<double><<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(x, (const double *)ph, n, ctl, j);
+        SIM_LAUNCHED(s);
+        if (cpr_apply(s, sv, sh, done) != SIM_OK) return s->err;
+        if (spmv_done(s, sh, zf, t, done) != SIM_OK) return s->err;
+        bicg_omega_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(t, sv, n, s->red, s->ticket, ctl);
+        SIM_LAUNCHED(s);
+        if (zf)
+            bicg_xr_kernel<float><<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(x, (const float *)ph, (const float *)sh, sv, t,
+                                                                                s->r, rh, n, s->red, s->ticket, ctl);
+        else
+            bicg_xr_kernel<double><<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(x, (const double *)ph, (const double *)sh,
+                                                                                 sv, t, s->r, rh, n, s->red, s->ticket, ctl);
+        SIM_LAUNCHED(s);
+    }
+    return SIM_OK;
+}
+
+static sim_status launch_bicg_chunk(sim_t *s, double *x) {
+    if (!s->opt.graphs) return enqueue_bicg_chunk(s, x);
+    // x is baked into the graph: recapture when it changes
+    if (!s->bicg_exec || s->bicg_gen != s->setup_gen || s->bicg_x != x) {
+        cudaGraph_t g = nullptr;
+        SIM_CK(s, cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+        const int64_t l0 = s->launches;
+        const sim_status st = enqueue_bicg_chunk(s, x);
+        const cudaError_t ec = cudaStreamEndCapture(s->stream, &g);
+        if (st != SIM_OK) { if (g) cudaGraphDestroy(g); return s->err; }
+        if (!sim_cuda_ok(s, ec, "cudaStreamEndCapture")) return s->err;
+        s->bicg_nodes = s->launches - l0;
+        if (s->bicg_exec) {
+            cudaGraphExecUpdateResultInfo ri;
+            if (cudaGraphExecUpdate(s->bicg_exec, g, &ri) != cudaSuccess) {
+                cudaGetLastError();
+                cudaGraphExecDestroy(s->bicg_exec);
+                s->bicg_exec = nullptr;
+            }
+        }
+        if (!s->bicg_exec) {
+            const cudaError_t ei = cudaGraphInstantiate(&s->bicg_exec, g, 0);
+            if (ei != cudaSuccess) { cudaGraphDestroy(g); s->bicg_exec = nullptr; sim_cuda_ok(s, ei, "cudaGraphInstantiate"); return s->err; }
+        }
+        cudaGraphDestroy(g);
+        s->bicg_gen = s->setup_gen;
+        s->bicg_x = x;
+    } else {
+        s->launches += s->bicg_nodes;
+    }
+    SIM_CK(s, cudaGraphLaunch(s->bicg_exec, s->stream));
+    return SIM_OK;
+}
+
+// true residual r = b - J x into s->r, its norm into ctl->rnorm; read back
+static sim_status bicg_true_residual(sim_t *s, const double *b, const double *x) {
+    const long n = (long)s->N * s->b;
+    if (k_spmv(s, x, s->w) != SIM_OK) return s->err;
+    resid_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(b, s->w, s->r, n, s->red, s->ticket, &s->bctl->rnorm);
+    SIM_LAUNCHED(s);
+    SIM_CK(s, cudaMemcpyAsync(s->bctl_host, s->bctl, sizeof(BicgCtl), cudaMemcpyDeviceToHost, s->stream));
+    SIM_CK(s, cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}
+
+// Right-preconditioned BiCGSTAB from x = 0.  When the recursive residual
+// meets the tolerance the true residual decides; if it does not, or on a
+// breakdown, the iteration restarts from the current x with rh = r.
+sim_status k_bicgstab(sim_t *s, const double *b, double *x, sim_linear_info *info) {
+    const long n = (long)s->N * s->b;
+    sim_linear_info li = {0, 0, 0, 0.0, 0.0};
+    if (!s->precond_ready) { if (cpr_setup(s) != SIM_OK) return s->err; }
+    double bn;
+    if (k_norm2(s, b, n, &bn) != SIM_OK) return s->err;
+    li.b_norm = bn;
+    SIM_CK(s, cudaMemsetAsync(x, 0, sizeof(double) * n, s->stream));
+    SIM_CK(s, cudaMemcpyAsync(s->r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->stream));
+    if (bn == 0.0) { li.converged = 1; if (info) *info = li; return SIM_OK; }
+    if (!(bn == bn)) { if (info) *info = li; return sim_fail(s, SIM_ENAN, "non-finite right-hand side"); }
+    const double tol = s->theta * bn;
+    s->learned_active = 0;   // the learned stage is used with FGMRES only (a nonlinear stage)
+    li.r_norm = bn;
+    BicgCtl *ctl = s->bctl;
+    bicg_init_kernel<<<1, 1, 0, s->stream>>>(ctl, tol, s->opt.lin_max_iter);
+    SIM_LAUNCHED(s);
+    bicg_restart_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(s->r, s->V, n, s->red, s->ticket, ctl);
+    SIM_LAUNCHED(s);
+    for (;;) {
+        if (launch_bicg_chunk(s, x) != SIM_OK) return s->err;
+        SIM_CK(s, cudaMemcpyAsync(s->bctl_host, ctl, sizeof(BicgCtl), cudaMemcpyDeviceToHost, s->stream));
+        SIM_CK(s, cudaStreamSynchronize(s->stream));
+        if (!s->bctl_host->done) continue;     // the device caps the iterations (flag 3)
+        if (bicg_true_residual(s, b, x) != SIM_OK) return s->err;
+        const BicgCtl &h = *s->bctl_host;
+        li.iterations = h.it;
+        li.r_norm = h.rnorm;
+        if (h.rnorm <= tol) { li.converged = 1; break; }
+        if (!(h.rnorm == h.rnorm) || h.it >= h.max_it) break;
+        bicg_restart_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(s->r, s->V, n, s->red, s->ticket, ctl);
+        SIM_LAUNCHED(s);
+        li.restarts++;
+    }
+    s->linear_total += li.iterations;
+    if (info) *info = li;
+    if (!(li.r_norm == li.r_norm)) return sim_fail(s, SIM_ENAN, "non-finite linear residual");
+    return SIM_OK;
+}
+
+sim_status k_linear_solve(sim_t *s, const double *b, double *x, sim_linear_info *info) {
+    return s->opt.krylov == SIM_KRYLOV_BICGSTAB ? k_bicgstab(s, b, x, info) : k_fgmres(s, b, x, info);
+}
+
+sim_status k_diff_norm2(sim_t *s, const double *a, const double *b, long n, double *out) {
+    diff_norm_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(a, b, n, s->red, s->ticket, s->scal);
+    SIM_LAUNCHED(s);
+    SIM_CK(s, cudaMemcpyAsync(s->h_pinned, s->scal, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    SIM_CK(s, cudaStreamSynchronize(s->stream));
+    *out = s->h_pinned[0];
     return SIM_OK;
 }

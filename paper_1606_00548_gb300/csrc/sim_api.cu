@@ -92,9 +92,11 @@ void sim_destroy(sim_t *s) {
     cpr_free(s);
     if (s->stream) cudaStreamSynchronize(s->stream);
     if (s->cycle_exec) cudaGraphExecDestroy(s->cycle_exec);
+    if (s->bicg_exec) cudaGraphExecDestroy(s->bicg_exec);
     for (void *p : s->allocs) cudaFree(p);
     if (s->h_pinned) cudaFreeHost(s->h_pinned);
     if (s->ctl_host) cudaFreeHost(s->ctl_host);
+    if (s->bctl_host) cudaFreeHost(s->bctl_host);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     delete s;
 }
@@ -115,6 +117,14 @@ sim_status sim_create(const sim_grid *g, const sim_rock *r, const sim_fluid *f, 
     if (o->amg_coarse_max < 1 || o->amg_coarse_max > 1024 || o->amg_rounds < 1 || o->amg_max_levels < 1 ||
         o->amg_cycles < 1 || o->amg_cycles > 16)
         return sim_fail(nullptr, SIM_EINVAL, "bad AMG options");
+    if (o->decouple < 0 || o->decouple > 1 || (o->cpr_stages != 2 && o->cpr_stages != 3))
+        return sim_fail(nullptr, SIM_EINVAL, "bad CPR decoupling / stage options");
+    if (o->krylov < 0 || o->krylov > 1 || o->lin_max_iter < 1 || o->forcing < 0 || o->forcing > 3 ||
+        !(o->lin_tol > 0 && o->lin_tol < 1) || !(o->theta_max >= o->lin_tol && o->theta_max < 1) ||
+        !(o->ew_gamma > 0 && o->ew_gamma <= 1) || !(o->ew_beta > 0))
+        return sim_fail(nullptr, SIM_EINVAL, "bad Krylov / forcing-term options");
+    if (o->krylov == SIM_KRYLOV_BICGSTAB && o->gmres_m < 2)
+        return sim_fail(nullptr, SIM_EINVAL, "BiCGSTAB needs gmres_m >= 2 (its two preconditioned vectors)");
     if (f->model == 3) {
         if (f->npvt < 2 || f->npvt > SIM_MAX_PVT) return sim_fail(nullptr, SIM_EINVAL, "npvt must be in 2..64");
         if (!f->pvt_p || !f->pvt_bo || !f->pvt_rs || !f->pvt_muo || !f->pvt_bg || !f->pvt_mug)
@@ -128,9 +138,10 @@ sim_status sim_create(const sim_grid *g, const sim_rock *r, const sim_fluid *f, 
               std::isfinite(r->poro[i])))
             return sim_fail(nullptr, SIM_EINVAL, "permeability and porosity must be positive and finite");
     // perforations: distinct cells
-    std::vector<int> pc, pt;
-    std::vector<double> pb, pz, prw, pskin;
+    std::vector<int> pc, pt, pw, woff(1, 0), wctrl;
+    std::vector<double> pz, prw, pskin, wrate, wbhp;
     std::set<int> seen;
+    int nrate = 0;
     for (int k = 0; k < nwells; k++) {
         const sim_well &W = w[k];
         if (W.i < 0 || W.i >= g->nx || W.j < 0 || W.j >= g->ny || W.k_top < 0 || W.k_bot >= g->nz || W.k_top > W.k_bot)
@@ -138,13 +149,20 @@ sim_status sim_create(const sim_grid *g, const sim_rock *r, const sim_fluid *f, 
         if (W.type != SIM_WELL_PRODUCER && W.type != SIM_WELL_WATER_INJECTOR)
             return sim_fail(nullptr, SIM_EINVAL, "unknown well type");
         if (!(W.r_w > 0)) return sim_fail(nullptr, SIM_EINVAL, "well radius must be positive");
+        if (W.control < SIM_WELL_BHP || W.control > SIM_WELL_OIL_RATE ||
+            (W.type == SIM_WELL_WATER_INJECTOR && W.control == SIM_WELL_OIL_RATE) || !std::isfinite(W.rate) ||
+            !std::isfinite(W.bhp))
+            return sim_fail(nullptr, SIM_EINVAL, "well " + std::to_string(k) + ": bad control");
+        if (W.control != SIM_WELL_BHP) nrate++;
         const double zh = g->top_depth + (W.k_top + 0.5) * g->dz;
         for (int kk = W.k_top; kk <= W.k_bot; kk++) {
             const int c = W.i + g->nx * (W.j + g->ny * kk);
             if (!seen.insert(c).second) return sim_fail(nullptr, SIM_EINVAL, "two perforations share a cell");
-            pc.push_back(c); pt.push_back(W.type); pb.push_back(W.bhp); pz.push_back(zh);
+            pc.push_back(c); pt.push_back(W.type); pw.push_back(k); pz.push_back(zh);
             prw.push_back(W.r_w); pskin.push_back(W.skin);
         }
+        woff.push_back((int)pc.size());
+        wctrl.push_back(W.control); wrate.push_back(W.rate); wbhp.push_back(W.bhp);
     }
 
     sim_t *s = new sim_t();
@@ -190,7 +208,24 @@ sim_status sim_create(const sim_grid *g, const sim_rock *r, const sim_fluid *f, 
     s->perf_type = (int *)A(sizeof(int) * (pc.size() + 1));
     s->perf_wi = (double *)A(sizeof(double) * (pc.size() + 1));
     s->perf_zh = (double *)A(sizeof(double) * (pc.size() + 1));
-    s->perf_bhp = (double *)A(sizeof(double) * (pc.size() + 1));
+    s->nwells = nwells;
+    s->nrate = nrate;
+    s->h_wctrl = wctrl;
+    s->perf_well = (int *)A(sizeof(int) * (pc.size() + 1));
+    s->woff = (int *)A(sizeof(int) * (nwells + 1));
+    s->wctrl = (int *)A(sizeof(int) * (nwells + 1));
+    s->wrate = (double *)A(sizeof(double) * (nwells + 1));
+    s->wbhp_c = (double *)A(sizeof(double) * (nwells + 1));
+    s->wp = (double *)A(sizeof(double) * (nwells + 1));
+    s->wp_old = (double *)A(sizeof(double) * (nwells + 1));
+    s->aww = (double *)A(sizeof(double) * (nwells + 1));
+    s->rw = (double *)A(sizeof(double) * (nwells + 1));
+    s->qwell = (double *)A(sizeof(double) * 3 * (nwells + 1));
+    s->apw = (double *)A(sizeof(double) * 3 * (pc.size() + 1));
+    s->awp = (double *)A(sizeof(double) * 3 * (pc.size() + 1));
+    s->qperf = (double *)A(sizeof(double) * 4 * (pc.size() + 1));
+    s->wcnv = (double *)A(sizeof(double));
+    if (nrate > 0) s->cell_perf = (int *)A(sizeof(int) * N);
     s->x = (double *)A(sizeof(double) * n);
     s->x_old = (double *)A(sizeof(double) * n);
     s->ph = (int8_t *)A(N);
@@ -203,7 +238,7 @@ sim_status sim_create(const sim_grid *g, const sim_rock *r, const sim_fluid *f, 
     s->red = (double *)A(sizeof(double) * (SIM_MAX_M + 2) * SIM_RED_BLOCKS);
     s->scal = (double *)A(sizeof(double) * 64);
     s->ticket = (unsigned int *)A(sizeof(unsigned int) * 4);
-    s->V = (double *)A(sizeof(double) * (s->m + 1) * n);
+    s->V = (double *)A(sizeof(double) * (s->m + 1 > 5 ? s->m + 1 : 5) * n);   // BiCGSTAB keeps 5 vectors here
     s->Z = A(tsz * s->m * n);
     s->w = (double *)A(sizeof(double) * n);
     s->r = (double *)A(sizeof(double) * n);
@@ -211,6 +246,9 @@ sim_status sim_create(const sim_grid *g, const sim_rock *r, const sim_fluid *f, 
     s->bl = (double *)A(sizeof(double) * n);
     s->dx = (double *)A(sizeof(double) * n);
     s->ctl = (KrylovCtl *)A(sizeof(KrylovCtl));
+    s->bctl = (BicgCtl *)A(sizeof(BicgCtl));
+    s->rlin = (double *)A(sizeof(double) * n);
+    s->theta = o->lin_tol;
     s->qiw = (double *)A(sizeof(double) * n);
     s->ap = (double *)A(sizeof(double) * 7 * N);
     s->qiwT = mixed ? A(sizeof(float) * n) : (void *)s->qiw;
@@ -222,6 +260,12 @@ sim_status sim_create(const sim_grid *g, const sim_rock *r, const sim_fluid *f, 
     s->rpT = A(tsz * N);
     s->epacc = A(tsz * N);
     s->zr = A(tsz * n);
+    s->lsc = (double *)A(sizeof(double) * b * b * N);
+    s->lscT = mixed ? A(sizeof(float) * b * b * N) : (void *)s->lsc;
+    if (o->cpr_stages == 3) {
+        s->rhT = A(tsz * n);
+        s->x0 = A(tsz * n);
+    }
     s->partner = (int *)A(sizeof(int) * N);
     s->pick = (int *)A(sizeof(int) * (N + 1));   // also holds founder ids + total
     s->aggA = (int *)A(sizeof(int) * N);
@@ -241,7 +285,8 @@ sim_status sim_create(const sim_grid *g, const sim_rock *r, const sim_fluid *f, 
         return sim_fail(nullptr, SIM_ENOMEM, m);
     }
     if (cudaMallocHost(&s->h_pinned, sizeof(double) * 64) != cudaSuccess ||
-        cudaMallocHost(&s->ctl_host, sizeof(KrylovCtl)) != cudaSuccess) {
+        cudaMallocHost(&s->ctl_host, sizeof(KrylovCtl)) != cudaSuccess ||
+        cudaMallocHost(&s->bctl_host, sizeof(BicgCtl)) != cudaSuccess) {
         sim_destroy(s);
         return sim_fail(nullptr, SIM_ENOMEM, "pinned host allocation failed");
     }
@@ -256,7 +301,26 @@ sim_status sim_create(const sim_grid *g, const sim_rock *r, const sim_fluid *f, 
     cudaMemsetAsync(s->ticket, 0, sizeof(unsigned int) * 4, s->stream);
     cudaMemsetAsync(s->x, 0, sizeof(double) * n, s->stream);
     cudaMemsetAsync(s->ph, 1, N, s->stream);
-    if (k_geometry(s, r->kx, r->ky, r->kz, r->poro, pc.data(), pt.data(), pb.data(), pz.data(), prw.data(),
+    if (ok && nwells > 0) {
+        std::vector<int> cp;
+        if (nrate > 0) {
+            cp.assign(N, -1);
+            for (size_t q = 0; q < pc.size(); q++)
+                if (wctrl[pw[q]] != SIM_WELL_BHP) cp[pc[q]] = (int)q;
+        }
+        bool up = cudaMemcpy(s->woff, woff.data(), sizeof(int) * (nwells + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(s->wctrl, wctrl.data(), sizeof(int) * nwells, cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(s->wrate, wrate.data(), sizeof(double) * nwells, cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(s->wbhp_c, wbhp.data(), sizeof(double) * nwells, cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(s->wp, wbhp.data(), sizeof(double) * nwells, cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(s->wp_old, wbhp.data(), sizeof(double) * nwells, cudaMemcpyHostToDevice) == cudaSuccess &&
+                  (nrate == 0 || cudaMemcpy(s->cell_perf, cp.data(), sizeof(int) * N, cudaMemcpyHostToDevice) == cudaSuccess);
+        if (!up) {
+            sim_destroy(s);
+            return sim_fail(nullptr, SIM_ECUDA, "well upload failed");
+        }
+    }
+    if (k_geometry(s, r->kx, r->ky, r->kz, r->poro, pc.data(), pt.data(), pw.data(), pz.data(), prw.data(),
                    pskin.data()) != SIM_OK) {
         std::string m = s->msg;
         sim_status st = s->err;
@@ -274,6 +338,7 @@ static sim_status begin_step(sim_t *s) {
     const long n = (long)s->N * s->b;
     SIM_CK(s, cudaMemcpyAsync(s->x_old, s->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->stream));
     SIM_CK(s, cudaMemcpyAsync(s->ph_old, s->ph, s->N, cudaMemcpyDeviceToDevice, s->stream));
+    if (s->nwells) SIM_CK(s, cudaMemcpyAsync(s->wp_old, s->wp, sizeof(double) * s->nwells, cudaMemcpyDeviceToDevice, s->stream));
     return k_accumulation(s, s->x, s->ph, s->mold);
 }
 
@@ -342,12 +407,62 @@ sim_status sim_cnv(sim_t *s, double dt, double *cnv) {
     return k_cnv(s, dt, cnv);
 }
 
-// solve J dx = -R and update; *lin receives the linear info
-static sim_status solve_and_update(sim_t *s, sim_linear_info *lin, bool *finite_ok) {
+// forcing state of one Newton solve (Algorithm 1, Eq. 14)
+struct Forcing {
+    int l = 0;                      // Newton iteration within the solve
+    double bprev = 0.0, rprev = 0.0, theta = 0.0;
+};
+
+// theta_l from ||b^l||, the previous ||b^{l-1}||, ||r^{l-1}|| and theta_{l-1}.
+// Choice 2 takes the absolute value of its numerator; the first iteration
+// uses theta_max; the Eisenstat-Walker safeguards keep theta from falling
+// below theta_{l-1}^((1+sqrt 5)/2) (choices 1, 2) or gamma theta_{l-1}^beta
+// (choice 3) while that bound exceeds 0.1; lin_tol <= theta <= theta_max.
+static sim_status forcing_term(sim_t *s, const Forcing &f, double bnorm, double *theta) {
+    const sim_options &o = s->opt;
+    if (o.forcing == SIM_FORCING_FIXED) { *theta = o.lin_tol; return SIM_OK; }
+    if (f.l == 0) { *theta = o.theta_max; return SIM_OK; }
+    double th, guard;
+    if (o.forcing == SIM_FORCING_EW1) {
+        double d;
+        if (k_diff_norm2(s, s->bl, s->rlin, (long)s->N * s->b, &d) != SIM_OK) return s->err;
+        th = d / f.bprev;
+        guard = pow(f.theta, 0.5 * (1.0 + sqrt(5.0)));
+    } else if (o.forcing == SIM_FORCING_EW2) {
+        th = fabs(bnorm - f.rprev) / f.bprev;
+        guard = pow(f.theta, 0.5 * (1.0 + sqrt(5.0)));
+    } else {
+        th = o.ew_gamma * pow(bnorm / f.bprev, o.ew_beta);
+        guard = o.ew_gamma * pow(f.theta, o.ew_beta);
+    }
+    if (guard > 0.1 && guard > th) th = guard;
+    if (th > o.theta_max) th = o.theta_max;
+    if (th < o.lin_tol) th = o.lin_tol;
+    *theta = th;
+    return SIM_OK;
+}
+
+// solve J dx = -R and update; *lin receives the linear info.  With a forcing
+// state the tolerance is its theta_l, else lin_tol.
+static sim_status solve_and_update(sim_t *s, sim_linear_info *lin, bool *finite_ok, Forcing *f = nullptr) {
     const long n = (long)s->N * s->b;
     negate_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(s->R, s->bl, n);
     SIM_LAUNCHED(s);
-    if (k_fgmres(s, s->bl, s->dx, lin) != SIM_OK) {
+    if (k_well_rhs(s, s->bl) != SIM_OK) return s->err;
+    double bnorm = 0.0;
+    s->theta = s->opt.lin_tol;
+    if (f && s->opt.forcing != SIM_FORCING_FIXED) {
+        if (k_norm2(s, s->bl, n, &bnorm) != SIM_OK) return s->err;
+        if (forcing_term(s, *f, bnorm, &s->theta) != SIM_OK) return s->err;
+    }
+    const sim_status st = k_linear_solve(s, s->bl, s->dx, lin);
+    const double theta_used = s->theta;
+    s->theta = s->opt.lin_tol;
+    if (f && s->opt.forcing != SIM_FORCING_FIXED && st == SIM_OK) {
+        f->bprev = bnorm; f->rprev = lin->r_norm; f->theta = theta_used; f->l++;
+        SIM_CK(s, cudaMemcpyAsync(s->rlin, s->r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->stream));
+    }
+    if (st != SIM_OK) {
         if (s->err == SIM_ENAN) { sim_clear_error(s); *finite_ok = false; return SIM_OK; }
         return s->err;
     }
@@ -355,6 +470,7 @@ static sim_status solve_and_update(sim_t *s, sim_linear_info *lin, bool *finite_
     if (k_finite(s, s->dx, n, &ok) != SIM_OK) return s->err;
     *finite_ok = ok != 0;
     if (!ok) return SIM_OK;
+    if (k_well_update(s, s->dx) != SIM_OK) return s->err;
     if (k_newton_update(s, s->dx) != SIM_OK) return s->err;
     s->newton_total++;
     return SIM_OK;
@@ -366,10 +482,10 @@ sim_status sim_newton_step(sim_t *s, double dt, sim_newton_info *info) {
     sim_newton_info ni;
     memset(&ni, 0, sizeof(ni));
     if (k_assemble(s, dt) != SIM_OK) return s->err;
-    double cnv;
-    if (k_cnv(s, dt, &cnv) != SIM_OK) return s->err;
+    double cnv, wcnv;
+    if (k_cnv(s, dt, &cnv, &wcnv) != SIM_OK) return s->err;
     ni.cnv = cnv;
-    if (cnv <= s->opt.newton_tol) { ni.converged = 1; if (info) *info = ni; return SIM_OK; }
+    if (cnv <= s->opt.newton_tol && wcnv <= s->opt.newton_tol) { ni.converged = 1; if (info) *info = ni; return SIM_OK; }
     sim_linear_info li;
     bool fin = true;
     if (solve_and_update(s, &li, &fin) != SIM_OK) return s->err;
@@ -383,17 +499,18 @@ sim_status sim_newton_step(sim_t *s, double dt, sim_newton_info *info) {
 // Newton loop; returns 0 converged, 1 not converged, 2 non-finite
 static int newton_solve(sim_t *s, double dt, sim_newton_info *ni) {
     memset(ni, 0, sizeof(*ni));
+    Forcing f;
     for (int l = 0;; l++) {
         if (k_assemble(s, dt) != SIM_OK) return -1;
-        double cnv;
-        if (k_cnv(s, dt, &cnv) != SIM_OK) return -1;
+        double cnv, wcnv;
+        if (k_cnv(s, dt, &cnv, &wcnv) != SIM_OK) return -1;
         ni->cnv = cnv;
-        if (!(cnv == cnv)) return 2;
-        if (cnv <= s->opt.newton_tol) { ni->converged = 1; return 0; }
+        if (!(cnv == cnv) || !(wcnv == wcnv)) return 2;
+        if (cnv <= s->opt.newton_tol && wcnv <= s->opt.newton_tol) { ni->converged = 1; return 0; }
         if (l >= s->opt.newton_max) return 1;
         sim_linear_info li;
         bool fin = true;
-        if (solve_and_update(s, &li, &fin) != SIM_OK) return -1;
+        if (solve_and_update(s, &li, &fin, &f) != SIM_OK) return -1;
         ni->newton_iterations++;
         ni->linear_iterations += li.iterations;
         ni->linear_failures += !li.converged;
@@ -435,6 +552,8 @@ sim_status sim_step(sim_t *s, double dt, sim_step_info *info) {
         } else {
             SIM_CK(s, cudaMemcpyAsync(s->x, s->x_old, sizeof(double) * s->N * s->b, cudaMemcpyDeviceToDevice, s->stream));
             SIM_CK(s, cudaMemcpyAsync(s->ph, s->ph_old, s->N, cudaMemcpyDeviceToDevice, s->stream));
+            if (s->nwells)
+                SIM_CK(s, cudaMemcpyAsync(s->wp, s->wp_old, sizeof(double) * s->nwells, cudaMemcpyDeviceToDevice, s->stream));
             si.cuts++;
             if (si.cuts > s->opt.max_cuts) { st = SIM_ENOCONV_NEWTON; break; }
             h *= 0.5;
@@ -450,7 +569,7 @@ sim_status sim_linear_solve(sim_t *s, const double *b_dev, double *x_dev, sim_li
     CHECK_HANDLE(s);
     if (!b_dev || !x_dev || b_dev == x_dev) return sim_fail(s, SIM_EINVAL, "bad vector pointers");
     sim_linear_info li;
-    if (k_fgmres(s, b_dev, x_dev, &li) != SIM_OK) return s->err;
+    if (k_linear_solve(s, b_dev, x_dev, &li) != SIM_OK) return s->err;
     if (info) *info = li;
     return li.converged ? SIM_OK : SIM_ENOCONV_LINEAR;
 }
@@ -544,6 +663,72 @@ sim_status sim_well_rates(sim_t *s, double *q3) {
     for (int c = 0; c < 3; c++) q3[c] = s->h_pinned[c];
     return SIM_OK;
 }
+
+int32_t sim_perforations(sim_t *s) { return s ? s->nperf : 0; }
+
+sim_status sim_get_well_bhp(sim_t *s, double *bhp) {
+    CHECK_HANDLE(s);
+    if (!bhp) return sim_fail(s, SIM_EINVAL, "NULL array");
+    if (s->nwells) SIM_CK(s, cudaMemcpyAsync(bhp, s->wp, sizeof(double) * s->nwells, cudaMemcpyDeviceToHost, s->stream));
+    SIM_CK(s, cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}
+
+sim_status sim_set_well_bhp(sim_t *s, const double *bhp) {
+    CHECK_HANDLE(s);
+    if (!bhp) return sim_fail(s, SIM_EINVAL, "NULL array");
+    if (s->nwells) SIM_CK(s, cudaMemcpyAsync(s->wp, bhp, sizeof(double) * s->nwells, cudaMemcpyHostToDevice, s->stream));
+    SIM_CK(s, cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}
+
+sim_status sim_well_component_rates(sim_t *s, double *q) {
+    CHECK_HANDLE(s);
+    if (!q) return sim_fail(s, SIM_EINVAL, "NULL array");
+    const int nw = s->nwells;
+    if (!nw) return SIM_OK;
+    std::vector<double> t(3 * (size_t)nw);
+    SIM_CK(s, cudaMemcpyAsync(t.data(), s->qwell, sizeof(double) * 3 * nw, cudaMemcpyDeviceToHost, s->stream));
+    SIM_CK(s, cudaStreamSynchronize(s->stream));
+    for (int w = 0; w < nw; w++)
+        for (int c = 0; c < 3; c++) q[w * 3 + c] = t[(size_t)c * nw + w];
+    return SIM_OK;
+}
+
+sim_status sim_get_well_system(sim_t *s, double *Rw, double *Apw, double *Awp, double *Aww) {
+    CHECK_HANDLE(s);
+    const int nw = s->nwells, np = s->nperf, b = s->b;
+    if (!nw) return SIM_OK;
+    std::vector<double> a(3 * (size_t)np), c(3 * (size_t)np);
+    if (Rw) SIM_CK(s, cudaMemcpyAsync(Rw, s->rw, sizeof(double) * nw, cudaMemcpyDeviceToHost, s->stream));
+    if (Aww) SIM_CK(s, cudaMemcpyAsync(Aww, s->aww, sizeof(double) * nw, cudaMemcpyDeviceToHost, s->stream));
+    SIM_CK(s, cudaMemcpyAsync(a.data(), s->apw, sizeof(double) * 3 * np, cudaMemcpyDeviceToHost, s->stream));
+    SIM_CK(s, cudaMemcpyAsync(c.data(), s->awp, sizeof(double) * 3 * np, cudaMemcpyDeviceToHost, s->stream));
+    SIM_CK(s, cudaStreamSynchronize(s->stream));
+    for (int q = 0; q < np; q++)
+        for (int k = 0; k < b; k++) {
+            if (Apw) Apw[q * b + k] = a[(size_t)k * np + q];
+            if (Awp) Awp[q * b + k] = c[(size_t)k * np + q];
+        }
+    return SIM_OK;
+}
+
+sim_status sim_set_well_system(sim_t *s, const double *Rw, const double *Apw, const double *Awp, const double *Aww) {
+    CHECK_HANDLE(s);
+    if (!Rw || !Apw || !Awp || !Aww) return sim_fail(s, SIM_EINVAL, "NULL array");
+    const int nw = s->nwells, np = s->nperf, b = s->b;
+    if (!nw) return SIM_OK;
+    std::vector<double> a(3 * (size_t)np, 0.0), c(3 * (size_t)np, 0.0);
+    for (int q = 0; q < np; q++)
+        for (int k = 0; k < b; k++) { a[(size_t)k * np + q] = Apw[q * b + k]; c[(size_t)k * np + q] = Awp[q * b + k]; }
+    SIM_CK(s, cudaMemcpyAsync(s->rw, Rw, sizeof(double) * nw, cudaMemcpyHostToDevice, s->stream));
+    SIM_CK(s, cudaMemcpyAsync(s->aww, Aww, sizeof(double) * nw, cudaMemcpyHostToDevice, s->stream));
+    SIM_CK(s, cudaMemcpyAsync(s->apw, a.data(), sizeof(double) * 3 * np, cudaMemcpyHostToDevice, s->stream));
+    SIM_CK(s, cudaMemcpyAsync(s->awp, c.data(), sizeof(double) * 3 * np, cudaMemcpyHostToDevice, s->stream));
+    SIM_CK(s, cudaStreamSynchronize(s->stream));
+    s->precond_ready = false;
+    return SIM_OK;
+}
 sim_status sim_set_learned_stage(sim_t *s, sim_net_t *net, int32_t enable) {
     CHECK_HANDLE(s);
     if (enable && !net) return sim_fail(s, SIM_EINVAL, "learned stage enabled without a network");
@@ -574,6 +759,10 @@ sim_status sim_learned_pairs(sim_t *s, int32_t k, float *x_dev, float *y_dev) {
         s->lrms = (double *)sim_alloc(s, sizeof(double) * 2);
         if (!s->lfeat || !s->lrms) return s->err;
         if (cpr_learned_features(s) != SIM_OK) return s->err;
+    }
+    if (!s->lres) {
+        s->lres = sim_alloc(s, (sim_mixed(s) ? sizeof(float) : sizeof(double)) * (size_t)s->N);
+        if (!s->lres) return s->err;
     }
     if (cpr_learned_pairs(s, k, x_dev, y_dev) != SIM_OK) return s->err;
     SIM_CK(s, cudaStreamSynchronize(s->stream));

@@ -47,6 +47,14 @@ struct KrylovCtl {
     unsigned int pad2;
 };
 
+// BiCGSTAB scalars (device); flag: 1 recursive residual met the tolerance,
+// 2 breakdown, 3 iteration limit (each also sets done)
+struct BicgCtl {
+    int done, flag, it, half_j;
+    int fresh, max_it;
+    double tol, rho, rho_old, alpha, omega, rnorm;
+};
+
 struct AmgLevel {
     int n = 0, width = 0;        // level 0: width 7, structured
     int *col = nullptr;          // ELL columns [width][n] (levels >= 1), -1 padding
@@ -57,7 +65,7 @@ struct AmgLevel {
     int *agg = nullptr;          // fine -> next level
     int *moff = nullptr, *mem = nullptr;   // members of each next-level aggregate, ascending (CSR)
     void *f = nullptr, *e = nullptr, *e2 = nullptr;   // V-cycle vectors (apply precision)
-    void *coarse_inv = nullptr;  // coarsest: dense inverse, row-major n*n (apply precision)
+    void *coarse_inv = nullptr;  // coarsest: dense inverse, row-major n*n (FP64 in both forms)
 };
 
 struct sim {
@@ -78,7 +86,20 @@ struct sim {
     double *poro = nullptr;      // [N] porosity at p_ref
     int nperf = 0;
     int *perf_cell = nullptr, *perf_type = nullptr;
-    double *perf_wi = nullptr, *perf_zh = nullptr, *perf_bhp = nullptr;
+    double *perf_wi = nullptr, *perf_zh = nullptr;
+    // wells (Eq. 16): perforations are grouped by well, woff[w]..woff[w+1]
+    int nwells = 0, nrate = 0;
+    int *perf_well = nullptr, *woff = nullptr, *wctrl = nullptr;
+    double *wrate = nullptr;                 // [nwells] target of rate controls
+    double *wbhp_c = nullptr;                // [nwells] BHP of BHP controls
+    double *wp = nullptr, *wp_old = nullptr; // [nwells] bottom-hole pressures (unknowns under rate control)
+    double *apw = nullptr, *awp = nullptr;   // [3][nperf] border blocks dR_cell/dp_h, dR_w/dx_cell
+    double *aww = nullptr, *rw = nullptr;    // [nwells] dR_w/dp_h, well equation residual
+    double *qwell = nullptr;                 // [3][nwells] component rates per well
+    double *qperf = nullptr;                 // [4][nperf] component rates and the controlled rate per perforation
+    double *wcnv = nullptr;                  // device scalar: largest |R_w| / max(|target|, 1)
+    int *cell_perf = nullptr;                // [N] perforation of a rate-controlled well, or -1 (rate wells only)
+    std::vector<int> h_wctrl;
 
     // state
     double *x = nullptr, *x_old = nullptr;   // [b][N]
@@ -107,6 +128,14 @@ struct sim {
     int cycle_learned = -1;                  // learned-stage state the graph was captured with
     int tune_spmv = SIM_THREADS, tune_amg = 128;   // block sizes picked by sim_autotune
     int last_cycle_k = 0;                    // inner iterations of the last restart cycle
+    // BiCGSTAB: control block and the graph of one chunk of iterations
+    BicgCtl *bctl = nullptr, *bctl_host = nullptr;
+    cudaGraphExec_t bicg_exec = nullptr;
+    int64_t bicg_gen = -1, bicg_nodes = 0;
+    const double *bicg_x = nullptr;          // solution vector the chunk graph was captured with
+    // inexact Newton: forcing term of the next solve, last linear residual b - J dx
+    double theta = 0.0;
+    double *rlin = nullptr;
 
     // CPR
     bool precond_ready = false;
@@ -130,6 +159,9 @@ struct sim {
     void *lep = nullptr;         // [N] pressure correction after the learned stage
     double *lrms = nullptr;      // device scalar
     void *zr = nullptr;          // [b][N]
+    double *lsc = nullptr;       // [b][b][N] per-cell left scaling L (quasi-IMPES or ABF)
+    void *lscT = nullptr;        // [b][b][N] apply precision (aliases lsc in FP64 mode)
+    void *rhT = nullptr, *x0 = nullptr;   // [b][N] CPR-FPF: L r - Ahat x0 and the first stage-F result
     std::vector<AmgLevel> lev;
     // AMG setup scratch
     int *partner = nullptr, *pick = nullptr, *host = nullptr, *flag = nullptr, *cnt = nullptr;
@@ -151,11 +183,14 @@ bool sim_mixed(const sim_t *s);
 
 // ---- assemble.cu ----------------------------------------------------------
 sim_status k_geometry(sim_t *s, const double *kx, const double *ky, const double *kz, const double *poro,
-                      const int *wcell_host, const int *wtype_host, const double *wbhp_host,
+                      const int *wcell_host, const int *wtype_host, const int *pwell_host,
                       const double *wzh_host, const double *wrw_host, const double *wskin_host);
+sim_status k_well_rhs(sim_t *s, double *b);                          // b += A_pw A_ww^-1 R_w
+sim_status k_well_update(sim_t *s, const double *dx);                // p_h += dp_h (rate wells)
+template <typename X> sim_status k_well_op(sim_t *s, const X *x, double *y, const int *done);   // y -= A_pw A_ww^-1 A_wp x
 sim_status k_accumulation(sim_t *s, const double *x, const int8_t *ph, double *acc);   // acc [b][N]
 sim_status k_assemble(sim_t *s, double dt);
-sim_status k_cnv(sim_t *s, double dt, double *cnv_host);
+sim_status k_cnv(sim_t *s, double dt, double *cnv_host, double *well_cnv_host = nullptr);
 sim_status k_component_mass(sim_t *s, double *m3_host);
 sim_status k_newton_update(sim_t *s, const double *dx);
 sim_status k_finite(sim_t *s, const double *v, long n, int *ok_host);
@@ -164,6 +199,9 @@ sim_status k_finite(sim_t *s, const double *v, long n, int *ok_host);
 sim_status k_spmv(sim_t *s, const double *x, double *y);                 // y = J x
 sim_status k_spmv_f(sim_t *s, const float *x, double *y);
 sim_status k_fgmres(sim_t *s, const double *b, double *x, sim_linear_info *info);
+sim_status k_bicgstab(sim_t *s, const double *b, double *x, sim_linear_info *info);
+sim_status k_linear_solve(sim_t *s, const double *b, double *x, sim_linear_info *info);
+sim_status k_diff_norm2(sim_t *s, const double *a, const double *b, long n, double *out);
 sim_status k_norm2(sim_t *s, const double *v, long n, double *out_host);
 sim_status k_spmv_block(sim_t *s, const double *x, double *y, int block);
 

@@ -3,9 +3,11 @@ arithmetic step runs in the CUDA library; this module sequences the calls).
 
 Training data are the simulator's own pressure systems: after each Newton
 iteration's CPR-FGMRES solve, the first Krylov vectors of its last restart
-cycle give pairs (decoupled pressure residual -> one AMG V-cycle correction),
-both normalised by the residual's RMS, plus standardised log-transmissibility
-features (include/sim.h, sim_learned_pairs).  The network is trained on the
+cycle give pairs (pressure residual left by the stage-P V-cycle -> the error
+it corresponds to, A_p^-1 r', from eight V-cycles of iterative refinement),
+each normalised by its RMS, plus standardised log-transmissibility features
+(include/sim.h, sim_learned_pairs).  The stage thus learns what the V-cycle
+misses, and is applied to exactly that residual inside the preconditioner.  The network is trained on the
 GPU by the library's own forward / backward kernels and Adam, then used as an
 extra CPR stage on a larger, more heterogeneous grid, where the solve's time
 to the FP64 tolerance is compared with plain FP64 CPR and FP32-preconditioned

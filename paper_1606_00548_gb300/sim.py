@@ -60,7 +60,8 @@ class sim_fluid(C.Structure):
 
 class sim_well(C.Structure):
     _fields_ = [("i", C.c_int32), ("j", C.c_int32), ("k_top", C.c_int32), ("k_bot", C.c_int32), ("type", C.c_int32),
-                ("bhp", C.c_double), ("r_w", C.c_double), ("skin", C.c_double)]
+                ("bhp", C.c_double), ("r_w", C.c_double), ("skin", C.c_double), ("control", C.c_int32),
+                ("rate", C.c_double)]
 
 
 class sim_options(C.Structure):
@@ -69,7 +70,10 @@ class sim_options(C.Structure):
                 ("stage2", C.c_int32), ("amg_theta", C.c_double), ("amg_rounds", C.c_int32),
                 ("amg_coarse_max", C.c_int32), ("amg_max_levels", C.c_int32), ("chop_ds", C.c_double),
                 ("chop_dp", C.c_double), ("max_cuts", C.c_int32), ("precision", C.c_int32),
-                ("amg_cycles", C.c_int32), ("graphs", C.c_int32)]
+                ("amg_cycles", C.c_int32), ("graphs", C.c_int32), ("decouple", C.c_int32),
+                ("cpr_stages", C.c_int32), ("krylov", C.c_int32), ("lin_max_iter", C.c_int32),
+                ("forcing", C.c_int32), ("ew_gamma", C.c_double), ("ew_beta", C.c_double),
+                ("theta_max", C.c_double), ("fused_coarse", C.c_int32)]
 
 
 class sim_linear_info(C.Structure):
@@ -121,6 +125,12 @@ _SIGS = {
     "sim_component_mass": ([_vp, _dp], C.c_int),
     "sim_cumulative_well_mass": ([_vp, _dp], C.c_int),
     "sim_well_rates": ([_vp, _dp], C.c_int),
+    "sim_perforations": ([_vp], C.c_int32),
+    "sim_get_well_bhp": ([_vp, _dp], C.c_int),
+    "sim_set_well_bhp": ([_vp, _dp], C.c_int),
+    "sim_well_component_rates": ([_vp, _dp], C.c_int),
+    "sim_get_well_system": ([_vp, _dp, _dp, _dp, _dp], C.c_int),
+    "sim_set_well_system": ([_vp, _dp, _dp, _dp, _dp], C.c_int),
     "sim_get_stats": ([_vp, C.POINTER(sim_stats)], C.c_int),
     "sim_block_size": ([_vp], C.c_int32),
     "sim_cnv_noalloc": ([C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double, C.c_int32,
@@ -257,13 +267,15 @@ class Net:
 
 def options_from(solver: dict, precision: int = 0) -> sim_options:
     o = sim_options()
-    for name in ("newton_tol", "lin_tol", "amg_theta", "chop_ds", "chop_dp"):
+    for name in ("newton_tol", "lin_tol", "amg_theta", "chop_ds", "chop_dp", "ew_gamma", "ew_beta", "theta_max"):
         setattr(o, name, float(solver[name]))
     for name in ("newton_max", "gmres_m", "gmres_max_restarts", "precond", "stage2", "amg_rounds",
-                 "amg_coarse_max", "amg_max_levels", "max_cuts", "amg_cycles"):
+                 "amg_coarse_max", "amg_max_levels", "max_cuts", "amg_cycles", "decouple", "cpr_stages",
+                 "krylov", "lin_max_iter", "forcing"):
         setattr(o, name, int(solver[name]))
     o.precision = int(precision)
     o.graphs = int(solver.get("graphs", 1))
+    o.fused_coarse = int(solver.get("fused_coarse", 1))
     return o
 
 
@@ -295,7 +307,8 @@ class Simulator:
         ws = case["wells"]
         W = (sim_well * max(1, len(ws)))()
         for k, w in enumerate(ws):
-            W[k] = sim_well(w["i"], w["j"], w["k0"], w["k1"], w["type"], w["bhp"], w["rw"], w["skin"])
+            W[k] = sim_well(w["i"], w["j"], w["k0"], w["k1"], w["type"], w["bhp"], w["rw"], w["skin"],
+                            int(w.get("ctrl", 0)), float(w.get("rate", 0.0)))
         sv = dict(case["solver"]); sv.update(solver_overrides)
         self.opts = options_from(sv, precision)
         h = _vp()
@@ -434,6 +447,45 @@ class Simulator:
 
     def well_rates(self):
         q = np.zeros(3); _check(self.h, self.L.sim_well_rates(self.h, q.ctypes.data_as(_dp))); return q
+
+    # well unknowns (host arrays) -------------------------------------------
+    @property
+    def nwells(self):
+        return len(self.case["wells"])
+
+    def perforations(self):
+        return int(self.L.sim_perforations(self.h))
+
+    def well_bhp(self):
+        p = np.zeros(max(self.nwells, 1))
+        _check(self.h, self.L.sim_get_well_bhp(self.h, p.ctypes.data_as(_dp)))
+        return p[:self.nwells]
+
+    def set_well_bhp(self, bhp):
+        p = np.ascontiguousarray(bhp, dtype=np.float64).reshape(-1)
+        if p.size == 0:
+            p = np.zeros(1)
+        _check(self.h, self.L.sim_set_well_bhp(self.h, p.ctypes.data_as(_dp)))
+
+    def well_component_rates(self):
+        q = np.zeros(3 * max(self.nwells, 1))
+        _check(self.h, self.L.sim_well_component_rates(self.h, q.ctypes.data_as(_dp)))
+        return q[:3 * self.nwells].reshape(self.nwells, 3)
+
+    def well_system(self):
+        nw, npf = max(self.nwells, 1), max(self.perforations(), 1)
+        Rw, Aww = np.zeros(nw), np.zeros(nw)
+        Apw, Awp = np.zeros(npf * self.b), np.zeros(npf * self.b)
+        _check(self.h, self.L.sim_get_well_system(self.h, Rw.ctypes.data_as(_dp), Apw.ctypes.data_as(_dp),
+                                                  Awp.ctypes.data_as(_dp), Aww.ctypes.data_as(_dp)))
+        npf = self.perforations()
+        return (Rw[:self.nwells], Apw[:npf * self.b].reshape(npf, self.b), Awp[:npf * self.b].reshape(npf, self.b),
+                Aww[:self.nwells])
+
+    def set_well_system(self, Rw, Apw, Awp, Aww):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64).reshape(-1) for a in (Rw, Apw, Awp, Aww)]
+        arrs = [a if a.size else np.zeros(1) for a in arrs]
+        _check(self.h, self.L.sim_set_well_system(self.h, *[a.ctypes.data_as(_dp) for a in arrs]))
 
     def set_learned_stage(self, net, enable=True):
         _check(self.h, self.L.sim_set_learned_stage(self.h, net.h if net is not None else None, 1 if enable else 0))

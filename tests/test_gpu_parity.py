@@ -101,10 +101,13 @@ def _loaded_pair(case, dt, seed, **kw):
 
 
 @pytest.mark.parametrize("name", ["ow_ragged", "bo_ragged"])
-def test_qi_and_amg_hierarchy_bitexact(torch_cuda, name):
+@pytest.mark.parametrize("decouple", [0, 1])
+def test_qi_and_amg_hierarchy_bitexact(torch_cuda, name, decouple):
+    """Decoupling weights (first row of L: quasi-IMPES or ABF), the pressure
+    block and the whole AMG hierarchy agree bit for bit."""
     case = CASES[name]()
     dt = 10.0 if case["model"] == 3 else 1.0
-    g, o = _loaded_pair(case, dt, 5, amg_coarse_max=32)
+    g, o = _loaded_pair(case, dt, 5, amg_coarse_max=32, decouple=decouple)
     N, b = g.N, g.b
     wg, apg = g.qi()
     wo, apo = o.qi()
@@ -129,12 +132,13 @@ def test_qi_and_amg_hierarchy_bitexact(torch_cuda, name):
 
 
 @pytest.mark.parametrize("name", ["ow_ragged", "bo_ragged"])
-@pytest.mark.parametrize("stage2,cycles", [(0, 1), (1, 1), (1, 3)])
-def test_cpr_apply_matches_oracle(torch_cuda, name, stage2, cycles):
+@pytest.mark.parametrize("stage2,cycles,decouple,stages", [(0, 1, 0, 2), (1, 1, 0, 2), (1, 3, 0, 2), (1, 1, 1, 2),
+                                                           (0, 1, 1, 2), (1, 1, 0, 3), (0, 1, 0, 3), (1, 2, 1, 3)])
+def test_cpr_apply_matches_oracle(torch_cuda, name, stage2, cycles, decouple, stages):
     torch = torch_cuda
     case = CASES[name]()
     dt = 10.0 if case["model"] == 3 else 1.0
-    g, o = _loaded_pair(case, dt, 6, stage2=stage2, amg_cycles=cycles)
+    g, o = _loaded_pair(case, dt, 6, stage2=stage2, amg_cycles=cycles, decouple=decouple, cpr_stages=stages)
     N, b = g.N, g.b
     r = np.random.default_rng(2).standard_normal(N * b)
     zo = o.precond_apply(r)
@@ -144,13 +148,14 @@ def test_cpr_apply_matches_oracle(torch_cuda, name, stage2, cycles):
     assert rel_err(to_il(zd.cpu().numpy(), N, b), zo) <= 1e-9
 
 
-@pytest.mark.parametrize("name,cycles", [("ow_ragged", 1), ("bo_ragged", 1), ("ow_1d", 1), ("bo_column", 1),
-                                         ("bo_ragged", 2)])
-def test_linear_solve_matches_oracle(torch_cuda, name, cycles):
+@pytest.mark.parametrize("name,cycles,decouple,stages", [
+    ("ow_ragged", 1, 0, 2), ("bo_ragged", 1, 0, 2), ("ow_1d", 1, 0, 2), ("bo_column", 1, 0, 2), ("bo_ragged", 2, 0, 2),
+    ("bo_ragged", 1, 1, 2), ("bo_ragged", 1, 0, 3), ("ow_ragged", 1, 1, 3), ("bo_column", 1, 1, 3)])
+def test_linear_solve_matches_oracle(torch_cuda, name, cycles, decouple, stages):
     torch = torch_cuda
     case = CASES[name]()
     dt = 10.0 if case["model"] == 3 else 1.0
-    g, o = _loaded_pair(case, dt, None, amg_cycles=cycles)
+    g, o = _loaded_pair(case, dt, None, amg_cycles=cycles, decouple=decouple, cpr_stages=stages)
     N, b = g.N, g.b
     rhs = np.random.default_rng(3).standard_normal(N * b)
     xo, io = o.linear_solve(rhs)
@@ -209,13 +214,17 @@ def test_time_steps_match_oracle(torch_cuda, which):
     for k, r in enumerate(rows):
         assert r["dp"] <= 1e-6 and r["dsw"] <= 1e-6 and r["dsg"] <= 1e-6 and r["ph"] == 0, (k, r)
         assert abs(r["ng"] - r["no"]) <= 1 and r["cg"] == r["co"], (k, r)
+        # linear iterations within 1 per linear solve of the step
+        assert abs(r["lg"] - r["lo"]) <= max(r["ng"], r["no"]), (k, r)
     mg, mo = g.component_mass(), o.component_mass()
     assert rel_err(mg, mo) <= 1e-9
     assert rel_err(g.cumulative_well_mass(), o.cumulative_well_mass()) <= 1e-6
 
 
-def test_mixed_precision_reaches_the_same_solution(torch_cuda):
+@pytest.mark.parametrize("decouple,stages", [(0, 2), (1, 3)])
+def test_mixed_precision_reaches_the_same_solution(torch_cuda, decouple, stages):
     case = synth.black_oil_case(nx=24, ny=24, nz=6, nsteps=3, dt=10.0, seed=47)
+    case["solver"].update(decouple=decouple, cpr_stages=stages)
     g, o, rows = _run_steps(case, 3, precision=1)
     for k, r in enumerate(rows):
         assert r["dp"] <= 1e-6 and r["dsw"] <= 1e-6 and r["dsg"] <= 1e-6, (k, r)
@@ -258,3 +267,78 @@ def test_graph_replay_matches_direct_launches(torch_cuda):
     pa = a.get_state(); pb = b.get_state()
     for u, v in zip(pa, pb):
         assert np.array_equal(u, v)
+
+
+@pytest.mark.parametrize("name,precond,decouple,stages", [("ow_ragged", 2, 0, 2), ("bo_ragged", 2, 0, 2),
+                                                          ("bo_ragged", 2, 1, 3), ("bo_column", 2, 0, 2),
+                                                          ("ow_1d", 1, 0, 2)])
+def test_bicgstab_matches_oracle(torch_cuda, name, precond, decouple, stages):
+    """BiCGSTAB (the paper's solver): iteration count within 2 of the oracle's
+    (the recurrence amplifies rounding differences), both at the tolerance."""
+    torch = torch_cuda
+    case = CASES[name]()
+    dt = 10.0 if case["model"] == 3 else 1.0
+    g, o = _loaded_pair(case, dt, None, krylov=1, lin_max_iter=400, precond=precond, decouple=decouple,
+                        cpr_stages=stages)
+    N, b = g.N, g.b
+    rhs = np.random.default_rng(8).standard_normal(N * b)
+    xo, io = o.linear_solve(rhs)
+    bd = torch.tensor(to_cm(rhs, N, b), device="cuda", dtype=torch.float64)
+    xd = torch.empty_like(bd)
+    st, ig = g.linear_solve(bd, xd)
+    assert ig.converged and io.converged
+    assert abs(ig.iterations - io.iterations) <= 2, (ig.iterations, io.iterations)
+    assert ig.r_norm <= 1e-8 * ig.b_norm
+    assert rel_err(to_il(xd.cpu().numpy(), N, b), xo) <= 1e-5
+
+
+def test_bicgstab_iteration_limit_and_graph_replay(torch_cuda):
+    """A solve stopped by the iteration limit returns the same iterate as the
+    oracle's after the same number of iterations (no convergence reached)."""
+    torch = torch_cuda
+    case = CASES["bo_ragged"]()
+    for graphs in (0, 1):
+        g, o = _loaded_pair(case, 10.0, None, krylov=1, lin_max_iter=3, lin_tol=1e-14, graphs=graphs)
+        N, b = g.N, g.b
+        rhs = np.random.default_rng(9).standard_normal(N * b)
+        xo, io = o.linear_solve(rhs)
+        bd = torch.tensor(to_cm(rhs, N, b), device="cuda", dtype=torch.float64)
+        xd = torch.empty_like(bd)
+        st, ig = g.linear_solve(bd, xd)
+        assert not ig.converged and ig.iterations == io.iterations == 3
+        assert rel_err(to_il(xd.cpu().numpy(), N, b), xo) <= 1e-8
+
+
+@pytest.mark.parametrize("forcing,krylov,precision", [(2, 1, 0), (1, 0, 0), (3, 1, 1)])
+def test_forcing_terms_match_oracle(torch_cuda, forcing, krylov, precision):
+    """Inexact Newton with the adaptive forcing terms of Eq. 14: the same
+    number of Newton iterations (within 1) and the same converged state."""
+    case = synth.black_oil_case(nx=24, ny=24, nz=6, nsteps=2, dt=1.0, seed=48)
+    case["solver"].update(forcing=forcing, krylov=krylov)
+    g, o, rows = _run_steps(case, 2, precision=precision)
+    for k, r in enumerate(rows):
+        assert r["dp"] <= 1e-6 and r["dsw"] <= 1e-6 and r["dsg"] <= 1e-6, (k, r)
+        assert abs(r["ng"] - r["no"]) <= 1, (k, r)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fused_coarse_cycle_matches_per_level_kernels(torch_cuda, precision):
+    """The one-launch cluster kernel for the coarse AMG levels computes what
+    the per-level kernels compute (same row operations, same order)."""
+    torch = torch_cuda
+    from paper_1606_00548_gb300.sim import Simulator
+    case = CASES["bo_ragged"]()
+    out = []
+    for fused in (0, 1):
+        g = Simulator(case, precision=precision, amg_coarse_max=32, fused_coarse=fused)
+        N, b = g.N, g.b
+        g.assemble(10.0)
+        g.precond_setup()
+        assert len(g.amg_levels()) >= 4
+        r = np.random.default_rng(11).standard_normal(N * b)
+        rd = torch.tensor(r, device="cuda", dtype=torch.float64)
+        zd = torch.empty_like(rd)
+        g.precond_apply(rd, zd)
+        out.append(zd.cpu().numpy())
+    tol = 1e-13 if precision == 0 else 1e-6
+    assert rel_err(out[1], out[0]) <= tol
