@@ -36,11 +36,11 @@ def workload(name: str, **solver):
     if name == "bo100":
         return synth.black_oil_100x100x20(**solver), "black-oil 100x100x20 (200k cells, 3x3 blocks), 10-day steps"
     if name == "bo100c":
-        return synth.black_oil_400cube(n=100, **solver), "black-oil 100^3 (1M cells), 10-day steps"
+        return synth.black_oil_400cube(n=100, **solver), "black-oil 100^3 (1M cells), 1-day steps"
     if name == "bo200":
-        return synth.black_oil_400cube(n=200, **solver), "black-oil 200^3 (8M cells), 10-day steps"
+        return synth.black_oil_400cube(n=200, **solver), "black-oil 200^3 (8M cells), 1-day steps"
     if name == "bo400":
-        return synth.black_oil_400cube(n=400, **solver), "black-oil 400^3 (64M cells), 10-day steps"
+        return synth.black_oil_400cube(n=400, **solver), "black-oil 400^3 (64M cells), 1-day steps"
     raise SystemExit(f"unknown workload {name}")
 
 

@@ -1435,8 +1435,8 @@ static int well_update(ora_sim *s, const double *dx) {
             for (int k = 0; k < b; k++) t -= s->awp[q * 3 + k] * dx[s->perf_cell[q] * b + k];
         }
         double d = t / s->aww[w];
-        if (!(d - d == 0.0)) return 0;
-        if (fabs(d) > s->in.chop_dp) d = d > 0 ? s->in.chop_dp : -s->in.chop_dp;
+        if (d != d) return 0;                                    /* NaN: the solve failed */
+        if (fabs(d) > s->in.chop_dp) d = d > 0 ? s->in.chop_dp : -s->in.chop_dp;   /* also +-inf */
         s->wp[w] += d;
     }
     return 1;

@@ -65,65 +65,93 @@ __device__ __forceinline__ int tap_nbr(const Dims &d, int x, int y, int z, int c
 //   MODE 1: outf[c] = acc[channel 0] + bias[0]        last layer forward
 //   MODE 2: out = bf16(acc * (mask > 0))              data gradient into a ReLU layer
 // wpk: packed weights [27][NT][8 n][8 k-pairs] (uint32 of two bf16)
+//
+// One block computes a brick of 16 x TBY x TBZ output cells: the brick and
+// its one-cell halo are staged in shared memory once (zero
+// outside the grid), so the 27 taps read shared memory instead of gathering
+// from global memory 27 times.  An MMA row block is one x-row of 16 cells;
+// cells are padded to 12 words in shared memory so that the 32 lanes of a
+// fragment load hit 32 distinct banks.
 // ---------------------------------------------------------------------------
+constexpr int TBX = 16, TBY = 8, TBZ = 4;
+constexpr int HX = TBX + 2, HY = TBY + 2, HZ = TBZ + 2, HCELLS = HX * HY * HZ;
+constexpr int CW = 12;                       // words per staged cell (8 used)
+constexpr int TWARPS = 16, TROWS = TBY * TBZ;   // 2 row blocks per warp
+
+template <int NT>
+constexpr int tiled_smem_bytes() { return (27 * NT * 64 + HCELLS * CW) * 4; }
+
 template <int NT, int MODE>
-__global__ void __launch_bounds__(128) conv_kernel(Dims d, const uint32_t *__restrict__ in, const uint32_t *__restrict__ wpk,
-                                                   const float *__restrict__ bias, const uint32_t *__restrict__ mask,
-                                                   uint32_t *__restrict__ out, float *__restrict__ outf, const int *done) {
+__global__ void __launch_bounds__(TWARPS * 32) conv_tiled_kernel(Dims d, const uint32_t *__restrict__ in,
+                                                               const uint32_t *__restrict__ wpk,
+                                                               const float *__restrict__ bias,
+                                                               const uint32_t *__restrict__ mask,
+                                                               uint32_t *__restrict__ out, float *__restrict__ outf,
+                                                               const int *done) {
     if (done != nullptr && *(volatile const int *)done) return;
-    __shared__ uint32_t ws[27 * NT * 64];
+    extern __shared__ uint32_t smem[];
+    uint32_t *ws = smem, *hs = smem + 27 * NT * 64;
+    const int bx0 = blockIdx.x * TBX, by0 = blockIdx.y * TBY, bz0 = blockIdx.z * TBZ;
     for (int k = threadIdx.x; k < 27 * NT * 64; k += blockDim.x) ws[k] = wpk[k];
+    for (int k = threadIdx.x; k < HCELLS * 8; k += blockDim.x) {
+        const int hc = k >> 3, w = k & 7;
+        const int hx = hc % HX, hy = (hc / HX) % HY, hz = hc / (HX * HY);
+        const int X = bx0 - 1 + hx, Y = by0 - 1 + hy, Z = bz0 - 1 + hz;
+        uint32_t v = 0u;
+        if (X >= 0 && X < d.nx && Y >= 0 && Y < d.ny && Z >= 0 && Z < d.nz)
+            v = in[((long)X + (long)d.nx * (Y + (long)d.ny * Z)) * 8 + w];
+        hs[hc * CW + w] = v;
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 2, t4 = lane & 3;
-    const int m0 = (blockIdx.x * 4 + warp) * 16;
-    if (m0 >= d.N) return;
-    const int r0 = m0 + g, r1 = m0 + g + 8;
-    const bool v0 = r0 < d.N, v1 = r1 < d.N;
-    int x0 = 0, y0 = 0, z0 = 0, x1 = 0, y1 = 0, z1 = 0;
-    if (v0) { x0 = r0 % d.nx; const int q = r0 / d.nx; y0 = q % d.ny; z0 = q / d.ny; }
-    if (v1) { x1 = r1 % d.nx; const int q = r1 / d.nx; y1 = q % d.ny; z1 = q / d.ny; }
-    float acc[NT][4];
+    for (int rb = warp; rb < TROWS; rb += TWARPS) {
+        const int my = rb % TBY, mz = rb / TBY;
+        const int Y = by0 + my, Z = bz0 + mz;
+        const int X0 = bx0 + g, X1 = bx0 + g + 8;
+        const bool rowok = Y < d.ny && Z < d.nz;
+        const bool v0 = rowok && X0 < d.nx, v1 = rowok && X1 < d.nx;
+        float acc[NT][4];
 #pragma unroll
-    for (int nt = 0; nt < NT; nt++)
+        for (int nt = 0; nt < NT; nt++)
 #pragma unroll
-        for (int q = 0; q < 4; q++) acc[nt][q] = 0.0f;
+            for (int q = 0; q < 4; q++) acc[nt][q] = 0.0f;
 #pragma unroll 3
-    for (int tap = 0; tap < 27; tap++) {
-        const int n0 = v0 ? tap_nbr(d, x0, y0, z0, r0, tap) : -1;
-        const int n1 = v1 ? tap_nbr(d, x1, y1, z1, r1, tap) : -1;
-        const uint32_t a0 = n0 >= 0 ? in[(long)n0 * 8 + t4] : 0u;
-        const uint32_t a1 = n1 >= 0 ? in[(long)n1 * 8 + t4] : 0u;
-        const uint32_t a2 = n0 >= 0 ? in[(long)n0 * 8 + 4 + t4] : 0u;
-        const uint32_t a3 = n1 >= 0 ? in[(long)n1 * 8 + 4 + t4] : 0u;
+        for (int tap = 0; tap < 27; tap++) {
+            const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;      // halo offsets 0..2
+            const int h0 = (g + dx) + HX * ((my + dy) + HY * (mz + dz));
+            const uint32_t *c0 = hs + h0 * CW, *c1 = hs + (h0 + 8) * CW;
+            const uint32_t a0 = c0[t4], a1 = c1[t4], a2 = c0[4 + t4], a3 = c1[4 + t4];
+#pragma unroll
+            for (int nt = 0; nt < NT; nt++) {
+                const uint32_t *wb = ws + ((tap * NT + nt) * 8 + g) * 8;
+                mma_bf16(acc[nt], a0, a1, a2, a3, wb[t4], wb[t4 + 4]);
+            }
+        }
+        const long r0 = (long)X0 + (long)d.nx * (Y + (long)d.ny * Z), r1 = r0 + 8;
 #pragma unroll
         for (int nt = 0; nt < NT; nt++) {
-            const uint32_t *wb = ws + ((tap * NT + nt) * 8 + g) * 8;
-            mma_bf16(acc[nt], a0, a1, a2, a3, wb[t4], wb[t4 + 4]);
-        }
-    }
-#pragma unroll
-    for (int nt = 0; nt < NT; nt++) {
-        const int col = nt * 8 + 2 * t4;
-        if (MODE == 0) {
-            const float b0 = bias[col], b1 = bias[col + 1];
-            if (v0) out[(long)r0 * 8 + nt * 4 + t4] = pack_bf16(fmaxf(acc[nt][0] + b0, 0.f), fmaxf(acc[nt][1] + b1, 0.f));
-            if (v1) out[(long)r1 * 8 + nt * 4 + t4] = pack_bf16(fmaxf(acc[nt][2] + b0, 0.f), fmaxf(acc[nt][3] + b1, 0.f));
-        } else if (MODE == 1) {
-            if (nt == 0 && t4 == 0) {
-                if (v0) outf[r0] = acc[0][0] + bias[0];
-                if (v1) outf[r1] = acc[0][2] + bias[0];
-            }
-        } else {
-            if (v0) {
-                const uint32_t mk = mask[(long)r0 * 8 + nt * 4 + t4];
-                out[(long)r0 * 8 + nt * 4 + t4] =
-                    pack_bf16(bf16_lo(mk) > 0.f ? acc[nt][0] : 0.f, bf16_hi(mk) > 0.f ? acc[nt][1] : 0.f);
-            }
-            if (v1) {
-                const uint32_t mk = mask[(long)r1 * 8 + nt * 4 + t4];
-                out[(long)r1 * 8 + nt * 4 + t4] =
-                    pack_bf16(bf16_lo(mk) > 0.f ? acc[nt][2] : 0.f, bf16_hi(mk) > 0.f ? acc[nt][3] : 0.f);
+            const int col = nt * 8 + 2 * t4;
+            if (MODE == 0) {
+                const float b0 = bias[col], b1 = bias[col + 1];
+                if (v0) out[r0 * 8 + nt * 4 + t4] = pack_bf16(fmaxf(acc[nt][0] + b0, 0.f), fmaxf(acc[nt][1] + b1, 0.f));
+                if (v1) out[r1 * 8 + nt * 4 + t4] = pack_bf16(fmaxf(acc[nt][2] + b0, 0.f), fmaxf(acc[nt][3] + b1, 0.f));
+            } else if (MODE == 1) {
+                if (nt == 0 && t4 == 0) {
+                    if (v0) outf[r0] = acc[0][0] + bias[0];
+                    if (v1) outf[r1] = acc[0][2] + bias[0];
+                }
+            } else {
+                if (v0) {
+                    const uint32_t mk = mask[r0 * 8 + nt * 4 + t4];
+                    out[r0 * 8 + nt * 4 + t4] =
+                        pack_bf16(bf16_lo(mk) > 0.f ? acc[nt][0] : 0.f, bf16_hi(mk) > 0.f ? acc[nt][1] : 0.f);
+                }
+                if (v1) {
+                    const uint32_t mk = mask[r1 * 8 + nt * 4 + t4];
+                    out[r1 * 8 + nt * 4 + t4] =
+                        pack_bf16(bf16_lo(mk) > 0.f ? acc[nt][2] : 0.f, bf16_hi(mk) > 0.f ? acc[nt][3] : 0.f);
+                }
             }
         }
     }
@@ -358,15 +386,34 @@ static sim_status pack_all(sim_net_t *n) {
     return SIM_OK;
 }
 
+static dim3 tiled_grid(const Dims &d) {
+    return dim3((d.nx + TBX - 1) / TBX, (d.ny + TBY - 1) / TBY, (d.nz + TBZ - 1) / TBZ);
+}
+
+// once per process: the tiled kernels need more than the default 48 KB of shared memory
+static bool tiled_attrs() {
+    static const bool ok = [] {
+        return cudaFuncSetAttribute(conv_tiled_kernel<2, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    tiled_smem_bytes<2>()) == cudaSuccess &&
+               cudaFuncSetAttribute(conv_tiled_kernel<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    tiled_smem_bytes<2>()) == cudaSuccess &&
+               cudaFuncSetAttribute(conv_tiled_kernel<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    tiled_smem_bytes<1>()) == cudaSuccess;
+    }();
+    return ok;
+}
+
 static sim_status net_forward(sim_net_t *n, const int *done = nullptr) {
-    const int blocks = (n->d.N + 63) / 64;
+    if (!tiled_attrs()) return SIM_ECUDA;
+    const dim3 grid = tiled_grid(n->d);
     for (int l = 0; l < NLAYER; l++) {
         const float *bias = n->param + n->off_b[l];
         if (l + 1 < NLAYER)
-            conv_kernel<2, 0><<<blocks, 128, 0, n->stream>>>(n->d, n->act[l], n->wf[l], bias, nullptr, n->act[l + 1], nullptr,
-                                                             done);
+            conv_tiled_kernel<2, 0><<<grid, TWARPS * 32, tiled_smem_bytes<2>(), n->stream>>>(
+                n->d, n->act[l], n->wf[l], bias, nullptr, n->act[l + 1], nullptr, done);
         else
-            conv_kernel<1, 1><<<blocks, 128, 0, n->stream>>>(n->d, n->act[l], n->wf[l], bias, nullptr, nullptr, n->out, done);
+            conv_tiled_kernel<1, 1><<<grid, TWARPS * 32, tiled_smem_bytes<1>(), n->stream>>>(
+                n->d, n->act[l], n->wf[l], bias, nullptr, nullptr, n->out, done);
         NET_LAUNCHED(n);
     }
     return SIM_OK;
@@ -380,7 +427,6 @@ static sim_status net_backward(sim_net_t *n, const float *target) {
     mse_fold_kernel<<<1, 32, 0, n->stream>>>(n->lblk, N, n->lpart, n->dloss);
     NET_LAUNCHED(n);
     uint32_t *gcur = n->g0, *gnext = n->g1;
-    const int blocks = (N + 63) / 64;
     for (int l = NLAYER - 1; l >= 0; l--) {
         const int NT = COUT[l] > 8 ? 2 : 1;
         dim3 grid(n->nchunk, 27);
@@ -396,8 +442,8 @@ static sim_status net_backward(sim_net_t *n, const float *target) {
         bgrad_fold_kernel<<<1, 32, 0, n->stream>>>(n->bblk, COUT[l], n->bpart, n->grad + n->off_b[l]);
         NET_LAUNCHED(n);
         if (l > 0) {   // data gradient through layer l into the ReLU output of layer l-1
-            conv_kernel<2, 2><<<blocks, 128, 0, n->stream>>>(n->d, gcur, n->wb[l], nullptr, n->act[l], gnext, nullptr,
-                                                             nullptr);
+            conv_tiled_kernel<2, 2><<<tiled_grid(n->d), TWARPS * 32, tiled_smem_bytes<2>(), n->stream>>>(
+                n->d, gcur, n->wb[l], nullptr, n->act[l], gnext, nullptr, nullptr);
             NET_LAUNCHED(n);
             uint32_t *t = gcur; gcur = gnext; gnext = t;
         }

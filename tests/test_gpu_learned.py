@@ -66,10 +66,12 @@ def torch_cuda():
     return torch
 
 
-def test_forward_and_gradients_match_reference(torch_cuda):
+@pytest.mark.parametrize("nx,ny,nz", [(13, 11, 5), (37, 9, 10)])
+def test_forward_and_gradients_match_reference(torch_cuda, nx, ny, nz):
+    """Sizes smaller than one brick of the tiled kernel and spanning several
+    bricks with ragged edges in every direction."""
     torch = torch_cuda
     from paper_1606_00548_gb300.sim import Net
-    nx, ny, nz = 13, 11, 5
     net = Net(nx, ny, nz, seed=3)
     rng = np.random.default_rng(4)
     p = net.get_params()
