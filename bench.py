@@ -57,13 +57,16 @@ def solver_overrides(args):
         o["decouple"] = 1
     if getattr(args, "cpr_stages", 2) == 3:
         o["cpr_stages"] = 3
+    if getattr(args, "orth", "cgs2") == "selective":
+        o["orth"] = 1
     return o
 
 
 def solver_desc(sv: dict) -> str:
     dec = "ABF" if sv.get("decouple", 0) == 1 else "QI"
     stages = "FPF" if sv.get("cpr_stages", 2) == 3 else "two-stage"
-    kry = "BiCGSTAB" if sv.get("krylov", 0) == 1 else f"FGMRES({sv.get('gmres_m', 30)})"
+    kry = "BiCGSTAB" if sv.get("krylov", 0) == 1 else \
+        f"FGMRES({sv.get('gmres_m', 30)}, {'selective CGS' if sv.get('orth', 0) else 'CGS2'})"
     forcing = "theta 1e-8" if sv.get("forcing", 0) == 0 else f"forcing choice {sv['forcing']} of Eq. 14"
     return (f"CPR {stages} ({dec}, aggregation AMG {sv.get('amg_cycles', 1)}x V(1,1), red-black block ILU0) "
             f"{kry}, {forcing}, CNV {sv.get('newton_tol', 1e-10):g}")
@@ -350,7 +353,7 @@ def run_ours(args):
         oracle.build()
         v, t = cpu_oracle_sample(case, 1)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"one Newton iteration of the first 10-day step ({t:.1f} s, 1 thread)"}
+               "sample": f"one Newton iteration of the first {dts[0]:g}-day step ({t:.1f} s, 1 thread)"}
 
     if rank == 0:
         line = {
@@ -487,6 +490,8 @@ def main():
                     help="paper: BiCGSTAB, adaptive forcing (Eq. 14 choice 2), CNV 1e-3")
     ap.add_argument("--decouple", default="qi", choices=["qi", "abf"])
     ap.add_argument("--cpr-stages", type=int, default=2, choices=[2, 3])
+    ap.add_argument("--orth", default="cgs2", choices=["cgs2", "selective"],
+                    help="FGMRES Gram-Schmidt: two passes always, or the second only when needed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -137,6 +137,8 @@ typedef struct {
     double ew_gamma, ew_beta;   /* constants of forcing choice 3 (gamma in (0, 1], beta > 0) */
     double theta_max;           /* theta of a Newton solve's first iteration and upper bound (lin_tol..1) */
     int32_t fused_coarse;       /* 1: the coarse AMG levels of a V-cycle run in one cluster launch */
+    int32_t orth;               /* FGMRES Gram-Schmidt: 0 CGS2 (always two passes), 1 the second pass only
+                                   when the first removed more than half of ||w||^2 */
 } sim_options;
 
 typedef struct {

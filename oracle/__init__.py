@@ -62,6 +62,7 @@ class OraInput(C.Structure):
         ("krylov", C.c_int32), ("lin_max_iter", C.c_int32), ("forcing", C.c_int32),
         ("ew_gamma", C.c_double), ("ew_beta", C.c_double), ("theta_max", C.c_double),
         ("w_ctrl", C.POINTER(C.c_int32)), ("w_rate", C.POINTER(C.c_double)),
+        ("orth", C.c_int32),
     ]
 
 
@@ -179,7 +180,7 @@ def make_input(case: dict, keep: list, **solver_overrides) -> OraInput:
         setattr(inp, name, float(sv[name]))
     for name in ("newton_max", "gmres_m", "gmres_max_restarts", "precond", "stage2", "amg_rounds",
                  "amg_coarse_max", "amg_max_levels", "max_cuts", "amg_cycles", "decouple", "cpr_stages",
-                 "krylov", "lin_max_iter", "forcing"):
+                 "krylov", "lin_max_iter", "forcing", "orth"):
         setattr(inp, name, int(sv[name]))
     return inp
 

@@ -1250,12 +1250,18 @@ int ora_linear_solve(ora_sim *s, const double *bvec, double *x, ora_lin_info *in
             ora_precond_apply(s, vj, zj);
             op_apply(s, zj, w);
             /* CGS pass 1 */
+            const double wn2 = dot(w, w, n);
             for (int i = 0; i <= j; i++) hcol[i] = dot(s->V + (size_t)i * n, w, n);
             for (int i = 0; i <= j; i++) { const double *vi = s->V + (size_t)i * n; for (int t = 0; t < n; t++) w[t] -= hcol[i] * vi[t]; }
-            /* CGS pass 2 */
-            for (int i = 0; i <= j; i++) hre[i] = dot(s->V + (size_t)i * n, w, n);
-            for (int i = 0; i <= j; i++) { const double *vi = s->V + (size_t)i * n; for (int t = 0; t < n; t++) w[t] -= hre[i] * vi[t]; }
-            for (int i = 0; i <= j; i++) hcol[i] += hre[i];
+            /* CGS pass 2: always (CGS2), or when pass 1 removed more than half of
+               ||w||^2, i.e. ||w||^2 - sum h^2 < ||w||^2 / 2 (selective form) */
+            double hh = 0.0;
+            for (int i = 0; i <= j; i++) hh += hcol[i] * hcol[i];
+            if (!in->orth || hh > 0.5 * wn2) {
+                for (int i = 0; i <= j; i++) hre[i] = dot(s->V + (size_t)i * n, w, n);
+                for (int i = 0; i <= j; i++) { const double *vi = s->V + (size_t)i * n; for (int t = 0; t < n; t++) w[t] -= hre[i] * vi[t]; }
+                for (int i = 0; i <= j; i++) hcol[i] += hre[i];
+            }
             double hn = sqrt(dot(w, w, n));
             double *vn = s->V + (size_t)(j + 1) * n;
             if (hn > 0.0) for (int t = 0; t < n; t++) vn[t] = w[t] / hn;

@@ -70,6 +70,8 @@ typedef struct {
        initial guess is w_bhp.  Injectors take water-rate control only. */
     const int32_t *w_ctrl;
     const double *w_rate;
+    int32_t orth;                  /* FGMRES: 0 CGS2; 1 second Gram-Schmidt pass only when the first
+                                      removed more than half of ||w||^2 (Daniel et al. 1976) */
 } ora_input;
 
 typedef struct {

@@ -63,6 +63,20 @@ __device__ __forceinline__ int nbr7(const GridDesc &g, int i, int d) {
     default: return iz < g.nz - 1 ? i + g.nx * g.ny : -1;
     }
 }
+// thread t of a launch over one colour (0: ix+iy+iz even, 1: odd): slot k of
+// x-row r holds the cell ix = 2k or 2k+1 of that colour, so a warp's threads
+// all work (a launch over every cell would leave half of each warp idle)
+__device__ __forceinline__ int colour_cell(const GridDesc &g, long t, int colour) {
+    const int hx = (g.nx + 1) >> 1;
+    const long r = t / hx;
+    const int k = (int)(t - r * hx);
+    if (r >= (long)g.ny * g.nz) return -1;
+    const int iy = (int)(r % g.ny), iz = (int)(r / g.ny);
+    const int ix = 2 * k + (((iy + iz) & 1) != colour ? 1 : 0);
+    if (ix >= g.nx) return -1;
+    return (int)(ix + (long)g.nx * r);
+}
+
 __device__ __forceinline__ int opp(int d) { return d == 0 ? 0 : ((d & 1) ? d + 1 : d - 1); }
 __device__ __forceinline__ bool is_black(const GridDesc &g, int i) {
     const int ix = i % g.nx, t = i / g.nx, iy = t % g.ny, iz = t / g.ny;
@@ -279,10 +293,10 @@ __device__ __forceinline__ void inv_block(const double *A, double *Ai) {
 template <int B>
 __global__ void diag_inv_kernel(GridDesc g, const double *__restrict__ J, WellCorr wc, const double *__restrict__ lsc,
                                 int mode, double *__restrict__ dinv) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const long N = g.N;
-    if (i >= N) return;
-    if (mode == 1 && is_black(g, i)) return;
+    const int i = mode == 1 ? colour_cell(g, blockIdx.x * (long)blockDim.x + threadIdx.x, 0)
+                            : (blockIdx.x * blockDim.x + threadIdx.x < N ? (int)(blockIdx.x * blockDim.x + threadIdx.x) : -1);
+    if (i < 0) return;
     double L[B * B], A[B * B], Ai[B * B];
     if (mode == 2) {
         load_jblock<B>(J, N, i, 0, i, wc, A);
@@ -299,9 +313,9 @@ __global__ void diag_inv_kernel(GridDesc g, const double *__restrict__ J, WellCo
 template <int B>
 __global__ void ilu_black_kernel(GridDesc g, const double *__restrict__ J, WellCorr wc, const double *__restrict__ lsc,
                                  double *__restrict__ dinv) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = colour_cell(g, blockIdx.x * (long)blockDim.x + threadIdx.x, 1);
     const long N = g.N;
-    if (i >= N || !is_black(g, i)) return;
+    if (i < 0) return;
     double Li[B * B];
     load_lsc<B>(lsc, N, i, Li);
     double D[B * B];
@@ -529,14 +543,130 @@ __global__ void sort_members_kernel(int nc, const int *__restrict__ moff, int *_
     }
 }
 
-// Galerkin row I of P^T A P: members moff/mem (ascending), entries summed
-// in member order then column order, columns sorted ascending.
+// entries of the members' rows of coarse row I (the list the Galerkin sum runs over)
+__device__ __forceinline__ int galerkin_list_len(const Mat<double> &A, const int *__restrict__ moff,
+                                                 const int *__restrict__ mem, int I) {
+    int L = 0;
+    for (int q = moff[I]; q < moff[I + 1]; q++) for_row(A, mem[q], [&](int, double) { L++; });
+    return L;
+}
+
+// Galerkin row I of P^T A P, one warp per row.  The members' row entries,
+// mapped to aggregate columns, are staged in member-then-column order (the
+// order of the sequential definition); each distinct column sums its entries
+// in that order, and the distinct columns are ranked ascending.  Rows whose
+// list exceeds kGalCap entries are left to galerkin_kernel.
+constexpr int kGalWarps = 8, kGalCap = 256;
+
+__global__ void __launch_bounds__(kGalWarps * 32) galerkin_warp_kernel(
+    Mat<double> A, const int *__restrict__ agg, const int *__restrict__ moff, const int *__restrict__ mem, int nc,
+    int mode, int *__restrict__ len, int W, int *__restrict__ ccol, double *__restrict__ cval, int *err) {
+    __shared__ int scol[kGalWarps][kGalCap];
+    __shared__ double sval[kGalWarps][kGalCap];
+    __shared__ unsigned char sfirst[kGalWarps][kGalCap];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int I = blockIdx.x * kGalWarps + w;
+    if (I >= nc) return;                          // whole warp
+    int *cl = scol[w];
+    double *vl = sval[w];
+    unsigned char *fl = sfirst[w];
+    // 1. the ordered list
+    int L = 0;
+    bool over = false;
+    for (int q = moff[I]; q < moff[I + 1] && !over; q++) {
+        const int m = mem[q];
+        if (A.st) {
+            // structured row: the 7-point entries in ascending column order
+            const int nx = A.g.nx, ny = A.g.ny, nxy = nx * ny;
+            const int ix = m % nx, t = m / nx, iy = t % ny, iz = t / ny;
+            const long n = A.n;
+            const int dirs[7] = {5, 3, 1, 0, 2, 4, 6};
+            const int offs[7] = {-nxy, -nx, -1, 0, 1, nx, nxy};
+            bool ok = false;
+            int col = 0, d = 0;
+            if (lane < 7) {
+                d = dirs[lane];
+                ok = (d == 0) || (d == 1 && ix > 0) || (d == 2 && ix < nx - 1) || (d == 3 && iy > 0) ||
+                     (d == 4 && iy < ny - 1) || (d == 5 && iz > 0) || (d == 6 && iz < A.g.nz - 1);
+                col = m + offs[lane];
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, ok);
+            const int cnt = __popc(bal);
+            if (L + cnt > kGalCap) { over = true; break; }
+            if (ok) {
+                const int pos = L + __popc(bal & ((1u << lane) - 1u));
+                cl[pos] = agg[col];
+                vl[pos] = A.val[d * n + m];
+            }
+            L += cnt;
+        } else {
+            for (int k0 = 0; k0 < A.width; k0 += 32) {
+                const int k = k0 + lane;
+                int col = -1;
+                double v = 0.0;
+                if (k < A.width) { col = A.col[(long)k * A.n + m]; if (col >= 0) v = A.val[(long)k * A.n + m]; }
+                const bool ok = col >= 0;
+                const unsigned bal = __ballot_sync(0xffffffffu, ok);
+                const int cnt = __popc(bal);
+                if (L + cnt > kGalCap) { over = true; break; }
+                if (ok) {
+                    const int pos = L + __popc(bal & ((1u << lane) - 1u));
+                    cl[pos] = agg[col];
+                    vl[pos] = v;
+                }
+                L += cnt;
+                if (cnt < 32) break;              // -1 padding: the row has ended
+            }
+        }
+    }
+    if (over) return;                             // galerkin_kernel takes this row
+    __syncwarp();
+    // 2. first occurrences, their count, their ordered sums and ranks
+    int D = 0;
+    for (int p0 = 0; p0 < L; p0 += 32) {
+        const int p = p0 + lane;
+        bool first = false;
+        if (p < L) {
+            first = true;
+            const int c = cl[p];
+            for (int q = 0; q < p; q++) if (cl[q] == c) { first = false; break; }
+            fl[p] = first;
+        }
+        D += __popc(__ballot_sync(0xffffffffu, first));
+    }
+    if (D > MAXE) { if (lane == 0) atomicExch(err, 1); return; }
+    if (mode == 0) {
+        if (lane == 0) { len[I] = D; atomicMax(len + nc, D); }
+        return;
+    }
+    __syncwarp();
+    for (int p0 = 0; p0 < L; p0 += 32) {
+        const int p = p0 + lane;
+        if (p >= L || !fl[p]) continue;
+        const int c = cl[p];
+        double sum = 0.0;
+        for (int q = p; q < L; q++) if (cl[q] == c) sum = __dadd_rn(sum, vl[q]);
+        int rank = 0;                             // distinct columns below c
+        for (int q = 0; q < L; q++) rank += (fl[q] && cl[q] < c);
+        ccol[(long)rank * nc + I] = c;
+        cval[(long)rank * nc + I] = sum;
+    }
+    for (int t = D + lane; t < W; t += 32) {
+        ccol[(long)t * nc + I] = -1;
+        cval[(long)t * nc + I] = 0.0;
+    }
+}
+
+// Galerkin row I of P^T A P, one thread per row (rows with long lists):
+// members moff/mem (ascending), entries summed in member order then column
+// order, columns sorted ascending.
 // mode 0: row length into len[I]; mode 1: write the ELL row of width W
 __global__ void galerkin_kernel(Mat<double> A, const int *__restrict__ agg, const int *__restrict__ moff,
                                 const int *__restrict__ mem, int nc, int mode, int *__restrict__ len, int W,
                                 int *__restrict__ ccol, double *__restrict__ cval, int *err) {
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nc) return;
+    if (galerkin_list_len(A, moff, mem, I) <= kGalCap) return;   // done by galerkin_warp_kernel
     int cols[MAXE];
     double vals[MAXE];
     int cnt = 0;
@@ -585,14 +715,31 @@ __global__ void l1_kernel(Mat<double> A, T *__restrict__ dinv) {
 // Gauss-Jordan step k without pivoting on the augmented [A | Inv] (n x 2n),
 // read from src and written to dst: the coarse pressure block is
 // diagonally dominant with a positive diagonal, so the pivots stay positive.
-__global__ void gj_step_kernel(int n, int k, const double *__restrict__ src, double *__restrict__ dst) {
-    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    const long w = 2L * n;
-    if (t >= (long)n * w) return;
-    const int i = (int)(t / w), j = (int)(t % w);
-    const double piv = src[(long)k * w + k];
-    const double pk = src[(long)k * w + j] / piv;
-    dst[t] = (i == k) ? pk : src[t] - src[(long)i * w + k] * pk;
+// Gauss-Jordan elimination without pivoting of [A | I] on the coarsest level,
+// in one launch of an 8-CTA cluster: step k writes, from the matrix left by
+// step k-1 (ping-pong buffers), pivot row k divided by its pivot and every
+// other row minus its column-k entry times that row; a cluster barrier
+// separates the steps; the result ends in A1 for odd n, else A0
+constexpr int kGjMax = 1024;   // largest coarsest level (rows)
+
+__global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(1024, 1)
+gj_cluster_kernel(int n, double *__restrict__ A0, double *__restrict__ A1) {
+    __shared__ double pk[2 * kGjMax];   // the pivot row over its pivot, per CTA (one division per entry)
+    const long w = 2L * n, total = (long)n * w;
+    const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x, nt = (long)gridDim.x * blockDim.x;
+    for (int k = 0; k < n; k++) {
+        const double *src = (k & 1) ? A1 : A0;
+        double *dst = (k & 1) ? A0 : A1;
+        const double piv = src[(long)k * w + k];
+        for (int j = threadIdx.x; j < w; j += blockDim.x) pk[j] = src[(long)k * w + j] / piv;
+        __syncthreads();
+        for (long t = tid; t < total; t += nt) {
+            const int i = (int)(t / w), j = (int)(t % w);
+            dst[t] = (i == k) ? pk[j] : src[t] - src[(long)i * w + k] * pk[j];
+        }
+        __threadfence();
+        cg::this_cluster().sync();   // also keeps pk from being overwritten early
+    }
 }
 
 __global__ void gj_init_kernel(Mat<double> A, double *__restrict__ aug) {
@@ -908,11 +1055,10 @@ __global__ void stage2_b_kernel(GridDesc g, const T *__restrict__ ahat, const T 
                                 const T *__restrict__ r2, T *__restrict__ z, const T *__restrict__ ep,
                                 const T *__restrict__ addv, TZ *__restrict__ out, const int *done) {
     if (skip(done)) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = colour_cell(g, blockIdx.x * (long)blockDim.x + threadIdx.x, 1);
     const long N = g.N;
-    if (i >= N) return;
+    if (i < 0) return;
     const Cell cc = cell_of(g, i);
-    if (((cc.ix + cc.iy + cc.iz) & 1) == 0) return;
     T t[B];
 #pragma unroll
     for (int c = 0; c < B; c++) t[c] = r2[(long)c * N + i];
@@ -945,18 +1091,19 @@ __global__ void stage2_c_kernel(GridDesc g, const T *__restrict__ ahat, const T 
                                 const T *__restrict__ ep, const T *__restrict__ addv, TZ *__restrict__ out, int rb,
                                 const int *done) {
     if (skip(done)) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const long N = g.N;
-    if (i >= N) return;
     if (!rb) {
+        const int i = blockIdx.x * blockDim.x + threadIdx.x;
+        if (i >= N) return;
 #pragma unroll
         for (int r = 0; r < B; r++) {
             out[(long)r * N + i] = (TZ)fin<T>(z[(long)r * N + i], r, i, N, ep, addv);
         }
         return;
     }
+    const int i = colour_cell(g, blockIdx.x * (long)blockDim.x + threadIdx.x, 0);   // red cells
+    if (i < 0) return;
     const Cell cc = cell_of(g, i);
-    if ((cc.ix + cc.iy + cc.iz) & 1) return;
     T t[B];
 #pragma unroll
     for (int c = 0; c < B; c++) t[c] = (T)0;
@@ -1244,9 +1391,12 @@ static int galerkin(sim_t *s, const Mat<double> &A, const int *agg, const int *m
     if (!len) return -1;
     if (!sim_cuda_ok(s, cudaMemsetAsync(len + nc, 0, sizeof(int), s->stream), "memset")) return -1;
     if (!sim_cuda_ok(s, cudaMemsetAsync(s->iscal + 1, 0, sizeof(int), s->stream), "memset")) return -1;
+    const int gw = (nc + kGalWarps - 1) / kGalWarps;
+    galerkin_warp_kernel<<<gw, kGalWarps * 32, 0, s->stream>>>(A, agg, moff, mem, nc, 0, len, 0, nullptr, nullptr,
+                                                              s->iscal + 1);
     galerkin_kernel<<<sim_blocks(nc), SIM_THREADS, 0, s->stream>>>(A, agg, moff, mem, nc, 0, len, 0, nullptr, nullptr,
                                                                    s->iscal + 1);
-    s->launches++;
+    s->launches += 2;
     int hv[2];
     if (!sim_cuda_ok(s, cudaMemcpyAsync(&s->h_pinned[0], len + nc, sizeof(int), cudaMemcpyDeviceToHost, s->stream), "copy") ||
         !sim_cuda_ok(s, cudaMemcpyAsync((char *)&s->h_pinned[0] + 4, s->iscal + 1, sizeof(int), cudaMemcpyDeviceToHost, s->stream), "copy") ||
@@ -1258,9 +1408,11 @@ static int galerkin(sim_t *s, const Mat<double> &A, const int *agg, const int *m
     *col = (int *)dev_alloc_async(s, sizeof(int) * (size_t)W * nc);
     *val = (double *)dev_alloc_async(s, sizeof(double) * (size_t)W * nc);
     if (!*col || !*val) return -1;
+    galerkin_warp_kernel<<<gw, kGalWarps * 32, 0, s->stream>>>(A, agg, moff, mem, nc, 1, len, W, *col, *val,
+                                                              s->iscal + 1);
     galerkin_kernel<<<sim_blocks(nc), SIM_THREADS, 0, s->stream>>>(A, agg, moff, mem, nc, 1, len, W, *col, *val,
                                                                    s->iscal + 1);
-    s->launches++;
+    s->launches += 2;
     dev_free_async(s, len);
     if (!sim_cuda_ok(s, cudaGetLastError(), "Galerkin")) return -1;
     return W;
@@ -1304,10 +1456,8 @@ static sim_status finish_levels(sim_t *s) {
     if (!A0 || !A1) return s->err;
     gj_init_kernel<<<sim_blocks(n), SIM_THREADS, 0, s->stream>>>(level_mat(s, C, nl - 1), A0);
     s->launches++;
-    for (int k = 0; k < n; k++) {
-        gj_step_kernel<<<sim_blocks((long)aug), SIM_THREADS, 0, s->stream>>>(n, k, (k & 1) ? A1 : A0, (k & 1) ? A0 : A1);
-        s->launches++;
-    }
+    gj_cluster_kernel<<<8, 1024, 0, s->stream>>>(n, A0, A1);
+    s->launches++;
     // the coarsest inverse stays FP64 in both forms: the coarse matrices of
     // strongly heterogeneous fields are ill-conditioned, and the product is tiny
     C.coarse_inv = dev_alloc_async(s, sizeof(double) * (size_t)n * n);
@@ -1366,10 +1516,15 @@ static sim_status amg_setup(sim_t *s) {
     return sim_mixed(s) ? finish_levels<float>(s) : finish_levels<double>(s);
 }
 
+// blocks of a launch over one colour (colour_cell)
+static int colour_blocks(const sim_t *s) {
+    return sim_blocks((long)((s->gd.nx + 1) / 2) * s->gd.ny * s->gd.nz);
+}
+
 template <int B, typename T>
 static sim_status setup_bt(sim_t *s) {
     const int N = s->N;
-    const int nb = sim_blocks(N);
+    const int nb = sim_blocks(N), nbc = colour_blocks(s);
     WellCorr wc;
     if (s->nrate > 0) {
         wc.cell_perf = s->cell_perf; wc.pwell = s->perf_well;
@@ -1388,10 +1543,10 @@ static sim_status setup_bt(sim_t *s) {
     if (amg_setup(s) != SIM_OK) return s->err;
     s->lev[0].valT = s->apT;
     const int rb = s->opt.stage2 == SIM_STAGE2_ILU0_RB;
-    diag_inv_kernel<B><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, s->J, wc, s->lsc, rb ? 1 : 0, s->dinv_d);
+    diag_inv_kernel<B><<<rb ? nbc : nb, SIM_THREADS, 0, s->stream>>>(s->gd, s->J, wc, s->lsc, rb ? 1 : 0, s->dinv_d);
     SIM_LAUNCHED(s);
     if (rb) {
-        ilu_black_kernel<B><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, s->J, wc, s->lsc, s->dinv_d);
+        ilu_black_kernel<B><<<nbc, SIM_THREADS, 0, s->stream>>>(s->gd, s->J, wc, s->lsc, s->dinv_d);
         SIM_LAUNCHED(s);
     }
     if (sizeof(T) != sizeof(double)) {
@@ -1499,11 +1654,11 @@ static sim_status apply_btz(sim_t *s, const double *r, TZ *z, const int *done) {
                                                                 (T *)s->zr, rb, done);
         SIM_LAUNCHED(s);
         if (rb) {
-            stage2_b_kernel<B, T, T><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, (const T *)s->ahat, dinv, (const T *)s->r2,
+            stage2_b_kernel<B, T, T><<<colour_blocks(s), SIM_THREADS, 0, s->stream>>>(s->gd, (const T *)s->ahat, dinv, (const T *)s->r2,
                                                                        (T *)s->zr, nullptr, nullptr, (T *)s->x0, done);
             SIM_LAUNCHED(s);
         }
-        stage2_c_kernel<B, T, T><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, (const T *)s->ahat, dinv, (const T *)s->zr,
+        stage2_c_kernel<B, T, T><<<rb ? colour_blocks(s) : nb, SIM_THREADS, 0, s->stream>>>(s->gd, (const T *)s->ahat, dinv, (const T *)s->zr,
                                                                    nullptr, nullptr, (T *)s->x0, rb, done);
         SIM_LAUNCHED(s);
         fpf_resid_kernel<B, T><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, r, (const T *)s->qiwT, lscT, (const T *)s->ahat,
@@ -1569,11 +1724,11 @@ static sim_status apply_btz(sim_t *s, const double *r, TZ *z, const int *done) {
                                                             (T *)s->zr, rb, done);
     SIM_LAUNCHED(s);
     if (rb) {
-        stage2_b_kernel<B, T, TZ><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, (const T *)s->ahat, dinv, (const T *)s->r2,
+        stage2_b_kernel<B, T, TZ><<<colour_blocks(s), SIM_THREADS, 0, s->stream>>>(s->gd, (const T *)s->ahat, dinv, (const T *)s->r2,
                                                                     (T *)s->zr, ep, addv, z, done);
         SIM_LAUNCHED(s);
     }
-    stage2_c_kernel<B, T, TZ><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, (const T *)s->ahat, dinv, (const T *)s->zr, ep, addv,
+    stage2_c_kernel<B, T, TZ><<<rb ? colour_blocks(s) : nb, SIM_THREADS, 0, s->stream>>>(s->gd, (const T *)s->ahat, dinv, (const T *)s->zr, ep, addv,
                                                                 z, rb, done);
     SIM_LAUNCHED(s);
     return SIM_OK;

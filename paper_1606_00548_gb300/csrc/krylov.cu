@@ -111,33 +111,49 @@ __device__ void fold(const double *partials, int nv, double *out) {
 
 constexpr int NVMAX = SIM_MAX_M + 1;
 
-// h[k] = V_k . w, k < NV (NV exact: no predicated work for absent vectors)
+// h[k] = V_k . w, k < NV (NV exact: no predicated work for absent vectors),
+// and h[NV] = w . w (the norm the selective reorthogonalisation test needs)
 template <int NV>
 __global__ void __launch_bounds__(SIM_THREADS) dots_kernel(const double *__restrict__ V, const double *__restrict__ w,
                                                            long n, double *partials, unsigned int *ticket,
                                                            double *out, const int *done) {
     if (skip(done)) return;
-    double acc[NV];
+    double acc[NV + 1];
 #pragma unroll
-    for (int k = 0; k < NV; k++) acc[k] = 0.0;
+    for (int k = 0; k <= NV; k++) acc[k] = 0.0;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
         const double wi = w[i];
 #pragma unroll
         for (int k = 0; k < NV; k++) acc[k] += V[k * n + i] * wi;
+        acc[NV] += wi * wi;
     }
-    block_partials<NV>(acc, NV, partials);
+    block_partials<NV + 1>(acc, NV + 1, partials);
     if (last_block(ticket)) {
-        fold(partials, NV, out);
+        fold(partials, NV + 1, out);
         if (threadIdx.x == 0) *ticket = 0u;
     }
 }
 
-// w -= sum_k h[k] V_k ; out[k] = V_k . w (second Gram-Schmidt pass)
+// second Gram-Schmidt pass needed?  Always for CGS2; for the selective form
+// (Daniel, Gragg, Kaufman, Stewart 1976) when the first pass removed more than
+// half of ||w||^2: ||w - V h||^2 = ||w||^2 - sum h^2 < ||w||^2 / 2.  Every
+// thread evaluates it the same way from the same h.
+__device__ __forceinline__ bool need_reorth(const double *h, int nv, int selective) {
+    if (!selective) return true;
+    double s = 0.0;
+    for (int k = 0; k < nv; k++) s += h[k] * h[k];
+    return s > 0.5 * h[nv];
+}
+
+// w -= sum_k h[k] V_k ; out[k] = V_k . w (second Gram-Schmidt pass); nothing
+// when the selective test finds no second pass is needed
 template <int NV>
 __global__ void __launch_bounds__(SIM_THREADS) orth_dots_kernel(const double *__restrict__ V, double *__restrict__ w,
                                                                 long n, const double *h, double *partials,
-                                                                unsigned int *ticket, double *out, const int *done) {
+                                                                unsigned int *ticket, double *out, const int *done,
+                                                                int selective) {
     if (skip(done)) return;
+    if (!need_reorth(h, NV, selective)) return;
     double hs[NV];
 #pragma unroll
     for (int k = 0; k < NV; k++) hs[k] = h[k];
@@ -169,9 +185,9 @@ struct OrthDispatch {
         else OrthDispatch<NV - 1>::dots(nv, st, V, w, n, part, tk, out, done);
     }
     static void orth(int nv, cudaStream_t st, const double *V, double *w, long n, const double *h, double *part,
-                     unsigned int *tk, double *out, const int *done) {
-        if (nv == NV) orth_dots_kernel<NV><<<SIM_RED_BLOCKS, SIM_THREADS, 0, st>>>(V, w, n, h, part, tk, out, done);
-        else OrthDispatch<NV - 1>::orth(nv, st, V, w, n, h, part, tk, out, done);
+                     unsigned int *tk, double *out, const int *done, int sel) {
+        if (nv == NV) orth_dots_kernel<NV><<<SIM_RED_BLOCKS, SIM_THREADS, 0, st>>>(V, w, n, h, part, tk, out, done, sel);
+        else OrthDispatch<NV - 1>::orth(nv, st, V, w, n, h, part, tk, out, done, sel);
     }
 };
 template <>
@@ -179,17 +195,18 @@ struct OrthDispatch<0> {
     static void dots(int, cudaStream_t, const double *, const double *, long, double *, unsigned int *, double *,
                      const int *) {}
     static void orth(int, cudaStream_t, const double *, double *, long, const double *, double *, unsigned int *,
-                     double *, const int *) {}
+                     double *, const int *, int) {}
 };
 
 // w -= sum_k h2[k] V_k ; ||w||; last block: Hessenberg column j, Givens, test
 __global__ void __launch_bounds__(SIM_THREADS) orth_norm_kernel(const double *__restrict__ V, double *__restrict__ w,
                                                                 long n, int j, int m, double *partials,
-                                                                unsigned int *ticket, KrylovCtl *ctl) {
+                                                                unsigned int *ticket, KrylovCtl *ctl, int selective) {
     if (ctl->done) return;
     const int nv = j + 1;
+    const bool re = need_reorth(ctl->h, nv, selective);   // else the first pass is subtracted here
     __shared__ double hs[NVMAX];
-    for (int k = threadIdx.x; k < nv; k += blockDim.x) hs[k] = ctl->h2[k];
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) hs[k] = re ? ctl->h2[k] : ctl->h[k];
     __syncthreads();
     double acc[1] = {0.0};
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
@@ -207,7 +224,7 @@ __global__ void __launch_bounds__(SIM_THREADS) orth_norm_kernel(const double *__
             *ticket = 0u;
             const double hn = sqrt(nrm);
             double col[NVMAX + 1];
-            for (int k = 0; k <= j; k++) col[k] = ctl->h[k] + ctl->h2[k];
+            for (int k = 0; k <= j; k++) col[k] = re ? ctl->h[k] + ctl->h2[k] : ctl->h[k];
             for (int k = 0; k < j; k++) {
                 const double a = col[k], c2 = col[k + 1];
                 col[k] = ctl->cs[k] * a + ctl->sn[k] * c2;
@@ -545,9 +562,11 @@ static sim_status enqueue_cycle(sim_t *s) {
         if (spmv_done(s, zj, zf, s->w, done) != SIM_OK) return s->err;
         OrthDispatch<SIM_MAX_M>::dots(j + 1, s->stream, s->V, s->w, n, s->red, s->ticket, ctl->h, done);
         SIM_LAUNCHED(s);
-        OrthDispatch<SIM_MAX_M>::orth(j + 1, s->stream, s->V, s->w, n, ctl->h, s->red, s->ticket, ctl->h2, done);
+        OrthDispatch<SIM_MAX_M>::orth(j + 1, s->stream, s->V, s->w, n, ctl->h, s->red, s->ticket, ctl->h2, done,
+                                      s->opt.orth);
         SIM_LAUNCHED(s);
-        orth_norm_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(s->V, s->w, n, j, m, s->red, s->ticket, ctl);
+        orth_norm_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(s->V, s->w, n, j, m, s->red, s->ticket, ctl,
+                                                                        s->opt.orth);
         SIM_LAUNCHED(s);
         scale_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(s->w, s->V + (size_t)(j + 1) * n, n, ctl, 0);
         SIM_LAUNCHED(s);

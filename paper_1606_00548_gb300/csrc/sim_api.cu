@@ -123,6 +123,7 @@ sim_status sim_create(const sim_grid *g, const sim_rock *r, const sim_fluid *f, 
         !(o->lin_tol > 0 && o->lin_tol < 1) || !(o->theta_max >= o->lin_tol && o->theta_max < 1) ||
         !(o->ew_gamma > 0 && o->ew_gamma <= 1) || !(o->ew_beta > 0))
         return sim_fail(nullptr, SIM_EINVAL, "bad Krylov / forcing-term options");
+    if (o->orth < 0 || o->orth > 1) return sim_fail(nullptr, SIM_EINVAL, "orth must be 0 or 1");
     if (o->krylov == SIM_KRYLOV_BICGSTAB && o->gmres_m < 2)
         return sim_fail(nullptr, SIM_EINVAL, "BiCGSTAB needs gmres_m >= 2 (its two preconditioned vectors)");
     if (f->model == 3) {

@@ -73,7 +73,7 @@ class sim_options(C.Structure):
                 ("amg_cycles", C.c_int32), ("graphs", C.c_int32), ("decouple", C.c_int32),
                 ("cpr_stages", C.c_int32), ("krylov", C.c_int32), ("lin_max_iter", C.c_int32),
                 ("forcing", C.c_int32), ("ew_gamma", C.c_double), ("ew_beta", C.c_double),
-                ("theta_max", C.c_double), ("fused_coarse", C.c_int32)]
+                ("theta_max", C.c_double), ("fused_coarse", C.c_int32), ("orth", C.c_int32)]
 
 
 class sim_linear_info(C.Structure):
@@ -276,6 +276,7 @@ def options_from(solver: dict, precision: int = 0) -> sim_options:
     o.precision = int(precision)
     o.graphs = int(solver.get("graphs", 1))
     o.fused_coarse = int(solver.get("fused_coarse", 1))
+    o.orth = int(solver.get("orth", 0))
     return o
 
 

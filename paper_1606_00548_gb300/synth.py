@@ -129,7 +129,7 @@ def default_solver(**kw):
         precond=2, stage2=1, amg_theta=0.25, amg_rounds=4, amg_coarse_max=256,
         amg_max_levels=16, chop_ds=0.2, chop_dp=50.0, max_cuts=8, amg_cycles=1,
         decouple=0, cpr_stages=2, krylov=0, lin_max_iter=100, forcing=0, ew_gamma=0.9, ew_beta=2.0,
-        theta_max=0.5,
+        theta_max=0.5, orth=0,
     )
     s.update(kw)
     return s

@@ -148,14 +148,15 @@ def test_cpr_apply_matches_oracle(torch_cuda, name, stage2, cycles, decouple, st
     assert rel_err(to_il(zd.cpu().numpy(), N, b), zo) <= 1e-9
 
 
-@pytest.mark.parametrize("name,cycles,decouple,stages", [
-    ("ow_ragged", 1, 0, 2), ("bo_ragged", 1, 0, 2), ("ow_1d", 1, 0, 2), ("bo_column", 1, 0, 2), ("bo_ragged", 2, 0, 2),
-    ("bo_ragged", 1, 1, 2), ("bo_ragged", 1, 0, 3), ("ow_ragged", 1, 1, 3), ("bo_column", 1, 1, 3)])
-def test_linear_solve_matches_oracle(torch_cuda, name, cycles, decouple, stages):
+@pytest.mark.parametrize("name,cycles,decouple,stages,orth", [
+    ("ow_ragged", 1, 0, 2, 0), ("bo_ragged", 1, 0, 2, 0), ("ow_1d", 1, 0, 2, 0), ("bo_column", 1, 0, 2, 0),
+    ("bo_ragged", 2, 0, 2, 0), ("bo_ragged", 1, 1, 2, 0), ("bo_ragged", 1, 0, 3, 0), ("ow_ragged", 1, 1, 3, 0),
+    ("bo_column", 1, 1, 3, 0), ("bo_ragged", 1, 0, 2, 1), ("ow_ragged", 1, 0, 2, 1)])
+def test_linear_solve_matches_oracle(torch_cuda, name, cycles, decouple, stages, orth):
     torch = torch_cuda
     case = CASES[name]()
     dt = 10.0 if case["model"] == 3 else 1.0
-    g, o = _loaded_pair(case, dt, None, amg_cycles=cycles, decouple=decouple, cpr_stages=stages)
+    g, o = _loaded_pair(case, dt, None, amg_cycles=cycles, decouple=decouple, cpr_stages=stages, orth=orth)
     N, b = g.N, g.b
     rhs = np.random.default_rng(3).standard_normal(N * b)
     xo, io = o.linear_solve(rhs)

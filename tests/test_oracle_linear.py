@@ -42,8 +42,10 @@ def assembled(case, dt, seed=0, **solver):
 
 
 @pytest.mark.parametrize("name,case,dt", tiny_cases())
-def test_fgmres_cpr_matches_dense_solve(oracle_lib, name, case, dt):
-    o = assembled(case, dt, lin_tol=1e-12)
+@pytest.mark.parametrize("orth", [0, 1])
+def test_fgmres_cpr_matches_dense_solve(oracle_lib, name, case, dt, orth):
+    """CGS2 and the selective second Gram-Schmidt pass both solve to LAPACK's answer."""
+    o = assembled(case, dt, lin_tol=1e-12, orth=orth)
     A = dense_from_blocks(o.jacobian(), case["nx"], case["ny"], case["nz"])
     b = -o.residual()
     x, info = o.linear_solve(b)
