@@ -516,9 +516,12 @@ void ora_assemble(ora_sim *s, double dt) {
         double *apw = &s->apw[q * 3], *awp = &s->awp[q * 3];
         for (int k = 0; k < 3; k++) { apw[k] = 0.0; awp[k] = 0.0; }
         const int cc = s->wctrl[w] == 1 ? CW : (s->wctrl[w] == 2 ? CO : -1);   /* controlled component */
-        if (s->perf_type[q] == 1) {
-            /* water injector: water at the cell's total mobility */
-            double Dw = s->wp[w] - p - P->rho[PW].v * dh;
+        const double Dw = s->wp[w] - p - P->rho[PW].v * dh;   /* head of the water-filled injector */
+        if (s->perf_type[q] == 1 && (Dw >= 0.0 || s->wctrl[w])) {
+            /* water injector: water at the cell's total mobility.  A rate-
+               controlled injector keeps this form for a negative head too: its
+               solution injects, and the form keeps dR_w/dp_h from vanishing on
+               the Newton path */
             dual lam = dmul(P->rhow, P->lamt);
             double qw = WI * lam.v * Dw;
             s->R[i * b + CW] -= qw;
@@ -533,8 +536,14 @@ void ora_assemble(ora_sim *s, double dt) {
             }
             if (cc == CW) { s->rw[w] += qw; s->aww[w] += WI * lam.v; }
         } else {
+            /* producer (Eq. 6 per phase), or a BHP-controlled injector whose
+               water head is below the cell pressure: the cell's phases flow
+               into the wellbore at their own mobilities, driven for the
+               injector by its water head (continuous with injection at Dw = 0) */
+            const int inj = s->perf_type[q] == 1;
             for (int ph = 0; ph < np; ph++) {
-                double Dp = s->wp[w] - p - P->rho[ph].v * dh;
+                double Dp = inj ? Dw : s->wp[w] - p - P->rho[ph].v * dh;
+                const int hp = inj ? PW : ph;             /* phase whose density sets the head */
                 for (int c = 0; c < b; c++) {
                     if (!carries(in->model, ph, c)) continue;
                     const dual *m = &P->mob[ph][c];
@@ -544,7 +553,7 @@ void ora_assemble(ora_sim *s, double dt) {
                     s->qwell[w * 3 + c] += qc;
                     apw[c] -= WI * m->v;
                     for (int k = 0; k < b; k++) {
-                        double dD = (k == 0 ? -1.0 : 0.0) - P->rho[ph].d[k] * dh;
+                        double dD = (k == 0 ? -1.0 : 0.0) - P->rho[hp].d[k] * dh;
                         double dq = WI * (m->d[k] * Dp + m->v * dD);
                         D[c * b + k] -= dq;
                         if (c == cc) awp[k] += dq;

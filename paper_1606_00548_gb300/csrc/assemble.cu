@@ -411,8 +411,12 @@ __global__ void well_kernel(FluidConst f, GridDesc g, const double *__restrict__
         const double W = wi[q];
         const double bhp = wp[w];
         double a_pw[3] = {0.0, 0.0, 0.0}, a_wp[3] = {0.0, 0.0, 0.0}, qc4[4] = {0.0, 0.0, 0.0, 0.0};
-        if (type[q] == SIM_WELL_WATER_INJECTOR) {
-            const double Dw = bhp - p - P.rho[0].v * dh;
+        const double Dw = bhp - p - P.rho[0].v * dh;     // head of a water-filled injector
+        const bool inj = type[q] == SIM_WELL_WATER_INJECTOR;
+        if (inj && (Dw >= 0.0 || ctrl)) {
+            // water at the cell's total mobility; a rate-controlled injector keeps
+            // this form for a negative head too (its solution injects, and the
+            // form keeps dR_w/dp_h from vanishing on the Newton path)
             const Dl<B> lam = P.rho[0] * P.lamt;
             const double qw = W * lam.v * Dw;
             R[i] -= qw;
@@ -428,9 +432,13 @@ __global__ void well_kernel(FluidConst f, GridDesc g, const double *__restrict__
             }
             if (cc == 0) { qc4[3] = qw; }
         } else {
+            // producer (Eq. 6 per phase), or a BHP-controlled injector in
+            // backflow: the cell's phases leave at their own mobilities, driven
+            // for the injector by its water head (continuous at Dw = 0)
 #pragma unroll
             for (int a = 0; a < B; a++) {
-                const double Dp = bhp - p - P.rho[a].v * dh;
+                const double Dp = inj ? Dw : bhp - p - P.rho[a].v * dh;
+                const int hp = inj ? 0 : a;
 #pragma unroll
                 for (int pq = 0; pq < Layout<B>::NPAIR; pq++) {
                     if (Layout<B>::pair_phase(pq) != a) continue;
@@ -443,7 +451,7 @@ __global__ void well_kernel(FluidConst f, GridDesc g, const double *__restrict__
                     a_pw[c] -= W * m.v;
 #pragma unroll
                     for (int k = 0; k < B; k++) {
-                        const double dD = (k == 0 ? -1.0 : 0.0) - P.rho[a].d[k] * dh;
+                        const double dD = (k == 0 ? -1.0 : 0.0) - P.rho[hp].d[k] * dh;
                         const double dq = W * (m.d[k] * Dp + m.v * dD);
                         J[(c * B + k) * N + i] -= dq;
                         if (c == cc) a_wp[k] += dq;
