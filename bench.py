@@ -287,36 +287,19 @@ def run_ours(args):
     e2e_value = sum_over_ranks(ws, float(N * e2e_newton)) / t_e2e
     state_bytes = N * (3 * 8 + 1)
 
-    # roofline of the block SpMV: y = J x, 7 b^2 + 2 b doubles per cell
+    # roofline of the block SpMV: y = J x, 7 b^2 + 2 b doubles per cell; device
+    # time of back-to-back launches on the library's stream (CUDA events)
     b = sim.b
-    x = torch.randn(N * b, dtype=torch.float64, device="cuda")
-    y = torch.empty_like(x)
-    with torch.cuda.stream(stream):
-        for _ in range(3):
-            sim.spmv(x, y)
-        torch.cuda.synchronize()
-        s0 = torch.cuda.Event(enable_timing=True); s1 = torch.cuda.Event(enable_timing=True)
-        reps = 20
-        s0.record(stream)
-        for _ in range(reps):
-            sim.spmv(x, y)
-        s1.record(stream)
-    torch.cuda.synchronize()
-    t_spmv = s0.elapsed_time(s1) / 1e3 / reps
+    sim.time_op(0, 3)
+    t_spmv = sim.time_op(0, 50) / 1e6
     # breakdown at the current Newton system: preconditioner apply and one full solve
     sim.assemble(dt_of(k))
     sim.precond_setup()
+    sim.time_op(1, 3)
+    t_prec = sim.time_op(1, 20) / 1e6
+    x = torch.randn(N * b, dtype=torch.float64, device="cuda")
     z = torch.empty_like(x)
-    with torch.cuda.stream(stream):
-        for _ in range(3):
-            sim.precond_apply(x, z)
-        torch.cuda.synchronize()
-        s0.record(stream)
-        for _ in range(reps):
-            sim.precond_apply(x, z)
-        s1.record(stream)
-    torch.cuda.synchronize()
-    t_prec = s0.elapsed_time(s1) / 1e3 / reps
+    s0 = torch.cuda.Event(enable_timing=True); s1 = torch.cuda.Event(enable_timing=True)
     rhs = torch.randn(N * b, dtype=torch.float64, device="cuda")
     with torch.cuda.stream(stream):
         s0.record(stream)

@@ -281,6 +281,14 @@ sim_status sim_cnv_noalloc(int32_t nx, int32_t ny, int32_t nz, double dx, double
    this handle.  Results do not depend on the shapes (each row's arithmetic
    is the same); only speed does. */
 sim_status sim_autotune(sim_t *s, double dt);
+/* Device time of one hot operation (measurement only; no paper counterpart):
+   `reps` launches on the handle's stream, each bracketed by CUDA events and
+   preceded by a 256 MB write that evicts its operands from L2.  which = 0: the
+   product y = S x of sim_spmv; 1: one CPR application as in sim_precond_apply
+   (set up first if needed).  Operands are the handle's own work vectors
+   (zeroed), so the caller's data are untouched; the eviction buffer is
+   allocated and freed inside the call.  *us = average microseconds per launch. */
+sim_status sim_time_op(sim_t *s, int32_t which, int32_t reps, double *us);
 
 /* ---- ensemble (no paper counterpart) ----
    Independent simulators (e.g. geological realisations on grids of different

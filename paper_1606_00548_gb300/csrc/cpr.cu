@@ -725,21 +725,80 @@ constexpr int kGjMax = 1024;   // largest coarsest level (rows)
 __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(1024, 1)
 gj_cluster_kernel(int n, double *__restrict__ A0, double *__restrict__ A1) {
     __shared__ double pk[2 * kGjMax];   // the pivot row over its pivot, per CTA (one division per entry)
-    const long w = 2L * n, total = (long)n * w;
-    const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x, nt = (long)gridDim.x * blockDim.x;
+    const int w = 2 * n;
+    // CTA c owns rows c, c + 8, ...; its threads stride over the columns (no index division)
+    const int tpr = blockDim.x < (unsigned)w ? blockDim.x : w;    // threads per row
+    const int rows_at_once = blockDim.x / tpr;
+    const int r0 = threadIdx.x / tpr, j0 = threadIdx.x % tpr;
     for (int k = 0; k < n; k++) {
         const double *src = (k & 1) ? A1 : A0;
         double *dst = (k & 1) ? A0 : A1;
         const double piv = src[(long)k * w + k];
         for (int j = threadIdx.x; j < w; j += blockDim.x) pk[j] = src[(long)k * w + j] / piv;
         __syncthreads();
-        for (long t = tid; t < total; t += nt) {
-            const int i = (int)(t / w), j = (int)(t % w);
-            dst[t] = (i == k) ? pk[j] : src[t] - src[(long)i * w + k] * pk[j];
+        if (r0 < rows_at_once) {
+            for (int i = blockIdx.x + r0 * gridDim.x; i < n; i += rows_at_once * gridDim.x) {
+                const double f = src[(long)i * w + k];
+                const double *si = src + (long)i * w;
+                double *di = dst + (long)i * w;
+                for (int j = j0; j < w; j += tpr) di[j] = (i == k) ? pk[j] : si[j] - f * pk[j];
+            }
         }
         __threadfence();
         cg::this_cluster().sync();   // also keeps pk from being overwritten early
     }
+}
+
+// The same elimination with the augmented matrix held in the shared memory of
+// the 8 CTAs of a cluster (n <= kGjSmem): CTA c owns a block of rows; step k's
+// owner divides pivot row k into its pivot buffer (double-buffered by step
+// parity), one cluster barrier publishes it, every CTA reads it through
+// distributed shared memory and updates its own rows.  The result (right half)
+// is written to inv; the arithmetic per entry is that of gj_cluster_kernel.
+constexpr int kGjSmem = 256;
+
+__global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(1024, 1)
+gj_dsmem_kernel(int n, const double *__restrict__ aug, double *__restrict__ inv) {
+    extern __shared__ double gsm[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int w = 2 * n, rpc = (n + 7) / 8;               // rows per CTA
+    const int me = (int)cl.block_rank();
+    double *R = gsm;                                      // [rpc][w] own rows
+    double *pkb = gsm + (long)rpc * w;                    // [2][w] pivot rows (by step parity)
+    double *pkl = pkb + 2 * w;                            // [w] local copy of the current pivot row
+    double *fcol = pkl + w;                               // [rpc] column-k entries of own rows
+    const int base = me * rpc, nrows = max(0, min(rpc, n - base));
+    for (int t = threadIdx.x; t < nrows * w; t += blockDim.x) R[t] = aug[(long)base * w + t];
+    __syncthreads();
+    for (int k = 0; k < n; k++) {
+        const int owner = k / rpc;
+        double *pk = pkb + (k & 1) * w;
+        if (me == owner) {
+            const double *row = R + (long)(k - base) * w;
+            const double piv = row[k];
+            for (int j = threadIdx.x; j < w; j += blockDim.x) pk[j] = row[j] / piv;
+        }
+        cl.sync();
+        const double *rpk = cl.map_shared_rank(pk, owner);
+        for (int j = threadIdx.x; j < w; j += blockDim.x) pkl[j] = rpk[j];
+        for (int r = threadIdx.x; r < nrows; r += blockDim.x) fcol[r] = R[(long)r * w + k];
+        __syncthreads();
+        for (int t = threadIdx.x; t < nrows * w; t += blockDim.x) {
+            const int r = t / w, j = t - r * w;
+            R[t] = (base + r == k) ? pkl[j] : R[t] - fcol[r] * pkl[j];
+        }
+        __syncthreads();
+    }
+    cl.sync();                                            // no CTA leaves while another may read its pivot rows
+    for (int t = threadIdx.x; t < nrows * n; t += blockDim.x) {
+        const int r = t / n, j = t - r * n;
+        inv[(long)(base + r) * n + j] = R[(long)r * w + n + j];
+    }
+}
+
+static size_t gj_dsmem_bytes(int n) {
+    const int w = 2 * n, rpc = (n + 7) / 8;
+    return sizeof(double) * ((size_t)rpc * w + 3 * (size_t)w + rpc);
 }
 
 __global__ void gj_init_kernel(Mat<double> A, double *__restrict__ aug) {
@@ -1456,14 +1515,23 @@ static sim_status finish_levels(sim_t *s) {
     if (!A0 || !A1) return s->err;
     gj_init_kernel<<<sim_blocks(n), SIM_THREADS, 0, s->stream>>>(level_mat(s, C, nl - 1), A0);
     s->launches++;
-    gj_cluster_kernel<<<8, 1024, 0, s->stream>>>(n, A0, A1);
-    s->launches++;
+    static bool dsmem_ok = cudaFuncSetAttribute(gj_dsmem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)gj_dsmem_bytes(kGjSmem)) == cudaSuccess;
+    const bool in_smem = dsmem_ok && n <= kGjSmem;
+    if (!in_smem) {
+        gj_cluster_kernel<<<8, 1024, 0, s->stream>>>(n, A0, A1);
+        s->launches++;
+    }
     // the coarsest inverse stays FP64 in both forms: the coarse matrices of
     // strongly heterogeneous fields are ill-conditioned, and the product is tiny
     C.coarse_inv = dev_alloc_async(s, sizeof(double) * (size_t)n * n);
     if (!C.coarse_inv) return s->err;
-    gj_extract_kernel<double><<<sim_blocks((long)n * n), SIM_THREADS, 0, s->stream>>>(n, (n & 1) ? A1 : A0,
-                                                                                    (double *)C.coarse_inv);
+    if (in_smem) {
+        gj_dsmem_kernel<<<8, 1024, gj_dsmem_bytes(n), s->stream>>>(n, A0, (double *)C.coarse_inv);
+    } else {
+        gj_extract_kernel<double><<<sim_blocks((long)n * n), SIM_THREADS, 0, s->stream>>>(n, (n & 1) ? A1 : A0,
+                                                                                        (double *)C.coarse_inv);
+    }
     s->launches++;
     dev_free_async(s, A0); dev_free_async(s, A1);
     SIM_CK(s, cudaGetLastError());

@@ -603,6 +603,39 @@ sim_status sim_spmv(sim_t *s, const double *x_dev, double *y_dev) {
     SIM_CK(s, cudaStreamSynchronize(s->stream));
     return SIM_OK;
 }
+sim_status sim_time_op(sim_t *s, int32_t which, int32_t reps, double *us) {
+    CHECK_HANDLE(s);
+    if (!us || reps < 1 || which < 0 || which > 1) return sim_fail(s, SIM_EINVAL, "sim_time_op: bad arguments");
+    const long n = (long)s->N * s->b;
+    if (which == 1 && !s->precond_ready && cpr_setup(s) != SIM_OK) return s->err;
+    // a buffer twice the L2 size, rewritten before every timed launch, so that
+    // each launch starts with its operands out of the cache
+    const size_t flush_bytes = 256u << 20;
+    void *flush = sim_alloc(s, flush_bytes);
+    if (!flush) return s->err;
+    SIM_CK(s, cudaMemsetAsync(s->V, 0, sizeof(double) * n, s->stream));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    sim_status st = SIM_OK;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = SIM_ECUDA;
+    double total_ms = 0.0;
+    for (int r = 0; r < reps && st == SIM_OK; r++) {
+        float ms = 0.f;
+        if (cudaMemsetAsync(flush, r & 0xff, flush_bytes, s->stream) != cudaSuccess ||
+            cudaEventRecord(e0, s->stream) != cudaSuccess) { st = SIM_ECUDA; break; }
+        st = which == 0 ? k_spmv(s, s->V, s->w) : cpr_apply(s, s->V, s->Z, nullptr);
+        if (st != SIM_OK) break;
+        if (cudaEventRecord(e1, s->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) { st = SIM_ECUDA; break; }
+        total_ms += ms;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    sim_free(s, flush);
+    if (st != SIM_OK) return s->err != SIM_OK ? s->err : sim_fail(s, SIM_ECUDA, "sim_time_op: event timing failed");
+    *us = 1e3 * total_ms / reps;
+    return SIM_OK;
+}
+
 sim_status sim_precond_setup(sim_t *s) {
     CHECK_HANDLE(s);
     if (cpr_setup(s) != SIM_OK) return s->err;

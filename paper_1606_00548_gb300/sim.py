@@ -125,6 +125,7 @@ _SIGS = {
     "sim_component_mass": ([_vp, _dp], C.c_int),
     "sim_cumulative_well_mass": ([_vp, _dp], C.c_int),
     "sim_well_rates": ([_vp, _dp], C.c_int),
+    "sim_time_op": ([_vp, C.c_int32, C.c_int32, _dp], C.c_int),
     "sim_perforations": ([_vp], C.c_int32),
     "sim_get_well_bhp": ([_vp, _dp], C.c_int),
     "sim_set_well_bhp": ([_vp, _dp], C.c_int),
@@ -445,6 +446,12 @@ class Simulator:
 
     def cumulative_well_mass(self):
         m = np.zeros(3); _check(self.h, self.L.sim_cumulative_well_mass(self.h, m.ctypes.data_as(_dp))); return m
+
+    def time_op(self, which, reps=20):
+        """Average device microseconds of `reps` back-to-back launches (0 SpMV, 1 CPR apply)."""
+        us = C.c_double()
+        _check(self.h, self.L.sim_time_op(self.h, int(which), int(reps), C.byref(us)))
+        return us.value
 
     def well_rates(self):
         q = np.zeros(3); _check(self.h, self.L.sim_well_rates(self.h, q.ctypes.data_as(_dp))); return q

@@ -343,3 +343,19 @@ def test_fused_coarse_cycle_matches_per_level_kernels(torch_cuda, precision):
         out.append(zd.cpu().numpy())
     tol = 1e-13 if precision == 0 else 1e-6
     assert rel_err(out[1], out[0]) <= tol
+
+
+def test_time_op_leaves_state_and_reports_time(torch_cuda):
+    """The measurement entry point times both operations without touching the
+    simulator's state (a later solve gives the same answer as before)."""
+    torch = torch_cuda
+    case = CASES["bo_ragged"]()
+    g, o = _loaded_pair(case, 10.0, None)
+    N, b = g.N, g.b
+    rhs = torch.tensor(np.random.default_rng(12).standard_normal(N * b), device="cuda", dtype=torch.float64)
+    x1 = torch.empty_like(rhs); x2 = torch.empty_like(rhs)
+    st, i1 = g.linear_solve(rhs, x1)
+    t_spmv, t_prec = g.time_op(0, 5), g.time_op(1, 5)
+    assert 0.0 < t_spmv < 1e5 and 0.0 < t_prec < 1e5
+    st, i2 = g.linear_solve(rhs, x2)
+    assert i1.iterations == i2.iterations and torch.equal(x1, x2)
