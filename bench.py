@@ -301,6 +301,7 @@ def run_ours(args):
     z = torch.empty_like(x)
     s0 = torch.cuda.Event(enable_timing=True); s1 = torch.cuda.Event(enable_timing=True)
     rhs = torch.randn(N * b, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()            # rhs is written on torch's stream, read on the library's
     with torch.cuda.stream(stream):
         s0.record(stream)
         _, li = sim.linear_solve(rhs, z)

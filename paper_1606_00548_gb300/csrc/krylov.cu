@@ -114,7 +114,7 @@ constexpr int NVMAX = SIM_MAX_M + 1;
 // h[k] = V_k . w, k < NV (NV exact: no predicated work for absent vectors),
 // and h[NV] = w . w (the norm the selective reorthogonalisation test needs)
 template <int NV>
-__global__ void __launch_bounds__(SIM_THREADS) dots_kernel(const double *__restrict__ V, const double *__restrict__ w,
+__global__ void __launch_bounds__(SIM_THREADS, 3) dots_kernel(const double *__restrict__ V, const double *__restrict__ w,
                                                            long n, double *partials, unsigned int *ticket,
                                                            double *out, const int *done) {
     if (skip(done)) return;
@@ -146,30 +146,55 @@ __device__ __forceinline__ bool need_reorth(const double *h, int nv, int selecti
 }
 
 // w -= sum_k h[k] V_k ; out[k] = V_k . w (second Gram-Schmidt pass); nothing
-// when the selective test finds no second pass is needed
+// when the selective test finds no second pass is needed.  A block takes
+// tiles of 128 elements: each thread updates one element, keeping the tile's
+// basis entries in shared memory, then thread (k, sub) accumulates
+// V_k . w over the tile's elements sub, sub + 4, ... (few registers, so
+// several blocks share an SM; rows padded to 132 doubles: conflict-free).
+constexpr int kOrthTile = 128, kOrthPad = 132;
+
 template <int NV>
-__global__ void __launch_bounds__(SIM_THREADS) orth_dots_kernel(const double *__restrict__ V, double *__restrict__ w,
-                                                                long n, const double *h, double *partials,
-                                                                unsigned int *ticket, double *out, const int *done,
-                                                                int selective) {
+__global__ void __launch_bounds__(kOrthTile) orth_dots_kernel(const double *__restrict__ V, double *__restrict__ w,
+                                                             long n, const double *h, double *partials,
+                                                             unsigned int *ticket, double *out, const int *done,
+                                                             int selective) {
     if (skip(done)) return;
     if (!need_reorth(h, NV, selective)) return;
-    double hs[NV];
+    __shared__ double sv[NV][kOrthPad];
+    __shared__ double sw[kOrthTile];
+    __shared__ double hs[NV];
+    for (int k = threadIdx.x; k < NV; k += blockDim.x) hs[k] = h[k];
+    __syncthreads();
+    const int kk = threadIdx.x >> 2, sub = threadIdx.x & 3;   // dot slot of this thread
+    double acc = 0.0;
+    for (long base = (long)blockIdx.x * kOrthTile; base < n; base += (long)gridDim.x * kOrthTile) {
+        const long i = base + threadIdx.x;
+        if (i < n) {
+            double wi = w[i];
 #pragma unroll
-    for (int k = 0; k < NV; k++) hs[k] = h[k];
-    double acc[NV];
+            for (int k = 0; k < NV; k++) {
+                const double v = V[k * n + i];
+                sv[k][threadIdx.x] = v;
+                wi -= hs[k] * v;
+            }
+            w[i] = wi;
+            sw[threadIdx.x] = wi;
+        } else {
 #pragma unroll
-    for (int k = 0; k < NV; k++) acc[k] = 0.0;
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-        double v[NV];
-        double wi = w[i];
-#pragma unroll
-        for (int k = 0; k < NV; k++) { v[k] = V[k * n + i]; wi -= hs[k] * v[k]; }
-        w[i] = wi;
-#pragma unroll
-        for (int k = 0; k < NV; k++) acc[k] += v[k] * wi;
+            for (int k = 0; k < NV; k++) sv[k][threadIdx.x] = 0.0;
+            sw[threadIdx.x] = 0.0;
+        }
+        __syncthreads();
+        if (kk < NV) {
+#pragma unroll 8
+            for (int e = sub; e < kOrthTile; e += 4) acc += sv[kk][e] * sw[e];
+        }
+        __syncthreads();
     }
-    block_partials<NV>(acc, NV, partials);
+    // the 4 threads of a slot are adjacent lanes: fold them, then one per slot writes
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    if (sub == 0 && kk < NV) partials[kk * gridDim.x + blockIdx.x] = acc;
     if (last_block(ticket)) {
         fold(partials, NV, out);
         if (threadIdx.x == 0) *ticket = 0u;
@@ -186,7 +211,8 @@ struct OrthDispatch {
     }
     static void orth(int nv, cudaStream_t st, const double *V, double *w, long n, const double *h, double *part,
                      unsigned int *tk, double *out, const int *done, int sel) {
-        if (nv == NV) orth_dots_kernel<NV><<<SIM_RED_BLOCKS, SIM_THREADS, 0, st>>>(V, w, n, h, part, tk, out, done, sel);
+        // 6 blocks of 128 threads per SM keep loads in flight while tiles are reduced
+        if (nv == NV) orth_dots_kernel<NV><<<2 * SIM_RED_BLOCKS, kOrthTile, 0, st>>>(V, w, n, h, part, tk, out, done, sel);
         else OrthDispatch<NV - 1>::orth(nv, st, V, w, n, h, part, tk, out, done, sel);
     }
 };

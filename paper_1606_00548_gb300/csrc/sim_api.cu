@@ -236,7 +236,7 @@ sim_status sim_create(const sim_grid *g, const sim_rock *r, const sim_fluid *f, 
     s->J = (double *)A(sizeof(double) * 7 * b * b * N);
     s->props = (double *)A(sizeof(double) * nq * (b + 1) * N);
     s->qtot = (double *)A(sizeof(double) * 4);
-    s->red = (double *)A(sizeof(double) * (SIM_MAX_M + 2) * SIM_RED_BLOCKS);
+    s->red = (double *)A(sizeof(double) * (SIM_MAX_M + 2) * 2 * SIM_RED_BLOCKS);   // orth_dots runs 2x the grid
     s->scal = (double *)A(sizeof(double) * 64);
     s->ticket = (unsigned int *)A(sizeof(unsigned int) * 4);
     s->V = (double *)A(sizeof(double) * (s->m + 1 > 5 ? s->m + 1 : 5) * n);   // BiCGSTAB keeps 5 vectors here

@@ -12,7 +12,7 @@
 #define SIM_MAX_PVT 64
 #define SIM_MAX_M 32
 #define SIM_MAX_ELL 512      // widest coarse AMG row: a wider Galerkin row stops coarsening
-#define SIM_RED_BLOCKS 608   // 4 x 152 SMs: grid of the reduction kernels
+#define SIM_RED_BLOCKS 456   // 3 x 152 SMs: grid of the reduction kernels (one wave at <= 85 registers)
 #define SIM_THREADS 256
 
 // fluid and rock constants, passed by value as a kernel parameter (about
