@@ -88,6 +88,7 @@ template <typename V>
 struct Mat {
     bool st;
     bool selfpad;    // ELL padded with (self column, 0) instead of -1: no early exit
+    bool diff;       // difference form: the diagonal slot holds the row sum (see row_dot)
     GridDesc g;      // structured
     const V *val;    // structured: [7][n]; ELL: [width][n]
     const int *col;  // ELL
@@ -119,6 +120,23 @@ __device__ __forceinline__ void for_row(const Mat<V> &A, int i, F f) {
             f(j, A.val[(long)k * A.n + i]);
         }
     }
+}
+
+// A_i . e.  In the difference form (the FP32 copies of the pressure matrices)
+// the diagonal slot holds the row sum d_i = sum_j a_ij, computed in FP64, and
+// A_i . e = d_i e_i + sum_{j != i} a_ij (e_j - e_i): the small row sum (the
+// accumulation term, 1e-4 to 1e-7 of the off-diagonals where permeability is
+// high) survives rounding to FP32, where a_ii + sum_{j != i} a_ij would lose it.
+template <typename T>
+__device__ __forceinline__ T row_dot(const Mat<T> &A, int i, const T *__restrict__ e) {
+    T t = (T)0;
+    if (A.diff) {
+        const T ei = e[i];
+        for_row(A, i, [&](int j, T v) { t += (j == i) ? v * ei : v * (e[j] - ei); });
+    } else {
+        for_row(A, i, [&](int j, T v) { t += v * e[j]; });
+    }
+    return t;
 }
 
 __global__ void selfpad_kernel(int n, int W, const int *__restrict__ col, int *__restrict__ colA) {
@@ -256,6 +274,7 @@ __global__ void qi_kernel(GridDesc g, const double *__restrict__ J, WellCorr wc,
 #pragma unroll
     for (int c = 0; c < B; c++) { qiw[(long)c * N + i] = L[c]; qiwT[(long)c * N + i] = (T)L[c]; }
     const Cell cc = cell_of(g, i);
+    double rsum = 0.0;                   // FP32 copy: row sum of A_p on the diagonal slot (difference form)
     for (int d = 0; d < 7; d++) {
         double A[B * B];
         const int j = nbrc(g, cc, d);
@@ -263,9 +282,11 @@ __global__ void qi_kernel(GridDesc g, const double *__restrict__ J, WellCorr wc,
         const bool has = j >= 0;
         ap[(long)d * N + i] = has ? A[0] : 0.0;
         apT[(long)d * N + i] = has ? (T)A[0] : (T)0;
+        if (sizeof(T) == sizeof(float) && has) rsum += A[0];
 #pragma unroll
         for (int t = 0; t < B * B; t++) ahat[(long)(d * B * B + t) * N + i] = (T)A[t];
     }
+    if (sizeof(T) == sizeof(float)) apT[i] = (T)rsum;
 }
 
 // ---------------------------------------------------------------------------
@@ -352,6 +373,25 @@ __global__ void ilu_black_kernel(GridDesc g, const double *__restrict__ J, WellC
     inv_block<B>(D, Di);
 #pragma unroll
     for (int t = 0; t < B * B; t++) dinv[(long)t * N + i] = Di[t];
+}
+
+// FP32 copy of an ELL level in the difference form: the diagonal entry is
+// replaced by the row sum (computed in FP64), the others rounded as they are
+__global__ void cast_diff_kernel(int n, int W, const int *__restrict__ col, const double *__restrict__ val,
+                                 float *__restrict__ valT) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double rs = 0.0;
+    for (int k = 0; k < W; k++) {
+        const int j = col[(long)k * n + i];
+        if (j < 0) break;
+        rs += val[(long)k * n + i];
+    }
+    for (int k = 0; k < W; k++) {
+        const long t = (long)k * n + i;
+        const int j = col[t];
+        valT[t] = j == i ? (float)rs : (float)val[t];
+    }
 }
 
 template <typename T>
@@ -841,9 +881,7 @@ __global__ void amg_resid_kernel(Mat<T> A, const T *__restrict__ f, const T *__r
     if (skip(done)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= A.n) return;
-    T t = (T)0;
-    for_row(A, i, [&](int j, T v) { t += v * e[j]; });
-    r[i] = f[i] - t;
+    r[i] = f[i] - row_dot(A, i, e);
 }
 
 // f_c = P^T r (members in ascending order); e_c = f_c / l1 (coarse pre-smoothing)
@@ -876,9 +914,7 @@ __global__ void amg_smooth_kernel(Mat<T> A, const T *__restrict__ f, const T *__
     if (skip(done)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= A.n) return;
-    T t = (T)0;
-    for_row(A, i, [&](int j, T v) { t += v * e[j]; });
-    e2[i] = e[i] + (f[i] - t) * dinv[i];
+    e2[i] = e[i] + (f[i] - row_dot(A, i, e)) * dinv[i];
 }
 
 // next stage-P cycle: f0 = rp - A_p ep; e0 = f0 / l1
@@ -888,9 +924,7 @@ __global__ void cycle_next_kernel(Mat<T> A, const T *__restrict__ rp, const T *_
     if (skip(done)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= A.n) return;
-    T t = (T)0;
-    for_row(A, i, [&](int j, T v) { t += v * ep[j]; });
-    const T f = rp[i] - t;
+    const T f = rp[i] - row_dot(A, i, ep);
     f0[i] = f;
     e0[i] = f * dinv[i];
 }
@@ -926,7 +960,7 @@ constexpr int kCoarseMaxLevels = 24;
 
 template <typename T>
 struct CoarseLevel {
-    int n, width;
+    int n, width, diff;
     const int *colA;     // self-padded ELL columns [width][n]
     const T *val;        // [width][n]
     const T *dinv;       // 1 / l1 row sums
@@ -945,6 +979,16 @@ struct CoarseCycle {
 template <typename T>
 __device__ __forceinline__ T ell_dot(const CoarseLevel<T> &L, int i, const T *__restrict__ e) {
     T t = (T)0;
+    if (L.diff) {                                  // difference form (see row_dot)
+        const T ei = e[i];
+#pragma unroll 4
+        for (int k = 0; k < L.width; k++) {
+            const int j = L.colA[(long)k * L.n + i];
+            const T v = L.val[(long)k * L.n + i];
+            t += (j == i) ? v * ei : v * (e[j] - ei);
+        }
+        return t;
+    }
 #pragma unroll 4
     for (int k = 0; k < L.width; k++) t += L.val[(long)k * L.n + i] * e[L.colA[(long)k * L.n + i]];
     return t;
@@ -1263,7 +1307,11 @@ __global__ void learned_apply_kernel(Mat<T> A, const float *__restrict__ y, cons
     if (i >= A.n) return;
     const double sc = *rms;
     T t = (T)0;
-    for_row(A, i, [&](int j, T v) { t += v * (T)((double)y[j] * sc); });
+    const T yi = (T)((double)y[i] * sc);
+    for_row(A, i, [&](int j, T v) {
+        const T yj = (T)((double)y[j] * sc);
+        t += A.diff ? ((j == i) ? v * yi : v * (yj - yi)) : v * yj;
+    });
     q[i] = t;
 }
 
@@ -1380,7 +1428,7 @@ void cpr_free(sim_t *s) {
 
 static Mat<double> level_mat(sim_t *s, const AmgLevel &L, int l) {
     Mat<double> A;
-    A.st = (l == 0); A.selfpad = false; A.g = s->gd; A.n = L.n; A.width = L.width;
+    A.st = (l == 0); A.selfpad = false; A.diff = false; A.g = s->gd; A.n = L.n; A.width = L.width;
     A.val = l == 0 ? s->ap : L.val;
     A.col = L.col;
     return A;
@@ -1388,7 +1436,7 @@ static Mat<double> level_mat(sim_t *s, const AmgLevel &L, int l) {
 template <typename T>
 static Mat<T> level_matT(sim_t *s, const AmgLevel &L, int l) {
     Mat<T> A;
-    A.st = (l == 0); A.selfpad = true; A.g = s->gd; A.n = L.n; A.width = L.width;
+    A.st = (l == 0); A.selfpad = true; A.diff = sizeof(T) == sizeof(float); A.g = s->gd; A.n = L.n; A.width = L.width;
     A.val = (const T *)L.valT;
     A.col = L.colA;
     return A;
@@ -1501,7 +1549,8 @@ static sim_status finish_levels(sim_t *s) {
             } else {
                 L.valT = dev_alloc_async(s, sizeof(T) * (size_t)L.width * L.n);
                 if (!L.valT) return s->err;
-                cast_kernel<T><<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(L.val, (T *)L.valT, (long)L.width * L.n);
+                cast_diff_kernel<<<sim_blocks(L.n), SIM_THREADS, 0, s->stream>>>(L.n, L.width, L.col, L.val,
+                                                                                (float *)L.valT);
                 s->launches++;
             }
         }
@@ -1556,7 +1605,7 @@ static sim_status amg_setup(sim_t *s) {
         const int W1 = galerkin(s, A, s->aggA, s->moffA, s->memA, n1, &c1, &v1);
         if (W1 < 0) return s->err;
         if (W1 == 0) break;   // a coarse row wider than SIM_MAX_ELL: this level is the coarsest
-        Mat<double> A1; A1.st = false; A1.selfpad = false; A1.g = s->gd; A1.n = n1; A1.width = W1; A1.col = c1; A1.val = v1;
+        Mat<double> A1; A1.st = false; A1.selfpad = false; A1.diff = false; A1.g = s->gd; A1.n = n1; A1.width = W1; A1.col = c1; A1.val = v1;
         const int n2 = aggregate_pass(s, A1, s->aggB, s->moffB, s->memB);
         if (n2 < 0) return s->err;
         if (4L * n2 > 3L * n) {   // coarsening stalled: this level is the coarsest
@@ -1652,7 +1701,8 @@ static sim_status coarse_cycle(sim_t *s, int l0, const int *done) {
     for (int l = l0; l < nl; l++) {
         const AmgLevel &L = s->lev[l];
         CoarseLevel<T> &d = cc.lv[l - l0];
-        d.n = L.n; d.width = L.width; d.colA = L.colA; d.val = (const T *)L.valT; d.dinv = (const T *)L.dinvT;
+        d.n = L.n; d.width = L.width; d.diff = sizeof(T) == sizeof(float); d.colA = L.colA; d.val = (const T *)L.valT;
+        d.dinv = (const T *)L.dinvT;
         d.agg = L.agg; d.moff = L.moff; d.mem = L.mem;
         d.f = (T *)L.f; d.e = (T *)L.e; d.e2 = (T *)L.e2;
     }
