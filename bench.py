@@ -438,8 +438,9 @@ def run_ensemble(args):
 
 def run_learned(args):
     """Second metric: CPR-FGMRES time to 1e-8 relative residual on the 256x256x64
-    black-oil system (sigma 2), FP64 CPR vs FP32 CPR vs FP32 CPR + learned stage
-    (network trained on the device on 128x128x32 systems)."""
+    black-oil system (sigma 2): FP64 CPR and FP32-preconditioned CPR (two-stage
+    and CPR-FPF), and FP32 CPR + learned stage (network trained on the device on
+    128x128x32 systems).  value = the learned form's time."""
     import torch
     from paper_1606_00548_gb300 import build, learned
     build.build()

@@ -209,6 +209,8 @@ struct OrthDispatch {
         if (nv == NV) dots_kernel<NV><<<SIM_RED_BLOCKS, SIM_THREADS, 0, st>>>(V, w, n, part, tk, out, done);
         else OrthDispatch<NV - 1>::dots(nv, st, V, w, n, part, tk, out, done);
     }
+    static void norm(int nv, cudaStream_t st, const double *V, double *w, long n, int m, double *part, unsigned int *tk,
+                     KrylovCtl *ctl, int sel);
     static void orth(int nv, cudaStream_t st, const double *V, double *w, long n, const double *h, double *part,
                      unsigned int *tk, double *out, const int *done, int sel) {
         // 6 blocks of 128 threads per SM keep loads in flight while tiles are reduced
@@ -222,14 +224,19 @@ struct OrthDispatch<0> {
                      const int *) {}
     static void orth(int, cudaStream_t, const double *, double *, long, const double *, double *, unsigned int *,
                      double *, const int *, int) {}
+    static void norm(int, cudaStream_t, const double *, double *, long, int, double *, unsigned int *, KrylovCtl *,
+                     int) {}
 };
 
 // w -= sum_k h2[k] V_k ; ||w||; last block: Hessenberg column j, Givens, test
-__global__ void __launch_bounds__(SIM_THREADS) orth_norm_kernel(const double *__restrict__ V, double *__restrict__ w,
+// (NV = j + 1 at compile time: the NV basis loads of an element are unrolled
+// and in flight together)
+template <int NV>
+__global__ void __launch_bounds__(SIM_THREADS, 3) orth_norm_kernel(const double *__restrict__ V, double *__restrict__ w,
                                                                 long n, int j, int m, double *partials,
                                                                 unsigned int *ticket, KrylovCtl *ctl, int selective) {
     if (ctl->done) return;
-    const int nv = j + 1;
+    const int nv = NV;
     const bool re = need_reorth(ctl->h, nv, selective);   // else the first pass is subtracted here
     __shared__ double hs[NVMAX];
     for (int k = threadIdx.x; k < nv; k += blockDim.x) hs[k] = re ? ctl->h2[k] : ctl->h[k];
@@ -237,7 +244,8 @@ __global__ void __launch_bounds__(SIM_THREADS) orth_norm_kernel(const double *__
     double acc[1] = {0.0};
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
         double wi = w[i];
-        for (int k = 0; k < nv; k++) wi -= hs[k] * V[k * n + i];
+#pragma unroll
+        for (int k = 0; k < NV; k++) wi -= hs[k] * V[k * n + i];
         w[i] = wi;
         acc[0] += wi * wi;
     }
@@ -271,6 +279,13 @@ __global__ void __launch_bounds__(SIM_THREADS) orth_norm_kernel(const double *__
             if (fabs(ctl->g[j + 1]) <= ctl->tol || j + 1 >= m) ctl->done = 1;
         }
     }
+}
+
+template <int NV>
+void OrthDispatch<NV>::norm(int nv, cudaStream_t st, const double *V, double *w, long n, int m, double *part,
+                            unsigned int *tk, KrylovCtl *ctl, int sel) {
+    if (nv == NV) orth_norm_kernel<NV><<<SIM_RED_BLOCKS, SIM_THREADS, 0, st>>>(V, w, n, NV - 1, m, part, tk, ctl, sel);
+    else OrthDispatch<NV - 1>::norm(nv, st, V, w, n, m, part, tk, ctl, sel);
 }
 
 // v = w / scale (scale = ctl->rnorm2 inside a cycle, ctl->beta at a restart)
@@ -591,8 +606,7 @@ static sim_status enqueue_cycle(sim_t *s) {
         OrthDispatch<SIM_MAX_M>::orth(j + 1, s->stream, s->V, s->w, n, ctl->h, s->red, s->ticket, ctl->h2, done,
                                       s->opt.orth);
         SIM_LAUNCHED(s);
-        orth_norm_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(s->V, s->w, n, j, m, s->red, s->ticket, ctl,
-                                                                        s->opt.orth);
+        OrthDispatch<SIM_MAX_M>::norm(j + 1, s->stream, s->V, s->w, n, m, s->red, s->ticket, ctl, s->opt.orth);
         SIM_LAUNCHED(s);
         scale_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(s->w, s->V + (size_t)(j + 1) * n, n, ctl, 0);
         SIM_LAUNCHED(s);

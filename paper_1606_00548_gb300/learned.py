@@ -60,11 +60,11 @@ def train(net, X, Y, steps=300, lr=1e-3, seed=0):
     return hist
 
 
-def time_solve(case, precision, net=None, repeats=1):
+def time_solve(case, precision, net=None, repeats=1, **solver):
     """Time of the first Newton system's CPR-FGMRES solve to the tolerance
-    (setup included), and its iterations."""
+    (setup included), and its iterations; solver overrides the case's options."""
     import torch
-    sim = Simulator(case, precision=precision)
+    sim = Simulator(case, precision=precision, **solver)
     if net is not None:
         sim.set_learned_stage(net, True)
     dt = case["dt"][0]
@@ -89,8 +89,9 @@ def time_solve(case, precision, net=None, repeats=1):
 
 
 def evaluate(train_case=None, eval_case=None, train_steps=300, lr=1e-3, pairs_newton=4, pairs_k=16, seed=0):
-    """Train on train_case, then compare solves on eval_case: FP64 CPR, FP32
-    CPR, FP32 CPR + learned stage (all to the same FP64 tolerance)."""
+    """Train on train_case, then compare solves on eval_case: FP64 CPR
+    (two-stage and CPR-FPF), FP32-preconditioned CPR (both), FP32 CPR + the
+    learned stage (all to the same FP64 tolerance)."""
     train_case = train_case or synth.black_oil_case(nx=128, ny=128, nz=32, sigma=1.0, corr_len=10.0, seed=1004)
     eval_case = eval_case or synth.black_oil_case(nx=256, ny=256, nz=64, sigma=2.0, corr_len=20.0, seed=1005)
     t0 = time.perf_counter()
@@ -107,7 +108,9 @@ def evaluate(train_case=None, eval_case=None, train_steps=300, lr=1e-3, pairs_ne
     net_e.set_params(params)
     res = {
         "fp64_cpr": time_solve(eval_case, 0),
+        "fp64_cpr_fpf": time_solve(eval_case, 0, cpr_stages=3),
         "mixed_cpr": time_solve(eval_case, 1),
+        "mixed_cpr_fpf": time_solve(eval_case, 1, cpr_stages=3),
         "mixed_cpr_learned": time_solve(eval_case, 1, net=net_e),
     }
     net_e.close()

@@ -155,7 +155,7 @@ def test_learned_stage_gain_is_measured(torch_cuda, capsys):
     ec = synth.black_oil_case(nx=48, ny=40, nz=12, sigma=2.0, corr_len=8.0, seed=52)
     ev = learned.evaluate(tc, ec, train_steps=80, pairs_newton=3, pairs_k=12)
     r = ev["results"]
-    for k in ("fp64_cpr", "mixed_cpr", "mixed_cpr_learned"):
+    for k in ("fp64_cpr", "fp64_cpr_fpf", "mixed_cpr", "mixed_cpr_fpf", "mixed_cpr_learned"):
         assert r[k]["converged"] and r[k]["rel_residual"] <= 1e-8, (k, r[k])
     assert ev["train_loss"][-1][1] < ev["train_loss"][0][1]
     with capsys.disabled():
