@@ -790,47 +790,87 @@ gj_cluster_kernel(int n, double *__restrict__ A0, double *__restrict__ A1) {
 }
 
 // The same elimination with the augmented matrix held in the shared memory of
-// the 8 CTAs of a cluster (n <= kGjSmem): CTA c owns a block of rows; step k's
-// owner divides pivot row k into its pivot buffer (double-buffered by step
-// parity), one cluster barrier publishes it, every CTA reads it through
-// distributed shared memory and updates its own rows.  The result (right half)
-// is written to inv; the arithmetic per entry is that of gj_cluster_kernel.
-constexpr int kGjSmem = 256;
+// the 8 CTAs of a cluster (n <= kGjSmem), kGjPanel pivots at a time: CTA c
+// owns a block of rows; for each panel of up to kGjPanel consecutive pivot
+// rows (all in one CTA) the owner reduces the panel to the identity on its
+// pivot columns (Gauss-Jordan within the panel), one cluster barrier
+// publishes it (double-buffered by panel parity), and every CTA reads it
+// through distributed shared memory and subtracts, from each of its other
+// rows, the panel rows times that row's entries in the pivot columns.  In
+// exact arithmetic this is the pivot-by-pivot elimination; it needs one
+// cluster barrier per panel instead of one per pivot.  The right half of the
+// result is written to inv.
+constexpr int kGjSmem = 256, kGjPanel = 4;
 
 __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(1024, 1)
 gj_dsmem_kernel(int n, const double *__restrict__ aug, double *__restrict__ inv) {
     extern __shared__ double gsm[];
     cg::cluster_group cl = cg::this_cluster();
     const int w = 2 * n, rpc = (n + 7) / 8;               // rows per CTA
-    const int me = (int)cl.block_rank();
+    const int me = (int)cl.block_rank(), tid = threadIdx.x, bd = blockDim.x;
     double *R = gsm;                                      // [rpc][w] own rows
-    double *pkb = gsm + (long)rpc * w;                    // [2][w] pivot rows (by step parity)
-    double *pkl = pkb + 2 * w;                            // [w] local copy of the current pivot row
-    double *fcol = pkl + w;                               // [rpc] column-k entries of own rows
+    double *P = R + (long)rpc * w;                        // [2][kGjPanel][w] panels (by panel parity)
+    double *PL = P + 2L * kGjPanel * w;                   // [kGjPanel][w] local copy of the current panel
+    double *F = PL + (long)kGjPanel * w;                  // [rpc][kGjPanel] own rows' pivot-column entries
     const int base = me * rpc, nrows = max(0, min(rpc, n - base));
-    for (int t = threadIdx.x; t < nrows * w; t += blockDim.x) R[t] = aug[(long)base * w + t];
+    for (int t = tid; t < nrows * w; t += bd) R[t] = aug[(long)base * w + t];
     __syncthreads();
-    for (int k = 0; k < n; k++) {
-        const int owner = k / rpc;
-        double *pk = pkb + (k & 1) * w;
-        if (me == owner) {
-            const double *row = R + (long)(k - base) * w;
-            const double piv = row[k];
-            for (int j = threadIdx.x; j < w; j += blockDim.x) pk[j] = row[j] / piv;
+    int panel = 0;
+    for (int c = 0; c < 8; c++) {
+        const int cb = c * rpc, cn = max(0, min(rpc, n - cb));
+        for (int k0 = cb; k0 < cb + cn; k0 += kGjPanel, panel++) {
+            const int ps = min(kGjPanel, cb + cn - k0);
+            double *Pb = P + (long)(panel & 1) * kGjPanel * w;
+            // the panel rows are zero outside columns [k0, n + k0 + ps) (left of k0
+            // eliminated, right of n + k0 + ps still the untouched identity), so only
+            // that window of width n + ps changes: half the FP64 work of the full 2n
+            const int j0 = k0, wa = n + ps;
+            if (me == c) {
+                for (int t = tid; t < ps * w; t += bd) Pb[t] = R[(long)(k0 - base) * w + t];
+                __syncthreads();
+                for (int q = 0; q < ps; q++) {
+                    const double piv = Pb[(long)q * w + k0 + q];
+                    __syncthreads();
+                    for (int j = j0 + tid; j < j0 + wa; j += bd) Pb[(long)q * w + j] = Pb[(long)q * w + j] / piv;
+                    __syncthreads();
+                    double fu[kGjPanel];
+#pragma unroll
+                    for (int u = 0; u < kGjPanel; u++) fu[u] = u < ps ? Pb[(long)u * w + k0 + q] : 0.0;
+                    __syncthreads();
+                    for (int t = tid; t < ps * wa; t += bd) {
+                        const int u = t / wa, j = j0 + (t - u * wa);
+                        if (u != q) Pb[(long)u * w + j] = Pb[(long)u * w + j] - fu[u] * Pb[(long)q * w + j];
+                    }
+                    __syncthreads();
+                }
+            }
+            cl.sync();
+            const double *rP = cl.map_shared_rank(Pb, c);
+            for (int t = tid; t < ps * wa; t += bd) {
+                const int u = t / wa, j = j0 + (t - u * wa);
+                PL[(long)u * w + j] = rP[(long)u * w + j];
+            }
+            for (int t = tid; t < nrows * ps; t += bd) {
+                const int r = t / ps, u = t - r * ps;
+                F[r * kGjPanel + u] = R[(long)r * w + k0 + u];
+            }
+            __syncthreads();
+            for (int t = tid; t < nrows * wa; t += bd) {
+                const int r = t / wa, j = j0 + (t - r * wa), gi = base + r;
+                double *Rr = R + (long)r * w + j;
+                if (gi >= k0 && gi < k0 + ps) {
+                    *Rr = PL[(long)(gi - k0) * w + j];
+                } else {
+                    double v = *Rr;
+                    for (int u = 0; u < ps; u++) v -= F[r * kGjPanel + u] * PL[(long)u * w + j];
+                    *Rr = v;
+                }
+            }
+            __syncthreads();
         }
-        cl.sync();
-        const double *rpk = cl.map_shared_rank(pk, owner);
-        for (int j = threadIdx.x; j < w; j += blockDim.x) pkl[j] = rpk[j];
-        for (int r = threadIdx.x; r < nrows; r += blockDim.x) fcol[r] = R[(long)r * w + k];
-        __syncthreads();
-        for (int t = threadIdx.x; t < nrows * w; t += blockDim.x) {
-            const int r = t / w, j = t - r * w;
-            R[t] = (base + r == k) ? pkl[j] : R[t] - fcol[r] * pkl[j];
-        }
-        __syncthreads();
     }
-    cl.sync();                                            // no CTA leaves while another may read its pivot rows
-    for (int t = threadIdx.x; t < nrows * n; t += blockDim.x) {
+    cl.sync();                                            // no CTA leaves while another may read its panels
+    for (int t = tid; t < nrows * n; t += bd) {
         const int r = t / n, j = t - r * n;
         inv[(long)(base + r) * n + j] = R[(long)r * w + n + j];
     }
@@ -838,7 +878,7 @@ gj_dsmem_kernel(int n, const double *__restrict__ aug, double *__restrict__ inv)
 
 static size_t gj_dsmem_bytes(int n) {
     const int w = 2 * n, rpc = (n + 7) / 8;
-    return sizeof(double) * ((size_t)rpc * w + 3 * (size_t)w + rpc);
+    return sizeof(double) * ((size_t)rpc * w + 3 * (size_t)kGjPanel * w + (size_t)rpc * kGjPanel);
 }
 
 __global__ void gj_init_kernel(Mat<double> A, double *__restrict__ aug) {
