@@ -583,14 +583,6 @@ __global__ void sort_members_kernel(int nc, const int *__restrict__ moff, int *_
     }
 }
 
-// entries of the members' rows of coarse row I (the list the Galerkin sum runs over)
-__device__ __forceinline__ int galerkin_list_len(const Mat<double> &A, const int *__restrict__ moff,
-                                                 const int *__restrict__ mem, int I) {
-    int L = 0;
-    for (int q = moff[I]; q < moff[I + 1]; q++) for_row(A, mem[q], [&](int, double) { L++; });
-    return L;
-}
-
 // Galerkin row I of P^T A P, one warp per row.  The members' row entries,
 // mapped to aggregate columns, are staged in member-then-column order (the
 // order of the sequential definition); each distinct column sums its entries
@@ -659,7 +651,10 @@ __global__ void __launch_bounds__(kGalWarps * 32) galerkin_warp_kernel(
             }
         }
     }
-    if (over) return;                             // galerkin_kernel takes this row
+    if (over) {                                   // galerkin_kernel takes this row
+        if (mode == 0 && lane == 0) len[I] = -1;
+        return;
+    }
     __syncwarp();
     // 2. first occurrences, their count, their ordered sums and ranks
     int D = 0;
@@ -706,7 +701,9 @@ __global__ void galerkin_kernel(Mat<double> A, const int *__restrict__ agg, cons
                                 int *__restrict__ ccol, double *__restrict__ cval, int *err) {
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nc) return;
-    if (galerkin_list_len(A, moff, mem, I) <= kGalCap) return;   // done by galerkin_warp_kernel
+    // rows the warp kernel left: len = -1 after its counting pass; this kernel
+    // then stores -(count) - 2, so the filling pass finds the same rows
+    if (mode == 0 ? len[I] != -1 : len[I] >= 0) return;
     int cols[MAXE];
     double vals[MAXE];
     int cnt = 0;
@@ -732,7 +729,7 @@ __global__ void galerkin_kernel(Mat<double> A, const int *__restrict__ agg, cons
         while (t >= 0 && cols[t] > cj) { cols[t + 1] = cols[t]; vals[t + 1] = vals[t]; t--; }
         cols[t + 1] = cj; vals[t + 1] = cv;
     }
-    if (mode == 0) { len[I] = cnt; atomicMax(len + nc, cnt); return; }
+    if (mode == 0) { len[I] = -cnt - 2; atomicMax(len + nc, cnt); return; }
     for (int t = 0; t < W; t++) {
         ccol[(long)t * nc + I] = t < cnt ? cols[t] : -1;
         cval[(long)t * nc + I] = t < cnt ? vals[t] : 0.0;
