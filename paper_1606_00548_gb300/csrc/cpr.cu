@@ -114,10 +114,13 @@ __device__ __forceinline__ void for_row(const Mat<V> &A, int i, F f) {
 #pragma unroll 4
         for (int k = 0; k < A.width; k++) f(A.col[(long)k * A.n + i], A.val[(long)k * A.n + i]);
     } else {
+        // -1 padding sits only at the end of a row: skipping it instead of
+        // stopping there visits the same entries in the same order, and the
+        // column loads no longer wait on one another
+#pragma unroll 4
         for (int k = 0; k < A.width; k++) {
             const int j = A.col[(long)k * A.n + i];
-            if (j < 0) break;
-            f(j, A.val[(long)k * A.n + i]);
+            if (j >= 0) f(j, A.val[(long)k * A.n + i]);
         }
     }
 }
@@ -787,7 +790,8 @@ gj_cluster_kernel(int n, double *__restrict__ A0, double *__restrict__ A1) {
 }
 
 // The same elimination with the augmented matrix held in the shared memory of
-// the 8 CTAs of a cluster (n <= kGjSmem), kGjPanel pivots at a time: CTA c
+// the CTAs of one cluster (8, or 16 where the part schedules a cluster that
+// large; n <= kGjSmem), kGjPanel pivots at a time: CTA c
 // owns a block of rows; for each panel of up to kGjPanel consecutive pivot
 // rows (all in one CTA) the owner reduces the panel to the identity on its
 // pivot columns (Gauss-Jordan within the panel), one cluster barrier
@@ -799,11 +803,11 @@ gj_cluster_kernel(int n, double *__restrict__ A0, double *__restrict__ A1) {
 // result is written to inv.
 constexpr int kGjSmem = 256, kGjPanel = 4;
 
-__global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(1024, 1)
+__global__ void __launch_bounds__(1024, 1)
 gj_dsmem_kernel(int n, const double *__restrict__ aug, double *__restrict__ inv) {
     extern __shared__ double gsm[];
     cg::cluster_group cl = cg::this_cluster();
-    const int w = 2 * n, rpc = (n + 7) / 8;               // rows per CTA
+    const int nc = (int)cl.num_blocks(), w = 2 * n, rpc = (n + nc - 1) / nc;   // rows per CTA
     const int me = (int)cl.block_rank(), tid = threadIdx.x, bd = blockDim.x;
     double *R = gsm;                                      // [rpc][w] own rows
     double *P = R + (long)rpc * w;                        // [2][kGjPanel][w] panels (by panel parity)
@@ -813,7 +817,7 @@ gj_dsmem_kernel(int n, const double *__restrict__ aug, double *__restrict__ inv)
     for (int t = tid; t < nrows * w; t += bd) R[t] = aug[(long)base * w + t];
     __syncthreads();
     int panel = 0;
-    for (int c = 0; c < 8; c++) {
+    for (int c = 0; c < nc; c++) {
         const int cb = c * rpc, cn = max(0, min(rpc, n - cb));
         for (int k0 = cb; k0 < cb + cn; k0 += kGjPanel, panel++) {
             const int ps = min(kGjPanel, cb + cn - k0);
@@ -873,17 +877,42 @@ gj_dsmem_kernel(int n, const double *__restrict__ aug, double *__restrict__ inv)
     }
 }
 
-static size_t gj_dsmem_bytes(int n) {
-    const int w = 2 * n, rpc = (n + 7) / 8;
+static size_t gj_dsmem_bytes(int n, int nc) {
+    const int w = 2 * n, rpc = (n + nc - 1) / nc;
     return sizeof(double) * ((size_t)rpc * w + 3 * (size_t)kGjPanel * w + (size_t)rpc * kGjPanel);
 }
 
+// [A | I], one thread per entry (row i, column j of the n x 2n array)
+// CTAs of the Gauss-Jordan cluster: 16 (a non-portable size) when the
+// occupancy query finds room for one such cluster at the largest shared-memory
+// size, else the portable 8; the query launches nothing
+static int gj_cluster_ctas() {
+    if (cudaFuncSetAttribute(gj_dsmem_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 8;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 16; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(16); cfg.blockDim = dim3(1024); cfg.dynamicSmemBytes = gj_dsmem_bytes(kGjSmem, 16);
+    cfg.attrs = at; cfg.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, gj_dsmem_kernel, &cfg) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 8;
+    }
+    return clusters > 0 ? 16 : 8;
+}
+
 __global__ void gj_init_kernel(Mat<double> A, double *__restrict__ aug) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= A.n) return;
     const long w = 2L * A.n;
-    for (int j = 0; j < 2 * A.n; j++) aug[i * w + j] = (j - A.n == i) ? 1.0 : 0.0;
-    for_row(A, i, [&](int j, double a) { aug[i * w + j] += a; });
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= (long)A.n * w) return;
+    const int i = (int)(t / w), j = (int)(t - (long)i * w);
+    double v = (j - A.n == i) ? 1.0 : 0.0;
+    if (j < A.n) for_row(A, i, [&](int c, double a) { if (c == j) v += a; });
+    aug[t] = v;
 }
 
 template <typename T>
@@ -1599,10 +1628,11 @@ static sim_status finish_levels(sim_t *s) {
     double *A0 = (double *)dev_alloc_async(s, sizeof(double) * aug);
     double *A1 = (double *)dev_alloc_async(s, sizeof(double) * aug);
     if (!A0 || !A1) return s->err;
-    gj_init_kernel<<<sim_blocks(n), SIM_THREADS, 0, s->stream>>>(level_mat(s, C, nl - 1), A0);
+    gj_init_kernel<<<sim_blocks(2L * n * n), SIM_THREADS, 0, s->stream>>>(level_mat(s, C, nl - 1), A0);
     s->launches++;
     static bool dsmem_ok = cudaFuncSetAttribute(gj_dsmem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)gj_dsmem_bytes(kGjSmem)) == cudaSuccess;
+                                                (int)gj_dsmem_bytes(kGjSmem, 8)) == cudaSuccess;
+    static int gj_ctas = gj_cluster_ctas();
     const bool in_smem = dsmem_ok && n <= kGjSmem;
     if (!in_smem) {
         gj_cluster_kernel<<<8, 1024, 0, s->stream>>>(n, A0, A1);
@@ -1613,7 +1643,15 @@ static sim_status finish_levels(sim_t *s) {
     C.coarse_inv = dev_alloc_async(s, sizeof(double) * (size_t)n * n);
     if (!C.coarse_inv) return s->err;
     if (in_smem) {
-        gj_dsmem_kernel<<<8, 1024, gj_dsmem_bytes(n), s->stream>>>(n, A0, (double *)C.coarse_inv);
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = gj_ctas; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(gj_ctas); cfg.blockDim = dim3(1024); cfg.dynamicSmemBytes = gj_dsmem_bytes(n, gj_ctas);
+        cfg.stream = s->stream; cfg.attrs = at; cfg.numAttrs = 1;
+        if (!sim_cuda_ok(s, cudaLaunchKernelEx(&cfg, gj_dsmem_kernel, n, (const double *)A0, (double *)C.coarse_inv),
+                         "coarsest inverse"))
+            return s->err;
     } else {
         gj_extract_kernel<double><<<sim_blocks((long)n * n), SIM_THREADS, 0, s->stream>>>(n, (n & 1) ? A1 : A0,
                                                                                         (double *)C.coarse_inv);
