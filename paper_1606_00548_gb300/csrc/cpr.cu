@@ -1069,13 +1069,18 @@ template <typename T>
 __global__ void __cluster_dims__(kCoarseCtas, 1, 1) __launch_bounds__(kCoarseThreads, 1)
 coarse_cycle_kernel(const CoarseCycle<T> cc, const int *done) {
     if (skip(done)) return;            // uniform over the cluster: no thread reaches a barrier alone
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    // each sweep splits a level's rows into one contiguous block per CTA, so every
+    // SM of the cluster carries an equal share of a small level's L2 traffic
+    // (a grid-wide thread index would leave a 1,000-row level to one or two SMs)
+    const int nb = gridDim.x, lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    auto lo_of = [&](int n) { const int per = (n + nb - 1) / nb; return min(n, (int)blockIdx.x * per); };
+    auto hi_of = [&](int n) { const int per = (n + nb - 1) / nb; return min(n, ((int)blockIdx.x + 1) * per); };
     const int last = cc.nlev - 1;
     for (int l = 0; l < last; l++) {
         const CoarseLevel<T> &L = cc.lv[l], &C = cc.lv[l + 1];
-        for (int i = tid; i < L.n; i += nt) L.e2[i] = L.f[i] - ell_dot(L, i, L.e);
+        for (int i = lo_of(L.n) + threadIdx.x; i < hi_of(L.n); i += blockDim.x) L.e2[i] = L.f[i] - ell_dot(L, i, L.e);
         cluster_barrier();
-        for (int I = tid; I < C.n; I += nt) {
+        for (int I = lo_of(C.n) + threadIdx.x; I < hi_of(C.n); I += blockDim.x) {
             T s = (T)0;
             for (int q = L.moff[I]; q < L.moff[I + 1]; q++) s += L.e2[L.mem[q]];
             C.f[I] = s;
@@ -1085,9 +1090,9 @@ coarse_cycle_kernel(const CoarseCycle<T> cc, const int *done) {
     }
     {
         const CoarseLevel<T> &C = cc.lv[last];
-        const int warp = tid >> 5, lane = threadIdx.x & 31, nw = nt >> 5;
-        for (int r = warp; r < C.n; r += nw) {
+        for (int r = lo_of(C.n) + wib; r < hi_of(C.n); r += wpb) {
             double s = 0.0;
+#pragma unroll 4
             for (int j = lane; j < C.n; j += 32) s += cc.inv[(long)r * C.n + j] * (double)C.f[j];
             for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
             if (lane == 0) C.e[r] = (T)s;
@@ -1097,9 +1102,10 @@ coarse_cycle_kernel(const CoarseCycle<T> cc, const int *done) {
     for (int l = last - 1; l >= 0; l--) {
         const CoarseLevel<T> &L = cc.lv[l], &C = cc.lv[l + 1];
         const T *ec = (l + 1 == last) ? C.e : C.e2;
-        for (int i = tid; i < L.n; i += nt) L.e[i] += ec[L.agg[i]];
+        for (int i = lo_of(L.n) + threadIdx.x; i < hi_of(L.n); i += blockDim.x) L.e[i] += ec[L.agg[i]];
         cluster_barrier();
-        for (int i = tid; i < L.n; i += nt) L.e2[i] = L.e[i] + (L.f[i] - ell_dot(L, i, L.e)) * L.dinv[i];
+        for (int i = lo_of(L.n) + threadIdx.x; i < hi_of(L.n); i += blockDim.x)
+            L.e2[i] = L.e[i] + (L.f[i] - ell_dot(L, i, L.e)) * L.dinv[i];
         if (l > 0) cluster_barrier();
     }
 }
