@@ -1060,6 +1060,19 @@ __device__ __forceinline__ T ell_dot(const CoarseLevel<T> &L, int i, const T *__
     return t;
 }
 
+// L2 prefetch of part `part` of `parts` of [p, p + bytes), its ends rounded
+// inwards to 16 bytes (a bulk prefetch is a hint; it never leaves the range)
+__device__ __forceinline__ void l2_prefetch_part(const void *p, size_t bytes, int part, int parts) {
+    if (p == nullptr || bytes < 16) return;
+    const size_t a = (size_t)p, e = a + bytes;
+    const size_t chunk = (bytes / parts + 15) & ~(size_t)15;
+    size_t lo = (a + (size_t)part * chunk + 15) & ~(size_t)15;
+    size_t hi = (a + (size_t)(part + 1) * chunk) & ~(size_t)15;
+    if (hi > (e & ~(size_t)15)) hi = e & ~(size_t)15;
+    if (hi <= lo) return;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((unsigned)(hi - lo)) : "memory");
+}
+
 __device__ __forceinline__ void cluster_barrier() {
     __threadfence();                   // global writes of this thread before the barrier
     cg::this_cluster().sync();
@@ -1076,6 +1089,21 @@ coarse_cycle_kernel(const CoarseCycle<T> cc, const int *done) {
     auto lo_of = [&](int n) { const int per = (n + nb - 1) / nb; return min(n, (int)blockIdx.x * per); };
     auto hi_of = [&](int n) { const int per = (n + nb - 1) / nb; return min(n, ((int)blockIdx.x + 1) * per); };
     const int last = cc.nlev - 1;
+    // the matrices of the levels below the first and the dense inverse come into
+    // L2 while the first level is swept: one bulk prefetch per (array, CTA)
+    if (threadIdx.x < 32) {
+        const int t = threadIdx.x;
+        const int lv = 1 + t / 4, a = t % 4;
+        if (lv <= last) {
+            const CoarseLevel<T> &Q = cc.lv[lv];
+            const size_t ell = (size_t)Q.width * Q.n;
+            if (a == 0) l2_prefetch_part(Q.colA, sizeof(int) * ell, blockIdx.x, nb);
+            else if (a == 1) l2_prefetch_part(Q.val, sizeof(T) * ell, blockIdx.x, nb);
+            else if (a == 2) l2_prefetch_part(Q.dinv, sizeof(T) * Q.n, blockIdx.x, nb);
+            else if (lv < last) l2_prefetch_part(Q.mem, sizeof(int) * Q.n, blockIdx.x, nb);
+            else l2_prefetch_part(cc.inv, sizeof(double) * (size_t)Q.n * Q.n, blockIdx.x, nb);
+        }
+    }
     for (int l = 0; l < last; l++) {
         const CoarseLevel<T> &L = cc.lv[l], &C = cc.lv[l + 1];
         for (int i = lo_of(L.n) + threadIdx.x; i < hi_of(L.n); i += blockDim.x) L.e2[i] = L.f[i] - ell_dot(L, i, L.e);
