@@ -111,8 +111,22 @@ __device__ __forceinline__ void for_row(const Mat<V> &A, int i, F f) {
         if (iy < ny - 1) f(i + nx, A.val[4 * n + i]);
         if (iz < A.g.nz - 1) f(i + nxy, A.val[6 * n + i]);
     } else if (A.selfpad) {
-#pragma unroll 4
-        for (int k = 0; k < A.width; k++) f(A.col[(long)k * A.n + i], A.val[(long)k * A.n + i]);
+        // batches of 8 entries: the batch's loads are issued together, then f
+        // runs on them in column-slot order
+        for (int k0 = 0; k0 < A.width; k0 += 8) {
+            int jj[8];
+            V vv[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const long q = (long)(k0 + u) * A.n + i;
+                const bool ok = k0 + u < A.width;
+                jj[u] = ok ? A.col[q] : i;
+                vv[u] = ok ? A.val[q] : V(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+                if (k0 + u < A.width) f(jj[u], vv[u]);
+        }
     } else {
         // -1 padding sits only at the end of a row: skipping it instead of
         // stopping there visits the same entries in the same order, and the
@@ -926,11 +940,41 @@ __global__ void gj_extract_kernel(int n, const double *__restrict__ aug, T *__re
 // ---------------------------------------------------------------------------
 // apply kernels (precision T)
 // ---------------------------------------------------------------------------
+// L2 prefetch of part `part` of `parts` of [p, p + bytes), its ends rounded
+// inwards to 16 bytes (a bulk prefetch is a hint; it never leaves the range)
+__device__ __forceinline__ void l2_prefetch_part(const void *p, size_t bytes, int part, int parts) {
+    if (p == nullptr || bytes < 16) return;
+    const size_t a = (size_t)p, e = a + bytes;
+    const size_t chunk = (bytes / parts + 15) & ~(size_t)15;
+    size_t lo = (a + (size_t)part * chunk + 15) & ~(size_t)15;
+    size_t hi = (a + (size_t)(part + 1) * chunk) & ~(size_t)15;
+    if (hi > (e & ~(size_t)15)) hi = e & ~(size_t)15;
+    if (hi <= lo) return;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((unsigned)(hi - lo)) : "memory");
+}
+
+// arrays to bring into L2 ahead of their use (the coarse levels of a V-cycle):
+// the first kernel of stage P issues the prefetches, the cluster launch of the
+// coarse levels starts tens of microseconds later with its data in L2
+constexpr int kPrefetchMax = 16;
+struct L2Prefetch {
+    int count;
+    const void *p[kPrefetchMax];
+    unsigned long long bytes[kPrefetchMax];
+};
+constexpr int kPrefetchParts = 8;
+__device__ __forceinline__ void issue_prefetch(const L2Prefetch &pf) {
+    if (blockIdx.x < kPrefetchParts && (int)threadIdx.x < pf.count)
+        l2_prefetch_part(pf.p[threadIdx.x], pf.bytes[threadIdx.x], blockIdx.x, kPrefetchParts);
+}
+
 // f0 = first row of L times r (quasi-IMPES: L_00 = 1); e0 = f0 / l1
 template <int B, typename T>
 __global__ void restrict_p_kernel(int N, const double *__restrict__ r, const T *__restrict__ wT, int full,
-                                  const T *__restrict__ dinv0, T *__restrict__ f0, T *__restrict__ e0, const int *done) {
+                                  const T *__restrict__ dinv0, T *__restrict__ f0, T *__restrict__ e0, const L2Prefetch pf,
+                                  const int *done) {
     if (skip(done)) return;
+    issue_prefetch(pf);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const T r0 = full ? wT[i] * (T)r[i] : (T)r[i];
@@ -1058,19 +1102,6 @@ __device__ __forceinline__ T ell_dot(const CoarseLevel<T> &L, int i, const T *__
 #pragma unroll 4
     for (int k = 0; k < L.width; k++) t += L.val[(long)k * L.n + i] * e[L.colA[(long)k * L.n + i]];
     return t;
-}
-
-// L2 prefetch of part `part` of `parts` of [p, p + bytes), its ends rounded
-// inwards to 16 bytes (a bulk prefetch is a hint; it never leaves the range)
-__device__ __forceinline__ void l2_prefetch_part(const void *p, size_t bytes, int part, int parts) {
-    if (p == nullptr || bytes < 16) return;
-    const size_t a = (size_t)p, e = a + bytes;
-    const size_t chunk = (bytes / parts + 15) & ~(size_t)15;
-    size_t lo = (a + (size_t)part * chunk + 15) & ~(size_t)15;
-    size_t hi = (a + (size_t)(part + 1) * chunk) & ~(size_t)15;
-    if (hi > (e & ~(size_t)15)) hi = e & ~(size_t)15;
-    if (hi <= lo) return;
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((unsigned)(hi - lo)) : "memory");
 }
 
 __device__ __forceinline__ void cluster_barrier() {
@@ -1202,8 +1233,9 @@ template <int B, typename T>
 __global__ void fpf_resid_kernel(GridDesc g, const double *__restrict__ r, const T *__restrict__ wT,
                                  const T *__restrict__ lscT, const T *__restrict__ ahat, const T *__restrict__ x0,
                                  const T *__restrict__ dinv0, T *__restrict__ rh, T *__restrict__ f0, T *__restrict__ e0,
-                                 const int *done) {
+                                 const L2Prefetch pf, const int *done) {
     if (skip(done)) return;
+    issue_prefetch(pf);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const long N = g.N;
     if (i >= N) return;
@@ -1801,6 +1833,27 @@ static int coarse_start(const sim_t *s) {
     return (nl - l0 >= 3) ? l0 : nl;   // worth a launch only when it replaces several
 }
 
+// the arrays the cluster launch of the coarse levels reads (none without it)
+template <typename T>
+static L2Prefetch coarse_prefetch(const sim_t *s) {
+    L2Prefetch pf{};
+    const int nl = (int)s->lev.size();
+    const int lf = s->opt.fused_coarse ? coarse_start(s) : nl;
+    auto add = [&](const void *p, size_t bytes) {
+        if (p && bytes >= 16 && pf.count < kPrefetchMax) { pf.p[pf.count] = p; pf.bytes[pf.count] = bytes; pf.count++; }
+    };
+    for (int l = lf; l < nl; l++) {
+        const AmgLevel &L = s->lev[l];
+        const size_t ell = (size_t)L.width * L.n;
+        if (l + 1 == nl) { add(L.coarse_inv, sizeof(double) * (size_t)L.n * L.n); break; }
+        add(L.colA, sizeof(int) * ell);
+        add(L.valT, sizeof(T) * ell);
+        add(L.dinvT, sizeof(T) * L.n);
+        add(L.mem, sizeof(int) * L.n);
+    }
+    return pf;
+}
+
 template <typename T>
 static sim_status coarse_cycle(sim_t *s, int l0, const int *done) {
     const int nl = (int)s->lev.size();
@@ -1890,11 +1943,11 @@ static sim_status apply_btz(sim_t *s, const double *r, TZ *z, const int *done) {
         SIM_LAUNCHED(s);
         fpf_resid_kernel<B, T><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, r, (const T *)s->qiwT, lscT, (const T *)s->ahat,
                                                                  (const T *)s->x0, (const T *)L0.dinvT, (T *)s->rhT,
-                                                                 (T *)L0.f, (T *)L0.e, done);
+                                                                 (T *)L0.f, (T *)L0.e, coarse_prefetch<T>(s), done);
         SIM_LAUNCHED(s);
     } else {
         restrict_p_kernel<B, T><<<nb, SIM_THREADS, 0, s->stream>>>(N, r, (const T *)s->qiwT, full, (const T *)L0.dinvT,
-                                                                  (T *)L0.f, (T *)L0.e, done);
+                                                                  (T *)L0.f, (T *)L0.e, coarse_prefetch<T>(s), done);
         SIM_LAUNCHED(s);
     }
     const T *ep;
@@ -2002,8 +2055,8 @@ static sim_status learned_pairs_t(sim_t *s, int k, float *x, float *y) {
     };
     for (int j = 0; j < k; j++) {
         const double *v = s->V + (size_t)j * N * s->b;
-        if (s->b == 2) restrict_p_kernel<2, T><<<sim_blocks(N), SIM_THREADS, 0, s->stream>>>(N, v, (const T *)s->qiwT, full, (const T *)L0.dinvT, (T *)L0.f, (T *)L0.e, nullptr);
-        else restrict_p_kernel<3, T><<<sim_blocks(N), SIM_THREADS, 0, s->stream>>>(N, v, (const T *)s->qiwT, full, (const T *)L0.dinvT, (T *)L0.f, (T *)L0.e, nullptr);
+        if (s->b == 2) restrict_p_kernel<2, T><<<sim_blocks(N), SIM_THREADS, 0, s->stream>>>(N, v, (const T *)s->qiwT, full, (const T *)L0.dinvT, (T *)L0.f, (T *)L0.e, L2Prefetch{}, nullptr);
+        else restrict_p_kernel<3, T><<<sim_blocks(N), SIM_THREADS, 0, s->stream>>>(N, v, (const T *)s->qiwT, full, (const T *)L0.dinvT, (T *)L0.f, (T *)L0.e, L2Prefetch{}, nullptr);
         SIM_LAUNCHED(s);
         if (cycle() != SIM_OK) return s->err;
         // r' = f - A_p e_p into rpT; the first refinement cycle starts from it
