@@ -112,9 +112,11 @@ __device__ void fold(const double *partials, int nv, double *out) {
 constexpr int NVMAX = SIM_MAX_M + 1;
 
 // h[k] = V_k . w, k < NV (NV exact: no predicated work for absent vectors),
-// and h[NV] = w . w (the norm the selective reorthogonalisation test needs)
+// and h[NV] = w . w (the norm the selective reorthogonalisation test needs).
+// Above 20 vectors two blocks per SM (128 registers a thread) keep more of an
+// element's NV loads in flight than three blocks at 80 registers.
 template <int NV>
-__global__ void __launch_bounds__(SIM_THREADS, 3) dots_kernel(const double *__restrict__ V, const double *__restrict__ w,
+__global__ void __launch_bounds__(SIM_THREADS, NV > 20 ? 2 : 3) dots_kernel(const double *__restrict__ V, const double *__restrict__ w,
                                                            long n, double *partials, unsigned int *ticket,
                                                            double *out, const int *done) {
     if (skip(done)) return;
@@ -232,7 +234,7 @@ struct OrthDispatch<0> {
 // (NV = j + 1 at compile time: the NV basis loads of an element are unrolled
 // and in flight together)
 template <int NV>
-__global__ void __launch_bounds__(SIM_THREADS, 3) orth_norm_kernel(const double *__restrict__ V, double *__restrict__ w,
+__global__ void __launch_bounds__(SIM_THREADS, NV > 20 ? 2 : 3) orth_norm_kernel(const double *__restrict__ V, double *__restrict__ w,
                                                                 long n, int j, int m, double *partials,
                                                                 unsigned int *ticket, KrylovCtl *ctl, int selective) {
     if (ctl->done) return;
