@@ -98,12 +98,23 @@ __device__ bool last_block(unsigned int *ticket) {
 }
 
 // one warp per value: lanes stride over the block partials, then a fixed
-// shuffle tree (the summation order does not depend on timing)
+// shuffle tree (the summation order does not depend on timing).  A lane loads
+// 8 of its partials before adding them in stride order, so the loads overlap
+// instead of each waiting for the previous add.
 __device__ void fold(const double *partials, int nv, double *out) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int G = (int)gridDim.x;
     for (int k = wid; k < nv; k += nw) {
+        const double *p = partials + (long)k * G;
         double s = 0.0;
-        for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(partials + (long)k * gridDim.x + b);
+        for (int b0 = lane; b0 < G; b0 += 32 * 8) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) v[u] = b0 + 32 * u < G ? __ldcg(p + b0 + 32 * u) : 0.0;
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+                if (b0 + 32 * u < G) s += v[u];
+        }
         s = warp_sum(s);
         if (lane == 0) out[k] = s;
     }
@@ -254,17 +265,23 @@ __global__ void __launch_bounds__(SIM_THREADS, NV > 20 ? 2 : 3) orth_norm_kernel
     block_partials<1>(acc, 1, partials);
     if (last_block(ticket)) {
         __shared__ double nrm;
+        // the column and the earlier rotations, staged by the whole block so
+        // that thread 0's rotation chain reads shared memory only
+        __shared__ double col[NVMAX + 1], rcs[NVMAX + 1], rsn[NVMAX + 1];
+        for (int k = threadIdx.x; k <= j; k += blockDim.x) {
+            col[k] = re ? ctl->h[k] + ctl->h2[k] : ctl->h[k];
+            rcs[k] = ctl->cs[k];
+            rsn[k] = ctl->sn[k];
+        }
         fold(partials, 1, &nrm);
         __syncthreads();
         if (threadIdx.x == 0) {
             *ticket = 0u;
             const double hn = sqrt(nrm);
-            double col[NVMAX + 1];
-            for (int k = 0; k <= j; k++) col[k] = re ? ctl->h[k] + ctl->h2[k] : ctl->h[k];
             for (int k = 0; k < j; k++) {
                 const double a = col[k], c2 = col[k + 1];
-                col[k] = ctl->cs[k] * a + ctl->sn[k] * c2;
-                col[k + 1] = -ctl->sn[k] * a + ctl->cs[k] * c2;
+                col[k] = rcs[k] * a + rsn[k] * c2;
+                col[k + 1] = -rsn[k] * a + rcs[k] * c2;
             }
             const double a = col[j], bb = hn;
             const double rr = sqrt(a * a + bb * bb);
@@ -301,14 +318,24 @@ __global__ void scale_kernel(const double *__restrict__ w, double *__restrict__ 
 }
 
 // y = H^{-1} g (k x k upper triangular), single thread
+// (H and g staged in shared memory by the block, so the one thread that runs
+// the dependent back substitution never waits on global memory)
 __global__ void backsolve_kernel(KrylovCtl *ctl) {
-    if (threadIdx.x != 0) return;
+    constexpr int LD = SIM_MAX_M + 1;
+    __shared__ double Hs[LD * LD], gs[LD], ys[LD];
     const int k = ctl->k;
-    for (int i = k - 1; i >= 0; i--) {
-        double t = ctl->g[i];
-        for (int c = i + 1; c < k; c++) t -= ctl->H[i * (SIM_MAX_M + 1) + c] * ctl->y[c];
-        ctl->y[i] = t / ctl->H[i * (SIM_MAX_M + 1) + i];
+    for (int t = threadIdx.x; t < k * LD; t += blockDim.x) Hs[t] = ctl->H[t];
+    for (int t = threadIdx.x; t < k; t += blockDim.x) gs[t] = ctl->g[t];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = k - 1; i >= 0; i--) {
+            double t = gs[i];
+            for (int c = i + 1; c < k; c++) t -= Hs[i * LD + c] * ys[c];
+            ys[i] = t / Hs[i * LD + i];
+        }
     }
+    __syncthreads();
+    for (int t = threadIdx.x; t < k; t += blockDim.x) ctl->y[t] = ys[t];
 }
 
 // x += sum_k y_k Z_k
