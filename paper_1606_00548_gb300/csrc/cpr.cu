@@ -349,8 +349,9 @@ __global__ void diag_inv_kernel(GridDesc g, const double *__restrict__ J, WellCo
 
 // black cells: D = Ahat_ii - sum_d Ahat_{i,d} Dinv_k Ahat_{k,opp(d)}
 template <int B>
-__global__ void ilu_black_kernel(GridDesc g, const double *__restrict__ J, WellCorr wc, const double *__restrict__ lsc,
-                                 double *__restrict__ dinv) {
+__global__ void __launch_bounds__(SIM_THREADS, 2) ilu_black_kernel(GridDesc g, const double *__restrict__ J, WellCorr wc,
+                                                                   const double *__restrict__ lsc,
+                                                                   double *__restrict__ dinv) {
     const int i = colour_cell(g, blockIdx.x * (long)blockDim.x + threadIdx.x, 1);
     const long N = g.N;
     if (i < 0) return;
@@ -1002,8 +1003,21 @@ __global__ void amg_restrict_kernel(const T *__restrict__ r, const int *__restri
     if (skip(done)) return;
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nc) return;
+    // members in batches of 8: the batch's indices, then its gathers, then the
+    // sum in member order (a plain loop would wait on each load in turn)
+    const int q0 = moff[I], q1 = moff[I + 1];
     T s = (T)0;
-    for (int q = moff[I]; q < moff[I + 1]; q++) s += r[mem[q]];
+    for (int qb = q0; qb < q1; qb += 8) {
+        int m[8];
+        T v[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) m[u] = qb + u < q1 ? mem[qb + u] : -1;
+#pragma unroll
+        for (int u = 0; u < 8; u++) v[u] = m[u] >= 0 ? r[m[u]] : (T)0;
+#pragma unroll
+        for (int u = 0; u < 8; u++)
+            if (qb + u < q1) s += v[u];
+    }
     fc[I] = s;
     if (ec) ec[I] = s * dinvc[I];
 }
