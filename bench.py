@@ -145,24 +145,41 @@ def barrier(ws):
         dist.barrier()
 
 
+def _all_reduce(v, op):
+    import torch
+    import torch.distributed as dist
+    # NCCL reduces device tensors; the gloo group of the CPU tests reduces host ones
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
+    return float(t.item())
+
+
 def max_over_ranks(ws, v):
     if ws == 1:
         return v
-    import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    return _all_reduce(v, dist.ReduceOp.MAX)
 
 
 def sum_over_ranks(ws, v):
     if ws == 1:
         return v
-    import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _all_reduce(v, dist.ReduceOp.SUM)
+
+
+def job_throughput(ws, work, seconds):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time.  Returns (value, max seconds)."""
+    t_max = max_over_ranks(ws, seconds)
+    return sum_over_ranks(ws, float(work)) / t_max, t_max
+
+
+def shard(items, ws, rank):
+    """The share of independent units (ensemble members) of one rank: every
+    ws-th item from `rank` on, so the ranks' shares partition the list."""
+    return items[rank::ws]
 
 
 def cpu_oracle_sample(case, newton_its=1):
@@ -266,9 +283,7 @@ def run_ours(args):
     clocks = sampler.stop() if sampler else None
     t_dev = e0.elapsed_time(e1) / 1e3
     st1 = sim.stats()
-    t_max = max_over_ranks(ws, t_dev)
-    work = sum_over_ranks(ws, float(N * newton))
-    value = work / t_max
+    value, t_max = job_throughput(ws, N * newton, t_dev)
 
     # end to end through the C ABI with host buffers: H2D state, step, D2H state
     p, sw, x3, ph = sim.get_state()
@@ -283,8 +298,7 @@ def run_ours(args):
         e2e_newton += info.newton_iterations
         p, sw, x3, ph = sim.get_state()
     torch.cuda.synchronize()
-    t_e2e = max_over_ranks(ws, time.perf_counter() - t0)
-    e2e_value = sum_over_ranks(ws, float(N * e2e_newton)) / t_e2e
+    e2e_value, t_e2e = job_throughput(ws, N * e2e_newton, time.perf_counter() - t0)
     state_bytes = N * (3 * 8 + 1)
 
     # roofline of the block SpMV: y = J x, 7 b^2 + 2 b doubles per cell; device
@@ -388,7 +402,7 @@ def run_ensemble(args):
     build.build()
     from paper_1606_00548_gb300.sim import Batch, Simulator
     prec = 1 if args.precision == "mixed" else 0
-    members = synth.ensemble_members(64, nsteps=20, dt=1.0)[rank::ws]
+    members = shard(synth.ensemble_members(64, nsteps=20, dt=1.0), ws, rank)
     sims = [Simulator(c, precision=prec) for c in members]
     cells = [c["nx"] * c["ny"] * c["nz"] for c in members]
     for sm in sims:
@@ -403,8 +417,7 @@ def run_ensemble(args):
         sts, infos = batch.step(1.0)
         work += sum(n * inf.newton_iterations for n, inf in zip(cells, infos))
     torch.cuda.synchronize()
-    t_batch = max_over_ranks(ws, time.perf_counter() - t0)
-    value = sum_over_ranks(ws, float(work)) / t_batch
+    value, t_batch = job_throughput(ws, work, time.perf_counter() - t0)
     # one member at a time (same handles, next steps)
     t0 = time.perf_counter()
     work_seq = 0
@@ -413,8 +426,7 @@ def run_ensemble(args):
             st, inf = sm.step(1.0)
             work_seq += n * inf.newton_iterations
     torch.cuda.synchronize()
-    t_seq = max_over_ranks(ws, time.perf_counter() - t0)
-    value_seq = sum_over_ranks(ws, float(work_seq)) / t_seq
+    value_seq, t_seq = job_throughput(ws, work_seq, time.perf_counter() - t0)
     if rank == 0:
         st0 = sims[0].stats()
         line = {
