@@ -176,7 +176,12 @@ void sim_destroy(sim_t *s);
 
 /* Accepted state (host arrays of N): pressure, Sw, x3 (Sg or pb), phase
    (1 saturated, 0 undersaturated; ignored for oil-water).  set_state also
-   zeroes the cumulative well masses and starts a new time step from it. */
+   zeroes the cumulative well masses and starts a new time step from it.
+   A non-finite value in p, Sw or x3 returns SIM_ENAN (sticky) and leaves
+   the handle's state as it was.  get_state followed by set_state on a handle
+   of the same case resumes a run: the following steps reproduce an
+   uninterrupted run bit for bit (BHP-controlled wells; the BHP unknowns of
+   rate-controlled wells are restored with sim_set_well_bhp). */
 sim_status sim_set_state(sim_t *s, const double *p, const double *sw, const double *x3, const int8_t *phase);
 sim_status sim_get_state(sim_t *s, double *p, double *sw, double *x3, int8_t *phase);
 
@@ -199,7 +204,8 @@ sim_status sim_newton_step(sim_t *s, double dt, sim_newton_info *info);
 sim_status sim_linear_solve(sim_t *s, const double *b_dev, double *x_dev, sim_linear_info *info);
 
 /* ---- inspection entry points (used by the parity tests) ---- */
-/* current Newton iterate, host arrays: x[b*N] component-major, phase[N] */
+/* current Newton iterate, host arrays: x[b*N] component-major, phase[N];
+   a non-finite x returns SIM_ENAN (sticky) with the iterate unchanged */
 sim_status sim_set_iterate(sim_t *s, const double *x, const int8_t *phase);
 sim_status sim_get_iterate(sim_t *s, double *x, int8_t *phase);
 /* residual and Jacobian at the current iterate for step length dt */
@@ -260,12 +266,14 @@ int32_t sim_block_size(sim_t *s);
      cnv_rho   host, b doubles (> 0), per-component density scale
      cnv_dev   device, 1 double: receives the result (NaN if any R is NaN)
      cuda_stream  cudaStream_t or NULL; the call is asynchronous on it.
-   Scratch: a library-owned static device array of 609 doubles (per-block
-   partial maxima plus a ticket word), held by every GPU that loads the
-   library until the process exits; no cudaMalloc / cudaFree is ever made.
-   The first call on a device looks up that array's device address
-   (cudaGetSymbolAddress) with the device current; make that first call
-   before any stream capture.  All calls share the array and it keeps the
+   Scratch: a library-owned static device array of 457 doubles (3,656
+   bytes: 456 per-block partial maxima plus a ticket word), held by every GPU
+   that loads the library until the process exits; no cudaMalloc / cudaFree
+   is ever made.  Every call looks up that array's device address
+   (cudaGetSymbolAddress, no allocation) on the caller's current device, so
+   a device reset between calls leaves no stale address behind; the first
+   call on a device may also load the library's device code, so make that
+   first call before any stream capture.  All calls share the array and it keeps the
    last call's contents (the ticket is cleared by each call): calls that
    overlap on the GPU (other streams, other threads) race and must not
    overlap.  Limits: b in {2, 3}; N*b < 2^31 (32-bit indexing), larger

@@ -14,7 +14,6 @@
 // One thread per cell writes only its own rows, so no atomics are needed;
 // each face flux is evaluated by both of its cells in the same canonical
 // (L, R) orientation, so the two contributions cancel exactly.
-#include <mutex>
 
 #include "sim_internal.cuh"
 
@@ -851,10 +850,12 @@ sim_status k_finite(sim_t *s, const double *v, long n, int *ok) {
 // CNV without device allocation (sim_cnv_noalloc)
 //
 // Scratch: the per-block partial maxima and the last-block ticket live in a
-// file-scope device array of NOALLOC_SCRATCH doubles (2.4 KB), held by every
+// file-scope device array of NOALLOC_SCRATCH = SIM_RED_BLOCKS + 1 doubles
+// (456 partials and one ticket word: 457 doubles, 3,656 bytes), held by every
 // GPU that loads the library until the process exits.  Host code never uses
-// the array's name as a pointer (on the host it is only a stand-in): the
-// device address is fetched once per device with cudaGetSymbolAddress.
+// the array's name as a pointer (on the host it is only a stand-in): every
+// call looks the device address up with cudaGetSymbolAddress, with the
+// caller's device current, so no address outlives a device reset.
 // ===========================================================================
 namespace {
 constexpr int NOALLOC_SCRATCH = SIM_RED_BLOCKS + 1;   // partials + ticket word
@@ -878,9 +879,6 @@ __global__ void cnv_noalloc_kernel(GridDesc g, const double *__restrict__ R, con
 }
 }  // namespace
 
-static std::mutex g_noalloc_mutex;
-static double *g_noalloc_addr[256];   // device address of g_cnv_scratch, per device ordinal
-
 extern "C" sim_status sim_cnv_noalloc(int32_t nx, int32_t ny, int32_t nz, double dx, double dy, double dz, int32_t b,
                                       const double *R_dev, const double *poro_dev, const double *cnv_rho, double dt,
                                       double *cnv_dev, void *cuda_stream) {
@@ -892,23 +890,14 @@ extern "C" sim_status sim_cnv_noalloc(int32_t nx, int32_t ny, int32_t nz, double
     const long long N = (long long)nx * ny * nz;
     if (N * b > 0x7fffffffLL)
         return sim_fail(nullptr, SIM_ELIMIT, "sim_cnv_noalloc: N*b must stay below 2^31 (32-bit indexing)");
-    int dev = 0;
+    int dev = 0;   // the caller's current device: the one whose copy of the array is used
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return sim_fail(nullptr, SIM_ECUDA, std::string("sim_cnv_noalloc: ") + cudaGetErrorString(e));
-    if (dev < 0 || dev >= 256) return sim_fail(nullptr, SIM_ELIMIT, "sim_cnv_noalloc: device ordinal above 255");
+    // the array's device address on that device (a lookup, no allocation)
     double *scratch = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-        if (!g_noalloc_addr[dev]) {
-            e = cudaGetSymbolAddress((void **)&g_noalloc_addr[dev], g_cnv_scratch);
-            if (e != cudaSuccess) {
-                g_noalloc_addr[dev] = nullptr;
-                return sim_fail(nullptr, SIM_ECUDA, std::string("sim_cnv_noalloc: cudaGetSymbolAddress: ") +
-                                                        cudaGetErrorString(e));
-            }
-        }
-        scratch = g_noalloc_addr[dev];
-    }
+    e = cudaGetSymbolAddress((void **)&scratch, g_cnv_scratch);
+    if (e != cudaSuccess || !scratch)
+        return sim_fail(nullptr, SIM_ECUDA, std::string("sim_cnv_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
     cudaStream_t st = (cudaStream_t)cuda_stream;
     // the ticket must start at zero; the partials are overwritten before use
     e = cudaMemsetAsync(scratch + SIM_RED_BLOCKS, 0, sizeof(double), st);

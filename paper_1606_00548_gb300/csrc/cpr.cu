@@ -22,6 +22,7 @@
 // entry k of row i at k*n + i, columns ascending, -1 padding.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include <cooperative_groups.h>
@@ -777,8 +778,18 @@ __global__ void l1_kernel(Mat<double> A, T *__restrict__ dinv) {
 // separates the steps; the result ends in A1 for odd n, else A0
 constexpr int kGjMax = 1024;   // largest coarsest level (rows)
 
+// A pivot whose magnitude is not above kGjPivotTol times the l1 norm of its
+// row of A (rn) -- zero, denormal, NaN, or pure rounding noise -- sets *bad;
+// the elimination still runs to its end (the cluster barriers need every CTA)
+// and the host turns the flag into an error instead of using the inverse.
+constexpr double kGjPivotTol = 1e-14;
+
+__device__ __forceinline__ void gj_check_pivot(double piv, double rnorm, int *bad) {
+    if (!(fabs(piv) > kGjPivotTol * rnorm)) *(volatile int *)bad = 1;
+}
+
 __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(1024, 1)
-gj_cluster_kernel(int n, double *__restrict__ A0, double *__restrict__ A1) {
+gj_cluster_kernel(int n, double *__restrict__ A0, double *__restrict__ A1, const double *__restrict__ rn, int *bad) {
     __shared__ double pk[2 * kGjMax];   // the pivot row over its pivot, per CTA (one division per entry)
     const int w = 2 * n;
     // CTA c owns rows c, c + 8, ...; its threads stride over the columns (no index division)
@@ -789,6 +800,7 @@ gj_cluster_kernel(int n, double *__restrict__ A0, double *__restrict__ A1) {
         const double *src = (k & 1) ? A1 : A0;
         double *dst = (k & 1) ? A0 : A1;
         const double piv = src[(long)k * w + k];
+        if (blockIdx.x == 0 && threadIdx.x == 0) gj_check_pivot(piv, rn[k], bad);
         for (int j = threadIdx.x; j < w; j += blockDim.x) pk[j] = src[(long)k * w + j] / piv;
         __syncthreads();
         if (r0 < rows_at_once) {
@@ -819,7 +831,8 @@ gj_cluster_kernel(int n, double *__restrict__ A0, double *__restrict__ A1) {
 constexpr int kGjSmem = 256, kGjPanel = 4;
 
 __global__ void __launch_bounds__(1024, 1)
-gj_dsmem_kernel(int n, const double *__restrict__ aug, double *__restrict__ inv) {
+gj_dsmem_kernel(int n, const double *__restrict__ aug, double *__restrict__ inv, const double *__restrict__ rn,
+                int *bad) {
     extern __shared__ double gsm[];
     cg::cluster_group cl = cg::this_cluster();
     const int nc = (int)cl.num_blocks(), w = 2 * n, rpc = (n + nc - 1) / nc;   // rows per CTA
@@ -846,6 +859,7 @@ gj_dsmem_kernel(int n, const double *__restrict__ aug, double *__restrict__ inv)
                 __syncthreads();
                 for (int q = 0; q < ps; q++) {
                     const double piv = Pb[(long)q * w + k0 + q];
+                    if (tid == 0) gj_check_pivot(piv, rn[k0 + q], bad);
                     __syncthreads();
                     for (int j = j0 + tid; j < j0 + wa; j += bd) Pb[(long)q * w + j] = Pb[(long)q * w + j] / piv;
                     __syncthreads();
@@ -928,6 +942,15 @@ __global__ void gj_init_kernel(Mat<double> A, double *__restrict__ aug) {
     double v = (j - A.n == i) ? 1.0 : 0.0;
     if (j < A.n) for_row(A, i, [&](int c, double a) { if (c == j) v += a; });
     aug[t] = v;
+}
+
+// l1 norm of each row of the coarsest matrix (the scale of the pivot test)
+__global__ void gj_rownorm_kernel(Mat<double> A, double *__restrict__ rn) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.n) return;
+    double t = 0.0;
+    for_row(A, i, [&](int, double a) { t += fabs(a); });
+    rn[i] = t;
 }
 
 template <typename T>
@@ -1707,15 +1730,20 @@ static sim_status finish_levels(sim_t *s) {
     const size_t aug = (size_t)n * 2 * n;
     double *A0 = (double *)dev_alloc_async(s, sizeof(double) * aug);
     double *A1 = (double *)dev_alloc_async(s, sizeof(double) * aug);
-    if (!A0 || !A1) return s->err;
+    double *rn = (double *)dev_alloc_async(s, sizeof(double) * n);
+    if (!A0 || !A1 || !rn) return s->err;
+    int *bad = s->iscal + 4;
+    SIM_CK(s, cudaMemsetAsync(bad, 0, sizeof(int), s->stream));
     gj_init_kernel<<<sim_blocks(2L * n * n), SIM_THREADS, 0, s->stream>>>(level_mat(s, C, nl - 1), A0);
+    s->launches++;
+    gj_rownorm_kernel<<<sim_blocks(n), SIM_THREADS, 0, s->stream>>>(level_mat(s, C, nl - 1), rn);
     s->launches++;
     static bool dsmem_ok = cudaFuncSetAttribute(gj_dsmem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                 (int)gj_dsmem_bytes(kGjSmem, 8)) == cudaSuccess;
     static int gj_ctas = gj_cluster_ctas();
     const bool in_smem = dsmem_ok && n <= kGjSmem;
     if (!in_smem) {
-        gj_cluster_kernel<<<8, 1024, 0, s->stream>>>(n, A0, A1);
+        gj_cluster_kernel<<<8, 1024, 0, s->stream>>>(n, A0, A1, rn, bad);
         s->launches++;
     }
     // the coarsest inverse stays FP64 in both forms: the coarse matrices of
@@ -1729,7 +1757,8 @@ static sim_status finish_levels(sim_t *s) {
         at[0].val.clusterDim.x = gj_ctas; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
         cfg.gridDim = dim3(gj_ctas); cfg.blockDim = dim3(1024); cfg.dynamicSmemBytes = gj_dsmem_bytes(n, gj_ctas);
         cfg.stream = s->stream; cfg.attrs = at; cfg.numAttrs = 1;
-        if (!sim_cuda_ok(s, cudaLaunchKernelEx(&cfg, gj_dsmem_kernel, n, (const double *)A0, (double *)C.coarse_inv),
+        if (!sim_cuda_ok(s, cudaLaunchKernelEx(&cfg, gj_dsmem_kernel, n, (const double *)A0, (double *)C.coarse_inv,
+                                               (const double *)rn, bad),
                          "coarsest inverse"))
             return s->err;
     } else {
@@ -1737,8 +1766,15 @@ static sim_status finish_levels(sim_t *s) {
                                                                                         (double *)C.coarse_inv);
     }
     s->launches++;
-    dev_free_async(s, A0); dev_free_async(s, A1);
+    dev_free_async(s, A0); dev_free_async(s, A1); dev_free_async(s, rn);
     SIM_CK(s, cudaGetLastError());
+    // the pivot test of the elimination (no pivoting: a vanishing pivot would
+    // leave inf / NaN in the coarsest inverse)
+    SIM_CK(s, cudaMemcpyAsync(&s->h_pinned[0], bad, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    SIM_CK(s, cudaStreamSynchronize(s->stream));
+    int hb = 0;
+    memcpy(&hb, &s->h_pinned[0], sizeof(int));
+    if (hb) return sim_fail(s, SIM_ENAN, "coarsest AMG level: a Gauss-Jordan pivot is not above 1e-14 of its row's l1 norm");
     return SIM_OK;
 }
 

@@ -347,10 +347,16 @@ sim_status sim_set_state(sim_t *s, const double *p, const double *sw, const doub
     CHECK_HANDLE(s);
     if (!p || !sw || (s->b == 3 && (!x3 || !phase))) return sim_fail(s, SIM_EINVAL, "NULL state array");
     const int N = s->N;
-    SIM_CK(s, cudaMemcpyAsync(s->x, p, sizeof(double) * N, cudaMemcpyHostToDevice, s->stream));
-    SIM_CK(s, cudaMemcpyAsync(s->x + N, sw, sizeof(double) * N, cudaMemcpyHostToDevice, s->stream));
+    // staged in a work vector and checked before the accepted state is touched
+    double *st = s->w;
+    SIM_CK(s, cudaMemcpyAsync(st, p, sizeof(double) * N, cudaMemcpyHostToDevice, s->stream));
+    SIM_CK(s, cudaMemcpyAsync(st + N, sw, sizeof(double) * N, cudaMemcpyHostToDevice, s->stream));
+    if (s->b == 3) SIM_CK(s, cudaMemcpyAsync(st + 2L * N, x3, sizeof(double) * N, cudaMemcpyHostToDevice, s->stream));
+    int ok = 1;
+    if (k_finite(s, st, (long)N * s->b, &ok) != SIM_OK) return s->err;
+    if (!ok) return sim_fail(s, SIM_ENAN, "sim_set_state: non-finite value in the state (state left unchanged)");
+    SIM_CK(s, cudaMemcpyAsync(s->x, st, sizeof(double) * N * s->b, cudaMemcpyDeviceToDevice, s->stream));
     if (s->b == 3) {
-        SIM_CK(s, cudaMemcpyAsync(s->x + 2L * N, x3, sizeof(double) * N, cudaMemcpyHostToDevice, s->stream));
         SIM_CK(s, cudaMemcpyAsync(s->ph, phase, N, cudaMemcpyHostToDevice, s->stream));
     } else {
         SIM_CK(s, cudaMemsetAsync(s->ph, 1, N, s->stream));
@@ -378,7 +384,12 @@ sim_status sim_get_state(sim_t *s, double *p, double *sw, double *x3, int8_t *ph
 sim_status sim_set_iterate(sim_t *s, const double *x, const int8_t *phase) {
     CHECK_HANDLE(s);
     if (!x || !phase) return sim_fail(s, SIM_EINVAL, "NULL iterate");
-    SIM_CK(s, cudaMemcpyAsync(s->x, x, sizeof(double) * s->N * s->b, cudaMemcpyHostToDevice, s->stream));
+    const long n = (long)s->N * s->b;
+    SIM_CK(s, cudaMemcpyAsync(s->w, x, sizeof(double) * n, cudaMemcpyHostToDevice, s->stream));
+    int ok = 1;
+    if (k_finite(s, s->w, n, &ok) != SIM_OK) return s->err;
+    if (!ok) return sim_fail(s, SIM_ENAN, "sim_set_iterate: non-finite value in the iterate (iterate left unchanged)");
+    SIM_CK(s, cudaMemcpyAsync(s->x, s->w, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->stream));
     SIM_CK(s, cudaMemcpyAsync(s->ph, phase, s->N, cudaMemcpyHostToDevice, s->stream));
     SIM_CK(s, cudaStreamSynchronize(s->stream));
     return SIM_OK;

@@ -335,6 +335,9 @@ class Simulator:
         except Exception:
             pass
 
+    def clear_error(self):
+        self.L.sim_clear_error(self.h)
+
     # state --------------------------------------------------------------------
     def set_state(self, p, sw, x3, phase):
         p, pp = _d(p); sw, sp = _d(sw); x3, xp = _d(x3)

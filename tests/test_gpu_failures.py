@@ -1,0 +1,140 @@
+"""Failure handling of the CUDA path, with every failure made on the host:
+non-finite input state, Newton solves that fail and cut the time step (as the
+"(1)" cuts of the paper's Tables 2 and 4), a vanishing pivot in the coarsest
+AMG level, and restarting a run from a saved state.  Nothing here faults,
+traps or hangs the GPU: the library reports each condition through its
+status codes and the handle stays usable.
+"""
+import numpy as np
+import pytest
+
+from paper_1606_00548_gb300 import synth
+from gpu_util import rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1606_00548_gb300 import build
+    build.build()
+    return torch
+
+
+def test_non_finite_state_is_rejected_and_the_handle_recovers(torch_cuda):
+    import oracle
+    from paper_1606_00548_gb300.sim import SIM_ENAN, SimError, Simulator
+    case = synth.quarter_five_spot_20x20x5(nsteps=1)
+    g = Simulator(case)
+    ini = case["init"]
+    p_bad = ini["p"].copy(); p_bad[123] = np.nan
+    with pytest.raises(SimError) as e:
+        g.set_state(p_bad, ini["sw"], ini["x3"], ini["phase"])
+    assert e.value.status == SIM_ENAN
+    # the error is sticky until cleared; the accepted state was not touched
+    with pytest.raises(SimError):
+        g.get_state()
+    g.clear_error()
+    p, sw, _, _ = g.get_state()
+    assert np.array_equal(p, ini["p"]) and np.array_equal(sw, ini["sw"])
+    x, ph = g.get_iterate()
+    x_bad = x.copy(); x_bad[-1] = np.inf
+    with pytest.raises(SimError) as e:
+        g.set_iterate(x_bad, ph)
+    assert e.value.status == SIM_ENAN
+    g.clear_error()
+    assert np.array_equal(g.get_iterate()[0], x)
+    # and it still steps like the oracle
+    o = oracle.Oracle(case)
+    sg, ig = g.step(case["dt"][0])
+    so, io = o.step(case["dt"][0])
+    assert sg == 0 and so == 0
+    assert rel_err(g.get_state()[0], o.get_state()[0]) <= 1e-6
+
+
+@pytest.mark.parametrize("newton_max,expect_ok", [(4, True), (3, False)])
+def test_time_step_cuts_match_oracle(torch_cuda, newton_max, expect_ok):
+    """A Newton limit of 4 iterations makes the 5-day steps of the quarter
+    five-spot cut (halve) several times before the substeps converge; with 3
+    iterations the cuts run out and the step fails with the state restored."""
+    import oracle
+    from paper_1606_00548_gb300.sim import SIM_ENOCONV_NEWTON, SIM_OK, Simulator
+    case = synth.quarter_five_spot_20x20x5(nsteps=2, dt=5.0)
+    g = Simulator(case, newton_max=newton_max)
+    o = oracle.Oracle(case, newton_max=newton_max)
+    for dt in case["dt"]:
+        p_start = g.get_state()[0]
+        sg, ig = g.step(dt)
+        so, io = o.step(dt)
+        assert (sg == SIM_OK) == expect_ok and (so == 0) == expect_ok
+        if not expect_ok:
+            assert sg == SIM_ENOCONV_NEWTON
+        assert ig.cuts == io.cuts and ig.substeps == io.substeps, (ig.cuts, io.cuts, ig.substeps, io.substeps)
+        assert ig.cuts > 0
+        assert abs(ig.newton_iterations - io.newton_iterations) <= max(1, ig.substeps)
+        pg, swg, _, _ = g.get_state()
+        po, swo, _, _ = o.get_state()
+        assert rel_err(pg, po) <= 1e-6 and np.abs(swg - swo).max() <= 1e-6
+        if not expect_ok:
+            # a failed step leaves the state where the step started
+            assert np.array_equal(pg, p_start)
+
+
+def test_resume_from_saved_state_is_bit_for_bit(torch_cuda):
+    from paper_1606_00548_gb300.sim import Simulator
+    case = synth.black_oil_case(nx=24, ny=24, nz=6, nsteps=4, dt=10.0, seed=46)
+    a = Simulator(case)
+    for dt in case["dt"]:
+        assert a.step(dt)[0] == 0
+    ref = a.get_state()
+    b = Simulator(case)
+    for dt in case["dt"][:2]:
+        assert b.step(dt)[0] == 0
+    saved = b.get_state()
+    b.close()
+    c = Simulator(case)               # a new handle, as after a restart of the program
+    c.set_state(*saved)
+    for dt in case["dt"][2:]:
+        assert c.step(dt)[0] == 0
+    got = c.get_state()
+    for u, v in zip(got, ref):
+        assert np.array_equal(u, v)
+
+
+@pytest.mark.parametrize("decouple", [0, 1])
+def test_vanishing_coarsest_pivot_is_reported(torch_cuda, decouple):
+    """A Jacobian whose pressure block has a singular leading 2 x 2 block
+    (cells 0 and 1 coupled only to each other, a_00 = a_01 = a_10 = a_11 = 1)
+    gives the Gauss-Jordan elimination of the coarsest level (here the whole
+    64-row pressure block) a zero second pivot.  The setup reports SIM_ENAN
+    instead of building an inverse full of inf / NaN; the handle recovers."""
+    from paper_1606_00548_gb300.sim import SIM_ENAN, SimError, Simulator
+    case = synth.oil_water_case(nx=8, ny=4, nz=2, sigma=0.5, seed=61)
+    g = Simulator(case, decouple=decouple, stage2=0)
+    N, b = g.N, g.b
+    g.assemble(1.0)
+    J0 = g.jacobian()
+    J = J0.reshape(7, b, b, N).copy()
+    for cell in (0, 1):
+        J[:, :, :, cell] = 0.0                  # rows of cells 0 and 1
+    # columns: blocks of other cells that point at cells 0 or 1
+    nx = case["nx"]
+    J[1, :, :, 2] = 0.0                         # cell 2, -x neighbour is cell 1
+    J[3, :, :, 0 + nx] = 0.0                    # cell nx, -y neighbour is cell 0
+    J[3, :, :, 1 + nx] = 0.0
+    J[5, :, :, 0 + nx * case["ny"]] = 0.0       # -z neighbours
+    J[5, :, :, 1 + nx * case["ny"]] = 0.0
+    for cell in (0, 1):
+        J[0, :, :, cell] = np.eye(b)
+    J[2, 0, 0, 0] = 1.0                         # cell 0 -> +x neighbour (cell 1), pressure column
+    J[1, 0, 0, 1] = 1.0                         # cell 1 -> -x neighbour (cell 0)
+    g.set_jacobian(J.reshape(-1))
+    with pytest.raises(SimError) as e:
+        g.precond_setup()
+    assert e.value.status == SIM_ENAN and "pivot" in str(e.value)
+    g.clear_error()
+    g.set_jacobian(J0)
+    g.precond_setup()                           # the assembled Jacobian sets up normally
