@@ -146,16 +146,45 @@ typedef struct {
     double b_norm, r_norm;      /* ||b||, true ||b - J x|| at exit */
 } sim_linear_info;
 
+/* Per-phase figures of a Newton call: device time between CUDA events
+   recorded on the handle's stream (microseconds) and the algorithmic bytes of
+   the phase, i.e. what its kernels must read and write at least once, from
+   the sizes alone (not measured traffic):
+     assembly  read x, the step's accumulation, T, porosity; write R, J:
+               N (7 b^2 + 3 b + 4) 8
+     setup     decoupling reads J, writes Ahat (t bytes per value: 8 FP64,
+               4 mixed) and A_p; ILU(0) / block Jacobi reads Ahat, writes the
+               inverted diagonal blocks; each coarsening reads its level's
+               matrix four times and writes the next level and its map:
+               N (7 b^2 (8 + 2 t) + 7 * 8 + b^2 t) + sum_l (4 w_l n_l 12 + w_{l+1} n_{l+1} 12 + 4 n_l)
+     solve     per FGMRES iteration with basis vectors 0..j: the product
+               (7 b^2 + b) 8 N + b N tz (tz: the direction's precision), one
+               CPR application (restriction, V-cycle: three passes over each
+               level's matrix, stage F: pressure columns of Ahat, the ILU
+               blocks, vectors), the Gram-Schmidt passes (3 (j + 1) + 7) n 8
+               (n = b N); per restart the solution update, one product and the
+               residual; BiCGSTAB: two products, two applications and 12
+               vector passes per iteration
+     update    read dx, x; write x: 3 b N 8
+   The newton_* counts of sim_step_info sum over substeps; the phase fields
+   sum over every Newton iteration of the call (failed substeps included). */
+typedef struct {
+    double assemble_us, setup_us, solve_us, update_us;
+    double assemble_bytes, setup_bytes, solve_bytes, update_bytes;
+} sim_phase_info;
+
 typedef struct {
     int32_t newton_iterations;  /* linear solves performed */
     int32_t linear_iterations;
     int32_t converged;
     int32_t linear_failures;
     double cnv;
+    sim_phase_info phase;
 } sim_newton_info;
 
 typedef struct {
     int32_t cuts, newton_iterations, linear_iterations, substeps, ok;
+    sim_phase_info phase;
 } sim_step_info;
 
 typedef struct {
@@ -194,6 +223,13 @@ sim_status sim_newton_solve(sim_t *s, double dt, sim_newton_info *info);
 /* One Newton iteration at the current iterate: assemble, test CNV, solve
    J dx = -R, update.  info->converged = 1 means CNV already met (no solve). */
 sim_status sim_newton_step(sim_t *s, double dt, sim_newton_info *info);
+/* Accept the current iterate as the converged state of a time step of
+   length dt: the well rates of the last assembly are added to the cumulative
+   well masses (times dt) and the next step starts from it (its accumulation
+   terms are formed).  For callers that drive Newton themselves with
+   sim_newton_step (the converged x of Algorithm 1 is the step's solution);
+   sim_step does this after every converged substep. */
+sim_status sim_accept_step(sim_t *s, double dt);
 /* Solve J x = b with the current Jacobian to ||b - J x|| <= lin_tol ||b||
    (FGMRES or BiCGSTAB per options.krylov, with the configured
    preconditioner).  b_dev, x_dev: device pointers, N*b doubles each,
@@ -295,7 +331,10 @@ sim_status sim_autotune(sim_t *s, double dt);
    product y = S x of sim_spmv; 1: one CPR application as in sim_precond_apply
    (set up first if needed).  Operands are the handle's own work vectors
    (zeroed), so the caller's data are untouched; the eviction buffer is
-   allocated and freed inside the call.  *us = average microseconds per launch. */
+   allocated and freed inside the call.  which = 2: one FGMRES Arnoldi
+   orthogonalisation step (the Gram-Schmidt passes against min(16, m) basis
+   vectors and the normalisation of the new one), as inside a restart cycle.
+   *us = average microseconds per launch. */
 sim_status sim_time_op(sim_t *s, int32_t which, int32_t reps, double *us);
 
 /* ---- ensemble (no paper counterpart) ----
@@ -358,9 +397,10 @@ int32_t sim_learned_available(sim_t *s);
 int64_t sim_learned_fallbacks(sim_t *s);
 
 /* Diagnostics (no paper counterpart): FP64 and FP32 fused-multiply-add rates
-   of the current device, measured with independent FMA chains and CUDA
-   events; the roofline of the FP64-bound kernels is taken against the FP64
-   rate.  Allocates a small scratch buffer; synchronises the device. */
+   of the current device, measured with independent FMA chains (8 or 16 per
+   thread, 4 or 8 blocks of 256 threads per SM; the best shape is reported)
+   and CUDA events; the roofline of the FP64-bound kernels is taken against
+   the FP64 rate.  Allocates a small scratch buffer; synchronises the device. */
 sim_status sim_probe_fma_rates(double *fp64_fma_per_s, double *fp32_fma_per_s);
 
 const char *sim_last_error(sim_t *s);   /* s may be NULL: last create error */

@@ -1226,7 +1226,7 @@ void ora_ilu_dinv(const ora_sim *s, double *dinv) { memcpy(dinv, s->dinv, sizeof
 
 /* ------------------------------------------------------------------------ */
 /* right-preconditioned FGMRES(m) with classical Gram-Schmidt + one full     */
-/* reorthogonalisation, Givens rotations, zero initial guess (Alg. 1 step 4) */
+/* reorthogonalisation, Givens rotations, zero initial guess (the inexact solve of Algorithm 1, Eq. 13) */
 /* ------------------------------------------------------------------------ */
 static double dot(const double *a, const double *b, int n) { double t = 0.0; for (int i = 0; i < n; i++) t += a[i] * b[i]; return t; }
 

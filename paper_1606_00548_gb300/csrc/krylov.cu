@@ -643,6 +643,27 @@ static sim_status enqueue_cycle(sim_t *s) {
     return SIM_OK;
 }
 
+// One Arnoldi orthogonalisation step of w against basis vectors 0..nv-1 of V
+// and the normalisation into V[nv], as inside a restart cycle (measurement
+// only: sim_time_op clears ctl->done and poisons ctl->tol first, so no
+// convergence test stops it).
+sim_status k_orth_step(sim_t *s, int nv) {
+    const long n = (long)s->N * s->b;
+    KrylovCtl *ctl = s->ctl;
+    const int *done = &ctl->done;
+    OrthDispatch<SIM_MAX_M>::dots(nv, s->stream, s->V, s->w, n, s->red, s->ticket, ctl->h, done);
+    SIM_LAUNCHED(s);
+    OrthDispatch<SIM_MAX_M>::orth(nv, s->stream, s->V, s->w, n, ctl->h, s->red, s->ticket, ctl->h2, done, s->opt.orth);
+    SIM_LAUNCHED(s);
+    OrthDispatch<SIM_MAX_M>::norm(nv, s->stream, s->V, s->w, n, s->m, s->red, s->ticket, ctl, s->opt.orth);
+    SIM_LAUNCHED(s);
+    scale_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(s->w, s->V + (size_t)nv * n, n, ctl, 0);
+    SIM_LAUNCHED(s);
+    return SIM_OK;
+}
+
+double k_orth_step_bytes(const sim_t *s, int nv) { return (3.0 * nv + 7) * (double)s->N * s->b * 8; }
+
 sim_status k_fgmres(sim_t *s, const double *b, double *x, sim_linear_info *info) {
     const long n = (long)s->N * s->b;
     const bool zf = sim_mixed(s);

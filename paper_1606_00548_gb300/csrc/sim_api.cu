@@ -6,6 +6,8 @@
 #include <cstring>
 #include <set>
 
+#include <algorithm>
+
 #include "sim_internal.cuh"
 
 static thread_local std::string g_create_error;
@@ -42,17 +44,23 @@ void sim_free(sim_t *s, void *p) {
 }
 
 namespace {
-// independent FMA chains, no memory traffic except one store per thread
-template <typename T>
+// NC independent FMA chains per thread, no memory traffic except one store
+// per thread; each chain has its own multiplier so no two chains share all
+// their operands
+template <typename T, int NC>
 __global__ void fma_probe_kernel(T *out, int iters) {
-    T a0 = threadIdx.x * (T)1e-3, a1 = a0 + (T)1, a2 = a0 + (T)2, a3 = a0 + (T)3;
-    T a4 = a0 + (T)4, a5 = a0 + (T)5, a6 = a0 + (T)6, a7 = a0 + (T)7;
-    const T m = (T)0.9999999, c = (T)1e-7;
+    T a[NC], m[NC];
+#pragma unroll
+    for (int c = 0; c < NC; c++) { a[c] = threadIdx.x * (T)1e-3 + (T)c; m[c] = (T)0.9999999 - (T)c * (T)1e-9; }
+    const T k = (T)1e-7;
     for (int i = 0; i < iters; i++) {
-        a0 = fma(a0, m, c); a1 = fma(a1, m, c); a2 = fma(a2, m, c); a3 = fma(a3, m, c);
-        a4 = fma(a4, m, c); a5 = fma(a5, m, c); a6 = fma(a6, m, c); a7 = fma(a7, m, c);
+#pragma unroll
+        for (int c = 0; c < NC; c++) a[c] = fma(a[c], m[c], k);
     }
-    out[blockIdx.x * blockDim.x + threadIdx.x] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+    T t = 0;
+#pragma unroll
+    for (int c = 0; c < NC; c++) t += a[c];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = t;
 }
 __global__ void widen_kernel(const float *__restrict__ a, double *__restrict__ b, long n) {
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) b[i] = (double)a[i];
@@ -95,6 +103,7 @@ void sim_destroy(sim_t *s) {
     if (s->bicg_exec) cudaGraphExecDestroy(s->bicg_exec);
     for (void *p : s->allocs) cudaFree(p);
     if (s->h_pinned) cudaFreeHost(s->h_pinned);
+    for (cudaEvent_t &e : s->pev) if (e) cudaEventDestroy(e);
     if (s->ctl_host) cudaFreeHost(s->ctl_host);
     if (s->bctl_host) cudaFreeHost(s->bctl_host);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
@@ -291,6 +300,13 @@ sim_status sim_create(const sim_grid *g, const sim_rock *r, const sim_fluid *f, 
         sim_destroy(s);
         return sim_fail(nullptr, SIM_ENOMEM, "pinned host allocation failed");
     }
+    for (cudaEvent_t &e : s->pev) {
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            e = nullptr;
+            sim_destroy(s);
+            return sim_fail(nullptr, SIM_ECUDA, "event creation failed");
+        }
+    }
     // a stream-ordered memory pool that keeps freed AMG buffers for reuse
     int dev = 0;
     cudaGetDevice(&dev);
@@ -454,10 +470,104 @@ static sim_status forcing_term(sim_t *s, const Forcing &f, double bnorm, double 
     return SIM_OK;
 }
 
+// ---- per-phase figures of a Newton iteration (sim_phase_info) ----------------
+// algorithmic bytes from the sizes alone (the model stated in sim.h)
+static double apply_bytes_per_value(const sim_t *s) { return sim_mixed(s) ? 4.0 : 8.0; }
+
+static double bytes_assembly(const sim_t *s) {
+    const double N = s->N, b = s->b;
+    return N * (7 * b * b + 3 * b + 4) * 8;
+}
+
+static double bytes_update(const sim_t *s) { return 3.0 * s->b * (double)s->N * 8; }
+
+static double bytes_setup(const sim_t *s) {
+    const double N = s->N, b = s->b, t = apply_bytes_per_value(s);
+    double v = N * (7 * b * b * (8 + 2 * t) + 7 * 8 + b * b * t);
+    const int nl = (int)s->lev.size();
+    for (int l = 0; l + 1 < nl; l++) {
+        const double n = s->lev[l].n, w = s->lev[l].width;
+        const double nn = s->lev[l + 1].n, wn = s->lev[l + 1].width;
+        v += 4 * w * n * 12 + wn * nn * 12 + 4 * n;
+    }
+    return v;
+}
+
+// one CPR application (two-stage; the three-stage form adds one stage F and
+// its residual)
+static double bytes_apply(const sim_t *s) {
+    const double N = s->N, b = s->b, t = apply_bytes_per_value(s);
+    double v = N * (8 * b + b * t + t);                       // restriction
+    const int nl = (int)s->lev.size();
+    for (int l = 0; l < nl; l++) {
+        const double n = s->lev[l].n;
+        if (l + 1 == nl) { v += n * n * 8 + 2 * n * t; break; }   // dense coarsest product
+        const double w = s->lev[l].width;
+        v += 3 * w * n * (l == 0 ? t : 4 + t) + 6 * n * t;      // smoothing, residual, prolongation
+    }
+    const double stage_f = N * (8 * b + b * b * t + 7 * b * t + t + b * t)      // r - Ahat x1 (pressure columns)
+                         + N * (7 * b * b * t + b * b * t + 3 * b * t + b * t); // red-black ILU(0) sweeps
+    v += stage_f;
+    if (s->opt.cpr_stages == 3) v += stage_f + N * 7 * b * b * t;
+    return v;
+}
+
+static double bytes_solve(const sim_t *s, const sim_linear_info &li) {
+    const double N = s->N, b = s->b, n = b * N;
+    const double tz = sim_mixed(s) ? 4.0 : 8.0;
+    const double spmv = (7 * b * b + b) * 8 * N + b * N * tz;
+    const double apply = s->opt.precond == SIM_PRECOND_CPR ? bytes_apply(s) : N * (b * b * 8 + 2 * b * 8);
+    if (s->opt.krylov == SIM_KRYLOV_BICGSTAB)
+        return li.iterations * (2 * spmv + 2 * apply + 12 * n * 8) + (li.restarts + 1) * (spmv + 3 * n * 8);
+    double v = 0.0;
+    int left = li.iterations;
+    const int cycles = li.restarts + 1;
+    for (int c = 0; c < cycles; c++) {
+        const int k = (c + 1 == cycles) ? left : (left < s->m ? left : s->m);
+        for (int j = 0; j < k; j++) v += spmv + apply + (3.0 * (j + 1) + 7) * n * 8;
+        v += k * n * tz + 2 * n * 8 + spmv + 3 * n * 8;    // x += Z y, then r = b - J x
+        left -= k;
+    }
+    return v;
+}
+
+static void phase_add(sim_phase_info *a, const sim_phase_info &b) {
+    a->assemble_us += b.assemble_us; a->setup_us += b.setup_us; a->solve_us += b.solve_us; a->update_us += b.update_us;
+    a->assemble_bytes += b.assemble_bytes; a->setup_bytes += b.setup_bytes;
+    a->solve_bytes += b.solve_bytes; a->update_bytes += b.update_bytes;
+}
+
+static double event_us(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) { (void)cudaGetLastError(); return 0.0; }
+    return 1e3 * ms;
+}
+
+// assemble and test CNV, with the assembly phase marked by pev[0], pev[1]
+static sim_status assemble_and_test(sim_t *s, double dt, double *cnv, double *wcnv, sim_phase_info *ph) {
+    SIM_CK(s, cudaEventRecord(s->pev[0], s->stream));
+    if (k_assemble(s, dt) != SIM_OK) return s->err;
+    if (k_cnv(s, dt, cnv, wcnv) != SIM_OK) return s->err;
+    SIM_CK(s, cudaEventRecord(s->pev[1], s->stream));
+    SIM_CK(s, cudaEventSynchronize(s->pev[1]));
+    ph->assemble_us += event_us(s->pev[0], s->pev[1]);
+    ph->assemble_bytes += bytes_assembly(s);
+    return SIM_OK;
+}
+
 // solve J dx = -R and update; *lin receives the linear info.  With a forcing
-// state the tolerance is its theta_l, else lin_tol.
-static sim_status solve_and_update(sim_t *s, sim_linear_info *lin, bool *finite_ok, Forcing *f = nullptr) {
+// state the tolerance is its theta_l, else lin_tol.  The preconditioner
+// setup, the solve and the update are marked by pev[1..4] into *ph.
+static sim_status solve_and_update(sim_t *s, sim_linear_info *lin, bool *finite_ok, sim_phase_info *ph,
+                                   Forcing *f = nullptr) {
     const long n = (long)s->N * s->b;
+    SIM_CK(s, cudaEventRecord(s->pev[1], s->stream));
+    if (!s->precond_ready) {
+        if (cpr_setup(s) != SIM_OK) return s->err;
+        ph->setup_bytes += s->opt.precond == SIM_PRECOND_CPR ? bytes_setup(s)
+                                                             : (double)s->N * s->b * s->b * 8 * 9;   // block Jacobi
+    }
+    SIM_CK(s, cudaEventRecord(s->pev[2], s->stream));
     negate_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(s->R, s->bl, n);
     SIM_LAUNCHED(s);
     if (k_well_rhs(s, s->bl) != SIM_OK) return s->err;
@@ -468,6 +578,8 @@ static sim_status solve_and_update(sim_t *s, sim_linear_info *lin, bool *finite_
         if (forcing_term(s, *f, bnorm, &s->theta) != SIM_OK) return s->err;
     }
     const sim_status st = k_linear_solve(s, s->bl, s->dx, lin);
+    SIM_CK(s, cudaEventRecord(s->pev[3], s->stream));
+    ph->solve_bytes += bytes_solve(s, *lin);
     const double theta_used = s->theta;
     s->theta = s->opt.lin_tol;
     if (f && s->opt.forcing != SIM_FORCING_FIXED && st == SIM_OK) {
@@ -484,6 +596,12 @@ static sim_status solve_and_update(sim_t *s, sim_linear_info *lin, bool *finite_
     if (!ok) return SIM_OK;
     if (k_well_update(s, s->dx) != SIM_OK) return s->err;
     if (k_newton_update(s, s->dx) != SIM_OK) return s->err;
+    SIM_CK(s, cudaEventRecord(s->pev[4], s->stream));
+    SIM_CK(s, cudaEventSynchronize(s->pev[4]));
+    ph->setup_us += event_us(s->pev[1], s->pev[2]);
+    ph->solve_us += event_us(s->pev[2], s->pev[3]);
+    ph->update_us += event_us(s->pev[3], s->pev[4]);
+    ph->update_bytes += bytes_update(s);
     s->newton_total++;
     return SIM_OK;
 }
@@ -493,14 +611,13 @@ sim_status sim_newton_step(sim_t *s, double dt, sim_newton_info *info) {
     if (!(dt > 0)) return sim_fail(s, SIM_EINVAL, "dt must be positive");
     sim_newton_info ni;
     memset(&ni, 0, sizeof(ni));
-    if (k_assemble(s, dt) != SIM_OK) return s->err;
     double cnv, wcnv;
-    if (k_cnv(s, dt, &cnv, &wcnv) != SIM_OK) return s->err;
+    if (assemble_and_test(s, dt, &cnv, &wcnv, &ni.phase) != SIM_OK) return s->err;
     ni.cnv = cnv;
     if (cnv <= s->opt.newton_tol && wcnv <= s->opt.newton_tol) { ni.converged = 1; if (info) *info = ni; return SIM_OK; }
     sim_linear_info li;
     bool fin = true;
-    if (solve_and_update(s, &li, &fin) != SIM_OK) return s->err;
+    if (solve_and_update(s, &li, &fin, &ni.phase) != SIM_OK) return s->err;
     ni.newton_iterations = 1;
     ni.linear_iterations = li.iterations;
     ni.linear_failures = !li.converged;
@@ -513,16 +630,15 @@ static int newton_solve(sim_t *s, double dt, sim_newton_info *ni) {
     memset(ni, 0, sizeof(*ni));
     Forcing f;
     for (int l = 0;; l++) {
-        if (k_assemble(s, dt) != SIM_OK) return -1;
         double cnv, wcnv;
-        if (k_cnv(s, dt, &cnv, &wcnv) != SIM_OK) return -1;
+        if (assemble_and_test(s, dt, &cnv, &wcnv, &ni->phase) != SIM_OK) return -1;
         ni->cnv = cnv;
         if (!(cnv == cnv) || !(wcnv == wcnv)) return 2;
         if (cnv <= s->opt.newton_tol && wcnv <= s->opt.newton_tol) { ni->converged = 1; return 0; }
         if (l >= s->opt.newton_max) return 1;
         sim_linear_info li;
         bool fin = true;
-        if (solve_and_update(s, &li, &fin, &f) != SIM_OK) return -1;
+        if (solve_and_update(s, &li, &fin, &ni->phase, &f) != SIM_OK) return -1;
         ni->newton_iterations++;
         ni->linear_iterations += li.iterations;
         ni->linear_failures += !li.converged;
@@ -540,6 +656,22 @@ sim_status sim_newton_solve(sim_t *s, double dt, sim_newton_info *info) {
     return rc == 0 ? SIM_OK : (rc == 2 ? SIM_ENAN : SIM_ENOCONV_NEWTON);
 }
 
+// the current iterate becomes the accepted state of a step of length dt
+static sim_status accept_step(sim_t *s, double dt) {
+    SIM_CK(s, cudaMemcpyAsync(s->h_pinned, s->qtot, sizeof(double) * 3, cudaMemcpyDeviceToHost, s->stream));
+    SIM_CK(s, cudaStreamSynchronize(s->stream));
+    for (int c = 0; c < 3; c++) s->cum_well[c] += dt * s->h_pinned[c];
+    return begin_step(s);
+}
+
+sim_status sim_accept_step(sim_t *s, double dt) {
+    CHECK_HANDLE(s);
+    if (!(dt > 0)) return sim_fail(s, SIM_EINVAL, "dt must be positive");
+    if (accept_step(s, dt) != SIM_OK) return s->err;
+    SIM_CK(s, cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}
+
 sim_status sim_step(sim_t *s, double dt, sim_step_info *info) {
     CHECK_HANDLE(s);
     if (!(dt > 0)) return sim_fail(s, SIM_EINVAL, "dt must be positive");
@@ -552,15 +684,13 @@ sim_status sim_step(sim_t *s, double dt, sim_step_info *info) {
         sim_newton_info ni;
         const int rc = newton_solve(s, h, &ni);
         if (rc < 0) return s->err;
+        phase_add(&si.phase, ni.phase);
         si.newton_iterations += ni.newton_iterations;
         si.linear_iterations += ni.linear_iterations;
         if (rc == 0) {
-            SIM_CK(s, cudaMemcpyAsync(s->h_pinned, s->qtot, sizeof(double) * 3, cudaMemcpyDeviceToHost, s->stream));
-            SIM_CK(s, cudaStreamSynchronize(s->stream));
-            for (int c = 0; c < 3; c++) s->cum_well[c] += h * s->h_pinned[c];
+            if (accept_step(s, h) != SIM_OK) return s->err;
             remaining -= h;
             si.substeps++;
-            if (begin_step(s) != SIM_OK) return s->err;
         } else {
             SIM_CK(s, cudaMemcpyAsync(s->x, s->x_old, sizeof(double) * s->N * s->b, cudaMemcpyDeviceToDevice, s->stream));
             SIM_CK(s, cudaMemcpyAsync(s->ph, s->ph_old, s->N, cudaMemcpyDeviceToDevice, s->stream));
@@ -616,7 +746,8 @@ sim_status sim_spmv(sim_t *s, const double *x_dev, double *y_dev) {
 }
 sim_status sim_time_op(sim_t *s, int32_t which, int32_t reps, double *us) {
     CHECK_HANDLE(s);
-    if (!us || reps < 1 || which < 0 || which > 1) return sim_fail(s, SIM_EINVAL, "sim_time_op: bad arguments");
+    if (!us || reps < 1 || which < 0 || which > 2) return sim_fail(s, SIM_EINVAL, "sim_time_op: bad arguments");
+    const int nv = s->m < 16 ? s->m : 16;
     const long n = (long)s->N * s->b;
     if (which == 1 && !s->precond_ready && cpr_setup(s) != SIM_OK) return s->err;
     // a buffer twice the L2 size, rewritten before every timed launch, so that
@@ -624,16 +755,20 @@ sim_status sim_time_op(sim_t *s, int32_t which, int32_t reps, double *us) {
     const size_t flush_bytes = 256u << 20;
     void *flush = sim_alloc(s, flush_bytes);
     if (!flush) return s->err;
-    SIM_CK(s, cudaMemsetAsync(s->V, 0, sizeof(double) * n, s->stream));
+    SIM_CK(s, cudaMemsetAsync(s->V, 0, sizeof(double) * n * (which == 2 ? nv + 1 : 1), s->stream));
+    if (which == 2) SIM_CK(s, cudaMemsetAsync(s->w, 0, sizeof(double) * n, s->stream));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     sim_status st = SIM_OK;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = SIM_ECUDA;
     double total_ms = 0.0;
     for (int r = 0; r < reps && st == SIM_OK; r++) {
         float ms = 0.f;
+        if (which == 2 &&   // no convergence test may stop the step: done = 0, tol = NaN
+            (cudaMemsetAsync(&s->ctl->done, 0, sizeof(int), s->stream) != cudaSuccess ||
+             cudaMemsetAsync(&s->ctl->tol, 0xff, sizeof(double), s->stream) != cudaSuccess)) { st = SIM_ECUDA; break; }
         if (cudaMemsetAsync(flush, r & 0xff, flush_bytes, s->stream) != cudaSuccess ||
             cudaEventRecord(e0, s->stream) != cudaSuccess) { st = SIM_ECUDA; break; }
-        st = which == 0 ? k_spmv(s, s->V, s->w) : cpr_apply(s, s->V, s->Z, nullptr);
+        st = which == 0 ? k_spmv(s, s->V, s->w) : which == 1 ? cpr_apply(s, s->V, s->Z, nullptr) : k_orth_step(s, nv);
         if (st != SIM_OK) break;
         if (cudaEventRecord(e1, s->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
             cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) { st = SIM_ECUDA; break; }
@@ -817,33 +952,42 @@ sim_status sim_learned_pairs(sim_t *s, int32_t k, float *x_dev, float *y_dev) {
 int64_t sim_learned_fallbacks(sim_t *s) { return s ? s->learned_fallbacks : 0; }
 int32_t sim_learned_available(sim_t *s) { return s ? (s->last_cycle_k + 1 < s->m + 1 ? s->last_cycle_k + 1 : s->m + 1) : 0; }
 
+// FMA rate of one launch shape: iters x NC FMAs per thread over the grid
+template <typename T, int NC>
+static double probe_rate(T *buf, int blocks, int threads, int iters) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0); cudaEventCreate(&e1);
+    fma_probe_kernel<T, NC><<<blocks, threads>>>(buf, 16);
+    cudaEventRecord(e0);
+    fma_probe_kernel<T, NC><<<blocks, threads>>>(buf, iters);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0); cudaEventDestroy(e1);
+    return ms > 0.f ? (double)blocks * threads * iters * NC / (ms * 1e-3) : 0.0;
+}
+
 sim_status sim_probe_fma_rates(double *fp64_fma_per_s, double *fp32_fma_per_s) {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return sim_fail(nullptr, SIM_ECUDA, "sim_probe_fma_rates: no CUDA device");
-    const int blocks = sms * 8, threads = 256;
+    const int max_blocks = sms * 8, threads = 256;
     void *buf = nullptr;
-    if (cudaMalloc(&buf, sizeof(double) * blocks * threads) != cudaSuccess)
+    if (cudaMalloc(&buf, sizeof(double) * max_blocks * threads) != cudaSuccess)
         return sim_fail(nullptr, SIM_ENOMEM, "sim_probe_fma_rates: allocation failed");
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0); cudaEventCreate(&e1);
-    float ms = 0.f;
-    const int it64 = 4096, it32 = 16384;
-    fma_probe_kernel<double><<<blocks, threads>>>((double *)buf, 16);
-    cudaEventRecord(e0);
-    fma_probe_kernel<double><<<blocks, threads>>>((double *)buf, it64);
-    cudaEventRecord(e1);
-    cudaEventSynchronize(e1);
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (fp64_fma_per_s) *fp64_fma_per_s = (double)blocks * threads * it64 * 8 / (ms * 1e-3);
-    fma_probe_kernel<float><<<blocks, threads>>>((float *)buf, 16);
-    cudaEventRecord(e0);
-    fma_probe_kernel<float><<<blocks, threads>>>((float *)buf, it32);
-    cudaEventRecord(e1);
-    cudaEventSynchronize(e1);
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (fp32_fma_per_s) *fp32_fma_per_s = (double)blocks * threads * it32 * 8 / (ms * 1e-3);
-    cudaEventDestroy(e0); cudaEventDestroy(e1);
+    // the best of several shapes (chains per thread, blocks per SM): the rate of
+    // the pipe, not of one shape's latency or tail
+    double f64 = 0.0, f32 = 0.0;
+    for (int bps : {4, 8}) {
+        const int blocks = sms * bps;
+        f64 = std::max(f64, probe_rate<double, 8>((double *)buf, blocks, threads, 8192));
+        f64 = std::max(f64, probe_rate<double, 16>((double *)buf, blocks, threads, 4096));
+        f32 = std::max(f32, probe_rate<float, 8>((float *)buf, blocks, threads, 32768));
+        f32 = std::max(f32, probe_rate<float, 16>((float *)buf, blocks, threads, 16384));
+    }
+    if (fp64_fma_per_s) *fp64_fma_per_s = f64;
+    if (fp32_fma_per_s) *fp32_fma_per_s = f32;
     cudaFree(buf);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return sim_fail(nullptr, SIM_ECUDA, std::string("sim_probe_fma_rates: ") + cudaGetErrorString(e));

@@ -115,6 +115,7 @@ struct sim {
     double *scal = nullptr;      // small device scalars
     unsigned int *ticket = nullptr;
     double *h_pinned = nullptr;  // pinned host mirror for small reads
+    cudaEvent_t pev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // phase marks of a Newton iteration
 
     // Krylov
     int m = 0;
@@ -204,6 +205,8 @@ sim_status k_linear_solve(sim_t *s, const double *b, double *x, sim_linear_info 
 sim_status k_diff_norm2(sim_t *s, const double *a, const double *b, long n, double *out);
 sim_status k_norm2(sim_t *s, const double *v, long n, double *out_host);
 sim_status k_spmv_block(sim_t *s, const double *x, double *y, int block);
+sim_status k_orth_step(sim_t *s, int nv);              // measurement: one Arnoldi orthogonalisation step
+double k_orth_step_bytes(const sim_t *s, int nv);      // its algorithmic bytes
 
 // ---- cpr.cu ---------------------------------------------------------------
 sim_status cpr_setup(sim_t *s);

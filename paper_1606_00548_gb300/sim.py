@@ -81,14 +81,23 @@ class sim_linear_info(C.Structure):
                 ("b_norm", C.c_double), ("r_norm", C.c_double)]
 
 
+class sim_phase_info(C.Structure):
+    _fields_ = [("assemble_us", C.c_double), ("setup_us", C.c_double), ("solve_us", C.c_double),
+                ("update_us", C.c_double), ("assemble_bytes", C.c_double), ("setup_bytes", C.c_double),
+                ("solve_bytes", C.c_double), ("update_bytes", C.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 class sim_newton_info(C.Structure):
     _fields_ = [("newton_iterations", C.c_int32), ("linear_iterations", C.c_int32), ("converged", C.c_int32),
-                ("linear_failures", C.c_int32), ("cnv", C.c_double)]
+                ("linear_failures", C.c_int32), ("cnv", C.c_double), ("phase", sim_phase_info)]
 
 
 class sim_step_info(C.Structure):
     _fields_ = [("cuts", C.c_int32), ("newton_iterations", C.c_int32), ("linear_iterations", C.c_int32),
-                ("substeps", C.c_int32), ("ok", C.c_int32)]
+                ("substeps", C.c_int32), ("ok", C.c_int32), ("phase", sim_phase_info)]
 
 
 class sim_stats(C.Structure):
@@ -106,6 +115,7 @@ _SIGS = {
     "sim_step": ([_vp, C.c_double, C.POINTER(sim_step_info)], C.c_int),
     "sim_newton_solve": ([_vp, C.c_double, C.POINTER(sim_newton_info)], C.c_int),
     "sim_newton_step": ([_vp, C.c_double, C.POINTER(sim_newton_info)], C.c_int),
+    "sim_accept_step": ([_vp, C.c_double], C.c_int),
     "sim_linear_solve": ([_vp, _vp, _vp, C.POINTER(sim_linear_info)], C.c_int),
     "sim_set_iterate": ([_vp, _dp, _i8p], C.c_int),
     "sim_get_iterate": ([_vp, _dp, _i8p], C.c_int),
@@ -382,6 +392,9 @@ class Simulator:
         if st not in (SIM_OK, SIM_ENAN):
             _check(self.h, st)
         return st, info
+
+    def accept_step(self, dt):
+        _check(self.h, self.L.sim_accept_step(self.h, float(dt)))
 
     # assembly / linear algebra -------------------------------------------------
     def assemble(self, dt):

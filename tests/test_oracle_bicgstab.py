@@ -8,7 +8,7 @@
   one iteration with x = J^-1 b;
 * BiCGSTAB + CPR (any decoupling / stage count) solves to the LAPACK
   solution;
-* the forcing terms satisfy the defining inequality of Algorithm 1 step 4,
+* the forcing terms satisfy the defining inequality of Algorithm 1's inexact solve (Eq. 13),
   theta_0 = theta_max, safeguards lin_tol <= theta <= theta_max, and at the
   first adaptive iteration choice 2 <= choice 1 (triangle inequality:
   | ||b|| - ||r|| | <= ||b - r||) on identical histories.
@@ -101,7 +101,7 @@ def test_forcing_terms(oracle_lib, forcing, krylov):
     assert len(th) == info.newton_iterations >= 2
     assert th[0] == 0.5                                   # theta_max on the first iteration
     assert (th >= 1e-8).all() and (th <= 0.5).all()
-    assert (rn <= th * bn * (1 + 1e-12)).all()           # ||b - A dx|| <= theta ||b|| (Alg. 1 step 4)
+    assert (rn <= th * bn * (1 + 1e-12)).all()           # ||b - A dx|| <= theta ||b|| (Eq. 13)
     # adaptive: looser than the fixed 1e-8 somewhere, and fewer linear iterations overall
     o2, rc2, info2 = _newton(case, 1.0, forcing=0, krylov=krylov)
     assert rc2 == 0 and info.linear_iterations < info2.linear_iterations
