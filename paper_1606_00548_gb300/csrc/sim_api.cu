@@ -62,6 +62,22 @@ __global__ void fma_probe_kernel(T *out, int iters) {
     for (int c = 0; c < NC; c++) t += a[c];
     out[blockIdx.x * blockDim.x + threadIdx.x] = t;
 }
+// FMA rate of one launch shape: iters x NC FMAs per thread over the grid
+template <typename T, int NC>
+static double probe_rate(T *buf, int blocks, int threads, int iters) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0); cudaEventCreate(&e1);
+    fma_probe_kernel<T, NC><<<blocks, threads>>>(buf, 16);
+    cudaEventRecord(e0);
+    fma_probe_kernel<T, NC><<<blocks, threads>>>(buf, iters);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0); cudaEventDestroy(e1);
+    return ms > 0.f ? (double)blocks * threads * iters * NC / (ms * 1e-3) : 0.0;
+}
+
 __global__ void widen_kernel(const float *__restrict__ a, double *__restrict__ b, long n) {
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) b[i] = (double)a[i];
 }
@@ -951,22 +967,6 @@ sim_status sim_learned_pairs(sim_t *s, int32_t k, float *x_dev, float *y_dev) {
 
 int64_t sim_learned_fallbacks(sim_t *s) { return s ? s->learned_fallbacks : 0; }
 int32_t sim_learned_available(sim_t *s) { return s ? (s->last_cycle_k + 1 < s->m + 1 ? s->last_cycle_k + 1 : s->m + 1) : 0; }
-
-// FMA rate of one launch shape: iters x NC FMAs per thread over the grid
-template <typename T, int NC>
-static double probe_rate(T *buf, int blocks, int threads, int iters) {
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0); cudaEventCreate(&e1);
-    fma_probe_kernel<T, NC><<<blocks, threads>>>(buf, 16);
-    cudaEventRecord(e0);
-    fma_probe_kernel<T, NC><<<blocks, threads>>>(buf, iters);
-    cudaEventRecord(e1);
-    cudaEventSynchronize(e1);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0); cudaEventDestroy(e1);
-    return ms > 0.f ? (double)blocks * threads * iters * NC / (ms * 1e-3) : 0.0;
-}
 
 sim_status sim_probe_fma_rates(double *fp64_fma_per_s, double *fp32_fma_per_s) {
     int dev = 0, sms = 0;

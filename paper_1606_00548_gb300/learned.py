@@ -92,8 +92,8 @@ def evaluate(train_case=None, eval_case=None, train_steps=300, lr=1e-3, pairs_ne
     """Train on train_case, then compare solves on eval_case: FP64 CPR
     (two-stage and CPR-FPF), FP32-preconditioned CPR (both), FP32 CPR + the
     learned stage (all to the same FP64 tolerance)."""
-    train_case = train_case or synth.black_oil_case(nx=128, ny=128, nz=32, sigma=1.0, corr_len=10.0, seed=1004)
-    eval_case = eval_case or synth.black_oil_case(nx=256, ny=256, nz=64, sigma=2.0, corr_len=20.0, seed=1005)
+    train_case = train_case or synth.black_oil_128x128x32()
+    eval_case = eval_case or synth.black_oil_256x256x64_sigma2()
     t0 = time.perf_counter()
     X, Y = collect_pairs(train_case, pairs_newton, pairs_k)
     t_pairs = time.perf_counter() - t0

@@ -258,6 +258,22 @@ def black_oil_400cube(n=400, **kw):
     return black_oil_case(**a)
 
 
+def black_oil_128x128x32(**kw):
+    """Black oil 128x128x32 (524k cells), sigma 1, l = 10 cells: the grid the
+    learned pressure stage is trained on."""
+    a = dict(nx=128, ny=128, nz=32, sigma=1.0, corr_len=10.0, seed=1004)
+    a.update(kw)
+    return black_oil_case(**a)
+
+
+def black_oil_256x256x64_sigma2(**kw):
+    """Black oil 256x256x64 (4.2M cells) with a heavier-tailed field (sigma 2,
+    l = 20 cells): the grid the learned pressure stage is evaluated on."""
+    a = dict(nx=256, ny=256, nz=64, sigma=2.0, corr_len=20.0, seed=1005)
+    a.update(kw)
+    return black_oil_case(**a)
+
+
 def ensemble_members(n_members=64, seed=1003, nsteps=20, dt=1.0, scale=1.0):
     """Uneven oil-water realisations: nx, ny ~ U{32..128}, nz ~ U{8..32}, sigma ~ U[0.5, 2]."""
     u = uniform01(4 * n_members, seed)

@@ -1,0 +1,158 @@
+"""Per-configuration parity of the CUDA path with the oracle, at the sizes of
+the configurations (Algorithm 1 per time step, Eq. 10 backward Euler):
+
+* black oil 100x100x20 (200k cells, 10-day steps): five whole time steps;
+* black oil 400^3 (64M cells): the first 1-day step on the 100^3 corner of the
+  same field (the oracle would need hours for the whole grid);
+* the 64-member oil-water ensemble (uneven grids, here at half the edge
+  lengths): two steps of every member, advanced together by the batch runtime;
+* the learned stage's evaluation grid, black oil 256x256x64 with sigma 2
+  (4.2M cells): one Newton step with plain FP64 CPR, FP32-preconditioned CPR
+  and FP32 CPR with the learned stage.
+
+After every step: pressure <= 1e-6 relative, saturations <= 1e-6 absolute,
+the same phase state, Newton counts within 1, linear iterations within 1 per
+linear solve, the same number of cuts.  The oracle runs in spawned worker
+processes while the GPU side runs here.
+"""
+import concurrent.futures as cf
+import multiprocessing as mp
+
+import numpy as np
+import pytest
+
+import config_jobs as cj
+from gpu_util import rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1606_00548_gb300 import build
+    build.build()
+    return torch
+
+
+@pytest.fixture(scope="module")
+def jobs(torch_cuda, oracle_lib):
+    ex = cf.ProcessPoolExecutor(max_workers=7, mp_context=mp.get_context("spawn"))
+    futs = {
+        "bo100": ex.submit(cj.run_steps, "black_oil_100x100x20", 5),
+        "bo400": ex.submit(cj.run_steps, "black_oil_400cube_corner100", 1),
+        "eval": ex.submit(cj.run_newton, "learned_eval_256x256x64"),
+    }
+    for q in range(4):
+        futs[f"ens{q}"] = ex.submit(cj.run_members, 0.5, 2, 16 * q, 16)
+    yield futs
+    ex.shutdown(wait=False, cancel_futures=True)
+
+
+def _compare_step(g_state, row, ng, lg, cg, where):
+    pg, swg, x3g, phg = g_state
+    assert row["rc"] == 0, where
+    assert np.array_equal(phg, row["ph"]), (where, int((phg != row["ph"]).sum()))
+    dp = rel_err(pg, row["p"])
+    dsw = np.abs(swg - row["sw"]).max()
+    sat = row["ph"] == 1
+    dsg = np.abs(np.where(sat, x3g - row["x3"], 0.0)).max()
+    dpb = np.abs(np.where(sat, 0.0, x3g - row["x3"])).max() / max(np.abs(row["p"]).max(), 1.0)
+    assert dp <= 1e-6 and dsw <= 1e-6 and dsg <= 1e-6 and dpb <= 1e-6, (where, dp, dsw, dsg, dpb)
+    assert abs(ng - row["newton"]) <= 1, (where, ng, row["newton"])
+    assert abs(lg - row["linear"]) <= max(ng, row["newton"]), (where, lg, row["linear"])
+    assert cg == row["cuts"], (where, cg, row["cuts"])
+
+
+def _gpu_steps(case, nsteps):
+    from paper_1606_00548_gb300.sim import Simulator
+    g = Simulator(case)
+    out = []
+    for k in range(nsteps):
+        st, info = g.step(case["dt"][k])
+        assert st == 0
+        out.append((g.get_state(), info.newton_iterations, info.linear_iterations, info.cuts))
+    g.close()
+    return out
+
+
+def test_black_oil_100x100x20_five_steps(jobs):
+    case = cj.case_of("black_oil_100x100x20")
+    rows_g = _gpu_steps(case, 5)
+    rows_o = jobs["bo100"].result()
+    for k, (gs, ng, lg, cg) in enumerate(rows_g):
+        _compare_step(gs, rows_o[k], ng, lg, cg, f"step {k}")
+
+
+def test_black_oil_400cube_first_step_on_the_100cube_corner(jobs):
+    case = cj.case_of("black_oil_400cube_corner100")
+    (gs, ng, lg, cg), = _gpu_steps(case, 1)
+    _compare_step(gs, jobs["bo400"].result()[0], ng, lg, cg, "step 0")
+
+
+def test_ensemble_members_two_steps(jobs):
+    from paper_1606_00548_gb300 import synth
+    from paper_1606_00548_gb300.sim import Batch, Simulator
+    members = synth.ensemble_members(64, nsteps=2, dt=1.0, scale=0.5)
+    sims = [Simulator(c) for c in members]
+    batch = Batch(sims)
+    rows_g = [[] for _ in members]
+    for k in range(2):
+        sts, infos = batch.step(1.0)
+        for m, (st, inf) in enumerate(zip(sts, infos)):
+            assert st == 0, m
+            p, sw, _, _ = sims[m].get_state()
+            rows_g[m].append((p, sw, inf.newton_iterations, inf.linear_iterations, inf.cuts))
+    batch.close()
+    rows_o = sum((jobs[f"ens{q}"].result() for q in range(4)), [])
+    assert len(rows_o) == 64
+    for m in range(64):
+        for k in range(2):
+            p, sw, ng, lg, cg = rows_g[m][k]
+            ro = rows_o[m][k]
+            assert ro["rc"] == 0
+            assert rel_err(p, ro["p"]) <= 1e-6 and np.abs(sw - ro["sw"]).max() <= 1e-6, (m, k)
+            assert abs(ng - ro["newton"]) <= 1 and cg == ro["cuts"], (m, k, ng, ro["newton"])
+            assert abs(lg - ro["linear"]) <= max(ng, ro["newton"]), (m, k, lg, ro["linear"])
+
+
+def test_learned_evaluation_grid_newton_step(jobs, torch_cuda):
+    """One Newton step on the 4.2M-cell evaluation field: plain FP64 CPR
+    (linear iterations within 1 of the oracle), FP32-preconditioned CPR and
+    FP32 CPR with a (briefly trained) learned stage reach the oracle's
+    iterate to the same tolerances."""
+    from paper_1606_00548_gb300 import learned, synth
+    from paper_1606_00548_gb300.sim import Net, Simulator
+    from gpu_util import to_cm
+    case = cj.case_of("learned_eval_256x256x64")
+    N = case["nx"] * case["ny"] * case["nz"]
+    X, Y = learned.collect_pairs(synth.black_oil_128x128x32(), newton_iterations=1, k=8)
+    net_t = Net(128, 128, 32, seed=0)
+    learned.train(net_t, X, Y, steps=40)
+    params = net_t.get_params()
+    net_t.close()
+    del X, Y
+    net = Net(case["nx"], case["ny"], case["nz"], seed=0)
+    net.set_params(params)
+    ro = jobs["eval"].result()
+    assert ro["rc"] == 0
+    b = 3
+    xo = to_cm(ro["x"], N, b)
+    for name, prec, use_net in (("fp64_cpr", 0, False), ("mixed_cpr", 1, False), ("mixed_cpr_learned", 1, True)):
+        g = Simulator(case, precision=prec)
+        if use_net:
+            g.set_learned_stage(net, True)
+        st, info = g.newton_step(case["dt"][0])
+        assert st == 0, name
+        xg, phg = g.get_iterate()
+        g.close()
+        assert np.array_equal(phg, ro["ph"]), name
+        assert rel_err(xg[:N], xo[:N]) <= 1e-6, name
+        assert np.abs(xg[N:2 * N] - xo[N:2 * N]).max() <= 1e-6, name
+        sat = ro["ph"] == 1
+        assert np.abs(np.where(sat, xg[2 * N:] - xo[2 * N:], 0.0)).max() <= 1e-6, name
+        if name == "fp64_cpr":
+            assert abs(info.linear_iterations - ro["linear"]) <= 1, (info.linear_iterations, ro["linear"])
+    net.close()
