@@ -339,18 +339,42 @@ sim_status sim_time_op(sim_t *s, int32_t which, int32_t reps, double *us);
 
 /* ---- ensemble (no paper counterpart) ----
    Independent simulators (e.g. geological realisations on grids of different
-   sizes) advanced together: a pool of persistent host threads runs the
-   members' time steps concurrently, each member on its own CUDA stream
-   (members must own distinct streams), so their kernels overlap on the GPU.
-   The batch does not own the members. */
+   sizes) advanced together on one GPU.  The batch does not own the members;
+   members must own distinct CUDA streams and live on the current device.
+
+   SIM_BATCH_LOCKSTEP (the default where every member allows it: the same
+   block size, precision and solver options, two-stage CPR with one V-cycle,
+   FGMRES with a fixed forcing term, no learned stage, no rate-controlled
+   wells, at most 16 AMG levels): the members' Newton loops advance in
+   rounds.  Per round each member in its step assembles and tests CNV
+   (accepting converged substeps and halving failed ones, as sim_step does)
+   and sets up its preconditioner -- concurrently, one worker thread and
+   stream per member -- and then one batched FGMRES solves every member's
+   Newton system at once: each Krylov operation (the block SpMV, each CPR
+   stage, each Gram-Schmidt pass) is a single launch over all members, a
+   restart cycle is one CUDA graph on the batch's own stream, and a member
+   whose solve has converged drops out of the remaining launches.  Each
+   member computes what its own sim_step computes.
+   SIM_BATCH_CONCURRENT: each member's sim_step runs on its own stream from
+   a pool worker (the members' kernels overlap on the device). */
+#define SIM_BATCH_LOCKSTEP 0
+#define SIM_BATCH_CONCURRENT 1
 typedef struct sim_batch sim_batch_t;
 /* nthreads <= 0: min(n, 64) worker threads */
 sim_status sim_batch_create(int32_t n, sim_t *const *members, int32_t nthreads, sim_batch_t **out);
 void sim_batch_destroy(sim_batch_t *b);
-/* sim_step(member k, dt[k]) for every member; infos / member_status (n
+/* SIM_EINVAL for an unknown mode, or LOCKSTEP when the members do not allow it */
+sim_status sim_batch_set_mode(sim_batch_t *b, int32_t mode);
+int32_t sim_batch_mode(sim_batch_t *b);
+/* one time step dt[k] for every member k; infos / member_status (n
    entries, may be NULL) receive each member's result; returns the first
-   non-OK member status. */
+   non-OK member status.  In lockstep mode the solve time of a round is
+   counted in the phase info of every member that solved in it. */
 sim_status sim_batch_step(sim_batch_t *b, const double *dt, sim_step_info *infos, sim_status *member_status);
+/* lockstep rounds and member solves so far, and kernels launched by the
+   batched solves (graph nodes included) */
+sim_status sim_batch_stats(sim_batch_t *b, int64_t *rounds, int64_t *solves, int64_t *launches);
+const char *sim_batch_last_error(sim_batch_t *b);
 
 /* ---- learned pressure stage (no paper counterpart) ----
    A 3-D convolutional network: 4 layers of 3x3x3 kernels (zero padding),

@@ -994,6 +994,17 @@ __device__ __forceinline__ void issue_prefetch(const L2Prefetch &pf) {
 
 // f0 = first row of L times r (quasi-IMPES: L_00 = 1); e0 = f0 / l1
 template <int B, typename T>
+__device__ __forceinline__ void restrict_p_row(int N, const double *__restrict__ r, const T *__restrict__ wT, int full,
+                                               const T *__restrict__ dinv0, T *__restrict__ f0, T *__restrict__ e0,
+                                               int i) {
+    const T r0 = full ? wT[i] * (T)r[i] : (T)r[i];
+    T t = r0 + wT[(long)N + i] * (T)r[(long)N + i];
+    if (B == 3) t += wT[2L * N + i] * (T)r[2L * N + i];
+    f0[i] = t;
+    e0[i] = t * dinv0[i];
+}
+
+template <int B, typename T>
 __global__ void restrict_p_kernel(int N, const double *__restrict__ r, const T *__restrict__ wT, int full,
                                   const T *__restrict__ dinv0, T *__restrict__ f0, T *__restrict__ e0, const L2Prefetch pf,
                                   const int *done) {
@@ -1001,11 +1012,7 @@ __global__ void restrict_p_kernel(int N, const double *__restrict__ r, const T *
     issue_prefetch(pf);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const T r0 = full ? wT[i] * (T)r[i] : (T)r[i];
-    T t = r0 + wT[(long)N + i] * (T)r[(long)N + i];
-    if (B == 3) t += wT[2L * N + i] * (T)r[2L * N + i];
-    f0[i] = t;
-    e0[i] = t * dinv0[i];
+    restrict_p_row<B, T>(N, r, wT, full, dinv0, f0, e0, i);
 }
 
 // r = f - A e (one thread per fine row: coalesced stencil / ELL reads)
@@ -1018,14 +1025,11 @@ __global__ void amg_resid_kernel(Mat<T> A, const T *__restrict__ f, const T *__r
     r[i] = f[i] - row_dot(A, i, e);
 }
 
-// f_c = P^T r (members in ascending order); e_c = f_c / l1 (coarse pre-smoothing)
+// f_c = P^T r of coarse row I
 template <typename T>
-__global__ void amg_restrict_kernel(const T *__restrict__ r, const int *__restrict__ moff, const int *__restrict__ mem,
-                                    int nc, T *__restrict__ fc, T *__restrict__ ec, const T *__restrict__ dinvc,
-                                    const int *done) {
-    if (skip(done)) return;
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
-    if (I >= nc) return;
+__device__ __forceinline__ void amg_restrict_row(const T *__restrict__ r, const int *__restrict__ moff,
+                                                 const int *__restrict__ mem, T *__restrict__ fc, T *__restrict__ ec,
+                                                 const T *__restrict__ dinvc, int I) {
     // members in batches of 8: the batch's indices, then its gathers, then the
     // sum in member order (a plain loop would wait on each load in turn)
     const int q0 = moff[I], q1 = moff[I + 1];
@@ -1044,6 +1048,18 @@ __global__ void amg_restrict_kernel(const T *__restrict__ r, const int *__restri
     fc[I] = s;
     if (ec) ec[I] = s * dinvc[I];
 }
+
+// f_c = P^T r (members in ascending order); e_c = f_c / l1 (coarse pre-smoothing)
+template <typename T>
+__global__ void amg_restrict_kernel(const T *__restrict__ r, const int *__restrict__ moff, const int *__restrict__ mem,
+                                    int nc, T *__restrict__ fc, T *__restrict__ ec, const T *__restrict__ dinvc,
+                                    const int *done) {
+    if (skip(done)) return;
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nc) return;
+    amg_restrict_row<T>(r, moff, mem, fc, ec, dinvc, I);
+}
+
 
 // e += P e_c
 template <typename T>
@@ -1146,16 +1162,15 @@ __device__ __forceinline__ void cluster_barrier() {
     cg::this_cluster().sync();
 }
 
+// the cycle run by CTA `rank` of the nb CTAs of one cluster
 template <typename T>
-__global__ void __cluster_dims__(kCoarseCtas, 1, 1) __launch_bounds__(kCoarseThreads, 1)
-coarse_cycle_kernel(const CoarseCycle<T> cc, const int *done) {
-    if (skip(done)) return;            // uniform over the cluster: no thread reaches a barrier alone
+__device__ __forceinline__ void coarse_cycle_body(const CoarseCycle<T> &cc, int rank, int nb) {
     // each sweep splits a level's rows into one contiguous block per CTA, so every
     // SM of the cluster carries an equal share of a small level's L2 traffic
     // (a grid-wide thread index would leave a 1,000-row level to one or two SMs)
-    const int nb = gridDim.x, lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    auto lo_of = [&](int n) { const int per = (n + nb - 1) / nb; return min(n, (int)blockIdx.x * per); };
-    auto hi_of = [&](int n) { const int per = (n + nb - 1) / nb; return min(n, ((int)blockIdx.x + 1) * per); };
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    auto lo_of = [&](int n) { const int per = (n + nb - 1) / nb; return min(n, rank * per); };
+    auto hi_of = [&](int n) { const int per = (n + nb - 1) / nb; return min(n, (rank + 1) * per); };
     const int last = cc.nlev - 1;
     // the matrices of the levels below the first and the dense inverse come into
     // L2 while the first level is swept: one bulk prefetch per (array, CTA)
@@ -1165,11 +1180,11 @@ coarse_cycle_kernel(const CoarseCycle<T> cc, const int *done) {
         if (lv <= last) {
             const CoarseLevel<T> &Q = cc.lv[lv];
             const size_t ell = (size_t)Q.width * Q.n;
-            if (a == 0) l2_prefetch_part(Q.colA, sizeof(int) * ell, blockIdx.x, nb);
-            else if (a == 1) l2_prefetch_part(Q.val, sizeof(T) * ell, blockIdx.x, nb);
-            else if (a == 2) l2_prefetch_part(Q.dinv, sizeof(T) * Q.n, blockIdx.x, nb);
-            else if (lv < last) l2_prefetch_part(Q.mem, sizeof(int) * Q.n, blockIdx.x, nb);
-            else l2_prefetch_part(cc.inv, sizeof(double) * (size_t)Q.n * Q.n, blockIdx.x, nb);
+            if (a == 0) l2_prefetch_part(Q.colA, sizeof(int) * ell, rank, nb);
+            else if (a == 1) l2_prefetch_part(Q.val, sizeof(T) * ell, rank, nb);
+            else if (a == 2) l2_prefetch_part(Q.dinv, sizeof(T) * Q.n, rank, nb);
+            else if (lv < last) l2_prefetch_part(Q.mem, sizeof(int) * Q.n, rank, nb);
+            else l2_prefetch_part(cc.inv, sizeof(double) * (size_t)Q.n * Q.n, rank, nb);
         }
     }
     for (int l = 0; l < last; l++) {
@@ -1206,18 +1221,24 @@ coarse_cycle_kernel(const CoarseCycle<T> cc, const int *done) {
     }
 }
 
+template <typename T>
+__global__ void __cluster_dims__(kCoarseCtas, 1, 1) __launch_bounds__(kCoarseThreads, 1)
+coarse_cycle_kernel(const __grid_constant__ CoarseCycle<T> cc, const int *done) {
+    if (skip(done)) return;            // uniform over the cluster: no thread reaches a barrier alone
+    // (a grid constant: the body reads the description in parameter space, no copy)
+    coarse_cycle_body<T>(cc, (int)blockIdx.x, (int)gridDim.x);
+}
+
 // stage F, pass 1: r2 = rhat - Ahat[:,p] e_p; red cells z = Dinv r2, black keep r2.
 // rhat = L r from the FP64 residual (lscT = null: quasi-IMPES, only the first row
 // differs from the identity) or, when r is null, the given vector rh; ep may be null.
 template <int B, typename T>
-__global__ void stage2_a_kernel(GridDesc g, const double *__restrict__ r, const T *__restrict__ wT,
-                                const T *__restrict__ lscT, const T *__restrict__ rh, const T *__restrict__ ahat,
-                                const T *__restrict__ dinv, const T *__restrict__ ep, T *__restrict__ r2,
-                                T *__restrict__ z, int rb, const int *done) {
-    if (skip(done)) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void stage2_a_row(const GridDesc &g, const double *__restrict__ r, const T *__restrict__ wT,
+                                             const T *__restrict__ lscT, const T *__restrict__ rh,
+                                             const T *__restrict__ ahat, const T *__restrict__ dinv,
+                                             const T *__restrict__ ep, T *__restrict__ r2, T *__restrict__ z, int rb,
+                                             int i) {
     const long N = g.N;
-    if (i >= N) return;
     T v[B];
     if (!r) {
 #pragma unroll
@@ -1262,6 +1283,17 @@ __global__ void stage2_a_kernel(GridDesc g, const double *__restrict__ r, const 
         for (int q = 0; q < B; q++) s += dinv[(long)(c * B + q) * N + i] * v[q];
         z[(long)c * N + i] = s;
     }
+}
+
+template <int B, typename T>
+__global__ void stage2_a_kernel(GridDesc g, const double *__restrict__ r, const T *__restrict__ wT,
+                                const T *__restrict__ lscT, const T *__restrict__ rh, const T *__restrict__ ahat,
+                                const T *__restrict__ dinv, const T *__restrict__ ep, T *__restrict__ r2,
+                                T *__restrict__ z, int rb, const int *done) {
+    if (skip(done)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.N) return;
+    stage2_a_row<B, T>(g, r, wT, lscT, rh, ahat, dinv, ep, r2, z, rb, i);
 }
 
 // CPR-FPF, after the first stage F (x0): rh = L r - Ahat x0 over the full 7-point
@@ -1323,13 +1355,10 @@ __device__ __forceinline__ T fin(T x, int r, int i, long N, const T *__restrict_
 
 // stage F, pass 2 (black cells): z = Dinv (r2 - sum_d Ahat_{i,d} z_red(nbr)); out = z + e_p
 template <int B, typename T, typename TZ>
-__global__ void stage2_b_kernel(GridDesc g, const T *__restrict__ ahat, const T *__restrict__ dinv,
-                                const T *__restrict__ r2, T *__restrict__ z, const T *__restrict__ ep,
-                                const T *__restrict__ addv, TZ *__restrict__ out, const int *done) {
-    if (skip(done)) return;
-    const int i = colour_cell(g, blockIdx.x * (long)blockDim.x + threadIdx.x, 1);
+__device__ __forceinline__ void stage2_b_row(const GridDesc &g, const T *__restrict__ ahat, const T *__restrict__ dinv,
+                                             const T *__restrict__ r2, T *__restrict__ z, const T *__restrict__ ep,
+                                             const T *__restrict__ addv, TZ *__restrict__ out, int i) {
     const long N = g.N;
-    if (i < 0) return;
     const Cell cc = cell_of(g, i);
     T t[B];
 #pragma unroll
@@ -1356,25 +1385,30 @@ __global__ void stage2_b_kernel(GridDesc g, const T *__restrict__ ahat, const T 
     }
 }
 
+template <int B, typename T, typename TZ>
+__global__ void stage2_b_kernel(GridDesc g, const T *__restrict__ ahat, const T *__restrict__ dinv,
+                                const T *__restrict__ r2, T *__restrict__ z, const T *__restrict__ ep,
+                                const T *__restrict__ addv, TZ *__restrict__ out, const int *done) {
+    if (skip(done)) return;
+    const int i = colour_cell(g, blockIdx.x * (long)blockDim.x + threadIdx.x, 1);
+    if (i < 0) return;
+    stage2_b_row<B, T, TZ>(g, ahat, dinv, r2, z, ep, addv, out, i);
+}
+
 // stage F, pass 3 (red cells): x = z - Dinv sum_d Ahat_{i,d} z_black(nbr); out = x + e_p
 // (rb = 0: block-Jacobi, out = z + e_p for every cell)
 template <int B, typename T, typename TZ>
-__global__ void stage2_c_kernel(GridDesc g, const T *__restrict__ ahat, const T *__restrict__ dinv, const T *__restrict__ z,
-                                const T *__restrict__ ep, const T *__restrict__ addv, TZ *__restrict__ out, int rb,
-                                const int *done) {
-    if (skip(done)) return;
+__device__ __forceinline__ void stage2_c_row(const GridDesc &g, const T *__restrict__ ahat, const T *__restrict__ dinv,
+                                             const T *__restrict__ z, const T *__restrict__ ep,
+                                             const T *__restrict__ addv, TZ *__restrict__ out, int rb, int i) {
     const long N = g.N;
     if (!rb) {
-        const int i = blockIdx.x * blockDim.x + threadIdx.x;
-        if (i >= N) return;
 #pragma unroll
         for (int r = 0; r < B; r++) {
             out[(long)r * N + i] = (TZ)fin<T>(z[(long)r * N + i], r, i, N, ep, addv);
         }
         return;
     }
-    const int i = colour_cell(g, blockIdx.x * (long)blockDim.x + threadIdx.x, 0);   // red cells
-    if (i < 0) return;
     const Cell cc = cell_of(g, i);
     T t[B];
 #pragma unroll
@@ -1398,6 +1432,17 @@ __global__ void stage2_c_kernel(GridDesc g, const T *__restrict__ ahat, const T 
         for (int q = 0; q < B; q++) s += dinv[(long)(r * B + q) * N + i] * t[q];
         out[(long)r * N + i] = (TZ)fin<T>(z[(long)r * N + i] - s, r, i, N, ep, addv);
     }
+}
+
+template <int B, typename T, typename TZ>
+__global__ void stage2_c_kernel(GridDesc g, const T *__restrict__ ahat, const T *__restrict__ dinv, const T *__restrict__ z,
+                                const T *__restrict__ ep, const T *__restrict__ addv, TZ *__restrict__ out, int rb,
+                                const int *done) {
+    if (skip(done)) return;
+    const int i = rb ? colour_cell(g, blockIdx.x * (long)blockDim.x + threadIdx.x, 0)   // red cells
+                     : (blockIdx.x * blockDim.x + threadIdx.x < (unsigned)g.N ? (int)(blockIdx.x * blockDim.x + threadIdx.x) : -1);
+    if (i < 0) return;
+    stage2_c_row<B, T, TZ>(g, ahat, dinv, z, ep, addv, out, rb, i);
 }
 
 // no preconditioner / plain block-Jacobi on J (no decoupling)
@@ -2073,6 +2118,334 @@ sim_status cpr_apply(sim_t *s, const double *r, void *z, const int *done) {
     if (s->b == 2)
         return sim_mixed(s) ? apply_btz<2, float, float>(s, r, (float *)z, done) : apply_btz<2, double, double>(s, r, (double *)z, done);
     return sim_mixed(s) ? apply_btz<3, float, float>(s, r, (float *)z, done) : apply_btz<3, double, double>(s, r, (double *)z, done);
+}
+
+// ===========================================================================
+// CPR application batched over the members of an ensemble
+//
+// One launch per stage covers every member: the restriction, each V-cycle
+// level's residual / restriction / prolongation / smoothing (a member takes
+// part in the launches of the levels it has), the coarse end (one 8-CTA
+// cluster per member for its fused coarse levels, or the dense product of its
+// coarsest level) and the three stage-F sweeps.  Block b of a launch takes
+// work[b] = (member, block of the member's rows), reads the member's operands
+// from a device table and runs the single-system row arithmetic, so every
+// member's result equals that of its own application.  A member whose restart
+// cycle is done (its FGMRES control word) returns at once.
+// ===========================================================================
+namespace {
+constexpr int kBatchLevels = 16;
+constexpr int kBatchAmgThreads = 128;
+
+template <typename T>
+struct BLevel {
+    Mat<T> A;                   // the level's matrix (apply precision)
+    const T *dinv;              // 1 / l1 row sums
+    const int *agg, *moff, *mem;
+    T *f, *e, *e2;
+    int n;
+};
+
+template <typename T>
+struct CMember {
+    GridDesc g;
+    long n;                     // b N
+    const double *V;            // input of application j: V + j n (FP64)
+    T *Z;                       // output: Z + j n
+    const T *wT, *lscT, *ahat, *dinv;
+    T *r2, *zr;
+    int full, rb, nl, lf;
+    const double *inv;          // dense inverse of the coarsest level
+    const CoarseCycle<T> *cc;   // the fused coarse levels (device copy) or null
+    const int *done;
+    BLevel<T> lv[kBatchLevels];
+};
+
+template <typename T>
+__device__ __forceinline__ const CMember<T> &cmember(const CMember<T> *M, const int2 *work, int *vb) {
+    const int2 wk = work[blockIdx.x];
+    *vb = wk.y;
+    return M[wk.x];
+}
+
+template <int B, typename T>
+__global__ void b_restrict_p_kernel(const CMember<T> *M, const int2 *work, int j) {
+    int vb;
+    const CMember<T> &m = cmember(M, work, &vb);
+    if (skip(m.done)) return;
+    const int i = vb * blockDim.x + threadIdx.x;
+    if (i >= m.g.N) return;
+    const BLevel<T> &L0 = m.lv[0];
+    restrict_p_row<B, T>(m.g.N, m.V + (size_t)j * m.n, m.wT, m.full, L0.dinv, L0.f, L0.e, i);
+}
+
+// down the V-cycle at level l: e2 = f - A e (mode 0, rows of l) or the
+// restriction of e2 to level l + 1 (mode 1, rows of l + 1)
+template <typename T>
+__global__ void b_amg_down_kernel(const CMember<T> *M, const int2 *work, int l, int mode) {
+    int vb;
+    const CMember<T> &m = cmember(M, work, &vb);
+    if (skip(m.done)) return;
+    const int i = vb * blockDim.x + threadIdx.x;
+    const BLevel<T> &L = m.lv[l];
+    if (mode == 0) {
+        if (i < L.n) L.e2[i] = L.f[i] - row_dot(L.A, i, L.e);
+    } else {
+        const BLevel<T> &C = m.lv[l + 1];
+        if (i < C.n) amg_restrict_row<T>(L.e2, L.moff, L.mem, C.f, l + 1 == m.nl - 1 ? nullptr : C.e, C.dinv, i);
+    }
+}
+
+// up the V-cycle at level l: e += P e_c (mode 0), then e2 = e + (f - A e) / l1 (mode 1)
+template <typename T>
+__global__ void b_amg_up_kernel(const CMember<T> *M, const int2 *work, int l, int mode) {
+    int vb;
+    const CMember<T> &m = cmember(M, work, &vb);
+    if (skip(m.done)) return;
+    const int i = vb * blockDim.x + threadIdx.x;
+    const BLevel<T> &L = m.lv[l];
+    if (i >= L.n) return;
+    if (mode == 0) {
+        const BLevel<T> &C = m.lv[l + 1];
+        const T *ec = (l + 1 == m.nl - 1) ? C.e : C.e2;
+        L.e[i] += ec[L.agg[i]];
+    } else {
+        L.e2[i] = L.e[i] + (L.f[i] - row_dot(L.A, i, L.e)) * L.dinv[i];
+    }
+}
+
+// coarsest level without the fused cycle: e = Inv f, one warp per row (a
+// one-level hierarchy writes e2 of level 0, the stage-P correction)
+template <typename T>
+__global__ void b_coarse_solve_kernel(const CMember<T> *M, const int2 *work) {
+    int vb;
+    const CMember<T> &m = cmember(M, work, &vb);
+    if (skip(m.done)) return;
+    const BLevel<T> &C = m.lv[m.nl - 1];
+    const int warp = (vb * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= C.n) return;
+    double s = 0.0;
+    for (int q = lane; q < C.n; q += 32) s += m.inv[(long)warp * C.n + q] * (double)C.f[q];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) (m.nl == 1 ? C.e2 : C.e)[warp] = (T)s;
+}
+
+// the fused coarse levels: cluster c runs member members[c]
+template <typename T>
+__global__ void __cluster_dims__(kCoarseCtas, 1, 1) __launch_bounds__(kCoarseThreads, 1)
+b_coarse_cycle_kernel(const CMember<T> *M, const int *members) {
+    const CMember<T> &m = M[members[blockIdx.x / kCoarseCtas]];
+    if (skip(m.done)) return;          // uniform over the cluster (one member)
+    coarse_cycle_body<T>(*m.cc, (int)(blockIdx.x % kCoarseCtas), kCoarseCtas);
+}
+
+// stage F on the residual of stage P: sweep 0 (all cells), 1 (black), 2 (red,
+// or all cells for block Jacobi)
+template <int B, typename T>
+__global__ void b_stage2_kernel(const CMember<T> *M, const int2 *work, int j, int sweep) {
+    int vb;
+    const CMember<T> &m = cmember(M, work, &vb);
+    if (skip(m.done)) return;
+    const long t = vb * (long)blockDim.x + threadIdx.x;
+    const T *ep = m.lv[0].e2;
+    T *out = m.Z + (size_t)j * m.n;
+    if (sweep == 0) {
+        if (t >= m.g.N) return;
+        stage2_a_row<B, T>(m.g, m.V + (size_t)j * m.n, m.wT, m.lscT, nullptr, m.ahat, m.dinv, ep, m.r2, m.zr, m.rb, (int)t);
+    } else if (sweep == 1) {
+        const int i = colour_cell(m.g, t, 1);
+        if (i >= 0) stage2_b_row<B, T, T>(m.g, m.ahat, m.dinv, m.r2, m.zr, ep, nullptr, out, i);
+    } else {
+        const int i = m.rb ? colour_cell(m.g, t, 0) : (t < m.g.N ? (int)t : -1);
+        if (i >= 0) stage2_c_row<B, T, T>(m.g, m.ahat, m.dinv, m.zr, ep, nullptr, out, m.rb, i);
+    }
+}
+}  // namespace
+
+struct CprBatch {
+    int nm = 0, b = 0, mixed = 0, rb = 0;
+    void *dmem = nullptr;  size_t mem_cap = 0;    // CMember<T>[nm]
+    void *dcc = nullptr;   size_t cc_cap = 0;     // CoarseCycle<T>[ncl]
+    int2 *dwork = nullptr; size_t work_cap = 0;
+    int *dcl = nullptr;    size_t cl_cap = 0;     // members with fused coarse levels
+    int ncl = 0;
+    struct List { long off = 0; int count = 0; };
+    List cell256, cell64, stage1, stage2, cs;
+    std::vector<List> down_r, down_c, up;
+};
+
+static cudaError_t grow(void **p, size_t *cap, size_t bytes) {
+    if (bytes <= *cap) return cudaSuccess;
+    if (*p) cudaFree(*p);
+    *p = nullptr; *cap = 0;
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) *cap = bytes;
+    return e;
+}
+
+// the members' current hierarchies are batchable: the same options, block
+// size and precision, two-stage CPR with one V-cycle, no learned stage, no
+// rate-controlled wells, at most kBatchLevels levels
+bool cpr_batchable(sim_t *const *ms, int nm) {
+    if (nm < 1) return false;
+    const sim_options &o = ms[0]->opt;
+    for (int k = 0; k < nm; k++) {
+        const sim_t *s = ms[k];
+        const sim_options &p = s->opt;
+        if (s->b != ms[0]->b || sim_mixed(s) != sim_mixed(ms[0]) || p.precond != SIM_PRECOND_CPR ||
+            p.stage2 != o.stage2 || p.decouple != o.decouple || p.cpr_stages != 2 || p.amg_cycles != 1 ||
+            p.krylov != SIM_KRYLOV_FGMRES || p.gmres_m != o.gmres_m || p.orth != o.orth || s->learned_on || s->nrate)
+            return false;
+    }
+    return true;
+}
+
+template <typename T>
+static cudaError_t batch_build_t(CprBatch *cb, sim_t *const *ms, int nm, cudaStream_t st) {
+    std::vector<CMember<T>> hm(nm);
+    std::vector<CoarseCycle<T>> hcc;
+    std::vector<int> hcl;
+    std::vector<int2> work;
+    cb->down_r.clear(); cb->down_c.clear(); cb->up.clear();
+    auto add_list = [&](CprBatch::List &L, auto blocks_of) {
+        L.off = (long)work.size();
+        for (int k = 0; k < nm; k++) {
+            const int nb = blocks_of(k);
+            for (int q = 0; q < nb; q++) work.push_back(make_int2(k, q));
+        }
+        L.count = (int)((long)work.size() - L.off);
+    };
+    int maxdown = 0, maxup = 0;
+    for (int k = 0; k < nm; k++) {
+        sim_t *s = ms[k];
+        CMember<T> &m = hm[k];
+        memset(&m, 0, sizeof(m));
+        const int nl = (int)s->lev.size();
+        if (nl < 1 || nl > kBatchLevels || !s->precond_ready) return cudaErrorInvalidValue;
+        m.g = s->gd; m.n = (long)s->N * s->b;
+        m.V = s->V; m.Z = (T *)s->Z;
+        m.wT = (const T *)s->qiwT;
+        m.full = s->opt.decouple == SIM_DECOUPLE_ABF;
+        m.lscT = m.full ? (const T *)s->lscT : nullptr;
+        m.ahat = (const T *)s->ahat;
+        m.dinv = sizeof(T) == sizeof(double) ? (const T *)s->dinv_d : (const T *)s->dinv;
+        m.r2 = (T *)s->r2; m.zr = (T *)s->zr;
+        m.rb = s->opt.stage2 == SIM_STAGE2_ILU0_RB;
+        m.nl = nl;
+        m.lf = (s->opt.fused_coarse && nl > 1) ? coarse_start(s) : nl;
+        m.inv = (const double *)s->lev[nl - 1].coarse_inv;
+        m.done = &s->ctl->done;
+        for (int l = 0; l < nl; l++) {
+            AmgLevel &L = s->lev[l];
+            BLevel<T> &d = m.lv[l];
+            d.A = level_matT<T>(s, L, l);
+            d.dinv = (const T *)L.dinvT; d.agg = L.agg; d.moff = L.moff; d.mem = L.mem;
+            d.f = (T *)L.f; d.e = (T *)L.e; d.e2 = (T *)L.e2; d.n = L.n;
+        }
+        if (m.lf < nl) {
+            CoarseCycle<T> cc;
+            cc.nlev = nl - m.lf;
+            cc.inv = m.inv;
+            for (int l = m.lf; l < nl; l++) {
+                const AmgLevel &L = s->lev[l];
+                CoarseLevel<T> &d = cc.lv[l - m.lf];
+                d.n = L.n; d.width = L.width; d.diff = sizeof(T) == sizeof(float); d.colA = L.colA;
+                d.val = (const T *)L.valT; d.dinv = (const T *)L.dinvT;
+                d.agg = L.agg; d.moff = L.moff; d.mem = L.mem;
+                d.f = (T *)L.f; d.e = (T *)L.e; d.e2 = (T *)L.e2;
+            }
+            hcc.push_back(cc);
+            hcl.push_back(k);
+        }
+        const int down = nl > 1 ? std::min(nl - 1, m.lf) : 0;
+        const int top = nl > 1 ? (m.lf < nl ? m.lf : nl - 1) : 0;
+        maxdown = std::max(maxdown, down);
+        maxup = std::max(maxup, top);
+    }
+    auto down_of = [&](int k) { const CMember<T> &m = hm[k]; return m.nl > 1 ? std::min(m.nl - 1, m.lf) : 0; };
+    auto top_of = [&](int k) { const CMember<T> &m = hm[k]; return m.nl > 1 ? (m.lf < m.nl ? m.lf : m.nl - 1) : 0; };
+    add_list(cb->cell256, [&](int k) { return sim_blocks(hm[k].g.N, SIM_THREADS); });
+    add_list(cb->cell64, [&](int k) { return sim_blocks(hm[k].g.N, kStageThreads); });
+    add_list(cb->stage1, [&](int k) { return hm[k].rb ? colour_blocks(ms[k], kStageThreads) : 0; });
+    add_list(cb->stage2, [&](int k) { return hm[k].rb ? colour_blocks(ms[k], kStageThreads) : sim_blocks(hm[k].g.N, kStageThreads); });
+    add_list(cb->cs, [&](int k) { const CMember<T> &m = hm[k];
+                                  return (m.nl == 1 || m.lf == m.nl) ? sim_blocks((long)m.lv[m.nl - 1].n * 32, SIM_THREADS) : 0; });
+    cb->down_r.resize(maxdown); cb->down_c.resize(maxdown); cb->up.resize(maxup);
+    for (int l = 0; l < maxdown; l++) {
+        add_list(cb->down_r[l], [&](int k) { return l < down_of(k) ? sim_blocks(hm[k].lv[l].n, kBatchAmgThreads) : 0; });
+        add_list(cb->down_c[l], [&](int k) { return l < down_of(k) ? sim_blocks(hm[k].lv[l + 1].n, kBatchAmgThreads) : 0; });
+    }
+    for (int l = 0; l < maxup; l++)
+        add_list(cb->up[l], [&](int k) { return l < top_of(k) ? sim_blocks(hm[k].lv[l].n, kBatchAmgThreads) : 0; });
+    cudaError_t e;
+    if ((e = grow(&cb->dmem, &cb->mem_cap, sizeof(CMember<T>) * nm)) != cudaSuccess) return e;
+    if ((e = grow((void **)&cb->dwork, &cb->work_cap, sizeof(int2) * std::max<size_t>(1, work.size()))) != cudaSuccess) return e;
+    if (!hcc.empty()) {
+        if ((e = grow(&cb->dcc, &cb->cc_cap, sizeof(CoarseCycle<T>) * hcc.size())) != cudaSuccess) return e;
+        if ((e = grow((void **)&cb->dcl, &cb->cl_cap, sizeof(int) * hcl.size())) != cudaSuccess) return e;
+        for (size_t c = 0; c < hcc.size(); c++) hm[hcl[c]].cc = (const CoarseCycle<T> *)cb->dcc + c;
+        if ((e = cudaMemcpyAsync(cb->dcc, hcc.data(), sizeof(CoarseCycle<T>) * hcc.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(cb->dcl, hcl.data(), sizeof(int) * hcl.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+    }
+    cb->ncl = (int)hcl.size();
+    if ((e = cudaMemcpyAsync(cb->dmem, hm.data(), sizeof(CMember<T>) * nm, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+    if (!work.empty() && (e = cudaMemcpyAsync(cb->dwork, work.data(), sizeof(int2) * work.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+    // the host tables must outlive the asynchronous copies
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+    cb->nm = nm; cb->b = ms[0]->b; cb->mixed = sim_mixed(ms[0]); cb->rb = hm[0].rb;
+    return cudaSuccess;
+}
+
+CprBatch *cpr_batch_new() { return new CprBatch(); }
+
+void cpr_batch_free(CprBatch *cb) {
+    if (!cb) return;
+    if (cb->dmem) cudaFree(cb->dmem);
+    if (cb->dcc) cudaFree(cb->dcc);
+    if (cb->dwork) cudaFree(cb->dwork);
+    if (cb->dcl) cudaFree(cb->dcl);
+    delete cb;
+}
+
+cudaError_t cpr_batch_build(CprBatch *cb, sim_t *const *ms, int nm, cudaStream_t st) {
+    return sim_mixed(ms[0]) ? batch_build_t<float>(cb, ms, nm, st) : batch_build_t<double>(cb, ms, nm, st);
+}
+
+template <int B, typename T>
+static int batch_apply_t(const CprBatch *cb, cudaStream_t st, int j) {
+    const CMember<T> *M = (const CMember<T> *)cb->dmem;
+    const int2 *W = cb->dwork;
+    int launches = 0;
+    auto go = [&](const CprBatch::List &L, int threads, auto launch) {
+        if (L.count > 0) { launch(L.count, threads, W + L.off); launches++; }
+    };
+    go(cb->cell256, SIM_THREADS, [&](int n, int t, const int2 *w) { b_restrict_p_kernel<B, T><<<n, t, 0, st>>>(M, w, j); });
+    for (size_t l = 0; l < cb->down_r.size(); l++) {
+        go(cb->down_r[l], kBatchAmgThreads, [&](int n, int t, const int2 *w) { b_amg_down_kernel<T><<<n, t, 0, st>>>(M, w, (int)l, 0); });
+        go(cb->down_c[l], kBatchAmgThreads, [&](int n, int t, const int2 *w) { b_amg_down_kernel<T><<<n, t, 0, st>>>(M, w, (int)l, 1); });
+    }
+    if (cb->ncl > 0) {
+        b_coarse_cycle_kernel<T><<<cb->ncl * kCoarseCtas, kCoarseThreads, 0, st>>>(M, cb->dcl);
+        launches++;
+    }
+    go(cb->cs, SIM_THREADS, [&](int n, int t, const int2 *w) { b_coarse_solve_kernel<T><<<n, t, 0, st>>>(M, w); });
+    for (int l = (int)cb->up.size() - 1; l >= 0; l--) {
+        go(cb->up[l], kBatchAmgThreads, [&](int n, int t, const int2 *w) { b_amg_up_kernel<T><<<n, t, 0, st>>>(M, w, l, 0); });
+        go(cb->up[l], kBatchAmgThreads, [&](int n, int t, const int2 *w) { b_amg_up_kernel<T><<<n, t, 0, st>>>(M, w, l, 1); });
+    }
+    go(cb->cell64, kStageThreads, [&](int n, int t, const int2 *w) { b_stage2_kernel<B, T><<<n, t, 0, st>>>(M, w, j, 0); });
+    go(cb->stage1, kStageThreads, [&](int n, int t, const int2 *w) { b_stage2_kernel<B, T><<<n, t, 0, st>>>(M, w, j, 1); });
+    go(cb->stage2, kStageThreads, [&](int n, int t, const int2 *w) { b_stage2_kernel<B, T><<<n, t, 0, st>>>(M, w, j, 2); });
+    return launches;
+}
+
+// one batched CPR application (input V_j, output Z_j of every member);
+// returns the number of kernels launched, or -1 on a launch error
+int cpr_batch_apply(const CprBatch *cb, cudaStream_t st, int j) {
+    int n;
+    if (cb->b == 2) n = cb->mixed ? batch_apply_t<2, float>(cb, st, j) : batch_apply_t<2, double>(cb, st, j);
+    else n = cb->mixed ? batch_apply_t<3, float>(cb, st, j) : batch_apply_t<3, double>(cb, st, j);
+    return cudaGetLastError() == cudaSuccess ? n : -1;
 }
 
 sim_status cpr_copy_level_ell(sim_t *s, int level, int *col, double *val) {

@@ -20,13 +20,9 @@ template <typename X> __device__ __forceinline__ double ld(const X *p, long i) {
 
 // y = J x on the 7-point block stencil; blocks of absent neighbours are skipped
 template <int B, typename X>
-__global__ void __launch_bounds__(512) spmv_kernel(GridDesc g, const double *__restrict__ J,
-                                                           const X *__restrict__ x, double *__restrict__ y,
-                                                           const int *done) {
-    if (skip(done)) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void spmv_row(const GridDesc &g, const double *__restrict__ J, const X *__restrict__ x,
+                                         double *__restrict__ y, int i) {
     const long N = g.N;
-    if (i >= N) return;
     const int ix = i % g.nx, t = i / g.nx, iy = t % g.ny, iz = t / g.ny;
     const int nxy = g.nx * g.ny;
     double acc[B];
@@ -57,6 +53,16 @@ __global__ void __launch_bounds__(512) spmv_kernel(GridDesc g, const double *__r
     for (int r = 0; r < B; r++) y[(long)r * N + i] = acc[r];
 }
 
+template <int B, typename X>
+__global__ void __launch_bounds__(512) spmv_kernel(GridDesc g, const double *__restrict__ J,
+                                                           const X *__restrict__ x, double *__restrict__ y,
+                                                           const int *done) {
+    if (skip(done)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.N) return;
+    spmv_row<B, X>(g, J, x, y, i);
+}
+
 // ---- block reduction of nv partial sums into partials[k][gridDim] ----------
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -64,8 +70,14 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// A block's place in the grid its reduction spans: the launch's own grid
+// (one system), or the member's share of a batched launch (one system per
+// member of an ensemble; partials and tickets are the member's own).
+struct VBlk { int id, count; };
+__device__ __forceinline__ VBlk grid_blk() { return VBlk{(int)blockIdx.x, (int)gridDim.x}; }
+
 template <int NV>
-__device__ void block_partials(const double (&acc)[NV], int nv, double *partials) {
+__device__ void block_partials(const double (&acc)[NV], int nv, double *partials, VBlk vb = grid_blk()) {
     __shared__ double sh[SIM_THREADS / 32][NV];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -79,18 +91,18 @@ __device__ void block_partials(const double (&acc)[NV], int nv, double *partials
     for (int k = threadIdx.x; k < nv; k += blockDim.x) {
         double s = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += sh[w][k];
-        partials[k * gridDim.x + blockIdx.x] = s;
+        partials[k * vb.count + vb.id] = s;
     }
 }
 
 // returns true in the last block to arrive (all partials visible)
-__device__ bool last_block(unsigned int *ticket) {
+__device__ bool last_block(unsigned int *ticket, int count = (int)gridDim.x) {
     __shared__ bool last;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned int t = atomicAdd(ticket, 1u);
-        last = (t == gridDim.x - 1);
+        last = (t == (unsigned int)count - 1);
     }
     __syncthreads();
     if (last) __threadfence();
@@ -101,9 +113,8 @@ __device__ bool last_block(unsigned int *ticket) {
 // shuffle tree (the summation order does not depend on timing).  A lane loads
 // 8 of its partials before adding them in stride order, so the loads overlap
 // instead of each waiting for the previous add.
-__device__ void fold(const double *partials, int nv, double *out) {
+__device__ void fold(const double *partials, int nv, double *out, int G = (int)gridDim.x) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int G = (int)gridDim.x;
     for (int k = wid; k < nv; k += nw) {
         const double *p = partials + (long)k * G;
         double s = 0.0;
@@ -127,24 +138,30 @@ constexpr int NVMAX = SIM_MAX_M + 1;
 // Above 20 vectors two blocks per SM (128 registers a thread) keep more of an
 // element's NV loads in flight than three blocks at 80 registers.
 template <int NV>
-__global__ void __launch_bounds__(SIM_THREADS, NV > 20 ? 2 : 3) dots_kernel(const double *__restrict__ V, const double *__restrict__ w,
-                                                           long n, double *partials, unsigned int *ticket,
-                                                           double *out, const int *done) {
-    if (skip(done)) return;
+__device__ __forceinline__ void dots_body(const double *__restrict__ V, const double *__restrict__ w, long n,
+                                          double *partials, unsigned int *ticket, double *out, VBlk vb) {
     double acc[NV + 1];
 #pragma unroll
     for (int k = 0; k <= NV; k++) acc[k] = 0.0;
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    for (long i = vb.id * (long)blockDim.x + threadIdx.x; i < n; i += (long)vb.count * blockDim.x) {
         const double wi = w[i];
 #pragma unroll
         for (int k = 0; k < NV; k++) acc[k] += V[k * n + i] * wi;
         acc[NV] += wi * wi;
     }
-    block_partials<NV + 1>(acc, NV + 1, partials);
-    if (last_block(ticket)) {
-        fold(partials, NV + 1, out);
+    block_partials<NV + 1>(acc, NV + 1, partials, vb);
+    if (last_block(ticket, vb.count)) {
+        fold(partials, NV + 1, out, vb.count);
         if (threadIdx.x == 0) *ticket = 0u;
     }
+}
+
+template <int NV>
+__global__ void __launch_bounds__(SIM_THREADS, NV > 20 ? 2 : 3) dots_kernel(const double *__restrict__ V, const double *__restrict__ w,
+                                                           long n, double *partials, unsigned int *ticket,
+                                                           double *out, const int *done) {
+    if (skip(done)) return;
+    dots_body<NV>(V, w, n, partials, ticket, out, grid_blk());
 }
 
 // second Gram-Schmidt pass needed?  Always for CGS2; for the selective form
@@ -167,11 +184,9 @@ __device__ __forceinline__ bool need_reorth(const double *h, int nv, int selecti
 constexpr int kOrthTile = 128, kOrthPad = 132;
 
 template <int NV>
-__global__ void __launch_bounds__(kOrthTile) orth_dots_kernel(const double *__restrict__ V, double *__restrict__ w,
-                                                             long n, const double *h, double *partials,
-                                                             unsigned int *ticket, double *out, const int *done,
-                                                             int selective) {
-    if (skip(done)) return;
+__device__ __forceinline__ void orth_dots_body(const double *__restrict__ V, double *__restrict__ w, long n,
+                                               const double *h, double *partials, unsigned int *ticket, double *out,
+                                               int selective, VBlk vb) {
     if (!need_reorth(h, NV, selective)) return;
     __shared__ double sv[NV][kOrthPad];
     __shared__ double sw[kOrthTile];
@@ -180,7 +195,7 @@ __global__ void __launch_bounds__(kOrthTile) orth_dots_kernel(const double *__re
     __syncthreads();
     const int kk = threadIdx.x >> 2, sub = threadIdx.x & 3;   // dot slot of this thread
     double acc = 0.0;
-    for (long base = (long)blockIdx.x * kOrthTile; base < n; base += (long)gridDim.x * kOrthTile) {
+    for (long base = (long)vb.id * kOrthTile; base < n; base += (long)vb.count * kOrthTile) {
         const long i = base + threadIdx.x;
         if (i < n) {
             double wi = w[i];
@@ -207,63 +222,44 @@ __global__ void __launch_bounds__(kOrthTile) orth_dots_kernel(const double *__re
     // the 4 threads of a slot are adjacent lanes: fold them, then one per slot writes
     acc += __shfl_xor_sync(0xffffffffu, acc, 1);
     acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-    if (sub == 0 && kk < NV) partials[kk * gridDim.x + blockIdx.x] = acc;
-    if (last_block(ticket)) {
-        fold(partials, NV, out);
+    if (sub == 0 && kk < NV) partials[kk * vb.count + vb.id] = acc;
+    if (last_block(ticket, vb.count)) {
+        fold(partials, NV, out, vb.count);
         if (threadIdx.x == 0) *ticket = 0u;
     }
 }
 
-// launch the NV-specialised kernels for a runtime vector count nv <= SIM_MAX_M
 template <int NV>
-struct OrthDispatch {
-    static void dots(int nv, cudaStream_t st, const double *V, const double *w, long n, double *part, unsigned int *tk,
-                     double *out, const int *done) {
-        if (nv == NV) dots_kernel<NV><<<SIM_RED_BLOCKS, SIM_THREADS, 0, st>>>(V, w, n, part, tk, out, done);
-        else OrthDispatch<NV - 1>::dots(nv, st, V, w, n, part, tk, out, done);
-    }
-    static void norm(int nv, cudaStream_t st, const double *V, double *w, long n, int m, double *part, unsigned int *tk,
-                     KrylovCtl *ctl, int sel);
-    static void orth(int nv, cudaStream_t st, const double *V, double *w, long n, const double *h, double *part,
-                     unsigned int *tk, double *out, const int *done, int sel) {
-        // 6 blocks of 128 threads per SM keep loads in flight while tiles are reduced
-        if (nv == NV) orth_dots_kernel<NV><<<2 * SIM_RED_BLOCKS, kOrthTile, 0, st>>>(V, w, n, h, part, tk, out, done, sel);
-        else OrthDispatch<NV - 1>::orth(nv, st, V, w, n, h, part, tk, out, done, sel);
-    }
-};
-template <>
-struct OrthDispatch<0> {
-    static void dots(int, cudaStream_t, const double *, const double *, long, double *, unsigned int *, double *,
-                     const int *) {}
-    static void orth(int, cudaStream_t, const double *, double *, long, const double *, double *, unsigned int *,
-                     double *, const int *, int) {}
-    static void norm(int, cudaStream_t, const double *, double *, long, int, double *, unsigned int *, KrylovCtl *,
-                     int) {}
-};
+__global__ void __launch_bounds__(kOrthTile) orth_dots_kernel(const double *__restrict__ V, double *__restrict__ w,
+                                                             long n, const double *h, double *partials,
+                                                             unsigned int *ticket, double *out, const int *done,
+                                                             int selective) {
+    if (skip(done)) return;
+    orth_dots_body<NV>(V, w, n, h, partials, ticket, out, selective, grid_blk());
+}
 
 // w -= sum_k h2[k] V_k ; ||w||; last block: Hessenberg column j, Givens, test
 // (NV = j + 1 at compile time: the NV basis loads of an element are unrolled
 // and in flight together)
 template <int NV>
-__global__ void __launch_bounds__(SIM_THREADS, NV > 20 ? 2 : 3) orth_norm_kernel(const double *__restrict__ V, double *__restrict__ w,
-                                                                long n, int j, int m, double *partials,
-                                                                unsigned int *ticket, KrylovCtl *ctl, int selective) {
-    if (ctl->done) return;
+__device__ __forceinline__ void orth_norm_body(const double *__restrict__ V, double *__restrict__ w, long n, int j,
+                                               int m, double *partials, unsigned int *ticket, KrylovCtl *ctl,
+                                               int selective, VBlk vb) {
     const int nv = NV;
     const bool re = need_reorth(ctl->h, nv, selective);   // else the first pass is subtracted here
     __shared__ double hs[NVMAX];
     for (int k = threadIdx.x; k < nv; k += blockDim.x) hs[k] = re ? ctl->h2[k] : ctl->h[k];
     __syncthreads();
     double acc[1] = {0.0};
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    for (long i = vb.id * (long)blockDim.x + threadIdx.x; i < n; i += (long)vb.count * blockDim.x) {
         double wi = w[i];
 #pragma unroll
         for (int k = 0; k < NV; k++) wi -= hs[k] * V[k * n + i];
         w[i] = wi;
         acc[0] += wi * wi;
     }
-    block_partials<1>(acc, 1, partials);
-    if (last_block(ticket)) {
+    block_partials<1>(acc, 1, partials, vb);
+    if (last_block(ticket, vb.count)) {
         __shared__ double nrm;
         // the column and the earlier rotations, staged by the whole block so
         // that thread 0's rotation chain reads shared memory only
@@ -273,7 +269,7 @@ __global__ void __launch_bounds__(SIM_THREADS, NV > 20 ? 2 : 3) orth_norm_kernel
             rcs[k] = ctl->cs[k];
             rsn[k] = ctl->sn[k];
         }
-        fold(partials, 1, &nrm);
+        fold(partials, 1, &nrm, vb.count);
         __syncthreads();
         if (threadIdx.x == 0) {
             *ticket = 0u;
@@ -301,26 +297,32 @@ __global__ void __launch_bounds__(SIM_THREADS, NV > 20 ? 2 : 3) orth_norm_kernel
 }
 
 template <int NV>
-void OrthDispatch<NV>::norm(int nv, cudaStream_t st, const double *V, double *w, long n, int m, double *part,
-                            unsigned int *tk, KrylovCtl *ctl, int sel) {
-    if (nv == NV) orth_norm_kernel<NV><<<SIM_RED_BLOCKS, SIM_THREADS, 0, st>>>(V, w, n, NV - 1, m, part, tk, ctl, sel);
-    else OrthDispatch<NV - 1>::norm(nv, st, V, w, n, m, part, tk, ctl, sel);
+__global__ void __launch_bounds__(SIM_THREADS, NV > 20 ? 2 : 3) orth_norm_kernel(const double *__restrict__ V, double *__restrict__ w,
+                                                                long n, int j, int m, double *partials,
+                                                                unsigned int *ticket, KrylovCtl *ctl, int selective) {
+    if (ctl->done) return;
+    orth_norm_body<NV>(V, w, n, j, m, partials, ticket, ctl, selective, grid_blk());
 }
 
 // v = w / scale (scale = ctl->rnorm2 inside a cycle, ctl->beta at a restart)
+__device__ __forceinline__ void scale_body(const double *__restrict__ w, double *__restrict__ v, long n,
+                                           const KrylovCtl *ctl, int use_beta, VBlk vb) {
+    const double sc = use_beta ? ctl->beta : ctl->rnorm2;
+    const double inv = sc > 0.0 ? 1.0 / sc : 0.0;
+    for (long i = vb.id * (long)blockDim.x + threadIdx.x; i < n; i += (long)vb.count * blockDim.x)
+        v[i] = sc > 0.0 ? w[i] * inv : 0.0;
+}
+
 __global__ void scale_kernel(const double *__restrict__ w, double *__restrict__ v, long n, const KrylovCtl *ctl,
                              int use_beta) {
     if (!use_beta && ctl->done) return;
-    const double sc = use_beta ? ctl->beta : ctl->rnorm2;
-    const double inv = sc > 0.0 ? 1.0 / sc : 0.0;
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-        v[i] = sc > 0.0 ? w[i] * inv : 0.0;
+    scale_body(w, v, n, ctl, use_beta, grid_blk());
 }
 
 // y = H^{-1} g (k x k upper triangular), single thread
 // (H and g staged in shared memory by the block, so the one thread that runs
 // the dependent back substitution never waits on global memory)
-__global__ void backsolve_kernel(KrylovCtl *ctl) {
+__device__ __forceinline__ void backsolve_body(KrylovCtl *ctl) {
     constexpr int LD = SIM_MAX_M + 1;
     __shared__ double Hs[LD * LD], gs[LD], ys[LD];
     const int k = ctl->k;
@@ -338,37 +340,53 @@ __global__ void backsolve_kernel(KrylovCtl *ctl) {
     for (int t = threadIdx.x; t < k; t += blockDim.x) ctl->y[t] = ys[t];
 }
 
+__global__ void backsolve_kernel(KrylovCtl *ctl) { backsolve_body(ctl); }
+
 // x += sum_k y_k Z_k
 template <typename Z>
-__global__ void xupdate_kernel(double *__restrict__ x, const Z *__restrict__ Zb, long n, const KrylovCtl *ctl) {
+__device__ __forceinline__ void xupdate_body(double *__restrict__ x, const Z *__restrict__ Zb, long n,
+                                             const KrylovCtl *ctl, VBlk vb) {
     __shared__ double ys[NVMAX];
     const int k = ctl->k;
     for (int t = threadIdx.x; t < k; t += blockDim.x) ys[t] = ctl->y[t];
     __syncthreads();
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    for (long i = vb.id * (long)blockDim.x + threadIdx.x; i < n; i += (long)vb.count * blockDim.x) {
         double s = x[i];
         for (int t = 0; t < k; t++) s += ys[t] * (double)Zb[t * n + i];
         x[i] = s;
     }
 }
 
+template <typename Z>
+__global__ void xupdate_kernel(double *__restrict__ x, const Z *__restrict__ Zb, long n, const KrylovCtl *ctl) {
+    xupdate_body<Z>(x, Zb, n, ctl, grid_blk());
+}
+
 // r = b - y ; ||r|| into *out
-__global__ void __launch_bounds__(SIM_THREADS) resid_kernel(const double *__restrict__ b, const double *__restrict__ y,
-                                                            double *__restrict__ r, long n, double *partials,
-                                                            unsigned int *ticket, double *out) {
+__device__ __forceinline__ bool resid_body(const double *__restrict__ b, const double *__restrict__ y,
+                                           double *__restrict__ r, long n, double *partials, unsigned int *ticket,
+                                           double *out, VBlk vb) {
     double acc[1] = {0.0};
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    for (long i = vb.id * (long)blockDim.x + threadIdx.x; i < n; i += (long)vb.count * blockDim.x) {
         const double v = b[i] - y[i];
         r[i] = v;
         acc[0] += v * v;
     }
-    block_partials<1>(acc, 1, partials);
-    if (last_block(ticket)) {
+    block_partials<1>(acc, 1, partials, vb);
+    if (last_block(ticket, vb.count)) {
         __shared__ double nrm;
-        fold(partials, 1, &nrm);
+        fold(partials, 1, &nrm, vb.count);
         __syncthreads();
         if (threadIdx.x == 0) { *ticket = 0u; *out = sqrt(nrm); }
+        return true;
     }
+    return false;
+}
+
+__global__ void __launch_bounds__(SIM_THREADS) resid_kernel(const double *__restrict__ b, const double *__restrict__ y,
+                                                            double *__restrict__ r, long n, double *partials,
+                                                            unsigned int *ticket, double *out) {
+    resid_body(b, y, r, n, partials, ticket, out, grid_blk());
 }
 
 __global__ void norm_kernel(const double *__restrict__ v, long n, double *partials, unsigned int *ticket, double *out) {
@@ -385,11 +403,185 @@ __global__ void norm_kernel(const double *__restrict__ v, long n, double *partia
 
 // start of a restart cycle: clear flags and the Givens state, g = beta e1
 // (ctl->tol is set once per solve)
-__global__ void cycle_init_kernel(KrylovCtl *ctl) {
+__device__ __forceinline__ void cycle_init_body(KrylovCtl *ctl, int done) {
     const int t = threadIdx.x;
-    if (t == 0) { ctl->done = 0; ctl->k = 0; ctl->g[0] = ctl->beta; }
+    if (t == 0) { ctl->done = done; ctl->k = 0; ctl->g[0] = ctl->beta; }
     for (int k = t + 1; k <= SIM_MAX_M; k += blockDim.x) ctl->g[k] = 0.0;
 }
+
+__global__ void cycle_init_kernel(KrylovCtl *ctl) { cycle_init_body(ctl, 0); }
+
+// ---- the same operations batched over the members of an ensemble ----------
+// One launch covers every member: block b of the launch takes the work item
+// work[b] = (member, virtual block), finds the member's operands in the table
+// M and runs the single-system body on its share (the member's reductions
+// keep their own partials, ticket and virtual grid of SIM_RED_BLOCKS blocks,
+// so each member's sums are the ones of a launch of its own).  A member whose
+// solve has converged (ctl->active = 0) or whose cycle is done returns at once.
+__device__ __forceinline__ const KMember &member_of(const KMember *M, const int2 *work, VBlk *vb, int count) {
+    const int2 wk = work[blockIdx.x];
+    vb->id = wk.y;
+    vb->count = count;
+    return M[wk.x];
+}
+
+__device__ __forceinline__ bool cycle_off(const KMember &m) { return *(volatile const int *)&m.ctl->done; }
+
+// start of a solve: r = b, x = 0, beta = ||b||, tol = theta ||b||, active
+// when beta is positive and finite
+__global__ void __launch_bounds__(SIM_THREADS) b_start_kernel(const KMember *M, const int2 *work) {
+    VBlk vb;
+    const KMember &m = member_of(M, work, &vb, SIM_RED_BLOCKS);
+    if (!m.rhs) return;                                  // not solving in this round
+    double acc[1] = {0.0};
+    for (long i = vb.id * (long)blockDim.x + threadIdx.x; i < m.n; i += (long)vb.count * blockDim.x) {
+        const double v = m.rhs[i];
+        m.r[i] = v;
+        m.x[i] = 0.0;
+        acc[0] += v * v;
+    }
+    block_partials<1>(acc, 1, m.red, vb);
+    if (last_block(m.ticket, vb.count)) {
+        __shared__ double nrm;
+        fold(m.red, 1, &nrm, vb.count);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            *m.ticket = 0u;
+            const double bn = sqrt(nrm);
+            m.ctl->beta = bn;
+            m.ctl->tol = m.theta * bn;
+            m.ctl->active = (bn > 0.0 && bn == bn) ? 1 : 0;
+            m.ctl->k = 0;
+            m.ctl->iters = 0;
+        }
+    }
+}
+
+__global__ void b_cycle_init_kernel(const KMember *M, const int2 *work) {
+    VBlk vb;
+    const KMember &m = member_of(M, work, &vb, 1);
+    cycle_init_body(m.ctl, m.rhs && m.ctl->active ? 0 : 1);
+}
+
+// v_j = w / scale: j = 0 from the residual (use_beta), else from w
+__global__ void b_scale_kernel(const KMember *M, const int2 *work, int j, int use_beta) {
+    VBlk vb;
+    const KMember &m = member_of(M, work, &vb, SIM_RED_BLOCKS);
+    if (cycle_off(m)) return;
+    scale_body(use_beta ? m.r : m.w, m.V + (size_t)j * m.n, m.n, m.ctl, use_beta, vb);
+}
+
+// w = J z_j (src 0, z_j in the direction precision) or w = J x (src 1)
+template <int B, typename X>
+__global__ void __launch_bounds__(512) b_spmv_kernel(const KMember *M, const int2 *work, int j, int src) {
+    VBlk vb;
+    const KMember &m = member_of(M, work, &vb, 0);
+    if (src == 0 ? cycle_off(m) : !(m.rhs && m.ctl->active)) return;
+    const int i = vb.id * blockDim.x + threadIdx.x;
+    if (i >= m.g.N) return;
+    const X *x = src == 0 ? (const X *)m.Z + (size_t)j * m.n : (const X *)m.x;
+    spmv_row<B, X>(m.g, m.J, x, m.w, i);
+}
+
+template <int NV>
+__global__ void __launch_bounds__(SIM_THREADS, NV > 20 ? 2 : 3) b_dots_kernel(const KMember *M, const int2 *work) {
+    VBlk vb;
+    const KMember &m = member_of(M, work, &vb, SIM_RED_BLOCKS);
+    if (cycle_off(m)) return;
+    dots_body<NV>(m.V, m.w, m.n, m.red, m.ticket, m.ctl->h, vb);
+}
+
+template <int NV>
+__global__ void __launch_bounds__(kOrthTile) b_orth_dots_kernel(const KMember *M, const int2 *work, int selective) {
+    VBlk vb;
+    const KMember &m = member_of(M, work, &vb, 2 * SIM_RED_BLOCKS);
+    if (cycle_off(m)) return;
+    orth_dots_body<NV>(m.V, m.w, m.n, m.ctl->h, m.red, m.ticket, m.ctl->h2, selective, vb);
+}
+
+template <int NV>
+__global__ void __launch_bounds__(SIM_THREADS, NV > 20 ? 2 : 3) b_orth_norm_kernel(const KMember *M, const int2 *work,
+                                                                                  int mrestart, int selective) {
+    VBlk vb;
+    const KMember &m = member_of(M, work, &vb, SIM_RED_BLOCKS);
+    if (cycle_off(m)) return;
+    orth_norm_body<NV>(m.V, m.w, m.n, NV - 1, mrestart, m.red, m.ticket, m.ctl, selective, vb);
+}
+
+// after a cycle (members still solving): y = H^-1 g; x += Z y; w = J x; r = b - w
+__global__ void b_backsolve_kernel(const KMember *M, const int2 *work) {
+    VBlk vb;
+    const KMember &m = member_of(M, work, &vb, 1);
+    if (!(m.rhs && m.ctl->active)) return;
+    backsolve_body(m.ctl);
+}
+
+template <typename Z>
+__global__ void b_xupdate_kernel(const KMember *M, const int2 *work) {
+    VBlk vb;
+    const KMember &m = member_of(M, work, &vb, SIM_RED_BLOCKS);
+    if (!(m.rhs && m.ctl->active)) return;
+    xupdate_body<Z>(m.x, (const Z *)m.Z, m.n, m.ctl, vb);
+}
+
+// r = b - w, beta = ||r||; the member stays active while beta > tol (finite)
+__global__ void __launch_bounds__(SIM_THREADS) b_resid_kernel(const KMember *M, const int2 *work) {
+    VBlk vb;
+    const KMember &m = member_of(M, work, &vb, SIM_RED_BLOCKS);
+    if (!(m.rhs && m.ctl->active)) return;
+    if (resid_body(m.rhs, m.w, m.r, m.n, m.red, m.ticket, &m.ctl->beta, vb) && threadIdx.x == 0) {
+        const double beta = m.ctl->beta;
+        m.ctl->iters += m.ctl->k;
+        m.ctl->active = (beta > m.ctl->tol && beta == beta) ? 1 : 0;
+    }
+}
+
+// launch the NV-specialised kernels for a runtime vector count nv <= SIM_MAX_M
+template <int NV>
+struct OrthDispatch {
+    static void dots(int nv, cudaStream_t st, const double *V, const double *w, long n, double *part, unsigned int *tk,
+                     double *out, const int *done) {
+        if (nv == NV) dots_kernel<NV><<<SIM_RED_BLOCKS, SIM_THREADS, 0, st>>>(V, w, n, part, tk, out, done);
+        else OrthDispatch<NV - 1>::dots(nv, st, V, w, n, part, tk, out, done);
+    }
+    static void norm(int nv, cudaStream_t st, const double *V, double *w, long n, int m, double *part, unsigned int *tk,
+                     KrylovCtl *ctl, int sel) {
+        if (nv == NV) orth_norm_kernel<NV><<<SIM_RED_BLOCKS, SIM_THREADS, 0, st>>>(V, w, n, NV - 1, m, part, tk, ctl, sel);
+        else OrthDispatch<NV - 1>::norm(nv, st, V, w, n, m, part, tk, ctl, sel);
+    }
+    static void orth(int nv, cudaStream_t st, const double *V, double *w, long n, const double *h, double *part,
+                     unsigned int *tk, double *out, const int *done, int sel) {
+        // 6 blocks of 128 threads per SM keep loads in flight while tiles are reduced
+        if (nv == NV) orth_dots_kernel<NV><<<2 * SIM_RED_BLOCKS, kOrthTile, 0, st>>>(V, w, n, h, part, tk, out, done, sel);
+        else OrthDispatch<NV - 1>::orth(nv, st, V, w, n, h, part, tk, out, done, sel);
+    }
+    // batched: one launch per pass over every member (work lists of SIM_RED_BLOCKS
+    // and 2 SIM_RED_BLOCKS virtual blocks per member)
+    static void bdots(int nv, cudaStream_t st, const KMember *M, const int2 *wred, int nred) {
+        if (nv == NV) b_dots_kernel<NV><<<nred, SIM_THREADS, 0, st>>>(M, wred);
+        else OrthDispatch<NV - 1>::bdots(nv, st, M, wred, nred);
+    }
+    static void borth(int nv, cudaStream_t st, const KMember *M, const int2 *worth, int north, int sel) {
+        if (nv == NV) b_orth_dots_kernel<NV><<<north, kOrthTile, 0, st>>>(M, worth, sel);
+        else OrthDispatch<NV - 1>::borth(nv, st, M, worth, north, sel);
+    }
+    static void bnorm(int nv, cudaStream_t st, const KMember *M, const int2 *wred, int nred, int m, int sel) {
+        if (nv == NV) b_orth_norm_kernel<NV><<<nred, SIM_THREADS, 0, st>>>(M, wred, m, sel);
+        else OrthDispatch<NV - 1>::bnorm(nv, st, M, wred, nred, m, sel);
+    }
+};
+template <>
+struct OrthDispatch<0> {
+    static void dots(int, cudaStream_t, const double *, const double *, long, double *, unsigned int *, double *,
+                     const int *) {}
+    static void orth(int, cudaStream_t, const double *, double *, long, const double *, double *, unsigned int *,
+                     double *, const int *, int) {}
+    static void norm(int, cudaStream_t, const double *, double *, long, int, double *, unsigned int *, KrylovCtl *,
+                     int) {}
+    static void bdots(int, cudaStream_t, const KMember *, const int2 *, int) {}
+    static void borth(int, cudaStream_t, const KMember *, const int2 *, int, int) {}
+    static void bnorm(int, cudaStream_t, const KMember *, const int2 *, int, int, int) {}
+};
 
 // ---- BiCGSTAB (right-preconditioned, van der Vorst) ---------------------
 // One iteration is a fixed kernel sequence reading its scalars from the
@@ -897,5 +1089,218 @@ sim_status k_diff_norm2(sim_t *s, const double *a, const double *b, long n, doub
     SIM_CK(s, cudaMemcpyAsync(s->h_pinned, s->scal, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     SIM_CK(s, cudaStreamSynchronize(s->stream));
     *out = s->h_pinned[0];
+    return SIM_OK;
+}
+
+// ===========================================================================
+// FGMRES batched over the members of an ensemble
+// ===========================================================================
+namespace {
+// per member after a cycle: active, inner iterations so far, beta
+__global__ void b_gather_kernel(const KMember *M, const int2 *work, double *out) {
+    VBlk vb;
+    const KMember &m = member_of(M, work, &vb, 1);
+    if (threadIdx.x == 0) {
+        double *o = out + 4 * (long)work[blockIdx.x].x;
+        o[0] = m.ctl->active;
+        o[1] = m.ctl->iters;
+        o[2] = m.ctl->beta;
+        o[3] = m.ctl->k;
+    }
+}
+}  // namespace
+
+struct KrylovBatch {
+    int nm = 0, m = 0, b = 0, zf = 0, orth = 0;
+    KMember *dmem = nullptr; size_t mem_cap = 0;
+    int2 *dwork = nullptr; size_t work_cap = 0;
+    double *dout = nullptr, *hout = nullptr; int out_cap = 0;
+    long red_off = 0, orth_off = 0, one_off = 0, cell_off = 0;
+    int red_n = 0, orth_n = 0, one_n = 0, cell_n = 0;
+    CprBatch *cpr = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t nodes = 0, launches = 0;
+};
+
+KrylovBatch *k_batch_new() {
+    KrylovBatch *kb = new KrylovBatch();
+    kb->cpr = cpr_batch_new();
+    return kb;
+}
+
+void k_batch_free(KrylovBatch *kb) {
+    if (!kb) return;
+    if (kb->exec) cudaGraphExecDestroy(kb->exec);
+    if (kb->dmem) cudaFree(kb->dmem);
+    if (kb->dwork) cudaFree(kb->dwork);
+    if (kb->dout) cudaFree(kb->dout);
+    if (kb->hout) cudaFreeHost(kb->hout);
+    cpr_batch_free(kb->cpr);
+    delete kb;
+}
+
+int64_t k_batch_launches(const KrylovBatch *kb) { return kb ? kb->launches : 0; }
+
+static cudaError_t kgrow(void **p, size_t *cap, size_t bytes) {
+    if (bytes <= *cap) return cudaSuccess;
+    if (*p) cudaFree(*p);
+    *p = nullptr; *cap = 0;
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) *cap = bytes;
+    return e;
+}
+
+// the kernels of one restart cycle for every member (captured as one graph)
+static cudaError_t enqueue_batch_cycle(KrylovBatch *kb, cudaStream_t st, int64_t *launches) {
+    const KMember *M = kb->dmem;
+    const int2 *W = kb->dwork;
+    int64_t n = 0;
+    b_cycle_init_kernel<<<kb->one_n, 64, 0, st>>>(M, W + kb->one_off); n++;
+    b_scale_kernel<<<kb->red_n, SIM_THREADS, 0, st>>>(M, W + kb->red_off, 0, 1); n++;
+    for (int j = 0; j < kb->m; j++) {
+        const int a = cpr_batch_apply(kb->cpr, st, j);
+        if (a < 0) return cudaErrorLaunchFailure;
+        n += a;
+        if (kb->b == 2) {
+            if (kb->zf) b_spmv_kernel<2, float><<<kb->cell_n, SIM_THREADS, 0, st>>>(M, W + kb->cell_off, j, 0);
+            else b_spmv_kernel<2, double><<<kb->cell_n, SIM_THREADS, 0, st>>>(M, W + kb->cell_off, j, 0);
+        } else {
+            if (kb->zf) b_spmv_kernel<3, float><<<kb->cell_n, SIM_THREADS, 0, st>>>(M, W + kb->cell_off, j, 0);
+            else b_spmv_kernel<3, double><<<kb->cell_n, SIM_THREADS, 0, st>>>(M, W + kb->cell_off, j, 0);
+        }
+        OrthDispatch<SIM_MAX_M>::bdots(j + 1, st, M, W + kb->red_off, kb->red_n);
+        OrthDispatch<SIM_MAX_M>::borth(j + 1, st, M, W + kb->orth_off, kb->orth_n, kb->orth);
+        OrthDispatch<SIM_MAX_M>::bnorm(j + 1, st, M, W + kb->red_off, kb->red_n, kb->m, kb->orth);
+        b_scale_kernel<<<kb->red_n, SIM_THREADS, 0, st>>>(M, W + kb->red_off, j + 1, 0);
+        n += 5;
+    }
+    *launches = n;
+    return cudaGetLastError();
+}
+
+// Solve J_k x_k = rhs_k for the members ms[0..nm) (their bl -> dx, at their
+// own tolerance theta * ||rhs||) by FGMRES(m) with the batched CPR
+// application: every Krylov operation is one launch over all members, a
+// restart cycle is one graph, and a member whose estimate meets its tolerance
+// stops (its kernels return at once) while the others go on.
+sim_status k_fgmres_batch(KrylovBatch *kb, sim_t *const *ms, int nm, cudaStream_t st, sim_linear_info *infos,
+                          std::string *err) {
+    auto fail = [&](const char *what, cudaError_t e) {
+        *err = std::string("batched FGMRES: ") + what + ": " + cudaGetErrorString(e);
+        return SIM_ECUDA;
+    };
+    const sim_t *s0 = ms[0];
+    kb->nm = nm; kb->m = s0->m; kb->b = s0->b; kb->zf = sim_mixed(s0) ? 1 : 0; kb->orth = s0->opt.orth;
+    std::vector<KMember> hm(nm);
+    std::vector<int2> work;
+    auto add = [&](long *off, int *count, int per_member_fixed, bool cells) {
+        *off = (long)work.size();
+        for (int k = 0; k < nm; k++) {
+            const int nb = cells ? sim_blocks(ms[k]->N, SIM_THREADS) : per_member_fixed;
+            for (int q = 0; q < nb; q++) work.push_back(make_int2(k, q));
+        }
+        *count = (int)((long)work.size() - *off);
+    };
+    for (int k = 0; k < nm; k++) {
+        sim_t *s = ms[k];
+        KMember &m = hm[k];
+        m.g = s->gd; m.n = (long)s->N * s->b; m.theta = s->theta; m.J = s->J;
+        m.V = s->V; m.w = s->w; m.r = s->r; m.x = s->dx; m.rhs = s->bl; m.Z = s->Z;
+        m.ctl = s->ctl; m.red = s->red; m.ticket = s->ticket;
+    }
+    add(&kb->red_off, &kb->red_n, SIM_RED_BLOCKS, false);
+    add(&kb->orth_off, &kb->orth_n, 2 * SIM_RED_BLOCKS, false);
+    add(&kb->one_off, &kb->one_n, 1, false);
+    add(&kb->cell_off, &kb->cell_n, 0, true);
+    cudaError_t e;
+    if ((e = kgrow((void **)&kb->dmem, &kb->mem_cap, sizeof(KMember) * nm)) != cudaSuccess) return fail("allocation", e);
+    if ((e = kgrow((void **)&kb->dwork, &kb->work_cap, sizeof(int2) * work.size())) != cudaSuccess) return fail("allocation", e);
+    if (kb->out_cap < nm) {
+        if (kb->dout) cudaFree(kb->dout);
+        if (kb->hout) cudaFreeHost(kb->hout);
+        kb->dout = nullptr; kb->hout = nullptr; kb->out_cap = 0;
+        if ((e = cudaMalloc(&kb->dout, sizeof(double) * 4 * nm)) != cudaSuccess) return fail("allocation", e);
+        if ((e = cudaMallocHost(&kb->hout, sizeof(double) * 4 * nm)) != cudaSuccess) return fail("allocation", e);
+        kb->out_cap = nm;
+    }
+    if ((e = cudaMemcpyAsync(kb->dmem, hm.data(), sizeof(KMember) * nm, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(kb->dwork, work.data(), sizeof(int2) * work.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return fail("table upload", e);
+    if ((e = cpr_batch_build(kb->cpr, ms, nm, st)) != cudaSuccess) return fail("CPR tables", e);   // synchronises st
+    // start: r = b, x = 0, beta = ||b||, tolerance, active
+    b_start_kernel<<<kb->red_n, SIM_THREADS, 0, st>>>(kb->dmem, kb->dwork + kb->red_off);
+    kb->launches++;
+    b_gather_kernel<<<kb->one_n, 32, 0, st>>>(kb->dmem, kb->dwork + kb->one_off, kb->dout);
+    kb->launches++;
+    if ((e = cudaMemcpyAsync(kb->hout, kb->dout, sizeof(double) * 4 * nm, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return fail("start", e);
+    std::vector<double> bnorm(nm);
+    std::vector<char> stopped(nm, 0);
+    int active = 0;
+    for (int k = 0; k < nm; k++) {
+        bnorm[k] = kb->hout[4 * k + 2];
+        infos[k] = sim_linear_info{0, 0, 0, bnorm[k], bnorm[k]};
+        if (bnorm[k] == 0.0) infos[k].converged = 1;
+        if (kb->hout[4 * k] != 0.0) active++;
+        else stopped[k] = 1;            // zero right-hand side (x = 0) or a non-finite one
+    }
+    // the cycle graph: captured for this call's tables (they change with every setup)
+    {
+        cudaGraph_t g = nullptr;
+        if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return fail("capture", e);
+        int64_t nl = 0;
+        const cudaError_t eq = enqueue_batch_cycle(kb, st, &nl);
+        const cudaError_t ec = cudaStreamEndCapture(st, &g);
+        if (eq != cudaSuccess || ec != cudaSuccess) { if (g) cudaGraphDestroy(g); return fail("capture", eq != cudaSuccess ? eq : ec); }
+        kb->nodes = nl;
+        if (kb->exec) {
+            cudaGraphExecUpdateResultInfo ri;
+            if (cudaGraphExecUpdate(kb->exec, g, &ri) != cudaSuccess) {
+                (void)cudaGetLastError();
+                cudaGraphExecDestroy(kb->exec);
+                kb->exec = nullptr;
+            }
+        }
+        if (!kb->exec && (e = cudaGraphInstantiate(&kb->exec, g, 0)) != cudaSuccess) {
+            cudaGraphDestroy(g);
+            kb->exec = nullptr;
+            return fail("instantiate", e);
+        }
+        cudaGraphDestroy(g);
+    }
+    const int maxr = s0->opt.gmres_max_restarts;
+    for (int cyc = 0; cyc <= maxr && active > 0; cyc++) {
+        if ((e = cudaGraphLaunch(kb->exec, st)) != cudaSuccess) return fail("cycle", e);
+        kb->launches += kb->nodes;
+        b_backsolve_kernel<<<kb->one_n, 32, 0, st>>>(kb->dmem, kb->dwork + kb->one_off);
+        if (kb->zf) b_xupdate_kernel<float><<<kb->red_n, SIM_THREADS, 0, st>>>(kb->dmem, kb->dwork + kb->red_off);
+        else b_xupdate_kernel<double><<<kb->red_n, SIM_THREADS, 0, st>>>(kb->dmem, kb->dwork + kb->red_off);
+        if (kb->b == 2) b_spmv_kernel<2, double><<<kb->cell_n, SIM_THREADS, 0, st>>>(kb->dmem, kb->dwork + kb->cell_off, 0, 1);
+        else b_spmv_kernel<3, double><<<kb->cell_n, SIM_THREADS, 0, st>>>(kb->dmem, kb->dwork + kb->cell_off, 0, 1);
+        b_resid_kernel<<<kb->red_n, SIM_THREADS, 0, st>>>(kb->dmem, kb->dwork + kb->red_off);
+        b_gather_kernel<<<kb->one_n, 32, 0, st>>>(kb->dmem, kb->dwork + kb->one_off, kb->dout);
+        kb->launches += 5;
+        if ((e = cudaGetLastError()) != cudaSuccess) return fail("launch", e);
+        if ((e = cudaMemcpyAsync(kb->hout, kb->dout, sizeof(double) * 4 * nm, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess)
+            return fail("cycle end", e);
+        active = 0;
+        for (int k = 0; k < nm; k++) {
+            if (stopped[k]) continue;
+            sim_linear_info &li = infos[k];
+            li.iterations = (int)kb->hout[4 * k + 1];
+            li.r_norm = kb->hout[4 * k + 2];
+            if (kb->hout[4 * k] != 0.0) {          // still above its tolerance: another cycle
+                active++;
+                if (cyc < maxr) li.restarts++;
+                continue;
+            }
+            stopped[k] = 1;                        // met its tolerance, or turned non-finite
+            li.converged = li.r_norm <= ms[k]->theta * bnorm[k] ? 1 : 0;
+            ms[k]->last_cycle_k = (int)kb->hout[4 * k + 3];
+        }
+    }
+    for (int k = 0; k < nm; k++) ms[k]->linear_total += infos[k].iterations;
     return SIM_OK;
 }

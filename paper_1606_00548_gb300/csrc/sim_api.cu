@@ -641,6 +641,79 @@ sim_status sim_newton_step(sim_t *s, double dt, sim_newton_info *info) {
     return fin ? SIM_OK : SIM_ENAN;
 }
 
+}  // extern "C"
+
+// ---- the pieces of a Newton iteration, for the ensemble runtime -------------
+// (the steps newton_solve and sim_step take, in the same order, so that a
+// member advanced by the batch computes what sim_step computes)
+sim_status nl_assemble_test(sim_t *s, double dt, int *state, sim_phase_info *ph) {
+    double cnv, wcnv;
+    if (assemble_and_test(s, dt, &cnv, &wcnv, ph) != SIM_OK) return s->err;
+    if (!(cnv == cnv) || !(wcnv == wcnv)) *state = 2;
+    else if (cnv <= s->opt.newton_tol && wcnv <= s->opt.newton_tol) *state = 1;
+    else *state = 0;
+    return SIM_OK;
+}
+
+// right-hand side -R (+ the rate wells' term) into bl, the preconditioner set up
+sim_status nl_prepare_solve(sim_t *s, sim_phase_info *ph) {
+    const long n = (long)s->N * s->b;
+    SIM_CK(s, cudaEventRecord(s->pev[1], s->stream));
+    if (!s->precond_ready) {
+        if (cpr_setup(s) != SIM_OK) return s->err;
+        ph->setup_bytes += bytes_setup(s);
+    }
+    SIM_CK(s, cudaEventRecord(s->pev[2], s->stream));
+    negate_kernel<<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(s->R, s->bl, n);
+    SIM_LAUNCHED(s);
+    if (k_well_rhs(s, s->bl) != SIM_OK) return s->err;
+    s->theta = s->opt.lin_tol;
+    SIM_CK(s, cudaEventSynchronize(s->pev[2]));
+    ph->setup_us += event_us(s->pev[1], s->pev[2]);
+    SIM_CK(s, cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}
+
+// after the (batched) solve of dx: finiteness, the wells' and cells' update
+sim_status nl_finish_solve(sim_t *s, const sim_linear_info &li, bool *finite_ok, sim_phase_info *ph) {
+    const long n = (long)s->N * s->b;
+    ph->solve_bytes += bytes_solve(s, li);
+    *finite_ok = li.r_norm == li.r_norm;
+    if (!*finite_ok) return SIM_OK;
+    SIM_CK(s, cudaEventRecord(s->pev[3], s->stream));
+    int ok = 1;
+    if (k_finite(s, s->dx, n, &ok) != SIM_OK) return s->err;
+    *finite_ok = ok != 0;
+    if (!ok) return SIM_OK;
+    if (k_well_update(s, s->dx) != SIM_OK) return s->err;
+    if (k_newton_update(s, s->dx) != SIM_OK) return s->err;
+    SIM_CK(s, cudaEventRecord(s->pev[4], s->stream));
+    SIM_CK(s, cudaEventSynchronize(s->pev[4]));
+    ph->update_us += event_us(s->pev[3], s->pev[4]);
+    ph->update_bytes += bytes_update(s);
+    s->newton_total++;
+    return SIM_OK;
+}
+
+// the start of the step again (a failed Newton solve, before the step is halved)
+sim_status nl_restore(sim_t *s) {
+    SIM_CK(s, cudaMemcpyAsync(s->x, s->x_old, sizeof(double) * s->N * s->b, cudaMemcpyDeviceToDevice, s->stream));
+    SIM_CK(s, cudaMemcpyAsync(s->ph, s->ph_old, s->N, cudaMemcpyDeviceToDevice, s->stream));
+    if (s->nwells)
+        SIM_CK(s, cudaMemcpyAsync(s->wp, s->wp_old, sizeof(double) * s->nwells, cudaMemcpyDeviceToDevice, s->stream));
+    return SIM_OK;
+}
+
+// the current iterate becomes the accepted state of a step of length dt
+sim_status accept_step(sim_t *s, double dt) {
+    SIM_CK(s, cudaMemcpyAsync(s->h_pinned, s->qtot, sizeof(double) * 3, cudaMemcpyDeviceToHost, s->stream));
+    SIM_CK(s, cudaStreamSynchronize(s->stream));
+    for (int c = 0; c < 3; c++) s->cum_well[c] += dt * s->h_pinned[c];
+    return begin_step(s);
+}
+
+extern "C" {
+
 // Newton loop; returns 0 converged, 1 not converged, 2 non-finite
 static int newton_solve(sim_t *s, double dt, sim_newton_info *ni) {
     memset(ni, 0, sizeof(*ni));
@@ -672,13 +745,6 @@ sim_status sim_newton_solve(sim_t *s, double dt, sim_newton_info *info) {
     return rc == 0 ? SIM_OK : (rc == 2 ? SIM_ENAN : SIM_ENOCONV_NEWTON);
 }
 
-// the current iterate becomes the accepted state of a step of length dt
-static sim_status accept_step(sim_t *s, double dt) {
-    SIM_CK(s, cudaMemcpyAsync(s->h_pinned, s->qtot, sizeof(double) * 3, cudaMemcpyDeviceToHost, s->stream));
-    SIM_CK(s, cudaStreamSynchronize(s->stream));
-    for (int c = 0; c < 3; c++) s->cum_well[c] += dt * s->h_pinned[c];
-    return begin_step(s);
-}
 
 sim_status sim_accept_step(sim_t *s, double dt) {
     CHECK_HANDLE(s);
@@ -708,10 +774,7 @@ sim_status sim_step(sim_t *s, double dt, sim_step_info *info) {
             remaining -= h;
             si.substeps++;
         } else {
-            SIM_CK(s, cudaMemcpyAsync(s->x, s->x_old, sizeof(double) * s->N * s->b, cudaMemcpyDeviceToDevice, s->stream));
-            SIM_CK(s, cudaMemcpyAsync(s->ph, s->ph_old, s->N, cudaMemcpyDeviceToDevice, s->stream));
-            if (s->nwells)
-                SIM_CK(s, cudaMemcpyAsync(s->wp, s->wp_old, sizeof(double) * s->nwells, cudaMemcpyDeviceToDevice, s->stream));
+            if (nl_restore(s) != SIM_OK) return s->err;
             si.cuts++;
             if (si.cuts > s->opt.max_cuts) { st = SIM_ENOCONV_NEWTON; break; }
             h *= 0.5;

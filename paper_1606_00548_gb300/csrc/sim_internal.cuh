@@ -37,14 +37,29 @@ struct GridDesc {
 struct KrylovCtl {
     int done;           // 1 once the Arnoldi residual estimate met the tolerance
     int k;              // inner iterations completed in the current cycle
-    int breakdown;
-    int pad;
+    int active;         // batched solves: 1 while this member's solve goes on
+    int iters;          // batched solves: inner iterations of this member's solve
     double tol, beta, rnorm2;
     double h[SIM_MAX_M + 1], h2[SIM_MAX_M + 1];
     double g[SIM_MAX_M + 1], cs[SIM_MAX_M + 1], sn[SIM_MAX_M + 1], y[SIM_MAX_M + 1];
     double H[(SIM_MAX_M + 1) * (SIM_MAX_M + 1)];
     unsigned int counter;   // last-block reduction ticket
     unsigned int pad2;
+};
+
+// One member of a batched FGMRES solve (an ensemble of independent systems):
+// its operands, read by the batched kernels from a device table
+struct KMember {
+    GridDesc g;
+    long n;                  // b N
+    double theta;            // relative tolerance of this member's solve
+    const double *J;
+    double *V, *w, *r, *x;   // Krylov basis, work vector, residual, solution
+    const double *rhs;       // right-hand side; null: the member does not solve in this round
+    void *Z;                 // preconditioned directions (FP64 or FP32)
+    KrylovCtl *ctl;
+    double *red;             // the member's reduction partials and ticket
+    unsigned int *ticket;
 };
 
 // BiCGSTAB scalars (device); flag: 1 recursive residual met the tolerance,
@@ -196,6 +211,13 @@ sim_status k_component_mass(sim_t *s, double *m3_host);
 sim_status k_newton_update(sim_t *s, const double *dx);
 sim_status k_finite(sim_t *s, const double *v, long n, int *ok_host);
 
+// ---- sim_api.cu: the pieces of a Newton iteration (ensemble runtime) --------
+sim_status nl_assemble_test(sim_t *s, double dt, int *state, sim_phase_info *ph);   // 0 solve, 1 converged, 2 non-finite
+sim_status nl_prepare_solve(sim_t *s, sim_phase_info *ph);
+sim_status nl_finish_solve(sim_t *s, const sim_linear_info &li, bool *finite_ok, sim_phase_info *ph);
+sim_status nl_restore(sim_t *s);
+sim_status accept_step(sim_t *s, double dt);
+
 // ---- krylov.cu ------------------------------------------------------------
 sim_status k_spmv(sim_t *s, const double *x, double *y);                 // y = J x
 sim_status k_spmv_f(sim_t *s, const float *x, double *y);
@@ -205,6 +227,13 @@ sim_status k_linear_solve(sim_t *s, const double *b, double *x, sim_linear_info 
 sim_status k_diff_norm2(sim_t *s, const double *a, const double *b, long n, double *out);
 sim_status k_norm2(sim_t *s, const double *v, long n, double *out_host);
 sim_status k_spmv_block(sim_t *s, const double *x, double *y, int block);
+// FGMRES batched over ensemble members: every Krylov operation one launch for all
+struct KrylovBatch;
+KrylovBatch *k_batch_new();
+void k_batch_free(KrylovBatch *kb);
+int64_t k_batch_launches(const KrylovBatch *kb);
+sim_status k_fgmres_batch(KrylovBatch *kb, sim_t *const *ms, int nm, cudaStream_t st, sim_linear_info *infos,
+                          std::string *err);
 sim_status k_orth_step(sim_t *s, int nv);              // measurement: one Arnoldi orthogonalisation step
 double k_orth_step_bytes(const sim_t *s, int nv);      // its algorithmic bytes
 
@@ -212,6 +241,13 @@ double k_orth_step_bytes(const sim_t *s, int nv);      // its algorithmic bytes
 sim_status cpr_setup(sim_t *s);
 sim_status cpr_apply(sim_t *s, const double *r, void *z, const int *done);   // z FP64 or FP32 (Z type)
 void cpr_free(sim_t *s);
+// batched CPR application over ensemble members (tables and work lists)
+struct CprBatch;
+bool cpr_batchable(sim_t *const *ms, int nm);
+CprBatch *cpr_batch_new();
+void cpr_batch_free(CprBatch *cb);
+cudaError_t cpr_batch_build(CprBatch *cb, sim_t *const *ms, int nm, cudaStream_t st);   // after every member's setup
+int cpr_batch_apply(const CprBatch *cb, cudaStream_t st, int j);                         // launches, or -1
 sim_status cpr_copy_level_ell(sim_t *s, int level, int *col, double *val);
 sim_status cpr_learned_pairs(sim_t *s, int k, float *x_dev, float *y_dev);
 sim_status cpr_learned_features(sim_t *s);

@@ -151,6 +151,10 @@ _SIGS = {
     "sim_batch_create": ([C.c_int32, C.POINTER(_vp), C.c_int32, C.POINTER(_vp)], C.c_int),
     "sim_batch_destroy": ([_vp], None),
     "sim_batch_step": ([_vp, _dp, C.POINTER(sim_step_info), C.POINTER(C.c_int)], C.c_int),
+    "sim_batch_set_mode": ([_vp, C.c_int32], C.c_int),
+    "sim_batch_mode": ([_vp], C.c_int32),
+    "sim_batch_stats": ([_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)], C.c_int),
+    "sim_batch_last_error": ([_vp], C.c_char_p),
     "sim_net_create": ([C.c_int32, C.c_int32, C.c_int32, C.c_uint64, _vp, C.POINTER(_vp)], C.c_int),
     "sim_net_destroy": ([_vp], None),
     "sim_net_param_count": ([_vp], C.c_int64),
@@ -530,10 +534,14 @@ class Simulator:
         _check(self.h, self.L.sim_autotune(self.h, float(dt)))
 
 
-class Batch:
-    """Concurrent time stepping of independent simulators (sim_batch_*)."""
+SIM_BATCH_LOCKSTEP, SIM_BATCH_CONCURRENT = 0, 1
 
-    def __init__(self, members, nthreads=0):
+
+class Batch:
+    """Time stepping of independent simulators together (sim_batch_*):
+    lockstep rounds with one batched solve per round, or concurrent members."""
+
+    def __init__(self, members, nthreads=0, mode=None):
         self.L = load()
         self.members = list(members)
         arr = (_vp * len(self.members))(*[m.h for m in self.members])
@@ -542,6 +550,21 @@ class Batch:
         if st != SIM_OK:
             raise SimError(st, (self.L.sim_last_error(None) or b"").decode())
         self.h = h
+        if mode is not None:
+            st = self.L.sim_batch_set_mode(self.h, int(mode))
+            if st != SIM_OK:
+                raise SimError(st, "sim_batch_set_mode: mode not available for these members")
+
+    def mode(self):
+        return self.L.sim_batch_mode(self.h)
+
+    def stats(self):
+        r, s, l = C.c_int64(), C.c_int64(), C.c_int64()
+        self.L.sim_batch_stats(self.h, C.byref(r), C.byref(s), C.byref(l))
+        return dict(rounds=r.value, solves=s.value, launches=l.value)
+
+    def last_error(self):
+        return (self.L.sim_batch_last_error(self.h) or b"").decode()
 
     def step(self, dts):
         n = len(self.members)
