@@ -78,15 +78,26 @@ def solver_desc(sv: dict) -> str:
             f"{kry}, {forcing}, CNV {sv.get('newton_tol', 1e-10):g}")
 
 
-def kernel_sha1(name: str) -> str:
-    """SHA-1 of a kernel's source text in csrc/krylov.cu (template line to the
-    closing brace), so recorded ncu counters are dropped once the kernel changes."""
+def kernel_sha1(*names: str) -> str:
+    """SHA-1 of kernel sources in csrc/krylov.cu (each from its template line to
+    the closing brace), so recorded ncu counters are dropped once they change."""
     import hashlib
     src = open(os.path.join(ROOT, "paper_1606_00548_gb300", "csrc", "krylov.cu")).read()
-    i = src.index(f" {name}(")
-    i = src.rindex("template", 0, i)
-    j = src.index("\n}\n", i)
-    return hashlib.sha1(src[i:j].encode()).hexdigest()
+    h = hashlib.sha1()
+    for name in names:
+        i = src.index(f" {name}(")
+        i = src.rindex("template", 0, i) if name != "scale_body" else src.rindex("\n", 0, i) + 1
+        j = src.index("\n}\n", i)
+        h.update(src[i:j].encode())
+    return h.hexdigest()
+
+
+# the Gram-Schmidt kernels' bodies (one Arnoldi step: dots, second pass, update and norm, scale)
+GS_SOURCES = ("dots_body", "orth_dots_body", "orth_norm_body", "scale_body")
+
+# FP64 rate of GB300 from the profiling recipe's unit counts and clocks: 152 SMs x
+# 2 FP64 FMA per clock x 2 FLOP x 2.07 GHz (1.26; the recipe's table: 1.25 TFLOP/s)
+FP64_NOMINAL_TFLOPS = 1.25
 
 
 class ClockSampler:
@@ -434,12 +445,19 @@ def run_ours(args):
                               "hbm_gbs": bytes_orth / t_orth / 1e9, "hbm_frac": bytes_orth / t_orth / 1e9 / hbm_peak},
         "cpr_apply": {"what": "one CPR application (restriction, V-cycle, stage F)", "launch_us": t_prec * 1e6},
     }
+    # one CGS2 Arnoldi step at NV basis vectors: dots NV + 1 FMAs per element,
+    # second pass (update and dots) 2 NV, update and norm NV + 1, scale 1
+    flops_orth = 2 * (4 * nv + 3) * n
+    kernels["gram_schmidt_step"].update(fp64_tflops=flops_orth / t_orth / 1e12,
+                                        fp64_frac=flops_orth / t_orth / 1e12 / FP64_NOMINAL_TFLOPS)
+    kernels["spmv_kernel"]["fp64_frac"] = flops_spmv / t_spmv / 1e12 / FP64_NOMINAL_TFLOPS
     dom = kernels["gram_schmidt_step"]
     traffic = None
     try:
         ctr = json.load(open(os.path.join(ROOT, "profiles", "roofline_counters.json")))[f"gram_schmidt_step<{b}>"]
-        if ctr.get("kernel_sha1") == kernel_sha1("orth_norm_kernel") and ctr.get("nv") == nv:
-            traffic = ctr["dram_bytes_per_cell"] * N
+        # counters count only for the kernel sources they were taken on
+        if ctr.get("kernel_sha1") == kernel_sha1(*GS_SOURCES) and ctr.get("nv") == nv:
+            traffic = ctr["dram_bytes_per_element"] * n
     except Exception:
         traffic = None
 
@@ -470,9 +488,16 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": iterate_bytes,
                     "d2h_bytes_per_step": iterate_bytes},
             "gpu_launches": int(st1.kernel_launches - st0.kernel_launches),
-            "roofline": {"kernel": dom["what"], "bound": "hbm", "achieved": dom["hbm_gbs"], "peak": hbm_peak,
-                         "unit": "GB/s", "frac": dom["hbm_frac"], "traffic": traffic, "peak_source": hbm_src,
-                         "bytes_per_launch": dom["bytes"], "launch_us": dom["launch_us"]},
+            "roofline": {"kernel": dom["what"], "bound": "alu", "achieved": dom["fp64_tflops"],
+                         "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s", "frac": dom["fp64_frac"],
+                         "traffic": traffic,
+                         "peak_source": "FP64 pipe: 152 SMs x 2 FMA/clk x 2.07 GHz (profiling recipe); FMA loops "
+                                        f"measure {fp64_tflops:.3f} TFLOP/s at best, the FP64 SpMV of this run "
+                                        f"{kernels['spmv_kernel']['fp64_tflops']:.3f}",
+                         "flops_per_launch": flops_orth, "launch_us": dom["launch_us"],
+                         "hbm_achieved_gbs": dom["hbm_gbs"], "hbm_peak_gbs": hbm_peak, "hbm_frac": dom["hbm_frac"],
+                         "hbm_peak_source": hbm_src, "bytes_per_launch": dom["bytes"],
+                         "share_of_kernel_time": "37% (profiles/launch_list_black_oil_400cube.md)"},
             "kernels": kernels,
             "fp64_probe_tflops": fp64_tflops,
             "phases_per_newton": {k: v / newton for k, v in phases.items()},

@@ -997,9 +997,10 @@ template <int B, typename T>
 __device__ __forceinline__ void restrict_p_row(int N, const double *__restrict__ r, const T *__restrict__ wT, int full,
                                                const T *__restrict__ dinv0, T *__restrict__ f0, T *__restrict__ e0,
                                                int i) {
+    // explicit FMAs: the same rounding in every kernel that inlines the row
     const T r0 = full ? wT[i] * (T)r[i] : (T)r[i];
-    T t = r0 + wT[(long)N + i] * (T)r[(long)N + i];
-    if (B == 3) t += wT[2L * N + i] * (T)r[2L * N + i];
+    T t = fma(wT[(long)N + i], (T)r[(long)N + i], r0);
+    if (B == 3) t = fma(wT[2L * N + i], (T)r[2L * N + i], t);
     f0[i] = t;
     e0[i] = t * dinv0[i];
 }
@@ -1249,15 +1250,15 @@ __device__ __forceinline__ void stage2_a_row(const GridDesc &g, const double *__
         for (int c = 0; c < B; c++) u[c] = (T)r[(long)c * N + i];
 #pragma unroll
         for (int rr = 0; rr < B; rr++) {
-            T t = lscT[(long)(rr * B) * N + i] * u[0] + lscT[(long)(rr * B + 1) * N + i] * u[1];
-            if (B == 3) t += lscT[(long)(rr * B + 2) * N + i] * u[2];
+            T t = fma(lscT[(long)(rr * B + 1) * N + i], u[1], lscT[(long)(rr * B) * N + i] * u[0]);
+            if (B == 3) t = fma(lscT[(long)(rr * B + 2) * N + i], u[2], t);
             v[rr] = t;
         }
     } else {
 #pragma unroll
         for (int c = 0; c < B; c++) v[c] = (T)r[(long)c * N + i];
-        T rp = v[0] + wT[(long)N + i] * v[1];
-        if (B == 3) rp += wT[2L * N + i] * v[2];
+        T rp = fma(wT[(long)N + i], v[1], v[0]);
+        if (B == 3) rp = fma(wT[2L * N + i], v[2], rp);
         v[0] = rp;
     }
     const Cell cc = cell_of(g, i);

@@ -274,13 +274,15 @@ __device__ __forceinline__ void orth_norm_body(const double *__restrict__ V, dou
         if (threadIdx.x == 0) {
             *ticket = 0u;
             const double hn = sqrt(nrm);
+            // two-product sums written as explicit FMAs: every kernel that
+            // inlines this body (one system or a batch) rounds them alike
             for (int k = 0; k < j; k++) {
                 const double a = col[k], c2 = col[k + 1];
-                col[k] = rcs[k] * a + rsn[k] * c2;
-                col[k + 1] = -rsn[k] * a + rcs[k] * c2;
+                col[k] = fma(rcs[k], a, rsn[k] * c2);
+                col[k + 1] = fma(-rsn[k], a, rcs[k] * c2);
             }
             const double a = col[j], bb = hn;
-            const double rr = sqrt(a * a + bb * bb);
+            const double rr = sqrt(fma(a, a, bb * bb));
             double c, s;
             if (rr == 0.0) { c = 1.0; s = 0.0; }
             else { c = a / rr; s = bb / rr; }
