@@ -461,6 +461,38 @@ def run_ours(args):
     except Exception:
         traffic = None
 
+    # time to the 1e-8 relative residual per Newton system (CPR set-up and
+    # CPR-FGMRES solve, the phases of the timed iterations)
+    def per_system(ph, its):
+        return {"setup_s": ph.get("setup_us", 0.0) / 1e6 / its, "solve_s": ph.get("solve_us", 0.0) / 1e6 / its,
+                "to_tolerance_s": (ph.get("setup_us", 0.0) + ph.get("solve_us", 0.0)) / 1e6 / its}
+    forms = {args.precision: dict(value=value, linear_iterations_per_newton=lin / newton, **per_system(phases, newton))}
+    if prec == 0 and args.mixed_steps > 0:
+        # the same workload with the FP32 preconditioner (FP64 Krylov loop, residual,
+        # update): a second handle after the first is freed (both do not fit in HBM)
+        sim.close()
+        torch.cuda.synchronize()
+        simm = Simulator(case, precision=1, stream=stream.cuda_stream)
+        drm = NewtonDriver(simm, case["dt"])
+        for _ in range(2):
+            drm.iteration()
+        evm = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.mixed_steps)]
+        lin_m, ph_m = 0, {}
+        torch.cuda.synchronize()
+        for k in range(args.mixed_steps):
+            evm[k][0].record(stream)
+            info, ph = drm.iteration()
+            evm[k][1].record(stream)
+            lin_m += info.linear_iterations
+            for key, v in ph.items():
+                ph_m[key] = ph_m.get(key, 0.0) + v
+        torch.cuda.synchronize()
+        t_m = sum(a.elapsed_time(b_) for a, b_ in evm) / 1e3
+        forms["mixed"] = dict(value=N * args.mixed_steps / t_m, linear_iterations_per_newton=lin_m / args.mixed_steps,
+                              newton_iterations=args.mixed_steps, **per_system(ph_m, args.mixed_steps))
+        forms["mixed_over_fp64_time_to_tolerance"] = forms["mixed"]["to_tolerance_s"] / forms["fp64"]["to_tolerance_s"]
+        simm.close()
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         ocase, _, where = oracle_sample_case(args, case, desc)
@@ -501,6 +533,7 @@ def run_ours(args):
             "kernels": kernels,
             "fp64_probe_tflops": fp64_tflops,
             "phases_per_newton": {k: v / newton for k, v in phases.items()},
+            "forms": forms,
             "clocks": clocks,
             "cpu_baseline": cpu,
         }
@@ -647,6 +680,8 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--workload", default="bo400", choices=["bo100", "bo100c", "bo200", "bo400", "learned", "ensemble"])
     ap.add_argument("--oracle-cut", type=int, default=48, help="edge of the corner cut the oracle runs on")
+    ap.add_argument("--mixed-steps", type=int, default=3,
+                    help="Newton iterations of the FP32-preconditioner form timed after the FP64 ones (0: none)")
     ap.add_argument("--train-steps", type=int, default=300)
     ap.add_argument("--amg-cycles", type=int, default=None, help="V-cycles per CPR pressure stage")
     ap.add_argument("--solver", default="default", choices=["default", "paper"],
