@@ -192,6 +192,7 @@ typedef struct {
     int64_t newton_iterations, linear_iterations;
     int64_t device_bytes;       /* device memory held by the handle */
     int32_t spmv_block, amg_block;   /* launch shapes in use (see sim_autotune) */
+    int32_t stage_block;             /* threads per block of the stage-F sweeps */
 } sim_stats;
 
 /* Create a simulator (copies every host array).  Validates sizes, table
@@ -321,10 +322,18 @@ sim_status sim_cnv_noalloc(int32_t nx, int32_t ny, int32_t nz, double dx, double
 
 /* Autotuner: assembles at the current iterate for step dt, then times the
    block SpMV with blocks of 64..512 threads and one CPR application with
-   AMG level kernels of 64..256 threads, and keeps the fastest shapes for
-   this handle.  Results do not depend on the shapes (each row's arithmetic
-   is the same); only speed does. */
+   AMG level kernels of 64..256 threads and stage-F sweeps of 32..256
+   threads, and keeps the fastest shapes for this handle.  Results do not
+   depend on the shapes (each row's arithmetic is the same); only speed does. */
 sim_status sim_autotune(sim_t *s, double dt);
+/* The same with the shapes cached in a JSON file (created if absent), one
+   entry per (block size, precision, grid dimensions):
+     {"b3_fp64_100x100x20": {"spmv": 256, "amg": 128, "stage": 64}, ...}
+   An entry for this handle's key is applied without timing (*from_cache = 1);
+   otherwise sim_autotune runs and its shapes are written into the file
+   (*from_cache = 0; the file is replaced by rename, so readers never see a
+   partial one).  from_cache may be NULL. */
+sim_status sim_autotune_cached(sim_t *s, double dt, const char *json_path, int32_t *from_cache);
 /* Device time of one hot operation (measurement only; no paper counterpart):
    `reps` launches on the handle's stream, each bracketed by CUDA events and
    preceded by a 256 MB write that evicts its operands from L2.  which = 0: the

@@ -1875,8 +1875,9 @@ static int colour_blocks(const sim_t *s, int threads = SIM_THREADS) {
     return sim_blocks((long)((s->gd.nx + 1) / 2) * s->gd.ny * s->gd.nz, threads);
 }
 
-// stage-F sweeps in blocks of 64 threads: at 0.3-0.6 waves the finer blocks
-// spread a launch's FP64 work more evenly over the SMs than blocks of 256
+// stage-F sweeps of a batched application in blocks of 64 threads (the default of
+// sim_autotune's stage-F shape: at 0.3-0.6 waves the finer blocks spread a
+// launch's FP64 work more evenly over the SMs than blocks of 256)
 constexpr int kStageThreads = 64;
 
 template <int B, typename T>
@@ -2029,16 +2030,16 @@ static sim_status apply_btz(sim_t *s, const double *r, TZ *z, const int *done) {
     const bool fpf = s->opt.cpr_stages == 3;
     if (fpf) {
         // CPR-FPF: stage F on L r first (x0), then stage P on the residual it leaves
-        stage2_a_kernel<B, T><<<sim_blocks(N, kStageThreads), kStageThreads, 0, s->stream>>>(s->gd, r, (const T *)s->qiwT, lscT, nullptr,
+        stage2_a_kernel<B, T><<<sim_blocks(N, s->tune_stage), s->tune_stage, 0, s->stream>>>(s->gd, r, (const T *)s->qiwT, lscT, nullptr,
                                                                 (const T *)s->ahat, dinv, nullptr, (T *)s->r2,
                                                                 (T *)s->zr, rb, done);
         SIM_LAUNCHED(s);
         if (rb) {
-            stage2_b_kernel<B, T, T><<<colour_blocks(s, kStageThreads), kStageThreads, 0, s->stream>>>(s->gd, (const T *)s->ahat, dinv, (const T *)s->r2,
+            stage2_b_kernel<B, T, T><<<colour_blocks(s, s->tune_stage), s->tune_stage, 0, s->stream>>>(s->gd, (const T *)s->ahat, dinv, (const T *)s->r2,
                                                                        (T *)s->zr, nullptr, nullptr, (T *)s->x0, done);
             SIM_LAUNCHED(s);
         }
-        stage2_c_kernel<B, T, T><<<rb ? colour_blocks(s, kStageThreads) : sim_blocks(N, kStageThreads), kStageThreads, 0, s->stream>>>(s->gd, (const T *)s->ahat, dinv, (const T *)s->zr,
+        stage2_c_kernel<B, T, T><<<rb ? colour_blocks(s, s->tune_stage) : sim_blocks(N, s->tune_stage), s->tune_stage, 0, s->stream>>>(s->gd, (const T *)s->ahat, dinv, (const T *)s->zr,
                                                                    nullptr, nullptr, (T *)s->x0, rb, done);
         SIM_LAUNCHED(s);
         fpf_resid_kernel<B, T><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, r, (const T *)s->qiwT, lscT, (const T *)s->ahat,
@@ -2099,16 +2100,16 @@ static sim_status apply_btz(sim_t *s, const double *r, TZ *z, const int *done) {
         ep = (const T *)s->lep;
     }
     const T *addv = fpf ? (const T *)s->x0 : nullptr;
-    stage2_a_kernel<B, T><<<sim_blocks(N, kStageThreads), kStageThreads, 0, s->stream>>>(s->gd, fpf ? nullptr : r, (const T *)s->qiwT, lscT,
+    stage2_a_kernel<B, T><<<sim_blocks(N, s->tune_stage), s->tune_stage, 0, s->stream>>>(s->gd, fpf ? nullptr : r, (const T *)s->qiwT, lscT,
                                                             (const T *)s->rhT, (const T *)s->ahat, dinv, ep, (T *)s->r2,
                                                             (T *)s->zr, rb, done);
     SIM_LAUNCHED(s);
     if (rb) {
-        stage2_b_kernel<B, T, TZ><<<colour_blocks(s, kStageThreads), kStageThreads, 0, s->stream>>>(s->gd, (const T *)s->ahat, dinv, (const T *)s->r2,
+        stage2_b_kernel<B, T, TZ><<<colour_blocks(s, s->tune_stage), s->tune_stage, 0, s->stream>>>(s->gd, (const T *)s->ahat, dinv, (const T *)s->r2,
                                                                     (T *)s->zr, ep, addv, z, done);
         SIM_LAUNCHED(s);
     }
-    stage2_c_kernel<B, T, TZ><<<rb ? colour_blocks(s, kStageThreads) : sim_blocks(N, kStageThreads), kStageThreads, 0, s->stream>>>(s->gd, (const T *)s->ahat, dinv, (const T *)s->zr, ep, addv,
+    stage2_c_kernel<B, T, TZ><<<rb ? colour_blocks(s, s->tune_stage) : sim_blocks(N, s->tune_stage), s->tune_stage, 0, s->stream>>>(s->gd, (const T *)s->ahat, dinv, (const T *)s->zr, ep, addv,
                                                                 z, rb, done);
     SIM_LAUNCHED(s);
     return SIM_OK;

@@ -1065,6 +1065,7 @@ sim_status sim_get_stats(sim_t *s, sim_stats *st) {
     st->device_bytes = (int64_t)s->bytes;
     st->spmv_block = s->tune_spmv;
     st->amg_block = s->tune_amg;
+    st->stage_block = s->tune_stage;
     return SIM_OK;
 }
 
@@ -1093,10 +1094,78 @@ sim_status sim_autotune(sim_t *s, double dt) {
             if (ms < best) { best = ms; pick = bs; }
         }
         s->tune_amg = pick;
+        static const int stage_cand[] = {32, 64, 128, 256};
+        best = 1e30f;
+        pick = s->tune_stage;
+        for (int bs : stage_cand) {
+            s->tune_stage = bs;
+            const float ms = time_launches(s, 3, [&] { cpr_apply(s, s->bl, s->Z, nullptr); });
+            if (ms < best) { best = ms; pick = bs; }
+        }
+        s->tune_stage = pick;
     }
     s->setup_gen++;   // the captured restart cycle used the old launch shapes
     SIM_CK(s, cudaGetLastError());
     SIM_CK(s, cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}
+
+// ---- launch shapes cached in a JSON file ---------------------------------
+// one entry per line, {"b<b>_<fp64|mixed>_<nx>x<ny>x<nz>": {"spmv": S, "amg": A, "stage": F}}
+static std::string tune_key(const sim_t *s) {
+    char k[128];
+    snprintf(k, sizeof(k), "b%d_%s_%dx%dx%d", s->b, sim_mixed(s) ? "mixed" : "fp64", s->gd.nx, s->gd.ny, s->gd.nz);
+    return k;
+}
+
+struct TuneEntry { std::string key; int spmv, amg, stage; };
+
+static std::vector<TuneEntry> read_tune_file(const char *path) {
+    std::vector<TuneEntry> out;
+    FILE *f = fopen(path, "r");
+    if (!f) return out;
+    char line[512], key[160];
+    int a, b, c;
+    while (fgets(line, sizeof(line), f)) {
+        if (sscanf(line, " \"%159[^\"]\": {\"spmv\": %d, \"amg\": %d, \"stage\": %d}", key, &a, &b, &c) == 4)
+            out.push_back(TuneEntry{key, a, b, c});
+    }
+    fclose(f);
+    return out;
+}
+
+static bool shape_ok(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
+
+sim_status sim_autotune_cached(sim_t *s, double dt, const char *json_path, int32_t *from_cache) {
+    CHECK_HANDLE(s);
+    if (!json_path) return sim_fail(s, SIM_EINVAL, "sim_autotune_cached: NULL path");
+    const std::string key = tune_key(s);
+    std::vector<TuneEntry> tab = read_tune_file(json_path);
+    for (const TuneEntry &e : tab) {
+        if (e.key == key && shape_ok(e.spmv, 32, 512) && shape_ok(e.amg, 32, 1024) && shape_ok(e.stage, 32, 1024)) {
+            s->tune_spmv = e.spmv; s->tune_amg = e.amg; s->tune_stage = e.stage;
+            s->setup_gen++;
+            if (from_cache) *from_cache = 1;
+            return SIM_OK;
+        }
+    }
+    if (sim_autotune(s, dt) != SIM_OK) return s->err;
+    if (from_cache) *from_cache = 0;
+    bool found = false;
+    for (TuneEntry &e : tab)
+        if (e.key == key) { e.spmv = s->tune_spmv; e.amg = s->tune_amg; e.stage = s->tune_stage; found = true; }
+    if (!found) tab.push_back(TuneEntry{key, s->tune_spmv, s->tune_amg, s->tune_stage});
+    // write a new file and move it over the old one (readers never see half a file)
+    const std::string tmp = std::string(json_path) + ".tmp";
+    FILE *f = fopen(tmp.c_str(), "w");
+    if (!f) return sim_fail(s, SIM_EINVAL, std::string("sim_autotune_cached: cannot write ") + tmp);
+    fprintf(f, "{\n");
+    for (size_t i = 0; i < tab.size(); i++)
+        fprintf(f, "\"%s\": {\"spmv\": %d, \"amg\": %d, \"stage\": %d}%s\n", tab[i].key.c_str(), tab[i].spmv,
+                tab[i].amg, tab[i].stage, i + 1 < tab.size() ? "," : "");
+    fprintf(f, "}\n");
+    const bool ok = fclose(f) == 0 && rename(tmp.c_str(), json_path) == 0;
+    if (!ok) return sim_fail(s, SIM_EINVAL, std::string("sim_autotune_cached: cannot replace ") + json_path);
     return SIM_OK;
 }
 

@@ -142,7 +142,7 @@ struct sim {
     cudaGraphExec_t cycle_exec = nullptr;   // captured restart cycle
     int64_t setup_gen = 0, cycle_gen = -1, graph_nodes = 0;
     int cycle_learned = -1;                  // learned-stage state the graph was captured with
-    int tune_spmv = SIM_THREADS, tune_amg = 128;   // block sizes picked by sim_autotune
+    int tune_spmv = SIM_THREADS, tune_amg = 128, tune_stage = 64;   // block sizes picked by sim_autotune
     int last_cycle_k = 0;                    // inner iterations of the last restart cycle
     // BiCGSTAB: control block and the graph of one chunk of iterations
     BicgCtl *bctl = nullptr, *bctl_host = nullptr;

@@ -103,7 +103,7 @@ class sim_step_info(C.Structure):
 class sim_stats(C.Structure):
     _fields_ = [("kernel_launches", C.c_int64), ("newton_iterations", C.c_int64),
                 ("linear_iterations", C.c_int64), ("device_bytes", C.c_int64),
-                ("spmv_block", C.c_int32), ("amg_block", C.c_int32)]
+                ("spmv_block", C.c_int32), ("amg_block", C.c_int32), ("stage_block", C.c_int32)]
 
 
 _SIGS = {
@@ -148,6 +148,7 @@ _SIGS = {
                          _vp, _vp, _dp, C.c_double, _vp, _vp], C.c_int),
     "sim_probe_fma_rates": ([_dp, _dp], C.c_int),
     "sim_autotune": ([_vp, C.c_double], C.c_int),
+    "sim_autotune_cached": ([_vp, C.c_double, C.c_char_p, C.POINTER(C.c_int32)], C.c_int),
     "sim_batch_create": ([C.c_int32, C.POINTER(_vp), C.c_int32, C.POINTER(_vp)], C.c_int),
     "sim_batch_destroy": ([_vp], None),
     "sim_batch_step": ([_vp, _dp, C.POINTER(sim_step_info), C.POINTER(C.c_int)], C.c_int),
@@ -529,6 +530,11 @@ class Simulator:
 
     def stats(self):
         s = sim_stats(); _check(self.h, self.L.sim_get_stats(self.h, C.byref(s))); return s
+
+    def autotune_cached(self, dt, path):
+        hit = C.c_int32()
+        _check(self.h, self.L.sim_autotune_cached(self.h, float(dt), os.fsencode(path), C.byref(hit)))
+        return bool(hit.value)
 
     def autotune(self, dt):
         _check(self.h, self.L.sim_autotune(self.h, float(dt)))

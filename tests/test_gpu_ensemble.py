@@ -136,3 +136,28 @@ def test_autotune_does_not_change_results(torch_cuda):
         a.step(dt); b.step(dt)
     for u, v in zip(a.get_state(), b.get_state()):
         assert np.array_equal(u, v)
+
+
+def test_autotune_cache_round_trip(torch_cuda, tmp_path):
+    """The tuned shapes go into the JSON cache on the first call and come back
+    from it, without timing, for another handle of the same grid; results do
+    not depend on them."""
+    import json
+    from paper_1606_00548_gb300.sim import Simulator
+    case = synth.black_oil_case(nx=26, ny=22, nz=5, nsteps=2, dt=10.0, seed=62)
+    path = str(tmp_path / "tuning.json")
+    a = Simulator(case)
+    assert a.autotune_cached(10.0, path) is False
+    entry = json.load(open(path))["b3_fp64_26x22x5"]
+    st = a.stats()
+    assert (entry["spmv"], entry["amg"], entry["stage"]) == (st.spmv_block, st.amg_block, st.stage_block)
+    assert st.stage_block in (32, 64, 128, 256)
+    b = Simulator(case)
+    assert b.autotune_cached(10.0, path) is True
+    sb = b.stats()
+    assert (sb.spmv_block, sb.amg_block, sb.stage_block) == (st.spmv_block, st.amg_block, st.stage_block)
+    c = Simulator(case)
+    for dt in case["dt"]:
+        b.step(dt); c.step(dt)
+    for u, v in zip(b.get_state(), c.get_state()):
+        assert np.array_equal(u, v)
