@@ -1079,7 +1079,25 @@ void ora_precond_setup(ora_sim *s) {
         int ix, iy, iz; cell_ijk(s, i, &ix, &iy, &iz);
         double *Di = &s->dinv[(size_t)i * b * b];
         if (in->stage2 == 1 && ((ix + iy + iz) & 1)) continue;   /* black cells after all red ones */
+        if (in->stage2 == 2) continue;                              /* natural order: below */
         inv_block(b, AH(s, i, 0), Di);
+    }
+    if (in->stage2 == 2) {
+        /* natural (lexicographic) order: on the 7-point pattern ILU(0) only
+           modifies the diagonal blocks, D_i = Ahat_ii - sum over the lower
+           neighbours j (-x, -y, -z) of Ahat_ij D_j^-1 Ahat_ji */
+        for (int i = 0; i < N; i++) {
+            double D[9], T1[9], T2[9];
+            memcpy(D, AH(s, i, 0), sizeof(double) * b * b);
+            for (int d = 1; d < 7; d += 2) {
+                int k = nbr(s, i, d);
+                if (k < 0) continue;
+                matmul_block(b, &s->dinv[(size_t)k * b * b], AH(s, k, opp(d)), T1);
+                matmul_block(b, AH(s, i, d), T1, T2);
+                for (int t = 0; t < b * b; t++) D[t] -= T2[t];
+            }
+            inv_block(b, D, &s->dinv[(size_t)i * b * b]);
+        }
     }
     if (in->stage2 == 1) {
         for (int i = 0; i < N; i++) {
@@ -1105,6 +1123,32 @@ void ora_precond_setup(ora_sim *s) {
 static void stage_f(ora_sim *s, const double *rhs, double *out) {
     int N = s->N, b = s->b;
     double t[3], u[3];
+    if (s->in.stage2 == 2) {
+        /* natural order: (D + L) D^-1 (D + U) x = rhs with L, U the lower (-x, -y,
+           -z) and upper (+x, +y, +z) neighbour blocks of Ahat */
+        for (int i = 0; i < N; i++) {          /* forward: y = (D + L)^-1 rhs, D y_i = rhs_i - L y */
+            for (int c = 0; c < b; c++) t[c] = rhs[i * b + c];
+            for (int d = 1; d < 7; d += 2) {
+                int k = nbr(s, i, d);
+                if (k < 0) continue;
+                matvec_block(b, AH(s, i, d), &out[k * b], u);
+                for (int c = 0; c < b; c++) t[c] -= u[c];
+            }
+            matvec_block(b, &s->dinv[(size_t)i * b * b], t, &out[i * b]);
+        }
+        for (int i = N - 1; i >= 0; i--) {     /* backward: x_i = y_i - D_i^-1 U x */
+            for (int c = 0; c < b; c++) t[c] = 0.0;
+            for (int d = 2; d < 7; d += 2) {
+                int k = nbr(s, i, d);
+                if (k < 0) continue;
+                matvec_block(b, AH(s, i, d), &out[k * b], u);
+                for (int c = 0; c < b; c++) t[c] += u[c];
+            }
+            matvec_block(b, &s->dinv[(size_t)i * b * b], t, u);
+            for (int c = 0; c < b; c++) out[i * b + c] -= u[c];
+        }
+        return;
+    }
     if (s->in.stage2 != 1) {
         for (int i = 0; i < N; i++) matvec_block(b, &s->dinv[(size_t)i * b * b], &rhs[i * b], &out[i * b]);
         return;

@@ -52,7 +52,9 @@ typedef struct {
     double newton_tol; int32_t newton_max;
     double lin_tol; int32_t gmres_m, gmres_max_restarts;
     int32_t precond;               /* 0 none, 1 block-Jacobi, 2 CPR */
-    int32_t stage2;                /* CPR second stage: 0 block-Jacobi, 1 red-black block ILU(0) */
+    int32_t stage2;                /* CPR second stage: 0 block-Jacobi, 1 red-black block ILU(0),
+                                      2 natural-order block ILU(0) (a study of the ordering; the CUDA
+                                      path has 0 and 1) */
     double amg_theta; int32_t amg_rounds, amg_coarse_max, amg_max_levels;
     double chop_ds, chop_dp; int32_t max_cuts;
     int32_t amg_cycles;            /* V-cycles per stage-P application (>= 1) */

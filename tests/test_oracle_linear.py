@@ -60,7 +60,7 @@ def test_fgmres_cpr_matches_dense_solve(oracle_lib, name, case, dt, orth):
 def test_preconditioners_give_same_solution(oracle_lib, name, case, dt):
     sols, its = [], []
     for pc, st, dec, stg in [(0, 0, 0, 2), (1, 0, 0, 2), (2, 0, 0, 2), (2, 1, 0, 2), (2, 1, 1, 2), (2, 1, 0, 3),
-                             (2, 0, 1, 3)]:
+                             (2, 0, 1, 3), (2, 2, 0, 2), (2, 2, 1, 3)]:
         # m >= n: unrestarted, so even the unpreconditioned solve terminates
         o = assembled(case, dt, lin_tol=1e-11, precond=pc, stage2=st, decouple=dec, cpr_stages=stg, gmres_m=60,
                       gmres_max_restarts=3)
@@ -257,3 +257,40 @@ def test_fpf_is_the_composition_of_its_stages(oracle_lib, name, case, dt, decoup
     assert np.abs(z3 - zc).max() <= 1e-10 * np.abs(zc).max()
     # and it differs from the two-stage operator (the first stage does something)
     assert np.abs(z3 - o2.precond_apply(r)).max() > 1e-6 * np.abs(zc).max()
+
+
+@pytest.mark.parametrize("name,case,dt", tiny_cases())
+def test_natural_ilu0_reproduces_pattern(oracle_lib, name, case, dt):
+    """Natural-order block ILU(0) (the ordering study of the second stage):
+    (D + L) D^-1 (D + U) equals the decoupled matrix on the 7-point pattern,
+    with L / U the blocks of the lower (-x, -y, -z) / upper neighbours, and
+    its application solves with that product."""
+    o = assembled(case, dt, stage2=2)
+    o.precond_setup()
+    nx, ny, nz = case["nx"], case["ny"], case["nz"]
+    N, b = o.N, o.b
+    J = o.jacobian()
+    w, _ = o.qi(); w = w.reshape(N, b)
+    Ah = J.copy()
+    Ah[:, :, 0, :] = np.einsum("ir,idrc->idc", w, J)
+    dinv = o.ilu_dinv()
+    D = np.zeros((N * b, N * b)); Lm = np.zeros_like(D); Um = np.zeros_like(D); Di = np.zeros_like(D)
+    pattern = np.zeros((N, N), bool)
+    for i in range(N):
+        sl = slice(i * b, (i + 1) * b)
+        D[sl, sl] = np.linalg.inv(dinv[i]); Di[sl, sl] = dinv[i]
+        for d in range(7):
+            j = neighbour(nx, ny, nz, i, d)
+            if j < 0:
+                continue
+            pattern[i, j] = True
+            if d in (1, 3, 5):
+                Lm[sl, j * b:(j + 1) * b] = Ah[i, d]
+            elif d in (2, 4, 6):
+                Um[sl, j * b:(j + 1) * b] = Ah[i, d]
+    M = (D + Lm) @ Di @ (D + Um)
+    Ad = dense_from_blocks(Ah, nx, ny, nz)
+    mask = np.kron(pattern, np.ones((b, b), bool))
+    assert np.abs((M - Ad)[mask]).max() <= 1e-10 * np.abs(Ad).max()
+    # the factors are lower / upper in the natural order
+    assert not np.tril(Um).any() and not np.triu(Lm).any()
