@@ -148,8 +148,13 @@ def test_learned_stage_inside_fgmres(torch_cuda):
 
 
 def test_learned_stage_gain_is_measured(torch_cuda, capsys):
-    """Train on one grid, evaluate on a larger, rougher one: all three forms
-    reach the FP64 tolerance; the iterations and times are reported."""
+    """Train on one grid, evaluate on a larger, rougher one: all forms reach
+    the FP64 tolerance.  The comparison with and without the learned stage is
+    reported and bounded: the stage (minimal-residual scaled, so it never
+    increases the pressure residual it corrects) may not cost iterations
+    against the same FP32 preconditioner without it, and whether its fallback
+    to plain CPR engaged is stated.  A gain is not asserted: on these systems
+    the stage saves no iteration."""
     from paper_1606_00548_gb300 import learned
     tc = synth.black_oil_case(nx=32, ny=32, nz=8, sigma=1.0, seed=51)
     ec = synth.black_oil_case(nx=48, ny=40, nz=12, sigma=2.0, corr_len=8.0, seed=52)
@@ -158,5 +163,9 @@ def test_learned_stage_gain_is_measured(torch_cuda, capsys):
     for k in ("fp64_cpr", "fp64_cpr_fpf", "mixed_cpr", "mixed_cpr_fpf", "mixed_cpr_learned"):
         assert r[k]["converged"] and r[k]["rel_residual"] <= 1e-8, (k, r[k])
     assert ev["train_loss"][-1][1] < ev["train_loss"][0][1]
+    with_stage, without = r["mixed_cpr_learned"], r["mixed_cpr"]
     with capsys.disabled():
         print("\nlearned-stage gain (small grid):", {k: (v["iterations"], round(v["seconds"] * 1e3, 2)) for k, v in r.items()})
+        print(f"learned stage: {with_stage['iterations']} iterations against {without['iterations']} without it "
+              f"(FP32 CPR); fallback to plain CPR engaged: {with_stage['fallbacks'] > 0}")
+    assert with_stage["fallbacks"] > 0 or with_stage["iterations"] <= without["iterations"] + 1
