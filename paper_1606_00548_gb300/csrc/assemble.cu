@@ -903,7 +903,7 @@ extern "C" sim_status sim_cnv_noalloc(int32_t nx, int32_t ny, int32_t nz, double
     e = cudaMemsetAsync(scratch + SIM_RED_BLOCKS, 0, sizeof(double), st);
     if (e != cudaSuccess) return sim_fail(nullptr, SIM_ECUDA, std::string("sim_cnv_noalloc: ") + cudaGetErrorString(e));
     GridDesc g;
-    g.nx = nx; g.ny = ny; g.nz = nz; g.N = (int)N; g.dx = dx; g.dy = dy; g.dz = dz; g.top = 0.0;
+    g.nx = nx; g.ny = ny; g.nz = nz; g.N = (int)N; g.dx = dx; g.dy = dy; g.dz = dz; g.top = 0.0; g.H = 0;
     const double r2 = b == 3 ? cnv_rho[2] : 1.0;
     if (b == 2)
         cnv_noalloc_kernel<2><<<SIM_RED_BLOCKS, SIM_THREADS, 0, st>>>(g, R_dev, poro_dev, dt, cnv_rho[0], cnv_rho[1], r2,

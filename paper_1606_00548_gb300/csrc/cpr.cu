@@ -78,6 +78,19 @@ __device__ __forceinline__ int colour_cell(const GridDesc &g, long t, int colour
     return (int)(ix + (long)g.nx * r);
 }
 
+// Colour-split storage of the blocks the red-black sweeps read (Ahat and the
+// inverted diagonal blocks): colour (ix + iy + iz) & 1 first, then the cell's
+// slot in colour_cell's order, so the threads of a one-colour sweep read
+// consecutive positions (component-major storage by cell would hand each warp
+// sectors half filled with the other colour's blocks).  2 H positions.
+__device__ __forceinline__ long cslot(const GridDesc &g, int ix, int iy, int iz) {
+    return (long)((ix + iy + iz) & 1) * g.H + (long)(iy + g.ny * iz) * ((g.nx + 1) >> 1) + (ix >> 1);
+}
+__device__ __forceinline__ long cslot_of(const GridDesc &g, int i) {
+    const int ix = i % g.nx, t = i / g.nx, iy = t % g.ny, iz = t / g.ny;
+    return cslot(g, ix, iy, iz);
+}
+
 __device__ __forceinline__ int opp(int d) { return d == 0 ? 0 : ((d & 1) ? d + 1 : d - 1); }
 __device__ __forceinline__ bool is_black(const GridDesc &g, int i) {
     const int ix = i % g.nx, t = i / g.nx, iy = t % g.ny, iz = t / g.ny;
@@ -292,6 +305,7 @@ __global__ void qi_kernel(GridDesc g, const double *__restrict__ J, WellCorr wc,
 #pragma unroll
     for (int c = 0; c < B; c++) { qiw[(long)c * N + i] = L[c]; qiwT[(long)c * N + i] = (T)L[c]; }
     const Cell cc = cell_of(g, i);
+    const long NS = 2L * g.H, si = cslot(g, cc.ix, cc.iy, cc.iz);
     double rsum = 0.0;                   // FP32 copy: row sum of A_p on the diagonal slot (difference form)
     for (int d = 0; d < 7; d++) {
         double A[B * B];
@@ -302,7 +316,7 @@ __global__ void qi_kernel(GridDesc g, const double *__restrict__ J, WellCorr wc,
         apT[(long)d * N + i] = has ? (T)A[0] : (T)0;
         if (sizeof(T) == sizeof(float) && has) rsum += A[0];
 #pragma unroll
-        for (int t = 0; t < B * B; t++) ahat[(long)(d * B * B + t) * N + i] = (T)A[t];
+        for (int t = 0; t < B * B; t++) ahat[(long)(d * B * B + t) * NS + si] = (T)A[t];
     }
     if (sizeof(T) == sizeof(float)) apT[i] = (T)rsum;
 }
@@ -344,8 +358,9 @@ __global__ void diag_inv_kernel(GridDesc g, const double *__restrict__ J, WellCo
         ahat_block<B>(J, N, i, 0, i, wc, L, A);
     }
     inv_block<B>(A, Ai);
+    const long NS = 2L * g.H, si = cslot_of(g, i);
 #pragma unroll
-    for (int t = 0; t < B * B; t++) dinv[(long)t * N + i] = Ai[t];
+    for (int t = 0; t < B * B; t++) dinv[(long)t * NS + si] = Ai[t];
 }
 
 // black cells: D = Ahat_ii - sum_d Ahat_{i,d} Dinv_k Ahat_{k,opp(d)}
@@ -367,8 +382,9 @@ __global__ void __launch_bounds__(SIM_THREADS, 2) ilu_black_kernel(GridDesc g, c
         load_lsc<B>(lsc, N, k, Lk);
         ahat_block<B>(J, N, i, d, k, wc, Li, Aik);
         ahat_block<B>(J, N, k, opp(d), i, wc, Lk, Aki);
+        const long sk = cslot_of(g, k);
 #pragma unroll
-        for (int t = 0; t < B * B; t++) Dk[t] = dinv[(long)t * N + k];
+        for (int t = 0; t < B * B; t++) Dk[t] = dinv[(long)t * 2L * g.H + sk];
 #pragma unroll
         for (int r = 0; r < B; r++)
 #pragma unroll
@@ -390,8 +406,9 @@ __global__ void __launch_bounds__(SIM_THREADS, 2) ilu_black_kernel(GridDesc g, c
     }
     double Di[B * B];
     inv_block<B>(D, Di);
+    const long NS = 2L * g.H, si = cslot_of(g, i);
 #pragma unroll
-    for (int t = 0; t < B * B; t++) dinv[(long)t * N + i] = Di[t];
+    for (int t = 0; t < B * B; t++) dinv[(long)t * NS + si] = Di[t];
 }
 
 // FP32 copy of an ELL level in the difference form: the diagonal entry is
@@ -1262,6 +1279,7 @@ __device__ __forceinline__ void stage2_a_row(const GridDesc &g, const double *__
         v[0] = rp;
     }
     const Cell cc = cell_of(g, i);
+    const long NS = 2L * g.H, si = cslot(g, cc.ix, cc.iy, cc.iz);
     if (ep) {
 #pragma unroll
         for (int d = 0; d < 7; d++) {
@@ -1269,7 +1287,7 @@ __device__ __forceinline__ void stage2_a_row(const GridDesc &g, const double *__
             if (j < 0) continue;
             const T e = ep[j];
 #pragma unroll
-            for (int c = 0; c < B; c++) v[c] -= ahat[(long)(d * B * B + c * B) * N + i] * e;
+            for (int c = 0; c < B; c++) v[c] -= ahat[(long)(d * B * B + c * B) * NS + si] * e;
         }
     }
     if (rb && is_black(g, i)) {
@@ -1281,7 +1299,7 @@ __device__ __forceinline__ void stage2_a_row(const GridDesc &g, const double *__
     for (int c = 0; c < B; c++) {
         T s = (T)0;
 #pragma unroll
-        for (int q = 0; q < B; q++) s += dinv[(long)(c * B + q) * N + i] * v[q];
+        for (int q = 0; q < B; q++) s += dinv[(long)(c * B + q) * NS + si] * v[q];
         z[(long)c * N + i] = s;
     }
 }
@@ -1327,6 +1345,7 @@ __global__ void fpf_resid_kernel(GridDesc g, const double *__restrict__ r, const
         v[0] = rp;
     }
     const Cell cc = cell_of(g, i);
+    const long NS = 2L * g.H, si = cslot(g, cc.ix, cc.iy, cc.iz);
 #pragma unroll
     for (int d = 0; d < 7; d++) {
         const int j = nbrc(g, cc, d);
@@ -1337,7 +1356,7 @@ __global__ void fpf_resid_kernel(GridDesc g, const double *__restrict__ r, const
 #pragma unroll
         for (int rr = 0; rr < B; rr++)
 #pragma unroll
-            for (int c = 0; c < B; c++) v[rr] -= ahat[(long)(d * B * B + rr * B + c) * N + i] * xj[c];
+            for (int c = 0; c < B; c++) v[rr] -= ahat[(long)(d * B * B + rr * B + c) * NS + si] * xj[c];
     }
 #pragma unroll
     for (int c = 0; c < B; c++) rh[(long)c * N + i] = v[c];
@@ -1361,6 +1380,7 @@ __device__ __forceinline__ void stage2_b_row(const GridDesc &g, const T *__restr
                                              const T *__restrict__ addv, TZ *__restrict__ out, int i) {
     const long N = g.N;
     const Cell cc = cell_of(g, i);
+    const long NS = 2L * g.H, si = cslot(g, cc.ix, cc.iy, cc.iz);
     T t[B];
 #pragma unroll
     for (int c = 0; c < B; c++) t[c] = r2[(long)c * N + i];
@@ -1374,13 +1394,13 @@ __device__ __forceinline__ void stage2_b_row(const GridDesc &g, const T *__restr
 #pragma unroll
         for (int r = 0; r < B; r++)
 #pragma unroll
-            for (int c = 0; c < B; c++) t[r] -= ahat[(long)(d * B * B + r * B + c) * N + i] * zk[c];
+            for (int c = 0; c < B; c++) t[r] -= ahat[(long)(d * B * B + r * B + c) * NS + si] * zk[c];
     }
 #pragma unroll
     for (int r = 0; r < B; r++) {
         T s = (T)0;
 #pragma unroll
-        for (int q = 0; q < B; q++) s += dinv[(long)(r * B + q) * N + i] * t[q];
+        for (int q = 0; q < B; q++) s += dinv[(long)(r * B + q) * NS + si] * t[q];
         z[(long)r * N + i] = s;
         out[(long)r * N + i] = (TZ)fin<T>(s, r, i, N, ep, addv);
     }
@@ -1411,6 +1431,7 @@ __device__ __forceinline__ void stage2_c_row(const GridDesc &g, const T *__restr
         return;
     }
     const Cell cc = cell_of(g, i);
+    const long NS = 2L * g.H, si = cslot(g, cc.ix, cc.iy, cc.iz);
     T t[B];
 #pragma unroll
     for (int c = 0; c < B; c++) t[c] = (T)0;
@@ -1424,13 +1445,13 @@ __device__ __forceinline__ void stage2_c_row(const GridDesc &g, const T *__restr
 #pragma unroll
         for (int r = 0; r < B; r++)
 #pragma unroll
-            for (int c = 0; c < B; c++) t[r] += ahat[(long)(d * B * B + r * B + c) * N + i] * zk[c];
+            for (int c = 0; c < B; c++) t[r] += ahat[(long)(d * B * B + r * B + c) * NS + si] * zk[c];
     }
 #pragma unroll
     for (int r = 0; r < B; r++) {
         T s = (T)0;
 #pragma unroll
-        for (int q = 0; q < B; q++) s += dinv[(long)(r * B + q) * N + i] * t[q];
+        for (int q = 0; q < B; q++) s += dinv[(long)(r * B + q) * NS + si] * t[q];
         out[(long)r * N + i] = (TZ)fin<T>(z[(long)r * N + i] - s, r, i, N, ep, addv);
     }
 }
@@ -1448,11 +1469,13 @@ __global__ void stage2_c_kernel(GridDesc g, const T *__restrict__ ahat, const T 
 
 // no preconditioner / plain block-Jacobi on J (no decoupling)
 template <int B, typename TZ>
-__global__ void simple_prec_kernel(int N, const double *__restrict__ r, const double *__restrict__ dinv, TZ *__restrict__ z,
+__global__ void simple_prec_kernel(GridDesc g, const double *__restrict__ r, const double *__restrict__ dinv, TZ *__restrict__ z,
                                    int use_dinv, const int *done) {
     if (skip(done)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const long N = g.N;
     if (i >= N) return;
+    const long NS = 2L * g.H, si = cslot_of(g, i);
     double v[B];
 #pragma unroll
     for (int c = 0; c < B; c++) v[c] = r[(long)c * N + i];
@@ -1462,7 +1485,7 @@ __global__ void simple_prec_kernel(int N, const double *__restrict__ r, const do
         if (use_dinv) {
             s = 0.0;
 #pragma unroll
-            for (int q = 0; q < B; q++) s += dinv[(long)(rr * B + q) * N + i] * v[q];
+            for (int q = 0; q < B; q++) s += dinv[(long)(rr * B + q) * NS + si] * v[q];
         }
         z[(long)rr * N + i] = (TZ)s;
     }
@@ -1909,7 +1932,7 @@ static sim_status setup_bt(sim_t *s) {
         SIM_LAUNCHED(s);
     }
     if (sizeof(T) != sizeof(double)) {
-        cast_kernel<T><<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(s->dinv_d, (T *)s->dinv, (long)B * B * N);
+        cast_kernel<T><<<SIM_RED_BLOCKS, SIM_THREADS, 0, s->stream>>>(s->dinv_d, (T *)s->dinv, (long)B * B * 2 * s->gd.H);
         SIM_LAUNCHED(s);
     }
     return SIM_OK;
@@ -2017,7 +2040,7 @@ static sim_status apply_btz(sim_t *s, const double *r, TZ *z, const int *done) {
     const int N = s->N;
     const int nb = sim_blocks(N);
     if (s->opt.precond != SIM_PRECOND_CPR) {
-        simple_prec_kernel<B, TZ><<<nb, SIM_THREADS, 0, s->stream>>>(N, r, s->dinv_d, z,
+        simple_prec_kernel<B, TZ><<<nb, SIM_THREADS, 0, s->stream>>>(s->gd, r, s->dinv_d, z,
                                                                    s->opt.precond == SIM_PRECOND_BJACOBI, done);
         SIM_LAUNCHED(s);
         return SIM_OK;

@@ -198,6 +198,7 @@ sim_status sim_create(const sim_grid *g, const sim_rock *r, const sim_fluid *f, 
     s->m = o->gmres_m;
     s->gd.nx = g->nx; s->gd.ny = g->ny; s->gd.nz = g->nz; s->gd.N = (int)N;
     s->gd.dx = g->dx; s->gd.dy = g->dy; s->gd.dz = g->dz; s->gd.top = g->top_depth;
+    s->gd.H = ((g->nx + 1) / 2) * g->ny * g->nz;
     FluidConst &c = s->fc;
     memset(&c, 0, sizeof(c));
     c.model = f->model; c.b = s->b; c.npvt = f->model == 3 ? f->npvt : 0;
@@ -279,9 +280,10 @@ sim_status sim_create(const sim_grid *g, const sim_rock *r, const sim_fluid *f, 
     s->ap = (double *)A(sizeof(double) * 7 * N);
     s->qiwT = mixed ? A(sizeof(float) * n) : (void *)s->qiw;
     s->apT = mixed ? A(sizeof(float) * 7 * N) : (void *)s->ap;
-    s->ahat = A(tsz * 7 * b * b * N);
-    s->dinv_d = (double *)A(sizeof(double) * b * b * N);
-    s->dinv = mixed ? A(sizeof(float) * b * b * N) : (void *)s->dinv_d;
+    const size_t NS = 2 * (size_t)s->gd.H;     // colour-split positions (>= N)
+    s->ahat = A(tsz * 7 * b * b * NS);
+    s->dinv_d = (double *)A(sizeof(double) * b * b * NS);
+    s->dinv = mixed ? A(sizeof(float) * b * b * NS) : (void *)s->dinv_d;
     s->r2 = A(tsz * n);
     s->rpT = A(tsz * N);
     s->epacc = A(tsz * N);

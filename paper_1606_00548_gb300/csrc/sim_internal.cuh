@@ -31,6 +31,7 @@ struct FluidConst {
 struct GridDesc {
     int nx, ny, nz, N;
     double dx, dy, dz, top;
+    int H;              // cells of one colour in the colour-split arrays: ceil(nx / 2) ny nz
 };
 
 // device control block of one FGMRES solve (Givens, Hessenberg, flags)

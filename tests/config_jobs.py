@@ -77,6 +77,6 @@ def run_members(scale, nsteps, first, count):
             rc, info = o.step(case["dt"][k])
             p, sw, _, _ = o.get_state()
             rows.append(dict(rc=rc, p=p, sw=sw, newton=info.newton_iterations, linear=info.linear_iterations,
-                             cuts=info.cuts))
+                             cuts=info.cuts, substeps=info.substeps))
         out.append(rows)
     return out
