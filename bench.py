@@ -625,9 +625,11 @@ def run_ensemble(args):
     for _ in range(args.warmup):
         batch.step(1.0)
     s0 = batch.stats()
+    ph0 = batch.phase_seconds()
     launches0 = sum(sm.stats().kernel_launches for sm in sims)
     value, t_lock, _ = timed(SIM_BATCH_LOCKSTEP)
     s1 = batch.stats()
+    ph1 = batch.phase_seconds()
     launches_lock = sum(sm.stats().kernel_launches for sm in sims) - launches0 + (s1["launches"] - s0["launches"])
     batch.L.sim_batch_set_mode(batch.h, SIM_BATCH_CONCURRENT)
     l1 = sum(sm.stats().kernel_launches for sm in sims)
@@ -654,7 +656,8 @@ def run_ensemble(args):
                        "runtime": "lockstep: one batched FGMRES per Newton round (one launch per Krylov "
                                   "operation over all members, restart cycle as one CUDA graph)",
                        "timing": "host wall clock around fully synchronised batch steps",
-                       "lockstep_rounds": s1["rounds"] - s0["rounds"], "member_solves": s1["solves"] - s0["solves"]},
+                       "lockstep_rounds": s1["rounds"] - s0["rounds"], "member_solves": s1["solves"] - s0["solves"],
+                       "lockstep_host_seconds": {k: ph1[k] - ph0[k] for k in ph1}},
             "gpu_launches": int(launches_lock),
             "concurrent": {"value": v_conc, "ms_per_step": 1e3 * t_conc / args.steps, "gpu_launches": int(launches_conc)},
             "one_at_a_time": {"value": value_seq, "ms_per_step": 1e3 * t_seq / args.steps},

@@ -384,6 +384,10 @@ sim_status sim_batch_step(sim_batch_t *b, const double *dt, sim_step_info *infos
    batched solves (graph nodes included) */
 sim_status sim_batch_stats(sim_batch_t *b, int64_t *rounds, int64_t *solves, int64_t *launches);
 const char *sim_batch_last_error(sim_batch_t *b);
+/* host seconds spent so far in the lockstep phases: the members' Newton phases
+   (assembly, CNV test, accepting or cutting, CPR set-up), the batched solves,
+   and the updates */
+sim_status sim_batch_phase_seconds(sim_batch_t *b, double *newton, double *solve, double *update);
 
 /* ---- learned pressure stage (no paper counterpart) ----
    A 3-D convolutional network: 4 layers of 3x3x3 kernels (zero padding),

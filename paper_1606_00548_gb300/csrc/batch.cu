@@ -17,6 +17,7 @@
 // worker (kernels of different members overlap; launches scale with members).
 // Members never exchange data.
 #include <atomic>
+#include <chrono>
 #include <condition_variable>
 #include <functional>
 #include <mutex>
@@ -44,6 +45,7 @@ struct sim_batch {
     KrylovBatch *kb = nullptr;
     bool batchable = false;
     int64_t rounds = 0, batched_solves = 0;
+    double t_newton = 0.0, t_solve = 0.0, t_update = 0.0;   // host seconds of the lockstep phases
     std::string msg;
 };
 
@@ -152,7 +154,10 @@ static sim_status step_lockstep(sim_batch *b, const double *dt, sim_step_info *i
         std::vector<int> live;
         for (int k : all) if (!ms[k].finished) live.push_back(k);
         if (live.empty()) break;
+        auto t0 = std::chrono::steady_clock::now();
         run_parallel(b, live, [&](int k) { phase_newton(b->members[k], ms[k]); });
+        auto t1 = std::chrono::steady_clock::now();
+        b->t_newton += std::chrono::duration<double>(t1 - t0).count();
         std::vector<int> solve;
         for (int k : live) if (ms[k].solving && !ms[k].finished) solve.push_back(k);
         if (solve.empty()) continue;
@@ -169,10 +174,13 @@ static sim_status step_lockstep(sim_batch *b, const double *dt, sim_step_info *i
             break;
         }
         cudaEventElapsedTime(&ms_solve, b->e0, b->e1);
+        auto t2 = std::chrono::steady_clock::now();
+        b->t_solve += std::chrono::duration<double>(t2 - t1).count();
         b->rounds++;
         b->batched_solves += (int64_t)solve.size();
         for (size_t q = 0; q < solve.size(); q++) ms[solve[q]].li = li[q];
         run_parallel(b, solve, [&](int k) { phase_update(b->members[k], ms[k], 1e3 * ms_solve); });
+        b->t_update += std::chrono::duration<double>(std::chrono::steady_clock::now() - t2).count();
     }
     sim_status first = SIM_OK;
     for (int k = 0; k < n; k++) {
@@ -274,6 +282,14 @@ sim_status sim_batch_stats(sim_batch_t *b, int64_t *rounds, int64_t *solves, int
 }
 
 const char *sim_batch_last_error(sim_batch_t *b) { return b ? b->msg.c_str() : ""; }
+
+sim_status sim_batch_phase_seconds(sim_batch_t *b, double *newton, double *solve, double *update) {
+    if (!b) return SIM_EINVAL;
+    if (newton) *newton = b->t_newton;
+    if (solve) *solve = b->t_solve;
+    if (update) *update = b->t_update;
+    return SIM_OK;
+}
 
 sim_status sim_batch_step(sim_batch_t *b, const double *dt, sim_step_info *infos, sim_status *member_status) {
     if (!b || !dt) return SIM_EINVAL;

@@ -156,6 +156,7 @@ _SIGS = {
     "sim_batch_mode": ([_vp], C.c_int32),
     "sim_batch_stats": ([_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)], C.c_int),
     "sim_batch_last_error": ([_vp], C.c_char_p),
+    "sim_batch_phase_seconds": ([_vp, _dp, _dp, _dp], C.c_int),
     "sim_net_create": ([C.c_int32, C.c_int32, C.c_int32, C.c_uint64, _vp, C.POINTER(_vp)], C.c_int),
     "sim_net_destroy": ([_vp], None),
     "sim_net_param_count": ([_vp], C.c_int64),
@@ -571,6 +572,11 @@ class Batch:
 
     def last_error(self):
         return (self.L.sim_batch_last_error(self.h) or b"").decode()
+
+    def phase_seconds(self):
+        a, b, c = C.c_double(), C.c_double(), C.c_double()
+        self.L.sim_batch_phase_seconds(self.h, C.byref(a), C.byref(b), C.byref(c))
+        return dict(newton=a.value, solve=b.value, update=c.value)
 
     def step(self, dts):
         n = len(self.members)
