@@ -880,6 +880,7 @@ sim_status k_fgmres(sim_t *s, const double *b, double *x, sim_linear_info *info)
     SIM_CK(s, cudaMemcpyAsync(&ctl->beta, &bn, sizeof(double), cudaMemcpyHostToDevice, s->stream));
     SIM_CK(s, cudaMemcpyAsync(&ctl->tol, &tol, sizeof(double), cudaMemcpyHostToDevice, s->stream));
     s->learned_active = (s->learned_on && s->net && s->opt.precond == SIM_PRECOND_CPR) ? 1 : 0;
+    const int learned_used = s->learned_active;
     for (int cyc = 0; cyc <= s->opt.gmres_max_restarts; cyc++) {
         if (s->opt.graphs) {
             // the restart cycle as one CUDA graph, captured once per preconditioner setup
@@ -945,6 +946,10 @@ sim_status k_fgmres(sim_t *s, const double *b, double *x, sim_linear_info *info)
     }
     s->linear_total += li.iterations;
     if (info) *info = li;
+    if (learned_used) {
+        const int ns = net_status_word(s->net, s->stream);
+        if (ns != 0) return sim_fail(s, ns < 0 ? SIM_ECUDA : SIM_ETIMEOUT, "learned stage: a convolution's bounded wait gave up");
+    }
     if (!(li.r_norm == li.r_norm)) return sim_fail(s, SIM_ENAN, "non-finite linear residual");
     return SIM_OK;
 }

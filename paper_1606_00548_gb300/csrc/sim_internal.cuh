@@ -256,4 +256,7 @@ sim_status cpr_learned_features(sim_t *s);
 // ---- learned.cu -----------------------------------------------------------
 sim_status net_infer(sim_net_t *n, const float *x_dev, float *y_dev, cudaStream_t st, const int *done);
 int64_t net_launches(sim_net_t *n);
+// the convolutions' status word after the stream has drained: 0 fine, > 0 a
+// bounded wait gave up, < 0 the read itself failed
+int net_status_word(sim_net_t *n, cudaStream_t st);
 int net_cells(sim_net_t *n);

@@ -5,7 +5,7 @@ The reference applies the same roundings the device applies (weights,
 inputs, hidden activations and back-propagated gradients to BF16), so the
 remaining difference is FP32-versus-FP64 accumulation and the rare BF16
 rounding flip of an intermediate value.  The grid is ragged with respect to
-the 16-cell MMA tiles and 64-cell blocks.
+the convolution's 128 x 2 x 8 output bricks and the 64-cell blocks.
 """
 import numpy as np
 import pytest
@@ -66,10 +66,11 @@ def torch_cuda():
     return torch
 
 
-@pytest.mark.parametrize("nx,ny,nz", [(13, 11, 5), (37, 9, 10)])
+@pytest.mark.parametrize("nx,ny,nz", [(13, 11, 5), (37, 9, 10), (150, 7, 19), (1, 1, 1)])
 def test_forward_and_gradients_match_reference(torch_cuda, nx, ny, nz):
-    """Sizes smaller than one brick of the tiled kernel and spanning several
-    bricks with ragged edges in every direction."""
+    """Sizes smaller than one 128 x 2 x 8 output brick of the tensor-core
+    convolution, one cell, and a grid spanning two bricks along x, four along y
+    and three along z with ragged edges in every direction."""
     torch = torch_cuda
     from paper_1606_00548_gb300.sim import Net
     net = Net(nx, ny, nz, seed=3)
