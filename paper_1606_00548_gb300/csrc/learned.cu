@@ -13,8 +13,8 @@
 //   weight gradient on mma.sync.m16n8k16: M = 16 input channels, N = output
 //   channels, K = cells (a training-only kernel; its (tap, channel) rows have
 //   no uniform shared-memory stride, which the tcgen05 operand layouts need).
-// Activations are stored channels-innermost as BF16 [N][16] (pairs of channels
-// per 32-bit word).
+// Activations are BF16, 16 channels per cell, stored as two planes of 8
+// channels (16 bytes per cell; see Dims).
 // Reductions over cells (weight and bias gradients, loss) are written as
 // per-block partials and folded in block order: results do not depend on
 // scheduling.
@@ -29,7 +29,6 @@
 
 namespace {
 
-constexpr int CH = 16;          // padded channel count
 constexpr int NLAYER = 4;
 constexpr int CIN[NLAYER] = {4, 16, 16, 16};
 constexpr int COUT[NLAYER] = {16, 16, 16, 1};
@@ -51,16 +50,33 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
+// Grid and activation layout.  Activations (and their gradients) are BF16,
+// 16 channels per cell, stored as two planes -- channels 0-7, then 8-15 --
+// of nxp x ny x nz cells, 16 bytes per cell, x padded to nxp (a multiple of 8)
+// with cells that stay zero: a TMA box row is then 8 cells (128 bytes), and a
+// plane is the shared-memory operand layout of the convolution as it stands.
 struct Dims {
     int nx, ny, nz, N;
+    int nxp;    // nx rounded up to a multiple of 8
+    long P;     // cells of one plane: nxp * ny * nz
 };
+// BF16 element offset of channel ch of cell (x, y, z)
+__device__ __forceinline__ long act_elem(const Dims &d, int x, int y, int z, int ch) {
+    return ((long)(ch >> 3) * d.P + (long)x + (long)d.nxp * (y + (long)d.ny * z)) * 8 + (ch & 7);
+}
+// the same for the cell of compact index c = x + nx (y + ny z)
+__device__ __forceinline__ long act_elem_c(const Dims &d, int c, int ch) {
+    const int x = c % d.nx, q = c / d.nx;
+    return act_elem(d, x, q % d.ny, q / d.ny, ch);
+}
 
-// neighbour of cell c through tap t (offset (t/9-1, (t/3)%3-1, t%3-1) in (z, y, x)), or -1
-__device__ __forceinline__ int tap_nbr(const Dims &d, int x, int y, int z, int c, int t) {
+// plane cell index (x + nxp (y + ny z)) of the neighbour of cell (x, y, z) through
+// tap t (offset (t/9-1, (t/3)%3-1, t%3-1) in (z, y, x)), or -1 outside the grid
+__device__ __forceinline__ long tap_nbr(const Dims &d, int x, int y, int z, int t) {
     const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
     const int X = x + dx, Y = y + dy, Z = z + dz;
     if (X < 0 || X >= d.nx || Y < 0 || Y >= d.ny || Z < 0 || Z >= d.nz) return -1;
-    return c + dx + d.nx * (dy + d.ny * dz);
+    return (long)X + (long)d.nxp * (Y + (long)d.ny * Z);
 }
 
 // ---------------------------------------------------------------------------
@@ -72,39 +88,54 @@ __device__ __forceinline__ int tap_nbr(const Dims &d, int x, int y, int z, int c
 //
 // Implicit GEMM per output line (an x-row of 128 cells at fixed y, z):
 //   D[x][o] += sum_k In[x + dx, y + dy, z + dz][k] * B_t[k][o]   over 27 taps t.
-// One CTA owns 128 x TC_TY x TC_TZ output cells.  TMA stages the input lines
-// (y0-1 .. y0+TC_TY, z0-1 .. z0+TC_TZ, x0-1 .. x0+128) into shared memory as two
-// planes, channels 0-7 and 8-15, 16 bytes per cell: that is the no-swizzle
-// K-major core-matrix layout (8 rows x 16 bytes per core matrix, the two
-// K halves one plane apart), so the A operand for any x-shift dx is the same
-// lines read from a start address 16 (dx + 1) bytes further on.  Out-of-grid
-// cells come in as zeros from the TMA bounds fill (the zero padding).
+// Work unit: a brick of 128 x TC_TY x TC_TZ output cells.  Its input is TC_SY
+// staged slabs (one y each: lines z0-1 .. z0+TC_TZ, cells x0-8 .. x0+135),
+// each loaded by TMA from the two activation planes (rows of 8 cells, 128
+// bytes): in shared memory a plane is the no-swizzle K-major core-matrix layout
+// (8 rows x 16 bytes per core matrix, the two K halves one plane apart), so the
+// A operand for any x-shift dx is the same lines read from a start address
+// 16 (dx + 8) bytes further on.  Out-of-grid cells are zeros: the TMA bounds
+// fill, and the zero cells that pad x to a multiple of 8.
 // One staged line (y_s, z_s) with fixed (dy, dx) feeds the three output lines
 // z' = z_s - dz, dz = +1, 0, -1, whose accumulators sit side by side in tensor
 // memory: a single MMA with N = 48 (fewer at the z edges) does all three taps,
 // its B operand the three tap matrices stacked along N.
-// One thread issues the TMA copies and the MMAs; all four warps initialise the
-// accumulators and run the epilogue (lane = cell).  Every wait is bounded: on a
-// timeout the kernel sets bit 0 (staging) or bit 1 (MMA) of *status, waits
-// once more, bounded, for its copies and MMAs, frees its tensor memory and
-// skips the epilogue; a staging buffer off the 128-byte alignment the TMA
-// needs sets bit 2, and nothing is copied or multiplied.
+//
+// Persistent and warp-specialised, one CTA per SM, bricks dealt round-robin:
+//   warp 0     TMA producer: slabs into a ring of TC_RING buffers
+//   warp 1     tensor-memory owner and MMA issuer: 180 MMAs per brick from
+//              precomputed descriptors; each slab's buffer is released by a
+//              tcgen05.commit once the MMAs reading it are done
+//   warps 2-5  epilogue (one lane = one cell of the 128): drains a brick's
+//              accumulators, writes the outputs, and re-seeds the columns with
+//              the bias for the brick after next
+// Two accumulator buffers of TC_ACC columns let the epilogue of one brick
+// overlap the MMAs of the next.  Every wait is bounded: on a timeout the CTA
+// sets bit 0 (producer), 1 (MMA) or 3 (epilogue) of *status, stops all its
+// roles, lets its copies and MMAs in flight land, frees its tensor memory and
+// exits; a staging ring off the 128-byte alignment the TMA needs sets bit 2,
+// and nothing is copied or multiplied.
 // ---------------------------------------------------------------------------
 constexpr int TC_M = 128;                                  // cells along x per output line
-constexpr int TC_TY = 2, TC_TZ = 8;                        // output lines per CTA (y, z)
-constexpr int TC_SY = TC_TY + 2, TC_SZ = TC_TZ + 2;        // staged lines (y, z)
-constexpr int TC_LINE = (TC_M + 2) * 16;                   // bytes of one staged line, one channel half
-constexpr int TC_BOX = TC_SZ * TC_LINE;                    // bytes of one TMA box: one staged y, TC_SZ lines
-constexpr int TC_SLAB = (TC_BOX + 127) / 128 * 128;        // its stride: TMA destinations are 128-byte aligned
-constexpr int TC_PLANE = TC_SY * TC_SLAB;                  // one channel half of the staged brick
+constexpr int TC_TY = 2, TC_TZ = 8;                        // output lines per brick (y, z)
+constexpr int TC_SY = TC_TY + 2, TC_SZ = TC_TZ + 2;        // staged slabs per brick, lines per slab
+constexpr int TC_XS = TC_M + 16;                           // staged cells per line: x0-8 .. x0+135 (8-cell units)
+constexpr int TC_LINE = TC_XS * 16;                        // bytes of one staged line, one channel half
+constexpr int TC_BOX = TC_SZ * TC_LINE;                    // bytes of one TMA box: one slab, one half
+constexpr int TC_HALF = (TC_BOX + 127) / 128 * 128;        // its stride: TMA destinations are 128-byte aligned
+constexpr int TC_SLOT = 2 * TC_HALF;                       // one ring buffer: a slab, both halves
+constexpr int TC_RING = 4;                                 // ring buffers
 constexpr int TC_WROWS = 48;                               // B rows per (dy, dx): 3 taps x 16 outputs
 constexpr int TC_WELEMS = 9 * 2 * TC_WROWS * 8;            // BF16 elements of the packed weights
 constexpr int TC_WBYTES = TC_WELEMS * 2;
-constexpr int TC_COLS = TC_TY * TC_TZ * 16;                // FP32 accumulator columns in tensor memory
-constexpr int TC_SMEM = 2 * TC_PLANE + TC_WBYTES + 128;    // + alignment slack
-static_assert(TC_COLS == 256, "tensor-memory allocation must be a power of two >= 32");
+constexpr int TC_ACC = TC_TY * TC_TZ * 16;                 // FP32 accumulator columns of one brick
+constexpr int TC_COLS = 2 * TC_ACC;                        // two bricks in flight
+constexpr int TC_THREADS = 192;
+constexpr int TC_SMEM = TC_RING * TC_SLOT + TC_WBYTES + 128;   // + alignment slack
+static_assert(TC_COLS == 512, "tensor-memory allocation: a power of two >= 32, at most 512");
+static_assert((TC_TY * TC_TZ) % 4 == 0, "the epilogue reads four output lines per tensor-memory load");
 static_assert(TC_SMEM <= 227 * 1024, "shared memory per CTA");
-static_assert((TC_LINE % 16) == 0 && (TC_SLAB % 128) == 0 && (TC_PLANE % 128) == 0 && (TC_PLANE >> 4) < (1 << 14),
+static_assert((TC_LINE % 128) == 0 && (TC_HALF % 128) == 0 && (TC_SLOT % 128) == 0 && (TC_HALF >> 4) < (1 << 14),
               "TMA destination alignment and descriptor fields");
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -132,35 +163,64 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
 }
-// bounded wait for phase `parity` of an mbarrier (about 2 s of SM clock)
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok)
+                 : "r"(smem_addr(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+// bounded wait for phase `parity` of an mbarrier (about 2 s of SM clock).  It
+// gives up early once *abort is set; on its own timeout it sets *abort and
+// the status bit, so that every role of the CTA stops.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort, int *status, int bit) {
     const long long t0 = clock64();
     for (;;) {
-        uint32_t ok;
-        asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(smem_addr(bar)), "r"(parity)
-            : "memory");
-        if (ok) return true;
-        if (clock64() - t0 > 4000000000LL) return false;
+        if (mbar_test(bar, parity)) return true;
+        if (*abort) return false;
+        if (clock64() - t0 > 4000000000LL) {
+            *abort = 1;
+            atomicOr(status, bit);
+            return false;
+        }
     }
 }
-__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+// the same without the early exit: used to let copies and MMAs in flight land
+// before the CTA frees its tensor memory and exits
+__device__ __forceinline__ bool mbar_drain(uint64_t *bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_test(bar, parity))
+        if (clock64() - t0 > 4000000000LL) return false;
+    return true;
+}
+__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3, int c4,
                                             uint64_t *bar) {
     asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
-        "[%6];" ::"r"(smem_addr(dst)),
-        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+        "%6}], [%7];" ::"r"(smem_addr(dst)),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_addr(bar))
         : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+// 64 consecutive columns (four output lines) of this warp's 32 lanes in one load
+__device__ __forceinline__ void tc_ld64(uint32_t taddr, uint32_t (&r)[64]) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,"
+        "%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,"
+        "%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]),
+          "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]),
+          "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]),
+          "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]),
+          "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -173,45 +233,49 @@ __device__ __forceinline__ void tc_st16(uint32_t taddr, const uint32_t (&r)[16])
         : "memory");
 }
 
+struct TcBars {
+    uint64_t full[TC_RING], empty[TC_RING];   // slab buffer: loaded / released
+    uint64_t acc_full[2], acc_empty[2];       // accumulator buffer: MMAs done / drained and re-seeded
+    uint64_t drain;                           // every MMA of the CTA done
+};
+
 template <int MODE>
-__global__ void __launch_bounds__(128, 1) conv_tc_kernel(const __grid_constant__ CUtensorMap tin, Dims d,
-                                                         const uint16_t *__restrict__ wtc,
-                                                         const float *__restrict__ bias,
-                                                         const uint32_t *__restrict__ mask, uint32_t *__restrict__ out,
-                                                         float *__restrict__ outf, const int *done,
-                                                         int *__restrict__ status) {
+__global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_constant__ CUtensorMap tin, Dims d,
+                                                                int nbricks, const uint16_t *__restrict__ wtc,
+                                                                const float *__restrict__ bias,
+                                                                const uint32_t *__restrict__ mask,
+                                                                uint32_t *__restrict__ out, float *__restrict__ outf,
+                                                                const int *done, int *__restrict__ status) {
     if (done != nullptr && *(volatile const int *)done) return;
     extern __shared__ uint8_t tc_raw[];
-    __shared__ uint64_t bar_slab[TC_SY];
-    __shared__ uint64_t bar_mma;
+    __shared__ TcBars bars;
     __shared__ uint32_t tmem_base;
-    __shared__ int issue_ok;
-    uint8_t *sA = tc_raw + ((128u - (smem_addr(tc_raw) & 127u)) & 127u);
-    uint8_t *sW = sA + 2 * TC_PLANE;
+    __shared__ int abort_flag;
+    volatile int *abort = &abort_flag;
+    uint8_t *ring = tc_raw + ((128u - (smem_addr(tc_raw) & 127u)) & 127u);
+    uint8_t *sW = ring + TC_RING * TC_SLOT;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int x0 = blockIdx.x * TC_M, y0 = blockIdx.y * TC_TY, z0 = blockIdx.z * TC_TZ;
+    const int gx = (d.nx + TC_M - 1) / TC_M, gy = (d.ny + TC_TY - 1) / TC_TY;
     if (tid == 0) {
-        for (int s = 0; s < TC_SY; s++) mbar_init(&bar_slab[s], 1);
-        mbar_init(&bar_mma, 1);
+        for (int i = 0; i < TC_RING; i++) {
+            mbar_init(&bars.full[i], 1);
+            mbar_init(&bars.empty[i], 1);
+        }
+        for (int i = 0; i < 2; i++) {
+            mbar_init(&bars.acc_full[i], 1);
+            mbar_init(&bars.acc_empty[i], 4);   // one arrival per epilogue warp
+        }
+        mbar_init(&bars.drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        issue_ok = 1;
-    }
-    __syncthreads();
-    if (tid == 0) {   // staged y slab s = y0 - 1 + s, both channel halves, lines z0-1 .. z0+TC_TZ, cells x0-1 ..
-        if ((smem_addr(sA) & 127u) != 0u) {   // TMA destinations must be 128-byte aligned: copy nothing
+        abort_flag = 0;
+        if ((smem_addr(ring) & 127u) != 0u) {   // TMA destinations must be 128-byte aligned: do nothing
+            abort_flag = 1;
             atomicOr(status, 4);
-            issue_ok = 0;
-        } else {
-            for (int s = 0; s < TC_SY; s++) {
-                mbar_expect(&bar_slab[s], 2 * TC_BOX);
-                for (int h = 0; h < 2; h++)
-                    tma_load_4d(sA + h * TC_PLANE + s * TC_SLAB, &tin, 8 * h, x0 - 1, y0 - 1 + s, z0 - 1, &bar_slab[s]);
-            }
         }
     }
-    for (int i = tid; i < TC_WBYTES / 16; i += 128) ((uint4 *)sW)[i] = ((const uint4 *)wtc)[i];
+    for (int i = tid; i < TC_WBYTES / 16; i += TC_THREADS) ((uint4 *)sW)[i] = ((const uint4 *)wtc)[i];
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // weights: generic writes -> tensor-core reads
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
                      "r"(TC_COLS)
                      : "memory");
@@ -221,88 +285,135 @@ __global__ void __launch_bounds__(128, 1) conv_tc_kernel(const __grid_constant__
     __syncthreads();
     tc_fence_after();
     const uint32_t tb = tmem_base;
-    const uint32_t lane_base = tb + ((uint32_t)(warp * 32) << 16);
-    {   // accumulators start at the bias (forward) or zero (data gradient)
-        uint32_t v[16];
-#pragma unroll
-        for (int j = 0; j < 16; j++)
-            v[j] = __float_as_uint(MODE == 0 ? bias[j] : (MODE == 1 && j == 0 ? bias[0] : 0.0f));
-        for (int l = 0; l < TC_TY * TC_TZ; l++) tc_st16(lane_base + l * 16, v);
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (tid == 0) {
-        tc_fence_after();
-        const uint32_t a0 = smem_addr(sA), w0 = smem_addr(sW);
-        int s = issue_ok ? 0 : TC_SY;
-        for (; s < TC_SY; s++) {
-            if (!mbar_wait(&bar_slab[s], 0)) break;
-            const int ys = s - 1;   // staged y relative to y0
-            for (int dy = -1; dy <= 1; dy++) {
-                const int yo = ys - dy;   // output line it feeds
-                if (yo < 0 || yo >= TC_TY) continue;
-                for (int dx = -1; dx <= 1; dx++) {
-                    const uint32_t wcb = w0 + ((dy + 1) * 3 + (dx + 1)) * (2 * TC_WROWS * 16);
-                    for (int zs = -1; zs <= TC_TZ; zs++) {
-                        const int zlo = max(0, zs - 1), zhi = min(TC_TZ - 1, zs + 1);
-                        const int j0 = zlo - zs + 1;   // B block of the first output line: 0 dz=+1, 1 dz=0, 2 dz=-1
-                        const uint64_t ad =
-                            tc_sdesc(a0 + s * TC_SLAB + ((zs + 1) * (TC_M + 2) + dx + 1) * 16, TC_PLANE, 128);
-                        const uint64_t bd = tc_sdesc(wcb + j0 * 256, TC_WROWS * 16, 128);
-                        tc_mma(tb + (uint32_t)((yo * TC_TZ + zlo) * 16), ad, bd, tc_idesc(TC_M, (zhi - zlo + 1) * 16));
-                    }
-                }
+    int issued = 0;   // producer: slabs whose copies were started
+    if (!*abort && warp == 0 && lane == 0) {
+        // ---------------- TMA producer ----------------
+        for (int br = blockIdx.x; br < nbricks && !*abort; br += gridDim.x) {
+            const int bx = br % gx, r = br / gx, by = r % gy, bz = r / gy;
+            const int x0 = bx * TC_M, y0 = by * TC_TY, z0 = bz * TC_TZ;
+            for (int s = 0; s < TC_SY; s++) {
+                const int slot = issued % TC_RING;
+                if (!mbar_wait(&bars.empty[slot], ((issued / TC_RING) & 1) ^ 1, abort, status, 1)) break;
+                mbar_expect(&bars.full[slot], 2 * TC_BOX);
+                for (int h = 0; h < 2; h++)
+                    tma_load_5d(ring + slot * TC_SLOT + h * TC_HALF, &tin, 0, x0 / 8 - 1, y0 - 1 + s, z0 - 1, h,
+                                &bars.full[slot]);
+                issued++;
             }
         }
-        tc_commit(&bar_mma);   // arrives once every MMA issued above has completed
-        if (issue_ok && s < TC_SY) {   // staging timed out: let the copies in flight land before the CTA exits
-            issue_ok = 0;
-            atomicOr(status, 1);
-            for (; s < TC_SY; s++) mbar_wait(&bar_slab[s], 0);
+    } else if (!*abort && warp == 1 && lane == 0) {
+        // ---------------- MMA issuer ----------------
+        const uint64_t a_desc0 = tc_sdesc(smem_addr(ring), TC_HALF, 128);
+        const uint64_t w_desc0 = tc_sdesc(smem_addr(sW), TC_WROWS * 16, 128);
+        const uint32_t id16 = tc_idesc(TC_M, 16), id32 = tc_idesc(TC_M, 32), id48 = tc_idesc(TC_M, 48);
+        int q = 0, i = 0;
+        for (int br = blockIdx.x; br < nbricks && !*abort; br += gridDim.x, i++) {
+            const int ab = i & 1;
+            if (!mbar_wait(&bars.acc_empty[ab], (i >> 1) & 1, abort, status, 2)) break;
+            tc_fence_after();
+            const uint32_t dbase = tb + (uint32_t)(ab * TC_ACC);
+            for (int s = 0; s < TC_SY; s++, q++) {
+                const int slot = q % TC_RING;
+                if (!mbar_wait(&bars.full[slot], (q / TC_RING) & 1, abort, status, 2)) break;
+                tc_fence_after();
+                const uint64_t abase = a_desc0 + (uint64_t)((slot * TC_SLOT) >> 4);
+                const int ys = s - 1;   // staged y relative to the brick
+#pragma unroll
+                for (int dy = -1; dy <= 1; dy++) {
+                    const int yo = ys - dy;   // output line it feeds
+                    if (yo < 0 || yo >= TC_TY) continue;
+                    const uint32_t dline = dbase + (uint32_t)(yo * TC_TZ * 16);
+#pragma unroll
+                    for (int dx = -1; dx <= 1; dx++) {
+                        const uint64_t bb = w_desc0 + (uint64_t)((((dy + 1) * 3 + (dx + 1)) * (2 * TC_WROWS * 16)) >> 4);
+                        const uint64_t aa = abase + (uint64_t)(dx + 8);
+#pragma unroll
+                        for (int zs = -1; zs <= TC_TZ; zs++) {
+                            const int zlo = zs - 1 < 0 ? 0 : zs - 1, zhi = zs + 1 > TC_TZ - 1 ? TC_TZ - 1 : zs + 1;
+                            const int nl = zhi - zlo + 1, j0 = zlo - zs + 1;   // B block of z' = zlo: 0 dz=+1, 1 dz=0, 2 dz=-1
+                            tc_mma(dline + (uint32_t)(zlo * 16), aa + (uint64_t)((zs + 1) * TC_XS),
+                                   bb + (uint64_t)(j0 * 16), nl == 3 ? id48 : nl == 2 ? id32 : id16);
+                        }
+                    }
+                }
+                tc_commit(&bars.empty[slot]);   // the buffer is free once these MMAs have read it
+            }
+            tc_commit(&bars.acc_full[ab]);
+        }
+    } else if (warp >= 2) {
+        // ---------------- epilogue: warps 2-5, lane quarter (warp % 4) ----------------
+        const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+        uint32_t seed[16];
+#pragma unroll
+        for (int j = 0; j < 16; j++)
+            seed[j] = __float_as_uint(MODE == 0 ? bias[j] : (MODE == 1 && j == 0 ? bias[0] : 0.0f));
+        for (int ab = 0; ab < 2; ab++) {
+            for (int l = 0; l < TC_TY * TC_TZ; l++) tc_st16(tb + lane_off + (uint32_t)(ab * TC_ACC + l * 16), seed);
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bars.acc_empty[ab]);
+        }
+        int i = 0;
+        for (int br = blockIdx.x; br < nbricks && !*abort; br += gridDim.x, i++) {
+            const int ab = i & 1;
+            if (!mbar_wait(&bars.acc_full[ab], (i >> 1) & 1, abort, status, 8)) break;
+            tc_fence_after();
+            const int bx = br % gx, r = br / gx, by = r % gy, bz = r / gy;
+            const int x = bx * TC_M + (warp & 3) * 32 + lane, y0 = by * TC_TY, z0 = bz * TC_TZ;
+            const uint32_t acc = tb + lane_off + (uint32_t)(ab * TC_ACC);
+            for (int l4 = 0; l4 < TC_TY * TC_TZ; l4 += 4) {
+                uint32_t v4[64];
+                tc_ld64(acc + (uint32_t)(l4 * 16), v4);   // four lines, one wait
+#pragma unroll
+                for (int k = 0; k < 4; k++) tc_st16(acc + (uint32_t)((l4 + k) * 16), seed);
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const int l = l4 + k;
+                    const uint32_t *v = v4 + 16 * k;
+                    const int Y = y0 + l / TC_TZ, Z = z0 + l % TC_TZ;
+                    if (x >= d.nx || Y >= d.ny || Z >= d.nz) continue;
+                    if (MODE == 1) {
+                        outf[(long)x + (long)d.nx * (Y + (long)d.ny * Z)] = __uint_as_float(v[0]);
+                        continue;
+                    }
+                    const long pc = (long)x + (long)d.nxp * (Y + (long)d.ny * Z);   // plane cell index
+                    uint32_t o[8];
+                    if (MODE == 0) {
+#pragma unroll
+                        for (int w = 0; w < 8; w++)
+                            o[w] = pack_bf16(fmaxf(__uint_as_float(v[2 * w]), 0.f), fmaxf(__uint_as_float(v[2 * w + 1]), 0.f));
+                    } else {
+                        const uint4 m0 = *(const uint4 *)(mask + pc * 4), m1 = *(const uint4 *)(mask + (d.P + pc) * 4);
+                        const uint32_t mk[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+#pragma unroll
+                        for (int w = 0; w < 8; w++)
+                            o[w] = pack_bf16(bf16_lo(mk[w]) > 0.f ? __uint_as_float(v[2 * w]) : 0.f,
+                                             bf16_hi(mk[w]) > 0.f ? __uint_as_float(v[2 * w + 1]) : 0.f);
+                    }
+                    *(uint4 *)(out + pc * 4) = make_uint4(o[0], o[1], o[2], o[3]);
+                    *(uint4 *)(out + (d.P + pc) * 4) = make_uint4(o[4], o[5], o[6], o[7]);
+                }
+            }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bars.acc_empty[ab]);
         }
     }
     __syncwarp();
-    bool ok = mbar_wait(&bar_mma, 0);
-    if (!ok) {
-        atomicOr(status, 2);
-        mbar_wait(&bar_mma, 0);
+    // ---------------- drain: nothing in flight when tensor memory is freed ----------------
+    if (warp == 1 && lane == 0) {
+        tc_commit(&bars.drain);
+        if (!mbar_drain(&bars.drain, 0)) atomicOr(status, 2);
     }
-    __syncthreads();
-    tc_fence_after();
-    if (ok && issue_ok) {
-        const int x = x0 + warp * 32 + lane;
-        for (int l = 0; l < TC_TY * TC_TZ; l++) {
-            uint32_t r[16];
-            tc_ld16(lane_base + l * 16, r);
-            const int Y = y0 + l / TC_TZ, Z = z0 + l % TC_TZ;
-            if (x >= d.nx || Y >= d.ny || Z >= d.nz) continue;
-            const long c = (long)x + (long)d.nx * (Y + (long)d.ny * Z);
-            if (MODE == 1) {
-                outf[c] = __uint_as_float(r[0]);
-                continue;
-            }
-            uint32_t o[8];
-            if (MODE == 0) {
-#pragma unroll
-                for (int k = 0; k < 8; k++)
-                    o[k] = pack_bf16(fmaxf(__uint_as_float(r[2 * k]), 0.f), fmaxf(__uint_as_float(r[2 * k + 1]), 0.f));
-            } else {
-                const uint4 m0 = ((const uint4 *)(mask + c * 8))[0], m1 = ((const uint4 *)(mask + c * 8))[1];
-                const uint32_t mk[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
-#pragma unroll
-                for (int k = 0; k < 8; k++)
-                    o[k] = pack_bf16(bf16_lo(mk[k]) > 0.f ? __uint_as_float(r[2 * k]) : 0.f,
-                                     bf16_hi(mk[k]) > 0.f ? __uint_as_float(r[2 * k + 1]) : 0.f);
-            }
-            uint4 *dst = (uint4 *)(out + c * 8);
-            dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
-            dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
-        }
+    if (warp == 0 && lane == 0 && *abort) {
+        for (int k = issued - TC_RING < 0 ? 0 : issued - TC_RING; k < issued; k++)
+            if (!mbar_drain(&bars.full[k % TC_RING], (k / TC_RING) & 1)) atomicOr(status, 1);
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tb), "r"(TC_COLS) : "memory");
     }
@@ -327,28 +438,31 @@ __global__ void __launch_bounds__(128) wgrad_kernel(Dims d, const uint16_t *__re
 #pragma unroll
         for (int q = 0; q < 4; q++) acc[nt][q] = 0.0f;
     for (int k0 = c_begin + warp * 16; k0 < c_end; k0 += 64) {
-        int cell[4], nb[4];
+        long cell[4], nb[4];   // plane cell indices of the cell and of its neighbour through the tap
         const int kk[4] = {2 * t4, 2 * t4 + 1, 2 * t4 + 8, 2 * t4 + 9};
 #pragma unroll
         for (int q = 0; q < 4; q++) {
-            cell[q] = k0 + kk[q];
             nb[q] = -1;
-            if (cell[q] < c_end) {
-                const int c = cell[q];
+            cell[q] = -1;
+            if (k0 + kk[q] < c_end) {
+                const int c = k0 + kk[q];
                 const int x = c % d.nx, qq = c / d.nx, y = qq % d.ny, z = qq / d.ny;
-                nb[q] = tap_nbr(d, x, y, z, c, tap);
-            } else {
-                cell[q] = -1;
+                cell[q] = (long)x + (long)d.nxp * (y + (long)d.ny * z);
+                nb[q] = tap_nbr(d, x, y, z, tap);
             }
         }
-        auto A = [&](int q, int ci) -> uint32_t { return nb[q] >= 0 ? bf16_bits(in + (long)nb[q] * CH + ci) : 0u; };
+        auto A = [&](int q, int ci) -> uint32_t {
+            return nb[q] >= 0 ? bf16_bits(in + ((long)(ci >> 3) * d.P + nb[q]) * 8 + (ci & 7)) : 0u;
+        };
         const uint32_t a0 = A(0, g) | (A(1, g) << 16);
         const uint32_t a1 = A(0, g + 8) | (A(1, g + 8) << 16);
         const uint32_t a2 = A(2, g) | (A(3, g) << 16);
         const uint32_t a3 = A(2, g + 8) | (A(3, g + 8) << 16);
 #pragma unroll
         for (int nt = 0; nt < NT; nt++) {
-            auto Bv = [&](int q) -> uint32_t { return cell[q] >= 0 ? bf16_bits(dout + (long)cell[q] * CH + nt * 8 + g) : 0u; };
+            auto Bv = [&](int q) -> uint32_t {
+                return cell[q] >= 0 ? bf16_bits(dout + ((long)nt * d.P + cell[q]) * 8 + g) : 0u;   // channel 8 nt + g
+            };
             const uint32_t b0 = Bv(0) | (Bv(1) << 16);
             const uint32_t b1 = Bv(2) | (Bv(3) << 16);
             mma_bf16(acc[nt], a0, a1, a2, a3, b0, b1);
@@ -384,12 +498,12 @@ __global__ void wgrad_fold_kernel(int nchunk, int cin, int cout, const float *__
 }
 
 // bias gradient partials: per block sums of dout channels
-__global__ void bgrad_kernel(int N, int cout, const uint16_t *__restrict__ dout, float *__restrict__ part) {
+__global__ void bgrad_kernel(Dims d, int cout, const uint16_t *__restrict__ dout, float *__restrict__ part) {
     __shared__ float sh[128][16];
     float s[16];
     for (int c = 0; c < 16; c++) s[c] = 0.f;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
-        for (int c = 0; c < cout; c++) s[c] += __uint_as_float(bf16_bits(dout + (long)i * CH + c) << 16);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.N; i += gridDim.x * blockDim.x)
+        for (int c = 0; c < cout; c++) s[c] += __uint_as_float(bf16_bits(dout + act_elem_c(d, i, c)) << 16);
     for (int c = 0; c < 16; c++) sh[threadIdx.x][c] = s[c];
     __syncthreads();
     if (threadIdx.x < 16) {
@@ -406,18 +520,19 @@ __global__ void bgrad_fold_kernel(int nblk, int cout, const float *__restrict__ 
     db[c] = t;
 }
 
-// MSE loss partials and dL/dy = 2 (y - target) / N into channel 0 of a BF16 [N][16] buffer
-__global__ void mse_kernel(int N, const float *__restrict__ y, const float *__restrict__ target, uint16_t *__restrict__ dout,
+// MSE loss partials and dL/dy = 2 (y - target) / N into channel 0 of a planar BF16 buffer
+__global__ void mse_kernel(Dims d, const float *__restrict__ y, const float *__restrict__ target, uint16_t *__restrict__ dout,
                            double *__restrict__ part) {
     __shared__ double sh[128];
     double s = 0.0;
+    const int N = d.N;
     const float scale = 2.0f / (float)N;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         const float e = y[i] - target[i];
         s += (double)e * e;
-        uint32_t *o = (uint32_t *)(dout + (long)i * CH);
-        o[0] = pack_bf16(e * scale, 0.f);
-        for (int k = 1; k < 8; k++) o[k] = 0u;
+        uint4 *o0 = (uint4 *)(dout + act_elem_c(d, i, 0)), *o1 = (uint4 *)(dout + act_elem_c(d, i, 8));
+        *o0 = make_uint4(pack_bf16(e * scale, 0.f), 0u, 0u, 0u);
+        *o1 = make_uint4(0u, 0u, 0u, 0u);
     }
     sh[threadIdx.x] = s;
     __syncthreads();
@@ -434,14 +549,14 @@ __global__ void mse_fold_kernel(int nblk, int N, const double *__restrict__ part
     *loss = t / N;
 }
 
-// FP32 features [N][4] -> BF16 [N][16] (channels 4..15 zero)
-__global__ void features_kernel(int N, const float *__restrict__ x, uint32_t *__restrict__ out, const int *done) {
+// FP32 features [N][4] -> planar BF16 activations (channels 4..15 zero)
+__global__ void features_kernel(Dims d, const float *__restrict__ x, uint16_t *__restrict__ out, const int *done) {
     if (done != nullptr && *(volatile const int *)done) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    out[(long)i * 8 + 0] = pack_bf16(x[(long)i * 4 + 0], x[(long)i * 4 + 1]);
-    out[(long)i * 8 + 1] = pack_bf16(x[(long)i * 4 + 2], x[(long)i * 4 + 3]);
-    for (int k = 2; k < 8; k++) out[(long)i * 8 + k] = 0u;
+    if (i >= d.N) return;
+    uint4 *o0 = (uint4 *)(out + act_elem_c(d, i, 0)), *o1 = (uint4 *)(out + act_elem_c(d, i, 8));
+    *o0 = make_uint4(pack_bf16(x[(long)i * 4 + 0], x[(long)i * 4 + 1]), pack_bf16(x[(long)i * 4 + 2], x[(long)i * 4 + 3]), 0u, 0u);
+    *o1 = make_uint4(0u, 0u, 0u, 0u);
 }
 
 // pack FP32 weights W[27][cin][cout] into the B operand of conv_tc_kernel:
@@ -532,6 +647,13 @@ static void *net_alloc(sim_net_t *n, size_t bytes) {
     return p;
 }
 
+// activations and gradients start at zero: the cells that pad x are never written
+static bool zero_acts(sim_net_t *n, size_t bytes) {
+    bool ok = true;
+    for (int l = 0; l <= NLAYER; l++) ok = ok && cudaMemset(n->act[l], 0, bytes) == cudaSuccess;
+    return ok && cudaMemset(n->g0, 0, bytes) == cudaSuccess && cudaMemset(n->g1, 0, bytes) == cudaSuccess;
+}
+
 static sim_status pack_all(sim_net_t *n) {
     for (int l = 0; l < NLAYER; l++) {
         pack_tc_kernel<<<sim_blocks(TC_WELEMS), SIM_THREADS, 0, n->stream>>>(CIN[l], COUT[l], 0, n->param + n->off_w[l], n->wf[l]);
@@ -542,8 +664,9 @@ static sim_status pack_all(sim_net_t *n) {
     return SIM_OK;
 }
 
-// TMA map of a BF16 [N][16] activation buffer as the 4-D tensor (channel, x, y, z);
-// one box is one channel half of a staged y slab: 8 x (128 + 2) x 1 x (TC_TZ + 2)
+// TMA map of a planar activation buffer as the 5-D tensor (8 cells x 8 channels,
+// x / 8, y, z, plane); one box is one plane of a staged slab: rows of 8 cells
+// (128 bytes), TC_XS / 8 rows per line, TC_SZ lines
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -561,16 +684,27 @@ static EncodeTiledFn encode_tiled() {
 static bool act_map(const Dims &d, void *buf, CUtensorMap *map) {
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return false;
-    const cuuint64_t dims[4] = {16, (cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)d.nz};
-    const cuuint64_t strides[3] = {32, (cuuint64_t)d.nx * 32, (cuuint64_t)d.nx * d.ny * 32};
-    const cuuint32_t box[4] = {8, TC_M + 2, 1, TC_SZ}, estr[4] = {1, 1, 1, 1};
-    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, buf, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    const cuuint64_t dims[5] = {64, (cuuint64_t)d.nxp / 8, (cuuint64_t)d.ny, (cuuint64_t)d.nz, 2};
+    const cuuint64_t strides[4] = {128, (cuuint64_t)d.nxp * 16, (cuuint64_t)d.nxp * d.ny * 16, (cuuint64_t)d.P * 16};
+    const cuuint32_t box[5] = {64, TC_XS / 8, 1, TC_SZ, 1}, estr[5] = {1, 1, 1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, buf, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
            CUDA_SUCCESS;
 }
 
-static dim3 tc_grid(const Dims &d) {
-    return dim3((d.nx + TC_M - 1) / TC_M, (d.ny + TC_TY - 1) / TC_TY, (d.nz + TC_TZ - 1) / TC_TZ);
+static int tc_bricks(const Dims &d) {
+    return ((d.nx + TC_M - 1) / TC_M) * ((d.ny + TC_TY - 1) / TC_TY) * ((d.nz + TC_TZ - 1) / TC_TZ);
+}
+// persistent grid: one CTA per SM (the kernel's shared memory admits no second), at most one per brick
+static int tc_grid(const Dims &d) {
+    static const int sms = [] {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            v = 1;
+        return v > 0 ? v : 1;
+    }();
+    const int nb = tc_bricks(d);
+    return nb < sms ? nb : sms;
 }
 
 // once per process: the convolution needs more than the default 48 KB of shared memory
@@ -585,15 +719,15 @@ static bool tc_attrs() {
 
 static sim_status net_forward(sim_net_t *n, const int *done = nullptr) {
     if (!tc_attrs()) return net_fail(n, SIM_ECUDA, "convolution kernel attributes");
-    const dim3 grid = tc_grid(n->d);
+    const int grid = tc_grid(n->d), nb = tc_bricks(n->d);
     for (int l = 0; l < NLAYER; l++) {
         const float *bias = n->param + n->off_b[l];
         if (l + 1 < NLAYER)
-            conv_tc_kernel<0><<<grid, 128, TC_SMEM, n->stream>>>(n->map_act[l], n->d, n->wf[l], bias, nullptr,
-                                                                 n->act[l + 1], nullptr, done, n->dstat);
+            conv_tc_kernel<0><<<grid, TC_THREADS, TC_SMEM, n->stream>>>(n->map_act[l], n->d, nb, n->wf[l], bias, nullptr,
+                                                                        n->act[l + 1], nullptr, done, n->dstat);
         else
-            conv_tc_kernel<1><<<grid, 128, TC_SMEM, n->stream>>>(n->map_act[l], n->d, n->wf[l], bias, nullptr, nullptr,
-                                                                 n->out, done, n->dstat);
+            conv_tc_kernel<1><<<grid, TC_THREADS, TC_SMEM, n->stream>>>(n->map_act[l], n->d, nb, n->wf[l], bias, nullptr,
+                                                                        nullptr, n->out, done, n->dstat);
         NET_LAUNCHED(n);
     }
     return SIM_OK;
@@ -602,7 +736,7 @@ static sim_status net_forward(sim_net_t *n, const int *done = nullptr) {
 // gradients of the MSE loss of the last forward pass into n->grad; loss into n->dloss
 static sim_status net_backward(sim_net_t *n, const float *target) {
     const int N = n->d.N;
-    mse_kernel<<<n->lblk, 128, 0, n->stream>>>(N, n->out, target, (uint16_t *)n->g0, n->lpart);
+    mse_kernel<<<n->lblk, 128, 0, n->stream>>>(n->d, n->out, target, (uint16_t *)n->g0, n->lpart);
     NET_LAUNCHED(n);
     mse_fold_kernel<<<1, 32, 0, n->stream>>>(n->lblk, N, n->lpart, n->dloss);
     NET_LAUNCHED(n);
@@ -618,13 +752,14 @@ static sim_status net_backward(sim_net_t *n, const float *target) {
         if (NT == 2) wgrad_fold_kernel<2><<<sim_blocks(ne), SIM_THREADS, 0, n->stream>>>(n->nchunk, CIN[l], COUT[l], n->wpart, n->grad + n->off_w[l]);
         else wgrad_fold_kernel<1><<<sim_blocks(ne), SIM_THREADS, 0, n->stream>>>(n->nchunk, CIN[l], COUT[l], n->wpart, n->grad + n->off_w[l]);
         NET_LAUNCHED(n);
-        bgrad_kernel<<<n->bblk, 128, 0, n->stream>>>(N, COUT[l], (const uint16_t *)gcur, n->bpart);
+        bgrad_kernel<<<n->bblk, 128, 0, n->stream>>>(n->d, COUT[l], (const uint16_t *)gcur, n->bpart);
         NET_LAUNCHED(n);
         bgrad_fold_kernel<<<1, 32, 0, n->stream>>>(n->bblk, COUT[l], n->bpart, n->grad + n->off_b[l]);
         NET_LAUNCHED(n);
         if (l > 0) {   // data gradient through layer l into the ReLU output of layer l-1
-            conv_tc_kernel<2><<<tc_grid(n->d), 128, TC_SMEM, n->stream>>>(n->map_g[gcur == n->g0 ? 0 : 1], n->d, n->wb[l],
-                                                                          nullptr, n->act[l], gnext, nullptr, nullptr, n->dstat);
+            conv_tc_kernel<2><<<tc_grid(n->d), TC_THREADS, TC_SMEM, n->stream>>>(
+                n->map_g[gcur == n->g0 ? 0 : 1], n->d, tc_bricks(n->d), n->wb[l], nullptr, n->act[l], gnext, nullptr,
+                nullptr, n->dstat);
             NET_LAUNCHED(n);
             uint32_t *t = gcur; gcur = gnext; gnext = t;
         }
@@ -641,6 +776,8 @@ sim_status sim_net_create(int32_t nx, int32_t ny, int32_t nz, uint64_t seed, voi
         return sim_fail(nullptr, SIM_EINVAL, "sim_net_create: bad grid");
     sim_net_t *n = new sim_net_t();
     n->d.nx = nx; n->d.ny = ny; n->d.nz = nz; n->d.N = nx * ny * nz;
+    n->d.nxp = (nx + 7) / 8 * 8;
+    n->d.P = (long)n->d.nxp * ny * nz;
     if (cuda_stream) n->stream = (cudaStream_t)cuda_stream;
     else {
         if (cudaStreamCreateWithFlags(&n->stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -666,10 +803,11 @@ sim_status sim_net_create(int32_t nx, int32_t ny, int32_t nz, uint64_t seed, voi
         n->wf[l] = (uint16_t *)A(TC_WBYTES);
         n->wb[l] = (uint16_t *)A(TC_WBYTES);
     }
-    for (int l = 0; l <= NLAYER; l++) n->act[l] = (uint32_t *)A(sizeof(uint32_t) * 8 * (size_t)N);
+    const size_t act_bytes = 32 * (size_t)n->d.P;   // two planes of 16 bytes per (padded) cell
+    for (int l = 0; l <= NLAYER; l++) n->act[l] = (uint32_t *)A(act_bytes);
     n->out = (float *)A(sizeof(float) * N);
-    n->g0 = (uint32_t *)A(sizeof(uint32_t) * 8 * (size_t)N);
-    n->g1 = (uint32_t *)A(sizeof(uint32_t) * 8 * (size_t)N);
+    n->g0 = (uint32_t *)A(act_bytes);
+    n->g1 = (uint32_t *)A(act_bytes);
     n->chunk = 4096;
     n->nchunk = (N + n->chunk - 1) / n->chunk;
     n->wpart = (float *)A(sizeof(float) * 27 * (size_t)n->nchunk * 16 * 16);
@@ -710,7 +848,7 @@ sim_status sim_net_create(int32_t nx, int32_t ny, int32_t nz, uint64_t seed, voi
     if (cudaMemcpy(n->param, h.data(), sizeof(float) * off, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(n->adam_m, 0, sizeof(float) * off) != cudaSuccess ||
         cudaMemset(n->adam_v, 0, sizeof(float) * off) != cudaSuccess || cudaMemset(n->dstat, 0, sizeof(int)) != cudaSuccess ||
-        pack_all(n) != SIM_OK) {
+        !zero_acts(n, act_bytes) || pack_all(n) != SIM_OK) {
         sim_net_destroy(n);
         return sim_fail(nullptr, SIM_ECUDA, "sim_net_create: initialisation failed");
     }
@@ -747,7 +885,7 @@ sim_status sim_net_get_params(sim_net_t *n, float *params) {
 sim_status sim_net_forward(sim_net_t *n, const float *x_dev, float *y_dev) {
     if (!n || !x_dev || !y_dev) return SIM_EINVAL;
     if (n->err != SIM_OK) return n->err;
-    features_kernel<<<sim_blocks(n->d.N), SIM_THREADS, 0, n->stream>>>(n->d.N, x_dev, n->act[0], nullptr);
+    features_kernel<<<sim_blocks(n->d.N), SIM_THREADS, 0, n->stream>>>(n->d, x_dev, (uint16_t *)n->act[0], nullptr);
     NET_LAUNCHED(n);
     if (net_forward(n) != SIM_OK) return n->err;
     NET_CK(n, cudaMemcpyAsync(y_dev, n->out, sizeof(float) * n->d.N, cudaMemcpyDeviceToDevice, n->stream));
@@ -757,7 +895,7 @@ sim_status sim_net_forward(sim_net_t *n, const float *x_dev, float *y_dev) {
 sim_status sim_net_loss_grad(sim_net_t *n, const float *x_dev, const float *target_dev, double *loss, float *grads) {
     if (!n || !x_dev || !target_dev) return SIM_EINVAL;
     if (n->err != SIM_OK) return n->err;
-    features_kernel<<<sim_blocks(n->d.N), SIM_THREADS, 0, n->stream>>>(n->d.N, x_dev, n->act[0], nullptr);
+    features_kernel<<<sim_blocks(n->d.N), SIM_THREADS, 0, n->stream>>>(n->d, x_dev, (uint16_t *)n->act[0], nullptr);
     NET_LAUNCHED(n);
     if (net_forward(n) != SIM_OK || net_backward(n, target_dev) != SIM_OK) return n->err;
     double l = 0.0;
@@ -771,7 +909,7 @@ sim_status sim_net_loss_grad(sim_net_t *n, const float *x_dev, const float *targ
 sim_status sim_net_train_step(sim_net_t *n, const float *x_dev, const float *target_dev, float lr, double *loss) {
     if (!n || !x_dev || !target_dev) return SIM_EINVAL;
     if (n->err != SIM_OK) return n->err;
-    features_kernel<<<sim_blocks(n->d.N), SIM_THREADS, 0, n->stream>>>(n->d.N, x_dev, n->act[0], nullptr);
+    features_kernel<<<sim_blocks(n->d.N), SIM_THREADS, 0, n->stream>>>(n->d, x_dev, (uint16_t *)n->act[0], nullptr);
     NET_LAUNCHED(n);
     if (net_forward(n) != SIM_OK || net_backward(n, target_dev) != SIM_OK) return n->err;
     n->adam_t++;
@@ -792,7 +930,7 @@ sim_status sim_net_train_step(sim_net_t *n, const float *x_dev, const float *tar
 sim_status net_infer(sim_net_t *n, const float *x_dev, float *y_dev, cudaStream_t st, const int *done) {
     cudaStream_t keep = n->stream;
     n->stream = st;
-    features_kernel<<<sim_blocks(n->d.N), SIM_THREADS, 0, st>>>(n->d.N, x_dev, n->act[0], done);
+    features_kernel<<<sim_blocks(n->d.N), SIM_THREADS, 0, st>>>(n->d, x_dev, (uint16_t *)n->act[0], done);
     n->launches++;
     sim_status r = net_forward(n, done);
     if (r == SIM_OK && cudaMemcpyAsync(y_dev, n->out, sizeof(float) * n->d.N, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
