@@ -70,15 +70,6 @@ __device__ __forceinline__ long act_elem_c(const Dims &d, int c, int ch) {
     return act_elem(d, x, q % d.ny, q / d.ny, ch);
 }
 
-// plane cell index (x + nxp (y + ny z)) of the neighbour of cell (x, y, z) through
-// tap t (offset (t/9-1, (t/3)%3-1, t%3-1) in (z, y, x)), or -1 outside the grid
-__device__ __forceinline__ long tap_nbr(const Dims &d, int x, int y, int z, int t) {
-    const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
-    const int X = x + dx, Y = y + dy, Z = z + dz;
-    if (X < 0 || X >= d.nx || Y < 0 || Y >= d.ny || Z < 0 || Z >= d.nz) return -1;
-    return (long)X + (long)d.nxp * (Y + (long)d.ny * Z);
-}
-
 // ---------------------------------------------------------------------------
 // forward convolution / data gradient on the 5th-generation tensor cores
 // (tcgen05.mma kind::f16, BF16 x BF16 -> FP32 accumulators in tensor memory)
@@ -420,80 +411,129 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
 }
 
 // ---------------------------------------------------------------------------
-// weight gradient: dW[tap][ci][co] = sum_c in[nbr(c, tap)][ci] * dout[c][co]
-// block (chunk, tap); 4 warps stride over 16-cell k-steps; per-block partials
+// weight gradient: dW[t][ci][co] = sum over cells c of In[c + off(t)][ci] * G[c][co]
+// (mma.sync.m16n8k16 BF16 -> FP32; per tap a 16 x 16 product with the cells
+// as the contraction: too narrow for the 128-row tcgen05 tile).
+// Persistent, two CTAs per SM, bricks of 128 x 1 x WG_TZ cells dealt
+// round-robin.  Per brick one thread stages by TMA the three input slabs
+// (y-1, y, y+1; lines z0-1 .. z0+WG_TZ; cells x0-8 .. x0+135) and the brick's
+// output-gradient lines, both activation planes each, in the rows of 16 bytes
+// the activations have; out-of-grid cells arrive as zeros (bounds fill and x
+// padding), so no cell is masked.  Warp w owns taps w, w+8, w+16, w+24; per
+// 16-cell step it loads the gradient fragment once (ldmatrix.trans: rows are
+// cells) and, per tap, the input fragment of the shifted cells, and issues two
+// MMAs (output channels 0-7, 8-15).  Accumulators stay in registers across the
+// CTA's bricks; each CTA writes one partial [27][16][16], folded in CTA order
+// (deterministic).  Waits are bounded (status bit 4 on a timeout).
 // ---------------------------------------------------------------------------
-template <int NT>
-__global__ void __launch_bounds__(128) wgrad_kernel(Dims d, const uint16_t *__restrict__ in,
-                                                    const uint16_t *__restrict__ dout, int cells_per_block,
-                                                    float *__restrict__ part) {
-    const int tap = blockIdx.y;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, t4 = lane & 3;
-    const int c_begin = blockIdx.x * cells_per_block;
-    const int c_end = min(d.N, c_begin + cells_per_block);
-    float acc[NT][4];
-#pragma unroll
-    for (int nt = 0; nt < NT; nt++)
-#pragma unroll
-        for (int q = 0; q < 4; q++) acc[nt][q] = 0.0f;
-    for (int k0 = c_begin + warp * 16; k0 < c_end; k0 += 64) {
-        long cell[4], nb[4];   // plane cell indices of the cell and of its neighbour through the tap
-        const int kk[4] = {2 * t4, 2 * t4 + 1, 2 * t4 + 8, 2 * t4 + 9};
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            nb[q] = -1;
-            cell[q] = -1;
-            if (k0 + kk[q] < c_end) {
-                const int c = k0 + kk[q];
-                const int x = c % d.nx, qq = c / d.nx, y = qq % d.ny, z = qq / d.ny;
-                cell[q] = (long)x + (long)d.nxp * (y + (long)d.ny * z);
-                nb[q] = tap_nbr(d, x, y, z, tap);
-            }
-        }
-        auto A = [&](int q, int ci) -> uint32_t {
-            return nb[q] >= 0 ? bf16_bits(in + ((long)(ci >> 3) * d.P + nb[q]) * 8 + (ci & 7)) : 0u;
-        };
-        const uint32_t a0 = A(0, g) | (A(1, g) << 16);
-        const uint32_t a1 = A(0, g + 8) | (A(1, g + 8) << 16);
-        const uint32_t a2 = A(2, g) | (A(3, g) << 16);
-        const uint32_t a3 = A(2, g + 8) | (A(3, g + 8) << 16);
-#pragma unroll
-        for (int nt = 0; nt < NT; nt++) {
-            auto Bv = [&](int q) -> uint32_t {
-                return cell[q] >= 0 ? bf16_bits(dout + ((long)nt * d.P + cell[q]) * 8 + g) : 0u;   // channel 8 nt + g
-            };
-            const uint32_t b0 = Bv(0) | (Bv(1) << 16);
-            const uint32_t b1 = Bv(2) | (Bv(3) << 16);
-            mma_bf16(acc[nt], a0, a1, a2, a3, b0, b1);
-        }
-    }
-    // fold the 4 warps in shared memory, then write the block partial [16][NT*8]
-    __shared__ float red[4][16 * 16];
-#pragma unroll
-    for (int nt = 0; nt < NT; nt++) {
-        const int col = nt * 8 + 2 * t4;
-        red[warp][g * 16 + col] = acc[nt][0];
-        red[warp][g * 16 + col + 1] = acc[nt][1];
-        red[warp][(g + 8) * 16 + col] = acc[nt][2];
-        red[warp][(g + 8) * 16 + col + 1] = acc[nt][3];
+constexpr int WG_TZ = 4;                                   // output lines per brick (z)
+constexpr int WG_SZ = WG_TZ + 2;                           // staged lines per input slab
+constexpr int WG_IBOX = WG_SZ * TC_LINE;                   // one input slab, one plane (TMA box)
+constexpr int WG_GBOX = WG_TZ * TC_M * 16;                 // output-gradient lines of a brick, one plane
+constexpr int WG_IN = 6 * WG_IBOX;                         // 3 slabs x 2 planes
+constexpr int WG_SMEM = WG_IN + 2 * WG_GBOX + 128;
+constexpr int WG_THREADS = 256;
+static_assert(WG_IBOX % 128 == 0 && WG_GBOX % 128 == 0, "TMA destinations 128-byte aligned");
+static_assert(2 * (WG_SMEM + 1024) <= 228 * 1024, "two CTAs per SM");
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+__global__ void __launch_bounds__(WG_THREADS, 2) wgrad_tc_kernel(const __grid_constant__ CUtensorMap tin,
+                                                                 const __grid_constant__ CUtensorMap tg, Dims d,
+                                                                 int nbricks, float *__restrict__ part,
+                                                                 int *__restrict__ status) {
+    extern __shared__ uint8_t wg_raw[];
+    __shared__ uint64_t bar;
+    __shared__ int abort_flag;
+    volatile int *abort = &abort_flag;
+    uint8_t *sin = wg_raw + ((128u - (smem_addr(wg_raw) & 127u)) & 127u);
+    uint8_t *sg = sin + WG_IN;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int gx = (d.nx + TC_M - 1) / TC_M;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_flag = (smem_addr(sin) & 127u) != 0u;
+        if (abort_flag) atomicOr(status, 4);
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < 16 * NT * 8; e += blockDim.x) {
-        const int ci = e / (NT * 8), co = e % (NT * 8);
-        const float s = red[0][ci * 16 + co] + red[1][ci * 16 + co] + red[2][ci * 16 + co] + red[3][ci * 16 + co];
-        part[(((long)tap * gridDim.x + blockIdx.x) * 16 + ci) * (NT * 8) + co] = s;
+    float acc[4][2][4];
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+#pragma unroll
+        for (int h = 0; h < 2; h++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) acc[j][h][q] = 0.f;
+    // ldmatrix row of this lane: lanes 8m .. 8m+7 address the rows (cells) of matrix m
+    const int mrow = lane & 7, mat = lane >> 3;
+    const uint32_t s_in = smem_addr(sin), s_g = smem_addr(sg);
+    int it = 0;
+    for (int br = blockIdx.x; br < nbricks && !*abort; br += gridDim.x, it++) {
+        const int bx = br % gx, r = br / gx, y = r % d.ny, bz = r / d.ny;
+        const int x0 = bx * TC_M, z0 = bz * WG_TZ;
+        if (tid == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect(&bar, WG_IN + 2 * WG_GBOX);
+            for (int s = 0; s < 3; s++)
+                for (int h = 0; h < 2; h++)
+                    tma_load_5d(sin + (s * 2 + h) * WG_IBOX, &tin, 0, x0 / 8 - 1, y - 1 + s, z0 - 1, h, &bar);
+            for (int h = 0; h < 2; h++) tma_load_5d(sg + h * WG_GBOX, &tg, 0, x0 / 8, y, z0, h, &bar);
+        }
+        if (!mbar_wait(&bar, it & 1, abort, status, 16)) break;
+        for (int zo = 0; zo < WG_TZ; zo++) {
+            for (int xk = 0; xk < TC_M; xk += 16) {
+                // gradient fragment (B, 16 cells x 16 outputs): matrices (plane 0, cells 0-7), (0, 8-15), (1, 0-7), (1, 8-15)
+                uint32_t b[4];
+                ldsm_x4_t(s_g + (uint32_t)((mat >> 1) * WG_GBOX + ((zo * TC_M + xk + (mat & 1) * 8 + mrow) * 16)), b[0], b[1],
+                          b[2], b[3]);
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const int t = warp + 8 * j;
+                    if (t < 27) {
+                        const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+                        // input fragment (A, 16 channels x 16 cells) at the shifted cells:
+                        // matrices (plane 0, cells 0-7), (1, 0-7), (0, 8-15), (1, 8-15)
+                        const int cell = (zo + dz + 1) * TC_XS + xk + dx + 8 + (mat >> 1) * 8 + mrow;
+                        uint32_t a[4];
+                        ldsm_x4_t(s_in + (uint32_t)(((dy + 1) * 2 + (mat & 1)) * WG_IBOX + cell * 16), a[0], a[1], a[2], a[3]);
+                        mma_bf16(acc[j][0], a[0], a[1], a[2], a[3], b[0], b[1]);
+                        mma_bf16(acc[j][1], a[0], a[1], a[2], a[3], b[2], b[3]);
+                    }
+                }
+            }
+        }
+        __syncthreads();   // every warp is done with the buffers before the next brick's copies
+    }
+    if (tid == 0 && *abort && !mbar_drain(&bar, it & 1)) atomicOr(status, 16);
+    // partial of this CTA: [27][16 ci][16 co]
+    const int g = lane >> 2, t4 = lane & 3;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const int t = warp + 8 * j;
+        if (t >= 27) continue;
+        float *o = part + ((long)blockIdx.x * 27 + t) * 256;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int co = 8 * h + 2 * t4;
+            o[g * 16 + co] = acc[j][h][0];
+            o[g * 16 + co + 1] = acc[j][h][1];
+            o[(g + 8) * 16 + co] = acc[j][h][2];
+            o[(g + 8) * 16 + co + 1] = acc[j][h][3];
+        }
     }
 }
 
-// dW[tap][ci][co] (FP32, logical cin x cout) = sum over chunks of the partials
-template <int NT>
-__global__ void wgrad_fold_kernel(int nchunk, int cin, int cout, const float *__restrict__ part, float *__restrict__ dW) {
+// dW[t][ci][co] (FP32, logical cin x cout) = sum of the CTAs' partials, in CTA order
+__global__ void wgrad_fold_kernel(int nblk, int cin, int cout, const float *__restrict__ part, float *__restrict__ dW) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= 27 * cin * cout) return;
     const int tap = e / (cin * cout), r = e % (cin * cout), ci = r / cout, co = r % cout;
     float s = 0.f;
-    for (int b = 0; b < nchunk; b++) s += part[(((long)tap * nchunk + b) * 16 + ci) * (NT * 8) + co];
+    for (int b = 0; b < nblk; b++) s += part[((long)b * 27 + tap) * 256 + ci * 16 + co];
     dW[e] = s;
 }
 
@@ -608,12 +648,14 @@ struct sim_net {
     uint32_t *act[NLAYER + 1];           // BF16 [N][16]: input features, hidden activations
     CUtensorMap map_act[NLAYER];         // TMA maps of act[0..3] (inputs of the forward layers)
     CUtensorMap map_g[2];                // TMA maps of g0, g1 (inputs of the data gradients)
+    CUtensorMap map_win[NLAYER];         // act[0..3] with the weight gradient's input box
+    CUtensorMap map_wg[2];               // g0, g1 with the weight gradient's output-gradient box
     int *dstat = nullptr;                // device status word of the convolutions (bounded waits)
     float *out = nullptr;                // [N]
     uint32_t *g0 = nullptr, *g1 = nullptr;   // BF16 [N][16] gradient buffers
     float *wpart = nullptr, *bpart = nullptr;
     double *lpart = nullptr, *dloss = nullptr;
-    int chunk = 0, nchunk = 0, bblk = 0, lblk = 0;
+    int wg_ctas = 0, bblk = 0, lblk = 0;
     int adam_t = 0;
     int64_t launches = 0;
 };
@@ -681,12 +723,12 @@ static EncodeTiledFn encode_tiled() {
     }();
     return fn;
 }
-static bool act_map(const Dims &d, void *buf, CUtensorMap *map) {
+static bool act_map(const Dims &d, void *buf, CUtensorMap *map, int box_x8 = TC_XS / 8, int box_z = TC_SZ) {
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return false;
     const cuuint64_t dims[5] = {64, (cuuint64_t)d.nxp / 8, (cuuint64_t)d.ny, (cuuint64_t)d.nz, 2};
     const cuuint64_t strides[4] = {128, (cuuint64_t)d.nxp * 16, (cuuint64_t)d.nxp * d.ny * 16, (cuuint64_t)d.P * 16};
-    const cuuint32_t box[5] = {64, TC_XS / 8, 1, TC_SZ, 1}, estr[5] = {1, 1, 1, 1, 1};
+    const cuuint32_t box[5] = {64, (cuuint32_t)box_x8, 1, (cuuint32_t)box_z, 1}, estr[5] = {1, 1, 1, 1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, buf, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
            CUDA_SUCCESS;
@@ -695,16 +737,26 @@ static bool act_map(const Dims &d, void *buf, CUtensorMap *map) {
 static int tc_bricks(const Dims &d) {
     return ((d.nx + TC_M - 1) / TC_M) * ((d.ny + TC_TY - 1) / TC_TY) * ((d.nz + TC_TZ - 1) / TC_TZ);
 }
-// persistent grid: one CTA per SM (the kernel's shared memory admits no second), at most one per brick
-static int tc_grid(const Dims &d) {
+static int tc_grid_sms() {
     static const int sms = [] {
         int dev = 0, v = 0;
         if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             v = 1;
         return v > 0 ? v : 1;
     }();
-    const int nb = tc_bricks(d);
+    return sms;
+}
+// persistent grid: one CTA per SM (the kernel's shared memory admits no second), at most one per brick
+static int tc_grid(const Dims &d) {
+    const int nb = tc_bricks(d), sms = tc_grid_sms();
     return nb < sms ? nb : sms;
+}
+
+static int wg_bricks(const Dims &d) { return ((d.nx + TC_M - 1) / TC_M) * d.ny * ((d.nz + WG_TZ - 1) / WG_TZ); }
+// persistent weight-gradient grid: two CTAs per SM, at most one per brick
+static int wg_grid(const Dims &d) {
+    const int nb = wg_bricks(d), two = 2 * tc_grid_sms();
+    return nb < two ? nb : two;
 }
 
 // once per process: the convolution needs more than the default 48 KB of shared memory
@@ -712,7 +764,8 @@ static bool tc_attrs() {
     static const bool ok = [] {
         return cudaFuncSetAttribute(conv_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM) == cudaSuccess &&
                cudaFuncSetAttribute(conv_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM) == cudaSuccess &&
-               cudaFuncSetAttribute(conv_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM) == cudaSuccess;
+               cudaFuncSetAttribute(conv_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM) == cudaSuccess &&
+               cudaFuncSetAttribute(wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, WG_SMEM) == cudaSuccess;
     }();
     return ok;
 }
@@ -743,14 +796,13 @@ static sim_status net_backward(sim_net_t *n, const float *target) {
     if (!tc_attrs()) return net_fail(n, SIM_ECUDA, "convolution kernel attributes");
     uint32_t *gcur = n->g0, *gnext = n->g1;
     for (int l = NLAYER - 1; l >= 0; l--) {
-        const int NT = COUT[l] > 8 ? 2 : 1;
-        dim3 grid(n->nchunk, 27);
-        if (NT == 2) wgrad_kernel<2><<<grid, 128, 0, n->stream>>>(n->d, (const uint16_t *)n->act[l], (const uint16_t *)gcur, n->chunk, n->wpart);
-        else wgrad_kernel<1><<<grid, 128, 0, n->stream>>>(n->d, (const uint16_t *)n->act[l], (const uint16_t *)gcur, n->chunk, n->wpart);
+        const int gi = gcur == n->g0 ? 0 : 1;
+        wgrad_tc_kernel<<<n->wg_ctas, WG_THREADS, WG_SMEM, n->stream>>>(n->map_win[l], n->map_wg[gi], n->d, wg_bricks(n->d),
+                                                                       n->wpart, n->dstat);
         NET_LAUNCHED(n);
         const int ne = 27 * CIN[l] * COUT[l];
-        if (NT == 2) wgrad_fold_kernel<2><<<sim_blocks(ne), SIM_THREADS, 0, n->stream>>>(n->nchunk, CIN[l], COUT[l], n->wpart, n->grad + n->off_w[l]);
-        else wgrad_fold_kernel<1><<<sim_blocks(ne), SIM_THREADS, 0, n->stream>>>(n->nchunk, CIN[l], COUT[l], n->wpart, n->grad + n->off_w[l]);
+        wgrad_fold_kernel<<<sim_blocks(ne), SIM_THREADS, 0, n->stream>>>(n->wg_ctas, CIN[l], COUT[l], n->wpart,
+                                                                          n->grad + n->off_w[l]);
         NET_LAUNCHED(n);
         bgrad_kernel<<<n->bblk, 128, 0, n->stream>>>(n->d, COUT[l], (const uint16_t *)gcur, n->bpart);
         NET_LAUNCHED(n);
@@ -808,9 +860,8 @@ sim_status sim_net_create(int32_t nx, int32_t ny, int32_t nz, uint64_t seed, voi
     n->out = (float *)A(sizeof(float) * N);
     n->g0 = (uint32_t *)A(act_bytes);
     n->g1 = (uint32_t *)A(act_bytes);
-    n->chunk = 4096;
-    n->nchunk = (N + n->chunk - 1) / n->chunk;
-    n->wpart = (float *)A(sizeof(float) * 27 * (size_t)n->nchunk * 16 * 16);
+    n->wg_ctas = wg_grid(n->d);
+    n->wpart = (float *)A(sizeof(float) * 27 * 256 * (size_t)n->wg_ctas);
     n->bblk = 256;
     n->bpart = (float *)A(sizeof(float) * n->bblk * 16);
     n->lblk = 256;
@@ -823,8 +874,10 @@ sim_status sim_net_create(int32_t nx, int32_t ny, int32_t nz, uint64_t seed, voi
         return sim_fail(nullptr, SIM_ENOMEM, "sim_net_create: " + m);
     }
     bool maps = true;
-    for (int l = 0; l < NLAYER; l++) maps = maps && act_map(n->d, n->act[l], &n->map_act[l]);
-    maps = maps && act_map(n->d, n->g0, &n->map_g[0]) && act_map(n->d, n->g1, &n->map_g[1]);
+    for (int l = 0; l < NLAYER; l++)
+        maps = maps && act_map(n->d, n->act[l], &n->map_act[l]) && act_map(n->d, n->act[l], &n->map_win[l], TC_XS / 8, WG_SZ);
+    maps = maps && act_map(n->d, n->g0, &n->map_g[0]) && act_map(n->d, n->g1, &n->map_g[1]) &&
+           act_map(n->d, n->g0, &n->map_wg[0], TC_M / 8, WG_TZ) && act_map(n->d, n->g1, &n->map_wg[1], TC_M / 8, WG_TZ);
     if (!maps) {
         sim_net_destroy(n);
         return sim_fail(nullptr, SIM_ECUDA, "sim_net_create: cannot encode the TMA maps of the activations");
