@@ -672,6 +672,45 @@ def run_ensemble(args):
     return 0
 
 
+def conv_roofline(nx=256, ny=256, nz=64, reps=10):
+    """The learned stage's kernels on the evaluation grid, each launch after an
+    L2 eviction: forward convolution of a 16 -> 16 layer (tcgen05), its weight
+    gradient (mma.sync, with the fold) and data gradient (tcgen05).  Algorithmic
+    work per cell: 2 x 27 x 16 x 16 FLOP; bytes: the input and output
+    activations, 32 B each (the weight gradient reads two 32-B activations and
+    writes 27 x 16 x 16 FP32 partials per CTA, counted)."""
+    import torch
+    from paper_1606_00548_gb300.sim import Net
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    hbm, bf16 = float(peaks["hbm_gbs"]), float(peaks["bf16_tflops"])
+    N = nx * ny * nz
+    net = Net(nx, ny, nz, seed=0)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn(N * 4, dtype=torch.float32, device="cuda", generator=g)
+    t = torch.randn(N, dtype=torch.float32, device="cuda", generator=g)
+    y = torch.empty(N, dtype=torch.float32, device="cuda")
+    net.forward(x, y)
+    net.loss_grad(x, t)
+    flop = 2.0 * 27 * 16 * 16 * N
+    out = {}
+    for which, name, nbytes in ((0, "conv_tc_kernel forward 16->16", 64.0 * N),
+                                (1, "wgrad_tc_kernel + fold", 64.0 * N),
+                                (2, "conv_tc_kernel data gradient 16->16", 96.0 * N)):
+        net.time_conv(which, 3)
+        us = net.time_conv(which, reps)
+        out[name] = {"us": us, "tflops": flop / us / 1e6, "tensor_frac_bf16": flop / us / 1e6 / bf16,
+                     "hbm_gbs": nbytes / us / 1e3, "hbm_frac": nbytes / us / 1e3 / hbm}
+    net.close()
+    fwd = out["conv_tc_kernel forward 16->16"]
+    roof = {"kernel": "conv_tc_kernel (forward, 16 -> 16 channels, 256x256x64)", "bound": "hbm",
+            "achieved": fwd["hbm_gbs"], "peak": hbm, "unit": "GB/s", "frac": fwd["hbm_frac"], "traffic": None,
+            "note": "arithmetic intensity 216 FLOP/B is below the measured BF16/HBM balance "
+                    f"{bf16 * 1e3 / hbm:.0f} FLOP/B, so HBM bounds it; the tensor-core fraction is "
+                    f"{fwd['tensor_frac_bf16']:.3f} of the measured {bf16:.0f} TFLOP/s BF16 "
+                    "(profiles/conv_kernels_learned_256x256x64.md)"}
+    return {"roofline": roof, "kernels": out}
+
+
 def run_learned(args):
     """Second metric: CPR-FGMRES time to 1e-8 relative residual on the 256x256x64
     black-oil system (sigma 2): FP64 CPR and FP32-preconditioned CPR (two-stage
@@ -683,6 +722,7 @@ def run_learned(args):
     ev = learned.evaluate(train_steps=args.train_steps)
     r = ev["results"]
     best = min(r, key=lambda k: r[k]["seconds"])
+    conv = conv_roofline()
     line = {
         "metric": "CPR-FGMRES time to 1e-8 rel. residual", "value": r["mixed_cpr_learned"]["seconds"], "unit": "s",
         "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
@@ -692,6 +732,7 @@ def run_learned(args):
                    "train_seconds": ev["train_seconds"], "pairs_seconds": ev["pairs_seconds"],
                    "train_loss": ev["train_loss"][-3:]},
         "results": r, "fastest": best,
+        "roofline": conv["roofline"], "conv_kernels": conv["kernels"],
     }
     print(json.dumps(line), flush=True)
     return 0

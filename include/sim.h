@@ -392,8 +392,10 @@ sim_status sim_batch_phase_seconds(sim_batch_t *b, double *newton, double *solve
 /* ---- learned pressure stage (no paper counterpart) ----
    A 3-D convolutional network: 4 layers of 3x3x3 kernels (zero padding),
    channels 4 -> 16 -> 16 -> 16 -> 1, ReLU between layers; BF16 weights and
-   activations, FP32 accumulation on the tensor cores (mma.sync), FP32 master
-   weights updated by Adam on the device.  Inputs per cell (x [N][4] FP32,
+   activations, FP32 accumulation on the tensor cores (forward and data
+   gradient on tcgen05 with tensor-memory accumulators and TMA-staged inputs,
+   weight gradient on mma.sync), FP32 master weights updated by Adam on the
+   device.  Inputs per cell (x [N][4] FP32,
    cell-major): the normalised pressure residual and three standardised log
    face-transmissibility sums; output y [N] FP32: a normalised pressure
    correction.  Parameters as one flat FP32 array: for each layer, W[27][cin][cout]
@@ -411,6 +413,16 @@ sim_status sim_net_loss_grad(sim_net_t *n, const float *x_dev, const float *targ
 /* one Adam step (beta 0.9 / 0.999) on the loss; loss may be NULL (then no synchronisation) */
 sim_status sim_net_train_step(sim_net_t *n, const float *x_dev, const float *target_dev, float lr, double *loss);
 const char *sim_net_last_error(sim_net_t *n);
+/* Device time of one convolution kernel on the net's grid (measurement only):
+   `reps` launches on the net's stream, each bracketed by CUDA events and
+   preceded by a 256 MB write that evicts L2.  which = 0: the forward
+   convolution of hidden layer 2 (16 -> 16 channels, bias and ReLU fused);
+   1: the weight gradient of that layer (the kernel and its fold of the
+   per-CTA partials); 2: its data gradient.  The operands are the net's own
+   buffers: activations of the last forward pass (zero before any) and
+   gradient buffers, which the call overwrites.  *us = average microseconds per
+   launch; SIM_EINVAL for a bad which or reps < 1. */
+sim_status sim_net_time_conv(sim_net_t *n, int32_t which, int32_t reps, double *us);
 /* Use net (same grid; not owned, must outlive its use) as an extra CPR stage
    after the AMG V-cycles: the pressure residual left by stage P is normalised,
    the network's correction c, scaled by the minimal-residual step

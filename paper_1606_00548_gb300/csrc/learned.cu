@@ -348,12 +348,34 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
         int i = 0;
         for (int br = blockIdx.x; br < nbricks && !*abort; br += gridDim.x, i++) {
             const int ab = i & 1;
-            if (!mbar_wait(&bars.acc_full[ab], (i >> 1) & 1, abort, status, 8)) break;
-            tc_fence_after();
             const int bx = br % gx, r = br / gx, by = r % gy, bz = r / gy;
             const int x = bx * TC_M + (warp & 3) * 32 + lane, y0 = by * TC_TY, z0 = bz * TC_TZ;
+            if (MODE == 2 && x < d.nx) {   // the brick's ReLU masks into L2 while its MMAs run
+                for (int l = 0; l < TC_TY * TC_TZ; l++) {
+                    const int Y = y0 + l / TC_TZ, Z = z0 + l % TC_TZ;
+                    if (Y >= d.ny || Z >= d.nz) continue;
+                    const long pc = (long)x + (long)d.nxp * (Y + (long)d.ny * Z);
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(mask + pc * 4));
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(mask + (d.P + pc) * 4));
+                }
+            }
+            if (!mbar_wait(&bars.acc_full[ab], (i >> 1) & 1, abort, status, 8)) break;
+            tc_fence_after();
             const uint32_t acc = tb + lane_off + (uint32_t)(ab * TC_ACC);
             for (int l4 = 0; l4 < TC_TY * TC_TZ; l4 += 4) {
+                uint4 mk4[4][2];   // data gradient: the group's masks, loaded before the accumulators
+                if (MODE == 2) {
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        const int l = l4 + k, Y = y0 + l / TC_TZ, Z = z0 + l % TC_TZ;
+                        mk4[k][0] = mk4[k][1] = make_uint4(0u, 0u, 0u, 0u);
+                        if (x < d.nx && Y < d.ny && Z < d.nz) {
+                            const long pc = (long)x + (long)d.nxp * (Y + (long)d.ny * Z);
+                            mk4[k][0] = *(const uint4 *)(mask + pc * 4);
+                            mk4[k][1] = *(const uint4 *)(mask + (d.P + pc) * 4);
+                        }
+                    }
+                }
                 uint32_t v4[64];
                 tc_ld64(acc + (uint32_t)(l4 * 16), v4);   // four lines, one wait
 #pragma unroll
@@ -375,7 +397,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
                         for (int w = 0; w < 8; w++)
                             o[w] = pack_bf16(fmaxf(__uint_as_float(v[2 * w]), 0.f), fmaxf(__uint_as_float(v[2 * w + 1]), 0.f));
                     } else {
-                        const uint4 m0 = *(const uint4 *)(mask + pc * 4), m1 = *(const uint4 *)(mask + (d.P + pc) * 4);
+                        const uint4 m0 = mk4[k][0], m1 = mk4[k][1];
                         const uint32_t mk[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
 #pragma unroll
                         for (int w = 0; w < 8; w++)
@@ -973,6 +995,53 @@ sim_status sim_net_train_step(sim_net_t *n, const float *x_dev, const float *tar
     NET_LAUNCHED(n);
     if (pack_all(n) != SIM_OK) return n->err;
     if (loss) NET_CK(n, cudaMemcpyAsync(loss, n->dloss, sizeof(double), cudaMemcpyDeviceToHost, n->stream));
+    return net_status(n);
+}
+
+sim_status sim_net_time_conv(sim_net_t *n, int32_t which, int32_t reps, double *us) {
+    if (!n || !us || which < 0 || which > 2 || reps < 1) return SIM_EINVAL;
+    if (n->err != SIM_OK) return n->err;
+    if (!tc_attrs()) return net_fail(n, SIM_ECUDA, "convolution kernel attributes");
+    const size_t flush_bytes = 256u << 20;
+    void *flush = nullptr;
+    NET_CK(n, cudaMalloc(&flush, flush_bytes));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    sim_status st = SIM_OK;
+    double total = 0.0;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = SIM_ECUDA;
+    const int l = 1;   // hidden layer 2: act[1] -> act[2]
+    for (int r = 0; r < reps && st == SIM_OK; r++) {
+        if (cudaMemsetAsync(flush, r & 0xff, flush_bytes, n->stream) != cudaSuccess ||
+            cudaEventRecord(e0, n->stream) != cudaSuccess) { st = SIM_ECUDA; break; }
+        if (which == 0) {
+            conv_tc_kernel<0><<<tc_grid(n->d), TC_THREADS, TC_SMEM, n->stream>>>(
+                n->map_act[l], n->d, tc_bricks(n->d), n->wf[l], n->param + n->off_b[l], nullptr, n->act[l + 1], nullptr,
+                nullptr, n->dstat);
+        } else if (which == 1) {
+            wgrad_tc_kernel<<<n->wg_ctas, WG_THREADS, WG_SMEM, n->stream>>>(n->map_win[l], n->map_wg[0], n->d,
+                                                                           wg_bricks(n->d), n->wpart, n->dstat);
+            n->launches++;
+            wgrad_fold_kernel<<<sim_blocks(27 * 256), SIM_THREADS, 0, n->stream>>>(n->wg_ctas, CIN[l], COUT[l], n->wpart,
+                                                                                    n->grad + n->off_w[l]);
+        } else {
+            conv_tc_kernel<2><<<tc_grid(n->d), TC_THREADS, TC_SMEM, n->stream>>>(
+                n->map_g[0], n->d, tc_bricks(n->d), n->wb[l], nullptr, n->act[l], n->g1, nullptr, nullptr, n->dstat);
+        }
+        n->launches++;
+        float ms = 0.f;
+        if (cudaGetLastError() != cudaSuccess || cudaEventRecord(e1, n->stream) != cudaSuccess ||
+            cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            st = SIM_ECUDA;
+            break;
+        }
+        total += ms;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(n->stream);
+    cudaFree(flush);
+    if (st != SIM_OK) return net_fail(n, st, "sim_net_time_conv: CUDA error");
+    *us = 1e3 * total / reps;
     return net_status(n);
 }
 

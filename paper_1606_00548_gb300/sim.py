@@ -166,6 +166,7 @@ _SIGS = {
     "sim_net_loss_grad": ([_vp, _vp, _vp, _dp, C.POINTER(C.c_float)], C.c_int),
     "sim_net_train_step": ([_vp, _vp, _vp, C.c_float, _dp], C.c_int),
     "sim_net_last_error": ([_vp], C.c_char_p),
+    "sim_net_time_conv": ([_vp, C.c_int32, C.c_int32, _dp], C.c_int),
     "sim_set_learned_stage": ([_vp, _vp, C.c_int32], C.c_int),
     "sim_learned_pairs": ([_vp, C.c_int32, _vp, _vp], C.c_int),
     "sim_learned_fallbacks": ([_vp], C.c_int64),
@@ -274,6 +275,13 @@ class Net:
         self._check(self.L.sim_net_loss_grad(self.h, _ptrf(x_dev), _ptrf(t_dev), C.byref(loss),
                                              g.ctypes.data_as(C.POINTER(C.c_float))))
         return loss.value, g
+
+    def time_conv(self, which, reps=10):
+        """microseconds per launch of one convolution kernel (0 forward, 1 weight
+        gradient with its fold, 2 data gradient) of hidden layer 2"""
+        v = C.c_double()
+        self._check(self.L.sim_net_time_conv(self.h, int(which), int(reps), C.byref(v)))
+        return v.value
 
     def train_step(self, x_dev, t_dev, lr, want_loss=True):
         loss = C.c_double()
