@@ -423,6 +423,14 @@ const char *sim_net_last_error(sim_net_t *n);
    gradient buffers, which the call overwrites.  *us = average microseconds per
    launch; SIM_EINVAL for a bad which or reps < 1. */
 sim_status sim_net_time_conv(sim_net_t *n, int32_t which, int32_t reps, double *us);
+/* Testing hook for the convolutions' bounded waits (no paper counterpart): in
+   the next forward pass, CTA 0 of the first convolution does not copy staged
+   slab `slab` of its sequence (0 = the first) and does not arm its barrier, so
+   the MMA thread's wait for it gives up after about 2 s; the CTA then stops
+   its roles, lets its copies land, frees its tensor memory and sets the
+   status word, and that call returns SIM_ETIMEOUT (sticky for this net).  No
+   fault and no hang: every wait is bounded.  SIM_EINVAL for slab < 0. */
+sim_status sim_net_inject_stall(sim_net_t *n, int32_t slab);
 /* Use net (same grid; not owned, must outlive its use) as an extra CPR stage
    after the AMG V-cycles: the pressure residual left by stage P is normalised,
    the network's correction c, scaled by the minimal-residual step

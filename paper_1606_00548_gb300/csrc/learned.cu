@@ -105,7 +105,9 @@ __device__ __forceinline__ long act_elem_c(const Dims &d, int c, int ch) {
 // sets bit 0 (producer), 1 (MMA) or 3 (epilogue) of *status, stops all its
 // roles, lets its copies and MMAs in flight land, frees its tensor memory and
 // exits; a staging ring off the 128-byte alignment the TMA needs sets bit 2,
-// and nothing is copied or multiplied.
+// and nothing is copied or multiplied.  stall_slab >= 0 (a testing hook, -1
+// otherwise) makes CTA 0 skip the copy of that slab of its sequence without
+// arming its barrier, so that the MMA thread's bounded wait runs out.
 // ---------------------------------------------------------------------------
 constexpr int TC_M = 128;                                  // cells along x per output line
 constexpr int TC_TY = 2, TC_TZ = 8;                        // output lines per brick (y, z)
@@ -236,7 +238,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
                                                                 const float *__restrict__ bias,
                                                                 const uint32_t *__restrict__ mask,
                                                                 uint32_t *__restrict__ out, float *__restrict__ outf,
-                                                                const int *done, int *__restrict__ status) {
+                                                                const int *done, int *__restrict__ status,
+                                                                int stall_slab) {
     if (done != nullptr && *(volatile const int *)done) return;
     extern __shared__ uint8_t tc_raw[];
     __shared__ TcBars bars;
@@ -285,6 +288,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
             for (int s = 0; s < TC_SY; s++) {
                 const int slot = issued % TC_RING;
                 if (!mbar_wait(&bars.empty[slot], ((issued / TC_RING) & 1) ^ 1, abort, status, 1)) break;
+                if (blockIdx.x == 0 && issued == stall_slab) {   // testing hook: this slab is never copied
+                    issued++;
+                    continue;
+                }
                 mbar_expect(&bars.full[slot], 2 * TC_BOX);
                 for (int h = 0; h < 2; h++)
                     tma_load_5d(ring + slot * TC_SLOT + h * TC_HALF, &tin, 0, x0 / 8 - 1, y0 - 1 + s, z0 - 1, h,
@@ -422,7 +429,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
     }
     if (warp == 0 && lane == 0 && *abort) {
         for (int k = issued - TC_RING < 0 ? 0 : issued - TC_RING; k < issued; k++)
-            if (!mbar_drain(&bars.full[k % TC_RING], (k / TC_RING) & 1)) atomicOr(status, 1);
+            if (!(blockIdx.x == 0 && k == stall_slab) && !mbar_drain(&bars.full[k % TC_RING], (k / TC_RING) & 1))
+                atomicOr(status, 1);
     }
     tc_fence_before();
     __syncthreads();
@@ -673,6 +681,7 @@ struct sim_net {
     CUtensorMap map_win[NLAYER];         // act[0..3] with the weight gradient's input box
     CUtensorMap map_wg[2];               // g0, g1 with the weight gradient's output-gradient box
     int *dstat = nullptr;                // device status word of the convolutions (bounded waits)
+    int stall_once = -1;                 // testing hook: slab whose copy the next forward pass skips
     float *out = nullptr;                // [N]
     uint32_t *g0 = nullptr, *g1 = nullptr;   // BF16 [N][16] gradient buffers
     float *wpart = nullptr, *bpart = nullptr;
@@ -795,14 +804,17 @@ static bool tc_attrs() {
 static sim_status net_forward(sim_net_t *n, const int *done = nullptr) {
     if (!tc_attrs()) return net_fail(n, SIM_ECUDA, "convolution kernel attributes");
     const int grid = tc_grid(n->d), nb = tc_bricks(n->d);
+    const int stall = n->stall_once;
+    n->stall_once = -1;
     for (int l = 0; l < NLAYER; l++) {
         const float *bias = n->param + n->off_b[l];
         if (l + 1 < NLAYER)
             conv_tc_kernel<0><<<grid, TC_THREADS, TC_SMEM, n->stream>>>(n->map_act[l], n->d, nb, n->wf[l], bias, nullptr,
-                                                                        n->act[l + 1], nullptr, done, n->dstat);
+                                                                        n->act[l + 1], nullptr, done, n->dstat,
+                                                                        l == 0 ? stall : -1);
         else
             conv_tc_kernel<1><<<grid, TC_THREADS, TC_SMEM, n->stream>>>(n->map_act[l], n->d, nb, n->wf[l], bias, nullptr,
-                                                                        nullptr, n->out, done, n->dstat);
+                                                                        nullptr, n->out, done, n->dstat, -1);
         NET_LAUNCHED(n);
     }
     return SIM_OK;
@@ -833,7 +845,7 @@ static sim_status net_backward(sim_net_t *n, const float *target) {
         if (l > 0) {   // data gradient through layer l into the ReLU output of layer l-1
             conv_tc_kernel<2><<<tc_grid(n->d), TC_THREADS, TC_SMEM, n->stream>>>(
                 n->map_g[gcur == n->g0 ? 0 : 1], n->d, tc_bricks(n->d), n->wb[l], nullptr, n->act[l], gnext, nullptr,
-                nullptr, n->dstat);
+                nullptr, n->dstat, -1);
             NET_LAUNCHED(n);
             uint32_t *t = gcur; gcur = gnext; gnext = t;
         }
@@ -998,6 +1010,12 @@ sim_status sim_net_train_step(sim_net_t *n, const float *x_dev, const float *tar
     return net_status(n);
 }
 
+sim_status sim_net_inject_stall(sim_net_t *n, int32_t slab) {
+    if (!n || slab < 0) return SIM_EINVAL;
+    n->stall_once = slab;
+    return SIM_OK;
+}
+
 sim_status sim_net_time_conv(sim_net_t *n, int32_t which, int32_t reps, double *us) {
     if (!n || !us || which < 0 || which > 2 || reps < 1) return SIM_EINVAL;
     if (n->err != SIM_OK) return n->err;
@@ -1016,7 +1034,7 @@ sim_status sim_net_time_conv(sim_net_t *n, int32_t which, int32_t reps, double *
         if (which == 0) {
             conv_tc_kernel<0><<<tc_grid(n->d), TC_THREADS, TC_SMEM, n->stream>>>(
                 n->map_act[l], n->d, tc_bricks(n->d), n->wf[l], n->param + n->off_b[l], nullptr, n->act[l + 1], nullptr,
-                nullptr, n->dstat);
+                nullptr, n->dstat, -1);
         } else if (which == 1) {
             wgrad_tc_kernel<<<n->wg_ctas, WG_THREADS, WG_SMEM, n->stream>>>(n->map_win[l], n->map_wg[0], n->d,
                                                                            wg_bricks(n->d), n->wpart, n->dstat);
@@ -1025,7 +1043,7 @@ sim_status sim_net_time_conv(sim_net_t *n, int32_t which, int32_t reps, double *
                                                                                     n->grad + n->off_w[l]);
         } else {
             conv_tc_kernel<2><<<tc_grid(n->d), TC_THREADS, TC_SMEM, n->stream>>>(
-                n->map_g[0], n->d, tc_bricks(n->d), n->wb[l], nullptr, n->act[l], n->g1, nullptr, nullptr, n->dstat);
+                n->map_g[0], n->d, tc_bricks(n->d), n->wb[l], nullptr, n->act[l], n->g1, nullptr, nullptr, n->dstat, -1);
         }
         n->launches++;
         float ms = 0.f;

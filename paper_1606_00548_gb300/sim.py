@@ -167,6 +167,7 @@ _SIGS = {
     "sim_net_train_step": ([_vp, _vp, _vp, C.c_float, _dp], C.c_int),
     "sim_net_last_error": ([_vp], C.c_char_p),
     "sim_net_time_conv": ([_vp, C.c_int32, C.c_int32, _dp], C.c_int),
+    "sim_net_inject_stall": ([_vp, C.c_int32], C.c_int),
     "sim_set_learned_stage": ([_vp, _vp, C.c_int32], C.c_int),
     "sim_learned_pairs": ([_vp, C.c_int32, _vp, _vp], C.c_int),
     "sim_learned_fallbacks": ([_vp], C.c_int64),
@@ -275,6 +276,11 @@ class Net:
         self._check(self.L.sim_net_loss_grad(self.h, _ptrf(x_dev), _ptrf(t_dev), C.byref(loss),
                                              g.ctypes.data_as(C.POINTER(C.c_float))))
         return loss.value, g
+
+    def inject_stall(self, slab=0):
+        """testing hook: the next forward pass's first convolution skips one
+        staged copy, so its bounded wait runs out (SIM_ETIMEOUT)"""
+        self._check(self.L.sim_net_inject_stall(self.h, int(slab)))
 
     def time_conv(self, which, reps=10):
         """microseconds per launch of one convolution kernel (0 forward, 1 weight

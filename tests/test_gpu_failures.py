@@ -1,9 +1,10 @@
 """Failure handling of the CUDA path, with every failure made on the host:
 non-finite input state, Newton solves that fail and cut the time step (as the
 "(1)" cuts of the paper's Tables 2 and 4), a vanishing pivot in the coarsest
-AMG level, and restarting a run from a saved state.  Nothing here faults,
-traps or hangs the GPU: the library reports each condition through its
-status codes and the handle stays usable.
+AMG level, restarting a run from a saved state, and a tensor-core
+convolution whose staged copy never arrives.  Nothing here faults, traps or
+hangs the GPU: every wait is bounded, the library reports each condition
+through its status codes and the context stays usable.
 """
 import numpy as np
 import pytest
@@ -138,3 +139,37 @@ def test_vanishing_coarsest_pivot_is_reported(torch_cuda, decouple):
     g.clear_error()
     g.set_jacobian(J0)
     g.precond_setup()                           # the assembled Jacobian sets up normally
+
+
+def test_convolution_wait_that_runs_out_is_reported(torch_cuda):
+    """The tensor-core convolution's bounded waits: a staged copy that never
+    arrives (the testing hook skips it, arming nothing) makes the MMA thread's
+    wait give up after about 2 s; the CTA stops, frees its tensor memory and
+    the call returns SIM_ETIMEOUT.  The context stays usable: a fresh network
+    on the same grid then computes the same output as another one."""
+    import time
+    torch = torch_cuda
+    from paper_1606_00548_gb300.sim import SIM_ETIMEOUT, Net, SimError
+    nx, ny, nz = 64, 8, 8
+    N = nx * ny * nz
+    x = torch.randn(N * 4, dtype=torch.float32, device="cuda", generator=torch.Generator(device="cuda").manual_seed(1))
+    y = torch.empty(N, dtype=torch.float32, device="cuda")
+    net = Net(nx, ny, nz, seed=2)
+    net.inject_stall(0)
+    t0 = time.perf_counter()
+    with pytest.raises(SimError) as e:
+        net.forward(x, y)
+    waited = time.perf_counter() - t0
+    assert e.value.status == SIM_ETIMEOUT, str(e.value)
+    assert waited > 0.5, waited
+    print(f"stalled convolution reported after {waited:.2f} s: {e.value}")
+    net.close()
+    outs = []
+    for _ in range(2):
+        n2 = Net(nx, ny, nz, seed=2)
+        y2 = torch.empty(N, dtype=torch.float32, device="cuda")
+        n2.forward(x, y2)
+        torch.cuda.synchronize()
+        outs.append(y2.cpu().numpy())
+        n2.close()
+    assert np.isfinite(outs[0]).all() and np.array_equal(outs[0], outs[1])
