@@ -420,6 +420,7 @@ def run_ours(args):
     barrier(ws)
     clocks = sampler.stop() if sampler else None
     st1 = sim.stats()
+    report = sim.run_report()   # the timed handle's run so far (warm-up included), before the kernel studies
     t_dev = sum(e0.elapsed_time(e1) for e0, e1 in events) / 1e3
     newton = args.steps
     value, t_max = job_throughput(ws, N * newton, t_dev)
@@ -557,6 +558,8 @@ def run_ours(args):
             "fp64_probe_tflops": fp64_tflops,
             "phases_per_newton": {k: v / newton for k, v in phases.items()},
             "forms": forms,
+            "run_report": {"counters": report["counters"], "phases": report["phases"],
+                           "note": "sim_run_report of the timed handle: warm-up and timed Newton iterations"},
             "clocks": clocks,
             "cpu_baseline": cpu,
         }

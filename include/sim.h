@@ -345,6 +345,17 @@ sim_status sim_autotune_cached(sim_t *s, double dt, const char *json_path, int32
    vectors and the normalisation of the new one), as inside a restart cycle.
    *us = average microseconds per launch. */
 sim_status sim_time_op(sim_t *s, int32_t which, int32_t reps, double *us);
+/* Run report (no paper counterpart; the paper reports steps, Newton and
+   linear iterations and times per run): a JSON object with the grid, model,
+   options, the run's counters (time steps, failed steps, accepted substeps,
+   cuts, simulated days, Newton and linear iterations, linear solves that hit
+   their limit, kernel launches), each phase's device time summed over every
+   Newton call of the handle (microseconds, CUDA events) with its algorithmic
+   bytes and the GB/s they imply, the device memory held and the launch shapes.
+   buf receives the text with its terminating NUL when cap >= *len + 1;
+   otherwise the call returns SIM_EINVAL (not sticky) with *len set, so that
+   buf = NULL, cap = 0 queries the size. */
+sim_status sim_run_report(sim_t *s, char *buf, int64_t cap, int64_t *len);
 
 /* ---- ensemble (no paper counterpart) ----
    Independent simulators (e.g. geological realisations on grids of different

@@ -133,6 +133,7 @@ static void phase_update(sim_t *s, MemberStep &m, double solve_us) {
     if (nl_finish_solve(s, m.li, &fin, &m.si.phase) != SIM_OK) { m.st = s->err; m.finished = true; return; }
     m.si.newton_iterations++;
     m.si.linear_iterations += m.li.iterations;
+    s->run_lin_failures += !m.li.converged;
     m.l++;
     if (!fin) cut(s, m);
 }
@@ -155,7 +156,10 @@ static sim_status step_lockstep(sim_batch *b, const double *dt, sim_step_info *i
         for (int k : all) if (!ms[k].finished) live.push_back(k);
         if (live.empty()) break;
         auto t0 = std::chrono::steady_clock::now();
-        run_parallel(b, live, [&](int k) { phase_newton(b->members[k], ms[k]); });
+        {
+            NvtxRange range("batch_newton_phase");
+            run_parallel(b, live, [&](int k) { phase_newton(b->members[k], ms[k]); });
+        }
         auto t1 = std::chrono::steady_clock::now();
         b->t_newton += std::chrono::duration<double>(t1 - t0).count();
         std::vector<int> solve;
@@ -165,10 +169,16 @@ static sim_status step_lockstep(sim_batch *b, const double *dt, sim_step_info *i
         for (int k : solve) sm.push_back(b->members[k]);
         std::vector<sim_linear_info> li(solve.size());
         float ms_solve = 0.f;
-        cudaEventRecord(b->e0, b->stream);
-        const sim_status st = k_fgmres_batch(b->kb, sm.data(), (int)sm.size(), b->stream, li.data(), &b->msg);
-        cudaEventRecord(b->e1, b->stream);
-        if (st != SIM_OK || cudaEventSynchronize(b->e1) != cudaSuccess) {
+        sim_status st;
+        bool synced;
+        {
+            NvtxRange solve_range("batched_fgmres");
+            cudaEventRecord(b->e0, b->stream);
+            st = k_fgmres_batch(b->kb, sm.data(), (int)sm.size(), b->stream, li.data(), &b->msg);
+            cudaEventRecord(b->e1, b->stream);
+            synced = st == SIM_OK && cudaEventSynchronize(b->e1) == cudaSuccess;
+        }
+        if (st != SIM_OK || !synced) {
             batch_err = st != SIM_OK ? st : SIM_ECUDA;
             for (int k : solve) { ms[k].st = batch_err; ms[k].finished = true; }
             break;
@@ -190,6 +200,7 @@ static sim_status step_lockstep(sim_batch *b, const double *dt, sim_step_info *i
             if (cudaStreamSynchronize(s->stream) != cudaSuccess) m.st = SIM_ECUDA;
         }
         m.si.ok = m.st == SIM_OK;
+        run_record_step(s, m.si, m.st);
         if (infos) infos[k] = m.si;
         if (mst) mst[k] = m.st;
         if (first == SIM_OK && m.st != SIM_OK) first = m.st;

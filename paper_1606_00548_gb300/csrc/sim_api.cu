@@ -563,6 +563,7 @@ static double event_us(cudaEvent_t a, cudaEvent_t b) {
 
 // assemble and test CNV, with the assembly phase marked by pev[0], pev[1]
 static sim_status assemble_and_test(sim_t *s, double dt, double *cnv, double *wcnv, sim_phase_info *ph) {
+    NvtxRange range("assemble");
     SIM_CK(s, cudaEventRecord(s->pev[0], s->stream));
     if (k_assemble(s, dt) != SIM_OK) return s->err;
     if (k_cnv(s, dt, cnv, wcnv) != SIM_OK) return s->err;
@@ -581,6 +582,7 @@ static sim_status solve_and_update(sim_t *s, sim_linear_info *lin, bool *finite_
     const long n = (long)s->N * s->b;
     SIM_CK(s, cudaEventRecord(s->pev[1], s->stream));
     if (!s->precond_ready) {
+        NvtxRange range("cpr_setup");
         if (cpr_setup(s) != SIM_OK) return s->err;
         ph->setup_bytes += s->opt.precond == SIM_PRECOND_CPR ? bytes_setup(s)
                                                              : (double)s->N * s->b * s->b * 8 * 9;   // block Jacobi
@@ -595,7 +597,11 @@ static sim_status solve_and_update(sim_t *s, sim_linear_info *lin, bool *finite_
         if (k_norm2(s, s->bl, n, &bnorm) != SIM_OK) return s->err;
         if (forcing_term(s, *f, bnorm, &s->theta) != SIM_OK) return s->err;
     }
-    const sim_status st = k_linear_solve(s, s->bl, s->dx, lin);
+    sim_status st;
+    {
+        NvtxRange range("linear_solve");
+        st = k_linear_solve(s, s->bl, s->dx, lin);
+    }
     SIM_CK(s, cudaEventRecord(s->pev[3], s->stream));
     ph->solve_bytes += bytes_solve(s, *lin);
     const double theta_used = s->theta;
@@ -608,6 +614,7 @@ static sim_status solve_and_update(sim_t *s, sim_linear_info *lin, bool *finite_
         if (s->err == SIM_ENAN) { sim_clear_error(s); *finite_ok = false; return SIM_OK; }
         return s->err;
     }
+    NvtxRange range("update");
     int ok = 1;
     if (k_finite(s, s->dx, n, &ok) != SIM_OK) return s->err;
     *finite_ok = ok != 0;
@@ -632,13 +639,20 @@ sim_status sim_newton_step(sim_t *s, double dt, sim_newton_info *info) {
     double cnv, wcnv;
     if (assemble_and_test(s, dt, &cnv, &wcnv, &ni.phase) != SIM_OK) return s->err;
     ni.cnv = cnv;
-    if (cnv <= s->opt.newton_tol && wcnv <= s->opt.newton_tol) { ni.converged = 1; if (info) *info = ni; return SIM_OK; }
+    if (cnv <= s->opt.newton_tol && wcnv <= s->opt.newton_tol) {
+        ni.converged = 1;
+        phase_add(&s->run_phase, ni.phase);
+        if (info) *info = ni;
+        return SIM_OK;
+    }
     sim_linear_info li;
     bool fin = true;
     if (solve_and_update(s, &li, &fin, &ni.phase) != SIM_OK) return s->err;
     ni.newton_iterations = 1;
     ni.linear_iterations = li.iterations;
     ni.linear_failures = !li.converged;
+    s->run_lin_failures += !li.converged;
+    phase_add(&s->run_phase, ni.phase);
     if (info) *info = ni;
     return fin ? SIM_OK : SIM_ENAN;
 }
@@ -711,7 +725,16 @@ sim_status accept_step(sim_t *s, double dt) {
     SIM_CK(s, cudaMemcpyAsync(s->h_pinned, s->qtot, sizeof(double) * 3, cudaMemcpyDeviceToHost, s->stream));
     SIM_CK(s, cudaStreamSynchronize(s->stream));
     for (int c = 0; c < 3; c++) s->cum_well[c] += dt * s->h_pinned[c];
+    s->run_substeps++;
+    s->run_days += dt;
     return begin_step(s);
+}
+
+void run_record_step(sim_t *s, const sim_step_info &si, sim_status st) {
+    if (st == SIM_OK) s->run_steps++;
+    else s->run_failed_steps++;
+    s->run_cuts += si.cuts;
+    phase_add(&s->run_phase, si.phase);
 }
 
 extern "C" {
@@ -733,6 +756,7 @@ static int newton_solve(sim_t *s, double dt, sim_newton_info *ni) {
         ni->newton_iterations++;
         ni->linear_iterations += li.iterations;
         ni->linear_failures += !li.converged;
+        s->run_lin_failures += !li.converged;
         if (!fin) return 2;
     }
 }
@@ -744,6 +768,7 @@ sim_status sim_newton_solve(sim_t *s, double dt, sim_newton_info *info) {
     const int rc = newton_solve(s, dt, &ni);
     if (info) *info = ni;
     if (rc < 0) return s->err;
+    phase_add(&s->run_phase, ni.phase);
     return rc == 0 ? SIM_OK : (rc == 2 ? SIM_ENAN : SIM_ENOCONV_NEWTON);
 }
 
@@ -759,6 +784,7 @@ sim_status sim_accept_step(sim_t *s, double dt) {
 sim_status sim_step(sim_t *s, double dt, sim_step_info *info) {
     CHECK_HANDLE(s);
     if (!(dt > 0)) return sim_fail(s, SIM_EINVAL, "dt must be positive");
+    NvtxRange range("sim_step");
     sim_step_info si;
     memset(&si, 0, sizeof(si));
     double remaining = dt, h = dt;
@@ -784,6 +810,7 @@ sim_status sim_step(sim_t *s, double dt, sim_step_info *info) {
     }
     SIM_CK(s, cudaStreamSynchronize(s->stream));
     si.ok = st == SIM_OK;
+    run_record_step(s, si, st);
     if (info) *info = si;
     return st;
 }
@@ -1056,6 +1083,126 @@ sim_status sim_probe_fma_rates(double *fp64_fma_per_s, double *fp32_fma_per_s) {
     cudaFree(buf);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return sim_fail(nullptr, SIM_ECUDA, std::string("sim_probe_fma_rates: ") + cudaGetErrorString(e));
+    return SIM_OK;
+}
+
+// ---- run report ----------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+struct Json {
+    std::string out;
+    bool first = true;
+    void key(const char *k) {
+        if (!first) out += ", ";
+        first = false;
+        out += '"';
+        out += k;
+        out += "\": ";
+    }
+    void num(const char *k, double v, const char *fmt = "%.17g") {
+        char b[64];
+        snprintf(b, sizeof b, fmt, v);
+        key(k);
+        out += (v == v && v - v == 0.0) ? b : "null";
+    }
+    void integer(const char *k, long long v) {
+        key(k);
+        out += std::to_string(v);
+    }
+    void str(const char *k, const char *v) {
+        key(k);
+        out += '"';
+        out += v;
+        out += '"';
+    }
+    void open(const char *k) {
+        key(k);
+        out += '{';
+        first = true;
+    }
+    void close() {
+        out += '}';
+        first = false;
+    }
+};
+void phase_json(Json &j, const char *name, double us, double bytes) {
+    j.open(name);
+    j.num("us", us, "%.3f");
+    j.num("bytes", bytes, "%.0f");
+    j.num("achieved_gbs", us > 0 ? bytes / us / 1e3 : 0.0, "%.1f");
+    j.close();
+}
+}  // namespace
+
+extern "C" {
+
+sim_status sim_run_report(sim_t *s, char *buf, int64_t cap, int64_t *len) {
+    if (!s || !len || (cap > 0 && !buf) || cap < 0) return SIM_EINVAL;
+    const sim_options &o = s->opt;
+    Json j;
+    j.out = "{";
+    j.open("grid");
+    j.integer("nx", s->gd.nx);
+    j.integer("ny", s->gd.ny);
+    j.integer("nz", s->gd.nz);
+    j.integer("cells", s->N);
+    j.close();
+    j.str("model", s->fc.model == 3 ? "black_oil" : "oil_water");
+    j.integer("unknowns_per_cell", s->b);
+    j.integer("wells", s->nwells);
+    j.integer("rate_controlled_wells", s->nrate);
+    j.open("options");
+    j.str("precision", o.precision == SIM_PRECISION_MIXED ? "fp32_preconditioner" : "fp64");
+    j.str("krylov", o.krylov == SIM_KRYLOV_BICGSTAB ? "bicgstab" : "fgmres");
+    j.integer("gmres_m", o.gmres_m);
+    j.integer("gmres_max_restarts", o.gmres_max_restarts);
+    j.str("precond", o.precond == SIM_PRECOND_CPR ? "cpr" : o.precond == SIM_PRECOND_BJACOBI ? "block_jacobi" : "none");
+    j.integer("cpr_stages", o.cpr_stages);
+    j.str("decouple", o.decouple == SIM_DECOUPLE_ABF ? "abf" : "quasi_impes");
+    j.str("stage2", o.stage2 == SIM_STAGE2_ILU0_RB ? "ilu0_red_black" : "block_jacobi");
+    j.integer("amg_cycles", o.amg_cycles);
+    j.num("lin_tol", o.lin_tol);
+    j.num("newton_tol", o.newton_tol);
+    j.integer("newton_max", o.newton_max);
+    j.integer("max_cuts", o.max_cuts);
+    j.str("forcing", o.forcing == SIM_FORCING_EW1 ? "ew1" : o.forcing == SIM_FORCING_EW2 ? "ew2"
+                     : o.forcing == SIM_FORCING_EW3 ? "ew3" : "fixed");
+    j.integer("graphs", o.graphs);
+    j.integer("orth", o.orth);
+    j.close();
+    j.open("learned_stage");
+    j.integer("enabled", s->learned_on && s->net ? 1 : 0);
+    j.integer("fallbacks", s->learned_fallbacks);
+    j.close();
+    j.open("counters");
+    j.integer("time_steps", s->run_steps);
+    j.integer("failed_time_steps", s->run_failed_steps);
+    j.integer("substeps", s->run_substeps);
+    j.integer("cuts", s->run_cuts);
+    j.num("simulated_days", s->run_days);
+    j.integer("newton_iterations", s->newton_total);
+    j.integer("linear_iterations", s->linear_total);
+    j.integer("linear_solves_not_converged", s->run_lin_failures);
+    j.integer("kernel_launches", s->launches);
+    j.close();
+    const sim_phase_info &p = s->run_phase;
+    j.open("phases");
+    phase_json(j, "assemble", p.assemble_us, p.assemble_bytes);
+    phase_json(j, "setup", p.setup_us, p.setup_bytes);
+    phase_json(j, "solve", p.solve_us, p.solve_bytes);
+    phase_json(j, "update", p.update_us, p.update_bytes);
+    j.close();
+    j.integer("device_bytes", (long long)s->bytes);
+    j.open("launch_shapes");
+    j.integer("spmv_block", s->tune_spmv);
+    j.integer("amg_block", s->tune_amg);
+    j.integer("stage_block", s->tune_stage);
+    j.close();
+    j.out += '}';
+    *len = (int64_t)j.out.size();
+    if (cap < *len + 1) return SIM_EINVAL;   // not sticky: the caller retries with *len + 1 bytes
+    memcpy(buf, j.out.c_str(), j.out.size() + 1);
     return SIM_OK;
 }
 

@@ -7,6 +7,17 @@
 
 #include "../../include/sim.h"
 
+#include <nvtx3/nvToolsExt.h>
+
+// NVTX range over a host scope (a phase of a step); no cost unless a tool such
+// as a profiler attaches to NVTX
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 #define SIM_GRAV 9.80665
 #define SIM_DARCY (86400.0 * 9.869233e-16 * 1e5 / 1e-3)
 #define SIM_MAX_PVT 64
@@ -95,6 +106,12 @@ struct sim {
     int N = 0, b = 0;
     int64_t launches = 0, newton_total = 0, linear_total = 0;
     size_t bytes = 0;
+    // run totals for the run report: time steps (completed / failed), accepted
+    // substeps, cuts, linear solves that hit their limit, simulated days, and the
+    // per-phase device time and algorithmic bytes summed over every Newton call
+    int64_t run_steps = 0, run_failed_steps = 0, run_substeps = 0, run_cuts = 0, run_lin_failures = 0;
+    double run_days = 0.0;
+    sim_phase_info run_phase = {};
     std::vector<void *> allocs;
 
     // geometry
@@ -218,6 +235,8 @@ sim_status nl_prepare_solve(sim_t *s, sim_phase_info *ph);
 sim_status nl_finish_solve(sim_t *s, const sim_linear_info &li, bool *finite_ok, sim_phase_info *ph);
 sim_status nl_restore(sim_t *s);
 sim_status accept_step(sim_t *s, double dt);
+// a finished time step (sim_step or one member of a batch step) into the run totals
+void run_record_step(sim_t *s, const sim_step_info &si, sim_status st);
 
 // ---- krylov.cu ------------------------------------------------------------
 sim_status k_spmv(sim_t *s, const double *x, double *y);                 // y = J x

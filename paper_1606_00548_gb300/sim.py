@@ -136,6 +136,7 @@ _SIGS = {
     "sim_cumulative_well_mass": ([_vp, _dp], C.c_int),
     "sim_well_rates": ([_vp, _dp], C.c_int),
     "sim_time_op": ([_vp, C.c_int32, C.c_int32, _dp], C.c_int),
+    "sim_run_report": ([_vp, C.c_char_p, C.c_int64, C.POINTER(C.c_int64)], C.c_int),
     "sim_perforations": ([_vp], C.c_int32),
     "sim_get_well_bhp": ([_vp, _dp], C.c_int),
     "sim_set_well_bhp": ([_vp, _dp], C.c_int),
@@ -488,6 +489,15 @@ class Simulator:
         us = C.c_double()
         _check(self.h, self.L.sim_time_op(self.h, int(which), int(reps), C.byref(us)))
         return us.value
+
+    def run_report(self):
+        """the handle's JSON run report (counters, per-phase device time and bytes), parsed"""
+        import json
+        n = C.c_int64(0)
+        self.L.sim_run_report(self.h, None, 0, C.byref(n))
+        buf = C.create_string_buffer(n.value + 1)
+        _check(self.h, self.L.sim_run_report(self.h, buf, n.value + 1, C.byref(n)))
+        return json.loads(buf.value.decode())
 
     def well_rates(self):
         q = np.zeros(3); _check(self.h, self.L.sim_well_rates(self.h, q.ctypes.data_as(_dp))); return q

@@ -2,7 +2,7 @@
 non-finite input state, Newton solves that fail and cut the time step (as the
 "(1)" cuts of the paper's Tables 2 and 4), a vanishing pivot in the coarsest
 AMG level, restarting a run from a saved state, and a tensor-core
-convolution whose staged copy never arrives.  Nothing here faults, traps or
+convolution whose staged copy never arrives; the run report counts the run.  Nothing here faults, traps or
 hangs the GPU: every wait is bounded, the library reports each condition
 through its status codes and the context stays usable.
 """
@@ -173,3 +173,27 @@ def test_convolution_wait_that_runs_out_is_reported(torch_cuda):
         outs.append(y2.cpu().numpy())
         n2.close()
     assert np.isfinite(outs[0]).all() and np.array_equal(outs[0], outs[1])
+
+
+def test_run_report_counts_the_run(torch_cuda):
+    """The JSON run report's counters and phase times are the sums of what the
+    step calls reported, for a run with cuts (a Newton limit of 4)."""
+    from paper_1606_00548_gb300.sim import Simulator
+    case = synth.quarter_five_spot_20x20x5(nsteps=2, dt=5.0)
+    g = Simulator(case, newton_max=4)
+    infos = [g.step(dt)[1] for dt in case["dt"]]
+    rep = g.run_report()
+    c = rep["counters"]
+    assert c["time_steps"] == sum(i.ok for i in infos)
+    assert c["cuts"] == sum(i.cuts for i in infos) and c["cuts"] > 0
+    assert c["substeps"] == sum(i.substeps for i in infos)
+    assert c["newton_iterations"] == sum(i.newton_iterations for i in infos)
+    assert c["linear_iterations"] == sum(i.linear_iterations for i in infos)
+    assert abs(c["simulated_days"] - sum(case["dt"][:len(infos)])) < 1e-9
+    assert c["kernel_launches"] == g.stats().kernel_launches
+    for ph in ("assemble", "setup", "solve", "update"):
+        us = sum(getattr(i.phase, ph + "_us") for i in infos)
+        assert abs(rep["phases"][ph]["us"] - us) <= 1e-6 * max(us, 1.0) + 1e-3, ph
+        assert rep["phases"][ph]["bytes"] > 0
+    assert rep["grid"]["cells"] == g.N and rep["options"]["newton_max"] == 4
+    print("run report:", rep["counters"], {k: v["achieved_gbs"] for k, v in rep["phases"].items()})
