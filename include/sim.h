@@ -185,6 +185,11 @@ typedef struct {
 typedef struct {
     int32_t cuts, newton_iterations, linear_iterations, substeps, ok;
     sim_phase_info phase;
+    /* mass-balance error of the step (Eq. 3, conservation): the largest over its
+       accepted substeps and the components c of |M_c(end) - M_c(start) - dt q_c|
+       / sum_c M_c(end), with M the component masses in place and q the wells'
+       net mass rate into the reservoir */
+    double mb_error;
 } sim_step_info;
 
 typedef struct {

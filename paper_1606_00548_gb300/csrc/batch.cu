@@ -117,6 +117,7 @@ static void phase_newton(sim_t *s, MemberStep &m) {
             if (accept_step(s, m.h) != SIM_OK) { m.st = s->err; m.finished = true; break; }
             m.remaining -= m.h;
             m.si.substeps++;
+            m.si.mb_error = fmax(m.si.mb_error, s->last_mb);
             m.l = 0;
             continue;
         }

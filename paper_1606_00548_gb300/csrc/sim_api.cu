@@ -369,11 +369,18 @@ sim_status sim_create(const sim_grid *g, const sim_rock *r, const sim_fluid *f, 
 // ---------------------------------------------------------------------------
 // state
 // ---------------------------------------------------------------------------
-static sim_status begin_step(sim_t *s) {
+// the current state becomes the start of a step; m_known: its component
+// masses when the caller has them, else they are computed here
+static sim_status begin_step(sim_t *s, const double *m_known = nullptr) {
     const long n = (long)s->N * s->b;
     SIM_CK(s, cudaMemcpyAsync(s->x_old, s->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->stream));
     SIM_CK(s, cudaMemcpyAsync(s->ph_old, s->ph, s->N, cudaMemcpyDeviceToDevice, s->stream));
     if (s->nwells) SIM_CK(s, cudaMemcpyAsync(s->wp_old, s->wp, sizeof(double) * s->nwells, cudaMemcpyDeviceToDevice, s->stream));
+    if (m_known) {
+        for (int c = 0; c < 3; c++) s->m_start[c] = m_known[c];
+    } else if (k_component_mass(s, s->m_start) != SIM_OK) {
+        return s->err;
+    }
     return k_accumulation(s, s->x, s->ph, s->mold);
 }
 
@@ -724,10 +731,21 @@ sim_status nl_restore(sim_t *s) {
 sim_status accept_step(sim_t *s, double dt) {
     SIM_CK(s, cudaMemcpyAsync(s->h_pinned, s->qtot, sizeof(double) * 3, cudaMemcpyDeviceToHost, s->stream));
     SIM_CK(s, cudaStreamSynchronize(s->stream));
-    for (int c = 0; c < 3; c++) s->cum_well[c] += dt * s->h_pinned[c];
+    double q[3], m[3];
+    for (int c = 0; c < 3; c++) q[c] = s->h_pinned[c];
+    for (int c = 0; c < 3; c++) s->cum_well[c] += dt * q[c];
+    // mass balance of the substep: the masses in place against the start's plus the wells' inflow
+    if (k_component_mass(s, m) != SIM_OK) return s->err;
+    double total = 0.0, worst = 0.0;
+    for (int c = 0; c < s->b; c++) {
+        total += m[c];
+        worst = fmax(worst, fabs(m[c] - s->m_start[c] - dt * q[c]));
+    }
+    s->last_mb = total > 0.0 ? worst / total : worst;
+    s->run_max_mb = fmax(s->run_max_mb, s->last_mb);
     s->run_substeps++;
     s->run_days += dt;
-    return begin_step(s);
+    return begin_step(s, m);
 }
 
 void run_record_step(sim_t *s, const sim_step_info &si, sim_status st) {
@@ -801,6 +819,7 @@ sim_status sim_step(sim_t *s, double dt, sim_step_info *info) {
             if (accept_step(s, h) != SIM_OK) return s->err;
             remaining -= h;
             si.substeps++;
+            si.mb_error = fmax(si.mb_error, s->last_mb);
         } else {
             if (nl_restore(s) != SIM_OK) return s->err;
             si.cuts++;
@@ -1184,6 +1203,7 @@ sim_status sim_run_report(sim_t *s, char *buf, int64_t cap, int64_t *len) {
     j.integer("newton_iterations", s->newton_total);
     j.integer("linear_iterations", s->linear_total);
     j.integer("linear_solves_not_converged", s->run_lin_failures);
+    j.num("max_mass_balance_error", s->run_max_mb, "%.3e");
     j.integer("kernel_launches", s->launches);
     j.close();
     const sim_phase_info &p = s->run_phase;

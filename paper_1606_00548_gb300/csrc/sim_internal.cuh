@@ -110,8 +110,10 @@ struct sim {
     // substeps, cuts, linear solves that hit their limit, simulated days, and the
     // per-phase device time and algorithmic bytes summed over every Newton call
     int64_t run_steps = 0, run_failed_steps = 0, run_substeps = 0, run_cuts = 0, run_lin_failures = 0;
-    double run_days = 0.0;
+    double run_days = 0.0, run_max_mb = 0.0;
     sim_phase_info run_phase = {};
+    double m_start[3] = {0.0, 0.0, 0.0};   // component masses of the current step's start
+    double last_mb = 0.0;                   // mass-balance error of the last accepted substep
     std::vector<void *> allocs;
 
     // geometry

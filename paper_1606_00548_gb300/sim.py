@@ -97,7 +97,7 @@ class sim_newton_info(C.Structure):
 
 class sim_step_info(C.Structure):
     _fields_ = [("cuts", C.c_int32), ("newton_iterations", C.c_int32), ("linear_iterations", C.c_int32),
-                ("substeps", C.c_int32), ("ok", C.c_int32), ("phase", sim_phase_info)]
+                ("substeps", C.c_int32), ("ok", C.c_int32), ("phase", sim_phase_info), ("mb_error", C.c_double)]
 
 
 class sim_stats(C.Structure):

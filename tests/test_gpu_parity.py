@@ -359,3 +359,30 @@ def test_time_op_leaves_state_and_reports_time(torch_cuda):
     assert 0.0 < t_spmv < 1e5 and 0.0 < t_prec < 1e5
     st, i2 = g.linear_solve(rhs, x2)
     assert i1.iterations == i2.iterations and torch.equal(x1, x2)
+
+
+@pytest.mark.parametrize("which", ["quarter_five_spot", "black_oil_small"])
+def test_step_reports_its_mass_balance_error(torch_cuda, which):
+    """sim_step_info.mb_error: |M_c(end) - M_c(start) - dt q_c| / sum_c M_c, the
+    conservation of Eq. (3) over the step.  With CNV at 1e-10 it stays near
+    that level, and for a step without cuts it equals what the component
+    masses and the cumulative well masses of the API give."""
+    from paper_1606_00548_gb300.sim import Simulator
+    if which == "quarter_five_spot":
+        case = synth.quarter_five_spot_20x20x5(nsteps=3)
+    else:
+        case = synth.black_oil_case(nx=24, ny=24, nz=6, nsteps=3, dt=10.0, seed=46)
+    g = Simulator(case)
+    m0, c0 = np.array(g.component_mass()), np.array(g.cumulative_well_mass())
+    worst = 0.0
+    for dt in case["dt"]:
+        st, info = g.step(dt)
+        assert st == 0
+        m1, c1 = np.array(g.component_mass()), np.array(g.cumulative_well_mass())
+        assert 0.0 < info.mb_error <= 1e-9, info.mb_error
+        if info.substeps == 1:
+            ref = np.abs((m1 - m0) - (c1 - c0))[:g.b].max() / m1[:g.b].sum()
+            assert abs(info.mb_error - ref) <= 1e-6 * ref + 1e-15, (info.mb_error, ref)
+        worst = max(worst, info.mb_error)
+        m0, c0 = m1, c1
+    assert g.run_report()["counters"]["max_mass_balance_error"] == pytest.approx(worst, rel=1e-3)
