@@ -475,6 +475,13 @@ int64_t sim_learned_fallbacks(sim_t *s);
    and CUDA events; the roofline of the FP64-bound kernels is taken against
    the FP64 rate.  Allocates a small scratch buffer; synchronises the device. */
 sim_status sim_probe_fma_rates(double *fp64_fma_per_s, double *fp32_fma_per_s);
+/* The FP64 pipe's rate per clock: the best FP64 shape of the probe above,
+   with the SM clock it ran at (clock64 cycles against %globaltimer
+   nanoseconds over each block's loop, median over blocks).  *fma_per_s: FMAs
+   per second; *sm_mhz: that clock; *fma_per_clk_per_sm = fma_per_s / (SMs x
+   clock), the measured FMAs per clock per SM, which times the SMs and the
+   clock of a run gives that run's FP64 peak. */
+sim_status sim_probe_fp64_pipe(double *fma_per_s, double *sm_mhz, double *fma_per_clk_per_sm);
 
 const char *sim_last_error(sim_t *s);   /* s may be NULL: last create error */
 void sim_clear_error(sim_t *s);

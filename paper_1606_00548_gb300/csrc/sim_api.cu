@@ -47,8 +47,18 @@ namespace {
 // NC independent FMA chains per thread, no memory traffic except one store
 // per thread; each chain has its own multiplier so no two chains share all
 // their operands
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// stamps (when not null): per block, SM clock cycles and global-timer
+// nanoseconds between the first thread's start and end of the loop
 template <typename T, int NC>
-__global__ void fma_probe_kernel(T *out, int iters) {
+__global__ void fma_probe_kernel(T *out, int iters, long long *stamps = nullptr) {
+    long long c0 = 0;
+    unsigned long long n0 = 0;
+    if (stamps && threadIdx.x == 0) { c0 = clock64(); n0 = global_ns(); }
     T a[NC], m[NC];
 #pragma unroll
     for (int c = 0; c < NC; c++) { a[c] = threadIdx.x * (T)1e-3 + (T)c; m[c] = (T)0.9999999 - (T)c * (T)1e-9; }
@@ -61,15 +71,19 @@ __global__ void fma_probe_kernel(T *out, int iters) {
 #pragma unroll
     for (int c = 0; c < NC; c++) t += a[c];
     out[blockIdx.x * blockDim.x + threadIdx.x] = t;
+    if (stamps && threadIdx.x == 0) {
+        stamps[2 * blockIdx.x] = clock64() - c0;
+        stamps[2 * blockIdx.x + 1] = (long long)(global_ns() - n0);
+    }
 }
 // FMA rate of one launch shape: iters x NC FMAs per thread over the grid
 template <typename T, int NC>
-static double probe_rate(T *buf, int blocks, int threads, int iters) {
+static double probe_rate(T *buf, int blocks, int threads, int iters, long long *stamps = nullptr) {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0); cudaEventCreate(&e1);
     fma_probe_kernel<T, NC><<<blocks, threads>>>(buf, 16);
     cudaEventRecord(e0);
-    fma_probe_kernel<T, NC><<<blocks, threads>>>(buf, iters);
+    fma_probe_kernel<T, NC><<<blocks, threads>>>(buf, iters, stamps);
     cudaEventRecord(e1);
     cudaEventSynchronize(e1);
     float ms = 0.f;
@@ -1102,6 +1116,44 @@ sim_status sim_probe_fma_rates(double *fp64_fma_per_s, double *fp32_fma_per_s) {
     cudaFree(buf);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return sim_fail(nullptr, SIM_ECUDA, std::string("sim_probe_fma_rates: ") + cudaGetErrorString(e));
+    return SIM_OK;
+}
+
+sim_status sim_probe_fp64_pipe(double *fma_per_s, double *sm_mhz, double *fma_per_clk_per_sm) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return sim_fail(nullptr, SIM_ECUDA, "sim_probe_fp64_pipe: no CUDA device");
+    const int threads = 256;
+    double best = 0.0, best_mhz = 0.0;
+    void *buf = nullptr, *st = nullptr;
+    if (cudaMalloc(&buf, sizeof(double) * sms * 8 * threads) != cudaSuccess ||
+        cudaMalloc(&st, sizeof(long long) * 2 * sms * 8) != cudaSuccess) {
+        cudaFree(buf);
+        return sim_fail(nullptr, SIM_ENOMEM, "sim_probe_fp64_pipe: allocation failed");
+    }
+    std::vector<long long> h(2 * sms * 8);
+    for (int bps : {4, 8}) {
+        const int blocks = sms * bps;
+        for (int nc : {8, 16}) {
+            const double r = nc == 8 ? probe_rate<double, 8>((double *)buf, blocks, threads, 8192, (long long *)st)
+                                     : probe_rate<double, 16>((double *)buf, blocks, threads, 4096, (long long *)st);
+            if (cudaMemcpy(h.data(), st, sizeof(long long) * 2 * blocks, cudaMemcpyDeviceToHost) != cudaSuccess) break;
+            std::vector<double> mhz;
+            for (int k = 0; k < blocks; k++)
+                if (h[2 * k + 1] > 0) mhz.push_back(1e3 * (double)h[2 * k] / (double)h[2 * k + 1]);
+            if (mhz.empty() || r <= best) continue;
+            std::nth_element(mhz.begin(), mhz.begin() + mhz.size() / 2, mhz.end());
+            best = r;
+            best_mhz = mhz[mhz.size() / 2];
+        }
+    }
+    cudaFree(buf);
+    cudaFree(st);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return sim_fail(nullptr, SIM_ECUDA, std::string("sim_probe_fp64_pipe: ") + cudaGetErrorString(e));
+    if (fma_per_s) *fma_per_s = best;
+    if (sm_mhz) *sm_mhz = best_mhz;
+    if (fma_per_clk_per_sm) *fma_per_clk_per_sm = best_mhz > 0 ? best / (sms * best_mhz * 1e6) : 0.0;
     return SIM_OK;
 }
 

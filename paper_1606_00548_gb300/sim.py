@@ -148,6 +148,7 @@ _SIGS = {
     "sim_cnv_noalloc": ([C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double, C.c_int32,
                          _vp, _vp, _dp, C.c_double, _vp, _vp], C.c_int),
     "sim_probe_fma_rates": ([_dp, _dp], C.c_int),
+    "sim_probe_fp64_pipe": ([_dp, _dp, _dp], C.c_int),
     "sim_autotune": ([_vp, C.c_double], C.c_int),
     "sim_autotune_cached": ([_vp, C.c_double, C.c_char_p, C.POINTER(C.c_int32)], C.c_int),
     "sim_batch_create": ([C.c_int32, C.POINTER(_vp), C.c_int32, C.POINTER(_vp)], C.c_int),
@@ -638,3 +639,11 @@ def sim_probe_fma_rates():
     a = C.c_double(); b = C.c_double()
     _check(None, L.sim_probe_fma_rates(C.byref(a), C.byref(b)))
     return a.value, b.value
+
+
+def sim_probe_fp64_pipe():
+    """(FP64 FMAs per second, SM MHz during the probe, FMAs per clock per SM)"""
+    L = load()
+    a, b, c = C.c_double(), C.c_double(), C.c_double()
+    _check(None, L.sim_probe_fp64_pipe(C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
