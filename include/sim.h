@@ -180,6 +180,9 @@ typedef struct {
     int32_t linear_failures;
     double cnv;
     sim_phase_info phase;
+    /* final true relative residual ||b - J dx|| / ||b|| of the linear solve
+       (the largest over the solves of a sim_newton_solve call); 0 without a solve */
+    double lin_residual;
 } sim_newton_info;
 
 typedef struct {

@@ -672,6 +672,7 @@ sim_status sim_newton_step(sim_t *s, double dt, sim_newton_info *info) {
     ni.newton_iterations = 1;
     ni.linear_iterations = li.iterations;
     ni.linear_failures = !li.converged;
+    ni.lin_residual = li.b_norm > 0 ? li.r_norm / li.b_norm : 0.0;
     s->run_lin_failures += !li.converged;
     phase_add(&s->run_phase, ni.phase);
     if (info) *info = ni;
@@ -788,6 +789,7 @@ static int newton_solve(sim_t *s, double dt, sim_newton_info *ni) {
         ni->newton_iterations++;
         ni->linear_iterations += li.iterations;
         ni->linear_failures += !li.converged;
+        ni->lin_residual = fmax(ni->lin_residual, li.b_norm > 0 ? li.r_norm / li.b_norm : 0.0);
         s->run_lin_failures += !li.converged;
         if (!fin) return 2;
     }

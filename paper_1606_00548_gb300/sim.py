@@ -92,7 +92,8 @@ class sim_phase_info(C.Structure):
 
 class sim_newton_info(C.Structure):
     _fields_ = [("newton_iterations", C.c_int32), ("linear_iterations", C.c_int32), ("converged", C.c_int32),
-                ("linear_failures", C.c_int32), ("cnv", C.c_double), ("phase", sim_phase_info)]
+                ("linear_failures", C.c_int32), ("cnv", C.c_double), ("phase", sim_phase_info),
+                ("lin_residual", C.c_double)]
 
 
 class sim_step_info(C.Structure):
