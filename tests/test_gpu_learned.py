@@ -170,3 +170,28 @@ def test_learned_stage_gain_is_measured(torch_cuda, capsys):
         print(f"learned stage: {with_stage['iterations']} iterations against {without['iterations']} without it "
               f"(FP32 CPR); fallback to plain CPR engaged: {with_stage['fallbacks'] > 0}")
     assert with_stage["fallbacks"] > 0 or with_stage["iterations"] <= without["iterations"] + 1
+
+
+def test_convolution_timing_call(torch_cuda):
+    """sim_net_time_conv times each convolution kernel (forward, weight
+    gradient, data gradient), leaves the network usable with the same outputs,
+    and rejects a bad kernel index without making the error sticky."""
+    torch = torch_cuda
+    from paper_1606_00548_gb300.sim import SIM_EINVAL, Net, SimError
+    nx, ny, nz = 40, 6, 9
+    N = nx * ny * nz
+    net = Net(nx, ny, nz, seed=7)
+    x = torch.randn(N * 4, dtype=torch.float32, device="cuda", generator=torch.Generator(device="cuda").manual_seed(2))
+    y0 = torch.empty(N, dtype=torch.float32, device="cuda")
+    y1 = torch.empty_like(y0)
+    net.forward(x, y0)
+    for which in (0, 1, 2):
+        us = net.time_conv(which, 2)
+        assert 0.0 < us < 1e6, (which, us)
+    with pytest.raises(SimError) as e:
+        net.time_conv(3, 1)
+    assert e.value.status == SIM_EINVAL
+    net.forward(x, y1)
+    torch.cuda.synchronize()
+    assert torch.equal(y0, y1)
+    net.close()
