@@ -366,7 +366,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
                     asm volatile("prefetch.global.L2 [%0];" ::"l"(mask + (d.P + pc) * 4));
                 }
             }
-            if (!mbar_wait(&bars.acc_full[ab], (i >> 1) & 1, abort, status, 8)) break;
+            const bool okw = mbar_wait(&bars.acc_full[ab], (i >> 1) & 1, abort, status, 8);
+            if (!__all_sync(0xffffffffu, okw)) break;   // the warp's lanes leave together
             tc_fence_after();
             const uint32_t acc = tb + lane_off + (uint32_t)(ab * TC_ACC);
             for (int l4 = 0; l4 < TC_TY * TC_TZ; l4 += 4) {
@@ -502,6 +503,7 @@ __global__ void __launch_bounds__(WG_THREADS, 2) wgrad_tc_kernel(const __grid_co
     const int mrow = lane & 7, mat = lane >> 3;
     const uint32_t s_in = smem_addr(sin), s_g = smem_addr(sg);
     int it = 0;
+    bool in_flight = false;   // thread 0: the current brick's copies were started and not yet waited for
     for (int br = blockIdx.x; br < nbricks && !*abort; br += gridDim.x, it++) {
         const int bx = br % gx, r = br / gx, y = r % d.ny, bz = r / d.ny;
         const int x0 = bx * TC_M, z0 = bz * WG_TZ;
@@ -512,8 +514,11 @@ __global__ void __launch_bounds__(WG_THREADS, 2) wgrad_tc_kernel(const __grid_co
                 for (int h = 0; h < 2; h++)
                     tma_load_5d(sin + (s * 2 + h) * WG_IBOX, &tin, 0, x0 / 8 - 1, y - 1 + s, z0 - 1, h, &bar);
             for (int h = 0; h < 2; h++) tma_load_5d(sg + h * WG_GBOX, &tg, 0, x0 / 8, y, z0, h, &bar);
+            in_flight = true;
         }
-        if (!mbar_wait(&bar, it & 1, abort, status, 16)) break;
+        const bool ok = mbar_wait(&bar, it & 1, abort, status, 16);
+        if (tid == 0 && ok) in_flight = false;
+        if (__syncthreads_or(!ok)) break;   // every thread leaves together: no barrier below waits on one that left
         for (int zo = 0; zo < WG_TZ; zo++) {
             for (int xk = 0; xk < TC_M; xk += 16) {
                 // gradient fragment (B, 16 cells x 16 outputs): matrices (plane 0, cells 0-7), (0, 8-15), (1, 0-7), (1, 8-15)
@@ -538,7 +543,7 @@ __global__ void __launch_bounds__(WG_THREADS, 2) wgrad_tc_kernel(const __grid_co
         }
         __syncthreads();   // every warp is done with the buffers before the next brick's copies
     }
-    if (tid == 0 && *abort && !mbar_drain(&bar, it & 1)) atomicOr(status, 16);
+    if (tid == 0 && in_flight && !mbar_drain(&bar, it & 1)) atomicOr(status, 16);
     // partial of this CTA: [27][16 ci][16 co]
     const int g = lane >> 2, t4 = lane & 3;
 #pragma unroll
