@@ -17,7 +17,9 @@
   identity, so the pressure row of every decoupled diagonal block is e_0;
 * CPR-FPF: the three-stage operator is the composition
   z = x0 + M_2 (r - J x0), x0 = stage F of L r, where M_2 is the two-stage
-  operator on the same hierarchy (every stage is linear in its input).
+  operator on the same hierarchy (every stage is linear in its input);
+* stage P with m V-cycles works on the residual the previous cycles leave:
+  the applications' successive differences shrink geometrically.
 """
 import numpy as np
 import pytest
@@ -294,3 +296,28 @@ def test_natural_ilu0_reproduces_pattern(oracle_lib, name, case, dt):
     assert np.abs((M - Ad)[mask]).max() <= 1e-10 * np.abs(Ad).max()
     # the factors are lower / upper in the natural order
     assert not np.tril(Um).any() and not np.triu(Lm).any()
+
+
+@pytest.mark.parametrize("name,case,dt", [
+    ("ow", synth.oil_water_case(nx=10, ny=8, nz=4, sigma=1.0, seed=23), 1.0),
+    ("bo", synth.black_oil_case(nx=10, ny=8, nz=4, seed=24), 10.0)])
+def test_stage_p_cycles_work_on_the_residual_they_leave(oracle_lib, name, case, dt):
+    """Stage P with m V-cycles: e_{m+1} = e_m + V(f - A_p e_m).  The CPR
+    application is affine in e, so the differences z_{m+1} - z_m = K E^m V f
+    (E = I - V A_p) shrink geometrically at the V-cycle's contraction rate
+    toward the application with the exact pressure solve.  A later cycle on the
+    original f would give equal differences, a sign error in the residual
+    growing ones.  Initial state of a physical system; hierarchy of 3 levels."""
+    import oracle
+    r = np.random.default_rng(9).standard_normal(case["nx"] * case["ny"] * case["nz"] * (2 if case["model"] == 2 else 3))
+    zs = []
+    for m in range(1, 8):
+        o = oracle.Oracle(case, amg_cycles=m, amg_coarse_max=16)
+        o.assemble(dt)
+        zs.append(o.precond_apply(r))
+        if m == 1:
+            assert len(o.amg_levels()) >= 3
+    d = np.array([np.linalg.norm(zs[k + 1] - zs[k]) for k in range(len(zs) - 1)])
+    assert d[0] > 1e-6 * np.linalg.norm(zs[0])          # the second cycle does something
+    ratios = d[1:] / d[:-1]
+    assert np.all(ratios > 0.2) and np.all(ratios < 0.85), ratios
